@@ -1,0 +1,267 @@
+"""FP64 CPU oracle for the grad-h SPH neighbour loop (GANDALF, arXiv:1709.04488).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The product path (the
+CUDA library ``paper_1709_04488_gb300`` and its binding) never imports, links or
+calls it, and it imports nothing from the product package.
+
+The arithmetic lives in ``sph_oracle.c`` (plain C, FP64, brute-force O(N^2)
+neighbour search, each function citing the paper's equation).  This module is
+the ctypes marshalling around it plus the analytic reference solutions used as
+pins (``riemann.py``).
+
+Parity status per function (see the pins in ``tests/test_oracle_pins.py``):
+  kernel f, f', W, dW/dr, dW/dh ........ pinned (normalisation, finite differences)
+  density / h solve / Omega ............ pinned (lattice neighbour count, <1 % lattice
+                                         offset, Eq. HRHO residual, continuity-equation
+                                         and energy-gradient identities)
+  forces (pressure) .................... pinned (exact gradient of the thermal energy)
+  forces (viscosity, conductivity) ..... pinned (pairwise antisymmetry, energy balance,
+                                         v=0 and uniform-u special cases)
+  KDK step ............................. pinned (free translation, Sod analytic window)
+  neighbour lists ...................... pinned (scipy cKDTree on the same points)
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sph_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+OK, EINVAL, EBOX, ENOCONV, ENOMEM = 0, -1, -2, -3, -9
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(
+            ["gcc", "-O3", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-std=c11",
+             "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Params(C.Structure):
+    _fields_ = [
+        ("periodic", C.c_int),
+        ("box_lo", C.c_double * 3),
+        ("box_len", C.c_double * 3),
+        ("eos", C.c_int),
+        ("gamma", C.c_double),
+        ("cs_iso", C.c_double),
+        ("eta", C.c_double),
+        ("alpha_av", C.c_double),
+        ("beta_av", C.c_double),
+        ("alpha_ac", C.c_double),
+        ("c_cfl", C.c_double),
+        ("h_tol", C.c_double),
+        ("h_max_iter", C.c_int),
+        ("use_grid", C.c_int),
+    ]
+
+
+_DP = C.POINTER(C.c_double)
+_IP = C.POINTER(C.c_int32)
+
+_FIELDS_D = ["x", "y", "z", "vx", "vy", "vz", "u", "m", "h",
+             "rho", "omega", "P", "c", "ax", "ay", "az", "du", "vsig"]
+_FIELDS_I = ["nngb", "iters"]
+
+
+class _State(C.Structure):
+    _fields_ = [(f, _DP) for f in _FIELDS_D] + [(f, _IP) for f in _FIELDS_I]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        for name in ("orc_f", "orc_df"):
+            fn = getattr(L, name)
+            fn.restype = C.c_double
+            fn.argtypes = [C.c_double]
+        for name in ("orc_W", "orc_dWdr", "orc_dWdh"):
+            fn = getattr(L, name)
+            fn.restype = C.c_double
+            fn.argtypes = [C.c_double, C.c_double]
+        PP, SP = C.POINTER(_Params), C.POINTER(_State)
+        L.orc_density.restype = C.c_int
+        L.orc_density.argtypes = [PP, C.c_int64, SP]
+        L.orc_forces.restype = C.c_int
+        L.orc_forces.argtypes = [PP, C.c_int64, SP]
+        L.orc_step.restype = C.c_int
+        L.orc_step.argtypes = [PP, C.c_int64, SP, C.c_double]
+        L.orc_cfl_dt.restype = C.c_double
+        L.orc_cfl_dt.argtypes = [PP, C.c_int64, SP]
+        L.orc_neighbours.restype = C.c_int64
+        L.orc_neighbours.argtypes = [PP, C.c_int64, SP, C.c_int, C.POINTER(C.c_int64), _IP, C.c_int64]
+        L.orc_density_at_h.restype = C.c_int
+        L.orc_density_at_h.argtypes = [PP, C.c_int64, SP, C.c_int64, C.c_double, _DP, _DP]
+        L.orc_num_threads.restype = C.c_int
+        L.orc_set_num_threads.argtypes = [C.c_int]
+        _lib = L
+    return _lib
+
+
+@dataclass
+class Params:
+    """Run-time parameters of the method (defaults from the paper: eta = 1.2,
+    alpha_AV = 1, beta_AV = 2 alpha_AV, C_CFL = 0.2)."""
+    periodic: bool = True
+    box_lo: tuple = (0.0, 0.0, 0.0)
+    box_len: tuple = (1.0, 1.0, 1.0)
+    eos: str = "adiabatic"          # or "isothermal"
+    gamma: float = 5.0 / 3.0
+    cs_iso: float = 1.0
+    eta: float = 1.2
+    alpha_av: float = 1.0
+    beta_av: float = 2.0
+    alpha_ac: float = 1.0
+    c_cfl: float = 0.2
+    h_tol: float = 1e-13
+    h_max_iter: int = 50
+    use_grid: bool = False
+
+    def _c(self) -> _Params:
+        p = _Params()
+        p.periodic = int(bool(self.periodic))
+        p.box_lo = (C.c_double * 3)(*self.box_lo)
+        p.box_len = (C.c_double * 3)(*self.box_len)
+        p.eos = 0 if self.eos == "adiabatic" else 1
+        p.gamma, p.cs_iso, p.eta = self.gamma, self.cs_iso, self.eta
+        p.alpha_av, p.beta_av, p.alpha_ac = self.alpha_av, self.beta_av, self.alpha_ac
+        p.c_cfl, p.h_tol, p.h_max_iter = self.c_cfl, self.h_tol, int(self.h_max_iter)
+        p.use_grid = int(bool(self.use_grid))
+        return p
+
+
+class State:
+    """SoA particle state, all FP64 (plus int32 neighbour counts and iteration
+    counts).  Construct from the inputs x, y, z, vx, vy, vz, u, m and h (h <= 0
+    asks for a default starting guess)."""
+
+    def __init__(self, **arrays):
+        n = len(arrays["x"])
+        self.n = n
+        for f in _FIELDS_D:
+            a = arrays.get(f)
+            a = np.zeros(n) if a is None else np.array(a, dtype=np.float64, copy=True)
+            setattr(self, f, np.ascontiguousarray(a, dtype=np.float64))
+        for f in _FIELDS_I:
+            setattr(self, f, np.zeros(n, dtype=np.int32))
+
+    def copy(self) -> "State":
+        s = State(**{f: getattr(self, f) for f in _FIELDS_D})
+        for f in _FIELDS_I:
+            setattr(s, f, getattr(self, f).copy())
+        return s
+
+    def _c(self) -> _State:
+        st = _State()
+        for f in _FIELDS_D:
+            a = getattr(self, f)
+            assert a.flags.c_contiguous and a.dtype == np.float64 and len(a) == self.n
+            setattr(st, f, a.ctypes.data_as(_DP))
+        for f in _FIELDS_I:
+            setattr(st, f, getattr(self, f).ctypes.data_as(_IP))
+        return st
+
+
+def density(p: Params, s: State) -> int:
+    """h, rho, Omega, P, c for every particle (Eqs. SPHRHO, HRHO, OMEGA)."""
+    return lib().orc_density(C.byref(p._c()), s.n, C.byref(s._c()))
+
+
+def forces(p: Params, s: State) -> int:
+    """a, du/dt and v_sig (Eqs. GRADHMOMEQN, GRADHENEQN, MON97ARTVISC, MON97ENERGYDISS, SPH_DT)."""
+    return lib().orc_forces(C.byref(p._c()), s.n, C.byref(s._c()))
+
+
+def step(p: Params, s: State, dt: float) -> int:
+    """One KDK step (Eqs. LFKDK1/2) with the predictor reading of the paper."""
+    return lib().orc_step(C.byref(p._c()), s.n, C.byref(s._c()), float(dt))
+
+
+def cfl_dt(p: Params, s: State) -> float:
+    """C_CFL min_i h_i / v_sig,i (Eq. SPH_DT)."""
+    return lib().orc_cfl_dt(C.byref(p._c()), s.n, C.byref(s._c()))
+
+
+def density_at_h(p: Params, s: State, i: int, h: float):
+    """(rho_i(h), drho_i/dh) at fixed positions, Eq. SPHRHO and its h-derivative."""
+    r, d = C.c_double(), C.c_double()
+    rc = lib().orc_density_at_h(C.byref(p._c()), s.n, C.byref(s._c()), int(i), float(h),
+                                C.byref(r), C.byref(d))
+    if rc:
+        raise ValueError(f"orc_density_at_h failed: {rc}")
+    return r.value, d.value
+
+
+def neighbours(p: Params, s: State, kind: int):
+    """CSR neighbour lists (ids ascending). kind 0: r < 2 h_i (incl. self);
+    kind 1: j != i, r < 2 max(h_i, h_j)."""
+    off = np.zeros(s.n + 1, dtype=np.int64)
+    cap = max(1, s.n * 80)
+    while True:
+        idx = np.zeros(cap, dtype=np.int32)
+        tot = lib().orc_neighbours(C.byref(p._c()), s.n, C.byref(s._c()), int(kind),
+                                   off.ctypes.data_as(C.POINTER(C.c_int64)),
+                                   idx.ctypes.data_as(_IP), cap)
+        if tot < 0:
+            raise ValueError(f"orc_neighbours failed: {tot}")
+        if tot <= cap:
+            return off, idx[:tot].copy()
+        cap = int(tot)
+
+
+def kernel_f(q):
+    return np.vectorize(lib().orc_f, otypes=[np.float64])(q)
+
+
+def kernel_df(q):
+    return np.vectorize(lib().orc_df, otypes=[np.float64])(q)
+
+
+def kernel_W(r, h):
+    return np.vectorize(lib().orc_W, otypes=[np.float64])(r, h)
+
+
+def kernel_dWdr(r, h):
+    return np.vectorize(lib().orc_dWdr, otypes=[np.float64])(r, h)
+
+
+def kernel_dWdh(r, h):
+    return np.vectorize(lib().orc_dWdh, otypes=[np.float64])(r, h)
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
+
+
+def set_num_threads(t: int) -> None:
+    lib().orc_set_num_threads(int(t))
+
+
+def diagnostics(p: Params, s: State) -> dict:
+    """FP64 conserved quantities: total mass, momentum, energy, and the rates
+    sum m a and sum m (v.a + du/dt)."""
+    m = s.m
+    mom = np.array([np.sum(m * s.vx), np.sum(m * s.vy), np.sum(m * s.vz)])
+    ekin = 0.5 * np.sum(m * (s.vx ** 2 + s.vy ** 2 + s.vz ** 2))
+    eth = np.sum(m * s.u) if p.eos == "adiabatic" else 0.0
+    fsum = np.array([np.sum(m * s.ax), np.sum(m * s.ay), np.sum(m * s.az)])
+    dedt = np.sum(m * (s.vx * s.ax + s.vy * s.ay + s.vz * s.az))
+    if p.eos == "adiabatic":
+        dedt += np.sum(m * s.du)
+    return {"mass": float(np.sum(m)), "momentum": mom, "energy": float(ekin + eth),
+            "force_sum": fsum, "dEdt": float(dedt)}

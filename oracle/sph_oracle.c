@@ -1,0 +1,731 @@
+/*
+ * Plain, slow FP64 CPU oracle for the grad-h SPH neighbour loop of GANDALF
+ * (Hubber, Rosotti & Booth 2018, arXiv:1709.04488).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path (the CUDA library and
+ * its Python binding) links, imports or calls this file; only the tests, the
+ * smoke check and the CPU-baseline leg of the benchmark do.  It shares no code,
+ * header or constant with the CUDA implementation.
+ *
+ * What it computes, in the paper's order and notation:
+ *   - M4 cubic-spline kernel, support 2h (Sec. 2, kernel functions).  The paper
+ *     defers the formulas to an earlier paper; we use the standard
+ *     Monaghan & Lattanzio (1985) M4 spline with 3D normalisation 1/pi.
+ *   - Density sum, Eq. SPHRHO, and the h-rho relation, Eq. HRHO (eta = 1.2 by
+ *     default), iterated to convergence by Newton-Raphson with a bisection
+ *     fallback (Sec. 2.2.1; Newton-Raphson is named in Sec. 2.5 for the same
+ *     solve).
+ *   - The grad-h correction Omega, Eq. OMEGA; pressure and sound speed from the
+ *     adiabatic or isothermal EOS (Sec. 2.2.1, Sec. 4.2).
+ *   - Grad-h momentum equation, Eq. GRADHMOMEQN; energy equation, Eq.
+ *     GRADHENEQN; Monaghan (1997) artificial viscosity and Wadsley (2008)
+ *     conductivity, Eqs. MON97ARTVISC and MON97ENERGYDISS.
+ *   - CFL time-step, Eq. SPH_DT with its signal speed; leapfrog KDK, Eqs.
+ *     LFKDK1/LFKDK2, with a predictor for the velocity-dependent forces.
+ *
+ * Neighbour search is brute force O(N^2) over all particles, with the periodic
+ * minimum image.  A uniform-grid prefilter (use_grid=1) returns exactly the
+ * same candidate set, sorted by particle id, so every sum is taken in the same
+ * order and the two modes give identical bits; it only makes large inputs
+ * affordable.  All sums run over j in ascending particle id with Kahan
+ * compensation.  Squared distances are formed as dx*dx + dy*dy + dz*dz, left to
+ * right; the file must be compiled with -ffp-contract=off.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_PI 3.14159265358979323846
+
+typedef struct {
+    int periodic;            /* 1 = periodic box [lo, lo+L) on every axis */
+    double box_lo[3];
+    double box_len[3];
+    int eos;                 /* 0 = adiabatic, 1 = isothermal */
+    double gamma;
+    double cs_iso;
+    double eta;              /* h = eta (m/rho)^(1/3), Eq. HRHO */
+    double alpha_av;
+    double beta_av;
+    double alpha_ac;
+    double c_cfl;
+    double h_tol;            /* stop when |dh|/h < h_tol */
+    int h_max_iter;
+    int use_grid;            /* 0 = brute force, 1 = grid prefilter (same result) */
+} orc_params;
+
+typedef struct {
+    double *x, *y, *z;
+    double *vx, *vy, *vz;
+    double *u, *m, *h;
+    double *rho, *omega, *P, *c;
+    double *ax, *ay, *az, *du, *vsig;
+    int32_t *nngb, *iters;
+} orc_state;
+
+enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_EBOX = -2, ORC_ENOCONV = -3, ORC_ENOMEM = -9 };
+
+/* ------------------------------------------------------------------------ */
+/* M4 cubic spline (Monaghan & Lattanzio 1985), 3D, support radius 2h.       */
+/* f(q) is the dimensionless shape: W(r,h) = f(r/h) / (pi h^3).              */
+/* ------------------------------------------------------------------------ */
+double orc_f(double q)
+{
+    if (q < 0.0) q = -q;
+    if (q < 1.0) return 1.0 - 1.5 * q * q + 0.75 * q * q * q;
+    if (q < 2.0) {
+        double t = 2.0 - q;
+        return 0.25 * t * t * t;
+    }
+    return 0.0;
+}
+
+/* df/dq */
+double orc_df(double q)
+{
+    if (q < 1.0) return -3.0 * q + 2.25 * q * q;
+    if (q < 2.0) {
+        double t = 2.0 - q;
+        return -0.75 * t * t;
+    }
+    return 0.0;
+}
+
+double orc_W(double r, double h) { return orc_f(r / h) / (ORC_PI * h * h * h); }
+
+/* dW/dr: magnitude of the kernel gradient along r_hat (negative inside 2h). */
+double orc_dWdr(double r, double h)
+{
+    return orc_df(r / h) / (ORC_PI * h * h * h * h);
+}
+
+/* dW/dh at fixed r: -(3 f + q f') / (pi h^4). */
+double orc_dWdh(double r, double h)
+{
+    double q = r / h;
+    return -(3.0 * orc_f(q) + q * orc_df(q)) / (ORC_PI * h * h * h * h);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Geometry                                                                  */
+/* ------------------------------------------------------------------------ */
+static double min_image(double d, double L, int periodic)
+{
+    if (!periodic) return d;
+    if (d > 0.5 * L) d -= L;
+    else if (d < -0.5 * L) d += L;
+    return d;
+}
+
+typedef struct {
+    double dx, dy, dz, r2;
+} sep_t;
+
+static sep_t separation(const orc_params *p, const orc_state *s, int64_t i, int64_t j)
+{
+    sep_t o;
+    o.dx = min_image(s->x[i] - s->x[j], p->box_len[0], p->periodic);
+    o.dy = min_image(s->y[i] - s->y[j], p->box_len[1], p->periodic);
+    o.dz = min_image(s->z[i] - s->z[j], p->box_len[2], p->periodic);
+    /* left to right, no contraction (compiled with -ffp-contract=off) */
+    o.r2 = o.dx * o.dx + o.dy * o.dy + o.dz * o.dz;
+    return o;
+}
+
+/* Kahan-compensated accumulator */
+typedef struct {
+    double s, c;
+} kahan_t;
+
+static void kadd(kahan_t *k, double v)
+{
+    double y = v - k->c;
+    double t = k->s + y;
+    k->c = (t - k->s) - y;
+    k->s = t;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Uniform-grid prefilter.  Only narrows the candidate set; the membership    */
+/* test below is the same expression as in brute-force mode, and candidate    */
+/* lists are sorted by id before use.                                         */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int nc[3];
+    double lo[3], cs[3];
+    int64_t *cell_start; /* ncell + 1 */
+    int64_t *ids;        /* particle ids grouped by cell, ascending within a cell */
+} grid_t;
+
+static int cell_coord(const grid_t *g, int a, double x)
+{
+    int c = (int)floor((x - g->lo[a]) / g->cs[a]);
+    if (c < 0) c = 0;
+    if (c >= g->nc[a]) c = g->nc[a] - 1;
+    return c;
+}
+
+static int grid_build(grid_t *g, const orc_params *p, const orc_state *s, int64_t n, double cell)
+{
+    double lo[3], hi[3];
+    const double *X[3] = {s->x, s->y, s->z};
+    for (int a = 0; a < 3; ++a) {
+        if (p->periodic) {
+            lo[a] = p->box_lo[a];
+            hi[a] = p->box_lo[a] + p->box_len[a];
+        } else {
+            lo[a] = hi[a] = X[a][0];
+            for (int64_t i = 1; i < n; ++i) {
+                if (X[a][i] < lo[a]) lo[a] = X[a][i];
+                if (X[a][i] > hi[a]) hi[a] = X[a][i];
+            }
+        }
+        double ext = hi[a] - lo[a];
+        int nc = (ext > 0 && cell > 0) ? (int)floor(ext / cell) : 1;
+        if (nc < 1) nc = 1;
+        if (nc > 512) nc = 512;
+        g->nc[a] = nc;
+        g->lo[a] = lo[a];
+        g->cs[a] = ext > 0 ? ext / nc : 1.0;
+    }
+    int64_t ncell = (int64_t)g->nc[0] * g->nc[1] * g->nc[2];
+    g->cell_start = (int64_t *)calloc((size_t)ncell + 1, sizeof(int64_t));
+    g->ids = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int64_t *cid = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    if (!g->cell_start || !g->ids || !cid) {
+        free(cid);
+        return ORC_ENOMEM;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        int cx = cell_coord(g, 0, s->x[i]), cy = cell_coord(g, 1, s->y[i]), cz = cell_coord(g, 2, s->z[i]);
+        cid[i] = ((int64_t)cz * g->nc[1] + cy) * g->nc[0] + cx;
+        g->cell_start[cid[i] + 1]++;
+    }
+    for (int64_t c = 0; c < ncell; ++c) g->cell_start[c + 1] += g->cell_start[c];
+    int64_t *fill = (int64_t *)malloc((size_t)ncell * sizeof(int64_t));
+    if (!fill) {
+        free(cid);
+        return ORC_ENOMEM;
+    }
+    memcpy(fill, g->cell_start, (size_t)ncell * sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) g->ids[fill[cid[i]]++] = i; /* ascending id within each cell */
+    free(fill);
+    free(cid);
+    return ORC_OK;
+}
+
+static void grid_free(grid_t *g)
+{
+    free(g->cell_start);
+    free(g->ids);
+    g->cell_start = NULL;
+    g->ids = NULL;
+}
+
+static int cmp_i64(const void *a, const void *b)
+{
+    int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* Growable list of ids */
+typedef struct {
+    int64_t *v;
+    int64_t n, cap;
+} idlist_t;
+
+static int push(idlist_t *l, int64_t j)
+{
+    if (l->n == l->cap) {
+        int64_t nc = l->cap ? 2 * l->cap : 256;
+        int64_t *nv = (int64_t *)realloc(l->v, (size_t)nc * sizeof(int64_t));
+        if (!nv) return ORC_ENOMEM;
+        l->v = nv;
+        l->cap = nc;
+    }
+    l->v[l->n++] = j;
+    return ORC_OK;
+}
+
+/*
+ * All j (including i itself) with r_ij^2 < R^2, ascending in j.
+ * mode "rmax_of_j": when hj != NULL the radius for pair (i,j) is
+ * 2 max(h_i, h_j) (the force list); otherwise the fixed radius R.
+ */
+static int gather(const orc_params *p, const orc_state *s, int64_t n, const grid_t *g,
+                  int64_t i, double R, const double *hforce, idlist_t *out)
+{
+    out->n = 0;
+    if (!g) {
+        for (int64_t j = 0; j < n; ++j) {
+            sep_t d = separation(p, s, i, j);
+            double Rj = R;
+            if (hforce) {
+                double hm = hforce[i] > hforce[j] ? hforce[i] : hforce[j];
+                Rj = 2.0 * hm;
+            }
+            if (d.r2 < Rj * Rj)
+                if (push(out, j)) return ORC_ENOMEM;
+        }
+        return ORC_OK;
+    }
+    /* grid: the query radius must cover the largest pair radius; for force
+       lists the caller passes R = 2 max_j h_j */
+    const double Rq = R;
+    const double X[3] = {s->x[i], s->y[i], s->z[i]};
+    int c0[3], c1[3], full[3];
+    for (int a = 0; a < 3; ++a) {
+        int span = (int)ceil(Rq / g->cs[a]) + 1;
+        int cc = cell_coord(g, a, X[a]);
+        c0[a] = cc - span;
+        c1[a] = cc + span;
+        full[a] = 0;
+        if (p->periodic) {
+            if (c1[a] - c0[a] + 1 >= g->nc[a]) {
+                c0[a] = 0;
+                c1[a] = g->nc[a] - 1;
+                full[a] = 1;
+            }
+        } else {
+            if (c0[a] < 0) c0[a] = 0;
+            if (c1[a] >= g->nc[a]) c1[a] = g->nc[a] - 1;
+        }
+    }
+    for (int cz = c0[2]; cz <= c1[2]; ++cz)
+        for (int cy = c0[1]; cy <= c1[1]; ++cy)
+            for (int cx = c0[0]; cx <= c1[0]; ++cx) {
+                int w[3] = {cx, cy, cz};
+                for (int a = 0; a < 3; ++a)
+                    if (p->periodic && !full[a]) w[a] = ((w[a] % g->nc[a]) + g->nc[a]) % g->nc[a];
+                int64_t cid = ((int64_t)w[2] * g->nc[1] + w[1]) * g->nc[0] + w[0];
+                for (int64_t k = g->cell_start[cid]; k < g->cell_start[cid + 1]; ++k) {
+                    int64_t j = g->ids[k];
+                    sep_t d = separation(p, s, i, j);
+                    double Rj = R;
+                    if (hforce) {
+                        double hm = hforce[i] > hforce[j] ? hforce[i] : hforce[j];
+                        Rj = 2.0 * hm;
+                    }
+                    if (d.r2 < Rj * Rj)
+                        if (push(out, j)) return ORC_ENOMEM;
+                }
+            }
+    qsort(out->v, (size_t)out->n, sizeof(int64_t), cmp_i64);
+    return ORC_OK;
+}
+
+static int params_ok(const orc_params *p, int64_t n)
+{
+    if (n < 0 || !p) return 0;
+    if (!(p->eta > 0) || !(p->h_tol > 0) || p->h_max_iter < 1) return 0;
+    if (p->periodic)
+        for (int a = 0; a < 3; ++a)
+            if (!(p->box_len[a] > 0)) return 0;
+    if (p->eos == 0 && !(p->gamma > 1.0)) return 0;
+    if (p->eos == 1 && !(p->cs_iso > 0)) return 0;
+    return 1;
+}
+
+static double median_spacing_guess(const orc_params *p, const orc_state *s, int64_t n)
+{
+    /* cell size for the grid prefilter: a few mean spacings */
+    double vol;
+    if (p->periodic) vol = p->box_len[0] * p->box_len[1] * p->box_len[2];
+    else {
+        double lo[3] = {s->x[0], s->y[0], s->z[0]}, hi[3] = {s->x[0], s->y[0], s->z[0]};
+        for (int64_t i = 1; i < n; ++i) {
+            double X[3] = {s->x[i], s->y[i], s->z[i]};
+            for (int a = 0; a < 3; ++a) {
+                if (X[a] < lo[a]) lo[a] = X[a];
+                if (X[a] > hi[a]) hi[a] = X[a];
+            }
+        }
+        vol = (hi[0] - lo[0] + 1e-300) * (hi[1] - lo[1] + 1e-300) * (hi[2] - lo[2] + 1e-300);
+    }
+    return cbrt(vol / (double)(n > 0 ? n : 1));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Density at a fixed h: rho = sum_j m_j W(r_ij, h) (Eq. SPHRHO, j includes  */
+/* i) and drho/dh = sum_j m_j dW/dh (r_ij, h).                               */
+/* ------------------------------------------------------------------------ */
+static int density_at(const orc_params *p, const orc_state *s, int64_t n, const grid_t *g,
+                      int64_t i, double h, idlist_t *buf, double *rho, double *drho, int32_t *nn)
+{
+    int rc = gather(p, s, n, g, i, 2.0 * h, NULL, buf);
+    if (rc) return rc;
+    kahan_t r = {0, 0}, d = {0, 0};
+    for (int64_t k = 0; k < buf->n; ++k) {
+        int64_t j = buf->v[k];
+        sep_t sp = separation(p, s, i, j);
+        double rr = sqrt(sp.r2);
+        kadd(&r, s->m[j] * orc_W(rr, h));
+        kadd(&d, s->m[j] * orc_dWdh(rr, h));
+    }
+    *rho = r.s;
+    *drho = d.s;
+    if (nn) *nn = (int32_t)buf->n;
+    return ORC_OK;
+}
+
+/* Exported for the pins: rho(h) and drho/dh(h) of particle i at a given h. */
+int orc_density_at_h(const orc_params *p, int64_t n, const orc_state *s, int64_t i, double h,
+                     double *rho, double *drho)
+{
+    if (!params_ok(p, n) || i < 0 || i >= n || !(h > 0)) return ORC_EINVAL;
+    idlist_t buf = {0, 0, 0};
+    int rc = density_at(p, s, n, NULL, i, h, &buf, rho, drho, NULL);
+    free(buf.v);
+    return rc;
+}
+
+static double initial_h(const orc_params *p, const orc_state *s, int64_t n, int64_t i)
+{
+    if (p->periodic) {
+        double M = 0;
+        for (int64_t j = 0; j < n; ++j) M += s->m[j];
+        double rhobar = M / (p->box_len[0] * p->box_len[1] * p->box_len[2]);
+        return p->eta * cbrt(s->m[i] / rhobar);
+    }
+    /* isolated: half the distance to the 58th nearest particle (brute force) */
+    int64_t k = n < 58 ? n : 58;
+    double *d2 = (double *)malloc((size_t)n * sizeof(double));
+    if (!d2) return 1.0;
+    for (int64_t j = 0; j < n; ++j) d2[j] = separation(p, s, i, j).r2;
+    /* partial selection of the k-th smallest */
+    for (int64_t a = 0; a < k; ++a) {
+        int64_t best = a;
+        for (int64_t b = a + 1; b < n; ++b)
+            if (d2[b] < d2[best]) best = b;
+        double t = d2[a];
+        d2[a] = d2[best];
+        d2[best] = t;
+    }
+    double r = sqrt(d2[k - 1]);
+    free(d2);
+    return r > 0 ? 0.5 * r : 1.0;
+}
+
+/*
+ * h-rho solve for one particle (Eqs. SPHRHO, HRHO).
+ * F(h) = rho_sum(h) - m (eta/h)^3,  F'(h) = drho/dh + 3 m eta^3 / h^4.
+ * The sign of F equals that of G(h) = h^3 rho_sum(h) - m eta^3, which is
+ * non-decreasing in h, so [lo, hi] brackets the unique root.  A Newton step
+ * that leaves the bracket, leaves [h/2, 2h] or meets F' <= 0 is replaced by
+ * bisection (or doubling while no upper bound is known).
+ * On return h holds the last iterate and rho, drho are evaluated at it.
+ */
+static int solve_h(const orc_params *p, const orc_state *s, int64_t n, const grid_t *g, int64_t i,
+                   idlist_t *buf, double *h_io, double *rho_o, double *drho_o, int32_t *nn_o,
+                   int32_t *it_o)
+{
+    double h = *h_io;
+    if (!(h > 0)) h = initial_h(p, s, n, i);
+    double lo = 0.0, hi = INFINITY;
+    const double m = s->m[i], eta3 = p->eta * p->eta * p->eta;
+    double rho = 0, drho = 0;
+    int32_t nn = 0;
+    int conv = 0, it;
+    for (it = 1; it <= p->h_max_iter; ++it) {
+        int rc = density_at(p, s, n, g, i, h, buf, &rho, &drho, &nn);
+        if (rc) return rc;
+        double h3 = h * h * h;
+        double F = rho - m * eta3 / h3;
+        double dF = drho + 3.0 * m * eta3 / (h3 * h);
+        if (F < 0) lo = h;
+        else hi = h;
+        double hn = (dF > 0) ? h - F / dF : NAN;
+        int bad = !(hn >= lo) || !(hn <= hi) || !(hn >= 0.5 * h) || !(hn <= 2.0 * h);
+        if (bad) hn = isinf(hi) ? 2.0 * h : 0.5 * (lo + hi);
+        if (p->periodic) {
+            /* the support 2h must stay below half the box for the minimum image */
+            double Lmin = p->box_len[0];
+            if (p->box_len[1] < Lmin) Lmin = p->box_len[1];
+            if (p->box_len[2] < Lmin) Lmin = p->box_len[2];
+            if (hn > 0.25 * Lmin) {
+                *h_io = h;
+                *it_o = it;
+                return ORC_EBOX;
+            }
+        }
+        if (fabs(hn - h) < p->h_tol * h) {
+            h = hn;
+            conv = 1;
+            break;
+        }
+        h = hn;
+    }
+    int rc = density_at(p, s, n, g, i, h, buf, &rho, &drho, &nn);
+    if (rc) return rc;
+    *h_io = h;
+    *rho_o = rho;
+    *drho_o = drho;
+    *nn_o = nn;
+    *it_o = it > p->h_max_iter ? p->h_max_iter : it;
+    return conv ? ORC_OK : ORC_ENOCONV;
+}
+
+static void eos(const orc_params *p, double rho, double u, double *P, double *c)
+{
+    if (p->eos == 1) {
+        *P = p->cs_iso * p->cs_iso * rho;
+        *c = p->cs_iso;
+    } else {
+        *P = (p->gamma - 1.0) * rho * u;
+        *c = sqrt(p->gamma * (*P) / rho);
+    }
+}
+
+/*
+ * Density, smoothing length, Omega (Eq. OMEGA), P and c for every particle.
+ * h is read as the starting guess (<= 0: a default guess) and overwritten.
+ * Returns ORC_ENOCONV if any particle failed to converge.
+ */
+int orc_density(const orc_params *p, int64_t n, orc_state *s)
+{
+    if (!params_ok(p, n)) return ORC_EINVAL;
+    if (n == 0) return ORC_OK;
+    grid_t g;
+    memset(&g, 0, sizeof g);
+    const grid_t *gp = NULL;
+    if (p->use_grid) {
+        if (grid_build(&g, p, s, n, 2.0 * median_spacing_guess(p, s, n))) return ORC_ENOMEM;
+        gp = &g;
+    }
+    int status = ORC_OK;
+#pragma omp parallel
+    {
+        idlist_t buf = {0, 0, 0};
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t i = 0; i < n; ++i) {
+            double rho = 0, drho = 0;
+            int32_t nn = 0, it = 0;
+            int rc = solve_h(p, s, n, gp, i, &buf, &s->h[i], &rho, &drho, &nn, &it);
+            s->rho[i] = rho;
+            /* Omega = 1 - (dh/drho) sum m dW/dh with dh/drho = -h/(3 rho) */
+            s->omega[i] = 1.0 + s->h[i] / (3.0 * rho) * drho;
+            eos(p, rho, s->u[i], &s->P[i], &s->c[i]);
+            if (s->nngb) s->nngb[i] = nn;
+            if (s->iters) s->iters[i] = it;
+            if (rc) {
+#pragma omp critical
+                status = rc;
+            }
+        }
+        free(buf.v);
+    }
+    if (gp) grid_free(&g);
+    return status;
+}
+
+/*
+ * Accelerations and energy rates (Eqs. GRADHMOMEQN, GRADHENEQN, MON97ARTVISC,
+ * MON97ENERGYDISS) and the signal speed of Eq. SPH_DT, over j != i with
+ * r_ij < 2 max(h_i, h_j).  Needs h, rho, Omega, P, c from orc_density.
+ */
+int orc_forces(const orc_params *p, int64_t n, orc_state *s)
+{
+    if (!params_ok(p, n)) return ORC_EINVAL;
+    if (n == 0) return ORC_OK;
+    double hmax = 0;
+    for (int64_t j = 0; j < n; ++j) hmax = s->h[j] > hmax ? s->h[j] : hmax;
+    grid_t g;
+    memset(&g, 0, sizeof g);
+    const grid_t *gp = NULL;
+    if (p->use_grid) {
+        if (grid_build(&g, p, s, n, 2.0 * median_spacing_guess(p, s, n))) return ORC_ENOMEM;
+        gp = &g;
+    }
+    const double alpha = p->alpha_av, beta = p->beta_av, aac = p->alpha_ac;
+    int status = ORC_OK;
+#pragma omp parallel
+    {
+        idlist_t buf = {0, 0, 0};
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t i = 0; i < n; ++i) {
+            int rc = gather(p, s, n, gp, i, 2.0 * hmax, s->h, &buf);
+            if (rc) {
+#pragma omp critical
+                status = rc;
+                continue;
+            }
+            const double Ai = s->P[i] / (s->omega[i] * s->rho[i] * s->rho[i]);
+            kahan_t ax = {0, 0}, ay = {0, 0}, az = {0, 0}, du = {0, 0};
+            double vsig = 2.0 * s->c[i]; /* no neighbour: c_i + c_i */
+            int have = 0;
+            for (int64_t k = 0; k < buf.n; ++k) {
+                int64_t j = buf.v[k];
+                if (j == i) continue;
+                sep_t sp = separation(p, s, i, j);
+                double r = sqrt(sp.r2);
+                double rx = sp.dx / r, ry = sp.dy / r, rz = sp.dz / r; /* r_hat_ij */
+                double gi = orc_dWdr(r, s->h[i]);                       /* grad_i W(h_i) = gi r_hat */
+                double gj = orc_dWdr(r, s->h[j]);                       /* grad_i W(h_j) = gj r_hat */
+                double Aj = s->P[j] / (s->omega[j] * s->rho[j] * s->rho[j]);
+                double mj = s->m[j];
+                /* pressure term, Eq. GRADHMOMEQN */
+                double fp = -mj * (Ai * gi + Aj * gj);
+                double vxij = s->vx[i] - s->vx[j], vyij = s->vy[i] - s->vy[j], vzij = s->vz[i] - s->vz[j];
+                double vdr = vxij * rx + vyij * ry + vzij * rz; /* v_ij . r_hat_ij */
+                double gbar = 0.5 * (gi + gj);                   /* r_hat . mean grad W */
+                double rhobar = 0.5 * (s->rho[i] + s->rho[j]);
+                double fav = 0.0, duav = 0.0;
+                double vs = s->c[i] + s->c[j] - beta * (vdr < 0 ? vdr : 0.0);
+                if (!have || vs > vsig) vsig = vs;
+                have = 1;
+                if (vdr < 0) {
+                    double mu = vdr; /* MIN(0, v_ij . r_hat_ij) */
+                    double vsig_av = s->c[i] + s->c[j] - beta * vdr;
+                    fav = mj / rhobar * alpha * vsig_av * mu * gbar;            /* Eq. MON97ARTVISC */
+                    duav = -mj / rhobar * 0.5 * alpha * vsig_av * mu * mu * gbar; /* Eq. MON97ENERGYDISS */
+                }
+                double f = fp + fav;
+                kadd(&ax, f * rx);
+                kadd(&ay, f * ry);
+                kadd(&az, f * rz);
+                if (p->eos == 0) {
+                    double dui = Ai * mj * vdr * gi; /* Eq. GRADHENEQN */
+                    double duac = mj / rhobar * aac * fabs(vdr) * (s->u[i] - s->u[j]) * gbar;
+                    kadd(&du, dui + duav + duac);
+                }
+            }
+            s->ax[i] = ax.s;
+            s->ay[i] = ay.s;
+            s->az[i] = az.s;
+            s->du[i] = (p->eos == 0) ? du.s : 0.0;
+            s->vsig[i] = vsig;
+        }
+        free(buf.v);
+    }
+    if (gp) grid_free(&g);
+    return status;
+}
+
+/* Global CFL time-step, Eq. SPH_DT: C_CFL * min_i h_i / v_sig,i. */
+double orc_cfl_dt(const orc_params *p, int64_t n, const orc_state *s)
+{
+    double dt = INFINITY;
+    for (int64_t i = 0; i < n; ++i) {
+        double d = p->c_cfl * s->h[i] / s->vsig[i];
+        if (d < dt) dt = d;
+    }
+    return dt;
+}
+
+static double wrap(double x, double lo, double L)
+{
+    double t = x - lo;
+    t -= L * floor(t / L);
+    if (t >= L) t -= L; /* guard rounding at the upper edge */
+    return lo + t;
+}
+
+/*
+ * One global-step kick-drift-kick (Eqs. LFKDK1, LFKDK2).  The state must hold
+ * a and du/dt from the previous force evaluation.  Velocity- and u-dependent
+ * forces are evaluated at the predicted v^ = v^(n+1/2) + a^n dt/2 and
+ * u^ = u^(n+1/2) + du^n dt/2; the closing kick uses the new rates.
+ */
+int orc_step(const orc_params *p, int64_t n, orc_state *s, double dt)
+{
+    if (!params_ok(p, n) || !(dt > 0)) return ORC_EINVAL;
+    double *vh = (double *)malloc((size_t)(n > 0 ? n : 1) * 4 * sizeof(double));
+    if (!vh) return ORC_ENOMEM;
+    double *vhx = vh, *vhy = vh + n, *vhz = vh + 2 * n, *uh = vh + 3 * n;
+    const int adi = (p->eos == 0);
+    for (int64_t i = 0; i < n; ++i) {
+        vhx[i] = s->vx[i] + 0.5 * s->ax[i] * dt;
+        vhy[i] = s->vy[i] + 0.5 * s->ay[i] * dt;
+        vhz[i] = s->vz[i] + 0.5 * s->az[i] * dt;
+        uh[i] = adi ? s->u[i] + 0.5 * s->du[i] * dt : s->u[i];
+        s->x[i] += vhx[i] * dt;
+        s->y[i] += vhy[i] * dt;
+        s->z[i] += vhz[i] * dt;
+        if (p->periodic) {
+            s->x[i] = wrap(s->x[i], p->box_lo[0], p->box_len[0]);
+            s->y[i] = wrap(s->y[i], p->box_lo[1], p->box_len[1]);
+            s->z[i] = wrap(s->z[i], p->box_lo[2], p->box_len[2]);
+        }
+        /* predictor */
+        s->vx[i] = vhx[i] + 0.5 * s->ax[i] * dt;
+        s->vy[i] = vhy[i] + 0.5 * s->ay[i] * dt;
+        s->vz[i] = vhz[i] + 0.5 * s->az[i] * dt;
+        if (adi) s->u[i] = uh[i] + 0.5 * s->du[i] * dt;
+    }
+    int rc = orc_density(p, n, s);
+    int rc2 = (rc == ORC_OK || rc == ORC_ENOCONV) ? orc_forces(p, n, s) : rc;
+    for (int64_t i = 0; i < n; ++i) {
+        s->vx[i] = vhx[i] + 0.5 * s->ax[i] * dt;
+        s->vy[i] = vhy[i] + 0.5 * s->ay[i] * dt;
+        s->vz[i] = vhz[i] + 0.5 * s->az[i] * dt;
+        if (adi) s->u[i] = uh[i] + 0.5 * s->du[i] * dt;
+    }
+    free(vh);
+    return rc2 ? rc2 : rc;
+}
+
+/*
+ * Neighbour lists in CSR form, ids ascending.
+ * kind 0: gather list {j : r_ij^2 < (2 h_i)^2} (includes i);
+ * kind 1: force list  {j != i : r_ij^2 < (2 max(h_i,h_j))^2}.
+ * offsets has n+1 entries.  Returns the total count (may exceed cap, in which
+ * case idx holds only the first cap entries), or a negative error.
+ */
+int64_t orc_neighbours(const orc_params *p, int64_t n, const orc_state *s, int kind,
+                       int64_t *offsets, int32_t *idx, int64_t cap)
+{
+    if (!params_ok(p, n) || (kind != 0 && kind != 1)) return ORC_EINVAL;
+    double hmax = 0;
+    for (int64_t j = 0; j < n; ++j) hmax = s->h[j] > hmax ? s->h[j] : hmax;
+    grid_t g;
+    memset(&g, 0, sizeof g);
+    const grid_t *gp = NULL;
+    if (p->use_grid && n > 0) {
+        if (grid_build(&g, p, s, n, 2.0 * median_spacing_guess(p, s, n))) return ORC_ENOMEM;
+        gp = &g;
+    }
+    offsets[0] = 0;
+    idlist_t buf = {0, 0, 0};
+    int64_t total = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        int rc = kind == 0 ? gather(p, s, n, gp, i, 2.0 * s->h[i], NULL, &buf)
+                           : gather(p, s, n, gp, i, 2.0 * hmax, s->h, &buf);
+        if (rc) {
+            free(buf.v);
+            if (gp) grid_free(&g);
+            return rc;
+        }
+        for (int64_t k = 0; k < buf.n; ++k) {
+            if (kind == 1 && buf.v[k] == i) continue;
+            if (total < cap) idx[total] = (int32_t)buf.v[k];
+            total++;
+        }
+        offsets[i + 1] = total;
+    }
+    free(buf.v);
+    if (gp) grid_free(&g);
+    return total;
+}
+
+int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void orc_set_num_threads(int t)
+{
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}

@@ -1,0 +1,419 @@
+"""Pins for the FP64 CPU oracle: facts fixed by the paper and by mathematics,
+not by re-typing the oracle's formulas.
+
+Each test names the passage it pins (section / equation of Hubber, Rosotti &
+Booth 2018) and the mathematical fact used.  Chosen so that a dropped term, a
+wrong sign, a wrong index or a transposed operand anywhere in the oracle
+fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from paper_1709_04488_gb300 import ics
+
+
+def _state(O, arrays):
+    return O.State(**arrays)
+
+
+# --------------------------------------------------------------------------
+# Kernel (Sec. 2: M4 cubic spline, support 2h)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("h", [1.0, 0.37, 2.5])
+def test_kernel_normalised(oracle_mod, h):
+    """A smoothing kernel integrates to one over its support: 4 pi int W r^2 dr = 1."""
+    O = oracle_mod
+    val = sum(integrate.quad(lambda r: 4 * math.pi * r * r * O.kernel_W(r, h), lo, hi,
+                             epsabs=1e-15, epsrel=1e-14)[0] for lo, hi in ((0, h), (h, 2 * h)))
+    assert abs(val - 1.0) < 1e-12
+
+
+def test_kernel_compact_and_continuous(oracle_mod):
+    """Support radius R = 2h (Sec. 2), shape continuous with a continuous first
+    derivative (a cubic spline), peak at the centre."""
+    O = oracle_mod
+    for q0 in (1.0, 2.0):
+        e = 1e-9
+        assert abs(O.kernel_f(q0 - e) - O.kernel_f(q0 + e)) < 1e-8
+        assert abs(O.kernel_df(q0 - e) - O.kernel_df(q0 + e)) < 1e-8
+    assert O.kernel_f(2.0) == 0.0 and O.kernel_f(3.0) == 0.0
+    assert O.kernel_df(2.0) == 0.0
+    q = np.linspace(0, 1.999, 500)
+    f = O.kernel_f(q)
+    assert np.all(np.diff(f) < 0) and f[0] == 1.0
+
+
+def test_kernel_derivatives_finite_difference(oracle_mod):
+    """dW/dr and dW/dh are the partial derivatives of W (central differences)."""
+    O = oracle_mod
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        h = rng.uniform(0.2, 3.0)
+        r = rng.uniform(0.0, 2.0) * h
+        if min(abs(r / h - 1.0), abs(r / h - 2.0)) < 1e-3:
+            continue
+        e = 1e-6 * h
+        fd_r = (O.kernel_W(r + e, h) - O.kernel_W(r - e, h)) / (2 * e) if r > e else None
+        fd_h = (O.kernel_W(r, h + e) - O.kernel_W(r, h - e)) / (2 * e)
+        scale = O.kernel_W(0.0, h) / h
+        if fd_r is not None:
+            assert abs(O.kernel_dWdr(r, h) - fd_r) < 1e-7 * scale
+        assert abs(O.kernel_dWdh(r, h) - fd_h) < 1e-7 * scale
+
+
+# --------------------------------------------------------------------------
+# Density and smoothing length (Eqs. SPHRHO, HRHO; Sec. 4.1 lattice offset)
+# --------------------------------------------------------------------------
+def test_lattice_density_neighbours_and_offset(oracle_mod):
+    """Perfect cubic lattice: the density sum recovers rho0 to better than 1 %
+    (the paper's 'consistent fractional offset of less than one percent',
+    Sec. 4.1), and with eta = 1.2 every particle has exactly 57 neighbours
+    inside 2h, counting itself: lattice shells |n|^2 = 0,1,2,3,4,5 hold
+    1+6+12+8+6+24 = 57 points and the next shell, |n|^2 = 6, lies at
+    2.449 spacings > 2h = 2.399 spacings."""
+    O = oracle_mod
+    a, p = ics.lattice(16, jitter=0.0)
+    P = O.Params(**p)
+    s = _state(O, a)
+    assert O.density(P, s) == O.OK
+    shells = 1 + 6 + 12 + 8 + 6 + 24
+    assert np.all(s.nngb == shells)
+    rho0 = 1.0
+    assert np.all(np.abs(s.rho / rho0 - 1.0) < 0.01)
+    assert np.all(s.rho > rho0)  # the offset is an over-estimate on a lattice
+    # Eq. HRHO holds at convergence
+    assert np.allclose(s.h, P.eta * np.cbrt(s.m / s.rho), rtol=1e-12, atol=0)
+    # h/spacing close to eta
+    assert np.all(np.abs(s.h * 16 - 1.2) < 0.01)
+
+
+def test_density_solution_satisfies_hrho(oracle_mod):
+    """After the iteration, h and rho satisfy Eq. HRHO to the tolerance and
+    rho is the density sum at the returned h (jittered lattice, cold start)."""
+    O = oracle_mod
+    a, p = ics.lattice(12, seed=7)
+    a["h"][:] = 0.0  # ask for the default starting guess
+    P = O.Params(**p)
+    s = _state(O, a)
+    assert O.density(P, s) == O.OK
+    assert np.allclose(s.h, P.eta * np.cbrt(s.m / s.rho), rtol=1e-12, atol=0)
+    for i in (0, 100, 999):
+        r, _ = O.density_at_h(P, s, i, s.h[i])
+        assert r == s.rho[i]
+    # a lightly jittered lattice keeps the 57 points of the first six shells;
+    # only the 24-point shell at 2.449 spacings can enter the 2h sphere
+    assert s.nngb.min() >= 57 - 6 and s.nngb.max() <= 57 + 24
+
+
+def test_density_h_derivative_finite_difference(oracle_mod):
+    """drho/dh used in Omega is the derivative of the density sum in h."""
+    O = oracle_mod
+    a, p = ics.random_cloud(400, seed=3)
+    P = O.Params(**p)
+    s = _state(O, a)
+    assert O.density(P, s) == O.OK
+    for i in (0, 17, 211):
+        h = s.h[i]
+        e = 1e-6 * h
+        rp, _ = O.density_at_h(P, s, i, h + e)
+        rm, _ = O.density_at_h(P, s, i, h - e)
+        _, d = O.density_at_h(P, s, i, h)
+        assert abs((rp - rm) / (2 * e) - d) < 1e-6 * abs(d)
+
+
+def _solve(O, P, a):
+    s = _state(O, a)
+    assert O.density(P, s) == O.OK
+    return s
+
+
+def test_continuity_identity_pins_omega(oracle_mod):
+    """Grad-h continuity: with h tied to rho (Eq. HRHO) the density changes at
+    d rho_i/dt = (1/Omega_i) sum_j m_j v_ij . grad_i W(h_i).  For adiabatic
+    flow the first law gives du_i/dt = (P_i/rho_i^2) d rho_i/dt, which is
+    Eq. GRADHENEQN.  So du/dt from the oracle's force routine (no dissipation)
+    must equal (P/rho^2) times the finite-difference rate of the density
+    re-solved at advected positions.  A wrong Omega (value or sign), a wrong
+    gradient sign or a v_ij index swap fails this."""
+    O = oracle_mod
+    a, p = ics.random_cloud(300, seed=11, mass_spread=0.3, vel=0.7, u_spread=0.5)
+    P = O.Params(**p, alpha_av=0.0, alpha_ac=0.0)
+    s = _solve(O, P, a)
+    assert O.forces(P, s) == O.OK
+    eps = 1e-6
+    rho = []
+    for sign in (+1, -1):
+        b = {k: v.copy() for k, v in a.items()}
+        b["h"] = s.h.copy()
+        for c, v in (("x", "vx"), ("y", "vy"), ("z", "vz")):
+            b[c] = (b[c] + sign * eps * b[v]) % 1.0
+        rho.append(_solve(O, P, b).rho)
+    drho = (rho[0] - rho[1]) / (2 * eps)
+    lhs = s.du
+    rhs = s.P / s.rho ** 2 * drho
+    scale = np.sqrt(np.mean(rhs ** 2))
+    assert np.max(np.abs(lhs - rhs)) < 1e-5 * scale
+
+
+def test_pressure_force_is_thermal_energy_gradient(oracle_mod):
+    """Eq. GRADHMOMEQN follows from the Lagrangian: with the entropy of each
+    particle held fixed, m_i a_i = -dE_th/dr_i where E_th = sum_j m_j u_j(rho_j),
+    u_j = K_j rho_j^(gamma-1) (Sec. 2.2.1 'derived from the Euler-Lagrange
+    equations').  Checked by central differences of the re-solved densities.
+    Pins the pressure term: both h_i and h_j parts, Omega, signs, indices."""
+    O = oracle_mod
+    a, p = ics.random_cloud(400, seed=5, mass_spread=0.4, u_spread=0.6)
+    P = O.Params(**p, alpha_av=0.0, alpha_ac=0.0)
+    s = _solve(O, P, a)
+    assert O.forces(P, s) == O.OK
+    g = P.gamma
+    K = s.u / s.rho ** (g - 1.0)
+
+    def eth(b):
+        r = _solve(O, P, b).rho
+        return np.sum(b["m"] * K * r ** (g - 1.0))
+
+    eps = 1e-6
+    for i in (0, 42, 399):
+        for c, acc in (("x", s.ax), ("y", s.ay), ("z", s.az)):
+            e2 = []
+            for sign in (+1, -1):
+                b = {k: v.copy() for k, v in a.items()}
+                b["h"] = s.h.copy()
+                b[c][i] = (b[c][i] + sign * eps) % 1.0
+                e2.append(eth(b))
+            grad = (e2[0] - e2[1]) / (2 * eps)
+            scale = np.sqrt(np.mean(s.m ** 2 * (s.ax ** 2 + s.ay ** 2 + s.az ** 2)))
+            assert abs(s.m[i] * acc[i] + grad) < 2e-6 * scale, (i, c)
+
+
+# --------------------------------------------------------------------------
+# Forces: conservation and special cases (Eqs. GRADHMOMEQN, GRADHENEQN,
+# MON97ARTVISC, MON97ENERGYDISS)
+# --------------------------------------------------------------------------
+def test_momentum_and_energy_conserved_pairwise(oracle_mod):
+    """Every term is antisymmetric under i<->j, so sum_i m_i a_i = 0 and
+    sum_i m_i (v_i.a_i + du_i/dt) = 0 to FP64 round-off (Sec. 2.2.1:
+    conservation of momentum and energy)."""
+    O = oracle_mod
+    a, p = ics.random_cloud(500, seed=9, mass_spread=0.5, vel=1.0, u_spread=0.8)
+    P = O.Params(**p)
+    s = _solve(O, P, a)
+    assert O.forces(P, s) == O.OK
+    ma = s.m[:, None] * np.stack([s.ax, s.ay, s.az], 1)
+    assert np.all(np.abs(ma.sum(0)) < 1e-13 * np.abs(ma).sum(0))
+    terms = s.m * (s.vx * s.ax + s.vy * s.ay + s.vz * s.az) + s.m * s.du
+    assert abs(terms.sum()) < 1e-12 * np.abs(terms).sum()
+    # dissipation heats: with viscosity on, total thermal energy rate exceeds
+    # the reversible p dV part
+    P0 = O.Params(**p, alpha_av=0.0, alpha_ac=0.0)
+    s0 = s.copy()
+    assert O.forces(P0, s0) == O.OK
+    assert np.sum(s.m * s.du) > np.sum(s0.m * s0.du)
+
+
+def test_static_gas_has_no_dissipation(oracle_mod):
+    """With v = 0 and uniform u the viscosity (mu_ij = 0) and conductivity
+    (u_i - u_j = 0) terms vanish identically, and du/dt = 0."""
+    O = oracle_mod
+    a, p = ics.lattice(10, seed=2)
+    s1 = _solve(O, O.Params(**p), a)
+    s2 = s1.copy()
+    assert O.forces(O.Params(**p), s1) == O.OK
+    assert O.forces(O.Params(**p, alpha_av=0.0, alpha_ac=0.0), s2) == O.OK
+    assert np.array_equal(s1.ax, s2.ax) and np.array_equal(s1.du, s2.du)
+    assert np.all(s1.du == 0.0)
+
+
+def test_perfect_lattice_is_in_equilibrium(oracle_mod):
+    """On a perfect lattice every particle sees a point-symmetric neighbourhood:
+    all accelerations vanish to round-off."""
+    O = oracle_mod
+    a, p = ics.lattice(12, jitter=0.0)
+    s = _solve(O, O.Params(**p), a)
+    assert O.forces(O.Params(**p), s) == O.OK
+    # scale of one pair term: m P/(rho^2) |grad W| ~ P/rho / h
+    scale = np.max(s.P / s.rho / s.h)
+    assert np.max(np.abs(np.stack([s.ax, s.ay, s.az]))) < 1e-12 * scale
+
+
+def test_galilean_invariance(oracle_mod):
+    """Adding a uniform velocity changes no v_ij, so a and du/dt are unchanged."""
+    O = oracle_mod
+    a, p = ics.random_cloud(300, seed=4, vel=0.5, u_spread=0.3)
+    P = O.Params(**p)
+    s1 = _solve(O, P, a)
+    b = {k: v.copy() for k, v in a.items()}
+    b["vx"] += 3.0
+    b["vz"] -= 1.25
+    s2 = _solve(O, P, b)
+    assert O.forces(P, s1) == O.OK and O.forces(P, s2) == O.OK
+    for f in ("ax", "ay", "az", "du", "vsig"):
+        x1, x2 = getattr(s1, f), getattr(s2, f)
+        assert np.max(np.abs(x1 - x2)) < 1e-11 * np.max(np.abs(x1))
+
+
+def test_isothermal_eos(oracle_mod):
+    """Isothermal EOS (Sec. 4.2): P = c_s^2 rho, c = c_s, u is not evolved."""
+    O = oracle_mod
+    a, p = ics.lattice(10, seed=3)
+    p.update(eos="isothermal", cs_iso=0.7)
+    a["vx"] = np.random.default_rng(1).normal(0, 0.3, len(a["x"]))
+    P = O.Params(**p)
+    s = _solve(O, P, a)
+    assert np.allclose(s.P, 0.49 * s.rho, rtol=1e-15) and np.all(s.c == 0.7)
+    assert O.forces(P, s) == O.OK
+    assert np.all(s.du == 0.0)
+
+
+def test_signal_speed_without_motion(oracle_mod):
+    """Eq. SPH_DT: with v = 0, v_sig,i = max_j (c_i + c_j); uniform c gives 2c."""
+    O = oracle_mod
+    a, p = ics.lattice(10, seed=5)
+    P = O.Params(**p)
+    s = _solve(O, P, a)
+    assert O.forces(P, s) == O.OK
+    assert np.allclose(s.vsig, 2 * s.c, rtol=1e-15)
+    assert O.cfl_dt(P, s) == pytest.approx(0.2 * np.min(s.h / s.vsig), rel=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Neighbour lists (exact FP64 membership)
+# --------------------------------------------------------------------------
+def test_neighbour_lists_match_kdtree(oracle_mod):
+    """Gather lists {j: |r_ij| < 2 h_i} agree with scipy's periodic k-d tree on
+    the same points (pairs within 1e-12 of the boundary excluded)."""
+    from scipy.spatial import cKDTree
+    O = oracle_mod
+    a, p = ics.random_cloud(700, seed=21)
+    P = O.Params(**p)
+    s = _solve(O, P, a)
+    off, idx = O.neighbours(P, s, 0)
+    pos = np.stack([s.x, s.y, s.z], 1)
+    tree = cKDTree(pos, boxsize=1.0)
+    for i in range(0, 700, 7):
+        mine = set(idx[off[i]:off[i + 1]].tolist())
+        ref = set(tree.query_ball_point(pos[i], 2 * s.h[i]))
+        diff = mine ^ ref
+        for j in diff:
+            d = pos[i] - pos[j]
+            d -= np.round(d)
+            assert abs(np.sqrt(d @ d) - 2 * s.h[i]) < 1e-12
+        assert list(idx[off[i]:off[i + 1]]) == sorted(mine)
+
+
+def test_force_lists_are_union_of_supports(oracle_mod):
+    """Force list of i = {j != i : j in gather(i) or i in gather(j)}."""
+    O = oracle_mod
+    a, p = ics.random_cloud(400, seed=8)
+    P = O.Params(**p)
+    s = _solve(O, P, a)
+    og, ig = O.neighbours(P, s, 0)
+    of, jf = O.neighbours(P, s, 1)
+    g = [set(ig[og[i]:og[i + 1]].tolist()) for i in range(s.n)]
+    for i in range(s.n):
+        want = {j for j in range(s.n) if j != i and (j in g[i] or i in g[j])}
+        assert set(jf[of[i]:of[i + 1]].tolist()) == want
+
+
+def test_grid_prefilter_gives_identical_bits(oracle_mod):
+    O = oracle_mod
+    a, p = ics.random_cloud(600, seed=13, vel=0.4, u_spread=0.3)
+    s1 = _solve(O, O.Params(**p), a)
+    s2 = _solve(O, O.Params(**p, use_grid=True), a)
+    assert O.forces(O.Params(**p), s1) == O.OK
+    assert O.forces(O.Params(**p, use_grid=True), s2) == O.OK
+    for f in ("h", "rho", "omega", "ax", "ay", "az", "du", "vsig"):
+        assert np.array_equal(getattr(s1, f), getattr(s2, f)), f
+
+
+# --------------------------------------------------------------------------
+# Edge cases of the solve
+# --------------------------------------------------------------------------
+def test_empty_input(oracle_mod):
+    O = oracle_mod
+    s = O.State(**{k: np.zeros(0) for k in ("x", "y", "z", "vx", "vy", "vz", "u", "m", "h")})
+    assert O.density(O.Params(), s) == O.OK
+    assert O.forces(O.Params(), s) == O.OK
+
+
+def test_too_few_particles_do_not_converge(oracle_mod):
+    """An isolated group of fewer than pi eta^3 ~ 5.4 equal masses has no
+    solution of Eq. HRHO (the density sum never reaches m (eta/h)^3)."""
+    O = oracle_mod
+    rng = np.random.default_rng(0)
+    a = {k: rng.uniform(0, 1, 4) for k in ("x", "y", "z")}
+    a.update(vx=np.zeros(4), vy=np.zeros(4), vz=np.zeros(4), u=np.ones(4), m=np.ones(4),
+             h=np.full(4, 0.1))
+    s = O.State(**a)
+    assert O.density(O.Params(periodic=False), s) == O.ENOCONV
+
+
+def test_box_too_small_is_reported(oracle_mod):
+    """Periodic minimum image needs 2h < L/2."""
+    O = oracle_mod
+    a, p = ics.lattice(4)  # 64 particles: 2h ~ 0.6 > L/2
+    s = O.State(**a)
+    assert O.density(O.Params(**p), s) == O.EBOX
+
+
+def test_free_translation_step(oracle_mod):
+    """Eqs. LFKDK1/2: with no forces (perfect lattice, uniform velocity) a
+    step moves every particle by v dt (wrapped) and leaves v unchanged."""
+    O = oracle_mod
+    a, p = ics.lattice(10, jitter=0.0)
+    a["vx"][:] = 0.3
+    a["vy"][:] = -0.2
+    P = O.Params(**p)
+    s = _solve(O, P, a)
+    assert O.forces(P, s) == O.OK
+    x0, y0 = s.x.copy(), s.y.copy()
+    dt = 0.01
+    assert O.step(P, s, dt) == O.OK
+    assert np.allclose(s.x, (x0 + 0.3 * dt) % 1.0, atol=1e-12)
+    assert np.allclose(s.y, (y0 - 0.2 * dt) % 1.0, atol=1e-12)
+    assert np.allclose(s.vx, 0.3, atol=1e-10) and np.allclose(s.vy, -0.2, atol=1e-10)
+
+
+def test_step_conserves_momentum_and_energy(oracle_mod):
+    """KDK with global dt conserves momentum exactly (pairwise forces) and
+    energy to the integration error, here over a few steps of a random cloud."""
+    O = oracle_mod
+    a, p = ics.random_cloud(400, seed=12, vel=0.3, u_spread=0.5)
+    P = O.Params(**p)
+    s = _solve(O, P, a)
+    assert O.forces(P, s) == O.OK
+    d0 = O.diagnostics(P, s)
+    for _ in range(4):
+        assert O.step(P, s, 0.5 * O.cfl_dt(P, s)) == O.OK
+    d1 = O.diagnostics(P, s)
+    assert np.all(np.abs(d1["momentum"] - d0["momentum"]) < 1e-14)
+    assert abs(d1["energy"] - d0["energy"]) < 1e-4 * d0["energy"]
+    assert d1["mass"] == d0["mass"]
+
+
+def test_conduction_flows_from_hot_to_cold(oracle_mod):
+    """The conductivity term of Eq. MON97ENERGYDISS diffuses u: it conserves
+    sum m u (antisymmetric pairs) and strictly lowers sum m u^2, i.e. heat
+    flows from hot to cold particles.  A sign error in (u_i - u_j) fails."""
+    O = oracle_mod
+    a, p = ics.random_cloud(400, seed=17, vel=0.5, u_spread=0.9)
+    P1 = O.Params(**p, alpha_av=0.0, alpha_ac=1.0)
+    P0 = O.Params(**p, alpha_av=0.0, alpha_ac=0.0)
+    s1 = _solve(O, P1, a)
+    s0 = s1.copy()
+    assert O.forces(P1, s1) == O.OK and O.forces(P0, s0) == O.OK
+    dac = s1.du - s0.du
+    assert abs(np.sum(s1.m * dac)) < 1e-12 * np.sum(np.abs(s1.m * dac))
+    assert np.sum(s1.m * s1.u * dac) < 0
+    # no conduction between particles at rest relative to each other
+    b = {k: v.copy() for k, v in a.items()}
+    for c in ("vx", "vy", "vz"):
+        b[c][:] = 0.0
+    t1 = _solve(O, P1, b)
+    t0 = t1.copy()
+    assert O.forces(P1, t1) == O.OK and O.forces(P0, t0) == O.OK
+    assert np.array_equal(t1.du, t0.du)
