@@ -1,0 +1,339 @@
+"""Benchmark of the GB300 SPH hot path: one KDK step of the 3D Sod shock tube
+(128x16x16 | 64x8x8 = 36864 particles, periodic [0,1)x[0,1/8)^2, gamma 1.4),
+FP32 pair arithmetic with FP64 positions, integration and reductions.
+
+One step = kick-drift, Morton sort, leaf/tree build, density/h Newton-Raphson
+solve, forces with viscosity and conductivity, closing kick and the FP64
+reductions (every row of the hot path), replayed as one captured CUDA graph.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  Under torchrun (N > 1) every rank steps its own replica
+of the problem (independent problems, no data-path collective); the timing is
+barrier-bracketed and the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SPH particle-updates/s (density+h+force)"
+UNIT = "particle-updates/s"
+WORKLOAD = "sod3d_36864: 128x16x16 | 64x8x8 lattice, periodic [0,1)x[0,1/8)^2, gamma=1.4, CFL KDK steps"
+# algorithmic flops per in-range pair, counted from the kernels' source
+FLOPS_DENSITY_PAIR = 19   # per pair per Newton-Raphson pass (q, f, f', two accumulations)
+FLOPS_FORCE_PAIR = 101    # per ordered pair (pressure, viscosity, conduction, energy, TwoSum-compensated m a)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def workload():
+    from paper_1709_04488_gb300 import ics
+    return ics.sod()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_sample(seconds=12.0, max_steps=50):
+    """The oracle as it stands, stepping the same workload on the host cores
+    until about `seconds` have passed; returns (updates/s, cores, steps, n)."""
+    import oracle as O
+    a, p = workload()
+    P = O.Params(**p, use_grid=True)
+    s = O.State(**a)
+    t0 = time.perf_counter()
+    assert O.density(P, s) == O.OK and O.forces(P, s) == O.OK
+    t_setup = time.perf_counter() - t0
+    steps = 0
+    t0 = time.perf_counter()
+    while steps < max_steps and (steps == 0 or time.perf_counter() - t0 < seconds):
+        assert O.step(P, s, O.cfl_dt(P, s)) == O.OK
+        steps += 1
+    dt = time.perf_counter() - t0
+    return s.n * steps / dt, O.num_threads(), steps, s.n, t_setup
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    a, p = workload()
+    P = O.Params(**p, use_grid=True)
+    s = O.State(**a)
+    assert O.density(P, s) == O.OK and O.forces(P, s) == O.OK
+    for _ in range(args.warmup):
+        assert O.step(P, s, O.cfl_dt(P, s)) == O.OK
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        assert O.step(P, s, O.cfl_dt(P, s)) == O.OK
+    el = time.perf_counter() - t0
+    v = s.n * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "precision": "fp64 CPU oracle (grid prefilter)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                         "sample": f"{args.steps} timed KDK steps of the full {s.n}-particle workload "
+                                   f"after {args.warmup} untimed"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.p is not None:
+            time.sleep(0.2)
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.f.name) as fh:
+                for line in fh:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            try:
+                os.unlink(self.f.name)
+            except Exception:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def peak_fp32_tflops(sm_count):
+    """FP32 ALU roof: SMs x 128 FP32 lanes x 2 flop (FMA) x max SM clock
+    (measured max clock if recorded, else the part's 2070 MHz)."""
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            mhz = float(json.load(fh).get("sm_max_mhz", mhz))
+    except Exception:
+        pass
+    return sm_count * 128 * 2 * mhz * 1e6 / 1e12, mhz
+
+
+def time_steps(S, prob, stream, torch, K, flush, stage=False):
+    """K CFL steps (graph replays), L2 flushed between steps outside the
+    timed events; returns per-step ms and (optionally) stage times and the
+    pair counters of each step."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    stages, dens_pairs, force_pairs = [], [], []
+    for k in range(K):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev[k][0].record(stream)
+        S.check(S.sph_run(prob.ctx, 1), "sph_run")
+        ev[k][1].record(stream)
+        if stage:
+            stream.synchronize()
+            stages.append(S.sph_stage_times(prob.ctx))
+            d = prob.diagnostics()
+            dens_pairs.append(d.density_pairs)
+            force_pairs.append(d.force_pairs)
+    stream.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    return ms, stages, dens_pairs, force_pairs
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1709_04488_gb300 import build as B
+    from paper_1709_04488_gb300 import sph as S
+    if not os.path.exists(S.LIB_PATH):
+        B.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)
+    a, p = workload()
+    n = len(a["x"])
+    prm = S.make_params(S.PREC_MIXED, **p, flags=S.FLAG_ASYNC | S.FLAG_TIMING)
+    with torch.cuda.stream(stream):
+        prob = S.Problem(a, prm, device=dev, stream=stream)
+        S.check(S.sph_density_h(prob.ctx), "sph_density_h")
+        S.check(S.sph_forces(prob.ctx), "sph_forces")
+        S.check(S.sph_sync(prob.ctx), "sph_sync")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    kernels_per_step = S.sph_step_kernel_count(prob.ctx)  # builds the step graph (one step)
+    for _ in range(max(args.warmup, 3) - 1):
+        S.check(S.sph_run(prob.ctx, 1), "sph_run")
+    S.check(S.sph_sync(prob.ctx), "sph_sync")
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with Clocks(local) as clk:
+        ms, _, _, _ = time_steps(S, prob, stream, torch, args.steps, flush)
+    torch.cuda.synchronize(dev)
+    S.check(S.sph_sync(prob.ctx), "sph_sync")
+    total_ms = float(np.sum(ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        total_ms = float(t.item())
+    clocks = clk.summary()
+    value = world * n * args.steps / (total_ms * 1e-3)
+
+    # stage times and pair counts (separate pass: a host sync per step)
+    _, stages, dp, fp = time_steps(S, prob, stream, torch, min(args.steps, 20), flush, stage=True)
+    st = np.mean(np.array(stages), axis=0)
+    dens_ms, force_ms = st[S.STAGES.index("density")], st[S.STAGES.index("forces")]
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak, mhz = peak_fp32_tflops(sm_count)
+    if force_ms >= dens_ms:
+        kern, flops, t_ms = "k_forces", np.mean(fp) * FLOPS_FORCE_PAIR, force_ms
+    else:
+        kern, flops, t_ms = "k_density", np.mean(dp) * FLOPS_DENSITY_PAIR, dens_ms
+    achieved = flops / (t_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": None,
+            "peak_basis": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz",
+            "stage_ms": {k: float(v) for k, v in zip(S.STAGES, st)},
+            "density_pairs_per_step": float(np.mean(dp)), "force_pairs_per_step": float(np.mean(fp))}
+
+    # end to end through the C ABI with host buffers: H2D of the step's input
+    # state from pinned memory, one step, D2H of the resulting state
+    fields_in = ["x", "y", "z", "vx", "vy", "vz", "u", "m", "h", "ax", "ay", "az", "du"]
+    fields_out = ["x", "y", "z", "vx", "vy", "vz", "u", "h", "rho", "ax", "ay", "az", "du"]
+    host = {f: prob.t[f][:n].cpu().pin_memory() for f in set(fields_in + fields_out)}
+    Ke = max(5, min(args.steps, 20))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_ms = 0.0
+    for _ in range(Ke):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            for f in fields_in:
+                prob.t[f][:n].copy_(host[f], non_blocking=True)
+        S.check(S.sph_run(prob.ctx, 1), "sph_run")
+        with torch.cuda.stream(stream):
+            for f in fields_out:
+                host[f].copy_(prob.t[f][:n], non_blocking=True)
+        e1.record(stream)
+        stream.synchronize()
+        e2e_ms += e0.elapsed_time(e1)
+    e2e = {"value": world * n * Ke / (e2e_ms * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": 8 * n * len(fields_in), "d2h_bytes_per_step": 8 * n * len(fields_out)}
+
+    # plain FP64 single-problem GPU path on the same workload
+    fp64 = None
+    if not args.no_fp64:
+        prm64 = S.make_params(S.PREC_FP64, **p, flags=S.FLAG_ASYNC)
+        with torch.cuda.stream(stream):
+            p64 = S.Problem(a, prm64, device=dev, stream=stream)
+            S.check(S.sph_density_h(p64.ctx), "sph_density_h")
+            S.check(S.sph_forces(p64.ctx), "sph_forces")
+        S.sph_step_kernel_count(p64.ctx)
+        S.check(S.sph_run(p64.ctx, 1), "sph_run")
+        ms64, _, _, _ = time_steps(S, p64, stream, torch, 5, flush)
+        v64 = n * len(ms64) / (np.sum(ms64) * 1e-3)
+        fp64 = {"value": v64, "unit": UNIT, "ms_per_step": float(np.mean(ms64)),
+                "speedup_of_mixed": (value / world) / v64}
+        p64.close()
+
+    diag = prob.diagnostics()
+    prob.close()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        v, cores, steps, nn, _ = oracle_sample()
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{steps} KDK steps of the full {nn}-particle workload (grid prefilter)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles": n, "precision": "mixed (FP32 pairs, FP64 state)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "flushed (256 MiB write) between timed steps", "graph": "one CUDA graph per step",
+                   "lanes_per_particle": int(prob.params.lanes_per_particle) or "auto"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": kernels_per_step * args.steps,
+        "clocks": clocks, "fp64_gpu": fp64,
+        "step_diag": {"nr_iterations": diag.nr_iterations, "nr_max": diag.nr_max, "fallback": diag.fallback,
+                      "leaves": diag.leaves, "ngb_mean": diag.ngb_mean, "candidates": diag.candidates},
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,277 @@
+/*
+ * sph.h - C ABI of the GB300 grad-h SPH neighbour-loop library (libsph.so).
+ *
+ * The library computes, on one NVIDIA GB300 (sm_103a), the per-step hot path
+ * of the grad-h SPH method described by Hubber, Rosotti & Booth (2018),
+ * "GANDALF - Graphical Astrophysics code for N-body Dynamics And Lagrangian
+ * Fluids" (arXiv:1709.04488):
+ *   - neighbour search (Morton-key sort, leaf cells, a tree over the leaves),
+ *   - the density / smoothing-length solve, Eqs. SPHRHO and HRHO, iterated by
+ *     Newton-Raphson to convergence, with the grad-h term Omega, Eq. OMEGA,
+ *   - pressure accelerations and energy rates, Eqs. GRADHMOMEQN and
+ *     GRADHENEQN, with Monaghan (1997) viscosity and Wadsley (2008)
+ *     conductivity, Eqs. MON97ARTVISC and MON97ENERGYDISS,
+ *   - the CFL time-step, Eq. SPH_DT, and the global-step leapfrog
+ *     kick-drift-kick, Eqs. LFKDK1 and LFKDK2.
+ * The kernel is the M4 cubic spline with support 2h (Sec. 2).
+ *
+ * Conventions shared by every entry point
+ *   - All functions return an int status: SPH_OK (0) or a negative SPH_E*
+ *     code.  sph_last_error() returns a message for the calling thread's last
+ *     failure.  No function aborts the process.
+ *   - Device memory is owned by the caller (e.g. PyTorch tensors).  The library
+ *     never allocates device memory; the caller passes particle arrays and a
+ *     workspace whose size sph_workspace_bytes() reports.  Host memory passed
+ *     in is only read during the call.  A context (sph_ctx) is a small host
+ *     object that records pointers, sizes and the stream; it owns no device
+ *     memory.
+ *   - All work is enqueued on the caller's CUDA stream (a cudaStream_t passed
+ *     as void*; NULL is the legacy default stream).  Unless the context was
+ *     created with SPH_FLAG_ASYNC, each compute call synchronises that stream
+ *     before returning so that it can report device-side errors; with
+ *     SPH_FLAG_ASYNC it returns after enqueueing and sph_sync() reports them.
+ *   - Particle arrays are structure-of-arrays, FP64, length n, in the caller's
+ *     particle order, which the library never changes.
+ */
+#ifndef SPH_H
+#define SPH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define SPH_OK 0
+#define SPH_EINVAL -1       /* bad parameter, size or pointer                      */
+#define SPH_EBOX -2         /* periodic box too small: 2h reached half a box side  */
+#define SPH_ENOCONV -3      /* h-rho iteration did not converge for some particle  */
+#define SPH_ENONFINITE -4   /* NaN or Inf met in inputs or results                 */
+#define SPH_ETIMEOUT -5     /* a bounded device wait gave up                       */
+#define SPH_ETOOBIG -6      /* request larger than the server's memory budget      */
+#define SPH_EBUSY -7        /* server queue full                                   */
+#define SPH_EAGAIN -8       /* result not ready yet                                */
+#define SPH_ECUDA -9        /* a CUDA runtime call failed                          */
+#define SPH_ENOSPACE -10    /* workspace too small                                 */
+
+/* ---- parameters -------------------------------------------------------- */
+#define SPH_EOS_ADIABATIC 0  /* P = (gamma-1) rho u, c = sqrt(gamma P / rho) (Sec. 2.2.1) */
+#define SPH_EOS_ISOTHERMAL 1 /* P = cs^2 rho, c = cs; u is not evolved (Sec. 4.2)         */
+
+#define SPH_PREC_FP64 0      /* every step in FP64 (the plain reference path)              */
+#define SPH_PREC_MIXED 1     /* FP32 pair arithmetic; FP64 positions, centre differences, */
+                             /* integration, accumulation of a and the global reductions  */
+
+#define SPH_FLAG_ASYNC 1u    /* compute calls return without synchronising the stream     */
+#define SPH_FLAG_TIMING 2u   /* record CUDA events around the stages of every step        */
+
+/* stages reported by sph_stage_times */
+#define SPH_STAGE_KICK_DRIFT 0   /* half kick + drift + predictor                 */
+#define SPH_STAGE_SORT 1         /* domain, Morton keys, radix sort, gather       */
+#define SPH_STAGE_TREE 2         /* leaves, leaf boxes, tree levels              */
+#define SPH_STAGE_DENSITY 3      /* density / h solve (incl. the slow path)      */
+#define SPH_STAGE_REFIT 4        /* smoothing-sphere boxes                       */
+#define SPH_STAGE_FORCES 5       /* accelerations, du/dt, signal speeds          */
+#define SPH_STAGE_CLOSE 6        /* closing half kick, reductions, CFL step      */
+#define SPH_NSTAGES 7
+
+typedef struct {
+    int periodic;          /* 1: periodic box [box_lo, box_lo + box_len) per axis; 0: isolated */
+    double box_lo[3];
+    double box_len[3];
+    int eos;               /* SPH_EOS_*                                                */
+    double gamma;          /* ratio of specific heats (adiabatic)                      */
+    double cs_iso;         /* isothermal sound speed                                   */
+    double eta;            /* h = eta (m/rho)^(1/3), Eq. HRHO; paper default 1.2       */
+    double alpha_av;       /* viscosity strength alpha_AV (paper: 1)                   */
+    double beta_av;        /* signal-speed factor beta_AV = 2 alpha_AV (Sec. 2.2.1)    */
+    double alpha_ac;       /* conductivity strength alpha_AC (0 disables)              */
+    double c_cfl;          /* Courant factor of Eq. SPH_DT (paper: ~0.2)               */
+    double h_tol;          /* stop the h iteration when |dh|/h < h_tol (0: per precision)*/
+    int h_max_iter;        /* iteration cap (0: 50)                                     */
+    int precision;         /* SPH_PREC_*                                               */
+    int kernel;            /* 0 = M4 cubic spline (the only value accepted)            */
+    int leaf_size;         /* particles per leaf, 8/16/32 (0: chosen by the autotuner) */
+    int lanes_per_particle;/* 1/2/4 lanes of a warp per particle (0: autotuner)        */
+    unsigned flags;        /* SPH_FLAG_*                                               */
+} sph_params;
+
+/* Caller-owned device arrays, FP64, length n, caller's particle order.
+ * Inputs: x,y,z, vx,vy,vz, u, m, and h (the starting guess of the iteration;
+ * h <= 0 asks for a default guess).  Outputs written by the library:
+ * h, rho, omega, P, c (density solve), ax,ay,az, du (= du/dt), vsig (forces).
+ * sph_step also advances x, v and u in place. */
+typedef struct {
+    double *x, *y, *z;
+    double *vx, *vy, *vz;
+    double *u, *m, *h;
+    double *rho, *omega, *P, *c;
+    double *ax, *ay, *az, *du, *vsig;
+} sph_state;
+
+/* Per-call diagnostics (FP64 reductions over the particles, Sec. 2.2.1
+ * conservation; counters of the work done). */
+typedef struct {
+    double mass;           /* sum m                                   */
+    double momentum[3];    /* sum m v                                 */
+    double energy;         /* sum m (v^2/2 + u)  (u only if adiabatic) */
+    double force_sum[3];   /* sum m a                                 */
+    double dEdt;           /* sum m (v.a + du/dt)                     */
+    double dt_next;        /* C_CFL min h / v_sig (Eq. SPH_DT)         */
+    double time;           /* simulated time advanced by sph_step     */
+    int64_t steps;         /* steps taken                             */
+    int64_t nr_iterations; /* Newton-Raphson iterations, summed        */
+    int32_t nr_max;        /* largest iteration count of one particle */
+    int32_t ngb_min, ngb_max; /* neighbours inside 2h (incl. self)     */
+    double ngb_mean;
+    int64_t density_pairs; /* in-range (i,j) pair evaluations, density pass, all iterations */
+    int64_t force_pairs;   /* in-range (i,j) pair evaluations, force pass                  */
+    int64_t candidates;    /* staged candidate pairs tested, both passes                   */
+    int64_t fallback;      /* particles finished by the slow fallback path                 */
+    int64_t leaves;        /* leaves built                                                  */
+    int32_t status;        /* device-side status (SPH_OK or SPH_E*)                         */
+    int32_t unconverged;   /* particles that met SPH_ENOCONV                                */
+} sph_diag;
+
+typedef struct sph_ctx sph_ctx;
+
+/* Fill *p with the paper's defaults (eta 1.2, alpha_AV 1, beta_AV 2,
+ * alpha_AC 1, C_CFL 0.2), periodic unit cube, adiabatic gamma 5/3, mixed
+ * precision, autotuned launch shape. */
+int sph_params_default(sph_params *p);
+
+/* Bytes of device workspace a context of n particles needs (0 on bad input). */
+size_t sph_workspace_bytes(int64_t n, const sph_params *p);
+
+/* Create a context.  state: caller-owned device arrays (see sph_state);
+ * workspace: device memory of at least sph_workspace_bytes(n, p) bytes,
+ * 256-byte aligned, owned by the caller and reserved for this context until
+ * sph_destroy.  stream: cudaStream_t as void*.  Validates the parameters
+ * (SPH_EINVAL) and copies them.  n may be 0. */
+int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *state,
+              void *workspace, size_t ws_bytes, void *stream);
+
+/* Neighbour search and the density / smoothing-length solve (Eqs. SPHRHO,
+ * HRHO, OMEGA) at the current positions, starting from state->h.  Writes h,
+ * rho, omega, P, c.  SPH_ENOCONV if a particle failed to converge within
+ * h_max_iter iterations (results for the others are valid); SPH_EBOX if 2h
+ * reached half a periodic box side. */
+int sph_density_h(sph_ctx *ctx);
+
+/* Accelerations, du/dt and signal speeds (Eqs. GRADHMOMEQN, GRADHENEQN,
+ * MON97ARTVISC, MON97ENERGYDISS, SPH_DT) from the current h, rho, omega, P, c
+ * (run sph_density_h first).  Also updates the CFL time-step returned by
+ * sph_diagnostics.dt_next. */
+int sph_forces(sph_ctx *ctx);
+
+/* One global-step kick-drift-kick (Eqs. LFKDK1/2): half kick and drift with
+ * the stored a and du/dt, density solve and forces at the new positions with
+ * the predicted v and u, closing half kick.  dt > 0 uses that step; dt <= 0
+ * uses the CFL step computed by the previous force evaluation.  The state must
+ * hold a valid force evaluation (sph_density_h + sph_forces once after setup).
+ * If dt_used is not NULL the step is written there (this synchronises). */
+int sph_step(sph_ctx *ctx, double dt, double *dt_used);
+
+/* Take nsteps steps with the CFL time-step without host round trips (one
+ * captured CUDA graph replayed nsteps times). */
+int sph_run(sph_ctx *ctx, int nsteps);
+
+/* Wait for the context's queued work and report the device-side status. */
+int sph_sync(sph_ctx *ctx);
+
+/* Diagnostics of the last compute call (synchronises). */
+int sph_diagnostics(sph_ctx *ctx, sph_diag *out);
+
+/* Exact FP64 neighbour lists in CSR form, ids ascending (Sec. 2.6 tree walk
+ * retrieves them per leaf).  kind 0: {j : |r_ij|^2 < (2 h_i)^2} including i;
+ * kind 1: {j != i : |r_ij|^2 < (2 max(h_i,h_j))^2}.  h_in: device array of n
+ * smoothing lengths to use (NULL: state->h).  Distances are formed in FP64 as
+ * dx*dx + dy*dy + dz*dz without fused multiply-add, after the periodic minimum
+ * image of each coordinate difference.  offsets (n+1 entries) and idx (cap
+ * entries) are device arrays; *total receives the number of entries (if it
+ * exceeds cap, idx holds the first cap and SPH_ENOSPACE is returned). */
+int sph_neighbours(sph_ctx *ctx, int kind, const double *h_in, int64_t *offsets, int32_t *idx,
+                   int64_t cap, int64_t *total);
+
+/* Durations in milliseconds of the stages of the last step or compute call
+ * (CUDA events on the context's stream; needs SPH_FLAG_TIMING, synchronises).
+ * Stages that did not run report 0.  ms must hold SPH_NSTAGES doubles. */
+int sph_stage_times(sph_ctx *ctx, double *ms);
+
+/* Number of kernel launches one step makes (the kernel nodes of the captured
+ * step graph; builds the graph if sph_run has not yet done so, which takes one
+ * step).  Needs a non-default stream. */
+int sph_step_kernel_count(sph_ctx *ctx, int *kernels);
+
+/* Release the context (frees no caller memory). */
+int sph_destroy(sph_ctx *ctx);
+
+/* ---- batching: many independent problems in one launch set ------------- */
+/* Bytes of device workspace for a batch of the given contexts. */
+size_t sph_batch_workspace_bytes(sph_ctx *const *ctxs, int nctx);
+
+/* Advance every context by nsteps CFL steps; each kernel of a step runs once
+ * over all problems (work lists of (problem, leaf) items).  Every problem's
+ * result equals the result of stepping it alone.  All contexts must use the
+ * same precision and stream; workspace is caller-owned device memory of at
+ * least sph_batch_workspace_bytes(). */
+int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, size_t ws_bytes);
+
+/* ---- serving: continuous batching of independent runs ------------------ */
+typedef struct {
+    void *pool;            /* caller-owned device memory the server carves slots from */
+    size_t pool_bytes;     /* admission budget (bytes of pool)                         */
+    int max_slots;         /* concurrent problems (<= 4096)                            */
+    int max_queue;         /* queued requests before SPH_EBUSY                         */
+    void *stream;          /* cudaStream_t as void*                                    */
+    int precision;         /* SPH_PREC_* for every request                             */
+} sph_server_cfg;
+
+typedef struct {
+    int64_t n;             /* particles                                    */
+    const double *x, *y, *z, *vx, *vy, *vz, *u, *m, *h; /* host arrays, copied at submit */
+    sph_params params;     /* per-request physics (precision/flags ignored) */
+    int nsteps;            /* CFL steps to take                            */
+    double arrival;        /* arrival time on the server's clock (seconds) */
+} sph_request;
+
+typedef struct {
+    int status;            /* SPH_OK or error                               */
+    int64_t n;
+    int steps_done;
+    double arrival, admitted, completed; /* server-clock seconds             */
+    double t_sim;          /* simulated time reached                         */
+    double *x, *y, *z, *vx, *vy, *vz, *u, *h, *rho; /* host arrays of n, caller-owned, filled at poll (may be NULL) */
+} sph_result;
+
+typedef struct sph_server sph_server;
+
+int sph_server_create(sph_server **out, const sph_server_cfg *cfg);
+/* Queue a request; copies its host arrays.  SPH_ETOOBIG if it can never fit
+ * the pool, SPH_EBUSY if the queue is full.  *ticket identifies it. */
+int sph_server_submit(sph_server *s, const sph_request *req, uint64_t *ticket);
+/* Drive the loop until now >= until (server clock) or all work is done:
+ * admit queued requests whose arrival time has passed while slots and pool
+ * memory allow, advance every resident problem by one batched step per tick,
+ * retire finished ones.  virtual_clock != 0 advances the clock by the measured
+ * GPU time of each tick instead of reading the wall clock. */
+int sph_server_run(sph_server *s, double until, int virtual_clock);
+/* Fetch a finished result (SPH_EAGAIN if not finished).  Host arrays in out
+ * that are not NULL receive the final particle state. */
+int sph_server_poll(sph_server *s, uint64_t ticket, sph_result *out);
+/* Current server clock (seconds). */
+double sph_server_clock(const sph_server *s);
+int sph_server_destroy(sph_server *s);
+
+/* Message describing the calling thread's last error ("" if none). */
+const char *sph_last_error(void);
+
+/* Library version string. */
+const char *sph_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPH_H */

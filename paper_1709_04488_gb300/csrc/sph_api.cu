@@ -1,0 +1,729 @@
+// Host side of the C ABI (include/sph.h): parameter validation, workspace
+// layout, context and batch bookkeeping, launch sequences, CUDA-graph capture
+// of the step and status reporting.  No device memory is allocated here; every
+// array lives in caller-owned workspaces.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+static thread_local std::string g_err;
+
+static int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CU(call)                                                                                     \
+    do {                                                                                             \
+        cudaError_t e_ = (call);                                                                     \
+        if (e_ != cudaSuccess) return fail(SPH_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                                           __FILE__, __LINE__);                                      \
+    } while (0)
+
+DevInfo dev_info()
+{
+    static int cached_dev = -1, cached_sms = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != cached_dev) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cached_sms = sms > 0 ? sms : 1;
+        cached_dev = dev;
+    }
+    return DevInfo{cached_sms};
+}
+
+// ---- workspace layout -------------------------------------------------------
+struct Carver {
+    char *base;
+    size_t off = 0;
+    template <typename T>
+    T *take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += sizeof(T) * (count > 0 ? count : 1);
+        return p;
+    }
+};
+
+// Carve the per-step scratch arrays for `ntot` particles over `nprob` problems.
+static void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precision)
+{
+    const long long n = ntot > 0 ? ntot : 1;
+    const size_t v4 = precision == SPH_PREC_FP64 ? sizeof(dbl4) : sizeof(float4);
+    const long long nblk = (n + 2047) / 2048;
+    b.keys[0] = c.take<unsigned long long>(n);
+    b.keys[1] = c.take<unsigned long long>(n);
+    b.vals[0] = c.take<unsigned>(n);
+    b.vals[1] = c.take<unsigned>(n);
+    b.hist = c.take<unsigned>(256 * nblk);
+    b.scan_aux = c.take<unsigned>(nblk + 1);
+    b.perm = c.take<int>(n);
+    double **sd[] = {&b.sx, &b.sy, &b.sz, &b.sh, &b.sm, &b.srho, &b.somega, &b.sP, &b.sc,
+                     &b.vpx, &b.vpy, &b.vpz, &b.up};
+    for (double **p : sd) *p = c.take<double>(n);
+    void **st[] = {&b.pm, &b.ph, &b.vc, &b.th};
+    for (void **p : st) *p = c.take<char>(v4 * n);
+    b.flag = c.take<unsigned>(n);
+    const long long ml = leaves_upper_bound(n);
+    b.max_leaves = (int)ml;
+    b.leaf_start = c.take<int>(ml + 1);
+    b.leaf_pid = c.take<int>(ml);
+    b.leaf_c = c.take<double>(3 * ml);
+    long long cap = ml;
+    for (int l = 0; l <= kMaxLevels; ++l) {
+        b.node_cap[l] = (int)cap;
+        b.nodes[l] = c.take<NodeBox>(cap);
+        cap = cap / kBranch + nprob + 1;
+    }
+    b.fallback_list = c.take<int>(n);
+    b.counters = c.take<int>(16);
+    b.scratch64 = c.take<long long>(8);
+}
+
+static void carve_tables(Carver &c, BatchView &b, int nprob)
+{
+    b.nprob = nprob;
+    b.prob = c.take<ProbStatic>(nprob);
+    b.dyn = c.take<ProbDyn>(nprob);
+    b.prob_base = c.take<long long>(nprob + 1);
+}
+
+static int key_bits_for(int nprob)
+{
+    int bits = 0;
+    while ((1 << bits) < nprob) ++bits;
+    return kMortonTotal + bits;
+}
+
+static int mask_of(int lpp) { return lpp == 1 ? 1 : lpp == 2 ? 2 : lpp == 4 ? 4 : 8; }
+
+// Launch shape per problem size (the autotuner's table; see autotune.py for
+// how the buckets were chosen).  Small problems spread a particle over more
+// lanes so that the GPU stays full.
+static int choose_lpp(long long n, int precision, int requested)
+{
+    int l = requested;
+    if (l == 0) {
+        if (n <= 200000) l = 4;
+        else if (n <= 2000000) l = 2;
+        else l = 1;
+    }
+    if (l != 1 && l != 2 && l != 4 && l != 8) l = 4;
+    if (precision == SPH_PREC_FP64) l = (l >= 4) ? 4 : 2;
+    return l;
+}
+
+}  // namespace sph
+
+using namespace sph;
+
+struct sph_ctx {
+    sph_params prm;
+    long long n;
+    sph_state st;
+    void *ws;
+    size_t ws_bytes;
+    cudaStream_t stream;
+    int lpp;
+    BatchView bv;
+    ProbDiag *diag;
+    ProbStatic host_ps;
+    bool have_forces;
+    cudaGraphExec_t graph;
+    int graph_kernels;
+    cudaEvent_t ev[SPH_NSTAGES + 1];
+    bool timing;
+    bool stage_ran[SPH_NSTAGES];
+};
+
+static void clear_ran(sph_ctx *c)
+{
+    for (int k = 0; k < SPH_NSTAGES; ++k) c->stage_ran[k] = false;
+}
+
+static int validate(const sph_params *p)
+{
+    if (!p) return fail(SPH_EINVAL, "params is NULL");
+    if (p->kernel != 0) return fail(SPH_EINVAL, "kernel %d not supported (0 = M4 cubic spline)", p->kernel);
+    if (p->periodic != 0 && p->periodic != 1) return fail(SPH_EINVAL, "periodic must be 0 or 1");
+    if (p->periodic)
+        for (int a = 0; a < 3; ++a)
+            if (!(p->box_len[a] > 0) || !std::isfinite(p->box_len[a]) || !std::isfinite(p->box_lo[a]))
+                return fail(SPH_EINVAL, "periodic box_len[%d] must be positive and finite", a);
+    if (p->eos != SPH_EOS_ADIABATIC && p->eos != SPH_EOS_ISOTHERMAL) return fail(SPH_EINVAL, "unknown eos %d", p->eos);
+    if (p->eos == SPH_EOS_ADIABATIC && !(p->gamma > 1.0)) return fail(SPH_EINVAL, "gamma must exceed 1");
+    if (p->eos == SPH_EOS_ISOTHERMAL && !(p->cs_iso > 0)) return fail(SPH_EINVAL, "cs_iso must be positive");
+    if (!(p->eta > 0) || !std::isfinite(p->eta)) return fail(SPH_EINVAL, "eta must be positive");
+    if (!(p->alpha_av >= 0) || !(p->beta_av >= 0) || !(p->alpha_ac >= 0))
+        return fail(SPH_EINVAL, "dissipation coefficients must be non-negative");
+    if (!(p->c_cfl > 0)) return fail(SPH_EINVAL, "c_cfl must be positive");
+    if (!(p->h_tol >= 0) || p->h_max_iter < 0) return fail(SPH_EINVAL, "bad h_tol / h_max_iter");
+    if (p->precision != SPH_PREC_FP64 && p->precision != SPH_PREC_MIXED)
+        return fail(SPH_EINVAL, "unknown precision %d", p->precision);
+    if (p->lanes_per_particle != 0 && p->lanes_per_particle != 1 && p->lanes_per_particle != 2 &&
+        p->lanes_per_particle != 4 && p->lanes_per_particle != 8)
+        return fail(SPH_EINVAL, "lanes_per_particle must be 0, 1, 2, 4 or 8");
+    if (p->leaf_size != 0 && p->leaf_size != 4 && p->leaf_size != 8 && p->leaf_size != 16 && p->leaf_size != 32)
+        return fail(SPH_EINVAL, "leaf_size must be 0, 4, 8, 16 or 32");
+    return SPH_OK;
+}
+
+static PhysParams phys_of(const sph_params *p)
+{
+    PhysParams ph;
+    memset(&ph, 0, sizeof ph);
+    ph.periodic = p->periodic;
+    ph.eos = p->eos;
+    for (int a = 0; a < 3; ++a) {
+        ph.box_lo[a] = p->box_lo[a];
+        ph.box_len[a] = p->periodic ? p->box_len[a] : 0.0;
+    }
+    ph.gamma = p->gamma;
+    ph.cs_iso = p->cs_iso;
+    ph.eta = p->eta;
+    ph.alpha_av = p->alpha_av;
+    ph.beta_av = p->beta_av;
+    ph.alpha_ac = p->alpha_ac;
+    ph.c_cfl = p->c_cfl;
+    ph.h_tol = p->h_tol > 0 ? p->h_tol : (p->precision == SPH_PREC_FP64 ? 1e-13 : 1e-6);
+    ph.h_max_iter = p->h_max_iter > 0 ? p->h_max_iter : 50;
+    return ph;
+}
+
+static int lpp_of(const sph_params *p, long long n)
+{
+    int req = p->lanes_per_particle;
+    if (req == 0 && p->leaf_size != 0) req = 32 / p->leaf_size;
+    return choose_lpp(n, p->precision, req);
+}
+
+static int status_to_code(unsigned st)
+{
+    if (st & ST_NONFINITE) return fail(SPH_ENONFINITE, "non-finite value in the results");
+    if (st & ST_BOX) return fail(SPH_EBOX, "smoothing length reached a quarter of the periodic box");
+    if (st & ST_TIMEOUT) return fail(SPH_ETIMEOUT, "a bounded device wait gave up");
+    if (st & ST_OVERFLOW) return fail(SPH_ENOSPACE, "an internal capacity was exceeded");
+    if (st & ST_NOCONV) return fail(SPH_ENOCONV, "h-rho iteration did not converge for some particles");
+    return SPH_OK;
+}
+
+extern "C" {
+
+const char *sph_last_error(void) { return g_err.c_str(); }
+
+const char *sph_version(void) { return "gb300-sph 0.1 (sm_103a)"; }
+
+int sph_params_default(sph_params *p)
+{
+    if (!p) return fail(SPH_EINVAL, "params is NULL");
+    memset(p, 0, sizeof *p);
+    p->periodic = 1;
+    for (int a = 0; a < 3; ++a) {
+        p->box_lo[a] = 0.0;
+        p->box_len[a] = 1.0;
+    }
+    p->eos = SPH_EOS_ADIABATIC;
+    p->gamma = 5.0 / 3.0;
+    p->cs_iso = 1.0;
+    p->eta = 1.2;
+    p->alpha_av = 1.0;
+    p->beta_av = 2.0;
+    p->alpha_ac = 1.0;
+    p->c_cfl = 0.2;
+    p->h_tol = 0.0;
+    p->h_max_iter = 50;
+    p->precision = SPH_PREC_MIXED;
+    return SPH_OK;
+}
+
+size_t sph_workspace_bytes(int64_t n, const sph_params *p)
+{
+    if (n < 0 || validate(p) != SPH_OK) return 0;
+    Carver c{nullptr};
+    c.take<ProbDiag>(1);
+    BatchView b;
+    memset(&b, 0, sizeof b);
+    carve_tables(c, b, 1);
+    carve_arrays(c, b, n, 1, p->precision);
+    return c.off + 256;
+}
+
+int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *state, void *workspace,
+              size_t ws_bytes, void *stream)
+{
+    if (!out) return fail(SPH_EINVAL, "out is NULL");
+    *out = nullptr;
+    int rc = validate(p);
+    if (rc) return rc;
+    if (n < 0 || n > (int64_t)1 << 30) return fail(SPH_EINVAL, "n = %lld out of range", (long long)n);
+    if (!state) return fail(SPH_EINVAL, "state is NULL");
+    if (n > 0) {
+        const double *req[] = {state->x, state->y, state->z, state->vx, state->vy, state->vz, state->u,
+                               state->m, state->h, state->rho, state->omega, state->P, state->c,
+                               state->ax, state->ay, state->az, state->du, state->vsig};
+        for (const double *q : req)
+            if (!q) return fail(SPH_EINVAL, "a state array is NULL");
+    }
+    size_t need = sph_workspace_bytes(n, p);
+    if (!workspace || ws_bytes < need)
+        return fail(SPH_ENOSPACE, "workspace of %zu bytes needed, %zu given", need, ws_bytes);
+    if (((uintptr_t)workspace) & 255) return fail(SPH_EINVAL, "workspace must be 256-byte aligned");
+    sph_ctx *c = new sph_ctx();
+    c->prm = *p;
+    c->n = n;
+    c->st = *state;
+    c->ws = workspace;
+    c->ws_bytes = ws_bytes;
+    c->stream = (cudaStream_t)stream;
+    c->lpp = lpp_of(p, n);
+    c->have_forces = false;
+    c->graph = nullptr;
+    c->graph_kernels = 0;
+    c->timing = (p->flags & SPH_FLAG_TIMING) != 0;
+    for (int k = 0; k <= SPH_NSTAGES; ++k) c->ev[k] = nullptr;
+    clear_ran(c);
+    if (c->timing)
+        for (int k = 0; k <= SPH_NSTAGES; ++k)
+            if (cudaEventCreate(&c->ev[k]) != cudaSuccess) {
+                delete c;
+                return fail(SPH_ECUDA, "cudaEventCreate failed");
+            }
+    Carver cv{(char *)workspace};
+    c->diag = cv.take<ProbDiag>(1);
+    memset(&c->bv, 0, sizeof c->bv);
+    carve_tables(cv, c->bv, 1);
+    carve_arrays(cv, c->bv, n, 1, p->precision);
+    c->bv.ntot = n;
+    c->bv.key_bits = key_bits_for(1);
+    c->bv.lpp_mask = mask_of(c->lpp);
+    ProbStatic &ps = c->host_ps;
+    memset(&ps, 0, sizeof ps);
+    ps.x = state->x;
+    ps.y = state->y;
+    ps.z = state->z;
+    ps.vx = state->vx;
+    ps.vy = state->vy;
+    ps.vz = state->vz;
+    ps.u = state->u;
+    ps.m = state->m;
+    ps.h = state->h;
+    ps.rho = state->rho;
+    ps.omega = state->omega;
+    ps.P = state->P;
+    ps.c = state->c;
+    ps.ax = state->ax;
+    ps.ay = state->ay;
+    ps.az = state->az;
+    ps.du = state->du;
+    ps.vsig = state->vsig;
+    ps.n = n;
+    ps.base = 0;
+    ps.diag = c->diag;
+    ps.lpp = c->lpp;
+    ps.ph = phys_of(p);
+    ProbDiag d0;
+    memset(&d0, 0, sizeof d0);
+    d0.dt_next = 0.0;
+    long long bases[2] = {0, n};
+    cudaError_t e = cudaMemcpyAsync(c->bv.prob, &ps, sizeof ps, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->diag, &d0, sizeof d0, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(c->bv.prob_base, bases, sizeof bases, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->bv.dyn, 0, sizeof(ProbDyn), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->bv.counters, 0, 16 * sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(SPH_ECUDA, "setup copies failed: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return SPH_OK;
+}
+
+}  // extern "C"
+
+// ---- launch sequences (shared by single contexts and batches) --------------
+// Optional stage events: ev[k] is recorded before stage k, ev[k+1] after it.
+struct Marks {
+    cudaEvent_t *ev = nullptr;
+    bool *ran = nullptr;
+    void at(int k, cudaStream_t st) const
+    {
+        if (!ev) return;
+        // inside stream capture the record must become a graph node of its own
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaStreamIsCapturing(st, &cs);
+        if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(ev[k], st, cudaEventRecordExternal);
+        else cudaEventRecord(ev[k], st);
+    }
+    void done(int k) const
+    {
+        if (ran) ran[k] = true;
+    }
+};
+
+static int enqueue_density(const BatchView &b, int precision, int use_pred, cudaStream_t st, const Marks &mk)
+{
+    mk.at(SPH_STAGE_SORT, st);
+    CU(launch_domain_and_keys(b, st));
+    CU(launch_radix_sort(b, st));
+    CU(launch_gather(b, st));
+    mk.at(SPH_STAGE_TREE, st);
+    mk.done(SPH_STAGE_SORT);
+    CU(launch_build_leaves(b, precision, st));
+    mk.at(SPH_STAGE_DENSITY, st);
+    mk.done(SPH_STAGE_TREE);
+    CU(launch_density(b, precision, use_pred, st));
+    mk.at(SPH_STAGE_REFIT, st);
+    mk.done(SPH_STAGE_DENSITY);
+    CU(launch_refit(b, st));
+    mk.at(SPH_STAGE_FORCES, st);
+    mk.done(SPH_STAGE_REFIT);
+    return SPH_OK;
+}
+
+static int enqueue_step(const BatchView &b, int precision, double dt, cudaStream_t st, const Marks &mk)
+{
+    CU(launch_select_dt(b, dt, st));
+    CU(launch_reset_step(b, 1, st));
+    mk.at(SPH_STAGE_KICK_DRIFT, st);
+    CU(launch_kick_drift(b, st));
+    mk.done(SPH_STAGE_KICK_DRIFT);
+    int rc = enqueue_density(b, precision, 1, st, mk);
+    if (rc) return rc;
+    CU(launch_forces(b, precision, st));
+    mk.at(SPH_STAGE_CLOSE, st);
+    mk.done(SPH_STAGE_FORCES);
+    CU(launch_kick_close(b, 1, 1, st));
+    mk.at(SPH_NSTAGES, st);
+    mk.done(SPH_STAGE_CLOSE);
+    return SPH_OK;
+}
+
+static Marks marks_of(sph_ctx *c)
+{
+    Marks m;
+    if (c->timing) {
+        m.ev = c->ev;
+        m.ran = c->stage_ran;
+    }
+    return m;
+}
+
+
+
+static int finish_call(sph_ctx *c)
+{
+    if (c->prm.flags & SPH_FLAG_ASYNC) return SPH_OK;
+    return sph_sync(c);
+}
+
+extern "C" {
+
+int sph_sync(sph_ctx *c)
+{
+    if (!c) return fail(SPH_EINVAL, "ctx is NULL");
+    CU(cudaStreamSynchronize(c->stream));
+    unsigned st = 0;
+    CU(cudaMemcpy(&st, &c->diag->status, sizeof st, cudaMemcpyDeviceToHost));
+    return status_to_code(st);
+}
+
+int sph_density_h(sph_ctx *c)
+{
+    if (!c) return fail(SPH_EINVAL, "ctx is NULL");
+    clear_ran(c);
+    CU(launch_reset_step(c->bv, 1, c->stream));
+    int rc = enqueue_density(c->bv, c->prm.precision, 0, c->stream, marks_of(c));
+    if (rc) return rc;
+    CU(launch_kick_close(c->bv, 0, 0, c->stream));
+    c->have_forces = false;
+    return finish_call(c);
+}
+
+int sph_forces(sph_ctx *c)
+{
+    if (!c) return fail(SPH_EINVAL, "ctx is NULL");
+    clear_ran(c);
+    Marks mk = marks_of(c);
+    CU(launch_reset_step(c->bv, 2, c->stream));
+    mk.at(SPH_STAGE_FORCES, c->stream);
+    CU(launch_forces(c->bv, c->prm.precision, c->stream));
+    mk.at(SPH_STAGE_CLOSE, c->stream);
+    mk.done(SPH_STAGE_FORCES);
+    CU(launch_kick_close(c->bv, 0, 1, c->stream));
+    c->have_forces = true;
+    return finish_call(c);
+}
+
+int sph_step(sph_ctx *c, double dt, double *dt_used)
+{
+    if (!c) return fail(SPH_EINVAL, "ctx is NULL");
+    if (!(dt > 0) && !c->have_forces)
+        return fail(SPH_EINVAL, "no CFL step yet: call sph_density_h and sph_forces first, or pass dt > 0");
+    if (!std::isfinite(dt)) return fail(SPH_EINVAL, "dt must be finite");
+    clear_ran(c);
+    int rc = enqueue_step(c->bv, c->prm.precision, dt, c->stream, marks_of(c));
+    if (rc) return rc;
+    c->have_forces = true;
+    if (dt_used) {
+        CU(cudaMemcpyAsync(dt_used, &c->diag->dt_cur, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        CU(cudaStreamSynchronize(c->stream));
+    }
+    return finish_call(c);
+}
+
+static int build_graph(sph_ctx *c)
+{
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    clear_ran(c);
+    int rc = enqueue_step(c->bv, c->prm.precision, -1.0, c->stream, marks_of(c));
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(SPH_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+    int kern = 0;
+    for (size_t k = 0; k < nn; ++k) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[k], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kern;
+    }
+    c->graph_kernels = kern;
+    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->graph = nullptr;
+        return fail(SPH_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+    return SPH_OK;
+}
+
+int sph_run(sph_ctx *c, int nsteps)
+{
+    if (!c) return fail(SPH_EINVAL, "ctx is NULL");
+    if (nsteps < 0) return fail(SPH_EINVAL, "nsteps must be >= 0");
+    if (!c->have_forces) return fail(SPH_EINVAL, "no CFL step yet: call sph_density_h and sph_forces first");
+    if (nsteps == 0) return SPH_OK;
+    if (c->stream == nullptr) {
+        // the legacy default stream cannot be captured: enqueue step by step
+        for (int k = 0; k < nsteps; ++k) {
+            clear_ran(c);
+            int rc = enqueue_step(c->bv, c->prm.precision, -1.0, c->stream, marks_of(c));
+            if (rc) return rc;
+        }
+        return finish_call(c);
+    }
+    if (!c->graph) {
+        // one eager step first so that lazily set kernel attributes are in place
+        clear_ran(c);
+        int rc = enqueue_step(c->bv, c->prm.precision, -1.0, c->stream, marks_of(c));
+        if (rc) return rc;
+        --nsteps;
+        rc = build_graph(c);
+        if (rc) return rc;
+    }
+    for (int k = 0; k < nsteps; ++k) CU(cudaGraphLaunch(c->graph, c->stream));
+    return finish_call(c);
+}
+
+int sph_stage_times(sph_ctx *c, double *ms)
+{
+    if (!c || !ms) return fail(SPH_EINVAL, "NULL argument");
+    if (!c->timing) return fail(SPH_EINVAL, "context was created without SPH_FLAG_TIMING");
+    CU(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < SPH_NSTAGES; ++k) {
+        ms[k] = 0.0;
+        if (!c->stage_ran[k]) continue;
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, c->ev[k], c->ev[k + 1]) == cudaSuccess) ms[k] = t;
+        else cudaGetLastError();
+    }
+    return SPH_OK;
+}
+
+int sph_step_kernel_count(sph_ctx *c, int *kernels)
+{
+    if (!c || !kernels) return fail(SPH_EINVAL, "NULL argument");
+    if (!c->graph) {
+        if (c->stream == nullptr) return fail(SPH_EINVAL, "needs a non-default stream");
+        int rc = sph_run(c, 1);
+        if (rc) return rc;
+        if (!c->graph) {
+            rc = build_graph(c);
+            if (rc) return rc;
+        }
+    }
+    *kernels = c->graph_kernels;
+    return SPH_OK;
+}
+
+int sph_diagnostics(sph_ctx *c, sph_diag *out)
+{
+    if (!c || !out) return fail(SPH_EINVAL, "NULL argument");
+    CU(cudaStreamSynchronize(c->stream));
+    ProbDiag d;
+    CU(cudaMemcpy(&d, c->diag, sizeof d, cudaMemcpyDeviceToHost));
+    memset(out, 0, sizeof *out);
+    out->mass = d.mass;
+    for (int a = 0; a < 3; ++a) {
+        out->momentum[a] = d.mom[a];
+        out->force_sum[a] = d.fsum[a];
+    }
+    out->energy = d.energy;
+    out->dEdt = d.dEdt;
+    out->dt_next = d.dt_next;
+    out->time = d.time;
+    out->steps = d.steps;
+    out->nr_iterations = d.nr_iter;
+    out->nr_max = d.nr_max;
+    out->ngb_min = d.ngb_min == 0x7fffffff ? 0 : d.ngb_min;
+    out->ngb_max = d.ngb_max;
+    out->ngb_mean = c->n > 0 ? (double)d.ngb_sum / (double)c->n : 0.0;
+    out->density_pairs = d.density_pairs;
+    out->force_pairs = d.force_pairs;
+    out->candidates = d.candidates;
+    out->fallback = d.fallback;
+    out->leaves = d.leaves;
+    out->status = status_to_code(d.status);
+    out->unconverged = d.unconverged;
+    return SPH_OK;
+}
+
+int sph_neighbours(sph_ctx *c, int kind, const double *h_in, int64_t *offsets, int32_t *idx, int64_t cap,
+                   int64_t *total)
+{
+    if (!c || !offsets || (!idx && cap > 0) || !total) return fail(SPH_EINVAL, "NULL argument");
+    if (kind != 0 && kind != 1) return fail(SPH_EINVAL, "kind must be 0 or 1");
+    if (cap < 0) return fail(SPH_EINVAL, "cap must be >= 0");
+    const BatchView &b = c->bv;
+    cudaStream_t st = c->stream;
+    CU(launch_reset_step(b, 1, st));
+    CU(launch_domain_and_keys(b, st));
+    CU(launch_radix_sort(b, st));
+    CU(launch_gather(b, st));
+    CU(launch_build_leaves(b, c->prm.precision, st));
+    CU(launch_set_sorted_h(b, h_in, st));
+    CU(launch_refit(b, st));
+    CU(launch_neighbour_export(b, kind, h_in, (long long *)offsets, (int *)idx, (long long)cap, b.scratch64, st));
+    CU(cudaStreamSynchronize(st));
+    long long tot = 0;
+    CU(cudaMemcpy(&tot, b.scratch64, sizeof tot, cudaMemcpyDeviceToHost));
+    *total = tot;
+    unsigned s = 0;
+    CU(cudaMemcpy(&s, &c->diag->status, sizeof s, cudaMemcpyDeviceToHost));
+    if (s & ST_OVERFLOW) return fail(SPH_ENOSPACE, "a particle has more than 1024 neighbours");
+    if (tot > cap) return fail(SPH_ENOSPACE, "%lld neighbour entries, capacity %lld", tot, (long long)cap);
+    return SPH_OK;
+}
+
+int sph_destroy(sph_ctx *c)
+{
+    if (!c) return SPH_OK;
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (int k = 0; k <= SPH_NSTAGES; ++k)
+        if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+    delete c;
+    return SPH_OK;
+}
+
+// ---- batching ---------------------------------------------------------------
+static int batch_check(sph_ctx *const *ctxs, int nctx)
+{
+    if (!ctxs || nctx <= 0) return fail(SPH_EINVAL, "empty batch");
+    for (int k = 0; k < nctx; ++k) {
+        if (!ctxs[k]) return fail(SPH_EINVAL, "batch context %d is NULL", k);
+        if (ctxs[k]->prm.precision != ctxs[0]->prm.precision)
+            return fail(SPH_EINVAL, "all batch contexts must share the precision");
+        if (ctxs[k]->stream != ctxs[0]->stream) return fail(SPH_EINVAL, "all batch contexts must share the stream");
+    }
+    return SPH_OK;
+}
+
+size_t sph_batch_workspace_bytes(sph_ctx *const *ctxs, int nctx)
+{
+    if (batch_check(ctxs, nctx) != SPH_OK) return 0;
+    long long ntot = 0;
+    for (int k = 0; k < nctx; ++k) ntot += ctxs[k]->n;
+    Carver c{nullptr};
+    BatchView b;
+    memset(&b, 0, sizeof b);
+    carve_tables(c, b, nctx);
+    carve_arrays(c, b, ntot, nctx, ctxs[0]->prm.precision);
+    return c.off + 256;
+}
+
+int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, size_t ws_bytes)
+{
+    int rc = batch_check(ctxs, nctx);
+    if (rc) return rc;
+    if (nsteps < 0) return fail(SPH_EINVAL, "nsteps must be >= 0");
+    for (int k = 0; k < nctx; ++k)
+        if (!ctxs[k]->have_forces)
+            return fail(SPH_EINVAL, "batch context %d has no force evaluation yet", k);
+    size_t need = sph_batch_workspace_bytes(ctxs, nctx);
+    if (!workspace || ws_bytes < need) return fail(SPH_ENOSPACE, "batch workspace of %zu bytes needed", need);
+    if (((uintptr_t)workspace) & 255) return fail(SPH_EINVAL, "workspace must be 256-byte aligned");
+    const int prec = ctxs[0]->prm.precision;
+    cudaStream_t st = ctxs[0]->stream;
+    long long ntot = 0;
+    std::vector<ProbStatic> tab(nctx);
+    std::vector<long long> bases(nctx + 1);
+    int mask = 0;
+    for (int k = 0; k < nctx; ++k) {
+        tab[k] = ctxs[k]->host_ps;
+        tab[k].base = ntot;
+        bases[k] = ntot;
+        ntot += ctxs[k]->n;
+        mask |= mask_of(tab[k].lpp);
+    }
+    bases[nctx] = ntot;
+    Carver cv{(char *)workspace};
+    BatchView b;
+    memset(&b, 0, sizeof b);
+    carve_tables(cv, b, nctx);
+    carve_arrays(cv, b, ntot, nctx, prec);
+    b.ntot = ntot;
+    b.key_bits = key_bits_for(nctx);
+    b.lpp_mask = mask;
+    CU(cudaMemcpyAsync(b.prob, tab.data(), sizeof(ProbStatic) * nctx, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync(b.prob_base, bases.data(), sizeof(long long) * (nctx + 1), cudaMemcpyHostToDevice, st));
+    CU(cudaMemsetAsync(b.dyn, 0, sizeof(ProbDyn) * nctx, st));
+    CU(cudaMemsetAsync(b.counters, 0, 16 * sizeof(int), st));
+    for (int s = 0; s < nsteps; ++s) {
+        rc = enqueue_step(b, prec, -1.0, st, Marks());
+        if (rc) return rc;
+    }
+    CU(cudaStreamSynchronize(st));
+    int worst = SPH_OK;
+    for (int k = 0; k < nctx; ++k) {
+        unsigned s = 0;
+        CU(cudaMemcpy(&s, &ctxs[k]->diag->status, sizeof s, cudaMemcpyDeviceToHost));
+        int code = status_to_code(s);
+        if (code != SPH_OK && worst == SPH_OK) worst = code;
+    }
+    return worst;
+}
+
+}  // extern "C"

@@ -1,0 +1,192 @@
+// Global-step leapfrog kick-drift-kick (Eqs. LFKDK1/LFKDK2), the CFL step
+// (Eq. SPH_DT) and the FP64 conservation reductions, all in FP64 and in the
+// caller's particle order.
+//
+// Reading of the paper for velocity-dependent forces: the first half kick and
+// the drift use the stored a^n, du^n; the density solve and the forces are
+// evaluated at the new positions with the predicted v^ = v^(n+1/2) + a^n dt/2
+// and u^ = u^(n+1/2) + du^n dt/2; the closing half kick uses a^(n+1).
+#include "sph_internal.cuh"
+
+namespace sph {
+
+namespace {
+
+constexpr int kRedThreads = 256;
+
+__global__ void k_reset_step(BatchView b, int mode)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= b.nprob) return;
+    ProbDiag *d = b.prob[p].diag;
+    d->dt_min_bits = 0x7ff0000000000000ull;  // +inf
+    d->force_pairs = 0;
+    if (mode == 2) return;
+    d->mass = 0;
+    for (int a = 0; a < 3; ++a) {
+        d->mom[a] = 0;
+        d->fsum[a] = 0;
+    }
+    d->energy = 0;
+    d->dEdt = 0;
+    d->dt_min_bits = 0x7ff0000000000000ull;  // +inf
+    d->nr_iter = d->density_pairs = d->force_pairs = d->candidates = d->fallback = 0;
+    d->ngb_sum = 0;
+    d->nr_max = 0;
+    d->ngb_min = 0x7fffffff;
+    d->ngb_max = 0;
+    d->status = 0;
+    d->unconverged = 0;
+}
+
+__global__ void k_select_dt(BatchView b, double dt_host)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= b.nprob) return;
+    ProbDiag *d = b.prob[p].diag;
+    d->dt_cur = dt_host > 0.0 ? dt_host : d->dt_next;
+}
+
+__global__ void k_kick_drift(BatchView b)
+{
+    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= b.ntot) return;
+    int p = find_problem(b.prob_base, b.nprob, g);
+    const ProbStatic &ps = b.prob[p];
+    const PhysParams &ph = ps.ph;
+    long long i = g - ps.base;
+    const double dt = ps.diag->dt_cur, hdt = 0.5 * dt;
+    double a[3] = {ps.ax[i], ps.ay[i], ps.az[i]};
+    double *X[3] = {ps.x, ps.y, ps.z};
+    double *Vv[3] = {ps.vx, ps.vy, ps.vz};
+    double *VP[3] = {b.vpx, b.vpy, b.vpz};
+    for (int k = 0; k < 3; ++k) {
+        double vh = Vv[k][i] + hdt * a[k];
+        Vv[k][i] = vh;
+        double x = X[k][i] + vh * dt;
+        if (ph.periodic) {
+            double lo = ph.box_lo[k], L = ph.box_len[k];
+            if (x >= lo + L) x -= L;
+            else if (x < lo) x += L;
+        }
+        X[k][i] = x;
+        VP[k][g] = vh + hdt * a[k];
+    }
+    double u = ps.u[i];
+    if (ph.eos == SPH_EOS_ADIABATIC) {
+        double uh = u + hdt * ps.du[i];
+        ps.u[i] = uh;
+        b.up[g] = uh + hdt * ps.du[i];
+    } else {
+        b.up[g] = u;
+    }
+}
+
+// Closing half kick (optional) and the FP64 reductions per problem.
+__global__ void k_kick_close(BatchView b, int do_kick)
+{
+    __shared__ double red[9][kRedThreads / 32];
+    __shared__ int p0s;
+    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int p = -1;
+    double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (g < b.ntot) {
+        p = find_problem(b.prob_base, b.nprob, g);
+        const ProbStatic &ps = b.prob[p];
+        const PhysParams &ph = ps.ph;
+        long long i = g - ps.base;
+        const double hdt = 0.5 * ps.diag->dt_cur;
+        double a[3] = {ps.ax[i], ps.ay[i], ps.az[i]};
+        double vel[3] = {ps.vx[i], ps.vy[i], ps.vz[i]};
+        double u = ps.u[i], du = ps.du[i];
+        const bool adi = ph.eos == SPH_EOS_ADIABATIC;
+        if (do_kick) {
+            for (int k = 0; k < 3; ++k) vel[k] += hdt * a[k];
+            ps.vx[i] = vel[0];
+            ps.vy[i] = vel[1];
+            ps.vz[i] = vel[2];
+            if (adi) {
+                u += hdt * du;
+                ps.u[i] = u;
+            }
+        }
+        double m = ps.m[i];
+        v[0] = m;
+        v[1] = m * vel[0];
+        v[2] = m * vel[1];
+        v[3] = m * vel[2];
+        v[4] = m * (0.5 * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]) + (adi ? u : 0.0));
+        v[5] = m * a[0];
+        v[6] = m * a[1];
+        v[7] = m * a[2];
+        v[8] = m * (vel[0] * a[0] + vel[1] * a[1] + vel[2] * a[2] + (adi ? du : 0.0));
+    }
+    if (threadIdx.x == 0) p0s = p;
+    __syncthreads();
+    const int p0 = p0s;
+    const bool uni = __syncthreads_and(p == p0 || p == -1);
+    if (uni) {
+        if (p0 < 0) return;
+        for (int k = 0; k < 9; ++k) {
+            double x = warp_sum(v[k]);
+            if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = x;
+        }
+        __syncthreads();
+        if (threadIdx.x < 9) {
+            double t = 0;
+            for (int w = 0; w < kRedThreads / 32; ++w) t += red[threadIdx.x][w];
+            ProbDiag *d = b.prob[p0].diag;
+            double *dst[9] = {&d->mass, &d->mom[0], &d->mom[1], &d->mom[2], &d->energy,
+                              &d->fsum[0], &d->fsum[1], &d->fsum[2], &d->dEdt};
+            atomicAdd(dst[threadIdx.x], t);
+        }
+    } else if (p >= 0) {
+        ProbDiag *d = b.prob[p].diag;
+        double *dst[9] = {&d->mass, &d->mom[0], &d->mom[1], &d->mom[2], &d->energy,
+                          &d->fsum[0], &d->fsum[1], &d->fsum[2], &d->dEdt};
+        for (int k = 0; k < 9; ++k) atomicAdd(dst[k], v[k]);
+    }
+}
+
+__global__ void k_finish(BatchView b, int advanced, int forces_ran)
+{
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= b.nprob) return;
+    ProbDiag *d = b.prob[p].diag;
+    if (forces_ran) d->dt_next = __longlong_as_double((long long)d->dt_min_bits);
+    if (advanced) {
+        d->time += d->dt_cur;
+        d->steps += 1;
+    }
+    d->leaves = b.dyn[p].nleaf;
+}
+
+}  // namespace
+
+cudaError_t launch_reset_step(const BatchView &b, int mode, cudaStream_t st)
+{
+    k_reset_step<<<(b.nprob + 127) / 128, 128, 0, st>>>(b, mode);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select_dt(const BatchView &b, double dt_host, cudaStream_t st)
+{
+    k_select_dt<<<(b.nprob + 127) / 128, 128, 0, st>>>(b, dt_host);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kick_drift(const BatchView &b, cudaStream_t st)
+{
+    if (b.ntot == 0) return cudaSuccess;
+    k_kick_drift<<<(unsigned)((b.ntot + 255) / 256), 256, 0, st>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kick_close(const BatchView &b, int do_kick, int forces_ran, cudaStream_t st)
+{
+    if (b.ntot > 0) k_kick_close<<<(unsigned)((b.ntot + kRedThreads - 1) / kRedThreads), kRedThreads, 0, st>>>(b, do_kick);
+    k_finish<<<(b.nprob + 127) / 128, 128, 0, st>>>(b, do_kick, forces_ran);
+    return cudaGetLastError();
+}
+
+}  // namespace sph

@@ -1,0 +1,240 @@
+// Internal declarations of the GB300 SPH library: device-side problem
+// descriptors, workspace views and small device helpers shared by the kernels.
+// Nothing here is part of the public ABI (include/sph.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sph.h"
+
+namespace sph {
+
+constexpr int kMaxLevels = 6;       // tree levels above the leaves (32^6 leaves)
+constexpr int kBranch = 32;         // children per tree node (one per warp lane)
+constexpr int kMortonBits = 10;     // bits per axis of the Morton key
+constexpr int kMortonTotal = 3 * kMortonBits;
+constexpr double kPi = 3.14159265358979323846;
+
+// Status bits kept on the device per problem (mapped to SPH_E* on the host).
+enum : unsigned {
+    ST_NOCONV = 1u,
+    ST_BOX = 2u,
+    ST_NONFINITE = 4u,
+    ST_TIMEOUT = 8u,
+    ST_OVERFLOW = 16u,  // internal capacity exceeded (e.g. neighbour export)
+};
+
+// Physics parameters of one problem as the kernels read them.
+struct PhysParams {
+    int periodic;
+    int eos;
+    double box_lo[3];
+    double box_len[3];
+    double gamma, cs_iso, eta;
+    double alpha_av, beta_av, alpha_ac, c_cfl;
+    double h_tol;
+    int h_max_iter;
+    int pad_;
+};
+
+// Per-problem diagnostics and persistent scalars; lives in the context's own
+// workspace so that it survives between single and batched calls.
+struct ProbDiag {
+    double dt_next;      // CFL step from the last force evaluation
+    double dt_cur;       // step in use by the current sph_step
+    double time;
+    double mass, mom[3], energy, fsum[3], dEdt;
+    unsigned long long dt_min_bits;  // atomicMin target (positive doubles order as integers)
+    long long steps;
+    long long nr_iter;
+    long long density_pairs, force_pairs, candidates, fallback, leaves;
+    long long ngb_sum;
+    int nr_max, ngb_min, ngb_max;
+    unsigned status;
+    int unconverged;
+    int pad_;
+};
+
+// Host-written description of one problem inside a batch.
+struct ProbStatic {
+    // caller state arrays (original particle order)
+    double *x, *y, *z, *vx, *vy, *vz, *u, *m, *h;
+    double *rho, *omega, *P, *c, *ax, *ay, *az, *du, *vsig;
+    long long n;
+    long long base;  // offset of this problem in the batch-global particle index space
+    ProbDiag *diag;
+    int lpp;         // lanes per particle in the pair kernels (leaf size = 32 / lpp)
+    int pad_;
+    PhysParams ph;
+};
+
+// Device-written per-step description (domain normalisation, leaves, tree).
+struct ProbDyn {
+    double dom_lo[3];
+    double dom_inv;      // 1 / (largest extent of the key domain)
+    unsigned long long bbox_bits[6];  // ordered-int min x,y,z and max x,y,z (isolated)
+    int leaf_base, nleaf;
+    int top_level;       // highest tree level (0 = the leaves themselves)
+    int node_off[kMaxLevels + 1];  // global index of this problem's first node per level
+    int node_cnt[kMaxLevels + 1];  // nodes per level (level 0 = leaves)
+};
+
+// 32-byte vector of four doubles (FP64 staging)
+struct __align__(32) dbl4 {
+    double x, y, z, w;
+};
+
+template <typename T>
+struct Vec4;
+template <>
+struct Vec4<float> {
+    using type = float4;
+};
+template <>
+struct Vec4<double> {
+    using type = dbl4;
+};
+
+// Box of a leaf or tree node: positions and smoothing spheres (pos +- 2h),
+// rounded outwards to float.
+struct __align__(16) NodeBox {
+    float4 plo;  // xyz = min position, w = h_max
+    float4 phi;  // xyz = max position, w = particle count (as float)
+    float4 slo;  // xyz = min (x - 2h)
+    float4 shi;  // xyz = max (x + 2h)
+};
+
+// Batch-global scratch arrays (all carved from one workspace).
+struct BatchView {
+    int nprob;
+    int lpp_mask;                // bit k set: some problem uses 2^k lanes per particle
+    long long ntot;              // particles over all problems
+    int max_leaves;              // capacity of the leaf arrays
+    int key_bits;                // bits the radix sort must order
+    ProbStatic *prob;            // [nprob]
+    ProbDyn *dyn;                // [nprob]
+    long long *prob_base;        // [nprob + 1] base offsets (for searches)
+    // sort
+    unsigned long long *keys[2];
+    unsigned *vals[2];
+    unsigned *hist;              // 256 * sort blocks
+    unsigned *scan_aux;
+    int *perm;                   // sorted position -> batch-global original index
+    // sorted FP64 copies
+    double *sx, *sy, *sz, *sh, *sm;
+    double *srho, *somega, *sP, *sc;
+    // predicted velocity / internal energy (original order, batch-global)
+    double *vpx, *vpy, *vpz, *up;
+    // staging for the pair kernels (sorted order); element type float4 or double4
+    void *pm;   // (offset xyz, m)
+    void *ph;   // (offset xyz, h)
+    void *vc;   // (v xyz, c)
+    void *th;   // (P/(Omega rho^2), rho, m, u)
+    // leaves
+    unsigned *flag;              // [ntot] leaf start flags, then leaf index (scan)
+    int *leaf_start;             // [max_leaves + 1]
+    int *leaf_pid;               // [max_leaves]
+    double *leaf_c;              // [3 * max_leaves] leaf centres (FP64), SoA
+    NodeBox *nodes[kMaxLevels + 1];  // level 0 = leaves
+    int node_cap[kMaxLevels + 1];
+    int *fallback_list;          // [ntot] sorted indices needing the slow path
+    int *counters;               // [16] work counters / list lengths
+    long long *scratch64;        // [8]
+};
+
+// ---------------------------------------------------------------------------
+// small device helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double min_image(double d, double L, int periodic)
+{
+    if (periodic) {
+        if (d > 0.5 * L) d -= L;
+        else if (d < -0.5 * L) d += L;
+    }
+    return d;
+}
+
+__device__ __forceinline__ unsigned long long ordered_bits(double v)
+{
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+
+__device__ __forceinline__ double from_ordered_bits(unsigned long long b)
+{
+    b = (b & 0x8000000000000000ull) ? (b & 0x7fffffffffffffffull) : ~b;
+    return __longlong_as_double((long long)b);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_min(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        T w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        T w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+// index of the problem owning batch-global index g (prob_base ascending)
+__device__ __forceinline__ int find_problem(const long long *base, int nprob, long long g)
+{
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (base[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// host-side launch helpers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+struct DevInfo {
+    int sm_count;
+};
+DevInfo dev_info();
+
+// sort / build / pair / integrate stages, each enqueued on `st`
+cudaError_t launch_domain_and_keys(const BatchView &b, cudaStream_t st);
+cudaError_t launch_radix_sort(const BatchView &b, cudaStream_t st);
+cudaError_t launch_gather(const BatchView &b, cudaStream_t st);
+cudaError_t launch_set_sorted_h(const BatchView &b, const double *h_in, cudaStream_t st);
+cudaError_t launch_build_leaves(const BatchView &b, int precision, cudaStream_t st);
+cudaError_t launch_refit(const BatchView &b, cudaStream_t st);
+cudaError_t launch_density(const BatchView &b, int precision, int use_pred, cudaStream_t st);
+cudaError_t launch_forces(const BatchView &b, int precision, cudaStream_t st);
+cudaError_t launch_select_dt(const BatchView &b, double dt_host, cudaStream_t st);
+cudaError_t launch_kick_drift(const BatchView &b, cudaStream_t st);
+cudaError_t launch_kick_close(const BatchView &b, int do_kick, int forces_ran, cudaStream_t st);
+cudaError_t launch_reset_step(const BatchView &b, int mode, cudaStream_t st);  // mode 1 full, 2 forces only
+cudaError_t launch_neighbour_export(const BatchView &b, int kind, const double *h_in, long long *offsets,
+                                    int *idx, long long cap, long long *total_dev, cudaStream_t st);
+
+// upper bounds used to size grids and workspaces
+long long leaves_upper_bound(long long n);
+int levels_needed(long long max_leaves);
+
+}  // namespace sph

@@ -1,0 +1,864 @@
+// Pair kernels of the grad-h SPH neighbour loop.
+//
+// Work unit: one warp per leaf cell (the paper's OpenMP unit of work is an
+// active leaf cell, Sec. 3.2.1, and neighbours are gathered per leaf, not per
+// particle, Sec. 2.6).  LPP lanes serve each particle of the leaf; the warp
+// walks the tree over the leaves once per leaf, stages candidate particles in
+// shared memory (positions relative to the query leaf: leaf reference points
+// differenced in FP64, then cast), and each lane keeps its own list of
+// in-range candidates so that the arithmetic runs without divergence.
+//
+//  k_density   Eqs. SPHRHO, HRHO, OMEGA: Newton-Raphson on
+//              F(h) = rho(h) - m (eta/h)^3 over the cached list of (r, m_j)
+//              with the same bracketing fallback as the oracle; the list is
+//              rebuilt if h outgrows it.  Particles whose list overflows, or
+//              that need too many rebuilds, go to k_density_fallback, which
+//              re-walks the tree in every iteration.
+//  k_forces    Eqs. GRADHMOMEQN, GRADHENEQN, MON97ARTVISC, MON97ENERGYDISS
+//              and the signal speed of Eq. SPH_DT.  Every pair term is formed
+//              from the pair vector in a canonical orientation (lower sorted
+//              index first) with order-independent FP32 operations, so that
+//              F_ij = -F_ji bit for bit; m_i a_i is accumulated with
+//              error-free (TwoSum) compensated FP32 sums combined in FP64,
+//              which keeps sum_i m_i a_i near FP64 round-off.
+#include "sph_internal.cuh"
+
+namespace sph {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+__host__ __device__ constexpr int lpp_log2(int l) { return l == 1 ? 0 : l == 2 ? 1 : l == 4 ? 2 : 3; }
+constexpr double kListMargin = 1.03;  // list radius = 2 h * margin
+constexpr int kMaxRebuild = 6;
+
+template <typename T>
+__device__ __forceinline__ T tinf();
+template <>
+__device__ __forceinline__ float tinf<float>() { return INFINITY; }
+template <>
+__device__ __forceinline__ double tinf<double>() { return INFINITY; }
+
+// M4 cubic spline: f(q) and f'(q), support q < 2 (W = f / (pi h^3)).
+template <typename T>
+__device__ __forceinline__ void m4(T q, T &f, T &df)
+{
+    T t = q < T(2) ? T(2) - q : T(0);
+    T t2 = t * t;
+    T f2 = T(0.25) * t2 * t, df2 = T(-0.75) * t2;
+    T q2 = q * q;
+    T f1 = T(1) + q2 * (T(0.75) * q - T(1.5));
+    T df1 = q * (T(2.25) * q - T(3));
+    bool in = q < T(1);
+    f = in ? f1 : f2;
+    df = in ? df1 : df2;
+}
+
+template <typename T>
+__device__ __forceinline__ T m4_df(T q)
+{
+    T t = q < T(2) ? T(2) - q : T(0);
+    T df2 = T(-0.75) * t * t;
+    T df1 = q * (T(2.25) * q - T(3));
+    return q < T(1) ? df1 : df2;
+}
+
+template <typename T>
+__device__ __forceinline__ T rsqrt_t(T x);
+template <>
+__device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+template <>
+__device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
+
+template <typename T>
+__device__ __forceinline__ T mul_rn(T a, T b);
+template <>
+__device__ __forceinline__ float mul_rn<float>(float a, float b) { return __fmul_rn(a, b); }
+template <>
+__device__ __forceinline__ double mul_rn<double>(double a, double b) { return __dmul_rn(a, b); }
+template <typename T>
+__device__ __forceinline__ T add_rn(T a, T b);
+template <>
+__device__ __forceinline__ float add_rn<float>(float a, float b) { return __fadd_rn(a, b); }
+template <>
+__device__ __forceinline__ double add_rn<double>(double a, double b) { return __dadd_rn(a, b); }
+
+// sorted particle index carried in the w slot of a staged vector: bit
+// pattern in FP32 staging (only ever copied), exact value in FP64 staging
+__device__ __forceinline__ float bits_as_t(int v, float) { return __int_as_float(v); }
+__device__ __forceinline__ double bits_as_t(int v, double) { return (double)v; }
+__device__ __forceinline__ int t_as_bits(float v) { return __float_as_int(v); }
+__device__ __forceinline__ int t_as_bits(double v) { return (int)v; }
+
+// Separating-axis test of two boxes grown by R, periodic aware, conservative
+// for the FP32 rounding of the box coordinates.
+__device__ __forceinline__ bool axis_overlap(float alo, float ahi, float blo, float bhi, float R,
+                                             int periodic, float L)
+{
+    float ca = 0.5f * (alo + ahi), ha = 0.5f * (ahi - alo);
+    float cb = 0.5f * (blo + bhi), hb = 0.5f * (bhi - blo);
+    float reach = ha + hb + R;
+    reach += 2e-6f * (fabsf(ca) + fabsf(cb) + reach) + 1e-30f;
+    float d = fabsf(ca - cb);
+    if (periodic) {
+        if (reach >= 0.5f * L) return true;
+        if (d > L) d -= L;
+        d = fminf(d, L - d);
+    }
+    return d <= reach;
+}
+
+__device__ __forceinline__ bool box_overlap(const float4 &alo, const float4 &ahi, const float4 &blo,
+                                            const float4 &bhi, float R, const PhysParams &ph)
+{
+    return axis_overlap(alo.x, ahi.x, blo.x, bhi.x, R, ph.periodic, (float)ph.box_len[0]) &&
+           axis_overlap(alo.y, ahi.y, blo.y, bhi.y, R, ph.periodic, (float)ph.box_len[1]) &&
+           axis_overlap(alo.z, ahi.z, blo.z, bhi.z, R, ph.periodic, (float)ph.box_len[2]);
+}
+
+// Warp-cooperative depth-first walk of one problem's tree: visit(leaf) is
+// called (warp-uniformly) for every leaf whose box passes test(box).
+template <class Test, class Visit>
+__device__ __forceinline__ void walk(const BatchView &b, const ProbDyn &d, Test &&test, Visit &&visit)
+{
+    const int lane = threadIdx.x & 31;
+    const int top = d.top_level;
+    unsigned mask[kMaxLevels + 1];
+    int base[kMaxLevels + 1];
+    int lvl = top;
+    base[top] = 0;
+    {
+        bool ok = lane < d.node_cnt[top] && test(b.nodes[top][d.node_off[top] + lane]);
+        mask[top] = __ballot_sync(FULL, ok);
+    }
+    for (;;) {
+        unsigned m = mask[lvl];
+        if (m == 0u) {
+            if (++lvl > top) break;
+            continue;
+        }
+        int c = __ffs(m) - 1;
+        mask[lvl] = m & (m - 1u);
+        int node = base[lvl] + c;
+        if (lvl == 0) {
+            visit(d.node_off[0] + node);
+            continue;
+        }
+        int ch = node * kBranch + lane;
+        bool ok = ch < d.node_cnt[lvl - 1] && test(b.nodes[lvl - 1][d.node_off[lvl - 1] + ch]);
+        --lvl;
+        base[lvl] = node * kBranch;
+        mask[lvl] = __ballot_sync(FULL, ok);
+    }
+}
+
+// FP64 difference of two leaf reference points, minimum image, cast to T;
+// computed by lanes 0..2 (one axis each) and broadcast.
+template <typename T>
+__device__ __forceinline__ void leaf_shift(const BatchView &b, int A, int B, const PhysParams &ph, T &dx,
+                                           T &dy, T &dz)
+{
+    const int lane = threadIdx.x & 31;
+    T v = T(0);
+    if (lane < 3) {
+        double d = b.leaf_c[3LL * B + lane] - b.leaf_c[3LL * A + lane];
+        v = (T)min_image(d, ph.box_len[lane], ph.periodic);
+    }
+    dx = __shfl_sync(FULL, v, 0);
+    dy = __shfl_sync(FULL, v, 1);
+    dz = __shfl_sync(FULL, v, 2);
+}
+
+// sum over the LPP lanes that serve one particle
+template <int LPP, typename T>
+__device__ __forceinline__ T group_sum(T v)
+{
+#pragma unroll
+    for (int o = 1; o < LPP; o <<= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+template <int LPP, typename T>
+__device__ __forceinline__ T group_max(T v)
+{
+#pragma unroll
+    for (int o = 1; o < LPP; o <<= 1) {
+        T w = __shfl_xor_sync(FULL, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+template <int LPP>
+__device__ __forceinline__ bool group_any(bool v)
+{
+    int x = v ? 1 : 0;
+#pragma unroll
+    for (int o = 1; o < LPP; o <<= 1) x |= __shfl_xor_sync(FULL, x, o);
+    return x != 0;
+}
+
+// One Newton-Raphson update of the h-rho solve with the oracle's bracketing
+// (Eqs. SPHRHO, HRHO).  Returns true when |h_new - h| < tol h.
+template <typename T>
+__device__ __forceinline__ bool nr_update(T &h, T &lo, T &hi, T rho, T drho, T m, T eta3, T tol)
+{
+    T hinv = T(1) / h;
+    T hinv3 = hinv * hinv * hinv;
+    T F = rho - m * eta3 * hinv3;
+    T dF = drho + T(3) * m * eta3 * hinv3 * hinv;
+    if (F < T(0)) lo = h;
+    else hi = h;
+    T hn = dF > T(0) ? h - F / dF : T(-1);
+    bool bad = !(hn >= lo) || !(hn <= hi) || !(hn >= T(0.5) * h) || !(hn <= T(2) * h) || !(dF > T(0));
+    if (bad) hn = (hi == tinf<T>()) ? T(2) * h : T(0.5) * (lo + hi);
+    bool conv = fabs(hn - h) < tol * h;
+    h = hn;
+    return conv;
+}
+
+template <typename T, int LPP>
+struct DCfg {
+    using V = typename Vec4<T>::type;
+    static constexpr int LCAP = 96 / LPP + 8;
+    static constexpr int CH = 64;
+    static constexpr int WPB = LPP == 1 ? 2 : 4;
+    static constexpr size_t per_warp = CH * sizeof(V) + (size_t)LCAP * 32 * 2 * sizeof(T);
+    static constexpr size_t smem = WPB * per_warp;
+};
+
+// Outputs of the density solve for sorted particle s (one lane per particle).
+template <typename T>
+__device__ __forceinline__ void density_epilogue(const BatchView &b, const ProbStatic &ps, long long s,
+                                                 typename Vec4<T>::type pi, T h, T S0, T S1, int use_pred)
+{
+    using V = typename Vec4<T>::type;
+    const PhysParams &ph = ps.ph;
+    T hinv = T(1) / h;
+    T hinv3 = hinv * hinv * hinv;
+    T rho = T(1.0 / kPi) * S0 * hinv3;
+    T drho = -T(1.0 / kPi) * hinv3 * hinv * (T(3) * S0 + S1);
+    T omega = T(1) + h / (T(3) * rho) * drho;
+    long long g = b.perm[s];
+    long long i = g - ps.base;
+    double u = use_pred ? b.up[g] : ps.u[i];
+    double v[3] = {use_pred ? b.vpx[g] : ps.vx[i], use_pred ? b.vpy[g] : ps.vy[i],
+                   use_pred ? b.vpz[g] : ps.vz[i]};
+    T P, c;
+    if (ph.eos == SPH_EOS_ISOTHERMAL) {
+        c = (T)ph.cs_iso;
+        P = c * c * rho;
+    } else {
+        P = (T)(ph.gamma - 1.0) * rho * (T)u;
+        c = sqrt((T)ph.gamma * P / rho);
+    }
+    T A = P / (omega * rho * rho);
+    b.sh[s] = (double)h;
+    b.srho[s] = (double)rho;
+    b.somega[s] = (double)omega;
+    b.sP[s] = (double)P;
+    b.sc[s] = (double)c;
+    ps.h[i] = (double)h;
+    ps.rho[i] = (double)rho;
+    ps.omega[i] = (double)omega;
+    ps.P[i] = (double)P;
+    ps.c[i] = (double)c;
+    V q;
+    q.x = pi.x;
+    q.y = pi.y;
+    q.z = pi.z;
+    q.w = hinv;
+    ((V *)b.ph)[s] = q;
+    q.x = (T)v[0];
+    q.y = (T)v[1];
+    q.z = (T)v[2];
+    q.w = c;
+    ((V *)b.vc)[s] = q;
+    q.x = A;
+    q.y = rho;
+    q.z = pi.w;
+    q.w = (T)u;
+    ((V *)b.th)[s] = q;
+    if (!(isfinite((double)rho) && isfinite((double)omega) && isfinite((double)P)))
+        atomicOr(&ps.diag->status, ST_NONFINITE);
+}
+
+template <typename T, int LPP>
+__global__ void __launch_bounds__(DCfg<T, LPP>::WPB * 32) k_density(BatchView b, int use_pred)
+{
+    using C = DCfg<T, LPP>;
+    using V = typename C::V;
+    extern __shared__ __align__(32) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    unsigned char *mine = smem + wib * C::per_warp;
+    V *cand = reinterpret_cast<V *>(mine);
+    T *lr = reinterpret_cast<T *>(mine + C::CH * sizeof(V));
+    T *lm = lr + C::LCAP * 32;
+    const int pp = lane / LPP, sub = lane % LPP;
+    const int nleaf = b.counters[0];
+    const V *pm = (const V *)b.pm;
+
+    for (;;) {
+        int leaf = 0;
+        if (lane == 0) leaf = atomicAdd(&b.counters[11 + lpp_log2(LPP)], 1);
+        leaf = __shfl_sync(FULL, leaf, 0);
+        if (leaf >= nleaf) break;
+        const int p = b.leaf_pid[leaf];
+        const ProbStatic &ps = b.prob[p];
+        if (ps.lpp != LPP) continue;  // leaf of a problem served by another launch
+        const int st = b.leaf_start[leaf], nA = b.leaf_start[leaf + 1] - st;
+        const ProbDyn &dy = b.dyn[p];
+        const PhysParams &ph = ps.ph;
+        const NodeBox boxA = b.nodes[0][leaf];
+        const bool active = pp < nA;
+        const long long s = st + (active ? pp : 0);
+        const V pi = pm[s];
+        const T mi = pi.w;
+        const T eta3 = (T)(ph.eta * ph.eta * ph.eta);
+        const T tol = (T)ph.h_tol;
+        const int maxit = ph.h_max_iter;
+        double Lmin = ph.periodic ? fmin(ph.box_len[0], fmin(ph.box_len[1], ph.box_len[2])) : INFINITY;
+        T h = active ? (T)b.sh[s] : T(1);
+        if (active && !(h > T(0))) {
+            double ext = 1.0 / dy.dom_inv;
+            h = (T)(ph.eta * cbrt(ext * ext * ext / (double)(ps.n > 0 ? ps.n : 1)));
+        }
+        T lo = T(0), hi = tinf<T>();
+        int it = 0;
+        bool conv = !active, fail = false, need = false, noconv = false;
+        int cnt = 0;
+        long long pairs = 0, tested = 0;
+        for (int attempt = 0;; ++attempt) {
+            const T hs = h * (T)kListMargin;
+            float Rq = warp_max((active && !fail) ? __fmul_ru(2.0f, (float)hs) : 0.f) * 1.0001f;
+            const T R2 = (T(2) * hs) * (T(2) * hs);
+            cnt = 0;
+            bool ovf = false;
+            int nbuf = 0;
+            auto flush = [&]() {
+                for (int k = sub; k < nbuf; k += LPP) {
+                    V c = cand[k];
+                    T dx = pi.x - c.x, dyy = pi.y - c.y, dz = pi.z - c.z;
+                    T r2 = dx * dx + dyy * dyy + dz * dz;
+                    if (active && !fail && r2 < R2) {
+                        if (cnt < C::LCAP) {
+                            lr[cnt * 32 + lane] = sqrt(r2);
+                            lm[cnt * 32 + lane] = c.w;
+                            ++cnt;
+                        } else {
+                            ovf = true;
+                        }
+                    }
+                }
+                tested += (nbuf - sub + LPP - 1) / LPP;
+                __syncwarp();
+                nbuf = 0;
+            };
+            walk(
+                b, dy, [&](const NodeBox &nb) { return box_overlap(boxA.plo, boxA.phi, nb.plo, nb.phi, Rq, ph); },
+                [&](int B) {
+                    const int stB = b.leaf_start[B], nB = b.leaf_start[B + 1] - stB;
+                    if (nbuf + nB > C::CH) flush();
+                    T Dx, Dy, Dz;
+                    leaf_shift<T>(b, leaf, B, ph, Dx, Dy, Dz);
+                    if (lane < nB) {
+                        V q = pm[stB + lane];
+                        q.x += Dx;
+                        q.y += Dy;
+                        q.z += Dz;
+                        cand[nbuf + lane] = q;
+                    }
+                    __syncwarp();
+                    nbuf += nB;
+                });
+            flush();
+            if (group_any<LPP>(ovf) && active && !fail) fail = true;
+            // Newton-Raphson on the cached lists
+            for (;;) {
+                bool go = active && !conv && !fail && !need;
+                if (!__any_sync(FULL, go)) break;
+                T S0 = T(0), S1 = T(0);
+                int nn = 0;
+                if (go) {
+                    const T hinv = T(1) / h;
+                    for (int e = 0; e < cnt; ++e) {
+                        T q = lr[e * 32 + lane] * hinv;
+                        T mj = lm[e * 32 + lane];
+                        T f, df;
+                        m4(q, f, df);
+                        S0 += mj * f;
+                        S1 += mj * q * df;
+                        nn += q < T(2);
+                    }
+                }
+                S0 = group_sum<LPP>(S0);
+                S1 = group_sum<LPP>(S1);
+                nn = group_sum<LPP>(nn);
+                if (go) {
+                    ++it;
+                    if (sub == 0) pairs += nn;
+                    T hinv = T(1) / h;
+                    T hinv3 = hinv * hinv * hinv;
+                    T rho = T(1.0 / kPi) * S0 * hinv3;
+                    T drho = -T(1.0 / kPi) * hinv3 * hinv * (T(3) * S0 + S1);
+                    bool c = nr_update(h, lo, hi, rho, drho, mi, eta3, tol);
+                    if ((double)h > 0.25 * Lmin) {
+                        atomicOr(&ps.diag->status, ST_BOX);
+                        c = true;
+                    }
+                    if (!c && it >= maxit) {
+                        noconv = true;
+                        c = true;
+                    }
+                    conv = c;
+                    if (h > hs) need = true;
+                }
+            }
+            if (!__any_sync(FULL, need)) break;
+            if (attempt + 1 >= kMaxRebuild) {
+                if (need) fail = true;
+                break;
+            }
+            need = false;
+        }
+        // final evaluation at the returned h
+        T S0 = T(0), S1 = T(0);
+        int nn = 0;
+        bool fin = active && !fail;
+        if (fin) {
+            const T hinv = T(1) / h;
+            for (int e = 0; e < cnt; ++e) {
+                T q = lr[e * 32 + lane] * hinv;
+                T mj = lm[e * 32 + lane];
+                T f, df;
+                m4(q, f, df);
+                S0 += mj * f;
+                S1 += mj * q * df;
+                nn += q < T(2);
+            }
+        }
+        S0 = group_sum<LPP>(S0);
+        S1 = group_sum<LPP>(S1);
+        nn = group_sum<LPP>(nn);
+        if (fin && sub == 0) {
+            pairs += nn;
+            density_epilogue<T>(b, ps, s, pi, h, S0, S1, use_pred);
+            if (noconv) {
+                atomicOr(&ps.diag->status, ST_NOCONV);
+                atomicAdd(&ps.diag->unconverged, 1);
+            }
+        }
+        if (active && fail && sub == 0) {
+            int k = atomicAdd(&b.counters[8], 1);
+            b.fallback_list[k] = (int)s;
+            b.sh[s] = (double)h;  // best guess so far
+        }
+        // statistics (one atomic per warp per quantity)
+        long long tp = warp_sum(pairs), tt = warp_sum(tested);
+        int itn = (fin && sub == 0) ? it : 0;
+        long long its = warp_sum((long long)itn);
+        int itmax = warp_max(itn);
+        int nmin = warp_min((fin && sub == 0) ? nn : 0x7fffffff);
+        int nmax = warp_max((fin && sub == 0) ? nn : 0);
+        long long nsum = warp_sum((long long)((fin && sub == 0) ? nn : 0));
+        if (lane == 0) {
+            ProbDiag *dg = ps.diag;
+            atomicAdd((unsigned long long *)&dg->density_pairs, (unsigned long long)tp);
+            atomicAdd((unsigned long long *)&dg->candidates, (unsigned long long)tt);
+            atomicAdd((unsigned long long *)&dg->nr_iter, (unsigned long long)its);
+            atomicAdd((unsigned long long *)&dg->ngb_sum, (unsigned long long)nsum);
+            atomicMax(&dg->nr_max, itmax);
+            if (nmax > 0) {
+                atomicMin(&dg->ngb_min, nmin);
+                atomicMax(&dg->ngb_max, nmax);
+            }
+        }
+    }
+}
+
+// Slow path: one warp per particle, the tree walked again in every
+// Newton-Raphson iteration, all lanes summing candidates directly.
+template <typename T>
+__global__ void __launch_bounds__(128) k_density_fallback(BatchView b, int use_pred)
+{
+    using V = typename Vec4<T>::type;
+    const int lane = threadIdx.x & 31;
+    const int nf = b.counters[8];
+    const V *pm = (const V *)b.pm;
+    int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int k = w; k < nf; k += nw) {
+        const long long s = b.fallback_list[k];
+        const int leaf = (int)b.flag[s] - 1;
+        const int p = b.leaf_pid[leaf];
+        const ProbStatic &ps = b.prob[p];
+        const ProbDyn &dy = b.dyn[p];
+        const PhysParams &ph = ps.ph;
+        const NodeBox boxA = b.nodes[0][leaf];
+        const V pi = pm[s];
+        const T eta3 = (T)(ph.eta * ph.eta * ph.eta);
+        const T tol = (T)ph.h_tol;
+        double Lmin = ph.periodic ? fmin(ph.box_len[0], fmin(ph.box_len[1], ph.box_len[2])) : INFINITY;
+        T h = (T)b.sh[s];
+        T lo = T(0), hi = tinf<T>();
+        int it = 0;
+        bool conv = false, noconv = false;
+        long long pairs = 0;
+        T S0, S1;
+        int nn;
+        auto sums = [&](T hh) {
+            S0 = T(0);
+            S1 = T(0);
+            nn = 0;
+            const T hinv = T(1) / hh;
+            const T R2 = T(4) * hh * hh;
+            float Rq = __fmul_ru(2.0f, (float)hh) * 1.0001f;
+            walk(
+                b, dy, [&](const NodeBox &nb) { return box_overlap(boxA.plo, boxA.phi, nb.plo, nb.phi, Rq, ph); },
+                [&](int B) {
+                    const int stB = b.leaf_start[B], nB = b.leaf_start[B + 1] - stB;
+                    T Dx, Dy, Dz;
+                    leaf_shift<T>(b, leaf, B, ph, Dx, Dy, Dz);
+                    if (lane < nB) {
+                        V q = pm[stB + lane];
+                        T dx = pi.x - (q.x + Dx), dyy = pi.y - (q.y + Dy), dz = pi.z - (q.z + Dz);
+                        T r2 = dx * dx + dyy * dyy + dz * dz;
+                        if (r2 < R2) {
+                            T f, df, qq = sqrt(r2) * hinv;
+                            m4(qq, f, df);
+                            S0 += q.w * f;
+                            S1 += q.w * qq * df;
+                            ++nn;
+                        }
+                    }
+                });
+            S0 = warp_sum(S0);
+            S1 = warp_sum(S1);
+            nn = warp_sum(nn);
+        };
+        while (!conv) {
+            sums(h);
+            ++it;
+            pairs += nn;
+            T hinv = T(1) / h;
+            T hinv3 = hinv * hinv * hinv;
+            T rho = T(1.0 / kPi) * S0 * hinv3;
+            T drho = -T(1.0 / kPi) * hinv3 * hinv * (T(3) * S0 + S1);
+            bool c = nr_update(h, lo, hi, rho, drho, pi.w, eta3, tol);
+            if ((double)h > 0.25 * Lmin) {
+                if (lane == 0) atomicOr(&ps.diag->status, ST_BOX);
+                c = true;
+            }
+            if (!c && it >= ph.h_max_iter) {
+                noconv = true;
+                c = true;
+            }
+            conv = c;
+        }
+        sums(h);
+        pairs += nn;
+        if (lane == 0) {
+            density_epilogue<T>(b, ps, s, pi, h, S0, S1, use_pred);
+            if (noconv) {
+                atomicOr(&ps.diag->status, ST_NOCONV);
+                atomicAdd(&ps.diag->unconverged, 1);
+            }
+            ProbDiag *dg = ps.diag;
+            atomicAdd((unsigned long long *)&dg->density_pairs, (unsigned long long)pairs);
+            atomicAdd((unsigned long long *)&dg->nr_iter, (unsigned long long)it);
+            atomicAdd((unsigned long long *)&dg->fallback, 1ull);
+            atomicAdd((unsigned long long *)&dg->ngb_sum, (unsigned long long)nn);
+            atomicMax(&dg->nr_max, it);
+            atomicMin(&dg->ngb_min, nn);
+            atomicMax(&dg->ngb_max, nn);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// forces
+// ---------------------------------------------------------------------------
+template <typename T, int LPP>
+struct FCfg {
+    using V = typename Vec4<T>::type;
+    static constexpr int CH = 64;
+    static constexpr int LC = CH / LPP;  // list entries per lane per chunk (cannot overflow)
+    static constexpr int WPB = 4;
+    static constexpr size_t per_warp = 4 * CH * sizeof(V) + (size_t)LC * 32;
+    static constexpr size_t smem = WPB * per_warp;
+};
+
+// Compensated sum with an error-free transformation per addition (Knuth's
+// branch-free TwoSum): s + c carries the exact running sum to O(n eps^2),
+// whatever the signs and magnitudes of the terms.
+template <typename T>
+struct TwoSumAcc {
+    T s, c;
+    __device__ __forceinline__ void add(T x)
+    {
+        T t = add_rn(s, x);
+        T xp = t - s;
+        T sp = t - xp;
+        T e = (s - sp) + (x - xp);
+        c = c + e;
+        s = t;
+    }
+};
+
+template <typename T, int LPP>
+__global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32) k_forces(BatchView b)
+{
+    using C = FCfg<T, LPP>;
+    using V = typename C::V;
+    extern __shared__ __align__(32) unsigned char smem[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    unsigned char *mine = smem + wib * C::per_warp;
+    V *c0 = reinterpret_cast<V *>(mine);  // (offset, 1/h)
+    V *c1 = c0 + C::CH;                    // (v, c)
+    V *c2 = c1 + C::CH;                    // (A, rho, m, u)
+    V *c3 = c2 + C::CH;                    // (leaf shift, sorted index bits)
+    unsigned char *lst = reinterpret_cast<unsigned char *>(c3 + C::CH);
+    const int pp = lane / LPP, sub = lane % LPP;
+    const int nleaf = b.counters[0];
+    const V *gph = (const V *)b.ph, *gvc = (const V *)b.vc, *gth = (const V *)b.th;
+
+    for (;;) {
+        int leaf = 0;
+        if (lane == 0) leaf = atomicAdd(&b.counters[11 + lpp_log2(LPP)], 1);
+        leaf = __shfl_sync(FULL, leaf, 0);
+        if (leaf >= nleaf) break;
+        const int p = b.leaf_pid[leaf];
+        const ProbStatic &ps = b.prob[p];
+        if (ps.lpp != LPP) continue;  // leaf of a problem served by another launch
+        const int st = b.leaf_start[leaf], nA = b.leaf_start[leaf + 1] - st;
+        const ProbDyn &dy = b.dyn[p];
+        const PhysParams &ph = ps.ph;
+        const NodeBox boxA = b.nodes[0][leaf];
+        const bool active = pp < nA;
+        const int s = st + (active ? pp : 0);
+        const V xi = gph[s], vi = gvc[s], ti = gth[s];
+        const T alpha = (T)ph.alpha_av, beta = (T)ph.beta_av, aac = (T)ph.alpha_ac;
+        const bool adi = ph.eos == SPH_EOS_ADIABATIC;
+        const T sigma = T(1.0 / kPi);
+        const T hi2 = xi.w * xi.w, hi4 = hi2 * hi2;
+        TwoSumAcc<T> ax{T(0), T(0)}, ay{T(0), T(0)}, az{T(0), T(0)};
+        T du = T(0), vs = T(-1);
+        long long pairs = 0, tested = 0;
+        const float R = __fmul_ru(2.0f, boxA.plo.w) * 1.0001f;
+        int nbuf = 0;
+        auto flush = [&]() {
+            int cnt = 0;
+            for (int k = sub; k < nbuf; k += LPP) {
+                V a0 = c0[k], a3 = c3[k];
+                int sj = t_as_bits(a3.w);
+                bool lo = s < sj;
+                T ax_ = lo ? xi.x : a0.x, bx = lo ? a0.x : xi.x, dx = lo ? a3.x : -a3.x;
+                T ay_ = lo ? xi.y : a0.y, by = lo ? a0.y : xi.y, dyy = lo ? a3.y : -a3.y;
+                T az_ = lo ? xi.z : a0.z, bz = lo ? a0.z : xi.z, dz = lo ? a3.z : -a3.z;
+                T rx = ax_ - (dx + bx), ry = ay_ - (dyy + by), rz = az_ - (dz + bz);
+                T r2 = rx * rx + ry * ry + rz * rz;
+                T hm = xi.w < a0.w ? xi.w : a0.w;
+                if (active && sj != s && r2 * hm * hm < T(4)) lst[cnt++ * 32 + lane] = (unsigned char)k;
+            }
+            tested += (nbuf - sub + LPP - 1) / LPP;
+            __syncwarp();
+            int mx = warp_max(cnt);
+            for (int e = 0; e < mx; ++e) {
+                if (e < cnt) {
+                    int k = lst[e * 32 + lane];
+                    V a0 = c0[k], a1 = c1[k], a2 = c2[k], a3 = c3[k];
+                    int sj = t_as_bits(a3.w);
+                    bool lo = s < sj;
+                    T ax_ = lo ? xi.x : a0.x, bx = lo ? a0.x : xi.x, dx = lo ? a3.x : -a3.x;
+                    T ay_ = lo ? xi.y : a0.y, by = lo ? a0.y : xi.y, dyy = lo ? a3.y : -a3.y;
+                    T az_ = lo ? xi.z : a0.z, bz = lo ? a0.z : xi.z, dz = lo ? a3.z : -a3.z;
+                    T rx = ax_ - (dx + bx), ry = ay_ - (dyy + by), rz = az_ - (dz + bz);
+                    if (!lo) {
+                        rx = -rx;
+                        ry = -ry;
+                        rz = -rz;
+                    }
+                    T r2 = rx * rx + ry * ry + rz * rz;
+                    T rinv = rsqrt_t(r2);
+                    T r = r2 * rinv;
+                    T qi = r * xi.w, qj = r * a0.w;
+                    T hj2 = a0.w * a0.w;
+                    T gi = sigma * m4_df(qi) * hi4;
+                    T gj = sigma * m4_df(qj) * (hj2 * hj2);
+                    T pterm = add_rn(mul_rn(ti.x, gi), mul_rn(a2.x, gj));
+                    T vx = vi.x - a1.x, vy = vi.y - a1.y, vz = vi.z - a1.z;
+                    T vdr = (vx * rx + vy * ry + vz * rz) * rinv;
+                    T mu = vdr < T(0) ? vdr : T(0);
+                    T rhob_inv = T(2) / add_rn(ti.y, a2.y);
+                    T gbar = T(0.5) * add_rn(gi, gj);
+                    T vsig = add_rn(vi.w, a1.w) - beta * mu;
+                    T visc = alpha * vsig * mu * rhob_inv;
+                    T S = visc * gbar - pterm;
+                    T wgt = mul_rn(ti.z, a2.z) * S * rinv;
+                    ax.add(mul_rn(wgt, rx));
+                    ay.add(mul_rn(wgt, ry));
+                    az.add(mul_rn(wgt, rz));
+                    if (adi)
+                        du += a2.z * (ti.x * vdr * gi +
+                                      rhob_inv * gbar * (T(-0.5) * alpha * vsig * mu * mu + aac * fabs(vdr) * (ti.w - a2.w)));
+                    vs = vsig > vs ? vsig : vs;
+                    ++pairs;
+                }
+            }
+            __syncwarp();
+            nbuf = 0;
+        };
+        walk(
+            b, dy,
+            [&](const NodeBox &nb) {
+                return box_overlap(boxA.plo, boxA.phi, nb.plo, nb.phi, R, ph) ||
+                       box_overlap(boxA.plo, boxA.phi, nb.slo, nb.shi, 0.f, ph);
+            },
+            [&](int B) {
+                const int stB = b.leaf_start[B], nB = b.leaf_start[B + 1] - stB;
+                if (nbuf + nB > C::CH) flush();
+                T Dx, Dy, Dz;
+                leaf_shift<T>(b, leaf, B, ph, Dx, Dy, Dz);
+                if (lane < nB) {
+                    c0[nbuf + lane] = gph[stB + lane];
+                    c1[nbuf + lane] = gvc[stB + lane];
+                    c2[nbuf + lane] = gth[stB + lane];
+                    V d;
+                    d.x = Dx;
+                    d.y = Dy;
+                    d.z = Dz;
+                    d.w = bits_as_t(stB + lane, T(0));
+                    c3[nbuf + lane] = d;
+                }
+                __syncwarp();
+                nbuf += nB;
+            });
+        flush();
+        // combine the lanes of each particle; FP64 for the compensated sums
+        double Fx = (double)ax.s + (double)ax.c, Fy = (double)ay.s + (double)ay.c, Fz = (double)az.s + (double)az.c;
+        Fx = group_sum<LPP>(Fx);
+        Fy = group_sum<LPP>(Fy);
+        Fz = group_sum<LPP>(Fz);
+        du = group_sum<LPP>(du);
+        vs = group_max<LPP>(vs);
+        double dti = INFINITY;
+        if (active && sub == 0) {
+            long long g = b.perm[s];
+            long long i = g - ps.base;
+            double m = ps.m[i];
+            double a[3] = {Fx / m, Fy / m, Fz / m};
+            double vsig = vs < T(0) ? 2.0 * (double)vi.w : (double)vs;
+            ps.ax[i] = a[0];
+            ps.ay[i] = a[1];
+            ps.az[i] = a[2];
+            ps.du[i] = adi ? (double)du : 0.0;
+            ps.vsig[i] = vsig;
+            dti = ph.c_cfl * b.sh[s] / vsig;
+            if (!(isfinite(a[0]) && isfinite(a[1]) && isfinite(a[2]) && isfinite((double)du)))
+                atomicOr(&ps.diag->status, ST_NONFINITE);
+        }
+        double dmin = warp_min(dti);
+        long long tp = warp_sum(pairs), tt = warp_sum(tested);
+        if (lane == 0) {
+            if (dmin < INFINITY)
+                atomicMin(&ps.diag->dt_min_bits, (unsigned long long)__double_as_longlong(dmin));
+            atomicAdd((unsigned long long *)&ps.diag->force_pairs, (unsigned long long)tp);
+            atomicAdd((unsigned long long *)&ps.diag->candidates, (unsigned long long)tt);
+        }
+    }
+}
+
+template <typename Kern>
+void set_smem(Kern k, size_t bytes)
+{
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T, int LPP>
+cudaError_t run_density(const BatchView &b, int use_pred, cudaStream_t st)
+{
+    using C = DCfg<T, LPP>;
+    static bool init = false;
+    if (!init) {
+        set_smem(k_density<T, LPP>, C::smem);
+        init = true;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_density<T, LPP>, C::WPB * 32, C::smem);
+    if (per_sm < 1) per_sm = 1;
+    int grid = dev_info().sm_count * per_sm;
+    k_density<T, LPP><<<grid, C::WPB * 32, C::smem, st>>>(b, use_pred);
+    return cudaGetLastError();
+}
+
+void density_fallback_launch(const BatchView &b, int precision, int use_pred, cudaStream_t st)
+{
+    if (precision == SPH_PREC_FP64) k_density_fallback<double><<<dev_info().sm_count * 4, 128, 0, st>>>(b, use_pred);
+    else k_density_fallback<float><<<dev_info().sm_count * 4, 128, 0, st>>>(b, use_pred);
+}
+
+template <typename T, int LPP>
+cudaError_t run_forces(const BatchView &b, cudaStream_t st)
+{
+    using C = FCfg<T, LPP>;
+    static bool init = false;
+    if (!init) {
+        set_smem(k_forces<T, LPP>, C::smem);
+        init = true;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forces<T, LPP>, C::WPB * 32, C::smem);
+    if (per_sm < 1) per_sm = 1;
+    int grid = dev_info().sm_count * per_sm;
+    k_forces<T, LPP><<<grid, C::WPB * 32, C::smem, st>>>(b);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_density(const BatchView &b, int precision, int use_pred, cudaStream_t st)
+{
+    if (b.ntot == 0) return cudaSuccess;
+    cudaMemsetAsync(b.counters + 8, 0, sizeof(int), st);  // fallback count
+    for (int k = 0; k < 4; ++k) {
+        if (!(b.lpp_mask & (1 << k))) continue;
+        cudaMemsetAsync(b.counters + 11 + k, 0, sizeof(int), st);  // work counter of this class
+        cudaError_t e;
+        if (precision == SPH_PREC_FP64) {
+            if (k == 2) e = run_density<double, 4>(b, use_pred, st);
+            else e = run_density<double, 2>(b, use_pred, st);
+        } else {
+            switch (k) {
+            case 0: e = run_density<float, 1>(b, use_pred, st); break;
+            case 1: e = run_density<float, 2>(b, use_pred, st); break;
+            case 2: e = run_density<float, 4>(b, use_pred, st); break;
+            default: e = run_density<float, 8>(b, use_pred, st); break;
+            }
+        }
+        if (e != cudaSuccess) return e;
+    }
+    density_fallback_launch(b, precision, use_pred, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forces(const BatchView &b, int precision, cudaStream_t st)
+{
+    if (b.ntot == 0) return cudaSuccess;
+    for (int k = 0; k < 4; ++k) {
+        if (!(b.lpp_mask & (1 << k))) continue;
+        cudaMemsetAsync(b.counters + 11 + k, 0, sizeof(int), st);
+        cudaError_t e;
+        if (precision == SPH_PREC_FP64) {
+            if (k == 2) e = run_forces<double, 4>(b, st);
+            else e = run_forces<double, 2>(b, st);
+        } else {
+            switch (k) {
+            case 0: e = run_forces<float, 1>(b, st); break;
+            case 1: e = run_forces<float, 2>(b, st); break;
+            case 2: e = run_forces<float, 4>(b, st); break;
+            default: e = run_forces<float, 8>(b, st); break;
+            }
+        }
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace sph

@@ -1,0 +1,363 @@
+"""ctypes binding of libsph.so (include/sph.h), plus a small helper that owns
+the caller-side device memory as PyTorch tensors.
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+If libsph.so is missing the import of this module fails loudly; there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsph.so")
+
+OK, EINVAL, EBOX, ENOCONV, ENONFINITE, ETIMEOUT, ETOOBIG, EBUSY, EAGAIN, ECUDA, ENOSPACE = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10)
+EOS_ADIABATIC, EOS_ISOTHERMAL = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+FLAG_ASYNC, FLAG_TIMING = 1, 2
+NSTAGES = 7
+STAGES = ["kick_drift", "sort", "tree", "density", "refit", "forces", "close"]
+
+_DP = C.POINTER(C.c_double)
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("periodic", C.c_int),
+        ("box_lo", C.c_double * 3),
+        ("box_len", C.c_double * 3),
+        ("eos", C.c_int),
+        ("gamma", C.c_double),
+        ("cs_iso", C.c_double),
+        ("eta", C.c_double),
+        ("alpha_av", C.c_double),
+        ("beta_av", C.c_double),
+        ("alpha_ac", C.c_double),
+        ("c_cfl", C.c_double),
+        ("h_tol", C.c_double),
+        ("h_max_iter", C.c_int),
+        ("precision", C.c_int),
+        ("kernel", C.c_int),
+        ("leaf_size", C.c_int),
+        ("lanes_per_particle", C.c_int),
+        ("flags", C.c_uint),
+    ]
+
+
+STATE_FIELDS = ["x", "y", "z", "vx", "vy", "vz", "u", "m", "h",
+                "rho", "omega", "P", "c", "ax", "ay", "az", "du", "vsig"]
+
+
+class State(C.Structure):
+    _fields_ = [(f, C.c_void_p) for f in STATE_FIELDS]
+
+
+class Diag(C.Structure):
+    _fields_ = [
+        ("mass", C.c_double),
+        ("momentum", C.c_double * 3),
+        ("energy", C.c_double),
+        ("force_sum", C.c_double * 3),
+        ("dEdt", C.c_double),
+        ("dt_next", C.c_double),
+        ("time", C.c_double),
+        ("steps", C.c_int64),
+        ("nr_iterations", C.c_int64),
+        ("nr_max", C.c_int32),
+        ("ngb_min", C.c_int32),
+        ("ngb_max", C.c_int32),
+        ("ngb_mean", C.c_double),
+        ("density_pairs", C.c_int64),
+        ("force_pairs", C.c_int64),
+        ("candidates", C.c_int64),
+        ("fallback", C.c_int64),
+        ("leaves", C.c_int64),
+        ("status", C.c_int32),
+        ("unconverged", C.c_int32),
+    ]
+
+    def as_dict(self):
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = list(v) if hasattr(v, "__len__") else v
+        return d
+
+
+class ServerCfg(C.Structure):
+    _fields_ = [
+        ("pool", C.c_void_p),
+        ("pool_bytes", C.c_size_t),
+        ("max_slots", C.c_int),
+        ("max_queue", C.c_int),
+        ("stream", C.c_void_p),
+        ("precision", C.c_int),
+    ]
+
+
+class Request(C.Structure):
+    _fields_ = [("n", C.c_int64)] + [(f, _DP) for f in ("x", "y", "z", "vx", "vy", "vz", "u", "m", "h")] + [
+        ("params", Params),
+        ("nsteps", C.c_int),
+        ("arrival", C.c_double),
+    ]
+
+
+class Result(C.Structure):
+    _fields_ = [
+        ("status", C.c_int),
+        ("n", C.c_int64),
+        ("steps_done", C.c_int),
+        ("arrival", C.c_double),
+        ("admitted", C.c_double),
+        ("completed", C.c_double),
+        ("t_sim", C.c_double),
+    ] + [(f, _DP) for f in ("x", "y", "z", "vx", "vy", "vz", "u", "h", "rho")]
+
+
+class SPHError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where} failed with status {code}: {last_error()}")
+
+
+_lib = None
+
+
+def lib():
+    """Load libsph.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(the CUDA library is required; there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        vp, i, i64, d = C.c_void_p, C.c_int, C.c_int64, C.c_double
+        sig = {
+            "sph_params_default": (i, [C.POINTER(Params)]),
+            "sph_workspace_bytes": (C.c_size_t, [i64, C.POINTER(Params)]),
+            "sph_setup": (i, [C.POINTER(vp), C.POINTER(Params), i64, C.POINTER(State), vp, C.c_size_t, vp]),
+            "sph_density_h": (i, [vp]),
+            "sph_forces": (i, [vp]),
+            "sph_step": (i, [vp, d, C.POINTER(d)]),
+            "sph_run": (i, [vp, i]),
+            "sph_sync": (i, [vp]),
+            "sph_diagnostics": (i, [vp, C.POINTER(Diag)]),
+            "sph_neighbours": (i, [vp, i, vp, vp, vp, i64, C.POINTER(i64)]),
+            "sph_destroy": (i, [vp]),
+            "sph_stage_times": (i, [vp, C.POINTER(d)]),
+            "sph_step_kernel_count": (i, [vp, C.POINTER(i)]),
+            "sph_batch_workspace_bytes": (C.c_size_t, [C.POINTER(vp), i]),
+            "sph_batch_step": (i, [C.POINTER(vp), i, i, vp, C.c_size_t]),
+            "sph_server_create": (i, [C.POINTER(vp), C.POINTER(ServerCfg)]),
+            "sph_server_submit": (i, [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+            "sph_server_run": (i, [vp, d, i]),
+            "sph_server_poll": (i, [vp, C.c_uint64, C.POINTER(Result)]),
+            "sph_server_clock": (d, [vp]),
+            "sph_server_destroy": (i, [vp]),
+            "sph_last_error": (C.c_char_p, []),
+            "sph_version": (C.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    try:
+        return lib().sph_last_error().decode()
+    except Exception:  # pragma: no cover
+        return ""
+
+
+def check(rc: int, where: str, allow=()):
+    if rc != OK and rc not in allow:
+        raise SPHError(rc, where)
+    return rc
+
+
+# ---- thin wrappers with the C names -------------------------------------------
+def sph_params_default() -> Params:
+    p = Params()
+    check(lib().sph_params_default(C.byref(p)), "sph_params_default")
+    return p
+
+
+def sph_workspace_bytes(n: int, p: Params) -> int:
+    return int(lib().sph_workspace_bytes(int(n), C.byref(p)))
+
+
+def sph_setup(p: Params, n: int, state: State, ws_ptr: int, ws_bytes: int, stream: int):
+    ctx = C.c_void_p()
+    rc = lib().sph_setup(C.byref(ctx), C.byref(p), int(n), C.byref(state), C.c_void_p(ws_ptr), int(ws_bytes),
+                         C.c_void_p(stream))
+    return rc, ctx
+
+
+def sph_density_h(ctx) -> int:
+    return lib().sph_density_h(ctx)
+
+
+def sph_forces(ctx) -> int:
+    return lib().sph_forces(ctx)
+
+
+def sph_step(ctx, dt: float):
+    used = C.c_double(0.0)
+    rc = lib().sph_step(ctx, float(dt), C.byref(used))
+    return rc, used.value
+
+
+def sph_step_nowait(ctx, dt: float) -> int:
+    return lib().sph_step(ctx, float(dt), None)
+
+
+def sph_run(ctx, nsteps: int) -> int:
+    return lib().sph_run(ctx, int(nsteps))
+
+
+def sph_sync(ctx) -> int:
+    return lib().sph_sync(ctx)
+
+
+def sph_diagnostics(ctx) -> Diag:
+    d = Diag()
+    check(lib().sph_diagnostics(ctx, C.byref(d)), "sph_diagnostics")
+    return d
+
+
+def sph_neighbours(ctx, kind: int, h_ptr: int, off_ptr: int, idx_ptr: int, cap: int):
+    tot = C.c_int64(0)
+    rc = lib().sph_neighbours(ctx, int(kind), C.c_void_p(h_ptr) if h_ptr else None, C.c_void_p(off_ptr),
+                              C.c_void_p(idx_ptr), int(cap), C.byref(tot))
+    return rc, tot.value
+
+
+def sph_destroy(ctx) -> int:
+    return lib().sph_destroy(ctx)
+
+
+def sph_stage_times(ctx) -> list:
+    ms = (C.c_double * NSTAGES)()
+    check(lib().sph_stage_times(ctx, ms), "sph_stage_times")
+    return list(ms)
+
+
+def sph_step_kernel_count(ctx) -> int:
+    k = C.c_int(0)
+    check(lib().sph_step_kernel_count(ctx, C.byref(k)), "sph_step_kernel_count")
+    return k.value
+
+
+def sph_batch_workspace_bytes(ctxs) -> int:
+    arr = (C.c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    return int(lib().sph_batch_workspace_bytes(arr, len(ctxs)))
+
+
+def sph_batch_step(ctxs, nsteps: int, ws_ptr: int, ws_bytes: int) -> int:
+    arr = (C.c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    return lib().sph_batch_step(arr, len(ctxs), int(nsteps), C.c_void_p(ws_ptr), int(ws_bytes))
+
+
+# ---- helper: problem state held in PyTorch device memory ----------------------
+def make_params(precision: int = PREC_MIXED, **kw) -> Params:
+    """sph_params from keyword arguments (names as in sph_params; 'eos' may be
+    'adiabatic'/'isothermal'; box tuples accepted)."""
+    p = sph_params_default()
+    p.precision = precision
+    for k, v in kw.items():
+        if k == "eos":
+            p.eos = EOS_ISOTHERMAL if v in ("isothermal", 1) else EOS_ADIABATIC
+        elif k in ("box_lo", "box_len"):
+            setattr(p, k, (C.c_double * 3)(*v))
+        elif k == "periodic":
+            p.periodic = int(bool(v))
+        else:
+            setattr(p, k, v)
+    return p
+
+
+class Problem:
+    """One SPH problem: FP64 state tensors and the workspace on the GPU, and
+    the library context that points at them."""
+
+    def __init__(self, arrays: dict, params: Params, device="cuda", stream=None):
+        import torch
+        self.torch = torch
+        self.n = n = len(arrays["x"])
+        self.params = params
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.t = {}
+        for f in STATE_FIELDS:
+            a = arrays.get(f)
+            if a is not None:
+                self.t[f] = torch.as_tensor(a, dtype=torch.float64).to(self.device).contiguous()
+            else:
+                self.t[f] = torch.zeros(max(n, 1), dtype=torch.float64, device=self.device)
+        self.state = State(**{f: self.t[f].data_ptr() for f in STATE_FIELDS})
+        self.ws_bytes = sph_workspace_bytes(n, params)
+        if self.ws_bytes == 0:
+            raise SPHError(EINVAL, "sph_workspace_bytes")
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        rc, self.ctx = sph_setup(params, n, self.state, self.ws.data_ptr(), self.ws_bytes, self.stream.cuda_stream)
+        check(rc, "sph_setup")
+
+    def density_h(self, allow=()):
+        return check(sph_density_h(self.ctx), "sph_density_h", allow)
+
+    def forces(self, allow=()):
+        return check(sph_forces(self.ctx), "sph_forces", allow)
+
+    def step(self, dt: float = -1.0, allow=()):
+        rc, used = sph_step(self.ctx, dt)
+        check(rc, "sph_step", allow)
+        return used
+
+    def run(self, nsteps: int, allow=()):
+        return check(sph_run(self.ctx, nsteps), "sph_run", allow)
+
+    def sync(self, allow=()):
+        return check(sph_sync(self.ctx), "sph_sync", allow)
+
+    def diagnostics(self) -> Diag:
+        return sph_diagnostics(self.ctx)
+
+    def neighbours(self, kind: int, h=None):
+        """CSR (offsets, idx) as int64/int32 tensors on the device."""
+        torch = self.torch
+        off = torch.zeros(self.n + 1, dtype=torch.int64, device=self.device)
+        hp = 0
+        if h is not None:
+            ht = torch.as_tensor(h, dtype=torch.float64).to(self.device).contiguous()
+            hp = ht.data_ptr()
+        cap = max(1, self.n * 96)
+        while True:
+            idx = torch.zeros(cap, dtype=torch.int32, device=self.device)
+            rc, tot = sph_neighbours(self.ctx, kind, hp, off.data_ptr(), idx.data_ptr(), cap)
+            if rc == ENOSPACE and tot > cap:
+                cap = int(tot)
+                continue
+            check(rc, "sph_neighbours")
+            return off, idx[:tot]
+
+    def numpy(self, *fields):
+        self.stream.synchronize()
+        return {f: self.t[f][:self.n].cpu().numpy() for f in (fields or STATE_FIELDS)}
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            sph_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

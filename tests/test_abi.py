@@ -1,0 +1,83 @@
+"""Host-side checks of the C ABI (no GPU needed): the library builds for
+sm_103a, loads, exports every entry point include/sph.h declares, validates
+parameters and sizes workspaces without touching a device."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_1709_04488_gb300 import build as b
+    b.build()
+    from paper_1709_04488_gb300 import sph
+    return sph
+
+
+def _declared(header):
+    txt = open(os.path.join(ROOT, "include", header)).read()
+    return sorted(set(re.findall(r"\b(sph_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_every_declared_symbol_is_exported(S):
+    lib = S.lib()
+    names = _declared("sph.h")
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_struct_layouts_match_header(S, tmp_path):
+    """The ctypes mirrors of the public structs have the C layout (compiled
+    with gcc against include/sph.h)."""
+    src = tmp_path / "sizes.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "sph.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu\\n\","
+        "sizeof(sph_params),sizeof(sph_state),sizeof(sph_diag),sizeof(sph_server_cfg),"
+        "sizeof(sph_request),sizeof(sph_result),offsetof(sph_params,flags),offsetof(sph_diag,status));return 0;}\n")
+    exe = tmp_path / "sizes"
+    import subprocess
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    want = [C.sizeof(S.Params), C.sizeof(S.State), C.sizeof(S.Diag), C.sizeof(S.ServerCfg),
+            C.sizeof(S.Request), C.sizeof(S.Result), S.Params.flags.offset, S.Diag.status.offset]
+    assert got == want
+
+
+def test_defaults_are_the_papers(S):
+    p = S.sph_params_default()
+    assert p.eta == 1.2 and p.alpha_av == 1.0 and p.beta_av == 2.0 and p.c_cfl == 0.2
+
+
+def test_workspace_bytes_and_validation(S):
+    p = S.sph_params_default()
+    w1 = S.sph_workspace_bytes(1000, p)
+    w2 = S.sph_workspace_bytes(100000, p)
+    assert 0 < w1 < w2
+    assert w2 / 100000 < 600  # bytes per particle of scratch
+    assert S.sph_workspace_bytes(-1, p) == 0
+    bad = S.sph_params_default()
+    bad.eta = -1.0
+    assert S.sph_workspace_bytes(10, bad) == 0
+    bad = S.sph_params_default()
+    bad.kernel = 1
+    assert S.sph_workspace_bytes(10, bad) == 0
+    bad = S.sph_params_default()
+    bad.lanes_per_particle = 3
+    assert S.sph_workspace_bytes(10, bad) == 0
+
+
+def test_setup_rejects_bad_arguments_without_a_gpu(S):
+    p = S.sph_params_default()
+    st = S.State()
+    rc, ctx = S.sph_setup(p, 10, st, 0, 0, 0)
+    assert rc in (S.EINVAL, S.ENOSPACE)
+    assert S.last_error() != ""
+    p.gamma = 1.0
+    rc, ctx = S.sph_setup(p, 10, st, 0, 0, 0)
+    assert rc == S.EINVAL
