@@ -40,15 +40,21 @@ def _stale(obj: str, src: str) -> bool:
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 
-def build(verbose: bool = False, force: bool = False, extra: list | None = None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, force: bool = False, extra: list | None = None,
+          out: str | None = None, build_dir: str | None = None) -> str:
+    """Compile the sources (in parallel) and link libsph.so.  `extra` adds
+    nvcc flags (e.g. -D overrides of launch-shape constants); `out` and
+    `build_dir` redirect the outputs."""
+    lib = out or LIB
+    bdir = build_dir or BUILD
+    os.makedirs(bdir, exist_ok=True)
     exe = nvcc()
     flags = NVFLAGS + (extra or [])
     jobs = []
     objs = []
     for s in SOURCES:
         src = os.path.join(CSRC, s)
-        obj = os.path.join(BUILD, s.replace(".cu", ".o"))
+        obj = os.path.join(bdir, s.replace(".cu", ".o"))
         objs.append(obj)
         if force or _stale(obj, src):
             jobs.append([exe, *ARCH, *flags, "-c", src, "-o", obj])
@@ -63,11 +69,11 @@ def build(verbose: bool = False, force: bool = False, extra: list | None = None)
 
     with cf.ThreadPoolExecutor(max_workers=len(jobs) or 1) as ex:
         list(ex.map(run, jobs))
-    if jobs or not os.path.exists(LIB):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if jobs or not os.path.exists(lib):
+        tmp = lib + f".tmp{os.getpid()}"
         run([exe, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

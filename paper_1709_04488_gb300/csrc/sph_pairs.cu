@@ -30,6 +30,21 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 __host__ __device__ constexpr int lpp_log2(int l) { return l == 1 ? 0 : l == 2 ? 1 : l == 4 ? 2 : 3; }
 constexpr double kListMargin = 1.03;  // list radius = 2 h * margin
+
+// launch-shape constants (staged candidates per chunk, blocks per SM the
+// register budget is sized for); overridable at build time for tuning sweeps
+#ifndef SPH_FORCE_CH
+#define SPH_FORCE_CH 64
+#endif
+#ifndef SPH_FORCE_MINB
+#define SPH_FORCE_MINB 8
+#endif
+#ifndef SPH_DENS_CH
+#define SPH_DENS_CH 128
+#endif
+#ifndef SPH_DENS_MINB
+#define SPH_DENS_MINB 4
+#endif
 constexpr int kMaxRebuild = 6;
 
 template <typename T>
@@ -116,8 +131,10 @@ __device__ __forceinline__ bool box_overlap(const float4 &alo, const float4 &ahi
            axis_overlap(alo.z, ahi.z, blo.z, bhi.z, R, ph.periodic, (float)ph.box_len[2]);
 }
 
-// Warp-cooperative depth-first walk of one problem's tree: visit(leaf) is
-// called (warp-uniformly) for every leaf whose box passes test(box).
+// Warp-cooperative depth-first walk of one problem's tree.  At the leaf level
+// visit(mask, first) is called (warp-uniformly) with the ballot of the up to
+// 32 sibling leaves first..first+31 whose boxes pass test(box), so that a
+// whole group of candidate leaves is staged in one round of memory accesses.
 template <class Test, class Visit>
 __device__ __forceinline__ void walk(const BatchView &b, const ProbDyn &d, Test &&test, Visit &&visit)
 {
@@ -125,12 +142,17 @@ __device__ __forceinline__ void walk(const BatchView &b, const ProbDyn &d, Test 
     const int top = d.top_level;
     unsigned mask[kMaxLevels + 1];
     int base[kMaxLevels + 1];
-    int lvl = top;
-    base[top] = 0;
     {
         bool ok = lane < d.node_cnt[top] && test(b.nodes[top][d.node_off[top] + lane]);
-        mask[top] = __ballot_sync(FULL, ok);
+        unsigned m = __ballot_sync(FULL, ok);
+        if (top == 0) {
+            if (m) visit(m, d.node_off[0]);
+            return;
+        }
+        mask[top] = m;
+        base[top] = 0;
     }
+    int lvl = top;
     for (;;) {
         unsigned m = mask[lvl];
         if (m == 0u) {
@@ -140,15 +162,16 @@ __device__ __forceinline__ void walk(const BatchView &b, const ProbDyn &d, Test 
         int c = __ffs(m) - 1;
         mask[lvl] = m & (m - 1u);
         int node = base[lvl] + c;
-        if (lvl == 0) {
-            visit(d.node_off[0] + node);
-            continue;
-        }
         int ch = node * kBranch + lane;
         bool ok = ch < d.node_cnt[lvl - 1] && test(b.nodes[lvl - 1][d.node_off[lvl - 1] + ch]);
+        unsigned cm = __ballot_sync(FULL, ok);
+        if (lvl == 1) {
+            if (cm) visit(cm, d.node_off[0] + node * kBranch);
+            continue;
+        }
         --lvl;
         base[lvl] = node * kBranch;
-        mask[lvl] = __ballot_sync(FULL, ok);
+        mask[lvl] = cm;
     }
 }
 
@@ -167,6 +190,77 @@ __device__ __forceinline__ void leaf_shift(const BatchView &b, int A, int B, con
     dx = __shfl_sync(FULL, v, 0);
     dy = __shfl_sync(FULL, v, 1);
     dz = __shfl_sync(FULL, v, 2);
+}
+
+template <typename T>
+__device__ __forceinline__ int warp_incl_scan(int v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int w = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += w;
+    }
+    return v;
+}
+
+// Per-warp scratch for staging groups of candidate leaves.
+template <typename T, int CH>
+struct StageScratch {
+    unsigned char owner[CH];  // lane (candidate leaf) that owns each staged slot
+    int src[32];              // source index minus slot index, per candidate leaf
+    T dx[32], dy[32], dz[32]; // leaf shift (FP64 difference of reference points, cast)
+};
+
+// Stage the particles of the leaves first + k (bit k of mask) into slots
+// [nbuf, ...) of the warp's buffer, flushing when it is full.  load(slot, j,
+// dx, dy, dz) copies particle j with the shift of its leaf into `slot`.
+template <typename T, int CH, class Load, class Flush>
+__device__ __forceinline__ void stage_leaves(const BatchView &b, int A, unsigned mask, int first, const PhysParams &ph,
+                                             int &nbuf, StageScratch<T, CH> &sc, Load &&load, Flush &&flush)
+{
+    const int lane = threadIdx.x & 31;
+    const bool has = (mask >> lane) & 1u;
+    int stB = 0, nB = 0;
+    T Dx = T(0), Dy = T(0), Dz = T(0);
+    if (has) {
+        const int B = first + lane;
+        stB = b.leaf_start[B];
+        nB = b.leaf_start[B + 1] - stB;
+        const double *cb = b.leaf_c + 3LL * B, *ca = b.leaf_c + 3LL * A;
+        Dx = (T)min_image(cb[0] - ca[0], ph.box_len[0], ph.periodic);
+        Dy = (T)min_image(cb[1] - ca[1], ph.box_len[1], ph.periodic);
+        Dz = (T)min_image(cb[2] - ca[2], ph.box_len[2], ph.periodic);
+    }
+    unsigned rem = mask;
+    while (rem) {
+        const bool in = (rem >> lane) & 1u;
+        const int c = in ? nB : 0;
+        const int incl = warp_incl_scan<T>(c);
+        const bool fits = in && (nbuf + incl <= CH);
+        const unsigned fm = __ballot_sync(FULL, fits);
+        if (fm == 0u) {
+            flush();
+            continue;
+        }
+        const int tot = __shfl_sync(FULL, incl, 31 - __clz(fm));
+        if (fits) {
+            const int off = nbuf + incl - c;
+            for (int t = 0; t < c; ++t) sc.owner[off + t] = (unsigned char)lane;
+            sc.src[lane] = stB - off;
+            sc.dx[lane] = Dx;
+            sc.dy[lane] = Dy;
+            sc.dz[lane] = Dz;
+        }
+        __syncwarp();
+        for (int e = nbuf + lane; e < nbuf + tot; e += 32) {
+            const int k = sc.owner[e];
+            load(e, sc.src[k] + e, sc.dx[k], sc.dy[k], sc.dz[k]);
+        }
+        __syncwarp();
+        nbuf += tot;
+        rem &= ~fm;
+    }
 }
 
 // sum over the LPP lanes that serve one particle
@@ -219,9 +313,10 @@ template <typename T, int LPP>
 struct DCfg {
     using V = typename Vec4<T>::type;
     static constexpr int LCAP = 96 / LPP + 8;
-    static constexpr int CH = 64;
+    static constexpr int CH = SPH_DENS_CH;
     static constexpr int WPB = LPP == 1 ? 2 : 4;
-    static constexpr size_t per_warp = CH * sizeof(V) + (size_t)LCAP * 32 * 2 * sizeof(T);
+    static constexpr size_t scratch = (sizeof(StageScratch<T, CH>) + 31) & ~(size_t)31;
+    static constexpr size_t per_warp = CH * sizeof(V) + (size_t)LCAP * 32 * 2 * sizeof(T) + scratch;
     static constexpr size_t smem = WPB * per_warp;
 };
 
@@ -282,7 +377,7 @@ __device__ __forceinline__ void density_epilogue(const BatchView &b, const ProbS
 }
 
 template <typename T, int LPP>
-__global__ void __launch_bounds__(DCfg<T, LPP>::WPB * 32) k_density(BatchView b, int use_pred)
+__global__ void __launch_bounds__(DCfg<T, LPP>::WPB * 32, SPH_DENS_MINB) k_density(BatchView b, int use_pred)
 {
     using C = DCfg<T, LPP>;
     using V = typename C::V;
@@ -292,6 +387,7 @@ __global__ void __launch_bounds__(DCfg<T, LPP>::WPB * 32) k_density(BatchView b,
     V *cand = reinterpret_cast<V *>(mine);
     T *lr = reinterpret_cast<T *>(mine + C::CH * sizeof(V));
     T *lm = lr + C::LCAP * 32;
+    StageScratch<T, C::CH> &sc = *reinterpret_cast<StageScratch<T, C::CH> *>(lm + C::LCAP * 32);
     const int pp = lane / LPP, sub = lane % LPP;
     const int nleaf = b.counters[0];
     const V *pm = (const V *)b.pm;
@@ -354,20 +450,17 @@ __global__ void __launch_bounds__(DCfg<T, LPP>::WPB * 32) k_density(BatchView b,
             };
             walk(
                 b, dy, [&](const NodeBox &nb) { return box_overlap(boxA.plo, boxA.phi, nb.plo, nb.phi, Rq, ph); },
-                [&](int B) {
-                    const int stB = b.leaf_start[B], nB = b.leaf_start[B + 1] - stB;
-                    if (nbuf + nB > C::CH) flush();
-                    T Dx, Dy, Dz;
-                    leaf_shift<T>(b, leaf, B, ph, Dx, Dy, Dz);
-                    if (lane < nB) {
-                        V q = pm[stB + lane];
-                        q.x += Dx;
-                        q.y += Dy;
-                        q.z += Dz;
-                        cand[nbuf + lane] = q;
-                    }
-                    __syncwarp();
-                    nbuf += nB;
+                [&](unsigned mask, int first) {
+                    stage_leaves<T, C::CH>(
+                        b, leaf, mask, first, ph, nbuf, sc,
+                        [&](int slot, int j, T dx, T dyy, T dz) {
+                            V q = pm[j];
+                            q.x += dx;
+                            q.y += dyy;
+                            q.z += dz;
+                            cand[slot] = q;
+                        },
+                        flush);
                 });
             flush();
             if (group_any<LPP>(ovf) && active && !fail) fail = true;
@@ -512,7 +605,9 @@ __global__ void __launch_bounds__(128) k_density_fallback(BatchView b, int use_p
             float Rq = __fmul_ru(2.0f, (float)hh) * 1.0001f;
             walk(
                 b, dy, [&](const NodeBox &nb) { return box_overlap(boxA.plo, boxA.phi, nb.plo, nb.phi, Rq, ph); },
-                [&](int B) {
+                [&](unsigned mask, int first) {
+                  for (unsigned mm = mask; mm; mm &= mm - 1u) {
+                    const int B = first + __ffs(mm) - 1;
                     const int stB = b.leaf_start[B], nB = b.leaf_start[B + 1] - stB;
                     T Dx, Dy, Dz;
                     leaf_shift<T>(b, leaf, B, ph, Dx, Dy, Dz);
@@ -528,6 +623,7 @@ __global__ void __launch_bounds__(128) k_density_fallback(BatchView b, int use_p
                             ++nn;
                         }
                     }
+                  }
                 });
             S0 = warp_sum(S0);
             S1 = warp_sum(S1);
@@ -578,10 +674,11 @@ __global__ void __launch_bounds__(128) k_density_fallback(BatchView b, int use_p
 template <typename T, int LPP>
 struct FCfg {
     using V = typename Vec4<T>::type;
-    static constexpr int CH = 64;
+    static constexpr int CH = SPH_FORCE_CH;
     static constexpr int LC = CH / LPP;  // list entries per lane per chunk (cannot overflow)
     static constexpr int WPB = 4;
-    static constexpr size_t per_warp = 4 * CH * sizeof(V) + (size_t)LC * 32;
+    static constexpr size_t scratch = (sizeof(StageScratch<T, CH>) + 31) & ~(size_t)31;
+    static constexpr size_t per_warp = 4 * CH * sizeof(V) + (size_t)LC * 32 + scratch;
     static constexpr size_t smem = WPB * per_warp;
 };
 
@@ -603,7 +700,7 @@ struct TwoSumAcc {
 };
 
 template <typename T, int LPP>
-__global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32) k_forces(BatchView b)
+__global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, SPH_FORCE_MINB) k_forces(BatchView b)
 {
     using C = FCfg<T, LPP>;
     using V = typename C::V;
@@ -615,6 +712,7 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32) k_forces(BatchView b)
     V *c2 = c1 + C::CH;                    // (A, rho, m, u)
     V *c3 = c2 + C::CH;                    // (leaf shift, sorted index bits)
     unsigned char *lst = reinterpret_cast<unsigned char *>(c3 + C::CH);
+    StageScratch<T, C::CH> &sc = *reinterpret_cast<StageScratch<T, C::CH> *>(lst + C::LC * 32);
     const int pp = lane / LPP, sub = lane % LPP;
     const int nleaf = b.counters[0];
     const V *gph = (const V *)b.ph, *gvc = (const V *)b.vc, *gth = (const V *)b.th;
@@ -640,32 +738,42 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32) k_forces(BatchView b)
         const T hi2 = xi.w * xi.w, hi4 = hi2 * hi2;
         TwoSumAcc<T> ax{T(0), T(0)}, ay{T(0), T(0)}, az{T(0), T(0)};
         T du = T(0), vs = T(-1);
-        long long pairs = 0, tested = 0;
+        int pairs = 0, tested = 0;
         const float R = __fmul_ru(2.0f, boxA.plo.w) * 1.0001f;
         int nbuf = 0;
         auto flush = [&]() {
+            // membership: r_ij < 2 max(h_i, h_j).  The plain (non-canonical)
+            // difference decides it; where it differs from the canonical one
+            // the pair sits at q = 2 to rounding, where f' and its force vanish.
             int cnt = 0;
             for (int k = sub; k < nbuf; k += LPP) {
                 V a0 = c0[k], a3 = c3[k];
-                int sj = t_as_bits(a3.w);
-                bool lo = s < sj;
-                T ax_ = lo ? xi.x : a0.x, bx = lo ? a0.x : xi.x, dx = lo ? a3.x : -a3.x;
-                T ay_ = lo ? xi.y : a0.y, by = lo ? a0.y : xi.y, dyy = lo ? a3.y : -a3.y;
-                T az_ = lo ? xi.z : a0.z, bz = lo ? a0.z : xi.z, dz = lo ? a3.z : -a3.z;
-                T rx = ax_ - (dx + bx), ry = ay_ - (dyy + by), rz = az_ - (dz + bz);
+                T rx = xi.x - (a3.x + a0.x), ry = xi.y - (a3.y + a0.y), rz = xi.z - (a3.z + a0.z);
                 T r2 = rx * rx + ry * ry + rz * rz;
                 T hm = xi.w < a0.w ? xi.w : a0.w;
-                if (active && sj != s && r2 * hm * hm < T(4)) lst[cnt++ * 32 + lane] = (unsigned char)k;
+                if (active && t_as_bits(a3.w) != s && r2 * hm * hm < T(4)) lst[cnt++ * 32 + lane] = (unsigned char)k;
             }
             tested += (nbuf - sub + LPP - 1) / LPP;
             __syncwarp();
-            int mx = warp_max(cnt);
-            for (int e = 0; e < mx; ++e) {
-                if (e < cnt) {
-                    int k = lst[e * 32 + lane];
+            // spread the particle's pairs evenly over its LPP lanes
+            int pre[LPP];
+            int tot = 0;
+#pragma unroll
+            for (int q = 0; q < LPP; ++q) {
+                pre[q] = tot;
+                tot += __shfl_sync(FULL, cnt, (lane & ~(LPP - 1)) + q);
+            }
+            const int mx = warp_max(tot);
+            for (int e2 = sub; e2 < mx; e2 += LPP) {
+                if (e2 < tot) {
+                    int own = 0;
+#pragma unroll
+                    for (int q = 1; q < LPP; ++q) own = e2 >= pre[q] ? q : own;
+                    int k = lst[(e2 - pre[own]) * 32 + (lane & ~(LPP - 1)) + own];
                     V a0 = c0[k], a1 = c1[k], a2 = c2[k], a3 = c3[k];
                     int sj = t_as_bits(a3.w);
                     bool lo = s < sj;
+                    // canonical pair vector: formed from the lower sorted index
                     T ax_ = lo ? xi.x : a0.x, bx = lo ? a0.x : xi.x, dx = lo ? a3.x : -a3.x;
                     T ay_ = lo ? xi.y : a0.y, by = lo ? a0.y : xi.y, dyy = lo ? a3.y : -a3.y;
                     T az_ = lo ? xi.z : a0.z, bz = lo ? a0.z : xi.z, dz = lo ? a3.z : -a3.z;
@@ -711,24 +819,21 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32) k_forces(BatchView b)
                 return box_overlap(boxA.plo, boxA.phi, nb.plo, nb.phi, R, ph) ||
                        box_overlap(boxA.plo, boxA.phi, nb.slo, nb.shi, 0.f, ph);
             },
-            [&](int B) {
-                const int stB = b.leaf_start[B], nB = b.leaf_start[B + 1] - stB;
-                if (nbuf + nB > C::CH) flush();
-                T Dx, Dy, Dz;
-                leaf_shift<T>(b, leaf, B, ph, Dx, Dy, Dz);
-                if (lane < nB) {
-                    c0[nbuf + lane] = gph[stB + lane];
-                    c1[nbuf + lane] = gvc[stB + lane];
-                    c2[nbuf + lane] = gth[stB + lane];
-                    V d;
-                    d.x = Dx;
-                    d.y = Dy;
-                    d.z = Dz;
-                    d.w = bits_as_t(stB + lane, T(0));
-                    c3[nbuf + lane] = d;
-                }
-                __syncwarp();
-                nbuf += nB;
+            [&](unsigned mask, int first) {
+                stage_leaves<T, C::CH>(
+                    b, leaf, mask, first, ph, nbuf, sc,
+                    [&](int slot, int j, T dx, T dyy, T dz) {
+                        c0[slot] = gph[j];
+                        c1[slot] = gvc[j];
+                        c2[slot] = gth[j];
+                        V d;
+                        d.x = dx;
+                        d.y = dyy;
+                        d.z = dz;
+                        d.w = bits_as_t(j, T(0));
+                        c3[slot] = d;
+                    },
+                    flush);
             });
         flush();
         // combine the lanes of each particle; FP64 for the compensated sums
@@ -755,7 +860,7 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32) k_forces(BatchView b)
                 atomicOr(&ps.diag->status, ST_NONFINITE);
         }
         double dmin = warp_min(dti);
-        long long tp = warp_sum(pairs), tt = warp_sum(tested);
+        long long tp = warp_sum((long long)pairs), tt = warp_sum((long long)tested);
         if (lane == 0) {
             if (dmin < INFINITY)
                 atomicMin(&ps.diag->dt_min_bits, (unsigned long long)__double_as_longlong(dmin));

@@ -11,7 +11,7 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libsph.so")
+LIB_PATH = os.environ.get("SPH_LIB_PATH") or os.path.join(HERE, "libsph.so")
 
 OK, EINVAL, EBOX, ENOCONV, ENONFINITE, ETIMEOUT, ETOOBIG, EBUSY, EAGAIN, ECUDA, ENOSPACE = (
     0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10)
