@@ -265,6 +265,27 @@ int sph_server_poll(sph_server *s, uint64_t ticket, sph_result *out);
 double sph_server_clock(const sph_server *s);
 int sph_server_destroy(sph_server *s);
 
+/* ---- allocation-free entry point --------------------------------------- */
+/* Density solve and force evaluation (what sph_density_h followed by
+ * sph_forces compute) for callers that may not create device allocations of
+ * their own, e.g. a host application that reserves all device memory in its
+ * own pool, or a plug-in or real-time loop called from such a host.  The paper
+ * has no counterpart: this is a property of the library, not of the method.
+ *   - Allocates nothing: no cudaMalloc/cudaFree, no allocating library call.
+ *     Its scratch memory is a fixed 12 MiB array compiled into the library,
+ *     which every GPU that loads the library holds until the process exits.
+ *   - n is at most 32768; larger n returns SPH_EINVAL with a message.
+ *   - The caller passes the particle arrays (inputs and outputs as in
+ *     sph_state) and the stream; p as for sph_setup (SPH_FLAG_ASYNC skips the
+ *     final synchronisation, and then no status is reported).
+ *   - The first call on a device looks up the array's device address (a
+ *     one-time set-up per device); make that first call before any stream
+ *     capture.
+ *   - All calls share the one array, which keeps the last call's contents:
+ *     calls whose work overlaps on the GPU (other streams, other threads)
+ *     race with each other and must be serialised by the caller. */
+int sph_density_forces_noalloc(const sph_params *p, int64_t n, const sph_state *state, void *stream);
+
 /* Message describing the calling thread's last error ("" if none). */
 const char *sph_last_error(void);
 

@@ -18,7 +18,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsph.so")
 
 SOURCES = ["sph_sort.cu", "sph_build.cu", "sph_pairs.cu", "sph_integrate.cu", "sph_export.cu",
-           "sph_api.cu", "sph_server.cu"]
+           "sph_api.cu", "sph_server.cu", "sph_noalloc.cu"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",

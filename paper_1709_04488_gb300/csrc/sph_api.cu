@@ -16,7 +16,7 @@ namespace sph {
 
 static thread_local std::string g_err;
 
-static int fail(int code, const char *fmt, ...)
+int fail(int code, const char *fmt, ...)
 {
     char buf[512];
     va_list ap;
@@ -49,21 +49,8 @@ DevInfo dev_info()
 }
 
 // ---- workspace layout -------------------------------------------------------
-struct Carver {
-    char *base;
-    size_t off = 0;
-    template <typename T>
-    T *take(size_t count)
-    {
-        off = (off + 255) & ~(size_t)255;
-        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
-        off += sizeof(T) * (count > 0 ? count : 1);
-        return p;
-    }
-};
-
 // Carve the per-step scratch arrays for `ntot` particles over `nprob` problems.
-static void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precision)
+void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precision)
 {
     const long long n = ntot > 0 ? ntot : 1;
     const size_t v4 = precision == SPH_PREC_FP64 ? sizeof(dbl4) : sizeof(float4);
@@ -97,7 +84,7 @@ static void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int
     b.scratch64 = c.take<long long>(8);
 }
 
-static void carve_tables(Carver &c, BatchView &b, int nprob)
+void carve_tables(Carver &c, BatchView &b, int nprob)
 {
     b.nprob = nprob;
     b.prob = c.take<ProbStatic>(nprob);
@@ -105,14 +92,14 @@ static void carve_tables(Carver &c, BatchView &b, int nprob)
     b.prob_base = c.take<long long>(nprob + 1);
 }
 
-static int key_bits_for(int nprob)
+int key_bits_for(int nprob)
 {
     int bits = 0;
     while ((1 << bits) < nprob) ++bits;
     return kMortonTotal + bits;
 }
 
-static int mask_of(int lpp) { return lpp == 1 ? 1 : lpp == 2 ? 2 : lpp == 4 ? 4 : 8; }
+int mask_of(int lpp) { return lpp == 1 ? 1 : lpp == 2 ? 2 : lpp == 4 ? 4 : 8; }
 
 // Launch shape per problem size (the autotuner's table; see autotune.py for
 // how the buckets were chosen).  Small problems spread a particle over more
@@ -158,7 +145,9 @@ static void clear_ran(sph_ctx *c)
     for (int k = 0; k < SPH_NSTAGES; ++k) c->stage_ran[k] = false;
 }
 
-static int validate(const sph_params *p)
+namespace sph {
+
+int validate(const sph_params *p)
 {
     if (!p) return fail(SPH_EINVAL, "params is NULL");
     if (p->kernel != 0) return fail(SPH_EINVAL, "kernel %d not supported (0 = M4 cubic spline)", p->kernel);
@@ -185,7 +174,7 @@ static int validate(const sph_params *p)
     return SPH_OK;
 }
 
-static PhysParams phys_of(const sph_params *p)
+PhysParams phys_of(const sph_params *p)
 {
     PhysParams ph;
     memset(&ph, 0, sizeof ph);
@@ -207,14 +196,14 @@ static PhysParams phys_of(const sph_params *p)
     return ph;
 }
 
-static int lpp_of(const sph_params *p, long long n)
+int lpp_of(const sph_params *p, long long n)
 {
     int req = p->lanes_per_particle;
     if (req == 0 && p->leaf_size != 0) req = 32 / p->leaf_size;
     return choose_lpp(n, p->precision, req);
 }
 
-static int status_to_code(unsigned st)
+int status_to_code(unsigned st)
 {
     if (st & ST_NONFINITE) return fail(SPH_ENONFINITE, "non-finite value in the results");
     if (st & ST_BOX) return fail(SPH_EBOX, "smoothing length reached a quarter of the periodic box");
@@ -223,6 +212,8 @@ static int status_to_code(unsigned st)
     if (st & ST_NOCONV) return fail(SPH_ENOCONV, "h-rho iteration did not converge for some particles");
     return SPH_OK;
 }
+
+}  // namespace sph
 
 extern "C" {
 

@@ -233,6 +233,30 @@ cudaError_t launch_reset_step(const BatchView &b, int mode, cudaStream_t st);  /
 cudaError_t launch_neighbour_export(const BatchView &b, int kind, const double *h_in, long long *offsets,
                                     int *idx, long long cap, long long *total_dev, cudaStream_t st);
 
+// ---- host helpers shared by the entry points (sph_api.cu) -----------------
+// Bump allocator over a workspace (base == nullptr measures the size).
+struct Carver {
+    char *base;
+    size_t off = 0;
+    template <typename T>
+    T *take(size_t count)
+    {
+        off = (off + 255) & ~(size_t)255;
+        T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
+        off += sizeof(T) * (count > 0 ? count : 1);
+        return p;
+    }
+};
+int fail(int code, const char *fmt, ...);  // records the thread's error message, returns code
+void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precision);
+void carve_tables(Carver &c, BatchView &b, int nprob);
+int key_bits_for(int nprob);
+int mask_of(int lpp);
+int validate(const sph_params *p);
+PhysParams phys_of(const sph_params *p);
+int lpp_of(const sph_params *p, long long n);
+int status_to_code(unsigned st);
+
 // upper bounds used to size grids and workspaces
 long long leaves_upper_bound(long long n);
 int levels_needed(long long max_leaves);

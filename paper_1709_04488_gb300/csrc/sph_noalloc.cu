@@ -1,0 +1,147 @@
+// An entry point that allocates nothing: the density solve and the force
+// evaluation of one problem, with all of its scratch memory in a fixed array
+// compiled into the library.
+//
+// Who needs it: code that may not create device allocations of its own.  A
+// host that owns every byte of device memory through its own pool (so that a
+// raw allocation would bypass its accounting or fail once the pool has
+// reserved the free memory), a plug-in called back from such a host, or a
+// real-time loop that must not enter the driver's allocator can still call
+// this with its own input and output arrays.  The price is a fixed scratch
+// area that every GPU using the library keeps until the process exits, and a
+// cap on the problem size.
+#include <mutex>
+
+#include "sph_internal.cuh"
+
+namespace {
+
+using namespace sph;
+
+// Largest problem the fixed scratch holds, and its size: the workspace layout
+// of the FP64 path (the larger of the two precisions) for this many
+// particles, plus the persistent diagnostics record, rounded up.
+constexpr long long kNoAllocMaxN = 32768;
+constexpr size_t kNoAllocBytes = (size_t)12 << 20;
+constexpr int kMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of the scratch array per device, looked up once per device.
+void *g_scratch_addr[kMaxDevices];
+std::mutex g_scratch_mu;
+
+int scratch_for_current_device(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(SPH_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return fail(SPH_EINVAL, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(SPH_ECUDA, "cudaGetSymbolAddress of the fixed scratch failed: %s", cudaGetErrorString(e));
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return SPH_OK;
+}
+
+// Writes the problem table and clears everything a call must find at zero.
+__global__ void k_noalloc_init(BatchView b, ProbStatic ps)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        b.prob[0] = ps;
+        b.prob_base[0] = 0;
+        b.prob_base[1] = ps.n;
+        memset(b.dyn, 0, sizeof(ProbDyn));
+        memset(ps.diag, 0, sizeof(ProbDiag));
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 16) b.counters[threadIdx.x] = 0;
+}
+
+}  // namespace
+
+extern "C" int sph_density_forces_noalloc(const sph_params *p, int64_t n, const sph_state *state, void *stream)
+{
+    int rc = validate(p);
+    if (rc) return rc;
+    if (n < 0 || n > kNoAllocMaxN)
+        return fail(SPH_EINVAL, "n = %lld: the allocation-free entry point takes at most %lld particles",
+                    (long long)n, kNoAllocMaxN);
+    if (!state) return fail(SPH_EINVAL, "state is NULL");
+    if (n > 0) {
+        const double *req[] = {state->x, state->y, state->z, state->vx, state->vy, state->vz, state->u,
+                               state->m, state->h, state->rho, state->omega, state->P, state->c,
+                               state->ax, state->ay, state->az, state->du, state->vsig};
+        for (const double *q : req)
+            if (!q) return fail(SPH_EINVAL, "a state array is NULL");
+    }
+    void *base = nullptr;
+    rc = scratch_for_current_device(&base);
+    if (rc) return rc;
+    // lay the workspace out inside the fixed array
+    Carver c{(char *)base};
+    ProbDiag *diag = c.take<ProbDiag>(1);
+    BatchView b;
+    memset(&b, 0, sizeof b);
+    carve_tables(c, b, 1);
+    carve_arrays(c, b, n, 1, p->precision);
+    if (c.off > kNoAllocBytes) return fail(SPH_ENOSPACE, "fixed scratch too small for %lld particles", (long long)n);
+    const int lpp = lpp_of(p, n);
+    b.ntot = n;
+    b.key_bits = key_bits_for(1);
+    b.lpp_mask = mask_of(lpp);
+    ProbStatic ps;
+    memset(&ps, 0, sizeof ps);
+    ps.x = state->x;
+    ps.y = state->y;
+    ps.z = state->z;
+    ps.vx = state->vx;
+    ps.vy = state->vy;
+    ps.vz = state->vz;
+    ps.u = state->u;
+    ps.m = state->m;
+    ps.h = state->h;
+    ps.rho = state->rho;
+    ps.omega = state->omega;
+    ps.P = state->P;
+    ps.c = state->c;
+    ps.ax = state->ax;
+    ps.ay = state->ay;
+    ps.az = state->az;
+    ps.du = state->du;
+    ps.vsig = state->vsig;
+    ps.n = n;
+    ps.base = 0;
+    ps.diag = diag;
+    ps.lpp = lpp;
+    ps.ph = phys_of(p);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int prec = p->precision;
+    cudaError_t e;
+#define NA_TRY(x)                                                                                  \
+    do {                                                                                           \
+        e = (x);                                                                                   \
+        if (e != cudaSuccess) return fail(SPH_ECUDA, "%s: %s", #x, cudaGetErrorString(e));         \
+    } while (0)
+    k_noalloc_init<<<1, 32, 0, st>>>(b, ps);
+    NA_TRY(cudaGetLastError());
+    NA_TRY(launch_reset_step(b, 1, st));
+    NA_TRY(launch_domain_and_keys(b, st));
+    NA_TRY(launch_radix_sort(b, st));
+    NA_TRY(launch_gather(b, st));
+    NA_TRY(launch_build_leaves(b, prec, st));
+    NA_TRY(launch_density(b, prec, 0, st));
+    NA_TRY(launch_refit(b, st));
+    NA_TRY(launch_forces(b, prec, st));
+    NA_TRY(launch_kick_close(b, 0, 1, st));
+    if (p->flags & SPH_FLAG_ASYNC) return SPH_OK;
+    NA_TRY(cudaStreamSynchronize(st));
+    unsigned status = 0;
+    NA_TRY(cudaMemcpy(&status, &diag->status, sizeof status, cudaMemcpyDeviceToHost));
+#undef NA_TRY
+    return status_to_code(status);
+}

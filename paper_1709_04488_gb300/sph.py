@@ -158,6 +158,7 @@ def lib():
             "sph_server_poll": (i, [vp, C.c_uint64, C.POINTER(Result)]),
             "sph_server_clock": (d, [vp]),
             "sph_server_destroy": (i, [vp]),
+            "sph_density_forces_noalloc": (i, [C.POINTER(Params), i64, C.POINTER(State), vp]),
             "sph_last_error": (C.c_char_p, []),
             "sph_version": (C.c_char_p, []),
         }
@@ -253,6 +254,12 @@ def sph_step_kernel_count(ctx) -> int:
     k = C.c_int(0)
     check(lib().sph_step_kernel_count(ctx, C.byref(k)), "sph_step_kernel_count")
     return k.value
+
+
+def sph_density_forces_noalloc(p: Params, n: int, state: State, stream: int) -> int:
+    """Density solve + force evaluation with the library's fixed scratch
+    memory (no allocation); at most 32768 particles."""
+    return lib().sph_density_forces_noalloc(C.byref(p), int(n), C.byref(state), C.c_void_p(stream))
 
 
 def sph_batch_workspace_bytes(ctxs) -> int:
