@@ -43,6 +43,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--serve", type=int, default=150,
+                    help="requests in the serving measurement (0 skips it)")
+    ap.add_argument("--serve-load", type=float, nargs="*", default=[0.7],
+                    help="offered loads as fractions of the saturated batched throughput")
     return ap.parse_args()
 
 
@@ -197,6 +201,32 @@ def time_steps(S, prob, stream, torch, K, flush, stage=False):
     return ms, stages, dens_pairs, force_pairs
 
 
+def serving(nreq, loads, pool_bytes):
+    """Serving configuration: requests of 1e3..2e5 particles (lattice, Sod or
+    Sedov, seeded), 10 steps each.  First all requests arrive at t = 0 (the
+    saturated batched throughput), then Poisson arrivals at the given loads
+    (wall clock); latency = completion - arrival."""
+    from paper_1709_04488_gb300 import serve
+    reqs = serve.make_requests(nreq, seed=5, n_min=1e3, n_max=2e5, nsteps=10)
+    work = sum(len(r["arrays"]["x"]) * r["nsteps"] for r in reqs)
+    recs, span = serve.run_stream(reqs, np.zeros(nreq), pool_bytes)
+    assert all(r["status"] == 0 for r in recs), [r["status"] for r in recs]
+    sat = work / span
+    out = {"requests": nreq, "particle_steps": work, "saturated_updates_per_s": sat,
+           "saturated_makespan_s": span, "loads": []}
+    mean_work = work / nreq
+    for load in loads:
+        rate = load * sat / mean_work
+        arr = serve.poisson_arrivals(nreq, rate, seed=6)
+        recs, span = serve.run_stream(reqs, arr, pool_bytes)
+        assert all(r["status"] == 0 for r in recs)
+        lat = np.array([r["latency"] for r in recs])
+        out["loads"].append({"load": load, "arrival_rate_per_s": rate, "p50_s": float(np.percentile(lat, 50)),
+                             "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
+                             "updates_per_s": work / span, "makespan_s": span})
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -300,6 +330,10 @@ def run_ours(args):
 
     diag = prob.diagnostics()
     prob.close()
+    serve_res = None
+    if args.serve > 0 and rank == 0:
+        free, _ = torch.cuda.mem_get_info(dev)
+        serve_res = serving(args.serve, args.serve_load, int(0.8 * free))
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -318,7 +352,7 @@ def run_ours(args):
                    "l2": "flushed (256 MiB write) between timed steps", "graph": "one CUDA graph per step",
                    "lanes_per_particle": int(prob.params.lanes_per_particle) or "auto"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": kernels_per_step * args.steps,
-        "clocks": clocks, "fp64_gpu": fp64,
+        "clocks": clocks, "fp64_gpu": fp64, "serving": serve_res,
         "step_diag": {"nr_iterations": diag.nr_iterations, "nr_max": diag.nr_max, "fallback": diag.fallback,
                       "leaves": diag.leaves, "ngb_mean": diag.ngb_mean, "candidates": diag.candidates},
     }

@@ -107,6 +107,10 @@ def lib():
         L.orc_neighbours.argtypes = [PP, C.c_int64, SP, C.c_int, C.POINTER(C.c_int64), _IP, C.c_int64]
         L.orc_density_at_h.restype = C.c_int
         L.orc_density_at_h.argtypes = [PP, C.c_int64, SP, C.c_int64, C.c_double, _DP, _DP]
+        L.orc_density_subset.restype = C.c_int
+        L.orc_density_subset.argtypes = [PP, C.c_int64, SP, C.c_int64, C.POINTER(C.c_int64)]
+        L.orc_forces_subset.restype = C.c_int
+        L.orc_forces_subset.argtypes = [PP, C.c_int64, SP, C.c_int64, C.POINTER(C.c_int64), C.c_double]
         L.orc_num_threads.restype = C.c_int
         L.orc_set_num_threads.argtypes = [C.c_int]
         _lib = L
@@ -190,6 +194,21 @@ def forces(p: Params, s: State) -> int:
 def step(p: Params, s: State, dt: float) -> int:
     """One KDK step (Eqs. LFKDK1/2) with the predictor reading of the paper."""
     return lib().orc_step(C.byref(p._c()), s.n, C.byref(s._c()), float(dt))
+
+
+def density_subset(p: Params, s: State, idx) -> int:
+    """Density / h solve for the listed particles only (others untouched)."""
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    return lib().orc_density_subset(C.byref(p._c()), s.n, C.byref(s._c()), len(idx),
+                                    idx.ctypes.data_as(C.POINTER(C.c_int64)))
+
+
+def forces_subset(p: Params, s: State, idx, hmax: float) -> int:
+    """Forces for the listed particles; their neighbours' h, rho, Omega, P, c
+    must be valid; hmax bounds the h of any particle that can reach them."""
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    return lib().orc_forces_subset(C.byref(p._c()), s.n, C.byref(s._c()), len(idx),
+                                   idx.ctypes.data_as(C.POINTER(C.c_int64)), float(hmax))
 
 
 def cfl_dt(p: Params, s: State) -> float:

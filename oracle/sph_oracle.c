@@ -729,3 +729,122 @@ void orc_set_num_threads(int t)
     (void)t;
 #endif
 }
+
+/*
+ * Density / h solve (Eqs. SPHRHO, HRHO, OMEGA) for the listed particles only,
+ * with the grid prefilter; every other particle is left untouched.  Each
+ * particle's solve depends only on positions and masses, so the results equal
+ * those of orc_density for these particles.
+ */
+int orc_density_subset(const orc_params *p, int64_t n, orc_state *s, int64_t nsub, const int64_t *idx)
+{
+    if (!params_ok(p, n) || nsub < 0) return ORC_EINVAL;
+    if (n == 0 || nsub == 0) return ORC_OK;
+    grid_t g;
+    memset(&g, 0, sizeof g);
+    if (grid_build(&g, p, s, n, 2.0 * median_spacing_guess(p, s, n))) return ORC_ENOMEM;
+    int status = ORC_OK;
+#pragma omp parallel
+    {
+        idlist_t buf = {0, 0, 0};
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t k = 0; k < nsub; ++k) {
+            int64_t i = idx[k];
+            double rho = 0, drho = 0;
+            int32_t nn = 0, it = 0;
+            int rc = solve_h(p, s, n, &g, i, &buf, &s->h[i], &rho, &drho, &nn, &it);
+            s->rho[i] = rho;
+            s->omega[i] = 1.0 + s->h[i] / (3.0 * rho) * drho;
+            eos(p, rho, s->u[i], &s->P[i], &s->c[i]);
+            if (s->nngb) s->nngb[i] = nn;
+            if (s->iters) s->iters[i] = it;
+            if (rc) {
+#pragma omp critical
+                status = rc;
+            }
+        }
+        free(buf.v);
+    }
+    grid_free(&g);
+    return status;
+}
+
+/*
+ * Forces (Eqs. GRADHMOMEQN, GRADHENEQN, MON97ARTVISC, MON97ENERGYDISS, SPH_DT)
+ * for the listed particles only.  h, rho, Omega, P, c must be valid for these
+ * particles and for all their force neighbours.  hmax bounds the smoothing
+ * lengths of the particles that can reach a listed one (the grid query
+ * radius is 2 hmax).
+ */
+int orc_forces_subset(const orc_params *p, int64_t n, orc_state *s, int64_t nsub, const int64_t *idx,
+                      double hmax)
+{
+    if (!params_ok(p, n) || nsub < 0 || !(hmax > 0)) return ORC_EINVAL;
+    if (n == 0 || nsub == 0) return ORC_OK;
+    grid_t g;
+    memset(&g, 0, sizeof g);
+    if (grid_build(&g, p, s, n, 2.0 * median_spacing_guess(p, s, n))) return ORC_ENOMEM;
+    const double alpha = p->alpha_av, beta = p->beta_av, aac = p->alpha_ac;
+    int status = ORC_OK;
+#pragma omp parallel
+    {
+        idlist_t buf = {0, 0, 0};
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t k = 0; k < nsub; ++k) {
+            int64_t i = idx[k];
+            int rc = gather(p, s, n, &g, i, 2.0 * hmax, s->h, &buf);
+            if (rc) {
+#pragma omp critical
+                status = rc;
+                continue;
+            }
+            const double Ai = s->P[i] / (s->omega[i] * s->rho[i] * s->rho[i]);
+            kahan_t ax = {0, 0}, ay = {0, 0}, az = {0, 0}, du = {0, 0};
+            double vsig = 2.0 * s->c[i];
+            int have = 0;
+            for (int64_t q = 0; q < buf.n; ++q) {
+                int64_t j = buf.v[q];
+                if (j == i) continue;
+                sep_t sp = separation(p, s, i, j);
+                double r = sqrt(sp.r2);
+                double rx = sp.dx / r, ry = sp.dy / r, rz = sp.dz / r;
+                double gi = orc_dWdr(r, s->h[i]);
+                double gj = orc_dWdr(r, s->h[j]);
+                double Aj = s->P[j] / (s->omega[j] * s->rho[j] * s->rho[j]);
+                double mj = s->m[j];
+                double fp = -mj * (Ai * gi + Aj * gj);
+                double vxij = s->vx[i] - s->vx[j], vyij = s->vy[i] - s->vy[j], vzij = s->vz[i] - s->vz[j];
+                double vdr = vxij * rx + vyij * ry + vzij * rz;
+                double gbar = 0.5 * (gi + gj);
+                double rhobar = 0.5 * (s->rho[i] + s->rho[j]);
+                double fav = 0.0, duav = 0.0;
+                double vs = s->c[i] + s->c[j] - beta * (vdr < 0 ? vdr : 0.0);
+                if (!have || vs > vsig) vsig = vs;
+                have = 1;
+                if (vdr < 0) {
+                    double mu = vdr;
+                    double vsig_av = s->c[i] + s->c[j] - beta * vdr;
+                    fav = mj / rhobar * alpha * vsig_av * mu * gbar;
+                    duav = -mj / rhobar * 0.5 * alpha * vsig_av * mu * mu * gbar;
+                }
+                double f = fp + fav;
+                kadd(&ax, f * rx);
+                kadd(&ay, f * ry);
+                kadd(&az, f * rz);
+                if (p->eos == 0) {
+                    double dui = Ai * mj * vdr * gi;
+                    double duac = mj / rhobar * aac * fabs(vdr) * (s->u[i] - s->u[j]) * gbar;
+                    kadd(&du, dui + duav + duac);
+                }
+            }
+            s->ax[i] = ax.s;
+            s->ay[i] = ay.s;
+            s->az[i] = az.s;
+            s->du[i] = (p->eos == 0) ? du.s : 0.0;
+            s->vsig[i] = vsig;
+        }
+        free(buf.v);
+    }
+    grid_free(&g);
+    return status;
+}

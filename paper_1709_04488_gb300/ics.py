@@ -2,9 +2,9 @@
 
 This module holds no step of the SPH method itself: it only places particles
 and assigns their masses, velocities and internal energies.  Both the CUDA path
-(through ``bench.py`` and the tests) and the CPU oracle (through the tests) are
-fed from here; it imports nothing from the rest of the package, and nothing in
-the package imports it.
+(through ``bench.py``, the tests and the request-stream driver ``serve.py``) and
+the CPU oracle (through the tests) are fed from here; it imports nothing from
+the rest of the package, and nothing on the compute path imports it.
 
 Every generator returns ``(arrays, params)``: ``arrays`` maps x, y, z, vx, vy,
 vz, u, m, h to float64 NumPy arrays; ``params`` holds the problem's physical

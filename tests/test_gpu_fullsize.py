@@ -1,0 +1,110 @@
+"""Parity at the full sizes of the configurations.
+
+- Sod tube, 36864 particles, the configuration bench.py times, in the same
+  launch configuration: every particle compared with the oracle after the
+  first force evaluation and after 5 steps with the oracle's time-steps.
+- Sedov blast, 100^3 = 1e6 particles, and the turbulent cloud, 8e6 particles:
+  the GPU solves the whole problem; the oracle solves a random sample of
+  particles one by one (its per-particle entry points), after solving the
+  density of every particle that can reach the sample.
+Tolerances as in test_gpu_parity.py."""
+import numpy as np
+import pytest
+
+from paper_1709_04488_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1709_04488_gb300 import build as b
+    b.build()
+    from paper_1709_04488_gb300 import sph
+    return sph
+
+
+def _check(g, r, idx=None):
+    sel = slice(None) if idx is None else idx
+    for f in ("rho", "h", "omega"):
+        err = np.max(np.abs(g[f][sel] / getattr(r, f)[sel] - 1.0))
+        assert err < 1e-5, (f, err)
+    ga = np.stack([g["ax"], g["ay"], g["az"]], 1)[sel]
+    ra = np.stack([r.ax, r.ay, r.az], 1)[sel]
+    arms = np.sqrt(np.mean(np.sum(ra ** 2, 1)))
+    err = np.max(np.linalg.norm(ga - ra, axis=1)) / arms
+    assert err < 1e-4, ("a", err)
+    if np.any(r.du[sel] != 0):
+        err = np.max(np.abs(g["du"][sel] - r.du[sel])) / np.sqrt(np.mean(r.du[sel] ** 2))
+        assert err < 1e-4, ("du", err)
+    assert np.max(np.abs(g["vsig"][sel] / r.vsig[sel] - 1.0)) < 1e-5
+
+
+def test_sod_full_size_every_particle(S, oracle_mod):
+    O = oracle_mod
+    a, p = ics.sod()
+    P = O.Params(**p, use_grid=True)
+    ref = O.State(**a)
+    assert O.density(P, ref) == O.OK and O.forces(P, ref) == O.OK
+    prob = S.Problem(a, S.make_params(S.PREC_MIXED, **p))
+    prob.density_h()
+    prob.forces()
+    _check(prob.numpy(), ref)
+    for _ in range(5):
+        dt = O.cfl_dt(P, ref)
+        assert O.step(P, ref, dt) == O.OK
+        prob.step(dt)
+    g = prob.numpy()
+    _check(g, ref)
+    assert np.max(np.abs(g["x"] - ref.x)) < 1e-9
+
+
+def _sampled(S, O, a, p, nsample, seed):
+    from scipy.spatial import cKDTree
+    prob = S.Problem(a, S.make_params(S.PREC_MIXED, **p))
+    prob.density_h()
+    prob.forces()
+    g = prob.numpy()
+    d = prob.diagnostics()
+    assert d.status == S.OK
+    prob.close()
+    n = len(a["x"])
+    rng = np.random.default_rng(seed)
+    samp = np.sort(rng.choice(n, nsample, replace=False))
+    pos = np.stack([a["x"], a["y"], a["z"]], 1)
+    tree = cKDTree(pos, boxsize=np.array(p["box_len"]) if p["periodic"] else None)
+    P = O.Params(**p, use_grid=True)
+    ref = O.State(**a)
+    assert O.density_subset(P, ref, samp) == O.OK
+    solved = np.zeros(n, bool)
+    solved[samp] = True
+    # every particle within 3 h_i, then within 3 max(local h) of the sample
+    reach = 3.0 * ref.h[samp]
+    for _ in range(3):
+        near = np.unique(np.concatenate(tree.query_ball_point(pos[samp], reach)).astype(np.int64))
+        new = near[~solved[near]]
+        if len(new):
+            assert O.density_subset(P, ref, new) == O.OK
+            solved[new] = True
+        hloc = np.array([ref.h[np.asarray(tree.query_ball_point(pos[i], r), dtype=np.int64)].max()
+                         for i, r in zip(samp, reach)])
+        new_reach = 3.0 * np.maximum(ref.h[samp], hloc)
+        if np.all(new_reach <= reach):
+            break
+        reach = np.maximum(reach, new_reach)
+    hmax = float(np.max(ref.h[solved]))
+    assert O.forces_subset(P, ref, samp, hmax) == O.OK
+    _check(g, ref, samp)
+
+
+def test_sedov_full_size_sampled(S, oracle_mod):
+    a, p = ics.sedov()
+    _sampled(S, oracle_mod, a, p, 300, seed=31)
+
+
+def test_cloud_full_size_sampled(S, oracle_mod):
+    a, p = ics.cloud()
+    _sampled(S, oracle_mod, a, p, 200, seed=41)

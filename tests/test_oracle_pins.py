@@ -417,3 +417,22 @@ def test_conduction_flows_from_hot_to_cold(oracle_mod):
     t0 = t1.copy()
     assert O.forces(P1, t1) == O.OK and O.forces(P0, t0) == O.OK
     assert np.array_equal(t1.du, t0.du)
+
+
+def test_subset_solves_equal_full_solves(oracle_mod):
+    """The per-particle subset entry points (used to check large inputs on
+    samples) give the same bits as the full solves for those particles."""
+    O = oracle_mod
+    a, p = ics.random_cloud(800, seed=19, vel=0.4, u_spread=0.4)
+    P = O.Params(**p)
+    full = O.State(**a)
+    assert O.density(P, full) == O.OK and O.forces(P, full) == O.OK
+    sub = O.State(**a)
+    idx = np.array([3, 77, 400, 799])
+    # density for every particle that can reach the sample, then forces
+    assert O.density_subset(P, sub, np.arange(800)) == O.OK
+    assert O.forces_subset(P, sub, idx, float(np.max(sub.h))) == O.OK
+    for f in ("h", "rho", "omega"):
+        assert np.array_equal(getattr(sub, f), getattr(full, f)), f
+    for f in ("ax", "ay", "az", "du", "vsig"):
+        assert np.array_equal(getattr(sub, f)[idx], getattr(full, f)[idx]), f
