@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--lpp", type=int, default=0, help="lanes per particle (0: autotuned)")
     ap.add_argument("--serve", type=int, default=150,
                     help="requests in the serving measurement (0 skips it)")
     ap.add_argument("--serve-load", type=float, nargs="*", default=[0.7],
@@ -242,7 +243,7 @@ def run_ours(args):
     stream = torch.cuda.Stream(dev)
     a, p = workload()
     n = len(a["x"])
-    prm = S.make_params(S.PREC_MIXED, **p, flags=S.FLAG_ASYNC | S.FLAG_TIMING)
+    prm = S.make_params(S.PREC_MIXED, **p, flags=S.FLAG_ASYNC | S.FLAG_TIMING, lanes_per_particle=args.lpp)
     with torch.cuda.stream(stream):
         prob = S.Problem(a, prm, device=dev, stream=stream)
         S.check(S.sph_density_h(prob.ctx), "sph_density_h")

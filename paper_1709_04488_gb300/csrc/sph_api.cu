@@ -55,11 +55,12 @@ void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precis
     const long long n = ntot > 0 ? ntot : 1;
     const size_t v4 = precision == SPH_PREC_FP64 ? sizeof(dbl4) : sizeof(float4);
     const long long nblk = (n + 2047) / 2048;
+    const long long passes = (key_bits_for(nprob) + 7) / 8;
     b.keys[0] = c.take<unsigned long long>(n);
     b.keys[1] = c.take<unsigned long long>(n);
     b.vals[0] = c.take<unsigned>(n);
     b.vals[1] = c.take<unsigned>(n);
-    b.hist = c.take<unsigned>(256 * nblk);
+    b.hist = c.take<unsigned>(passes * 256 + 8 + passes * nblk * 256);
     b.scan_aux = c.take<unsigned>(nblk + 1);
     b.perm = c.take<int>(n);
     double **sd[] = {&b.sx, &b.sy, &b.sz, &b.sh, &b.sm, &b.srho, &b.somega, &b.sP, &b.sc,
@@ -80,7 +81,7 @@ void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precis
         cap = cap / kBranch + nprob + 1;
     }
     b.fallback_list = c.take<int>(n);
-    b.counters = c.take<int>(16);
+    b.counters = c.take<int>(32);
     b.scratch64 = c.take<long long>(8);
 }
 
@@ -100,6 +101,8 @@ int key_bits_for(int nprob)
 }
 
 int mask_of(int lpp) { return lpp == 1 ? 1 : lpp == 2 ? 2 : lpp == 4 ? 4 : 8; }
+
+int dens_class_bit(int lpp, int uniform_m) { return mask_of(lpp) << (uniform_m ? 4 : 0); }
 
 // Launch shape per problem size (the autotuner's table; see autotune.py for
 // how the buckets were chosen).  Small problems spread a particle over more
@@ -304,6 +307,7 @@ int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *st
     c->bv.ntot = n;
     c->bv.key_bits = key_bits_for(1);
     c->bv.lpp_mask = mask_of(c->lpp);
+    c->bv.any_isolated = p->periodic ? 0 : 1;
     ProbStatic &ps = c->host_ps;
     memset(&ps, 0, sizeof ps);
     ps.x = state->x;
@@ -329,6 +333,23 @@ int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *st
     ps.diag = c->diag;
     ps.lpp = c->lpp;
     ps.ph = phys_of(p);
+    // equal masses (the usual SPH set-up; masses never change) let the
+    // density lists keep distances only
+    if (n > 0) {
+        std::vector<double> mh((size_t)n);
+        cudaError_t me = cudaMemcpyAsync(mh.data(), state->m, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost,
+                                         c->stream);
+        if (me == cudaSuccess) me = cudaStreamSynchronize(c->stream);
+        if (me != cudaSuccess) {
+            delete c;
+            return fail(SPH_ECUDA, "reading the masses failed: %s", cudaGetErrorString(me));
+        }
+        bool uni = true;
+        for (long long k = 1; k < n && uni; ++k) uni = mh[(size_t)k] == mh[0];
+        ps.uniform_m = uni ? 1 : 0;
+        ps.m_uniform = mh[0];
+    }
+    c->bv.dens_mask = dens_class_bit(c->lpp, ps.uniform_m);
     ProbDiag d0;
     memset(&d0, 0, sizeof d0);
     d0.dt_next = 0.0;
@@ -337,7 +358,7 @@ int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *st
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->diag, &d0, sizeof d0, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->bv.prob_base, bases, sizeof bases, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->bv.dyn, 0, sizeof(ProbDyn), c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->bv.counters, 0, 16 * sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->bv.counters, 0, 32 * sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         delete c;
@@ -681,13 +702,15 @@ int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, 
     long long ntot = 0;
     std::vector<ProbStatic> tab(nctx);
     std::vector<long long> bases(nctx + 1);
-    int mask = 0;
+    int mask = 0, dmask = 0, b_any_isolated = 0;
     for (int k = 0; k < nctx; ++k) {
         tab[k] = ctxs[k]->host_ps;
         tab[k].base = ntot;
         bases[k] = ntot;
         ntot += ctxs[k]->n;
         mask |= mask_of(tab[k].lpp);
+        dmask |= dens_class_bit(tab[k].lpp, tab[k].uniform_m);
+        if (!tab[k].ph.periodic) b_any_isolated = 1;
     }
     bases[nctx] = ntot;
     Carver cv{(char *)workspace};
@@ -698,10 +721,12 @@ int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, 
     b.ntot = ntot;
     b.key_bits = key_bits_for(nctx);
     b.lpp_mask = mask;
+    b.dens_mask = dmask;
+    b.any_isolated = b_any_isolated;
     CU(cudaMemcpyAsync(b.prob, tab.data(), sizeof(ProbStatic) * nctx, cudaMemcpyHostToDevice, st));
     CU(cudaMemcpyAsync(b.prob_base, bases.data(), sizeof(long long) * (nctx + 1), cudaMemcpyHostToDevice, st));
     CU(cudaMemsetAsync(b.dyn, 0, sizeof(ProbDyn) * nctx, st));
-    CU(cudaMemsetAsync(b.counters, 0, 16 * sizeof(int), st));
+    CU(cudaMemsetAsync(b.counters, 0, 32 * sizeof(int), st));
     for (int s = 0; s < nsteps; ++s) {
         rc = enqueue_step(b, prec, -1.0, st, Marks());
         if (rc) return rc;

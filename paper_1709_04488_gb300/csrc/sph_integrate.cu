@@ -21,6 +21,7 @@ __global__ void k_reset_step(BatchView b, int mode)
     ProbDiag *d = b.prob[p].diag;
     d->dt_min_bits = 0x7ff0000000000000ull;  // +inf
     d->force_pairs = 0;
+    if (p == 0) b.counters[15] = 0;  // sort look-back timeout flag
     if (mode == 2) return;
     d->mass = 0;
     for (int a = 0; a < 3; ++a) {
@@ -154,6 +155,7 @@ __global__ void k_finish(BatchView b, int advanced, int forces_ran)
     if (p >= b.nprob) return;
     ProbDiag *d = b.prob[p].diag;
     if (forces_ran) d->dt_next = __longlong_as_double((long long)d->dt_min_bits);
+    if (b.counters[15]) atomicOr(&d->status, ST_TIMEOUT);
     if (advanced) {
         d->time += d->dt_cur;
         d->steps += 1;

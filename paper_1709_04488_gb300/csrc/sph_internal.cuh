@@ -65,7 +65,8 @@ struct ProbStatic {
     long long base;  // offset of this problem in the batch-global particle index space
     ProbDiag *diag;
     int lpp;         // lanes per particle in the pair kernels (leaf size = 32 / lpp)
-    int pad_;
+    int uniform_m;   // all masses equal (m_uniform): neighbour lists keep distances only
+    double m_uniform;
     PhysParams ph;
 };
 
@@ -109,16 +110,18 @@ struct __align__(16) NodeBox {
 struct BatchView {
     int nprob;
     int lpp_mask;                // bit k set: some problem uses 2^k lanes per particle
+    int dens_mask;               // bit (k + 4 u): density class (2^k lanes, uniform masses u)
     long long ntot;              // particles over all problems
     int max_leaves;              // capacity of the leaf arrays
     int key_bits;                // bits the radix sort must order
+    int any_isolated;            // some problem is isolated (needs a bounding box)
     ProbStatic *prob;            // [nprob]
     ProbDyn *dyn;                // [nprob]
     long long *prob_base;        // [nprob + 1] base offsets (for searches)
     // sort
     unsigned long long *keys[2];
     unsigned *vals[2];
-    unsigned *hist;              // 256 * sort blocks
+    unsigned *hist;              // sort: digit histograms, tile counters, look-back status
     unsigned *scan_aux;
     int *perm;                   // sorted position -> batch-global original index
     // sorted FP64 copies
@@ -139,7 +142,8 @@ struct BatchView {
     NodeBox *nodes[kMaxLevels + 1];  // level 0 = leaves
     int node_cap[kMaxLevels + 1];
     int *fallback_list;          // [ntot] sorted indices needing the slow path
-    int *counters;               // [16] work counters / list lengths
+    int *counters;               // [32]: 0 leaves, 1..7 nodes per level, 8 slow-path count,
+                                 // 15 sort timeout, 16.. work counters per kernel class
     long long *scratch64;        // [8]
 };
 
@@ -252,6 +256,7 @@ void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precis
 void carve_tables(Carver &c, BatchView &b, int nprob);
 int key_bits_for(int nprob);
 int mask_of(int lpp);
+int dens_class_bit(int lpp, int uniform_m);
 int validate(const sph_params *p);
 PhysParams phys_of(const sph_params *p);
 int lpp_of(const sph_params *p, long long n);

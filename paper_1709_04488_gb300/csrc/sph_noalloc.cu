@@ -59,7 +59,7 @@ __global__ void k_noalloc_init(BatchView b, ProbStatic ps)
         memset(b.dyn, 0, sizeof(ProbDyn));
         memset(ps.diag, 0, sizeof(ProbDiag));
     }
-    if (blockIdx.x == 0 && threadIdx.x < 16) b.counters[threadIdx.x] = 0;
+    if (blockIdx.x == 0) b.counters[threadIdx.x] = 0;  // 32 counters
 }
 
 }  // namespace
@@ -94,6 +94,8 @@ extern "C" int sph_density_forces_noalloc(const sph_params *p, int64_t n, const 
     b.ntot = n;
     b.key_bits = key_bits_for(1);
     b.lpp_mask = mask_of(lpp);
+    b.dens_mask = dens_class_bit(lpp, 0);  // masses are not inspected here: distance-and-mass lists
+    b.any_isolated = p->periodic ? 0 : 1;
     ProbStatic ps;
     memset(&ps, 0, sizeof ps);
     ps.x = state->x;

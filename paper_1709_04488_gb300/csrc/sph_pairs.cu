@@ -309,14 +309,15 @@ __device__ __forceinline__ bool nr_update(T &h, T &lo, T &hi, T rho, T drho, T m
     return conv;
 }
 
-template <typename T, int LPP>
+template <typename T, int LPP, bool UM>
 struct DCfg {
     using V = typename Vec4<T>::type;
     static constexpr int LCAP = 96 / LPP + 8;
     static constexpr int CH = SPH_DENS_CH;
-    static constexpr int WPB = LPP == 1 ? 2 : 4;
+    static constexpr int WPB = 4;
+    static constexpr int LW = UM ? 1 : 2;  // list words per entry: r (and m_j unless masses are equal)
     static constexpr size_t scratch = (sizeof(StageScratch<T, CH>) + 31) & ~(size_t)31;
-    static constexpr size_t per_warp = CH * sizeof(V) + (size_t)LCAP * 32 * 2 * sizeof(T) + scratch;
+    static constexpr size_t per_warp = CH * sizeof(V) + (size_t)LCAP * 32 * LW * sizeof(T) + scratch;
     static constexpr size_t smem = WPB * per_warp;
 };
 
@@ -376,30 +377,31 @@ __device__ __forceinline__ void density_epilogue(const BatchView &b, const ProbS
         atomicOr(&ps.diag->status, ST_NONFINITE);
 }
 
-template <typename T, int LPP>
-__global__ void __launch_bounds__(DCfg<T, LPP>::WPB * 32, SPH_DENS_MINB) k_density(BatchView b, int use_pred)
+template <typename T, int LPP, bool UM>
+__global__ void __launch_bounds__(DCfg<T, LPP, UM>::WPB * 32, SPH_DENS_MINB) k_density(BatchView b, int use_pred)
 {
-    using C = DCfg<T, LPP>;
+    using C = DCfg<T, LPP, UM>;
     using V = typename C::V;
     extern __shared__ __align__(32) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     unsigned char *mine = smem + wib * C::per_warp;
     V *cand = reinterpret_cast<V *>(mine);
     T *lr = reinterpret_cast<T *>(mine + C::CH * sizeof(V));
-    T *lm = lr + C::LCAP * 32;
-    StageScratch<T, C::CH> &sc = *reinterpret_cast<StageScratch<T, C::CH> *>(lm + C::LCAP * 32);
+    T *lm = lr + C::LCAP * 32;  // used only when masses differ
+    StageScratch<T, C::CH> &sc = *reinterpret_cast<StageScratch<T, C::CH> *>(lr + C::LCAP * 32 * C::LW);
     const int pp = lane / LPP, sub = lane % LPP;
     const int nleaf = b.counters[0];
     const V *pm = (const V *)b.pm;
 
     for (;;) {
         int leaf = 0;
-        if (lane == 0) leaf = atomicAdd(&b.counters[11 + lpp_log2(LPP)], 1);
+        if (lane == 0) leaf = atomicAdd(&b.counters[16 + lpp_log2(LPP) + (UM ? 4 : 0)], 1);
         leaf = __shfl_sync(FULL, leaf, 0);
         if (leaf >= nleaf) break;
         const int p = b.leaf_pid[leaf];
         const ProbStatic &ps = b.prob[p];
-        if (ps.lpp != LPP) continue;  // leaf of a problem served by another launch
+        if (ps.lpp != LPP || (ps.uniform_m != 0) != UM) continue;  // served by another launch
+        const T mu_all = (T)ps.m_uniform;
         const int st = b.leaf_start[leaf], nA = b.leaf_start[leaf + 1] - st;
         const ProbDyn &dy = b.dyn[p];
         const PhysParams &ph = ps.ph;
@@ -414,7 +416,7 @@ __global__ void __launch_bounds__(DCfg<T, LPP>::WPB * 32, SPH_DENS_MINB) k_densi
         double Lmin = ph.periodic ? fmin(ph.box_len[0], fmin(ph.box_len[1], ph.box_len[2])) : INFINITY;
         T h = active ? (T)b.sh[s] : T(1);
         if (active && !(h > T(0))) {
-            double ext = 1.0 / dy.dom_inv;
+            double ext = ph.periodic ? fmax(ph.box_len[0], fmax(ph.box_len[1], ph.box_len[2])) : 1.0 / dy.dom_inv;
             h = (T)(ph.eta * cbrt(ext * ext * ext / (double)(ps.n > 0 ? ps.n : 1)));
         }
         T lo = T(0), hi = tinf<T>();
@@ -437,7 +439,7 @@ __global__ void __launch_bounds__(DCfg<T, LPP>::WPB * 32, SPH_DENS_MINB) k_densi
                     if (active && !fail && r2 < R2) {
                         if (cnt < C::LCAP) {
                             lr[cnt * 32 + lane] = sqrt(r2);
-                            lm[cnt * 32 + lane] = c.w;
+                            if (!UM) lm[cnt * 32 + lane] = c.w;
                             ++cnt;
                         } else {
                             ovf = true;
@@ -474,7 +476,7 @@ __global__ void __launch_bounds__(DCfg<T, LPP>::WPB * 32, SPH_DENS_MINB) k_densi
                     const T hinv = T(1) / h;
                     for (int e = 0; e < cnt; ++e) {
                         T q = lr[e * 32 + lane] * hinv;
-                        T mj = lm[e * 32 + lane];
+                        T mj = UM ? mu_all : lm[e * 32 + lane];
                         T f, df;
                         m4(q, f, df);
                         S0 += mj * f;
@@ -520,7 +522,7 @@ __global__ void __launch_bounds__(DCfg<T, LPP>::WPB * 32, SPH_DENS_MINB) k_densi
             const T hinv = T(1) / h;
             for (int e = 0; e < cnt; ++e) {
                 T q = lr[e * 32 + lane] * hinv;
-                T mj = lm[e * 32 + lane];
+                T mj = UM ? mu_all : lm[e * 32 + lane];
                 T f, df;
                 m4(q, f, df);
                 S0 += mj * f;
@@ -567,13 +569,22 @@ __global__ void __launch_bounds__(DCfg<T, LPP>::WPB * 32, SPH_DENS_MINB) k_densi
     }
 }
 
-// Slow path: one warp per particle, the tree walked again in every
-// Newton-Raphson iteration, all lanes summing candidates directly.
+// Slow path: one warp per particle for the particles whose per-lane lists in
+// k_density overflowed or outgrew their radius.  The warp gathers the
+// particle's neighbours (within 2 h x 1.1) into a list spread over its 32
+// lanes (up to kFbPerLane each) and iterates on it, walking the tree again
+// only when h outgrows the list; if even that list overflows, every
+// iteration walks the tree and sums the candidates directly.
+constexpr int kFbPerLane = 16;
+constexpr double kFbMargin = 1.1;
+
 template <typename T>
 __global__ void __launch_bounds__(128) k_density_fallback(BatchView b, int use_pred)
 {
     using V = typename Vec4<T>::type;
-    const int lane = threadIdx.x & 31;
+    __shared__ T fr[4][kFbPerLane][32];
+    __shared__ T fm[4][kFbPerLane][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int nf = b.counters[8];
     const V *pm = (const V *)b.pm;
     int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
@@ -596,40 +607,79 @@ __global__ void __launch_bounds__(128) k_density_fallback(BatchView b, int use_p
         long long pairs = 0;
         T S0, S1;
         int nn;
+        // neighbour candidates of the particle within radius R, one visited leaf at a time
+        auto visit_all = [&](float Rq, auto &&fn) {
+            walk(
+                b, dy, [&](const NodeBox &nb) { return box_overlap(boxA.plo, boxA.phi, nb.plo, nb.phi, Rq, ph); },
+                [&](unsigned mask, int first) {
+                    for (unsigned mm = mask; mm; mm &= mm - 1u) {
+                        const int B = first + __ffs(mm) - 1;
+                        const int stB = b.leaf_start[B], nB = b.leaf_start[B + 1] - stB;
+                        T Dx, Dy, Dz;
+                        leaf_shift<T>(b, leaf, B, ph, Dx, Dy, Dz);
+                        if (lane < nB) {
+                            V q = pm[stB + lane];
+                            T dx = pi.x - (q.x + Dx), dyy = pi.y - (q.y + Dy), dz = pi.z - (q.z + Dz);
+                            fn(dx * dx + dyy * dyy + dz * dz, q.w);
+                        }
+                    }
+                });
+        };
+        bool direct = false;
+        T hs = T(0);
+        int cnt = 0;
+        auto build = [&]() {
+            hs = h * (T)kFbMargin;
+            const T R2 = T(4) * hs * hs;
+            cnt = 0;
+            bool ovf = false;
+            visit_all(__fmul_ru(2.0f, (float)hs) * 1.0001f, [&](T r2, T mj) {
+                if (r2 < R2) {
+                    if (cnt < kFbPerLane) {
+                        fr[wib][cnt][lane] = sqrt(r2);
+                        fm[wib][cnt][lane] = mj;
+                        ++cnt;
+                    } else {
+                        ovf = true;
+                    }
+                }
+            });
+            direct = __any_sync(FULL, ovf);
+            __syncwarp();
+        };
         auto sums = [&](T hh) {
             S0 = T(0);
             S1 = T(0);
             nn = 0;
             const T hinv = T(1) / hh;
-            const T R2 = T(4) * hh * hh;
-            float Rq = __fmul_ru(2.0f, (float)hh) * 1.0001f;
-            walk(
-                b, dy, [&](const NodeBox &nb) { return box_overlap(boxA.plo, boxA.phi, nb.plo, nb.phi, Rq, ph); },
-                [&](unsigned mask, int first) {
-                  for (unsigned mm = mask; mm; mm &= mm - 1u) {
-                    const int B = first + __ffs(mm) - 1;
-                    const int stB = b.leaf_start[B], nB = b.leaf_start[B + 1] - stB;
-                    T Dx, Dy, Dz;
-                    leaf_shift<T>(b, leaf, B, ph, Dx, Dy, Dz);
-                    if (lane < nB) {
-                        V q = pm[stB + lane];
-                        T dx = pi.x - (q.x + Dx), dyy = pi.y - (q.y + Dy), dz = pi.z - (q.z + Dz);
-                        T r2 = dx * dx + dyy * dyy + dz * dz;
-                        if (r2 < R2) {
-                            T f, df, qq = sqrt(r2) * hinv;
-                            m4(qq, f, df);
-                            S0 += q.w * f;
-                            S1 += q.w * qq * df;
-                            ++nn;
-                        }
+            if (!direct) {
+                for (int e = 0; e < cnt; ++e) {
+                    T f, df, qq = fr[wib][e][lane] * hinv;
+                    m4(qq, f, df);
+                    T mj = fm[wib][e][lane];
+                    S0 += mj * f;
+                    S1 += mj * qq * df;
+                    nn += qq < T(2);
+                }
+            } else {
+                const T R2 = T(4) * hh * hh;
+                visit_all(__fmul_ru(2.0f, (float)hh) * 1.0001f, [&](T r2, T mj) {
+                    if (r2 < R2) {
+                        T f, df, qq = sqrt(r2) * hinv;
+                        m4(qq, f, df);
+                        S0 += mj * f;
+                        S1 += mj * qq * df;
+                        ++nn;
                     }
-                  }
                 });
+            }
             S0 = warp_sum(S0);
             S1 = warp_sum(S1);
             nn = warp_sum(nn);
         };
+        build();
         while (!conv) {
+            if (!direct && h > hs) build();
             sums(h);
             ++it;
             pairs += nn;
@@ -648,6 +698,7 @@ __global__ void __launch_bounds__(128) k_density_fallback(BatchView b, int use_p
             }
             conv = c;
         }
+        if (!direct && h > hs) build();
         sums(h);
         pairs += nn;
         if (lane == 0) {
@@ -719,7 +770,7 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, SPH_FORCE_MINB) k_forc
 
     for (;;) {
         int leaf = 0;
-        if (lane == 0) leaf = atomicAdd(&b.counters[11 + lpp_log2(LPP)], 1);
+        if (lane == 0) leaf = atomicAdd(&b.counters[16 + lpp_log2(LPP)], 1);
         leaf = __shfl_sync(FULL, leaf, 0);
         if (leaf >= nleaf) break;
         const int p = b.leaf_pid[leaf];
@@ -876,20 +927,18 @@ void set_smem(Kern k, size_t bytes)
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <typename T, int LPP>
+template <typename T, int LPP, bool UM>
 cudaError_t run_density(const BatchView &b, int use_pred, cudaStream_t st)
 {
-    using C = DCfg<T, LPP>;
-    static bool init = false;
-    if (!init) {
-        set_smem(k_density<T, LPP>, C::smem);
-        init = true;
+    using C = DCfg<T, LPP, UM>;
+    static int per_sm = 0;
+    if (!per_sm) {
+        set_smem(k_density<T, LPP, UM>, C::smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_density<T, LPP, UM>, C::WPB * 32, C::smem);
+        if (per_sm < 1) per_sm = 1;
     }
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_density<T, LPP>, C::WPB * 32, C::smem);
-    if (per_sm < 1) per_sm = 1;
-    int grid = dev_info().sm_count * per_sm;
-    k_density<T, LPP><<<grid, C::WPB * 32, C::smem, st>>>(b, use_pred);
+    cudaMemsetAsync(b.counters + 16 + lpp_log2(LPP) + (UM ? 4 : 0), 0, sizeof(int), st);
+    k_density<T, LPP, UM><<<dev_info().sm_count * per_sm, C::WPB * 32, C::smem, st>>>(b, use_pred);
     return cudaGetLastError();
 }
 
@@ -921,20 +970,21 @@ cudaError_t run_forces(const BatchView &b, cudaStream_t st)
 cudaError_t launch_density(const BatchView &b, int precision, int use_pred, cudaStream_t st)
 {
     if (b.ntot == 0) return cudaSuccess;
-    cudaMemsetAsync(b.counters + 8, 0, sizeof(int), st);  // fallback count
-    for (int k = 0; k < 4; ++k) {
-        if (!(b.lpp_mask & (1 << k))) continue;
-        cudaMemsetAsync(b.counters + 11 + k, 0, sizeof(int), st);  // work counter of this class
+    cudaMemsetAsync(b.counters + 8, 0, sizeof(int), st);  // slow-path count
+    for (int cls = 0; cls < 8; ++cls) {
+        if (!(b.dens_mask & (1 << cls))) continue;
+        const int k = cls & 3;
+        const bool um = cls >= 4;
         cudaError_t e;
         if (precision == SPH_PREC_FP64) {
-            if (k == 2) e = run_density<double, 4>(b, use_pred, st);
-            else e = run_density<double, 2>(b, use_pred, st);
+            if (k == 2) e = um ? run_density<double, 4, true>(b, use_pred, st) : run_density<double, 4, false>(b, use_pred, st);
+            else e = um ? run_density<double, 2, true>(b, use_pred, st) : run_density<double, 2, false>(b, use_pred, st);
         } else {
             switch (k) {
-            case 0: e = run_density<float, 1>(b, use_pred, st); break;
-            case 1: e = run_density<float, 2>(b, use_pred, st); break;
-            case 2: e = run_density<float, 4>(b, use_pred, st); break;
-            default: e = run_density<float, 8>(b, use_pred, st); break;
+            case 0: e = um ? run_density<float, 1, true>(b, use_pred, st) : run_density<float, 1, false>(b, use_pred, st); break;
+            case 1: e = um ? run_density<float, 2, true>(b, use_pred, st) : run_density<float, 2, false>(b, use_pred, st); break;
+            case 2: e = um ? run_density<float, 4, true>(b, use_pred, st) : run_density<float, 4, false>(b, use_pred, st); break;
+            default: e = um ? run_density<float, 8, true>(b, use_pred, st) : run_density<float, 8, false>(b, use_pred, st); break;
             }
         }
         if (e != cudaSuccess) return e;
@@ -948,7 +998,7 @@ cudaError_t launch_forces(const BatchView &b, int precision, cudaStream_t st)
     if (b.ntot == 0) return cudaSuccess;
     for (int k = 0; k < 4; ++k) {
         if (!(b.lpp_mask & (1 << k))) continue;
-        cudaMemsetAsync(b.counters + 11 + k, 0, sizeof(int), st);
+        cudaMemsetAsync(b.counters + 16 + k, 0, sizeof(int), st);
         cudaError_t e;
         if (precision == SPH_PREC_FP64) {
             if (k == 2) e = run_forces<double, 4>(b, st);

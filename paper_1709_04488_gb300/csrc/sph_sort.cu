@@ -26,6 +26,18 @@ __device__ __forceinline__ unsigned spread10(unsigned v)
     return v;
 }
 
+// Shared-memory histogram update aggregated over the warp: lanes holding the
+// same digit are combined first (Morton digits of neighbouring keys repeat,
+// and 32 atomics on one address would serialise).  Every lane of the warp
+// must call it; lanes with valid == false contribute nothing.
+__device__ __forceinline__ void warp_hist_add(unsigned *h, unsigned d, bool valid)
+{
+    const int lane = threadIdx.x & 31;
+    unsigned dd = valid ? d : 0xffffffffu;
+    unsigned peers = __match_any_sync(0xffffffffu, dd);
+    if (valid && (peers & ((1u << lane) - 1u)) == 0u) atomicAdd(&h[d], (unsigned)__popc(peers));
+}
+
 __global__ void k_reset_bbox(ProbDyn *dyn, int nprob)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -125,88 +137,131 @@ __global__ void k_domain(BatchView b)
     d.dom_inv = ext > 0.0 ? 1.0 / ext : 1.0;
 }
 
-__global__ void k_keys(BatchView b)
+// ---- single-pass LSD radix sort ("onesweep"): one fused key + histogram
+// kernel for all passes, then one kernel per 8-bit pass whose tiles find
+// their global offsets by a decoupled look-back over the earlier tiles.
+constexpr unsigned kFlagAgg = 1u << 30, kFlagPre = 2u << 30, kCountMask = (1u << 30) - 1u;
+constexpr long long kSpinLimit = 1ll << 24;
+
+__device__ __forceinline__ unsigned morton_key_code(const BatchView &b, int p, long long g)
 {
-    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= b.ntot) return;
-    int p = find_problem(b.prob_base, b.nprob, g);
     const ProbStatic &ps = b.prob[p];
     const ProbDyn &d = b.dyn[p];
     long long i = g - ps.base;
     double X[3] = {ps.x[i], ps.y[i], ps.z[i]};
+    double lo[3], inv;
+    if (ps.ph.periodic) {
+        double ext = fmax(ps.ph.box_len[0], fmax(ps.ph.box_len[1], ps.ph.box_len[2]));
+        for (int a = 0; a < 3; ++a) lo[a] = ps.ph.box_lo[a];
+        inv = 1.0 / ext;
+    } else {
+        for (int a = 0; a < 3; ++a) lo[a] = d.dom_lo[a];
+        inv = d.dom_inv;
+    }
     unsigned code = 0;
     for (int a = 0; a < 3; ++a) {
-        double t = (X[a] - d.dom_lo[a]) * d.dom_inv * (double)(1 << kMortonBits);
+        double t = (X[a] - lo[a]) * inv * (double)(1 << kMortonBits);
         int c = t > 0.0 ? (int)t : 0;  // NaN maps to 0
         c = c > (1 << kMortonBits) - 1 ? (1 << kMortonBits) - 1 : c;
         code |= spread10((unsigned)c) << a;
     }
-    b.keys[0][g] = ((unsigned long long)p << kMortonTotal) | code;
-    b.vals[0][g] = (unsigned)g;
+    return code;
 }
 
-// ---- radix sort: per-tile digit histograms, one scan, stable scatter -----
-__global__ void k_radix_hist(const unsigned long long *keys, long long n, int shift, unsigned *hist,
-                             int nblk)
+// Keys of every particle, and the digit histograms of every pass.
+__global__ void k_keys_hist(BatchView b, unsigned *hist, int passes)
 {
-    __shared__ unsigned cnt[256];
-    cnt[threadIdx.x] = 0;
+    __shared__ unsigned h[8][256];
+    for (int k = threadIdx.x; k < 8 * 256; k += blockDim.x) (&h[0][0])[k] = 0u;
     __syncthreads();
-    long long base = (long long)blockIdx.x * kSortTile;
-    for (int r = 0; r < kSortItems; ++r) {
-        long long k = base + r * kSortThreads + threadIdx.x;
-        if (k < n) atomicAdd(&cnt[(unsigned)(keys[k] >> shift) & 255u], 1u);
+    for (long long g0 = (long long)blockIdx.x * blockDim.x; g0 < b.ntot; g0 += (long long)gridDim.x * blockDim.x) {
+        const long long g = g0 + threadIdx.x;
+        const bool ok = g < b.ntot;
+        unsigned long long key = 0ull;
+        if (ok) {
+            int p = find_problem(b.prob_base, b.nprob, g);
+            key = ((unsigned long long)p << kMortonTotal) | morton_key_code(b, p, g);
+            b.keys[0][g] = key;
+        }
+        for (int q = 0; q < passes; ++q) warp_hist_add(h[q], (unsigned)(key >> (8 * q)) & 255u, ok);
     }
     __syncthreads();
-    hist[(long long)threadIdx.x * nblk + blockIdx.x] = cnt[threadIdx.x];
-}
-
-// Exclusive scan of `len` values in place with one block of 1024 threads.
-__global__ void k_scan_single(unsigned *a, long long len)
-{
-    __shared__ unsigned part[1024];
-    long long per = (len + blockDim.x - 1) / blockDim.x;
-    long long lo = threadIdx.x * per, hi = lo + per < len ? lo + per : len;
-    unsigned s = 0;
-    for (long long k = lo; k < hi; ++k) s += a[k];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-        unsigned t = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
-        __syncthreads();
-        part[threadIdx.x] += t;
-        __syncthreads();
-    }
-    unsigned run = part[threadIdx.x] - s;
-    for (long long k = lo; k < hi; ++k) {
-        unsigned v = a[k];
-        a[k] = run;
-        run += v;
+    for (int k = threadIdx.x; k < passes * 256; k += blockDim.x) {
+        unsigned v = (&h[0][0])[k];
+        if (v) atomicAdd(&hist[k], v);
     }
 }
 
-// Stable scatter: items of a tile are ranked in index order (round-major,
-// thread-minor), warp peers found with __match_any_sync, warps combined
-// through shared per-warp digit counts.
-__global__ void k_radix_scatter(const unsigned long long *kin, const unsigned *vin,
-                                unsigned long long *kout, unsigned *vout, long long n, int shift,
-                                const unsigned *hist, int nblk, int identity_vals)
+__global__ void k_onesweep(const unsigned long long *kin, const unsigned *vin, unsigned long long *kout,
+                           unsigned *vout, long long n, int shift, const unsigned *hist, unsigned *status,
+                           unsigned *tile_ctr, int identity_vals, unsigned *timeout_flag)
 {
     constexpr int NW = kSortThreads / 32;
     __shared__ unsigned run[256];
     __shared__ unsigned wcnt[NW][256];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    run[threadIdx.x] = hist[(long long)threadIdx.x * nblk + blockIdx.x];
-    for (int w = 0; w < NW; ++w) wcnt[w][threadIdx.x] = 0;
+    __shared__ unsigned cnt[256];
+    __shared__ unsigned gpre[256];
+    __shared__ int s_tile;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, t = threadIdx.x;
+    if (t == 0) s_tile = (int)atomicAdd(tile_ctr, 1u);
+    cnt[t] = 0u;
+    for (int w = 0; w < NW; ++w) wcnt[w][t] = 0u;
+    // exclusive scan of the pass's global digit histogram
+    gpre[t] = hist[t];
     __syncthreads();
-    long long base = (long long)blockIdx.x * kSortTile;
+    for (int o = 1; o < 256; o <<= 1) {
+        unsigned v = t >= o ? gpre[t - o] : 0u;
+        __syncthreads();
+        gpre[t] += v;
+        __syncthreads();
+    }
+    const unsigned gstart = gpre[t] - hist[t];
+    const int tile = s_tile;
+    const long long base = (long long)tile * kSortTile;
+    // local digit counts
+    unsigned long long keys[kSortItems];
+    for (int r = 0; r < kSortItems; ++r) {
+        long long k = base + r * kSortThreads + t;
+        keys[r] = k < n ? kin[k] : 0ull;
+        warp_hist_add(cnt, (unsigned)(keys[r] >> shift) & 255u, k < n);
+    }
+    __syncthreads();
+    // publish this tile's counts, then look back over the earlier tiles
+    unsigned *st = status + (long long)tile * 256;
+    const unsigned mine = cnt[t];
+    if (tile == 0) {
+        atomicExch(&st[t], kFlagPre | mine);
+        run[t] = gstart;
+    } else {
+        atomicExch(&st[t], kFlagAgg | mine);
+        unsigned excl = 0u;
+        long long spins = 0;
+        for (int pred = tile - 1; pred >= 0;) {
+            unsigned v = *(volatile unsigned *)(status + (long long)pred * 256 + t);
+            unsigned f = v & ~kCountMask;
+            if (f == 0u) {
+                if (++spins > kSpinLimit) {
+                    atomicOr(timeout_flag, 1u);
+                    break;
+                }
+                continue;
+            }
+            excl += v & kCountMask;
+            if (f == kFlagPre) break;
+            --pred;
+        }
+        atomicExch(&st[t], kFlagPre | (excl + mine));
+        run[t] = gstart + excl;
+    }
+    __syncthreads();
+    // stable ranks inside the tile (index order), then scatter
     const unsigned lt = (1u << lane) - 1u;
     for (int r = 0; r < kSortItems; ++r) {
-        long long k = base + r * kSortThreads + threadIdx.x;
+        long long k = base + r * kSortThreads + t;
         bool ok = k < n;
-        unsigned long long key = ok ? kin[k] : 0ull;
+        unsigned long long key = keys[r];
         unsigned val = ok ? (identity_vals ? (unsigned)k : vin[k]) : 0u;
-        unsigned d = ok ? (unsigned)(key >> shift) & 255u : 256u + lane;  // unique dummies
+        unsigned d = ok ? (unsigned)(key >> shift) & 255u : 256u + lane;
         unsigned peers = __match_any_sync(0xffffffffu, d);
         unsigned rank = __popc(peers & lt);
         bool leader = (peers & lt) == 0u;
@@ -221,31 +276,27 @@ __global__ void k_radix_scatter(const unsigned long long *kin, const unsigned *v
         __syncthreads();
         unsigned tot = 0;
         for (int w = 0; w < NW; ++w) {
-            tot += wcnt[w][threadIdx.x];
-            wcnt[w][threadIdx.x] = 0;
+            tot += wcnt[w][t];
+            wcnt[w][t] = 0;
         }
-        run[threadIdx.x] += tot;
+        run[t] += tot;
         __syncthreads();
     }
 }
 
-__global__ void k_copy_perm(const unsigned *vals, int *perm, long long n)
-{
-    long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) perm[k] = (int)vals[k];
-}
 
 }  // namespace
 
 cudaError_t launch_domain_and_keys(const BatchView &b, cudaStream_t st)
 {
-    if (b.ntot == 0) return cudaSuccess;
+    // the keys themselves are formed by the sort's first kernel; here only the
+    // bounding boxes of isolated problems (periodic boxes need no pass)
+    if (b.ntot == 0 || !b.any_isolated) return cudaSuccess;
     int pb = (b.nprob + 127) / 128;
     k_reset_bbox<<<pb, 128, 0, st>>>(b.dyn, b.nprob);
     long long nb = (b.ntot + kBboxThreads - 1) / kBboxThreads;
     k_bbox<<<(unsigned)nb, kBboxThreads, 0, st>>>(b);
     k_domain<<<pb, 128, 0, st>>>(b);
-    k_keys<<<(unsigned)((b.ntot + 255) / 256), 256, 0, st>>>(b);
     return cudaGetLastError();
 }
 
@@ -253,18 +304,23 @@ cudaError_t launch_radix_sort(const BatchView &b, cudaStream_t st)
 {
     if (b.ntot == 0) return cudaSuccess;
     const long long n = b.ntot;
-    const int nblk = (int)((n + kSortTile - 1) / kSortTile);
+    const int ntile = (int)((n + kSortTile - 1) / kSortTile);
     const int passes = (b.key_bits + 7) / 8;
+    // hist[passes][256] | tile counters[passes] | status[passes][ntile][256]
+    unsigned *hist = b.hist, *ctr = b.hist + passes * 256, *status = b.hist + passes * 256 + 8;
+    cudaMemsetAsync(b.hist, 0, sizeof(unsigned) * ((size_t)passes * 256 + 8 + (size_t)passes * ntile * 256), st);
+    int kb = (int)((n + 255) / 256);
+    int cap = dev_info().sm_count * 8;
+    k_keys_hist<<<kb < cap ? kb : cap, 256, 0, st>>>(b, hist, passes);
     int src = 0;
     for (int pass = 0; pass < passes; ++pass) {
-        int shift = 8 * pass;
-        k_radix_hist<<<nblk, kSortThreads, 0, st>>>(b.keys[src], n, shift, b.hist, nblk);
-        k_scan_single<<<1, 1024, 0, st>>>(b.hist, 256LL * nblk);
-        k_radix_scatter<<<nblk, kSortThreads, 0, st>>>(b.keys[src], b.vals[src], b.keys[src ^ 1],
-                                                       b.vals[src ^ 1], n, shift, b.hist, nblk, 0);
+        const bool last = pass == passes - 1;
+        unsigned *vdst = last ? (unsigned *)b.perm : b.vals[src ^ 1];
+        k_onesweep<<<ntile, kSortThreads, 0, st>>>(b.keys[src], b.vals[src], b.keys[src ^ 1], vdst, n, 8 * pass,
+                                                   hist + pass * 256, status + (size_t)pass * ntile * 256,
+                                                   ctr + pass, pass == 0, (unsigned *)&b.counters[15]);
         src ^= 1;
     }
-    k_copy_perm<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(b.vals[src], b.perm, n);
     if (src != 0) {
         // leave the sorted keys in keys[0] for the leaf builder
         cudaMemcpyAsync(b.keys[0], b.keys[1], sizeof(unsigned long long) * n, cudaMemcpyDeviceToDevice, st);
