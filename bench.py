@@ -29,7 +29,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "SPH particle-updates/s (density+h+force)"
 UNIT = "particle-updates/s"
-WORKLOAD = "sod3d_36864: 128x16x16 | 64x8x8 lattice, periodic [0,1)x[0,1/8)^2, gamma=1.4, CFL KDK steps"
+WORKLOADS = {
+    "sod": "sod3d_36864: 128x16x16 | 64x8x8 lattice, periodic [0,1)x[0,1/8)^2, gamma=1.4, CFL KDK steps",
+    "sedov": "sedov3d_1e6: 100^3 jittered lattice, periodic unit cube, E=1 on 64 central particles, gamma=5/3, CFL KDK steps",
+    "cloud": "cloud_8e6: isolated sphere rho ~ 1/(1+r^2/a^2), a=0.1, isothermal, Mach-5 k^-4 velocity field, CFL KDK steps",
+}
+WORKLOAD = WORKLOADS["sod"]
 # algorithmic flops per in-range pair, counted from the kernels' source
 FLOPS_DENSITY_PAIR = 19   # per pair per Newton-Raphson pass (q, f, f', two accumulations)
 FLOPS_FORCE_PAIR = 101    # per ordered pair (pressure, viscosity, conduction, energy, TwoSum-compensated m a)
@@ -44,6 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--lpp", type=int, default=0, help="lanes per particle (0: autotuned)")
+    ap.add_argument("--workload", default="sod", choices=sorted(WORKLOADS),
+                    help="sod (the default measured configuration), sedov or cloud")
     ap.add_argument("--serve", type=int, default=150,
                     help="requests in the serving measurement (0 skips it)")
     ap.add_argument("--serve-load", type=float, nargs="*", default=[0.7],
@@ -51,9 +58,25 @@ def parse():
     return ap.parse_args()
 
 
-def workload():
+def workload(name="sod"):
     from paper_1709_04488_gb300 import ics
-    return ics.sod()
+    return {"sod": ics.sod, "sedov": ics.sedov, "cloud": ics.cloud}[name]()
+
+
+def traffic_for(kernel_src, workload):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if the kernel source is unchanged since that capture."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as fh:
+            rec = json.load(fh).get(workload)
+        with open(kernel_src, "rb") as fh:
+            sha = hashlib.sha256(fh.read()).hexdigest()
+        if rec and rec.get("source_sha256") == sha:
+            return rec
+    except Exception:
+        pass
+    return None
 
 
 def dist_env():
@@ -241,7 +264,7 @@ def run_ours(args):
         B.build()
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
-    a, p = workload()
+    a, p = workload(args.workload)
     n = len(a["x"])
     prm = S.make_params(S.PREC_MIXED, **p, flags=S.FLAG_ASYNC | S.FLAG_TIMING, lanes_per_particle=args.lpp)
     with torch.cuda.stream(stream):
@@ -282,8 +305,12 @@ def run_ours(args):
     else:
         kern, flops, t_ms = "k_density", np.mean(dp) * FLOPS_DENSITY_PAIR, dens_ms
     achieved = flops / (t_ms * 1e-3) / 1e12
+    tr = traffic_for(os.path.join(ROOT, "paper_1709_04488_gb300", "csrc", "sph_pairs.cu"), args.workload)
+    traffic = None
+    if tr and tr.get("kernel") == kern:
+        traffic = tr["dram_bytes_per_launch"]
     roof = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": traffic,
             "peak_basis": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz",
             "stage_ms": {k: float(v) for k, v in zip(S.STAGES, st)},
             "density_pairs_per_step": float(np.mean(dp)), "force_pairs_per_step": float(np.mean(fp))}
@@ -340,7 +367,7 @@ def run_ours(args):
             dist.destroy_process_group()
         return
     cpu = None
-    if not args.no_cpu_baseline and world == 1:
+    if not args.no_cpu_baseline and world == 1 and args.workload == "sod":
         v, cores, steps, nn, _ = oracle_sample()
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{steps} KDK steps of the full {nn}-particle workload (grid prefilter)"}
@@ -348,7 +375,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "particles": n, "precision": "mixed (FP32 pairs, FP64 state)",
+        "config": {"workload": WORKLOADS[args.workload], "particles": n, "precision": "mixed (FP32 pairs, FP64 state)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "flushed (256 MiB write) between timed steps", "graph": "one CUDA graph per step",
                    "lanes_per_particle": int(prob.params.lanes_per_particle) or "auto"},

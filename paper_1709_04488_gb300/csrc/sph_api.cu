@@ -111,9 +111,7 @@ static int choose_lpp(long long n, int precision, int requested)
 {
     int l = requested;
     if (l == 0) {
-        if (n <= 200000) l = 4;
-        else if (n <= 2000000) l = 2;
-        else l = 1;
+        l = n <= 200000 ? 4 : 1;
     }
     if (l != 1 && l != 2 && l != 4 && l != 8) l = 4;
     if (precision == SPH_PREC_FP64) l = (l >= 4) ? 4 : 2;

@@ -16,9 +16,9 @@
 //              re-walks the tree in every iteration.
 //  k_forces    Eqs. GRADHMOMEQN, GRADHENEQN, MON97ARTVISC, MON97ENERGYDISS
 //              and the signal speed of Eq. SPH_DT.  Every pair term is formed
-//              from the pair vector in a canonical orientation (lower sorted
-//              index first) with order-independent FP32 operations, so that
-//              F_ij = -F_ji bit for bit; m_i a_i is accumulated with
+//              from an exactly antisymmetric pair vector with order-independent
+//              FP32 operations, so that F_ij = -F_ji bit for bit; m_i a_i is
+//              accumulated with
 //              error-free (TwoSum) compensated FP32 sums combined in FP64,
 //              which keeps sum_i m_i a_i near FP64 round-off.
 #include "sph_internal.cuh"
@@ -97,6 +97,11 @@ template <>
 __device__ __forceinline__ float add_rn<float>(float a, float b) { return __fadd_rn(a, b); }
 template <>
 __device__ __forceinline__ double add_rn<double>(double a, double b) { return __dadd_rn(a, b); }
+
+// 2/(rho_i + rho_j): a deterministic function of the commutative sum, so
+// both sides of a pair get the same bits (fast reciprocal in FP32)
+__device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
 
 // sorted particle index carried in the w slot of a staged vector: bit
 // pattern in FP32 staging (only ever copied), exact value in FP64 staging
@@ -432,6 +437,7 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM>::WPB * 32, SPH_DENS_MINB) k_d
             bool ovf = false;
             int nbuf = 0;
             auto flush = [&]() {
+#pragma unroll 4
                 for (int k = sub; k < nbuf; k += LPP) {
                     V c = cand[k];
                     T dx = pi.x - c.x, dyy = pi.y - c.y, dz = pi.z - c.z;
@@ -797,9 +803,10 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, SPH_FORCE_MINB) k_forc
             // difference decides it; where it differs from the canonical one
             // the pair sits at q = 2 to rounding, where f' and its force vanish.
             int cnt = 0;
+#pragma unroll 4
             for (int k = sub; k < nbuf; k += LPP) {
                 V a0 = c0[k], a3 = c3[k];
-                T rx = xi.x - (a3.x + a0.x), ry = xi.y - (a3.y + a0.y), rz = xi.z - (a3.z + a0.z);
+                T rx = (xi.x - a0.x) - a3.x, ry = (xi.y - a0.y) - a3.y, rz = (xi.z - a0.z) - a3.z;
                 T r2 = rx * rx + ry * ry + rz * rz;
                 T hm = xi.w < a0.w ? xi.w : a0.w;
                 if (active && t_as_bits(a3.w) != s && r2 * hm * hm < T(4)) lst[cnt++ * 32 + lane] = (unsigned char)k;
@@ -822,18 +829,9 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, SPH_FORCE_MINB) k_forc
                     for (int q = 1; q < LPP; ++q) own = e2 >= pre[q] ? q : own;
                     int k = lst[(e2 - pre[own]) * 32 + (lane & ~(LPP - 1)) + own];
                     V a0 = c0[k], a1 = c1[k], a2 = c2[k], a3 = c3[k];
-                    int sj = t_as_bits(a3.w);
-                    bool lo = s < sj;
-                    // canonical pair vector: formed from the lower sorted index
-                    T ax_ = lo ? xi.x : a0.x, bx = lo ? a0.x : xi.x, dx = lo ? a3.x : -a3.x;
-                    T ay_ = lo ? xi.y : a0.y, by = lo ? a0.y : xi.y, dyy = lo ? a3.y : -a3.y;
-                    T az_ = lo ? xi.z : a0.z, bz = lo ? a0.z : xi.z, dz = lo ? a3.z : -a3.z;
-                    T rx = ax_ - (dx + bx), ry = ay_ - (dyy + by), rz = az_ - (dz + bz);
-                    if (!lo) {
-                        rx = -rx;
-                        ry = -ry;
-                        rz = -rz;
-                    }
+                    // r_ij = (o_i - o_j) - D_AB: IEEE subtraction is sign-symmetric and
+                    // D_BA = -D_AB exactly, so particle j forms exactly -r_ij
+                    T rx = (xi.x - a0.x) - a3.x, ry = (xi.y - a0.y) - a3.y, rz = (xi.z - a0.z) - a3.z;
                     T r2 = rx * rx + ry * ry + rz * rz;
                     T rinv = rsqrt_t(r2);
                     T r = r2 * rinv;
@@ -845,7 +843,7 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, SPH_FORCE_MINB) k_forc
                     T vx = vi.x - a1.x, vy = vi.y - a1.y, vz = vi.z - a1.z;
                     T vdr = (vx * rx + vy * ry + vz * rz) * rinv;
                     T mu = vdr < T(0) ? vdr : T(0);
-                    T rhob_inv = T(2) / add_rn(ti.y, a2.y);
+                    T rhob_inv = fast_div(T(2), add_rn(ti.y, a2.y));
                     T gbar = T(0.5) * add_rn(gi, gj);
                     T vsig = add_rn(vi.w, a1.w) - beta * mu;
                     T visc = alpha * vsig * mu * rhob_inv;
