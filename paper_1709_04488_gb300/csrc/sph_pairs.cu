@@ -37,7 +37,7 @@ constexpr double kListMargin = 1.03;  // list radius = 2 h * margin
 #define SPH_FORCE_CH 64
 #endif
 #ifndef SPH_FORCE_MINB
-#define SPH_FORCE_MINB 8
+#define SPH_FORCE_MINB 6
 #endif
 #ifndef SPH_DENS_CH
 #define SPH_DENS_CH 128
@@ -180,23 +180,6 @@ __device__ __forceinline__ void walk(const BatchView &b, const ProbDyn &d, Test 
     }
 }
 
-// FP64 difference of two leaf reference points, minimum image, cast to T;
-// computed by lanes 0..2 (one axis each) and broadcast.
-template <typename T>
-__device__ __forceinline__ void leaf_shift(const BatchView &b, int A, int B, const PhysParams &ph, T &dx,
-                                           T &dy, T &dz)
-{
-    const int lane = threadIdx.x & 31;
-    T v = T(0);
-    if (lane < 3) {
-        double d = b.leaf_c[3LL * B + lane] - b.leaf_c[3LL * A + lane];
-        v = (T)min_image(d, ph.box_len[lane], ph.periodic);
-    }
-    dx = __shfl_sync(FULL, v, 0);
-    dy = __shfl_sync(FULL, v, 1);
-    dz = __shfl_sync(FULL, v, 2);
-}
-
 template <typename T>
 __device__ __forceinline__ int warp_incl_scan(int v)
 {
@@ -209,21 +192,41 @@ __device__ __forceinline__ int warp_incl_scan(int v)
     return v;
 }
 
-// Per-warp scratch for staging groups of candidate leaves.
-template <typename T, int CH>
+// Per-warp scratch for staging one group of up to 32 candidate leaves of at
+// most NOWN / 32 particles each.
+template <typename T, int NOWN>
 struct StageScratch {
-    unsigned char owner[CH];  // lane (candidate leaf) that owns each staged slot
-    int src[32];              // source index minus slot index, per candidate leaf
-    T dx[32], dy[32], dz[32]; // leaf shift (FP64 difference of reference points, cast)
+    unsigned char owner[NOWN];  // candidate leaf (lane of the group) of each particle of the group
+    int first[32];              // group element index of each candidate leaf's first particle
+    int start[32];              // sorted index of each candidate leaf's first particle
+    T dx[32], dy[32], dz[32];   // leaf shift (FP64 difference of reference points, cast)
 };
 
-// Stage the particles of the leaves first + k (bit k of mask) into slots
-// [nbuf, ...) of the warp's buffer, flushing when it is full.  load(slot, j,
-// dx, dy, dz) copies particle j with the shift of its leaf into `slot`.
-template <typename T, int CH, class Load, class Flush>
-__device__ __forceinline__ void stage_leaves(const BatchView &b, int A, unsigned mask, int first, const PhysParams &ph,
-                                             int &nbuf, StageScratch<T, CH> &sc, Load &&load, Flush &&flush)
+// Squared distance from point q to the box [lo, hi] (zero inside).
+template <typename T, typename V>
+__device__ __forceinline__ T box_dist2(const V &q, const V &lo, const V &hi)
 {
+    T dx = fmax(fmax(lo.x - q.x, q.x - hi.x), T(0));
+    T dy = fmax(fmax(lo.y - q.y, q.y - hi.y), T(0));
+    T dz = fmax(fmax(lo.z - q.z, q.z - hi.z), T(0));
+    return dx * dx + dy * dy + dz * dz;
+}
+
+// Stage the particles of the leaves first + k (bit k of mask) that keep()
+// accepts, compacted into slots [nbuf, ...) of the warp's candidate buffer of
+// capacity CH; flush() runs first whenever fewer than 32 slots are free.
+// The particles are read 32 at a time, one per lane, through load(j) (j the
+// sorted index) and moved into the query leaf A's frame by the leaf shift
+// (FP64 difference of the reference points, minimum image, cast) before
+// keep(q) sees them.  group(has, B, stB, D) runs on every lane once per call
+// (lane k: candidate leaf first + k if has); store(slot, q, k, idx) writes a
+// kept particle (k: its leaf's lane, idx: its index within that leaf).
+template <typename T, int CH, int NOWN, class Group, class Load, class Keep, class Store, class Flush>
+__device__ __forceinline__ void stage_group(const BatchView &b, int A, unsigned mask, int first, const PhysParams &ph,
+                                            int &nbuf, StageScratch<T, NOWN> &sc, Group &&group, Load &&load,
+                                            Keep &&keep, Store &&store, Flush &&flush)
+{
+    using V = typename Vec4<T>::type;
     const int lane = threadIdx.x & 31;
     const bool has = (mask >> lane) & 1u;
     int stB = 0, nB = 0;
@@ -237,35 +240,53 @@ __device__ __forceinline__ void stage_leaves(const BatchView &b, int A, unsigned
         Dy = (T)min_image(cb[1] - ca[1], ph.box_len[1], ph.periodic);
         Dz = (T)min_image(cb[2] - ca[2], ph.box_len[2], ph.periodic);
     }
-    unsigned rem = mask;
-    while (rem) {
-        const bool in = (rem >> lane) & 1u;
-        const int c = in ? nB : 0;
-        const int incl = warp_incl_scan<T>(c);
-        const bool fits = in && (nbuf + incl <= CH);
-        const unsigned fm = __ballot_sync(FULL, fits);
-        if (fm == 0u) {
-            flush();
-            continue;
-        }
-        const int tot = __shfl_sync(FULL, incl, 31 - __clz(fm));
-        if (fits) {
-            const int off = nbuf + incl - c;
-            for (int t = 0; t < c; ++t) sc.owner[off + t] = (unsigned char)lane;
-            sc.src[lane] = stB - off;
-            sc.dx[lane] = Dx;
-            sc.dy[lane] = Dy;
-            sc.dz[lane] = Dz;
-        }
-        __syncwarp();
-        for (int e = nbuf + lane; e < nbuf + tot; e += 32) {
-            const int k = sc.owner[e];
-            load(e, sc.src[k] + e, sc.dx[k], sc.dy[k], sc.dz[k]);
-        }
-        __syncwarp();
-        nbuf += tot;
-        rem &= ~fm;
+    group(has, first + lane, stB, Dx, Dy, Dz);
+    const int incl = warp_incl_scan<T>(nB);
+    const int tot = __shfl_sync(FULL, incl, 31);
+    __syncwarp();  // earlier readers of the scratch are done
+    if (has) {
+        const int off = incl - nB;
+        for (int t = 0; t < nB; ++t) sc.owner[off + t] = (unsigned char)lane;
+        sc.first[lane] = off;
+        sc.start[lane] = stB;
+        sc.dx[lane] = Dx;
+        sc.dy[lane] = Dy;
+        sc.dz[lane] = Dz;
     }
+    __syncwarp();
+    const unsigned below = (1u << lane) - 1u;
+    for (int e0 = 0; e0 < tot; e0 += 32) {
+        if (nbuf > CH - 32) flush();
+        const int e = e0 + lane;
+        bool ok = false;
+        V q;
+        int k = 0, idx = 0;
+        if (e < tot) {
+            k = sc.owner[e];
+            idx = e - sc.first[k];
+            q = load(sc.start[k] + idx);
+            q.x += sc.dx[k];
+            q.y += sc.dy[k];
+            q.z += sc.dz[k];
+            ok = keep(q);
+        }
+        const unsigned bal = __ballot_sync(FULL, ok);
+        if (ok) store(nbuf + __popc(bal & below), q, k, idx);
+        nbuf += __popc(bal);
+    }
+}
+
+// Box of the query leaf's particles in its own frame (offsets from the
+// reference point), over the lanes with on set.
+template <typename V, typename T>
+__device__ __forceinline__ void frame_box(const V &x, bool on, V &lo, V &hi)
+{
+    lo.x = warp_min(on ? x.x : tinf<T>());
+    lo.y = warp_min(on ? x.y : tinf<T>());
+    lo.z = warp_min(on ? x.z : tinf<T>());
+    hi.x = warp_max(on ? x.x : -tinf<T>());
+    hi.y = warp_max(on ? x.y : -tinf<T>());
+    hi.z = warp_max(on ? x.z : -tinf<T>());
 }
 
 // sum over the LPP lanes that serve one particle
@@ -317,11 +338,13 @@ __device__ __forceinline__ bool nr_update(T &h, T &lo, T &hi, T rho, T drho, T m
 template <typename T, int LPP, bool UM>
 struct DCfg {
     using V = typename Vec4<T>::type;
-    static constexpr int LCAP = 96 / LPP + 8;
+    // list entries per lane: room for ~2x the mean neighbour count of 58 per particle
+    static constexpr int LCAP = LPP == 1 ? 104 : LPP == 2 ? 64 : LPP == 4 ? 40 : 24;
     static constexpr int CH = SPH_DENS_CH;
     static constexpr int WPB = 4;
+    static constexpr int NOWN = 32 * (32 / LPP);  // particles of a group of 32 candidate leaves
     static constexpr int LW = UM ? 1 : 2;  // list words per entry: r (and m_j unless masses are equal)
-    static constexpr size_t scratch = (sizeof(StageScratch<T, CH>) + 31) & ~(size_t)31;
+    static constexpr size_t scratch = (sizeof(StageScratch<T, NOWN>) + 31) & ~(size_t)31;
     static constexpr size_t per_warp = CH * sizeof(V) + (size_t)LCAP * 32 * LW * sizeof(T) + scratch;
     static constexpr size_t smem = WPB * per_warp;
 };
@@ -393,7 +416,7 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM>::WPB * 32, SPH_DENS_MINB) k_d
     V *cand = reinterpret_cast<V *>(mine);
     T *lr = reinterpret_cast<T *>(mine + C::CH * sizeof(V));
     T *lm = lr + C::LCAP * 32;  // used only when masses differ
-    StageScratch<T, C::CH> &sc = *reinterpret_cast<StageScratch<T, C::CH> *>(lr + C::LCAP * 32 * C::LW);
+    StageScratch<T, C::NOWN> &sc = *reinterpret_cast<StageScratch<T, C::NOWN> *>(lr + C::LCAP * 32 * C::LW);
     const int pp = lane / LPP, sub = lane % LPP;
     const int nleaf = b.counters[0];
     const V *pm = (const V *)b.pm;
@@ -415,6 +438,8 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM>::WPB * 32, SPH_DENS_MINB) k_d
         const long long s = st + (active ? pp : 0);
         const V pi = pm[s];
         const T mi = pi.w;
+        V flo, fhi;
+        frame_box<V, T>(pi, active, flo, fhi);
         const T eta3 = (T)(ph.eta * ph.eta * ph.eta);
         const T tol = (T)ph.h_tol;
         const int maxit = ph.h_max_iter;
@@ -429,48 +454,88 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM>::WPB * 32, SPH_DENS_MINB) k_d
         bool conv = !active, fail = false, need = false, noconv = false;
         int cnt = 0;
         long long pairs = 0, tested = 0;
+        // bal: in-range candidates are dealt to the particle's LPP lanes by
+        // their rank among the group's hits instead of by slot, so that the
+        // lists fill evenly; taken after a slot-dealt list overflowed
+        bool bal = false;
         for (int attempt = 0;; ++attempt) {
             const T hs = h * (T)kListMargin;
             float Rq = warp_max((active && !fail) ? __fmul_ru(2.0f, (float)hs) : 0.f) * 1.0001f;
             const T R2 = (T(2) * hs) * (T(2) * hs);
             cnt = 0;
+            int gcnt = 0;
             bool ovf = false;
             int nbuf = 0;
             auto flush = [&]() {
+                __syncwarp();  // staged candidates visible to every lane
+                if (LPP == 1 || !bal) {
 #pragma unroll 4
-                for (int k = sub; k < nbuf; k += LPP) {
-                    V c = cand[k];
-                    T dx = pi.x - c.x, dyy = pi.y - c.y, dz = pi.z - c.z;
-                    T r2 = dx * dx + dyy * dyy + dz * dz;
-                    if (active && !fail && r2 < R2) {
-                        if (cnt < C::LCAP) {
-                            lr[cnt * 32 + lane] = sqrt(r2);
-                            if (!UM) lm[cnt * 32 + lane] = c.w;
-                            ++cnt;
-                        } else {
-                            ovf = true;
+                    for (int k = sub; k < nbuf; k += LPP) {
+                        V c = cand[k];
+                        T dx = pi.x - c.x, dyy = pi.y - c.y, dz = pi.z - c.z;
+                        T r2 = dx * dx + dyy * dyy + dz * dz;
+                        if (active && !fail && r2 < R2) {
+                            if (cnt < C::LCAP) {
+                                lr[cnt * 32 + lane] = sqrt(r2);
+                                if (!UM) lm[cnt * 32 + lane] = c.w;
+                                ++cnt;
+                            } else {
+                                ovf = true;
+                            }
                         }
+                    }
+                } else {
+                    const unsigned below = (1u << sub) - 1u;
+                    for (int k0 = 0; k0 < nbuf; k0 += LPP) {
+                        const int k = k0 + sub;
+                        bool hit = false;
+                        T r = T(0), mj = T(0);
+                        if (k < nbuf) {
+                            V c = cand[k];
+                            T dx = pi.x - c.x, dyy = pi.y - c.y, dz = pi.z - c.z;
+                            T r2 = dx * dx + dyy * dyy + dz * dz;
+                            hit = active && !fail && r2 < R2;
+                            r = sqrt(r2);
+                            mj = c.w;
+                        }
+                        const unsigned gm = (__ballot_sync(FULL, hit) >> (pp * LPP)) & ((1u << LPP) - 1u);
+                        if (hit) {
+                            const int e = gcnt + __popc(gm & below);
+                            if (e < C::LCAP * LPP) {
+                                const int o = (e / LPP) * 32 + pp * LPP + e % LPP;
+                                lr[o] = r;
+                                if (!UM) lm[o] = mj;
+                            } else {
+                                ovf = true;
+                            }
+                        }
+                        gcnt += __popc(gm);
                     }
                 }
                 tested += (nbuf - sub + LPP - 1) / LPP;
                 __syncwarp();
                 nbuf = 0;
             };
+            const T Rq2 = (T)Rq * (T)Rq;
             walk(
                 b, dy, [&](const NodeBox &nb) { return box_overlap(boxA.plo, boxA.phi, nb.plo, nb.phi, Rq, ph); },
                 [&](unsigned mask, int first) {
-                    stage_leaves<T, C::CH>(
-                        b, leaf, mask, first, ph, nbuf, sc,
-                        [&](int slot, int j, T dx, T dyy, T dz) {
-                            V q = pm[j];
-                            q.x += dx;
-                            q.y += dyy;
-                            q.z += dz;
-                            cand[slot] = q;
-                        },
-                        flush);
+                    stage_group<T, C::CH>(
+                        b, leaf, mask, first, ph, nbuf, sc, [](bool, int, int, T, T, T) {},
+                        [&](int j) { return pm[j]; },
+                        [&](const V &q) { return box_dist2<T>(q, flo, fhi) < Rq2; },
+                        [&](int slot, const V &q, int, int) { cand[slot] = q; }, flush);
                 });
             flush();
+            if (LPP > 1 && bal) {
+                const int mine_n = gcnt > sub ? (gcnt - sub - 1) / LPP + 1 : 0;
+                cnt = mine_n < C::LCAP ? mine_n : C::LCAP;
+            }
+            if (LPP > 1 && !bal && __any_sync(FULL, ovf)) {
+                bal = true;  // same radius again, dealt by rank
+                --attempt;
+                continue;
+            }
             if (group_any<LPP>(ovf) && active && !fail) fail = true;
             // Newton-Raphson on the cached lists
             for (;;) {
@@ -576,21 +641,37 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM>::WPB * 32, SPH_DENS_MINB) k_d
 }
 
 // Slow path: one warp per particle for the particles whose per-lane lists in
-// k_density overflowed or outgrew their radius.  The warp gathers the
-// particle's neighbours (within 2 h x 1.1) into a list spread over its 32
-// lanes (up to kFbPerLane each) and iterates on it, walking the tree again
-// only when h outgrows the list; if even that list overflows, every
-// iteration walks the tree and sums the candidates directly.
-constexpr int kFbPerLane = 16;
+// k_density overflowed or outgrew their radius.  The warp stages the leaf's
+// candidate leaves in groups, as k_density does, gathers the particle's
+// neighbours (within 2 h x 1.1) into a list spread over its 32 lanes (up to
+// kFbPerLane each) and iterates on it, walking the tree again only when h
+// outgrows the list; if even that list overflows, every iteration walks the
+// tree and sums the staged candidates directly.
+constexpr int kFbPerLane = 24;
+constexpr int kFbCH = 128;
 constexpr double kFbMargin = 1.1;
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_density_fallback(BatchView b, int use_pred)
-{
+struct FbCfg {
     using V = typename Vec4<T>::type;
-    __shared__ T fr[4][kFbPerLane][32];
-    __shared__ T fm[4][kFbPerLane][32];
+    static constexpr int WPB = 4;
+    static constexpr size_t scratch = (sizeof(StageScratch<T, 1024>) + 31) & ~(size_t)31;
+    static constexpr size_t per_warp = kFbCH * sizeof(V) + (size_t)2 * kFbPerLane * 32 * sizeof(T) + scratch;
+    static constexpr size_t smem = WPB * per_warp;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(FbCfg<T>::WPB * 32) k_density_fallback(BatchView b, int use_pred)
+{
+    using C = FbCfg<T>;
+    using V = typename C::V;
+    extern __shared__ __align__(32) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    unsigned char *mine = smem + wib * C::per_warp;
+    V *cand = reinterpret_cast<V *>(mine);
+    T *fr = reinterpret_cast<T *>(mine + kFbCH * sizeof(V));
+    T *fm = fr + kFbPerLane * 32;
+    StageScratch<T, 1024> &sc = *reinterpret_cast<StageScratch<T, 1024> *>(fm + kFbPerLane * 32);
     const int nf = b.counters[8];
     const V *pm = (const V *)b.pm;
     int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
@@ -613,23 +694,30 @@ __global__ void __launch_bounds__(128) k_density_fallback(BatchView b, int use_p
         long long pairs = 0;
         T S0, S1;
         int nn;
-        // neighbour candidates of the particle within radius R, one visited leaf at a time
+        // every particle within Rq of particle s, staged in groups of
+        // leaves; fn(r2, m_j) sees one candidate per lane
         auto visit_all = [&](float Rq, auto &&fn) {
+            const T Rq2 = (T)Rq * (T)Rq;
+            int nbuf = 0;
+            auto flush = [&]() {
+                __syncwarp();
+                for (int e = lane; e < nbuf; e += 32) {
+                    const V c = cand[e];
+                    T dx = pi.x - c.x, dyy = pi.y - c.y, dz = pi.z - c.z;
+                    fn(dx * dx + dyy * dyy + dz * dz, c.w);
+                }
+                __syncwarp();
+                nbuf = 0;
+            };
             walk(
                 b, dy, [&](const NodeBox &nb) { return box_overlap(boxA.plo, boxA.phi, nb.plo, nb.phi, Rq, ph); },
                 [&](unsigned mask, int first) {
-                    for (unsigned mm = mask; mm; mm &= mm - 1u) {
-                        const int B = first + __ffs(mm) - 1;
-                        const int stB = b.leaf_start[B], nB = b.leaf_start[B + 1] - stB;
-                        T Dx, Dy, Dz;
-                        leaf_shift<T>(b, leaf, B, ph, Dx, Dy, Dz);
-                        if (lane < nB) {
-                            V q = pm[stB + lane];
-                            T dx = pi.x - (q.x + Dx), dyy = pi.y - (q.y + Dy), dz = pi.z - (q.z + Dz);
-                            fn(dx * dx + dyy * dyy + dz * dz, q.w);
-                        }
-                    }
+                    stage_group<T, kFbCH>(
+                        b, leaf, mask, first, ph, nbuf, sc, [](bool, int, int, T, T, T) {},
+                        [&](int j) { return pm[j]; }, [&](const V &q) { return box_dist2<T>(q, pi, pi) < Rq2; },
+                        [&](int slot, const V &q, int, int) { cand[slot] = q; }, flush);
                 });
+            flush();
         };
         bool direct = false;
         T hs = T(0);
@@ -642,8 +730,8 @@ __global__ void __launch_bounds__(128) k_density_fallback(BatchView b, int use_p
             visit_all(__fmul_ru(2.0f, (float)hs) * 1.0001f, [&](T r2, T mj) {
                 if (r2 < R2) {
                     if (cnt < kFbPerLane) {
-                        fr[wib][cnt][lane] = sqrt(r2);
-                        fm[wib][cnt][lane] = mj;
+                        fr[cnt * 32 + lane] = sqrt(r2);
+                        fm[cnt * 32 + lane] = mj;
                         ++cnt;
                     } else {
                         ovf = true;
@@ -660,9 +748,9 @@ __global__ void __launch_bounds__(128) k_density_fallback(BatchView b, int use_p
             const T hinv = T(1) / hh;
             if (!direct) {
                 for (int e = 0; e < cnt; ++e) {
-                    T f, df, qq = fr[wib][e][lane] * hinv;
+                    T f, df, qq = fr[e * 32 + lane] * hinv;
                     m4(qq, f, df);
-                    T mj = fm[wib][e][lane];
+                    T mj = fm[e * 32 + lane];
                     S0 += mj * f;
                     S1 += mj * qq * df;
                     nn += qq < T(2);
@@ -728,14 +816,31 @@ __global__ void __launch_bounds__(128) k_density_fallback(BatchView b, int use_p
 // ---------------------------------------------------------------------------
 // forces
 // ---------------------------------------------------------------------------
+// Force walk: the staged candidates (CH per chunk) are tested against the
+// lane's particle and each pair found is appended to the lane's list as a
+// 16-bit code (slot of its leaf in the warp's table of candidate leaves << 5 |
+// index within that leaf); the lists are evaluated, reading the partner's
+// data from global memory, when one of them or the table fills and at the end,
+// so that every lane evaluates about the same number of pairs.
+#ifndef SPH_FORCE_LC
+#define SPH_FORCE_LC 64
+#endif
+#ifndef SPH_FORCE_TAB
+#define SPH_FORCE_TAB 128
+#endif
 template <typename T, int LPP>
 struct FCfg {
     using V = typename Vec4<T>::type;
     static constexpr int CH = SPH_FORCE_CH;
-    static constexpr int LC = CH / LPP;  // list entries per lane per chunk (cannot overflow)
+    static constexpr int LC = SPH_FORCE_LC;    // list entries per lane
+    static constexpr int TAB = SPH_FORCE_TAB;  // candidate leaves per table fill (<= 2048)
+    static constexpr int SB = 32;              // candidates tested per list-room check
+    static constexpr int NOWN = 32 * (32 / LPP);
     static constexpr int WPB = 4;
-    static constexpr size_t scratch = (sizeof(StageScratch<T, CH>) + 31) & ~(size_t)31;
-    static constexpr size_t per_warp = 4 * CH * sizeof(V) + (size_t)LC * 32 + scratch;
+    static_assert(TAB <= 2048 && LC >= 2 * SB / LPP, "force list layout");
+    static constexpr size_t scratch = (sizeof(StageScratch<T, NOWN>) + 31) & ~(size_t)31;
+    static constexpr size_t codes = ((size_t)(CH + LC * 32) * 2 + 31) & ~(size_t)31;
+    static constexpr size_t per_warp = (CH + TAB) * sizeof(V) + scratch + codes;
     static constexpr size_t smem = WPB * per_warp;
 };
 
@@ -756,6 +861,23 @@ struct TwoSumAcc {
     }
 };
 
+template <typename V>
+__device__ __forceinline__ V ld_ro(const V *p);
+template <>
+__device__ __forceinline__ float4 ld_ro<float4>(const float4 *p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ dbl4 ld_ro<dbl4>(const dbl4 *p)
+{
+    const double2 a = __ldg(reinterpret_cast<const double2 *>(p));
+    const double2 c = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+    dbl4 v;
+    v.x = a.x;
+    v.y = a.y;
+    v.z = c.x;
+    v.w = c.y;
+    return v;
+}
+
 template <typename T, int LPP>
 __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, SPH_FORCE_MINB) k_forces(BatchView b)
 {
@@ -764,13 +886,13 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, SPH_FORCE_MINB) k_forc
     extern __shared__ __align__(32) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     unsigned char *mine = smem + wib * C::per_warp;
-    V *c0 = reinterpret_cast<V *>(mine);  // (offset, 1/h)
-    V *c1 = c0 + C::CH;                    // (v, c)
-    V *c2 = c1 + C::CH;                    // (A, rho, m, u)
-    V *c3 = c2 + C::CH;                    // (leaf shift, sorted index bits)
-    unsigned char *lst = reinterpret_cast<unsigned char *>(c3 + C::CH);
-    StageScratch<T, C::CH> &sc = *reinterpret_cast<StageScratch<T, C::CH> *>(lst + C::LC * 32);
+    V *cand = reinterpret_cast<V *>(mine);  // staged (offset + leaf shift, 1/h)
+    V *table = cand + C::CH;                // per candidate leaf: (leaf shift, first sorted index)
+    StageScratch<T, C::NOWN> &sc = *reinterpret_cast<StageScratch<T, C::NOWN> *>(table + C::TAB);
+    unsigned short *code = reinterpret_cast<unsigned short *>(mine + (C::CH + C::TAB) * sizeof(V) + C::scratch);
+    unsigned short *lst = code + C::CH;
     const int pp = lane / LPP, sub = lane % LPP;
+    const unsigned below = (1u << lane) - 1u;
     const int nleaf = b.counters[0];
     const V *gph = (const V *)b.ph, *gvc = (const V *)b.vc, *gth = (const V *)b.th;
 
@@ -797,68 +919,70 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, SPH_FORCE_MINB) k_forc
         T du = T(0), vs = T(-1);
         int pairs = 0, tested = 0;
         const float R = __fmul_ru(2.0f, boxA.plo.w) * 1.0001f;
-        int nbuf = 0;
-        auto flush = [&]() {
-            // membership: r_ij < 2 max(h_i, h_j).  The plain (non-canonical)
-            // difference decides it; where it differs from the canonical one
-            // the pair sits at q = 2 to rounding, where f' and its force vanish.
-            int cnt = 0;
-#pragma unroll 4
-            for (int k = sub; k < nbuf; k += LPP) {
-                V a0 = c0[k], a3 = c3[k];
-                T rx = (xi.x - a0.x) - a3.x, ry = (xi.y - a0.y) - a3.y, rz = (xi.z - a0.z) - a3.z;
-                T r2 = rx * rx + ry * ry + rz * rz;
-                T hm = xi.w < a0.w ? xi.w : a0.w;
-                if (active && t_as_bits(a3.w) != s && r2 * hm * hm < T(4)) lst[cnt++ * 32 + lane] = (unsigned char)k;
-            }
-            tested += (nbuf - sub + LPP - 1) / LPP;
+        const T RA2 = (T)R * (T)R;
+        V flo, fhi;
+        frame_box<V, T>(xi, active, flo, fhi);
+        int nbuf = 0, cnt = 0, ntab = 0, tA = -1;
+        unsigned gmask = 0u;
+        auto eval_lists = [&]() {
             __syncwarp();
-            // spread the particle's pairs evenly over its LPP lanes
-            int pre[LPP];
-            int tot = 0;
-#pragma unroll
-            for (int q = 0; q < LPP; ++q) {
-                pre[q] = tot;
-                tot += __shfl_sync(FULL, cnt, (lane & ~(LPP - 1)) + q);
+            for (int e = 0; e < cnt; ++e) {
+                const unsigned cd = lst[e * 32 + lane];
+                const V tb = table[cd >> 5];
+                const int j = t_as_bits(tb.w) + (int)(cd & 31u);
+                const V a0 = ld_ro(gph + j), a1 = ld_ro(gvc + j), a2 = ld_ro(gth + j);
+                // r_ij = (o_i - o_j) - D_AB: IEEE subtraction is sign-symmetric and
+                // D_BA = -D_AB exactly, so particle j forms exactly -r_ij
+                T rx = (xi.x - a0.x) - tb.x, ry = (xi.y - a0.y) - tb.y, rz = (xi.z - a0.z) - tb.z;
+                T r2 = rx * rx + ry * ry + rz * rz;
+                T rinv = rsqrt_t(r2);
+                T r = r2 * rinv;
+                T qi = r * xi.w, qj = r * a0.w;
+                T hj2 = a0.w * a0.w;
+                T gi = sigma * m4_df(qi) * hi4;
+                T gj = sigma * m4_df(qj) * (hj2 * hj2);
+                T pterm = add_rn(mul_rn(ti.x, gi), mul_rn(a2.x, gj));
+                T vx = vi.x - a1.x, vy = vi.y - a1.y, vz = vi.z - a1.z;
+                T vdr = (vx * rx + vy * ry + vz * rz) * rinv;
+                T mu = vdr < T(0) ? vdr : T(0);
+                T rhob_inv = fast_div(T(2), add_rn(ti.y, a2.y));
+                T gbar = T(0.5) * add_rn(gi, gj);
+                T vsig = add_rn(vi.w, a1.w) - beta * mu;
+                T visc = alpha * vsig * mu * rhob_inv;
+                T S = visc * gbar - pterm;
+                T wgt = mul_rn(ti.z, a2.z) * S * rinv;
+                ax.add(mul_rn(wgt, rx));
+                ay.add(mul_rn(wgt, ry));
+                az.add(mul_rn(wgt, rz));
+                if (adi)
+                    du += a2.z * (ti.x * vdr * gi +
+                                  rhob_inv * gbar * (T(-0.5) * alpha * vsig * mu * mu + aac * fabs(vdr) * (ti.w - a2.w)));
+                vs = vsig > vs ? vsig : vs;
             }
-            const int mx = warp_max(tot);
-            for (int e2 = sub; e2 < mx; e2 += LPP) {
-                if (e2 < tot) {
-                    int own = 0;
-#pragma unroll
-                    for (int q = 1; q < LPP; ++q) own = e2 >= pre[q] ? q : own;
-                    int k = lst[(e2 - pre[own]) * 32 + (lane & ~(LPP - 1)) + own];
-                    V a0 = c0[k], a1 = c1[k], a2 = c2[k], a3 = c3[k];
-                    // r_ij = (o_i - o_j) - D_AB: IEEE subtraction is sign-symmetric and
-                    // D_BA = -D_AB exactly, so particle j forms exactly -r_ij
-                    T rx = (xi.x - a0.x) - a3.x, ry = (xi.y - a0.y) - a3.y, rz = (xi.z - a0.z) - a3.z;
+            pairs += cnt;
+            cnt = 0;
+            __syncwarp();  // table and lists free for reuse
+        };
+        // membership: r_ij < 2 max(h_i, h_j), decided on the staged
+        // (offset + shift) difference; where its rounding differs from the
+        // pair vector's the pair sits at q = 2, where f' and the force vanish
+        auto test = [&]() {
+            __syncwarp();  // staged candidates visible to every lane
+            const int self = tA >= 0 ? ((tA << 5) | pp) : -1;
+            for (int k0 = 0; k0 < nbuf; k0 += C::SB) {
+                if (__any_sync(FULL, cnt > C::LC - C::SB / LPP)) eval_lists();
+                const int ke = k0 + C::SB < nbuf ? k0 + C::SB : nbuf;
+#pragma unroll 4
+                for (int k = k0 + sub; k < ke; k += LPP) {
+                    const V c = cand[k];
+                    T rx = xi.x - c.x, ry = xi.y - c.y, rz = xi.z - c.z;
                     T r2 = rx * rx + ry * ry + rz * rz;
-                    T rinv = rsqrt_t(r2);
-                    T r = r2 * rinv;
-                    T qi = r * xi.w, qj = r * a0.w;
-                    T hj2 = a0.w * a0.w;
-                    T gi = sigma * m4_df(qi) * hi4;
-                    T gj = sigma * m4_df(qj) * (hj2 * hj2);
-                    T pterm = add_rn(mul_rn(ti.x, gi), mul_rn(a2.x, gj));
-                    T vx = vi.x - a1.x, vy = vi.y - a1.y, vz = vi.z - a1.z;
-                    T vdr = (vx * rx + vy * ry + vz * rz) * rinv;
-                    T mu = vdr < T(0) ? vdr : T(0);
-                    T rhob_inv = fast_div(T(2), add_rn(ti.y, a2.y));
-                    T gbar = T(0.5) * add_rn(gi, gj);
-                    T vsig = add_rn(vi.w, a1.w) - beta * mu;
-                    T visc = alpha * vsig * mu * rhob_inv;
-                    T S = visc * gbar - pterm;
-                    T wgt = mul_rn(ti.z, a2.z) * S * rinv;
-                    ax.add(mul_rn(wgt, rx));
-                    ay.add(mul_rn(wgt, ry));
-                    az.add(mul_rn(wgt, rz));
-                    if (adi)
-                        du += a2.z * (ti.x * vdr * gi +
-                                      rhob_inv * gbar * (T(-0.5) * alpha * vsig * mu * mu + aac * fabs(vdr) * (ti.w - a2.w)));
-                    vs = vsig > vs ? vsig : vs;
-                    ++pairs;
+                    T hm = xi.w < c.w ? xi.w : c.w;
+                    const int cd = code[k];
+                    if (active && cd != self && r2 * hm * hm < T(4)) lst[cnt++ * 32 + lane] = (unsigned short)cd;
                 }
             }
+            tested += (nbuf - sub + LPP - 1) / LPP;
             __syncwarp();
             nbuf = 0;
         };
@@ -869,22 +993,41 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, SPH_FORCE_MINB) k_forc
                        box_overlap(boxA.plo, boxA.phi, nb.slo, nb.shi, 0.f, ph);
             },
             [&](unsigned mask, int first) {
-                stage_leaves<T, C::CH>(
+                if (ntab + __popc(mask) > C::TAB) {
+                    test();
+                    eval_lists();
+                    ntab = 0;
+                    tA = -1;
+                }
+                stage_group<T, C::CH>(
                     b, leaf, mask, first, ph, nbuf, sc,
-                    [&](int slot, int j, T dx, T dyy, T dz) {
-                        c0[slot] = gph[j];
-                        c1[slot] = gvc[j];
-                        c2[slot] = gth[j];
-                        V d;
-                        d.x = dx;
-                        d.y = dyy;
-                        d.z = dz;
-                        d.w = bits_as_t(j, T(0));
-                        c3[slot] = d;
+                    [&](bool has, int B, int stB, T Dx, T Dy, T Dz) {
+                        gmask = mask;
+                        if (has) {
+                            V t;
+                            t.x = Dx;
+                            t.y = Dy;
+                            t.z = Dz;
+                            t.w = bits_as_t(stB, T(0));
+                            table[ntab + __popc(mask & below)] = t;
+                        }
+                        const unsigned am = __ballot_sync(FULL, has && B == leaf);
+                        if (am) tA = ntab + __popc(mask & ((1u << (__ffs(am) - 1)) - 1u));
                     },
-                    flush);
+                    [&](int j) { return gph[j]; },
+                    [&](const V &q) {
+                        const T d2 = box_dist2<T>(q, flo, fhi);
+                        return d2 < RA2 || d2 * q.w * q.w < T(4.0004);
+                    },
+                    [&](int slot, const V &q, int k, int idx) {
+                        cand[slot] = q;
+                        code[slot] = (unsigned short)(((ntab + __popc(gmask & ((1u << k) - 1u))) << 5) | idx);
+                    },
+                    test);
+                ntab += __popc(mask);
             });
-        flush();
+        test();
+        eval_lists();
         // combine the lanes of each particle; FP64 for the compensated sums
         double Fx = (double)ax.s + (double)ax.c, Fy = (double)ay.s + (double)ay.c, Fz = (double)az.s + (double)az.c;
         Fx = group_sum<LPP>(Fx);
@@ -940,10 +1083,22 @@ cudaError_t run_density(const BatchView &b, int use_pred, cudaStream_t st)
     return cudaGetLastError();
 }
 
+template <typename T>
+void run_density_fallback(const BatchView &b, int use_pred, cudaStream_t st)
+{
+    using C = FbCfg<T>;
+    static bool init = false;
+    if (!init) {
+        set_smem(k_density_fallback<T>, C::smem);
+        init = true;
+    }
+    k_density_fallback<T><<<dev_info().sm_count * 4, C::WPB * 32, C::smem, st>>>(b, use_pred);
+}
+
 void density_fallback_launch(const BatchView &b, int precision, int use_pred, cudaStream_t st)
 {
-    if (precision == SPH_PREC_FP64) k_density_fallback<double><<<dev_info().sm_count * 4, 128, 0, st>>>(b, use_pred);
-    else k_density_fallback<float><<<dev_info().sm_count * 4, 128, 0, st>>>(b, use_pred);
+    if (precision == SPH_PREC_FP64) run_density_fallback<double>(b, use_pred, st);
+    else run_density_fallback<float>(b, use_pred, st);
 }
 
 template <typename T, int LPP>
