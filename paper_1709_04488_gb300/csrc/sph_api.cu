@@ -61,7 +61,6 @@ void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precis
     b.vals[0] = c.take<unsigned>(n);
     b.vals[1] = c.take<unsigned>(n);
     b.hist = c.take<unsigned>(passes * 256 + 8 + passes * nblk * 256);
-    b.scan_aux = c.take<unsigned>(nblk + 1);
     b.perm = c.take<int>(n);
     double **sd[] = {&b.sx, &b.sy, &b.sz, &b.sh, &b.sm, &b.srho, &b.somega, &b.sP, &b.sc,
                      &b.vpx, &b.vpy, &b.vpz, &b.up};
@@ -74,6 +73,8 @@ void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precis
     b.leaf_start = c.take<int>(ml + 1);
     b.leaf_pid = c.take<int>(ml);
     b.leaf_c = c.take<double>(3 * ml);
+    b.leaf_cf = c.take<float>(6 * ml);
+    b.hf = c.take<float>(n);
     long long cap = ml;
     for (int l = 0; l <= kMaxLevels; ++l) {
         b.node_cap[l] = (int)cap;
@@ -83,6 +84,12 @@ void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precis
     b.fallback_list = c.take<int>(n);
     b.counters = c.take<int>(32);
     b.scratch64 = c.take<long long>(8);
+    // zero region (kept zero by the kernels that use it)
+    b.tile_state = c.take<unsigned>(leaf_tiles(n) + 2);
+    b.zero_lo = (char *)b.tile_state;
+    b.node_ctr[0] = nullptr;
+    for (int l = 1; l <= kMaxLevels; ++l) b.node_ctr[l] = c.take<int>(b.node_cap[l]);
+    b.zero_bytes = c.base ? (size_t)((char *)(b.node_ctr[kMaxLevels] + b.node_cap[kMaxLevels]) - b.zero_lo) : 0;
 }
 
 void carve_tables(Carver &c, BatchView &b, int nprob)
@@ -357,6 +364,7 @@ int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *st
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->bv.prob_base, bases, sizeof bases, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->bv.dyn, 0, sizeof(ProbDyn), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->bv.counters, 0, 32 * sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->bv.zero_lo, 0, c->bv.zero_bytes, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         delete c;
@@ -402,7 +410,7 @@ static int enqueue_density(const BatchView &b, int precision, int use_pred, cuda
     CU(launch_density(b, precision, use_pred, st));
     mk.at(SPH_STAGE_REFIT, st);
     mk.done(SPH_STAGE_DENSITY);
-    CU(launch_refit(b, st));
+    CU(launch_refit(b, precision, st));
     mk.at(SPH_STAGE_FORCES, st);
     mk.done(SPH_STAGE_REFIT);
     return SPH_OK;
@@ -410,10 +418,8 @@ static int enqueue_density(const BatchView &b, int precision, int use_pred, cuda
 
 static int enqueue_step(const BatchView &b, int precision, double dt, cudaStream_t st, const Marks &mk)
 {
-    CU(launch_select_dt(b, dt, st));
-    CU(launch_reset_step(b, 1, st));
     mk.at(SPH_STAGE_KICK_DRIFT, st);
-    CU(launch_kick_drift(b, st));
+    CU(launch_kick_drift(b, dt, st));
     mk.done(SPH_STAGE_KICK_DRIFT);
     int rc = enqueue_density(b, precision, 1, st, mk);
     if (rc) return rc;
@@ -635,7 +641,7 @@ int sph_neighbours(sph_ctx *c, int kind, const double *h_in, int64_t *offsets, i
     CU(launch_gather(b, st));
     CU(launch_build_leaves(b, c->prm.precision, st));
     CU(launch_set_sorted_h(b, h_in, st));
-    CU(launch_refit(b, st));
+    CU(launch_refit(b, c->prm.precision, st));
     CU(launch_neighbour_export(b, kind, h_in, (long long *)offsets, (int *)idx, (long long)cap, b.scratch64, st));
     CU(cudaStreamSynchronize(st));
     long long tot = 0;
@@ -725,6 +731,7 @@ int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, 
     CU(cudaMemcpyAsync(b.prob_base, bases.data(), sizeof(long long) * (nctx + 1), cudaMemcpyHostToDevice, st));
     CU(cudaMemsetAsync(b.dyn, 0, sizeof(ProbDyn) * nctx, st));
     CU(cudaMemsetAsync(b.counters, 0, 32 * sizeof(int), st));
+    CU(cudaMemsetAsync(b.zero_lo, 0, b.zero_bytes, st));
     for (int s = 0; s < nsteps; ++s) {
         rc = enqueue_step(b, prec, -1.0, st, Marks());
         if (rc) return rc;

@@ -3,21 +3,28 @@
 // and per-cell "smallest box containing all the smoothing spheres" is
 // replaced by:
 //   - leaves = octree cells of the Morton order: for each particle the
-//     coarsest cell holding at most 2*leaf_size particles of its problem,
+//     coarsest cell holding at most 4*leaf_size particles of its problem,
 //     split into ceil(count/leaf_size) equal consecutive chunks;
 //   - an implicit 32-ary tree over each problem's leaves (32 consecutive
 //     leaves per level-1 node, 32 level-1 nodes per level-2 node, ...), whose
 //     nodes keep a position box and a smoothing-sphere box, both FP32 rounded
-//     outwards from FP64 data.
+//     outwards from FP64 data.  Node boxes are formed bottom-up in the same
+//     kernel as the leaf boxes: the warp that completes a node's last child
+//     forms the node.
 #include "sph_internal.cuh"
 
 namespace sph {
 
 namespace {
 
-constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;
-constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int kLeafThreads = 256;
+constexpr int kLeafItems = 1;  // consecutive particles per thread
+constexpr int kLeafTile = kLeafThreads * kLeafItems;
+// leaf cell: the coarsest cell with at most cell_limit(leaf size) particles
+__host__ __device__ constexpr int cell_limit(int leaf) { return 4 * leaf; }
+constexpr int kHalo = 128;  // >= cell_limit of every leaf size (1..32)
+constexpr unsigned kTileAgg = 1u << 30, kTilePre = 2u << 30, kTileMask = (1u << 30) - 1u;
+constexpr long long kTileSpinLimit = 1ll << 24;
 
 __global__ void k_gather(BatchView b)
 {
@@ -40,175 +47,316 @@ __device__ __forceinline__ int common_levels(unsigned long long a, unsigned long
     return (__clz(x) - (32 - kMortonTotal)) / 3;
 }
 
-// Leaf start flags (see the file comment for the rule).
-__global__ void k_leaf_flags(BatchView b)
+// Leaf start flag of sorted particle s (see the file comment for the rule);
+// K holds the keys of [k0, k0 + kLeafTile + 2 kHalo), s inside the middle part.
+// The common key prefix with s shrinks monotonically away from s, so the
+// cell of s at level l is found by two binary searches; only levels whose
+// cell excludes s - ncell and s + ncell can hold at most ncell particles.
+__device__ unsigned leaf_flag(const BatchView &b, const unsigned long long *K, long long k0, long long s)
 {
-    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= b.ntot) return;
-    const unsigned long long *K = b.keys[0];
-    const unsigned long long ks = K[s];
+    const unsigned long long ks = K[s - k0];
     const int p = (int)(ks >> kMortonTotal);
     const long long lo = b.prob[p].base, hi = lo + b.prob[p].n - 1;
-    const int leaf = 32 / b.prob[p].lpp, ncell = 2 * leaf;
-    long long pl = s - lo < ncell ? s - lo : ncell;
-    long long pr = hi - s < ncell ? hi - s : ncell;
-    int found = -1;
-    for (int l = 0; l <= kMortonBits; ++l) {
-        while (pl > 0 && common_levels(ks, K[s - pl]) < l) --pl;
-        while (pr > 0 && common_levels(ks, K[s + pr]) < l) --pr;
-        if (1 + pl + pr <= ncell) {
-            found = l;
-            break;
-        }
-    }
-    unsigned flag;
-    if (found >= 0) {
-        long long cs = s - pl, cc = 1 + pl + pr;
-        long long nch = (cc + leaf - 1) / leaf;
-        long long off = s - cs;
-        flag = (off == 0) || ((off * nch) / cc != ((off - 1) * nch) / cc);
-    } else {
-        // more than 2*leaf_size identical keys: chunk the run of equal keys
-        long long a = lo, z = s;
+    const int leaf = kBranch / b.prob[p].lpp, ncell = cell_limit(leaf);
+    auto cl = [&](long long t) { return common_levels(ks, K[t - k0]); };
+    int l = 0;
+    if (s - ncell >= lo) l = max(l, cl(s - ncell) + 1);
+    if (s + ncell <= hi) l = max(l, cl(s + ncell) + 1);
+    const long long wl = max(lo, s - ncell + 1), wr = min(hi, s + ncell - 1);
+    for (; l <= kMortonBits; ++l) {
+        long long a = wl, z = s;  // first t with cl(t) >= l
         while (a < z) {
-            long long mid = (a + z) >> 1;
-            if (K[mid] < ks) a = mid + 1;
-            else z = mid;
+            const long long mid = (a + z) >> 1;
+            if (cl(mid) >= l) z = mid;
+            else a = mid + 1;
         }
-        flag = ((s - a) % leaf) == 0;
-    }
-    b.flag[s] = flag;
-}
-
-// ---- inclusive scan of the flags (block sums, one-block scan, apply) ------
-__global__ void k_scan_tile_sums(const unsigned *a, long long n, unsigned *sums)
-{
-    __shared__ unsigned red[kScanThreads / 32];
-    long long base = (long long)blockIdx.x * kScanTile;
-    unsigned s = 0;
-    for (int r = 0; r < kScanItems; ++r) {
-        long long k = base + r * kScanThreads + threadIdx.x;
-        if (k < n) s += a[k];
-    }
-    s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned t = 0;
-        for (int w = 0; w < kScanThreads / 32; ++w) t += red[w];
-        sums[blockIdx.x] = t;
-    }
-}
-
-__global__ void k_scan_single_excl(unsigned *a, long long len)
-{
-    __shared__ unsigned part[1024];
-    long long per = (len + blockDim.x - 1) / blockDim.x;
-    long long lo = threadIdx.x * per, hi = lo + per < len ? lo + per : len;
-    unsigned s = 0;
-    for (long long k = lo; k < hi; ++k) s += a[k];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 1; o < (int)blockDim.x; o <<= 1) {
-        unsigned t = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
-        __syncthreads();
-        part[threadIdx.x] += t;
-        __syncthreads();
-    }
-    unsigned run = part[threadIdx.x] - s;
-    for (long long k = lo; k < hi; ++k) {
-        unsigned v = a[k];
-        a[k] = run;
-        run += v;
-    }
-}
-
-// Tile-local inclusive scan plus the tile offset; items are contiguous per
-// thread (thread t owns items [t*8, t*8+8) of the tile).
-__global__ void k_scan_apply(unsigned *a, long long n, const unsigned *offs)
-{
-    __shared__ unsigned part[kScanThreads];
-    long long base = (long long)blockIdx.x * kScanTile + (long long)threadIdx.x * kScanItems;
-    unsigned v[kScanItems];
-    unsigned s = 0;
-    for (int r = 0; r < kScanItems; ++r) {
-        long long k = base + r;
-        v[r] = k < n ? a[k] : 0u;
-        s += v[r];
-        v[r] = s;
-    }
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 1; o < kScanThreads; o <<= 1) {
-        unsigned t = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0u;
-        __syncthreads();
-        part[threadIdx.x] += t;
-        __syncthreads();
-    }
-    unsigned pre = offs[blockIdx.x] + part[threadIdx.x] - s;
-    for (int r = 0; r < kScanItems; ++r) {
-        long long k = base + r;
-        if (k < n) a[k] = pre + v[r];
-    }
-}
-
-__global__ void k_leaf_starts(BatchView b)
-{
-    long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= b.ntot) return;
-    unsigned inc = b.flag[s];
-    bool start = (s == 0) || (b.flag[s - 1] != inc);
-    if (start) {
-        int leaf = (int)inc - 1;
-        b.leaf_start[leaf] = (int)s;
-        b.leaf_pid[leaf] = (int)(b.keys[0][s] >> kMortonTotal);
-    }
-    if (s == b.ntot - 1) {
-        b.leaf_start[inc] = (int)b.ntot;
-        b.counters[0] = (int)inc;
-    }
-}
-
-// Leaf counts per problem and the layout of every tree level (one thread;
-// the prefix over problems is serial and tiny).
-__global__ void k_problem_meta(BatchView b)
-{
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int off[kMaxLevels + 1];
-    for (int l = 0; l <= kMaxLevels; ++l) off[l] = 0;
-    for (int p = 0; p < b.nprob; ++p) {
-        ProbDyn &d = b.dyn[p];
-        const ProbStatic &ps = b.prob[p];
-        int nl = 0, lb = off[0];
-        if (ps.n > 0) {
-            lb = (int)b.flag[ps.base] - 1;
-            nl = (int)b.flag[ps.base + ps.n - 1] - lb;
+        long long c = s, e = wr;  // last t with cl(t) >= l
+        while (c < e) {
+            const long long mid = (c + e + 1) >> 1;
+            if (cl(mid) >= l) c = mid;
+            else e = mid - 1;
         }
-        d.leaf_base = lb;
-        d.nleaf = nl;
-        d.node_cnt[0] = nl;
-        d.node_off[0] = lb;
-        off[0] = lb + nl;
+        const long long cc = c - a + 1;
+        if (cc <= ncell) {
+            const long long nch = (cc + leaf - 1) / leaf, off = s - a;
+            return (off == 0) || ((off * nch) / cc != ((off - 1) * nch) / cc);
+        }
+    }
+    // more than ncell identical keys: chunk the run of equal keys
+    const unsigned long long *G = b.keys[0];
+    long long a = lo, z = s;
+    while (a < z) {
+        long long mid = (a + z) >> 1;
+        if (G[mid] < ks) a = mid + 1;
+        else z = mid;
+    }
+    return ((s - a) % leaf) == 0;
+}
+
+// exclusive scan over the block (blockDim == kLeafThreads); total returned in *tot
+__device__ __forceinline__ int block_excl_scan(int v, int *wsum, int *tot)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    __syncthreads();  // wsum free
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    int before = 0, all = 0;
+    for (int k = 0; k < kLeafThreads / 32; ++k) {
+        const int t = wsum[k];
+        if (k < w) before += t;
+        all += t;
+    }
+    *tot = all;
+    return before + x - v;
+}
+
+// Leaf counts of every problem and the layout of every tree level, by one
+// block (exclusive scans over the problems, in chunks of the block size).
+__device__ void problem_meta(const BatchView &b)
+{
+    __shared__ int run[kMaxLevels + 1];
+    __shared__ int wsum[kLeafThreads / 32];
+    if (threadIdx.x <= kMaxLevels) run[threadIdx.x] = 0;
+    __syncthreads();
+    for (int p0 = 0; p0 < b.nprob; p0 += blockDim.x) {
+        const int p = p0 + threadIdx.x;
+        int cnt[kMaxLevels + 1];
+        for (int l = 0; l <= kMaxLevels; ++l) cnt[l] = 0;
+        if (p < b.nprob) {
+            const ProbStatic &ps = b.prob[p];
+            if (ps.n > 0) {
+                const int lb = (int)__ldcg(&b.flag[ps.base]) - 1;
+                cnt[0] = (int)__ldcg(&b.flag[ps.base + ps.n - 1]) - lb;
+            }
+            for (int l = 1; l <= kMaxLevels; ++l)
+                cnt[l] = cnt[l - 1] > kBranch ? (cnt[l - 1] + kBranch - 1) / kBranch : 0;
+        }
         int top = 0;
-        for (int l = 1; l <= kMaxLevels; ++l) {
-            int c = d.node_cnt[l - 1] > kBranch ? (d.node_cnt[l - 1] + kBranch - 1) / kBranch : 0;
-            d.node_cnt[l] = c;
-            d.node_off[l] = off[l];
-            off[l] += c;
-            if (c > 0) top = l;
+        for (int l = 0; l <= kMaxLevels; ++l) {
+            int tot;
+            const int ex = block_excl_scan(cnt[l], wsum, &tot);
+            if (p < b.nprob) {
+                ProbDyn &d = b.dyn[p];
+                d.node_off[l] = run[l] + ex;
+                d.node_cnt[l] = cnt[l];
+                if (l == 0) {
+                    d.leaf_base = run[0] + ex;
+                    d.nleaf = cnt[0];
+                }
+                if (cnt[l] > 0) top = l;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) run[l] += tot;
         }
-        d.top_level = top;
+        if (p < b.nprob) b.dyn[p].top_level = top;
     }
-    for (int l = 0; l <= kMaxLevels; ++l) b.counters[1 + l] = off[l];
+    __syncthreads();
+    if (threadIdx.x <= kMaxLevels) b.counters[1 + threadIdx.x] = run[threadIdx.x];
 }
 
-__device__ __forceinline__ float f_rd(double v) { return __double2float_rd(v); }
-__device__ __forceinline__ float f_ru(double v) { return __double2float_ru(v); }
+// Leaf start flags, their inclusive scan (the leaf index of every particle)
+// with a decoupled look-back between tiles, the leaf starts and owners; the
+// last block to finish lays out the leaves and tree levels of every problem
+// and clears the tile state for the next build.
+__global__ void __launch_bounds__(kLeafThreads) k_leaf_scan(BatchView b)
+{
+    __shared__ unsigned long long sk[kLeafTile + 2 * kHalo];
+    __shared__ int wsum[kLeafThreads / 32];
+    __shared__ unsigned s_tile, s_prefix;
+    __shared__ int s_last;
+    unsigned *ts = b.tile_state;  // [0] tile ticket, [1] finished tiles, [2 + t] status of tile t
+    if (threadIdx.x == 0) s_tile = atomicAdd(&ts[0], 1u);
+    __syncthreads();
+    const unsigned tile = s_tile;
+    const long long n = b.ntot;
+    const long long base = (long long)tile * kLeafTile;
+    const long long k0 = base - kHalo;
+    for (int k = threadIdx.x; k < kLeafTile + 2 * kHalo; k += blockDim.x) {
+        const long long g = k0 + k;
+        sk[k] = (g >= 0 && g < n) ? b.keys[0][g] : 0ull;
+    }
+    __syncthreads();
+    unsigned f[kLeafItems];
+    int tsum = 0;
+    const long long s0 = base + (long long)threadIdx.x * kLeafItems;
+    for (int r = 0; r < kLeafItems; ++r) {
+        f[r] = s0 + r < n ? leaf_flag(b, sk, k0, s0 + r) : 0u;
+        tsum += (int)f[r];
+    }
+    int agg;
+    const int ex = block_excl_scan(tsum, wsum, &agg);
+    // decoupled look-back, 32 predecessors per round (warp 0)
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        volatile unsigned *vs = ts + 2;
+        unsigned prefix = 0;
+        if (tile == 0) {
+            if (lane == 0) {
+                __threadfence();
+                vs[0] = kTilePre | (unsigned)agg;
+            }
+        } else {
+            if (lane == 0) vs[tile] = kTileAgg | (unsigned)agg;
+            __threadfence();
+            long long t = (long long)tile - 1, spins = 0;
+            for (;;) {
+                const long long tt = t - lane;
+                const unsigned v = tt >= 0 ? (unsigned)vs[tt] : (unsigned)kTilePre;  // before tile 0: an empty prefix
+                const unsigned pre = __ballot_sync(0xffffffffu, (v & kTilePre) != 0u);
+                const unsigned pend = __ballot_sync(0xffffffffu, (v & ~kTileMask) == 0u);
+                const int np = pre ? __ffs(pre) - 1 : 31;  // nearest inclusive prefix (or the window)
+                const unsigned need = np == 31 ? 0xffffffffu : ((1u << (np + 1)) - 1u);
+                if (pend & need) {
+                    if (++spins > kTileSpinLimit) {
+                        if (lane == 0) atomicExch(&b.counters[15], 1);  // reported as a timeout
+                        break;
+                    }
+                    continue;
+                }
+                prefix += warp_sum(lane <= np ? (v & kTileMask) : 0u);
+                if (pre) break;
+                t -= 32;
+            }
+            if (lane == 0) {
+                __threadfence();
+                vs[tile] = kTilePre | (prefix + (unsigned)agg);
+            }
+        }
+        if (lane == 0) s_prefix = prefix;
+    }
+    __syncthreads();
+    unsigned run = s_prefix + (unsigned)ex;
+    for (int r = 0; r < kLeafItems; ++r) {
+        const long long s = s0 + r;
+        if (s >= n) break;
+        run += f[r];
+        b.flag[s] = run;
+        if (f[r]) {
+            b.leaf_start[run - 1] = (int)s;
+            b.leaf_pid[run - 1] = (int)(sk[s - k0] >> kMortonTotal);
+        }
+        if (s == n - 1) {
+            b.leaf_start[run] = (int)n;
+            b.counters[0] = (int)run;
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(&ts[1], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x) ts[2 + k] = 0u;
+    if (threadIdx.x == 0) {
+        ts[0] = 0u;
+        ts[1] = 0u;
+    }
+    problem_meta(b);
+}
+
+
+__device__ __forceinline__ NodeBox ld_node(const NodeBox *p)
+{
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+    NodeBox nb;
+    nb.plo = __ldcg(q);
+    nb.phi = __ldcg(q + 1);
+    nb.slo = __ldcg(q + 2);
+    nb.shi = __ldcg(q + 3);
+    return nb;
+}
+
+// Union of the (up to 32) child boxes held by the lanes with on set, written
+// by lane 0 to *out.
+__device__ __forceinline__ void union_children(const NodeBox &c, bool on, NodeBox *out)
+{
+    float v[12];
+    v[0] = on ? c.plo.x : INFINITY;
+    v[1] = on ? c.plo.y : INFINITY;
+    v[2] = on ? c.plo.z : INFINITY;
+    v[3] = on ? c.phi.x : -INFINITY;
+    v[4] = on ? c.phi.y : -INFINITY;
+    v[5] = on ? c.phi.z : -INFINITY;
+    v[6] = on ? c.slo.x : INFINITY;
+    v[7] = on ? c.slo.y : INFINITY;
+    v[8] = on ? c.slo.z : INFINITY;
+    v[9] = on ? c.shi.x : -INFINITY;
+    v[10] = on ? c.shi.y : -INFINITY;
+    v[11] = on ? c.shi.z : -INFINITY;
+    float hm = warp_max(on ? c.plo.w : 0.f);
+    float cnt = warp_sum(on ? c.phi.w : 0.f);
+    for (int a = 0; a < 3; ++a) {
+        v[a] = warp_min(v[a]);
+        v[3 + a] = warp_max(v[3 + a]);
+        v[6 + a] = warp_min(v[6 + a]);
+        v[9 + a] = warp_max(v[9 + a]);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        NodeBox nb;
+        nb.plo = make_float4(v[0], v[1], v[2], hm);
+        nb.phi = make_float4(v[3], v[4], v[5], cnt);
+        nb.slo = make_float4(v[6], v[7], v[8], 0.f);
+        nb.shi = make_float4(v[9], v[10], v[11], 0.f);
+        *out = nb;
+    }
+}
+
+// After lane 0 wrote the box of `leaf`: the warp that completes the last
+// child of a node (arrival counter per node, cleared again by that warp)
+// forms the node's box from its children and carries on upwards.
+__device__ void tree_up(const BatchView &b, int leaf)
+{
+    const int lane = threadIdx.x & 31;
+    const ProbDyn &d = b.dyn[b.leaf_pid[leaf]];
+    const int top = d.top_level;
+    int k = leaf - d.node_off[0];
+    for (int lvl = 0; lvl < top; ++lvl) {
+        const int parent = k / kBranch;
+        const int nch = min(kBranch, d.node_cnt[lvl] - parent * kBranch);
+        int *ctr = b.node_ctr[lvl + 1] + d.node_off[lvl + 1] + parent;
+        int old = 0;
+        if (lane == 0) {
+            __threadfence();  // this warp's child box before its arrival
+            old = atomicAdd(ctr, 1);
+        }
+        old = __shfl_sync(0xffffffffu, old, 0);
+        if (old != nch - 1) return;
+        if (lane == 0) *ctr = 0;
+        __threadfence();
+        const bool on = lane < nch;
+        NodeBox c;
+        if (on) c = ld_node(b.nodes[lvl] + d.node_off[lvl] + parent * kBranch + lane);
+        union_children(c, on, b.nodes[lvl + 1] + d.node_off[lvl + 1] + parent);
+        k = parent;
+    }
+}
+
+// Float bounds of an offset known to within one rounding (|v| 2^-24) of the
+// exact FP64 difference, widened by four times that.
+__device__ __forceinline__ float widen_dn(float v, float mag) { return __fsub_rd(v, mag * 2.4e-7f); }
+__device__ __forceinline__ float widen_up(float v, float mag) { return __fadd_ru(v, mag * 2.4e-7f); }
+
+// lane a (< 3) gets v[a]
+__device__ __forceinline__ float axis_of(const float *v, int lane)
+{
+    return lane == 0 ? v[0] : lane == 1 ? v[1] : v[2];
+}
+
+__device__ __forceinline__ float offset_f(float v) { return v; }
+__device__ __forceinline__ float offset_f(double v) { return (float)v; }
 
 // Leaf reference point, position box and the offsets of its particles from
 // that point.  The reference point is the leaf's first particle (FP64); the
-// FP64 difference is taken before the cast to the staging precision, and the
-// box is formed from the offsets (FP64 adds, rounded outwards to float).
+// FP64 difference is taken before the cast to the staging precision.  The
+// box is formed in FP32 from the offsets, widened for their rounding, plus
+// the reference point rounded down (up): only these two conversions per axis
+// and leaf, by lanes 0..2, run on the FP64 pipe besides the offsets.
 template <typename T4>
 __global__ void k_leaf_props(BatchView b)
 {
@@ -216,139 +364,110 @@ __global__ void k_leaf_props(BatchView b)
     const int nleaf = b.counters[0];
     int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     for (int leaf = w; leaf < nleaf; leaf += nw) {
-        int st = b.leaf_start[leaf], cnt = b.leaf_start[leaf + 1] - st;
-        bool on = lane < cnt;
-        double c[3] = {b.sx[st], b.sy[st], b.sz[st]};
-        float o[3] = {0.f, 0.f, 0.f};
-        double od[3] = {0.0, 0.0, 0.0};
-        if (on) {
-            od[0] = b.sx[st + lane] - c[0];
-            od[1] = b.sy[st + lane] - c[1];
-            od[2] = b.sz[st + lane] - c[2];
-            for (int a = 0; a < 3; ++a) o[a] = (float)od[a];
-            T4 v;
-            v.x = (decltype(v.x))od[0];
-            v.y = (decltype(v.y))od[1];
-            v.z = (decltype(v.z))od[2];
-            v.w = (decltype(v.w))b.sm[st + lane];
-            ((T4 *)b.pm)[st + lane] = v;
-        }
+        const int st = b.leaf_start[leaf], cnt = b.leaf_start[leaf + 1] - st;
+        const ProbStatic &ps = b.prob[b.leaf_pid[leaf]];
+        const bool on = lane < cnt;
+        const double c[3] = {b.sx[st], b.sy[st], b.sz[st]};
         float lo[3], hi[3];
-        for (int a = 0; a < 3; ++a) {
-            lo[a] = warp_min(on ? o[a] : INFINITY);
-            hi[a] = warp_max(on ? o[a] : -INFINITY);
-        }
-        if (lane == 0) {
-            for (int a = 0; a < 3; ++a) b.leaf_c[3 * (long long)leaf + a] = c[a];
-            // float offsets are within one rounding of the FP64 ones: widen by it
-            NodeBox nb;
-            float l3[3], h3[3];
+        if (on) {
+            T4 v;
+            v.x = (decltype(v.x))(b.sx[st + lane] - c[0]);
+            v.y = (decltype(v.y))(b.sy[st + lane] - c[1]);
+            v.z = (decltype(v.z))(b.sz[st + lane] - c[2]);
+            v.w = ps.uniform_m ? (decltype(v.w))ps.m_uniform : (decltype(v.w))b.sm[st + lane];
+            ((T4 *)b.pm)[st + lane] = v;
+            const float o[3] = {offset_f(v.x), offset_f(v.y), offset_f(v.z)};
             for (int a = 0; a < 3; ++a) {
-                double e = 1e-6 * ((double)fabsf(lo[a]) + (double)fabsf(hi[a])) + 1e-30;
-                l3[a] = f_rd(c[a] + (double)lo[a] - e);
-                h3[a] = f_ru(c[a] + (double)hi[a] + e);
+                lo[a] = widen_dn(o[a], fabsf(o[a]));
+                hi[a] = widen_up(o[a], fabsf(o[a]));
             }
-            nb.plo = make_float4(l3[0], l3[1], l3[2], 0.f);
-            nb.phi = make_float4(h3[0], h3[1], h3[2], (float)cnt);
+        } else {
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = INFINITY;
+                hi[a] = -INFINITY;
+            }
+        }
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = warp_min(lo[a]);
+            hi[a] = warp_max(hi[a]);
+        }
+        float bl = 0.f, bh = 0.f;
+        if (lane < 3) {
+            const double ca = lane == 0 ? c[0] : lane == 1 ? c[1] : c[2];
+            const float cd = __double2float_rd(ca), cu = __double2float_ru(ca);
+            b.leaf_c[3 * (long long)leaf + lane] = ca;
+            b.leaf_cf[6 * (long long)leaf + lane] = cd;
+            b.leaf_cf[6 * (long long)leaf + 3 + lane] = cu;
+            bl = __fadd_rd(cd, axis_of(lo, lane));
+            bh = __fadd_ru(cu, axis_of(hi, lane));
+        }
+        const float l0 = __shfl_sync(0xffffffffu, bl, 0), l1 = __shfl_sync(0xffffffffu, bl, 1),
+                    l2 = __shfl_sync(0xffffffffu, bl, 2);
+        const float h0 = __shfl_sync(0xffffffffu, bh, 0), h1 = __shfl_sync(0xffffffffu, bh, 1),
+                    h2 = __shfl_sync(0xffffffffu, bh, 2);
+        if (lane == 0) {
+            NodeBox nb;
+            nb.plo = make_float4(l0, l1, l2, 0.f);
+            nb.phi = make_float4(h0, h1, h2, (float)cnt);
             nb.slo = nb.plo;
             nb.shi = nb.phi;
             b.nodes[0][leaf] = nb;
         }
+        tree_up(b, leaf);
     }
 }
 
 // Smoothing-sphere boxes and h_max of the leaves after the density solve,
-// formed from the FP64 offsets to the leaf reference point (FP32 arithmetic
-// on offsets, one FP64 add per axis, rounded outwards).
+// in FP32 from the staged offsets and the float h (rounded up) the density
+// solve left, widened for the offsets' rounding, plus the reference point
+// rounded down (up) that the leaf pass kept.
+template <typename T4>
 __global__ void k_leaf_refit(BatchView b)
 {
     const int lane = threadIdx.x & 31;
     const int nleaf = b.counters[0];
     int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     for (int leaf = w; leaf < nleaf; leaf += nw) {
-        int st = b.leaf_start[leaf], cnt = b.leaf_start[leaf + 1] - st;
-        bool on = lane < cnt;
-        double c[3] = {b.leaf_c[3 * (long long)leaf], b.leaf_c[3 * (long long)leaf + 1],
-                       b.leaf_c[3 * (long long)leaf + 2]};
-        float o[3] = {0.f, 0.f, 0.f}, h2 = 0.f;
-        double h = 0.0;
+        const int st = b.leaf_start[leaf], cnt = b.leaf_start[leaf + 1] - st;
+        const bool on = lane < cnt;
+        float slo[3], shi[3], hm = 0.f;
         if (on) {
-            o[0] = (float)(b.sx[st + lane] - c[0]);
-            o[1] = (float)(b.sy[st + lane] - c[1]);
-            o[2] = (float)(b.sz[st + lane] - c[2]);
-            h = b.sh[st + lane];
-            h2 = __double2float_ru(2.0 * h);
+            const T4 v = ((const T4 *)b.pm)[st + lane];
+            const float o[3] = {offset_f(v.x), offset_f(v.y), offset_f(v.z)};
+            const float h = b.hf[st + lane], h2 = __fmul_ru(2.0f, h);
+            hm = h;
+            for (int a = 0; a < 3; ++a) {
+                const float mag = __fadd_ru(fabsf(o[a]), h2);
+                slo[a] = widen_dn(__fsub_rd(o[a], h2), mag);
+                shi[a] = widen_up(__fadd_ru(o[a], h2), mag);
+            }
+        } else {
+            for (int a = 0; a < 3; ++a) {
+                slo[a] = INFINITY;
+                shi[a] = -INFINITY;
+            }
         }
-        float hmax = warp_max(on ? __double2float_ru(h) : 0.f);
-        float slo[3], shi[3];
+        hm = warp_max(hm);
         for (int a = 0; a < 3; ++a) {
-            slo[a] = warp_min(on ? __fsub_rd(o[a], h2) : INFINITY);
-            shi[a] = warp_max(on ? __fadd_ru(o[a], h2) : -INFINITY);
+            slo[a] = warp_min(slo[a]);
+            shi[a] = warp_max(shi[a]);
         }
+        float bl = 0.f, bh = 0.f;
+        if (lane < 3) {
+            bl = __fadd_rd(b.leaf_cf[6 * (long long)leaf + lane], axis_of(slo, lane));
+            bh = __fadd_ru(b.leaf_cf[6 * (long long)leaf + 3 + lane], axis_of(shi, lane));
+        }
+        const float l0 = __shfl_sync(0xffffffffu, bl, 0), l1 = __shfl_sync(0xffffffffu, bl, 1),
+                    l2 = __shfl_sync(0xffffffffu, bl, 2);
+        const float h0 = __shfl_sync(0xffffffffu, bh, 0), h1 = __shfl_sync(0xffffffffu, bh, 1),
+                    h2 = __shfl_sync(0xffffffffu, bh, 2);
         if (lane == 0) {
             NodeBox &nb = b.nodes[0][leaf];
-            float l3[3], h3[3];
-            for (int a = 0; a < 3; ++a) {
-                double e = 1e-6 * ((double)fabsf(slo[a]) + (double)fabsf(shi[a])) + 1e-30;
-                l3[a] = f_rd(c[a] + (double)slo[a] - e);
-                h3[a] = f_ru(c[a] + (double)shi[a] + e);
-            }
-            nb.plo.w = hmax;
-            nb.slo = make_float4(l3[0], l3[1], l3[2], 0.f);
-            nb.shi = make_float4(h3[0], h3[1], h3[2], 0.f);
+            nb.plo.w = hm;
+            nb.slo = make_float4(l0, l1, l2, 0.f);
+            nb.shi = make_float4(h0, h1, h2, 0.f);
         }
-    }
-}
-
-// One tree level: node box = union of its (up to 32) children's boxes.
-__global__ void k_tree_level(BatchView b, int level)
-{
-    const int lane = threadIdx.x & 31;
-    const int total = b.counters[1 + level];
-    int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-    for (int G = w; G < total; G += nw) {
-        // owning problem: last p with node_off[level] <= G and a non-empty level
-        int lo = 0, hi = b.nprob - 1;
-        while (lo < hi) {
-            int mid = (lo + hi + 1) >> 1;
-            if (b.dyn[mid].node_off[level] <= G) lo = mid;
-            else hi = mid - 1;
-        }
-        const ProbDyn &d = b.dyn[lo];
-        int k = G - d.node_off[level];
-        int ch = kBranch * k + lane;
-        bool on = ch < d.node_cnt[level - 1];
-        NodeBox c;
-        if (on) c = b.nodes[level - 1][d.node_off[level - 1] + ch];
-        float v[12];
-        v[0] = on ? c.plo.x : INFINITY;
-        v[1] = on ? c.plo.y : INFINITY;
-        v[2] = on ? c.plo.z : INFINITY;
-        v[3] = on ? c.phi.x : -INFINITY;
-        v[4] = on ? c.phi.y : -INFINITY;
-        v[5] = on ? c.phi.z : -INFINITY;
-        v[6] = on ? c.slo.x : INFINITY;
-        v[7] = on ? c.slo.y : INFINITY;
-        v[8] = on ? c.slo.z : INFINITY;
-        v[9] = on ? c.shi.x : -INFINITY;
-        v[10] = on ? c.shi.y : -INFINITY;
-        v[11] = on ? c.shi.z : -INFINITY;
-        float hm = warp_max(on ? c.plo.w : 0.f);
-        float cnt = warp_sum(on ? c.phi.w : 0.f);
-        for (int a = 0; a < 3; ++a) {
-            v[a] = warp_min(v[a]);
-            v[3 + a] = warp_max(v[3 + a]);
-            v[6 + a] = warp_min(v[6 + a]);
-            v[9 + a] = warp_max(v[9 + a]);
-        }
-        if (lane == 0) {
-            NodeBox nb;
-            nb.plo = make_float4(v[0], v[1], v[2], hm);
-            nb.phi = make_float4(v[3], v[4], v[5], cnt);
-            nb.slo = make_float4(v[6], v[7], v[8], 0.f);
-            nb.shi = make_float4(v[9], v[10], v[11], 0.f);
-            b.nodes[level][G] = nb;
-        }
+        tree_up(b, leaf);
     }
 }
 
@@ -381,42 +500,26 @@ cudaError_t launch_gather(const BatchView &b, cudaStream_t st)
     return cudaGetLastError();
 }
 
-static cudaError_t launch_tree_levels(const BatchView &b, cudaStream_t st)
-{
-    int L = levels_needed(b.max_leaves);
-    for (int l = 1; l <= L; ++l) {
-        long long cap = b.node_cap[l];
-        long long warps = cap < 152LL * 32 ? cap : 152LL * 32;
-        if (warps < 1) warps = 1;
-        k_tree_level<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(b, l);
-    }
-    return cudaGetLastError();
-}
-
 cudaError_t launch_build_leaves(const BatchView &b, int precision, cudaStream_t st)
 {
     if (b.ntot == 0) return cudaSuccess;
-    const long long n = b.ntot;
-    unsigned g256 = (unsigned)((n + 255) / 256);
-    k_leaf_flags<<<g256, 256, 0, st>>>(b);
-    int nt = (int)((n + kScanTile - 1) / kScanTile);
-    k_scan_tile_sums<<<nt, kScanThreads, 0, st>>>(b.flag, n, b.scan_aux);
-    k_scan_single_excl<<<1, 1024, 0, st>>>(b.scan_aux, nt);
-    k_scan_apply<<<nt, kScanThreads, 0, st>>>(b.flag, n, b.scan_aux);
-    k_leaf_starts<<<g256, 256, 0, st>>>(b);
-    k_problem_meta<<<1, 32, 0, st>>>(b);
+    const long long tiles = (b.ntot + kLeafTile - 1) / kLeafTile;
+    k_leaf_scan<<<(unsigned)tiles, kLeafThreads, 0, st>>>(b);
     int pb = persistent_blocks(256);
     if (precision == SPH_PREC_FP64) k_leaf_props<dbl4><<<pb, 256, 0, st>>>(b);
     else k_leaf_props<float4><<<pb, 256, 0, st>>>(b);
-    return launch_tree_levels(b, st);
+    return cudaGetLastError();
 }
 
-cudaError_t launch_refit(const BatchView &b, cudaStream_t st)
+cudaError_t launch_refit(const BatchView &b, int precision, cudaStream_t st)
 {
     if (b.ntot == 0) return cudaSuccess;
     int pb = persistent_blocks(256);
-    k_leaf_refit<<<pb, 256, 0, st>>>(b);
-    return launch_tree_levels(b, st);
+    if (precision == SPH_PREC_FP64) k_leaf_refit<dbl4><<<pb, 256, 0, st>>>(b);
+    else k_leaf_refit<float4><<<pb, 256, 0, st>>>(b);
+    return cudaGetLastError();
 }
+
+long long leaf_tiles(long long n) { return (n + kLeafTile - 1) / kLeafTile; }
 
 }  // namespace sph

@@ -43,7 +43,9 @@ __global__ void k_set_sorted_h(BatchView b, const double *h_in)
     if (s >= b.ntot) return;
     int p = (int)(b.keys[0][s] >> kMortonTotal);
     long long i = (long long)b.perm[s] - b.prob[p].base;
-    b.sh[s] = h_in ? h_in[i] : b.prob[p].h[i];
+    const double h = h_in ? h_in[i] : b.prob[p].h[i];
+    b.sh[s] = h;
+    b.hf[s] = __double2float_ru(h);
 }
 
 // pass 0: count into cnt[i]; pass 1: write sorted ids at offsets[i]

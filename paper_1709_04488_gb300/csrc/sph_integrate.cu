@@ -14,14 +14,13 @@ namespace {
 
 constexpr int kRedThreads = 256;
 
-__global__ void k_reset_step(BatchView b, int mode)
+constexpr int kCloseItems = 8;  // particles per thread in the closing kernel
+
+__device__ void reset_diag(const BatchView &b, int p, int mode)
 {
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= b.nprob) return;
     ProbDiag *d = b.prob[p].diag;
     d->dt_min_bits = 0x7ff0000000000000ull;  // +inf
     d->force_pairs = 0;
-    if (p == 0) b.counters[15] = 0;  // sort look-back timeout flag
     if (mode == 2) return;
     d->mass = 0;
     for (int a = 0; a < 3; ++a) {
@@ -30,8 +29,7 @@ __global__ void k_reset_step(BatchView b, int mode)
     }
     d->energy = 0;
     d->dEdt = 0;
-    d->dt_min_bits = 0x7ff0000000000000ull;  // +inf
-    d->nr_iter = d->density_pairs = d->force_pairs = d->candidates = d->fallback = 0;
+    d->nr_iter = d->density_pairs = d->candidates = d->fallback = 0;
     d->ngb_sum = 0;
     d->nr_max = 0;
     d->ngb_min = 0x7fffffff;
@@ -40,23 +38,39 @@ __global__ void k_reset_step(BatchView b, int mode)
     d->unconverged = 0;
 }
 
-__global__ void k_select_dt(BatchView b, double dt_host)
+__global__ void k_reset_step(BatchView b, int mode)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= b.nprob) return;
-    ProbDiag *d = b.prob[p].diag;
-    d->dt_cur = dt_host > 0.0 ? dt_host : d->dt_next;
+    if (p == 0) b.counters[15] = 0;  // sort look-back timeout flag
+    if (p < b.nprob) reset_diag(b, p, mode);
 }
 
-__global__ void k_kick_drift(BatchView b)
+// step size of problem p: the caller's, else the CFL step of the last forces
+__device__ __forceinline__ double step_dt(const ProbDiag *d, double dt_host)
 {
+    return dt_host > 0.0 ? dt_host : d->dt_next;
+}
+
+// Opening half kick and drift (Eq. LFKDK1) with the predicted v and u; block
+// 0 also selects each problem's step and resets its diagnostics.
+__global__ void k_kick_drift(BatchView b, double dt_host)
+{
+    if (blockIdx.x == 0) {
+        if (threadIdx.x == 0) b.counters[15] = 0;
+        for (int p = threadIdx.x; p < b.nprob; p += blockDim.x) {
+            ProbDiag *d = b.prob[p].diag;
+            const double dt = step_dt(d, dt_host);
+            reset_diag(b, p, 1);
+            d->dt_cur = dt;
+        }
+    }
     long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= b.ntot) return;
     int p = find_problem(b.prob_base, b.nprob, g);
     const ProbStatic &ps = b.prob[p];
     const PhysParams &ph = ps.ph;
     long long i = g - ps.base;
-    const double dt = ps.diag->dt_cur, hdt = 0.5 * dt;
+    const double dt = step_dt(ps.diag, dt_host), hdt = 0.5 * dt;
     double a[3] = {ps.ax[i], ps.ay[i], ps.az[i]};
     double *X[3] = {ps.x, ps.y, ps.z};
     double *Vv[3] = {ps.vx, ps.vy, ps.vz};
@@ -83,16 +97,55 @@ __global__ void k_kick_drift(BatchView b)
     }
 }
 
-// Closing half kick (optional) and the FP64 reductions per problem.
-__global__ void k_kick_close(BatchView b, int do_kick)
+__device__ __forceinline__ void add_diag(ProbDiag *d, const double *v)
+{
+    double *dst[9] = {&d->mass, &d->mom[0], &d->mom[1], &d->mom[2], &d->energy,
+                      &d->fsum[0], &d->fsum[1], &d->fsum[2], &d->dEdt};
+    for (int k = 0; k < 9; ++k) atomicAdd(dst[k], v[k]);
+}
+
+// Closing half kick (Eq. LFKDK2, optional) and the FP64 reductions per
+// problem: each block takes kCloseItems * blockDim consecutive particles and
+// sums them per problem in registers, then reduces over the block when the
+// whole block is in one problem (one set of atomics per block), else adds per
+// thread.  Block 0 also finishes each problem's step record (CFL step of the
+// forces just computed, time, step count, leaf count), which reads nothing
+// this kernel writes.
+__global__ void k_kick_close(BatchView b, int do_kick, int forces_ran)
 {
     __shared__ double red[9][kRedThreads / 32];
-    __shared__ int p0s;
-    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int p = -1;
+    __shared__ int pfirst, plast;
+    if (blockIdx.x == 0) {
+        for (int p = threadIdx.x; p < b.nprob; p += blockDim.x) {
+            ProbDiag *d = b.prob[p].diag;
+            if (forces_ran) d->dt_next = __longlong_as_double((long long)d->dt_min_bits);
+            if (b.counters[15]) atomicOr(&d->status, ST_TIMEOUT);
+            if (do_kick) {
+                d->time += d->dt_cur;
+                d->steps += 1;
+            }
+            d->leaves = b.dyn[p].nleaf;
+        }
+    }
+    const long long base = (long long)blockIdx.x * blockDim.x * kCloseItems;
+    if (base >= b.ntot) return;
+    const long long end = base + (long long)blockDim.x * kCloseItems < b.ntot ? base + (long long)blockDim.x * kCloseItems : b.ntot;
+    if (threadIdx.x == 0) {
+        pfirst = find_problem(b.prob_base, b.nprob, base);
+        plast = find_problem(b.prob_base, b.nprob, end - 1);
+    }
+    __syncthreads();
     double v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    if (g < b.ntot) {
-        p = find_problem(b.prob_base, b.nprob, g);
+    int cur = -1;
+    for (long long g = base + threadIdx.x; g < end; g += blockDim.x) {
+        const int p = pfirst == plast ? pfirst : find_problem(b.prob_base, b.nprob, g);
+        if (p != cur) {
+            if (cur >= 0) {
+                add_diag(b.prob[cur].diag, v);
+                for (int k = 0; k < 9; ++k) v[k] = 0.0;
+            }
+            cur = p;
+        }
         const ProbStatic &ps = b.prob[p];
         const PhysParams &ph = ps.ph;
         long long i = g - ps.base;
@@ -112,22 +165,17 @@ __global__ void k_kick_close(BatchView b, int do_kick)
             }
         }
         double m = ps.m[i];
-        v[0] = m;
-        v[1] = m * vel[0];
-        v[2] = m * vel[1];
-        v[3] = m * vel[2];
-        v[4] = m * (0.5 * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]) + (adi ? u : 0.0));
-        v[5] = m * a[0];
-        v[6] = m * a[1];
-        v[7] = m * a[2];
-        v[8] = m * (vel[0] * a[0] + vel[1] * a[1] + vel[2] * a[2] + (adi ? du : 0.0));
+        v[0] += m;
+        v[1] += m * vel[0];
+        v[2] += m * vel[1];
+        v[3] += m * vel[2];
+        v[4] += m * (0.5 * (vel[0] * vel[0] + vel[1] * vel[1] + vel[2] * vel[2]) + (adi ? u : 0.0));
+        v[5] += m * a[0];
+        v[6] += m * a[1];
+        v[7] += m * a[2];
+        v[8] += m * (vel[0] * a[0] + vel[1] * a[1] + vel[2] * a[2] + (adi ? du : 0.0));
     }
-    if (threadIdx.x == 0) p0s = p;
-    __syncthreads();
-    const int p0 = p0s;
-    const bool uni = __syncthreads_and(p == p0 || p == -1);
-    if (uni) {
-        if (p0 < 0) return;
+    if (pfirst == plast) {
         for (int k = 0; k < 9; ++k) {
             double x = warp_sum(v[k]);
             if ((threadIdx.x & 31) == 0) red[k][threadIdx.x >> 5] = x;
@@ -136,31 +184,14 @@ __global__ void k_kick_close(BatchView b, int do_kick)
         if (threadIdx.x < 9) {
             double t = 0;
             for (int w = 0; w < kRedThreads / 32; ++w) t += red[threadIdx.x][w];
-            ProbDiag *d = b.prob[p0].diag;
+            ProbDiag *d = b.prob[pfirst].diag;
             double *dst[9] = {&d->mass, &d->mom[0], &d->mom[1], &d->mom[2], &d->energy,
                               &d->fsum[0], &d->fsum[1], &d->fsum[2], &d->dEdt};
             atomicAdd(dst[threadIdx.x], t);
         }
-    } else if (p >= 0) {
-        ProbDiag *d = b.prob[p].diag;
-        double *dst[9] = {&d->mass, &d->mom[0], &d->mom[1], &d->mom[2], &d->energy,
-                          &d->fsum[0], &d->fsum[1], &d->fsum[2], &d->dEdt};
-        for (int k = 0; k < 9; ++k) atomicAdd(dst[k], v[k]);
+    } else if (cur >= 0) {
+        add_diag(b.prob[cur].diag, v);
     }
-}
-
-__global__ void k_finish(BatchView b, int advanced, int forces_ran)
-{
-    int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= b.nprob) return;
-    ProbDiag *d = b.prob[p].diag;
-    if (forces_ran) d->dt_next = __longlong_as_double((long long)d->dt_min_bits);
-    if (b.counters[15]) atomicOr(&d->status, ST_TIMEOUT);
-    if (advanced) {
-        d->time += d->dt_cur;
-        d->steps += 1;
-    }
-    d->leaves = b.dyn[p].nleaf;
 }
 
 }  // namespace
@@ -171,23 +202,18 @@ cudaError_t launch_reset_step(const BatchView &b, int mode, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_select_dt(const BatchView &b, double dt_host, cudaStream_t st)
+cudaError_t launch_kick_drift(const BatchView &b, double dt_host, cudaStream_t st)
 {
-    k_select_dt<<<(b.nprob + 127) / 128, 128, 0, st>>>(b, dt_host);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_kick_drift(const BatchView &b, cudaStream_t st)
-{
-    if (b.ntot == 0) return cudaSuccess;
-    k_kick_drift<<<(unsigned)((b.ntot + 255) / 256), 256, 0, st>>>(b);
+    const long long blocks = b.ntot > 0 ? (b.ntot + 255) / 256 : 1;
+    k_kick_drift<<<(unsigned)blocks, 256, 0, st>>>(b, dt_host);
     return cudaGetLastError();
 }
 
 cudaError_t launch_kick_close(const BatchView &b, int do_kick, int forces_ran, cudaStream_t st)
 {
-    if (b.ntot > 0) k_kick_close<<<(unsigned)((b.ntot + kRedThreads - 1) / kRedThreads), kRedThreads, 0, st>>>(b, do_kick);
-    k_finish<<<(b.nprob + 127) / 128, 128, 0, st>>>(b, do_kick, forces_ran);
+    const long long per = (long long)kRedThreads * kCloseItems;
+    const long long blocks = b.ntot > 0 ? (b.ntot + per - 1) / per : 1;
+    k_kick_close<<<(unsigned)blocks, kRedThreads, 0, st>>>(b, do_kick, forces_ran);
     return cudaGetLastError();
 }
 

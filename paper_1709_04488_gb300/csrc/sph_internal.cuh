@@ -122,7 +122,6 @@ struct BatchView {
     unsigned long long *keys[2];
     unsigned *vals[2];
     unsigned *hist;              // sort: digit histograms, tile counters, look-back status
-    unsigned *scan_aux;
     int *perm;                   // sorted position -> batch-global original index
     // sorted FP64 copies
     double *sx, *sy, *sz, *sh, *sm;
@@ -138,9 +137,16 @@ struct BatchView {
     unsigned *flag;              // [ntot] leaf start flags, then leaf index (scan)
     int *leaf_start;             // [max_leaves + 1]
     int *leaf_pid;               // [max_leaves]
-    double *leaf_c;              // [3 * max_leaves] leaf centres (FP64), SoA
+    double *leaf_c;              // [3 * max_leaves] leaf reference points (FP64)
+    float *leaf_cf;              // [6 * max_leaves] the same rounded down (xyz) and up (xyz)
+    float *hf;                   // [ntot] h after the density solve, float rounded up
     NodeBox *nodes[kMaxLevels + 1];  // level 0 = leaves
     int node_cap[kMaxLevels + 1];
+    // state that must be zero before a build; the kernels clear what they use
+    unsigned *tile_state;        // leaf scan: ticket, finished tiles, look-back status per tile
+    int *node_ctr[kMaxLevels + 1];  // arrival counters of the nodes of levels 1..
+    char *zero_lo;               // [zero_lo, zero_lo + zero_bytes) holds the two above
+    size_t zero_bytes;
     int *fallback_list;          // [ntot] sorted indices needing the slow path
     int *counters;               // [32]: 0 leaves, 1..7 nodes per level, 8 slow-path count,
                                  // 15 sort timeout, 16.. work counters per kernel class
@@ -227,11 +233,10 @@ cudaError_t launch_radix_sort(const BatchView &b, cudaStream_t st);
 cudaError_t launch_gather(const BatchView &b, cudaStream_t st);
 cudaError_t launch_set_sorted_h(const BatchView &b, const double *h_in, cudaStream_t st);
 cudaError_t launch_build_leaves(const BatchView &b, int precision, cudaStream_t st);
-cudaError_t launch_refit(const BatchView &b, cudaStream_t st);
+cudaError_t launch_refit(const BatchView &b, int precision, cudaStream_t st);
 cudaError_t launch_density(const BatchView &b, int precision, int use_pred, cudaStream_t st);
 cudaError_t launch_forces(const BatchView &b, int precision, cudaStream_t st);
-cudaError_t launch_select_dt(const BatchView &b, double dt_host, cudaStream_t st);
-cudaError_t launch_kick_drift(const BatchView &b, cudaStream_t st);
+cudaError_t launch_kick_drift(const BatchView &b, double dt_host, cudaStream_t st);  // also selects dt, resets diagnostics
 cudaError_t launch_kick_close(const BatchView &b, int do_kick, int forces_ran, cudaStream_t st);
 cudaError_t launch_reset_step(const BatchView &b, int mode, cudaStream_t st);  // mode 1 full, 2 forces only
 cudaError_t launch_neighbour_export(const BatchView &b, int kind, const double *h_in, long long *offsets,
@@ -264,6 +269,7 @@ int status_to_code(unsigned st);
 
 // upper bounds used to size grids and workspaces
 long long leaves_upper_bound(long long n);
+long long leaf_tiles(long long n);  // tiles of the leaf scan
 int levels_needed(long long max_leaves);
 
 }  // namespace sph

@@ -131,13 +131,14 @@ extern "C" int sph_density_forces_noalloc(const sph_params *p, int64_t n, const 
     } while (0)
     k_noalloc_init<<<1, 32, 0, st>>>(b, ps);
     NA_TRY(cudaGetLastError());
+    NA_TRY(cudaMemsetAsync(b.zero_lo, 0, b.zero_bytes, st));
     NA_TRY(launch_reset_step(b, 1, st));
     NA_TRY(launch_domain_and_keys(b, st));
     NA_TRY(launch_radix_sort(b, st));
     NA_TRY(launch_gather(b, st));
     NA_TRY(launch_build_leaves(b, prec, st));
     NA_TRY(launch_density(b, prec, 0, st));
-    NA_TRY(launch_refit(b, st));
+    NA_TRY(launch_refit(b, prec, st));
     NA_TRY(launch_forces(b, prec, st));
     NA_TRY(launch_kick_close(b, 0, 1, st));
     if (p->flags & SPH_FLAG_ASYNC) return SPH_OK;

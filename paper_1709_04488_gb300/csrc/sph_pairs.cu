@@ -37,13 +37,16 @@ constexpr double kListMargin = 1.03;  // list radius = 2 h * margin
 #define SPH_FORCE_CH 64
 #endif
 #ifndef SPH_FORCE_MINB
-#define SPH_FORCE_MINB 6
+#define SPH_FORCE_MINB 5
 #endif
 #ifndef SPH_DENS_CH
 #define SPH_DENS_CH 128
 #endif
 #ifndef SPH_DENS_MINB
 #define SPH_DENS_MINB 4
+#endif
+#ifndef SPH_DENS_LCAP1
+#define SPH_DENS_LCAP1 104  // list entries per lane at one lane per particle
 #endif
 constexpr int kMaxRebuild = 6;
 
@@ -102,6 +105,9 @@ __device__ __forceinline__ double add_rn<double>(double a, double b) { return __
 // both sides of a pair get the same bits (fast reciprocal in FP32)
 __device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
+
+__device__ __forceinline__ float to_float_ru(float v) { return v; }
+__device__ __forceinline__ float to_float_ru(double v) { return __double2float_ru(v); }
 
 // sorted particle index carried in the w slot of a staged vector: bit
 // pattern in FP32 staging (only ever copied), exact value in FP64 staging
@@ -339,7 +345,7 @@ template <typename T, int LPP, bool UM>
 struct DCfg {
     using V = typename Vec4<T>::type;
     // list entries per lane: room for ~2x the mean neighbour count of 58 per particle
-    static constexpr int LCAP = LPP == 1 ? 104 : LPP == 2 ? 64 : LPP == 4 ? 40 : 24;
+    static constexpr int LCAP = LPP == 1 ? SPH_DENS_LCAP1 : LPP == 2 ? 64 : LPP == 4 ? 40 : 24;
     static constexpr int CH = SPH_DENS_CH;
     static constexpr int WPB = 4;
     static constexpr int NOWN = 32 * (32 / LPP);  // particles of a group of 32 candidate leaves
@@ -376,6 +382,7 @@ __device__ __forceinline__ void density_epilogue(const BatchView &b, const ProbS
     }
     T A = P / (omega * rho * rho);
     b.sh[s] = (double)h;
+    b.hf[s] = to_float_ru(h);
     b.srho[s] = (double)rho;
     b.somega[s] = (double)omega;
     b.sP[s] = (double)P;
@@ -924,13 +931,19 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, SPH_FORCE_MINB) k_forc
         frame_box<V, T>(xi, active, flo, fhi);
         int nbuf = 0, cnt = 0, ntab = 0, tA = -1;
         unsigned gmask = 0u;
+        auto fetch = [&](int e, V &tb, V &a0, V &a1, V &a2) {
+            const unsigned cd = lst[e * 32 + lane];
+            tb = table[cd >> 5];
+            const int j = t_as_bits(tb.w) + (int)(cd & 31u);
+            a0 = ld_ro(gph + j);
+            a1 = ld_ro(gvc + j);
+            a2 = ld_ro(gth + j);
+        };
         auto eval_lists = [&]() {
             __syncwarp();
             for (int e = 0; e < cnt; ++e) {
-                const unsigned cd = lst[e * 32 + lane];
-                const V tb = table[cd >> 5];
-                const int j = t_as_bits(tb.w) + (int)(cd & 31u);
-                const V a0 = ld_ro(gph + j), a1 = ld_ro(gvc + j), a2 = ld_ro(gth + j);
+                V tb, a0, a1, a2;
+                fetch(e, tb, a0, a1, a2);
                 // r_ij = (o_i - o_j) - D_AB: IEEE subtraction is sign-symmetric and
                 // D_BA = -D_AB exactly, so particle j forms exactly -r_ij
                 T rx = (xi.x - a0.x) - tb.x, ry = (xi.y - a0.y) - tb.y, rz = (xi.z - a0.z) - tb.z;

@@ -142,6 +142,7 @@ __global__ void k_domain(BatchView b)
 // their global offsets by a decoupled look-back over the earlier tiles.
 constexpr unsigned kFlagAgg = 1u << 30, kFlagPre = 2u << 30, kCountMask = (1u << 30) - 1u;
 constexpr long long kSpinLimit = 1ll << 24;
+constexpr int kLookBack = 8;
 
 __device__ __forceinline__ unsigned morton_key_code(const BatchView &b, int p, long long g)
 {
@@ -234,21 +235,35 @@ __global__ void k_onesweep(const unsigned long long *kin, const unsigned *vin, u
         run[t] = gstart;
     } else {
         atomicExch(&st[t], kFlagAgg | mine);
+        // look back over the earlier tiles' counts of digit t, kLookBack
+        // predecessors per round (their loads in flight together)
         unsigned excl = 0u;
         long long spins = 0;
         for (int pred = tile - 1; pred >= 0;) {
-            unsigned v = *(volatile unsigned *)(status + (long long)pred * 256 + t);
-            unsigned f = v & ~kCountMask;
-            if (f == 0u) {
-                if (++spins > kSpinLimit) {
-                    atomicOr(timeout_flag, 1u);
-                    break;
+            unsigned v[kLookBack];
+#pragma unroll
+            for (int k = 0; k < kLookBack; ++k)
+                v[k] = pred - k >= 0 ? (unsigned)*(volatile unsigned *)(status + (long long)(pred - k) * 256 + t) : (unsigned)kFlagPre;
+            int used = 0;
+            bool done = false, pending = false;
+#pragma unroll
+            for (int k = 0; k < kLookBack; ++k) {
+                if (done || pending) continue;
+                const unsigned f = v[k] & ~kCountMask;
+                if (f == 0u) {
+                    pending = true;
+                    continue;
                 }
-                continue;
+                excl += v[k] & kCountMask;
+                ++used;
+                if (f == kFlagPre) done = true;
             }
-            excl += v & kCountMask;
-            if (f == kFlagPre) break;
-            --pred;
+            if (done) break;
+            pred -= used;
+            if (pending && ++spins > kSpinLimit) {
+                atomicOr(timeout_flag, 1u);
+                break;
+            }
         }
         atomicExch(&st[t], kFlagPre | (excl + mine));
         run[t] = gstart + excl;
