@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kLeafThreads) k_leaf_scan(BatchView b)
                 const unsigned need = np == 31 ? 0xffffffffu : ((1u << (np + 1)) - 1u);
                 if (pend & need) {
                     if (++spins > kTileSpinLimit) {
-                        if (lane == 0) atomicExch(&b.counters[15], 1);  // reported as a timeout
+                        if (lane == 0) atomicExch(&b.counters[kTimeoutCounter], 1);  // reported as a timeout
                         break;
                     }
                     continue;

@@ -14,7 +14,7 @@ namespace {
 
 constexpr int kRedThreads = 256;
 
-constexpr int kCloseItems = 8;  // particles per thread in the closing kernel
+constexpr int kCloseItems = 8;  // most particles per thread in the closing kernel
 
 __device__ void reset_diag(const BatchView &b, int p, int mode)
 {
@@ -38,10 +38,21 @@ __device__ void reset_diag(const BatchView &b, int p, int mode)
     d->unconverged = 0;
 }
 
+// Clear the per-call counters (block 0, first 32 threads): mode 1 all of a
+// step's, mode 2 those of a forces-only call.
+__device__ __forceinline__ void reset_counters(const BatchView &b, int mode)
+{
+    const int k = threadIdx.x;
+    if (blockIdx.x != 0 || k >= 32) return;
+    const bool all = k == kSlowCounter || k == kTimeoutCounter || (k >= kDensityCounter && k < kForceCounter + 4);
+    const bool forces = k == kTimeoutCounter || (k >= kForceCounter && k < kForceCounter + 4);
+    if (mode == 1 ? all : forces) b.counters[k] = 0;
+}
+
 __global__ void k_reset_step(BatchView b, int mode)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p == 0) b.counters[15] = 0;  // sort look-back timeout flag
+    reset_counters(b, mode);
     if (p < b.nprob) reset_diag(b, p, mode);
 }
 
@@ -55,8 +66,8 @@ __device__ __forceinline__ double step_dt(const ProbDiag *d, double dt_host)
 // 0 also selects each problem's step and resets its diagnostics.
 __global__ void k_kick_drift(BatchView b, double dt_host)
 {
+    reset_counters(b, 1);
     if (blockIdx.x == 0) {
-        if (threadIdx.x == 0) b.counters[15] = 0;
         for (int p = threadIdx.x; p < b.nprob; p += blockDim.x) {
             ProbDiag *d = b.prob[p].diag;
             const double dt = step_dt(d, dt_host);
@@ -105,13 +116,13 @@ __device__ __forceinline__ void add_diag(ProbDiag *d, const double *v)
 }
 
 // Closing half kick (Eq. LFKDK2, optional) and the FP64 reductions per
-// problem: each block takes kCloseItems * blockDim consecutive particles and
+// problem: each block takes items * blockDim consecutive particles and
 // sums them per problem in registers, then reduces over the block when the
 // whole block is in one problem (one set of atomics per block), else adds per
 // thread.  Block 0 also finishes each problem's step record (CFL step of the
 // forces just computed, time, step count, leaf count), which reads nothing
 // this kernel writes.
-__global__ void k_kick_close(BatchView b, int do_kick, int forces_ran)
+__global__ void k_kick_close(BatchView b, int do_kick, int forces_ran, int items)
 {
     __shared__ double red[9][kRedThreads / 32];
     __shared__ int pfirst, plast;
@@ -119,7 +130,7 @@ __global__ void k_kick_close(BatchView b, int do_kick, int forces_ran)
         for (int p = threadIdx.x; p < b.nprob; p += blockDim.x) {
             ProbDiag *d = b.prob[p].diag;
             if (forces_ran) d->dt_next = __longlong_as_double((long long)d->dt_min_bits);
-            if (b.counters[15]) atomicOr(&d->status, ST_TIMEOUT);
+            if (b.counters[kTimeoutCounter]) atomicOr(&d->status, ST_TIMEOUT);
             if (do_kick) {
                 d->time += d->dt_cur;
                 d->steps += 1;
@@ -127,9 +138,9 @@ __global__ void k_kick_close(BatchView b, int do_kick, int forces_ran)
             d->leaves = b.dyn[p].nleaf;
         }
     }
-    const long long base = (long long)blockIdx.x * blockDim.x * kCloseItems;
+    const long long base = (long long)blockIdx.x * blockDim.x * items;
     if (base >= b.ntot) return;
-    const long long end = base + (long long)blockDim.x * kCloseItems < b.ntot ? base + (long long)blockDim.x * kCloseItems : b.ntot;
+    const long long end = base + (long long)blockDim.x * items < b.ntot ? base + (long long)blockDim.x * items : b.ntot;
     if (threadIdx.x == 0) {
         pfirst = find_problem(b.prob_base, b.nprob, base);
         plast = find_problem(b.prob_base, b.nprob, end - 1);
@@ -211,9 +222,13 @@ cudaError_t launch_kick_drift(const BatchView &b, double dt_host, cudaStream_t s
 
 cudaError_t launch_kick_close(const BatchView &b, int do_kick, int forces_ran, cudaStream_t st)
 {
-    const long long per = (long long)kRedThreads * kCloseItems;
+    // enough blocks to fill the GPU twice, up to kCloseItems particles a thread
+    const long long fill = 2LL * dev_info().sm_count * kRedThreads;
+    long long items = (b.ntot + fill - 1) / fill;
+    items = items < 1 ? 1 : items > kCloseItems ? kCloseItems : items;
+    const long long per = (long long)kRedThreads * items;
     const long long blocks = b.ntot > 0 ? (b.ntot + per - 1) / per : 1;
-    k_kick_close<<<(unsigned)blocks, kRedThreads, 0, st>>>(b, do_kick, forces_ran);
+    k_kick_close<<<(unsigned)blocks, kRedThreads, 0, st>>>(b, do_kick, forces_ran, (int)items);
     return cudaGetLastError();
 }
 

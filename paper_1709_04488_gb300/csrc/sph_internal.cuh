@@ -15,6 +15,11 @@ constexpr int kBranch = 32;         // children per tree node (one per warp lane
 constexpr int kMortonBits = 10;     // bits per axis of the Morton key
 constexpr int kMortonTotal = 3 * kMortonBits;
 constexpr double kPi = 3.14159265358979323846;
+// slots of BatchView::counters: 0 leaves, 1..7 nodes per level, 8 slow-path
+// count, 15 look-back timeout, 16..23 density leaf tickets (per class),
+// 24..27 force leaf tickets (per lanes per particle); the step's first
+// kernel clears 8, 15 and 16..27, a forces-only call clears 15 and 24..27
+constexpr int kSlowCounter = 8, kTimeoutCounter = 15, kDensityCounter = 16, kForceCounter = 24;
 
 // Status bits kept on the device per problem (mapped to SPH_E* on the host).
 enum : unsigned {
@@ -148,8 +153,7 @@ struct BatchView {
     char *zero_lo;               // [zero_lo, zero_lo + zero_bytes) holds the two above
     size_t zero_bytes;
     int *fallback_list;          // [ntot] sorted indices needing the slow path
-    int *counters;               // [32]: 0 leaves, 1..7 nodes per level, 8 slow-path count,
-                                 // 15 sort timeout, 16.. work counters per kernel class
+    int *counters;               // [32], slots as listed at kSlowCounter
     long long *scratch64;        // [8]
 };
 

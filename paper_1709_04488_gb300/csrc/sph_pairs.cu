@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM>::WPB * 32, SPH_DENS_MINB) k_d
 
     for (;;) {
         int leaf = 0;
-        if (lane == 0) leaf = atomicAdd(&b.counters[16 + lpp_log2(LPP) + (UM ? 4 : 0)], 1);
+        if (lane == 0) leaf = atomicAdd(&b.counters[kDensityCounter + lpp_log2(LPP) + (UM ? 4 : 0)], 1);
         leaf = __shfl_sync(FULL, leaf, 0);
         if (leaf >= nleaf) break;
         const int p = b.leaf_pid[leaf];
@@ -620,7 +620,7 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM>::WPB * 32, SPH_DENS_MINB) k_d
             }
         }
         if (active && fail && sub == 0) {
-            int k = atomicAdd(&b.counters[8], 1);
+            int k = atomicAdd(&b.counters[kSlowCounter], 1);
             b.fallback_list[k] = (int)s;
             b.sh[s] = (double)h;  // best guess so far
         }
@@ -679,7 +679,7 @@ __global__ void __launch_bounds__(FbCfg<T>::WPB * 32) k_density_fallback(BatchVi
     T *fr = reinterpret_cast<T *>(mine + kFbCH * sizeof(V));
     T *fm = fr + kFbPerLane * 32;
     StageScratch<T, 1024> &sc = *reinterpret_cast<StageScratch<T, 1024> *>(fm + kFbPerLane * 32);
-    const int nf = b.counters[8];
+    const int nf = b.counters[kSlowCounter];
     const V *pm = (const V *)b.pm;
     int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     for (int k = w; k < nf; k += nw) {
@@ -905,7 +905,7 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, SPH_FORCE_MINB) k_forc
 
     for (;;) {
         int leaf = 0;
-        if (lane == 0) leaf = atomicAdd(&b.counters[16 + lpp_log2(LPP)], 1);
+        if (lane == 0) leaf = atomicAdd(&b.counters[kForceCounter + lpp_log2(LPP)], 1);
         leaf = __shfl_sync(FULL, leaf, 0);
         if (leaf >= nleaf) break;
         const int p = b.leaf_pid[leaf];
@@ -1091,7 +1091,6 @@ cudaError_t run_density(const BatchView &b, int use_pred, cudaStream_t st)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_density<T, LPP, UM>, C::WPB * 32, C::smem);
         if (per_sm < 1) per_sm = 1;
     }
-    cudaMemsetAsync(b.counters + 16 + lpp_log2(LPP) + (UM ? 4 : 0), 0, sizeof(int), st);
     k_density<T, LPP, UM><<<dev_info().sm_count * per_sm, C::WPB * 32, C::smem, st>>>(b, use_pred);
     return cudaGetLastError();
 }
@@ -1136,7 +1135,6 @@ cudaError_t run_forces(const BatchView &b, cudaStream_t st)
 cudaError_t launch_density(const BatchView &b, int precision, int use_pred, cudaStream_t st)
 {
     if (b.ntot == 0) return cudaSuccess;
-    cudaMemsetAsync(b.counters + 8, 0, sizeof(int), st);  // slow-path count
     for (int cls = 0; cls < 8; ++cls) {
         if (!(b.dens_mask & (1 << cls))) continue;
         const int k = cls & 3;
@@ -1164,7 +1162,6 @@ cudaError_t launch_forces(const BatchView &b, int precision, cudaStream_t st)
     if (b.ntot == 0) return cudaSuccess;
     for (int k = 0; k < 4; ++k) {
         if (!(b.lpp_mask & (1 << k))) continue;
-        cudaMemsetAsync(b.counters + 16 + k, 0, sizeof(int), st);
         cudaError_t e;
         if (precision == SPH_PREC_FP64) {
             if (k == 2) e = run_forces<double, 4>(b, st);

@@ -333,7 +333,7 @@ cudaError_t launch_radix_sort(const BatchView &b, cudaStream_t st)
         unsigned *vdst = last ? (unsigned *)b.perm : b.vals[src ^ 1];
         k_onesweep<<<ntile, kSortThreads, 0, st>>>(b.keys[src], b.vals[src], b.keys[src ^ 1], vdst, n, 8 * pass,
                                                    hist + pass * 256, status + (size_t)pass * ntile * 256,
-                                                   ctr + pass, pass == 0, (unsigned *)&b.counters[15]);
+                                                   ctr + pass, pass == 0, (unsigned *)&b.counters[kTimeoutCounter]);
         src ^= 1;
     }
     if (src != 0) {
