@@ -40,13 +40,13 @@ constexpr double kListMargin = 1.03;  // list radius = 2 h * margin
 #define SPH_FORCE_MINB 5
 #endif
 #ifndef SPH_DENS_CH
-#define SPH_DENS_CH 128
+#define SPH_DENS_CH 64
 #endif
 #ifndef SPH_DENS_MINB
 #define SPH_DENS_MINB 4
 #endif
 #ifndef SPH_DENS_LCAP1
-#define SPH_DENS_LCAP1 104  // list entries per lane at one lane per particle
+#define SPH_DENS_LCAP1 96  // list entries per lane at one lane per particle
 #endif
 constexpr int kMaxRebuild = 6;
 
@@ -198,15 +198,26 @@ __device__ __forceinline__ int warp_incl_scan(int v)
     return v;
 }
 
-// Per-warp scratch for staging one group of up to 32 candidate leaves of at
-// most NOWN / 32 particles each.
-template <typename T, int NOWN>
+// Per-warp scratch for staging one group of up to 32 candidate leaves.
+template <typename T>
 struct StageScratch {
-    unsigned char owner[NOWN];  // candidate leaf (lane of the group) of each particle of the group
-    int first[32];              // group element index of each candidate leaf's first particle
-    int start[32];              // sorted index of each candidate leaf's first particle
-    T dx[32], dy[32], dz[32];   // leaf shift (FP64 difference of reference points, cast)
+    int first[32];             // group element index of each candidate leaf's first particle
+    int start[32];             // sorted index of each candidate leaf's first particle
+    T dx[32], dy[32], dz[32];  // leaf shift (FP64 difference of reference points, cast)
 };
+
+// candidate leaf (lane of the group) holding group element e: the last lane
+// whose first element is <= e (lanes without particles share the next
+// lane's first element and are passed over)
+template <typename T>
+__device__ __forceinline__ int owner_of(const StageScratch<T> &sc, int e)
+{
+    int k = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1)
+        if (sc.first[k + step] <= e) k += step;
+    return k;
+}
 
 // Squared distance from point q to the box [lo, hi] (zero inside).
 template <typename T, typename V>
@@ -227,9 +238,9 @@ __device__ __forceinline__ T box_dist2(const V &q, const V &lo, const V &hi)
 // keep(q) sees them.  group(has, B, stB, D) runs on every lane once per call
 // (lane k: candidate leaf first + k if has); store(slot, q, k, idx) writes a
 // kept particle (k: its leaf's lane, idx: its index within that leaf).
-template <typename T, int CH, int NOWN, class Group, class Load, class Keep, class Store, class Flush>
+template <typename T, int CH, class Group, class Load, class Keep, class Store, class Flush>
 __device__ __forceinline__ void stage_group(const BatchView &b, int A, unsigned mask, int first, const PhysParams &ph,
-                                            int &nbuf, StageScratch<T, NOWN> &sc, Group &&group, Load &&load,
+                                            int &nbuf, StageScratch<T> &sc, Group &&group, Load &&load,
                                             Keep &&keep, Store &&store, Flush &&flush)
 {
     using V = typename Vec4<T>::type;
@@ -250,15 +261,11 @@ __device__ __forceinline__ void stage_group(const BatchView &b, int A, unsigned 
     const int incl = warp_incl_scan<T>(nB);
     const int tot = __shfl_sync(FULL, incl, 31);
     __syncwarp();  // earlier readers of the scratch are done
-    if (has) {
-        const int off = incl - nB;
-        for (int t = 0; t < nB; ++t) sc.owner[off + t] = (unsigned char)lane;
-        sc.first[lane] = off;
-        sc.start[lane] = stB;
-        sc.dx[lane] = Dx;
-        sc.dy[lane] = Dy;
-        sc.dz[lane] = Dz;
-    }
+    sc.first[lane] = incl - nB;
+    sc.start[lane] = stB;
+    sc.dx[lane] = Dx;
+    sc.dy[lane] = Dy;
+    sc.dz[lane] = Dz;
     __syncwarp();
     const unsigned below = (1u << lane) - 1u;
     for (int e0 = 0; e0 < tot; e0 += 32) {
@@ -268,7 +275,7 @@ __device__ __forceinline__ void stage_group(const BatchView &b, int A, unsigned 
         V q;
         int k = 0, idx = 0;
         if (e < tot) {
-            k = sc.owner[e];
+            k = owner_of(sc, e);
             idx = e - sc.first[k];
             q = load(sc.start[k] + idx);
             q.x += sc.dx[k];
@@ -348,9 +355,8 @@ struct DCfg {
     static constexpr int LCAP = LPP == 1 ? SPH_DENS_LCAP1 : LPP == 2 ? 64 : LPP == 4 ? 40 : 24;
     static constexpr int CH = SPH_DENS_CH;
     static constexpr int WPB = 4;
-    static constexpr int NOWN = 32 * (32 / LPP);  // particles of a group of 32 candidate leaves
     static constexpr int LW = UM ? 1 : 2;  // list words per entry: r (and m_j unless masses are equal)
-    static constexpr size_t scratch = (sizeof(StageScratch<T, NOWN>) + 31) & ~(size_t)31;
+    static constexpr size_t scratch = (sizeof(StageScratch<T>) + 31) & ~(size_t)31;
     static constexpr size_t per_warp = CH * sizeof(V) + (size_t)LCAP * 32 * LW * sizeof(T) + scratch;
     static constexpr size_t smem = WPB * per_warp;
 };
@@ -423,7 +429,7 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM>::WPB * 32, SPH_DENS_MINB) k_d
     V *cand = reinterpret_cast<V *>(mine);
     T *lr = reinterpret_cast<T *>(mine + C::CH * sizeof(V));
     T *lm = lr + C::LCAP * 32;  // used only when masses differ
-    StageScratch<T, C::NOWN> &sc = *reinterpret_cast<StageScratch<T, C::NOWN> *>(lr + C::LCAP * 32 * C::LW);
+    StageScratch<T> &sc = *reinterpret_cast<StageScratch<T> *>(lr + C::LCAP * 32 * C::LW);
     const int pp = lane / LPP, sub = lane % LPP;
     const int nleaf = b.counters[0];
     const V *pm = (const V *)b.pm;
@@ -662,7 +668,7 @@ template <typename T>
 struct FbCfg {
     using V = typename Vec4<T>::type;
     static constexpr int WPB = 4;
-    static constexpr size_t scratch = (sizeof(StageScratch<T, 1024>) + 31) & ~(size_t)31;
+    static constexpr size_t scratch = (sizeof(StageScratch<T>) + 31) & ~(size_t)31;
     static constexpr size_t per_warp = kFbCH * sizeof(V) + (size_t)2 * kFbPerLane * 32 * sizeof(T) + scratch;
     static constexpr size_t smem = WPB * per_warp;
 };
@@ -678,7 +684,7 @@ __global__ void __launch_bounds__(FbCfg<T>::WPB * 32) k_density_fallback(BatchVi
     V *cand = reinterpret_cast<V *>(mine);
     T *fr = reinterpret_cast<T *>(mine + kFbCH * sizeof(V));
     T *fm = fr + kFbPerLane * 32;
-    StageScratch<T, 1024> &sc = *reinterpret_cast<StageScratch<T, 1024> *>(fm + kFbPerLane * 32);
+    StageScratch<T> &sc = *reinterpret_cast<StageScratch<T> *>(fm + kFbPerLane * 32);
     const int nf = b.counters[kSlowCounter];
     const V *pm = (const V *)b.pm;
     int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
@@ -835,17 +841,27 @@ __global__ void __launch_bounds__(FbCfg<T>::WPB * 32) k_density_fallback(BatchVi
 #ifndef SPH_FORCE_TAB
 #define SPH_FORCE_TAB 128
 #endif
+#ifndef SPH_FORCE_SB
+#define SPH_FORCE_SB 32
+#endif
+#ifndef SPH_FORCE_LC1
+#define SPH_FORCE_LC1 96
+#endif
+#ifndef SPH_FORCE_SB1
+#define SPH_FORCE_SB1 8
+#endif
 template <typename T, int LPP>
 struct FCfg {
     using V = typename Vec4<T>::type;
     static constexpr int CH = SPH_FORCE_CH;
-    static constexpr int LC = SPH_FORCE_LC;    // list entries per lane
+    // list entries per lane, and candidates tested per list-room check: at
+    // one lane per particle a lane holds all of its particle's ~60 pairs
+    static constexpr int LC = LPP == 1 ? SPH_FORCE_LC1 : SPH_FORCE_LC;
+    static constexpr int SB = LPP == 1 ? SPH_FORCE_SB1 : SPH_FORCE_SB;
     static constexpr int TAB = SPH_FORCE_TAB;  // candidate leaves per table fill (<= 2048)
-    static constexpr int SB = 32;              // candidates tested per list-room check
-    static constexpr int NOWN = 32 * (32 / LPP);
     static constexpr int WPB = 4;
     static_assert(TAB <= 2048 && LC >= 2 * SB / LPP, "force list layout");
-    static constexpr size_t scratch = (sizeof(StageScratch<T, NOWN>) + 31) & ~(size_t)31;
+    static constexpr size_t scratch = (sizeof(StageScratch<T>) + 31) & ~(size_t)31;
     static constexpr size_t codes = ((size_t)(CH + LC * 32) * 2 + 31) & ~(size_t)31;
     static constexpr size_t per_warp = (CH + TAB) * sizeof(V) + scratch + codes;
     static constexpr size_t smem = WPB * per_warp;
@@ -895,7 +911,7 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, SPH_FORCE_MINB) k_forc
     unsigned char *mine = smem + wib * C::per_warp;
     V *cand = reinterpret_cast<V *>(mine);  // staged (offset + leaf shift, 1/h)
     V *table = cand + C::CH;                // per candidate leaf: (leaf shift, first sorted index)
-    StageScratch<T, C::NOWN> &sc = *reinterpret_cast<StageScratch<T, C::NOWN> *>(table + C::TAB);
+    StageScratch<T> &sc = *reinterpret_cast<StageScratch<T> *>(table + C::TAB);
     unsigned short *code = reinterpret_cast<unsigned short *>(mine + (C::CH + C::TAB) * sizeof(V) + C::scratch);
     unsigned short *lst = code + C::CH;
     const int pp = lane / LPP, sub = lane % LPP;
