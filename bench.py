@@ -63,16 +63,26 @@ def workload(name="sod"):
     return {"sod": ics.sod, "sedov": ics.sedov, "cloud": ics.cloud}[name]()
 
 
-def traffic_for(kernel_src, workload):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, if the kernel source is unchanged since that capture."""
+def kernel_source_sha(srcs):
+    """sha256 over the pair kernels' sources (kernels and their tuned shape)."""
     import hashlib
+    h = hashlib.sha256()
+    for src in srcs:
+        with open(src, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+PAIR_SOURCES = [os.path.join(ROOT, "paper_1709_04488_gb300", "csrc", f) for f in ("sph_pairs.cu", "sph_tuned.h")]
+
+
+def traffic_for(workload):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if the kernel sources are unchanged since that capture."""
     try:
         with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as fh:
             rec = json.load(fh).get(workload)
-        with open(kernel_src, "rb") as fh:
-            sha = hashlib.sha256(fh.read()).hexdigest()
-        if rec and rec.get("source_sha256") == sha:
+        if rec and rec.get("source_sha256") == kernel_source_sha(PAIR_SOURCES):
             return rec
     except Exception:
         pass
@@ -305,7 +315,7 @@ def run_ours(args):
     else:
         kern, flops, t_ms = "k_density", np.mean(dp) * FLOPS_DENSITY_PAIR, dens_ms
     achieved = flops / (t_ms * 1e-3) / 1e12
-    tr = traffic_for(os.path.join(ROOT, "paper_1709_04488_gb300", "csrc", "sph_pairs.cu"), args.workload)
+    tr = traffic_for(args.workload)
     traffic = None
     if tr and tr.get("kernel") == kern:
         traffic = tr["dram_bytes_per_launch"]

@@ -57,8 +57,8 @@ extern "C" {
 #define SPH_ENOSPACE -10    /* workspace too small                                 */
 
 /* ---- parameters -------------------------------------------------------- */
-#define SPH_EOS_ADIABATIC 0  /* P = (gamma-1) rho u, c = sqrt(gamma P / rho) (Sec. 2.2.1) */
-#define SPH_EOS_ISOTHERMAL 1 /* P = cs^2 rho, c = cs; u is not evolved (Sec. 4.2)         */
+#define SPH_EOS_ADIABATIC 0  /* P = (gamma-1) rho u, c = sqrt(gamma P / rho) (Sec. 2.1.1) */
+#define SPH_EOS_ISOTHERMAL 1 /* P = cs^2 rho, c = cs; u is not evolved (Sec. 6.2)         */
 
 #define SPH_PREC_FP64 0      /* every step in FP64 (the plain reference path)              */
 #define SPH_PREC_MIXED 1     /* FP32 pair arithmetic; FP64 positions, centre differences, */
@@ -86,7 +86,7 @@ typedef struct {
     double cs_iso;         /* isothermal sound speed                                   */
     double eta;            /* h = eta (m/rho)^(1/3), Eq. HRHO; paper default 1.2       */
     double alpha_av;       /* viscosity strength alpha_AV (paper: 1)                   */
-    double beta_av;        /* signal-speed factor beta_AV = 2 alpha_AV (Sec. 2.2.1)    */
+    double beta_av;        /* signal-speed factor beta_AV = 2 alpha_AV (Sec. 2.1.1)    */
     double alpha_ac;       /* conductivity strength alpha_AC (0 disables)              */
     double c_cfl;          /* Courant factor of Eq. SPH_DT (paper: ~0.2)               */
     double h_tol;          /* stop the h iteration when |dh|/h < h_tol (0: per precision)*/
@@ -111,7 +111,7 @@ typedef struct {
     double *ax, *ay, *az, *du, *vsig;
 } sph_state;
 
-/* Per-call diagnostics (FP64 reductions over the particles, Sec. 2.2.1
+/* Per-call diagnostics (FP64 reductions over the particles, Sec. 2.1.1
  * conservation; counters of the work done). */
 typedef struct {
     double mass;           /* sum m                                   */
@@ -184,7 +184,7 @@ int sph_sync(sph_ctx *ctx);
 /* Diagnostics of the last compute call (synchronises). */
 int sph_diagnostics(sph_ctx *ctx, sph_diag *out);
 
-/* Exact FP64 neighbour lists in CSR form, ids ascending (Sec. 2.6 tree walk
+/* Exact FP64 neighbour lists in CSR form, ids ascending (Sec. 4.2 tree walk
  * retrieves them per leaf).  kind 0: {j : |r_ij|^2 < (2 h_i)^2} including i;
  * kind 1: {j != i : |r_ij|^2 < (2 max(h_i,h_j))^2}.  h_in: device array of n
  * smoothing lengths to use (NULL: state->h).  Distances are formed in FP64 as
@@ -285,6 +285,18 @@ int sph_server_destroy(sph_server *s);
  *     calls whose work overlaps on the GPU (other streams, other threads)
  *     race with each other and must be serialised by the caller. */
 int sph_density_forces_noalloc(const sph_params *p, int64_t n, const sph_state *state, void *stream);
+
+/* Launch-shape table for contexts whose params leave lanes_per_particle and
+ * leaf_size at 0: a problem of n particles uses lanes[k] lanes per particle
+ * (leaf size 32 / lanes[k]) for the first row k with n <= n_max[k]; sizes
+ * beyond the last row, and every size when rows == 0 (the state at load
+ * time), use the built-in rule (4 lanes up to 200000 particles, else 1).
+ * The table is process-wide and copied; it applies to contexts set up after
+ * the call.  lanes[k] must be 1, 2, 4 or 8 and n_max must increase;
+ * otherwise SPH_EINVAL and the table is unchanged.  At most 32 rows.  The
+ * FP64 path clamps lanes to 2 or 4.  No counterpart in the paper: the
+ * package's autotuner measures the table on the GPU and installs it. */
+int sph_set_launch_table(const int64_t *n_max, const int32_t *lanes, int rows);
 
 /* Message describing the calling thread's last error ("" if none). */
 const char *sph_last_error(void);

@@ -1,6 +1,6 @@
 """Exact solution of the 1D Riemann problem for an ideal gas and for an
 isothermal gas (test infrastructure; used as the analytic pin for the
-shock-tube tests of Sec. 4.2, Figs. ADSOD/ISOSOD).
+shock-tube tests of Sec. 6.2, Figs. ADSOD/ISOSOD).
 
 Written from the textbook mathematics of the Riemann problem (pressure
 function across shocks and rarefactions, Newton iteration for the star

@@ -13,10 +13,10 @@
  *     Monaghan & Lattanzio (1985) M4 spline with 3D normalisation 1/pi.
  *   - Density sum, Eq. SPHRHO, and the h-rho relation, Eq. HRHO (eta = 1.2 by
  *     default), iterated to convergence by Newton-Raphson with a bisection
- *     fallback (Sec. 2.2.1; Newton-Raphson is named in Sec. 2.5 for the same
+ *     fallback (Sec. 2.1.1; Newton-Raphson is named in Sec. 4.1 for the same
  *     solve).
  *   - The grad-h correction Omega, Eq. OMEGA; pressure and sound speed from the
- *     adiabatic or isothermal EOS (Sec. 2.2.1, Sec. 4.2).
+ *     adiabatic or isothermal EOS (Sec. 2.1.1, Sec. 6.2).
  *   - Grad-h momentum equation, Eq. GRADHMOMEQN; energy equation, Eq.
  *     GRADHENEQN; Monaghan (1997) artificial viscosity and Wadsley (2008)
  *     conductivity, Eqs. MON97ARTVISC and MON97ENERGYDISS.

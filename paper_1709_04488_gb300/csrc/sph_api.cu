@@ -111,14 +111,27 @@ int mask_of(int lpp) { return lpp == 1 ? 1 : lpp == 2 ? 2 : lpp == 4 ? 4 : 8; }
 
 int dens_class_bit(int lpp, int uniform_m) { return mask_of(lpp) << (uniform_m ? 4 : 0); }
 
-// Launch shape per problem size (the autotuner's table; see autotune.py for
-// how the buckets were chosen).  Small problems spread a particle over more
-// lanes so that the GPU stays full.
+// Lanes per particle by problem size: a table of (largest n, lanes) rows
+// installed with sph_set_launch_table (the package's autotuner measures one
+// and installs it when the library is loaded), else the built-in rule.
+// Small problems spread a particle over more lanes so that the GPU stays full.
+constexpr int kMaxTableRows = 32;
+static std::mutex g_table_mu;
+static int g_table_rows = 0;
+static long long g_table_n[kMaxTableRows];
+static int g_table_lpp[kMaxTableRows];
+
 static int choose_lpp(long long n, int precision, int requested)
 {
     int l = requested;
     if (l == 0) {
         l = n <= 200000 ? 4 : 1;
+        std::lock_guard<std::mutex> g(g_table_mu);
+        for (int k = 0; k < g_table_rows; ++k)
+            if (n <= g_table_n[k]) {
+                l = g_table_lpp[k];
+                break;
+            }
     }
     if (l != 1 && l != 2 && l != 4 && l != 8) l = 4;
     if (precision == SPH_PREC_FP64) l = (l >= 4) ? 4 : 2;
@@ -228,6 +241,24 @@ extern "C" {
 const char *sph_last_error(void) { return g_err.c_str(); }
 
 const char *sph_version(void) { return "gb300-sph 0.1 (sm_103a)"; }
+
+int sph_set_launch_table(const int64_t *n_max, const int32_t *lanes, int rows)
+{
+    if (rows < 0 || rows > kMaxTableRows) return fail(SPH_EINVAL, "rows must be in [0, %d]", kMaxTableRows);
+    if (rows > 0 && (!n_max || !lanes)) return fail(SPH_EINVAL, "NULL table");
+    for (int k = 0; k < rows; ++k) {
+        if (lanes[k] != 1 && lanes[k] != 2 && lanes[k] != 4 && lanes[k] != 8)
+            return fail(SPH_EINVAL, "row %d: lanes per particle must be 1, 2, 4 or 8", k);
+        if (k > 0 && n_max[k] <= n_max[k - 1]) return fail(SPH_EINVAL, "row %d: n_max must increase", k);
+    }
+    std::lock_guard<std::mutex> g(g_table_mu);
+    for (int k = 0; k < rows; ++k) {
+        g_table_n[k] = (long long)n_max[k];
+        g_table_lpp[k] = lanes[k];
+    }
+    g_table_rows = rows;
+    return SPH_OK;
+}
 
 int sph_params_default(sph_params *p)
 {

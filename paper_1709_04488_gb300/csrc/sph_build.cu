@@ -1,4 +1,4 @@
-// Leaf cells and the tree over them (Sec. 2.6, tree; Sec. 2.6 also the
+// Leaf cells and the tree over them (Sec. 4.2, tree; Sec. 4.2 also the
 // per-leaf neighbour walk).  The paper's KD tree with N_LEAF-particle leaves
 // and per-cell "smallest box containing all the smoothing spheres" is
 // replaced by:

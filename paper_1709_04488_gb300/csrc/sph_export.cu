@@ -1,5 +1,5 @@
 // Exact FP64 neighbour lists (CSR, ids ascending) for one problem: the
-// per-leaf tree walk retrieves the candidates (Sec. 2.6), membership is
+// per-leaf tree walk retrieves the candidates (Sec. 4.2), membership is
 // decided on absolute FP64 positions with the periodic minimum image and
 // r^2 = dx*dx + dy*dy + dz*dz formed without fused multiply-add, compared
 // with (2h)*(2h) (gather list) or (2 max(h_i,h_j))^2 (force list).  Used by

@@ -1,8 +1,8 @@
 // Pair kernels of the grad-h SPH neighbour loop.
 //
 // Work unit: one warp per leaf cell (the paper's OpenMP unit of work is an
-// active leaf cell, Sec. 3.2.1, and neighbours are gathered per leaf, not per
-// particle, Sec. 2.6).  LPP lanes serve each particle of the leaf; the warp
+// active leaf cell, Sec. 5.2.1, and neighbours are gathered per leaf, not per
+// particle, Sec. 4.2).  LPP lanes serve each particle of the leaf; the warp
 // walks the tree over the leaves once per leaf, stages candidate particles in
 // shared memory (positions relative to the query leaf: leaf reference points
 // differenced in FP64, then cast), and each lane keeps its own list of
@@ -22,6 +22,7 @@
 //              error-free (TwoSum) compensated FP32 sums combined in FP64,
 //              which keeps sum_i m_i a_i near FP64 round-off.
 #include "sph_internal.cuh"
+#include "sph_tuned.h"
 
 namespace sph {
 
@@ -31,23 +32,6 @@ constexpr unsigned FULL = 0xffffffffu;
 __host__ __device__ constexpr int lpp_log2(int l) { return l == 1 ? 0 : l == 2 ? 1 : l == 4 ? 2 : 3; }
 constexpr double kListMargin = 1.03;  // list radius = 2 h * margin
 
-// launch-shape constants (staged candidates per chunk, blocks per SM the
-// register budget is sized for); overridable at build time for tuning sweeps
-#ifndef SPH_FORCE_CH
-#define SPH_FORCE_CH 64
-#endif
-#ifndef SPH_FORCE_MINB
-#define SPH_FORCE_MINB 5
-#endif
-#ifndef SPH_DENS_CH
-#define SPH_DENS_CH 64
-#endif
-#ifndef SPH_DENS_MINB
-#define SPH_DENS_MINB 4
-#endif
-#ifndef SPH_DENS_LCAP1
-#define SPH_DENS_LCAP1 96  // list entries per lane at one lane per particle
-#endif
 constexpr int kMaxRebuild = 6;
 
 template <typename T>
@@ -835,21 +819,6 @@ __global__ void __launch_bounds__(FbCfg<T>::WPB * 32) k_density_fallback(BatchVi
 // index within that leaf); the lists are evaluated, reading the partner's
 // data from global memory, when one of them or the table fills and at the end,
 // so that every lane evaluates about the same number of pairs.
-#ifndef SPH_FORCE_LC
-#define SPH_FORCE_LC 64
-#endif
-#ifndef SPH_FORCE_TAB
-#define SPH_FORCE_TAB 128
-#endif
-#ifndef SPH_FORCE_SB
-#define SPH_FORCE_SB 32
-#endif
-#ifndef SPH_FORCE_LC1
-#define SPH_FORCE_LC1 96
-#endif
-#ifndef SPH_FORCE_SB1
-#define SPH_FORCE_SB1 8
-#endif
 template <typename T, int LPP>
 struct FCfg {
     using V = typename Vec4<T>::type;

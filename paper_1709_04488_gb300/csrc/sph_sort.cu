@@ -1,7 +1,7 @@
 // Morton keys and a stable LSD radix sort of (key, index) pairs.
 //
-// The paper builds a KD tree by recursive median bisection (Sec. 2.6, tree;
-// Sec. 3.2 notes the serial top levels limit its parallel scaling).  Here the
+// The paper builds a KD tree by recursive median bisection (Sec. 4.2, tree;
+// Sec. 5.2 notes the serial top levels limit its parallel scaling).  Here the
 // spatial order comes from one fully parallel sort instead: a 30-bit Morton
 // key (10 bits per axis) per particle, prefixed by the problem index in a
 // batch, sorted stably so that ties keep the original particle order.

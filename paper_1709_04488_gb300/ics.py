@@ -15,15 +15,15 @@ implied by the set-up); converged results do not depend on it.
 Recipes (seeds fixed; same bits on any host):
   lattice  periodic unit cube, n^3 particles at cell centres plus a uniform
            jitter of +-0.1 spacing per axis, total mass 1, v = 0, u = 1.5,
-           gamma = 5/3 (the paper's uniform-density set-ups, Sec. 4.1).
+           gamma = 5/3 (the paper's uniform-density set-ups, Sec. 6.1).
   sod      3D shock tube in the periodic box [0,1) x [0,1/8) x [0,1/8):
            left x < 0.5 rho = 1, P = 1 on a 128x16x16 lattice, right rho = 0.125,
            P = 0.1 on a 64x8x8 lattice (equal masses), gamma = 1.4, v = 0
-           (Sec. 4.2 shock tubes, in 3D with the classic Sod states).
+           (Sec. 6.2 shock tubes, in 3D with the classic Sod states).
   sedov    n^3 jittered lattice in the periodic unit cube, rho = 1, u = 1e-5,
            energy E deposited into the 64 particles nearest the centre with
            weights of the M4 shape at h_c = half the distance of the 65th
-           nearest particle (Sec. 4.3, in 3D).
+           nearest particle (Sec. 6.3, in 3D).
   cloud    isolated sphere of radius 1 and mass 1 with rho ~ 1/(1 + r^2/a^2),
            a = 0.1; isothermal, c_s = 1; Gaussian random velocity field with
            |v_k|^2 ~ k^-4 for 2 <= |k| <= 64 on a 128^3 grid over [-1,1]^3,

@@ -161,13 +161,39 @@ def lib():
             "sph_density_forces_noalloc": (i, [C.POINTER(Params), i64, C.POINTER(State), vp]),
             "sph_last_error": (C.c_char_p, []),
             "sph_version": (C.c_char_p, []),
+            "sph_set_launch_table": (i, [C.POINTER(i64), C.POINTER(C.c_int32), i]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
             fn.restype = res
             fn.argtypes = args
         _lib = L
+        _install_tuning(L)
     return _lib
+
+
+TUNING_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning.json")
+
+
+def set_launch_table(rows, L=None):
+    """Install [(n_max, lanes_per_particle), ...] (see sph_set_launch_table)."""
+    L = L or lib()
+    n = len(rows)
+    nm = (C.c_int64 * max(n, 1))(*[int(r[0]) for r in rows])
+    ln = (C.c_int32 * max(n, 1))(*[int(r[1]) for r in rows])
+    rc = L.sph_set_launch_table(nm, ln, n)
+    if rc != OK:
+        raise SPHError(rc, "sph_set_launch_table")
+
+
+def _install_tuning(L):
+    # the autotuner's measured table (paper_1709_04488_gb300/tuning.json), if any
+    if os.environ.get("SPH_NO_TUNING") or not os.path.exists(TUNING_PATH):
+        return
+    import json
+    with open(TUNING_PATH) as f:
+        rows = json.load(f).get("lpp_table", [])
+    set_launch_table(rows, L)
 
 
 def last_error() -> str:

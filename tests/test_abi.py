@@ -81,3 +81,26 @@ def test_setup_rejects_bad_arguments_without_a_gpu(S):
     p.gamma = 1.0
     rc, ctx = S.sph_setup(p, 10, st, 0, 0, 0)
     assert rc == S.EINVAL
+
+
+def test_launch_table_validation(S):
+    """sph_set_launch_table accepts increasing rows of 1/2/4/8 lanes and
+    rejects the rest without changing the installed table."""
+    lib = S.lib()
+
+    def call(rows):
+        n = len(rows)
+        nm = (C.c_int64 * max(n, 1))(*[r[0] for r in rows])
+        ln = (C.c_int32 * max(n, 1))(*[r[1] for r in rows])
+        return lib.sph_set_launch_table(nm, ln, n)
+
+    assert call([(1000, 8), (100000, 4), (1 << 40, 1)]) == S.OK
+    assert call([(1000, 3)]) == S.EINVAL
+    assert call([(1000, 4), (1000, 2)]) == S.EINVAL
+    assert call([(k + 1, 4) for k in range(33)]) == S.EINVAL
+    assert lib.sph_set_launch_table(None, None, 1) == S.EINVAL
+    assert call([]) == S.OK  # back to the built-in rule
+    if os.path.exists(S.TUNING_PATH):  # the autotuned table the binding installs
+        import json
+        rows = json.load(open(S.TUNING_PATH))["lpp_table"]
+        assert call(rows) == S.OK

@@ -65,12 +65,12 @@ def test_kernel_derivatives_finite_difference(oracle_mod):
 
 
 # --------------------------------------------------------------------------
-# Density and smoothing length (Eqs. SPHRHO, HRHO; Sec. 4.1 lattice offset)
+# Density and smoothing length (Eqs. SPHRHO, HRHO; Sec. 6.1 lattice offset)
 # --------------------------------------------------------------------------
 def test_lattice_density_neighbours_and_offset(oracle_mod):
     """Perfect cubic lattice: the density sum recovers rho0 to better than 1 %
     (the paper's 'consistent fractional offset of less than one percent',
-    Sec. 4.1), and with eta = 1.2 every particle has exactly 57 neighbours
+    Sec. 6.1), and with eta = 1.2 every particle has exactly 57 neighbours
     inside 2h, counting itself: lattice shells |n|^2 = 0,1,2,3,4,5 hold
     1+6+12+8+6+24 = 57 points and the next shell, |n|^2 = 6, lies at
     2.449 spacings > 2h = 2.399 spacings."""
@@ -161,7 +161,7 @@ def test_continuity_identity_pins_omega(oracle_mod):
 def test_pressure_force_is_thermal_energy_gradient(oracle_mod):
     """Eq. GRADHMOMEQN follows from the Lagrangian: with the entropy of each
     particle held fixed, m_i a_i = -dE_th/dr_i where E_th = sum_j m_j u_j(rho_j),
-    u_j = K_j rho_j^(gamma-1) (Sec. 2.2.1 'derived from the Euler-Lagrange
+    u_j = K_j rho_j^(gamma-1) (Sec. 2.1.1 'derived from the Euler-Lagrange
     equations').  Checked by central differences of the re-solved densities.
     Pins the pressure term: both h_i and h_j parts, Omega, signs, indices."""
     O = oracle_mod
@@ -196,7 +196,7 @@ def test_pressure_force_is_thermal_energy_gradient(oracle_mod):
 # --------------------------------------------------------------------------
 def test_momentum_and_energy_conserved_pairwise(oracle_mod):
     """Every term is antisymmetric under i<->j, so sum_i m_i a_i = 0 and
-    sum_i m_i (v_i.a_i + du_i/dt) = 0 to FP64 round-off (Sec. 2.2.1:
+    sum_i m_i (v_i.a_i + du_i/dt) = 0 to FP64 round-off (Sec. 2.1.1:
     conservation of momentum and energy)."""
     O = oracle_mod
     a, p = ics.random_cloud(500, seed=9, mass_spread=0.5, vel=1.0, u_spread=0.8)
@@ -257,7 +257,7 @@ def test_galilean_invariance(oracle_mod):
 
 
 def test_isothermal_eos(oracle_mod):
-    """Isothermal EOS (Sec. 4.2): P = c_s^2 rho, c = c_s, u is not evolved."""
+    """Isothermal EOS (Sec. 6.2): P = c_s^2 rho, c = c_s, u is not evolved."""
     O = oracle_mod
     a, p = ics.lattice(10, seed=3)
     p.update(eos="isothermal", cs_iso=0.7)

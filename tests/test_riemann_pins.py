@@ -1,4 +1,4 @@
-"""Pins for the analytic shock-tube solutions (Sec. 4.2) and an oracle SPH
+"""Pins for the analytic shock-tube solutions (Sec. 6.2) and an oracle SPH
 shock tube checked against them.
 
 The exact Riemann solver is pinned by the conservation laws it must satisfy
@@ -67,7 +67,7 @@ def _binned(x, q, edges):
 
 @pytest.mark.slow
 def test_oracle_sod_wave_positions(oracle_mod):
-    """3D Sod tube (Sec. 4.2 set-up in 3D: left rho=1, P=1 on 32x16x16, right
+    """3D Sod tube (Sec. 6.2 set-up in 3D: left rho=1, P=1 on 32x16x16, right
     rho=0.125, P=0.1 on 16x8x8, periodic [0,1) x [0,1/4)^2, gamma=1.4), run with
     the oracle to t = 0.1, before the mirrored interface at x = 0 interacts.
     The rarefaction head, the contact and the shock must sit where the exact
