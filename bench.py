@@ -89,6 +89,23 @@ def traffic_for(workload):
     return None
 
 
+def reduce_max_ms(total_ms, world, dist=None, device=None):
+    """The slowest rank's timed total (all-reduce MAX, then a barrier)."""
+    if world <= 1:
+        return total_ms
+    import torch
+    t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def replica_value(n, steps, world, total_ms):
+    """Whole-job particle-updates/s: every rank steps its own n-particle
+    replica, so the job does world * n * steps updates in the slowest time."""
+    return world * n * steps / (total_ms * 1e-3)
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -295,14 +312,9 @@ def run_ours(args):
         ms, _, _, _ = time_steps(S, prob, stream, torch, args.steps, flush)
     torch.cuda.synchronize(dev)
     S.check(S.sph_sync(prob.ctx), "sph_sync")
-    total_ms = float(np.sum(ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-        total_ms = float(t.item())
+    total_ms = reduce_max_ms(float(np.sum(ms)), world, dist if world > 1 else None, dev)
     clocks = clk.summary()
-    value = world * n * args.steps / (total_ms * 1e-3)
+    value = replica_value(n, args.steps, world, total_ms)
 
     # stage times and pair counts (separate pass: a host sync per step)
     _, stages, dp, fp = time_steps(S, prob, stream, torch, min(args.steps, 20), flush, stage=True)
