@@ -234,3 +234,51 @@ def test_batch_equals_alone(S):
         g = pr.numpy()
         for f in ("x", "vx", "u", "h", "rho", "ax", "du"):
             assert np.array_equal(g[f], ref[f]), f
+
+
+def test_batch_mixed_launch_classes_equal_alone(S):
+    """A batch whose problems fall in different launch classes (1, 2, 4 and
+    8 lanes per particle; equal and unequal masses; periodic and isolated)
+    gives bit-identical states to each problem stepped alone."""
+    import torch
+    ua, up = ics.random_cloud(3000, seed=21, mass_spread=0.5, vel=0.2, u_spread=0.3)
+    ca, cp = ics.cloud(6000, seed=22)
+    cases = [(_moving_lattice(12, seed=9), 1), ((ua, up), 2), (ics.sod(left=(32, 16, 16), right=(16, 8, 8), width=0.25), 4),
+             ((ca, cp), 8)]
+    alone = []
+    for (a, p), l in cases:
+        prob = _gpu(S, a, p, S.PREC_MIXED, lanes_per_particle=l)
+        for _ in range(2):
+            prob.step(-1.0)
+        alone.append(prob.numpy())
+    probs = [_gpu(S, a, p, S.PREC_MIXED, lanes_per_particle=l) for (a, p), l in cases]
+    ctxs = [pr.ctx for pr in probs]
+    wb = S.sph_batch_workspace_bytes(ctxs)
+    ws = torch.empty(wb, dtype=torch.uint8, device="cuda")
+    S.check(S.sph_batch_step(ctxs, 2, ws.data_ptr(), wb), "sph_batch_step")
+    for pr, ref in zip(probs, alone):
+        g = pr.numpy()
+        for f in ("x", "vx", "u", "h", "rho", "ax", "du", "vsig"):
+            assert np.array_equal(g[f], ref[f]), f
+
+
+def test_launch_table_selects_lanes(S, oracle_mod):
+    """An installed launch table decides the lanes per particle of contexts
+    that leave it to the library; results keep their parity either way."""
+    O = oracle_mod
+    a, p = ics.lattice(16, seed=3)
+    _, ref = _oracle(O, a, p)
+    leaves = {}
+    try:
+        for lanes in (1, 8):
+            S.set_launch_table([(1 << 40, lanes)])
+            prob = _gpu(S, a, p, S.PREC_MIXED)
+            leaves[lanes] = prob.diagnostics().leaves
+            g = prob.numpy()
+            assert _rel(g["rho"], ref.rho) < 1e-5
+            assert _rms_err(_acc(g), np.stack([ref.ax, ref.ay, ref.az], 1)) < 1e-4
+        # leaf size 32 / lanes: eight lanes per particle means 8x smaller leaves
+        assert leaves[8] > 4 * leaves[1]
+    finally:
+        S.set_launch_table([])
+        S._install_tuning(S.lib())
