@@ -3,11 +3,14 @@
 Two tables, both measured on the GPU it runs on:
 
 ``lanes``  lanes per particle (the leaf size is 32 / lanes) by problem size.
-           For each size of a jittered-lattice problem it times CFL steps at
-           1, 2, 4 and 8 lanes, keeps the fastest, and writes
-           ``tuning.json`` (rows ``[n_max, lanes]``, bucket edges at the
-           geometric means of neighbouring sizes).  The binding installs the
-           table (``sph_set_launch_table``) whenever it loads the library.
+           For each size it times CFL steps at 1, 2, 4 and 8 lanes of a
+           jittered lattice, a Sedov blast and (from 15552 particles) a Sod
+           tube of about that size, scores each choice by the sum over the
+           problems of its time relative to the problem's fastest, keeps the
+           best, and writes ``tuning.json`` (rows ``[n_max, lanes]``, bucket
+           edges at the geometric means of neighbouring sizes).  The binding
+           installs the table (``sph_set_launch_table``) whenever it loads
+           the library.
 
 ``build``  compile-time shapes of the pair kernels (staged candidates per
            chunk, list capacities, register budgets).  Coordinate descent:
@@ -37,7 +40,7 @@ TUNED_H = os.path.join(HERE, "csrc", "sph_tuned.h")
 TUNING_JSON = os.path.join(HERE, "tuning.json")
 
 LANES = (1, 2, 4, 8)
-LATTICE_SIDES = (12, 20, 32, 50, 80, 126)  # 1728 ... 2.0e6 particles
+LATTICE_SIDES = (12, 20, 33, 50, 80, 126)  # 1728 ... 2.0e6 particles (33: the Sod configuration's size)
 
 # candidate values of the compile-time shapes, in the order they are tuned
 BUILD_SPACE = {
@@ -52,42 +55,64 @@ BUILD_SPACE = {
 }
 
 
-def time_steps(arrays, params, steps=5, warmup=2, lanes=0):
-    """Median device time (ms) of one CFL step of a problem, through the
-    library's graph-replayed step with stage timing off."""
+def time_steps(arrays, params, steps=5, warmup=3, lanes=0):
+    """Median device time (ms) of one CFL step of a problem, timed as the
+    benchmark times it: the step replayed as a CUDA graph (sph_run), stage
+    timing off, L2 flushed (a 256 MiB write) before every timed step."""
     import numpy as np
     import torch
     from . import sph as S
     st = torch.cuda.Stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     with torch.cuda.stream(st):
-        prob = S.Problem(arrays, S.make_params(S.PREC_MIXED, lanes_per_particle=lanes, **params), stream=st)
+        prm = S.make_params(S.PREC_MIXED, lanes_per_particle=lanes, flags=S.FLAG_ASYNC, **params)
+        prob = S.Problem(arrays, prm, stream=st)
         prob.density_h()
         prob.forces()
-        for _ in range(warmup):
-            prob.step(-1.0)
+        prob.run(warmup)
+        prob.sync()
         ts = []
         for _ in range(steps):
+            flush.fill_(1)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(st)
-            prob.step(-1.0)
+            prob.run(1)
             e1.record(st)
             e1.synchronize()
             ts.append(e0.elapsed_time(e1))
+        prob.sync()
         prob.close()
     return float(np.median(ts))
 
 
-def tune_lanes(steps=5):
+def _problems_of_size(side):
+    """Problems of about side^3 particles: lattice, Sedov and (if large
+    enough) a Sod tube with the bench configuration's resolution."""
     from . import ics
+    from .serve import sod_request
+    out = {"lattice": ics.lattice(side, seed=7), "sedov": ics.sedov(side, seed=8)}
+    if side ** 3 >= 9 * 12 ** 3:
+        out["sod"] = ics.sod() if side == 33 else sod_request(side ** 3, ratio=8.0)
+    return out
+
+
+def tune_lanes(steps=5):
     rows, measured = [], {}
     for side in LATTICE_SIDES:
-        a, p = ics.lattice(side, seed=7)
         n = side ** 3
-        t = {l: time_steps(a, p, steps=steps, lanes=l) for l in LANES}
-        best = min(t, key=t.get)
-        measured[str(n)] = {"ms": {str(k): round(v, 4) for k, v in t.items()}, "best": best}
+        score = {l: 0.0 for l in LANES}
+        per = {}
+        for kind, (a, p) in _problems_of_size(side).items():
+            t = {l: time_steps(a, p, steps=steps, lanes=l) for l in LANES}
+            per[kind] = {str(k): round(v, 4) for k, v in t.items()}
+            fastest = min(t.values())
+            for l in LANES:
+                score[l] += t[l] / fastest
+            print(f"n~{n:8d} {kind:8s} " + " ".join(f"{l}:{t[l]:.3f}ms" for l in LANES), flush=True)
+        best = min(score, key=score.get)
+        measured[str(n)] = {"ms": per, "score": {str(k): round(v, 4) for k, v in score.items()}, "best": best}
         rows.append((n, best))
-        print(f"n={n:8d} " + " ".join(f"{l}:{t[l]:.3f}ms" for l in LANES) + f" -> {best}", flush=True)
+        print(f"n~{n:8d} -> {best}", flush=True)
     table = []
     for k, (n, lanes) in enumerate(rows):
         if k + 1 < len(rows):
@@ -99,7 +124,7 @@ def tune_lanes(steps=5):
         else:
             table.append([edge, lanes])
     out = {"lpp_table": table, "measured": measured,
-           "note": "jittered periodic lattices, median of CFL steps, mixed precision"}
+           "note": "lattice, Sedov and Sod problems per size, median of CFL steps, mixed precision"}
     with open(TUNING_JSON, "w") as f:
         json.dump(out, f, indent=1)
     print("wrote", TUNING_JSON, table)

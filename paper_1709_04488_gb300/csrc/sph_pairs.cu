@@ -314,7 +314,9 @@ __device__ __forceinline__ bool group_any(bool v)
 }
 
 // One Newton-Raphson update of the h-rho solve with the oracle's bracketing
-// (Eqs. SPHRHO, HRHO).  Returns true when |h_new - h| < tol h.
+// (Eqs. SPHRHO, HRHO).  Returns true when |h_new - h| < tol h; h then stays
+// (it is within the tolerance of the root, and the caller's sums at h stay
+// valid), else h becomes h_new.
 template <typename T>
 __device__ __forceinline__ bool nr_update(T &h, T &lo, T &hi, T rho, T drho, T m, T eta3, T tol)
 {
@@ -327,8 +329,8 @@ __device__ __forceinline__ bool nr_update(T &h, T &lo, T &hi, T rho, T drho, T m
     T hn = dF > T(0) ? h - F / dF : T(-1);
     bool bad = !(hn >= lo) || !(hn <= hi) || !(hn >= T(0.5) * h) || !(hn <= T(2) * h) || !(dF > T(0));
     if (bad) hn = (hi == tinf<T>()) ? T(2) * h : T(0.5) * (lo + hi);
-    bool conv = fabs(hn - h) < tol * h;
-    h = hn;
+    const bool conv = fabs(hn - h) < tol * h;
+    if (!conv) h = hn;
     return conv;
 }
 
@@ -449,6 +451,9 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM>::WPB * 32, SPH_DENS_MINB) k_d
         T lo = T(0), hi = tinf<T>();
         int it = 0;
         bool conv = !active, fail = false, need = false, noconv = false;
+        bool kept = false;  // converged by tolerance: the sums at the returned h are kS0, kS1
+        T kS0 = T(0), kS1 = T(0);
+        int knn = 0;
         int cnt = 0;
         long long pairs = 0, tested = 0;
         // bal: in-range candidates are dealt to the particle's LPP lanes by
@@ -563,9 +568,16 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM>::WPB * 32, SPH_DENS_MINB) k_d
                     T rho = T(1.0 / kPi) * S0 * hinv3;
                     T drho = -T(1.0 / kPi) * hinv3 * hinv * (T(3) * S0 + S1);
                     bool c = nr_update(h, lo, hi, rho, drho, mi, eta3, tol);
+                    if (c) {
+                        kept = true;
+                        kS0 = S0;
+                        kS1 = S1;
+                        knn = nn;
+                    }
                     if ((double)h > 0.25 * Lmin) {
                         atomicOr(&ps.diag->status, ST_BOX);
                         c = true;
+                        kept = false;
                     }
                     if (!c && it >= maxit) {
                         noconv = true;
@@ -582,27 +594,37 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM>::WPB * 32, SPH_DENS_MINB) k_d
             }
             need = false;
         }
-        // final evaluation at the returned h
-        T S0 = T(0), S1 = T(0);
-        int nn = 0;
-        bool fin = active && !fail;
-        if (fin) {
-            const T hinv = T(1) / h;
-            for (int e = 0; e < cnt; ++e) {
-                T q = lr[e * 32 + lane] * hinv;
-                T mj = UM ? mu_all : lm[e * 32 + lane];
-                T f, df;
-                m4(q, f, df);
-                S0 += mj * f;
-                S1 += mj * q * df;
-                nn += q < T(2);
+        // final evaluation at the returned h, unless the sums there are kept
+        T S0 = kS0, S1 = kS1;
+        int nn = knn;
+        const bool fin = active && !fail;
+        const bool redo = fin && !kept;
+        if (__any_sync(FULL, redo)) {
+            T R0 = T(0), R1 = T(0);
+            int rn = 0;
+            if (redo) {
+                const T hinv = T(1) / h;
+                for (int e = 0; e < cnt; ++e) {
+                    T q = lr[e * 32 + lane] * hinv;
+                    T mj = UM ? mu_all : lm[e * 32 + lane];
+                    T f, df;
+                    m4(q, f, df);
+                    R0 += mj * f;
+                    R1 += mj * q * df;
+                    rn += q < T(2);
+                }
+            }
+            R0 = group_sum<LPP>(R0);
+            R1 = group_sum<LPP>(R1);
+            rn = group_sum<LPP>(rn);
+            if (redo) {
+                S0 = R0;
+                S1 = R1;
+                nn = rn;
+                if (sub == 0) pairs += rn;
             }
         }
-        S0 = group_sum<LPP>(S0);
-        S1 = group_sum<LPP>(S1);
-        nn = group_sum<LPP>(nn);
         if (fin && sub == 0) {
-            pairs += nn;
             density_epilogue<T>(b, ps, s, pi, h, S0, S1, use_pred);
             if (noconv) {
                 atomicOr(&ps.diag->status, ST_NOCONV);

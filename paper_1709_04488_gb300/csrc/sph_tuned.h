@@ -11,7 +11,7 @@
 #define SPH_DENS_CH 64
 #endif
 #ifndef SPH_DENS_MINB
-#define SPH_DENS_MINB 4
+#define SPH_DENS_MINB 5
 #endif
 #ifndef SPH_DENS_LCAP1
 #define SPH_DENS_LCAP1 96
@@ -27,7 +27,7 @@
 #define SPH_FORCE_MINB 5
 #endif
 #ifndef SPH_FORCE_TAB
-#define SPH_FORCE_TAB 128
+#define SPH_FORCE_TAB 64
 #endif
 #ifndef SPH_FORCE_LC
 #define SPH_FORCE_LC 64
@@ -36,7 +36,7 @@
 #define SPH_FORCE_SB 32
 #endif
 #ifndef SPH_FORCE_LC1
-#define SPH_FORCE_LC1 96
+#define SPH_FORCE_LC1 80
 #endif
 #ifndef SPH_FORCE_SB1
 #define SPH_FORCE_SB1 8
