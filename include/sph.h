@@ -272,7 +272,7 @@ int sph_server_destroy(sph_server *s);
  * own pool, or a plug-in or real-time loop called from such a host.  The paper
  * has no counterpart: this is a property of the library, not of the method.
  *   - Allocates nothing: no cudaMalloc/cudaFree, no allocating library call.
- *     Its scratch memory is a fixed 12 MiB array compiled into the library,
+ *     Its scratch memory is a fixed 16 MiB array compiled into the library,
  *     which every GPU that loads the library holds until the process exits.
  *   - n is at most 32768; larger n returns SPH_EINVAL with a message.
  *   - The caller passes the particle arrays (inputs and outputs as in

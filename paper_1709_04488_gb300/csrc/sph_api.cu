@@ -54,7 +54,7 @@ void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precis
 {
     const long long n = ntot > 0 ? ntot : 1;
     const size_t v4 = precision == SPH_PREC_FP64 ? sizeof(dbl4) : sizeof(float4);
-    const long long nblk = (n + 2047) / 2048;
+    const long long nblk = sort_tiles(n);
     const long long passes = (key_bits_for(nprob) + 7) / 8;
     b.keys[0] = c.take<unsigned long long>(n);
     b.keys[1] = c.take<unsigned long long>(n);

@@ -274,6 +274,7 @@ int status_to_code(unsigned st);
 // upper bounds used to size grids and workspaces
 long long leaves_upper_bound(long long n);
 long long leaf_tiles(long long n);  // tiles of the leaf scan
+long long sort_tiles(long long n);  // tiles of one radix-sort pass
 int levels_needed(long long max_leaves);
 
 }  // namespace sph

@@ -22,7 +22,7 @@ using namespace sph;
 // of the FP64 path (the larger of the two precisions) for this many
 // particles, plus the persistent diagnostics record, rounded up.
 constexpr long long kNoAllocMaxN = 32768;
-constexpr size_t kNoAllocBytes = (size_t)12 << 20;
+constexpr size_t kNoAllocBytes = (size_t)16 << 20;
 constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];

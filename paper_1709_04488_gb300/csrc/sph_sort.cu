@@ -12,8 +12,11 @@ namespace sph {
 namespace {
 
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 8;
-constexpr int kSortTile = kSortThreads * kSortItems;  // 2048 keys per block
+// keys per thread of a radix pass: small problems take short tiles (more
+// blocks in flight), large ones long tiles (fewer look-back records)
+constexpr int kSortItemsSmall = 2, kSortItemsLarge = 8;
+constexpr long long kSortSmallMax = 1ll << 18;
+int sort_items(long long n) { return n <= kSortSmallMax ? kSortItemsSmall : kSortItemsLarge; }
 constexpr int kBboxThreads = 1024;
 
 __device__ __forceinline__ unsigned spread10(unsigned v)
@@ -193,11 +196,13 @@ __global__ void k_keys_hist(BatchView b, unsigned *hist, int passes)
     }
 }
 
+template <int ITEMS>
 __global__ void k_onesweep(const unsigned long long *kin, const unsigned *vin, unsigned long long *kout,
                            unsigned *vout, long long n, int shift, const unsigned *hist, unsigned *status,
                            unsigned *tile_ctr, int identity_vals, unsigned *timeout_flag)
 {
     constexpr int NW = kSortThreads / 32;
+    constexpr int TILE = kSortThreads * ITEMS;
     __shared__ unsigned run[256];
     __shared__ unsigned wcnt[NW][256];
     __shared__ unsigned cnt[256];
@@ -218,10 +223,10 @@ __global__ void k_onesweep(const unsigned long long *kin, const unsigned *vin, u
     }
     const unsigned gstart = gpre[t] - hist[t];
     const int tile = s_tile;
-    const long long base = (long long)tile * kSortTile;
+    const long long base = (long long)tile * TILE;
     // local digit counts
-    unsigned long long keys[kSortItems];
-    for (int r = 0; r < kSortItems; ++r) {
+    unsigned long long keys[ITEMS];
+    for (int r = 0; r < ITEMS; ++r) {
         long long k = base + r * kSortThreads + t;
         keys[r] = k < n ? kin[k] : 0ull;
         warp_hist_add(cnt, (unsigned)(keys[r] >> shift) & 255u, k < n);
@@ -271,7 +276,7 @@ __global__ void k_onesweep(const unsigned long long *kin, const unsigned *vin, u
     __syncthreads();
     // stable ranks inside the tile (index order), then scatter
     const unsigned lt = (1u << lane) - 1u;
-    for (int r = 0; r < kSortItems; ++r) {
+    for (int r = 0; r < ITEMS; ++r) {
         long long k = base + r * kSortThreads + t;
         bool ok = k < n;
         unsigned long long key = keys[r];
@@ -315,11 +320,19 @@ cudaError_t launch_domain_and_keys(const BatchView &b, cudaStream_t st)
     return cudaGetLastError();
 }
 
+long long sort_tiles(long long n)
+{
+    const long long t = (long long)kSortThreads * sort_items(n);
+    return (n + t - 1) / t;
+}
+
 cudaError_t launch_radix_sort(const BatchView &b, cudaStream_t st)
 {
     if (b.ntot == 0) return cudaSuccess;
     const long long n = b.ntot;
-    const int ntile = (int)((n + kSortTile - 1) / kSortTile);
+    const int items = sort_items(n);
+    const long long tile_keys = (long long)kSortThreads * items;
+    const int ntile = (int)((n + tile_keys - 1) / tile_keys);
     const int passes = (b.key_bits + 7) / 8;
     // hist[passes][256] | tile counters[passes] | status[passes][ntile][256]
     unsigned *hist = b.hist, *ctr = b.hist + passes * 256, *status = b.hist + passes * 256 + 8;
@@ -331,9 +344,10 @@ cudaError_t launch_radix_sort(const BatchView &b, cudaStream_t st)
     for (int pass = 0; pass < passes; ++pass) {
         const bool last = pass == passes - 1;
         unsigned *vdst = last ? (unsigned *)b.perm : b.vals[src ^ 1];
-        k_onesweep<<<ntile, kSortThreads, 0, st>>>(b.keys[src], b.vals[src], b.keys[src ^ 1], vdst, n, 8 * pass,
-                                                   hist + pass * 256, status + (size_t)pass * ntile * 256,
-                                                   ctr + pass, pass == 0, (unsigned *)&b.counters[kTimeoutCounter]);
+        auto kern = items == kSortItemsSmall ? k_onesweep<kSortItemsSmall> : k_onesweep<kSortItemsLarge>;
+        kern<<<ntile, kSortThreads, 0, st>>>(b.keys[src], b.vals[src], b.keys[src ^ 1], vdst, n, 8 * pass,
+                                             hist + pass * 256, status + (size_t)pass * ntile * 256, ctr + pass,
+                                             pass == 0, (unsigned *)&b.counters[kTimeoutCounter]);
         src ^= 1;
     }
     if (src != 0) {
