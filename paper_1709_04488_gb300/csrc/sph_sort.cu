@@ -12,11 +12,21 @@ namespace sph {
 namespace {
 
 constexpr int kSortThreads = 256;
-// keys per thread of a radix pass: small problems take short tiles (more
-// blocks in flight), large ones long tiles (fewer look-back records)
-constexpr int kSortItemsSmall = 2, kSortItemsLarge = 8;
-constexpr long long kSortSmallMax = 1ll << 18;
-int sort_items(long long n) { return n <= kSortSmallMax ? kSortItemsSmall : kSortItemsLarge; }
+// keys per thread of a radix pass (1, 2, 4 or 8): small problems take short
+// tiles (more blocks in flight), large ones long tiles (fewer look-back records)
+#ifndef SPH_SORT_ITEMS_S
+#define SPH_SORT_ITEMS_S 2  // up to 2^18 keys
+#endif
+#ifndef SPH_SORT_ITEMS_M
+#define SPH_SORT_ITEMS_M 8  // up to 2^22 keys
+#endif
+#ifndef SPH_SORT_ITEMS_L
+#define SPH_SORT_ITEMS_L 8
+#endif
+int sort_items(long long n)
+{
+    return n <= (1ll << 18) ? SPH_SORT_ITEMS_S : n <= (1ll << 22) ? SPH_SORT_ITEMS_M : SPH_SORT_ITEMS_L;
+}
 constexpr int kBboxThreads = 1024;
 
 __device__ __forceinline__ unsigned spread10(unsigned v)
@@ -344,7 +354,7 @@ cudaError_t launch_radix_sort(const BatchView &b, cudaStream_t st)
     for (int pass = 0; pass < passes; ++pass) {
         const bool last = pass == passes - 1;
         unsigned *vdst = last ? (unsigned *)b.perm : b.vals[src ^ 1];
-        auto kern = items == kSortItemsSmall ? k_onesweep<kSortItemsSmall> : k_onesweep<kSortItemsLarge>;
+        auto kern = items == 1 ? k_onesweep<1> : items == 2 ? k_onesweep<2> : items == 4 ? k_onesweep<4> : k_onesweep<8>;
         kern<<<ntile, kSortThreads, 0, st>>>(b.keys[src], b.vals[src], b.keys[src ^ 1], vdst, n, 8 * pass,
                                              hist + pass * 256, status + (size_t)pass * ntile * 256, ctr + pass,
                                              pass == 0, (unsigned *)&b.counters[kTimeoutCounter]);
