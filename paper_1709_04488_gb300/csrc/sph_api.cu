@@ -204,6 +204,7 @@ PhysParams phys_of(const sph_params *p)
     for (int a = 0; a < 3; ++a) {
         ph.box_lo[a] = p->box_lo[a];
         ph.box_len[a] = p->periodic ? p->box_len[a] : 0.0;
+        ph.box_len_f[a] = (float)ph.box_len[a];
     }
     ph.gamma = p->gamma;
     ph.cs_iso = p->cs_iso;
@@ -384,6 +385,7 @@ int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *st
         for (long long k = 1; k < n && uni; ++k) uni = mh[(size_t)k] == mh[0];
         ps.uniform_m = uni ? 1 : 0;
         ps.m_uniform = mh[0];
+        ps.inv_m_uniform = uni && mh[0] != 0.0 ? 1.0 / mh[0] : 0.0;
     }
     c->bv.dens_mask = dens_class_bit(c->lpp, ps.uniform_m);
     ProbDiag d0;

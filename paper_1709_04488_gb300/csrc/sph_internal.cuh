@@ -41,6 +41,8 @@ struct PhysParams {
     double h_tol;
     int h_max_iter;
     int pad_;
+    float box_len_f[3];  // box_len as float (node tests run in FP32)
+    float pad2_;
 };
 
 // Per-problem diagnostics and persistent scalars; lives in the context's own
@@ -72,6 +74,7 @@ struct ProbStatic {
     int lpp;         // lanes per particle in the pair kernels (leaf size = 32 / lpp)
     int uniform_m;   // all masses equal (m_uniform): neighbour lists keep distances only
     double m_uniform;
+    double inv_m_uniform;  // 1 / m_uniform (0 unless uniform_m)
     PhysParams ph;
 };
 

@@ -121,9 +121,9 @@ __device__ __forceinline__ bool axis_overlap(float alo, float ahi, float blo, fl
 __device__ __forceinline__ bool box_overlap(const float4 &alo, const float4 &ahi, const float4 &blo,
                                             const float4 &bhi, float R, const PhysParams &ph)
 {
-    return axis_overlap(alo.x, ahi.x, blo.x, bhi.x, R, ph.periodic, (float)ph.box_len[0]) &&
-           axis_overlap(alo.y, ahi.y, blo.y, bhi.y, R, ph.periodic, (float)ph.box_len[1]) &&
-           axis_overlap(alo.z, ahi.z, blo.z, bhi.z, R, ph.periodic, (float)ph.box_len[2]);
+    return axis_overlap(alo.x, ahi.x, blo.x, bhi.x, R, ph.periodic, ph.box_len_f[0]) &&
+           axis_overlap(alo.y, ahi.y, blo.y, bhi.y, R, ph.periodic, ph.box_len_f[1]) &&
+           axis_overlap(alo.z, ahi.z, blo.z, bhi.z, R, ph.periodic, ph.box_len_f[2]);
 }
 
 // Warp-cooperative depth-first walk of one problem's tree.  At the leaf level
@@ -442,7 +442,8 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM>::WPB * 32, SPH_DENS_MINB) k_d
         const T eta3 = (T)(ph.eta * ph.eta * ph.eta);
         const T tol = (T)ph.h_tol;
         const int maxit = ph.h_max_iter;
-        double Lmin = ph.periodic ? fmin(ph.box_len[0], fmin(ph.box_len[1], ph.box_len[2])) : INFINITY;
+        const double Lmin = ph.periodic ? fmin(ph.box_len[0], fmin(ph.box_len[1], ph.box_len[2])) : INFINITY;
+        const T hbox = (T)(0.25 * Lmin);  // h beyond a quarter of the box: SPH_EBOX
         T h = active ? (T)b.sh[s] : T(1);
         if (active && !(h > T(0))) {
             double ext = ph.periodic ? fmax(ph.box_len[0], fmax(ph.box_len[1], ph.box_len[2])) : 1.0 / dy.dom_inv;
@@ -574,7 +575,7 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM>::WPB * 32, SPH_DENS_MINB) k_d
                         kS1 = S1;
                         knn = nn;
                     }
-                    if ((double)h > 0.25 * Lmin) {
+                    if (h > hbox) {
                         atomicOr(&ps.diag->status, ST_BOX);
                         c = true;
                         kept = false;
@@ -1055,27 +1056,31 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, SPH_FORCE_MINB) k_forc
         Fz = group_sum<LPP>(Fz);
         du = group_sum<LPP>(du);
         vs = group_max<LPP>(vs);
-        double dti = INFINITY;
+        // a = F / m in FP64 (m a stays F to FP64 round-off), one reciprocal
+        // per particle (none for equal masses); the CFL step C h / v_sig of
+        // Eq. SPH_DT in the pair precision (FP32: the FP64 pipe is much
+        // narrower than the FP32 one on this part)
+        T dti = tinf<T>();
         if (active && sub == 0) {
             long long g = b.perm[s];
             long long i = g - ps.base;
-            double m = ps.m[i];
-            double a[3] = {Fx / m, Fy / m, Fz / m};
-            double vsig = vs < T(0) ? 2.0 * (double)vi.w : (double)vs;
+            const double minv = ps.uniform_m ? ps.inv_m_uniform : 1.0 / ps.m[i];
+            double a[3] = {Fx * minv, Fy * minv, Fz * minv};
+            const T vsig_t = vs < T(0) ? T(2) * vi.w : vs;
             ps.ax[i] = a[0];
             ps.ay[i] = a[1];
             ps.az[i] = a[2];
             ps.du[i] = adi ? (double)du : 0.0;
-            ps.vsig[i] = vsig;
-            dti = ph.c_cfl * b.sh[s] / vsig;
-            if (!(isfinite(a[0]) && isfinite(a[1]) && isfinite(a[2]) && isfinite((double)du)))
+            ps.vsig[i] = (double)vsig_t;
+            dti = (T)ph.c_cfl * (T)b.sh[s] / vsig_t;
+            if (!(isfinite(a[0]) && isfinite(a[1]) && isfinite(a[2]) && isfinite(du)))
                 atomicOr(&ps.diag->status, ST_NONFINITE);
         }
-        double dmin = warp_min(dti);
+        const T dmin = warp_min(dti);
         long long tp = warp_sum((long long)pairs), tt = warp_sum((long long)tested);
         if (lane == 0) {
             if (dmin < INFINITY)
-                atomicMin(&ps.diag->dt_min_bits, (unsigned long long)__double_as_longlong(dmin));
+                atomicMin(&ps.diag->dt_min_bits, (unsigned long long)__double_as_longlong((double)dmin));
             atomicAdd((unsigned long long *)&ps.diag->force_pairs, (unsigned long long)tp);
             atomicAdd((unsigned long long *)&ps.diag->candidates, (unsigned long long)tt);
         }

@@ -282,3 +282,16 @@ def test_launch_table_selects_lanes(S, oracle_mod):
     finally:
         S.set_launch_table([])
         S._install_tuning(S.lib())
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_cfl_step_matches_oracle(S, oracle_mod, prec):
+    """The CFL step the force pass leaves (Eq. SPH_DT, min over particles of
+    C_CFL h / v_sig) against the oracle's."""
+    O = oracle_mod
+    a, p = _moving_lattice(14, seed=12)
+    P, ref = _oracle(O, a, p)
+    prob = _gpu(S, a, p, S.PREC_MIXED if prec == "mixed" else S.PREC_FP64)
+    got = prob.diagnostics().dt_next
+    want = O.cfl_dt(P, ref)
+    assert abs(got / want - 1.0) < (1e-5 if prec == "mixed" else 1e-12)
