@@ -126,6 +126,35 @@ __device__ __forceinline__ bool box_overlap(const float4 &alo, const float4 &ahi
            axis_overlap(alo.z, ahi.z, blo.z, bhi.z, R, ph.periodic, ph.box_len_f[2]);
 }
 
+// Gap between the two boxes' extents along one axis (minimum image if
+// periodic), shrunk for the FP32 rounding of the box coordinates.
+__device__ __forceinline__ float axis_gap(float alo, float ahi, float blo, float bhi, int periodic, float L)
+{
+    float ca = 0.5f * (alo + ahi), ha = 0.5f * (ahi - alo);
+    float cb = 0.5f * (blo + bhi), hb = 0.5f * (bhi - blo);
+    float reach = ha + hb;
+    reach += 2e-6f * (fabsf(ca) + fabsf(cb) + reach) + 1e-30f;
+    float d = fabsf(ca - cb);
+    if (periodic) {
+        if (reach >= 0.5f * L) return 0.f;
+        if (d > L) d -= L;
+        d = fminf(d, L - d);
+    }
+    return fmaxf(d - reach, 0.f);
+}
+
+// Do two boxes come within (Euclidean) distance R of each other?  Tighter
+// than growing one box by R along each axis: the grown box's corners, where
+// no point is within R, are left out.
+__device__ __forceinline__ bool box_within(const float4 &alo, const float4 &ahi, const float4 &blo,
+                                           const float4 &bhi, float R, const PhysParams &ph)
+{
+    const float gx = axis_gap(alo.x, ahi.x, blo.x, bhi.x, ph.periodic, ph.box_len_f[0]);
+    const float gy = axis_gap(alo.y, ahi.y, blo.y, bhi.y, ph.periodic, ph.box_len_f[1]);
+    const float gz = axis_gap(alo.z, ahi.z, blo.z, bhi.z, ph.periodic, ph.box_len_f[2]);
+    return gx * gx + gy * gy + gz * gz <= R * R * 1.00001f;
+}
+
 // Warp-cooperative depth-first walk of one problem's tree.  At the leaf level
 // visit(mask, first) is called (warp-uniformly) with the ballot of the up to
 // 32 sibling leaves first..first+31 whose boxes pass test(box), so that a
@@ -521,7 +550,7 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM>::WPB * 32, SPH_DENS_MINB) k_d
             };
             const T Rq2 = (T)Rq * (T)Rq;
             walk(
-                b, dy, [&](const NodeBox &nb) { return box_overlap(boxA.plo, boxA.phi, nb.plo, nb.phi, Rq, ph); },
+                b, dy, [&](const NodeBox &nb) { return box_within(boxA.plo, boxA.phi, nb.plo, nb.phi, Rq, ph); },
                 [&](unsigned mask, int first) {
                     stage_group<T, C::CH>(
                         b, leaf, mask, first, ph, nbuf, sc, [](bool, int, int, T, T, T) {},
@@ -730,7 +759,7 @@ __global__ void __launch_bounds__(FbCfg<T>::WPB * 32) k_density_fallback(BatchVi
                 nbuf = 0;
             };
             walk(
-                b, dy, [&](const NodeBox &nb) { return box_overlap(boxA.plo, boxA.phi, nb.plo, nb.phi, Rq, ph); },
+                b, dy, [&](const NodeBox &nb) { return box_within(boxA.plo, boxA.phi, nb.plo, nb.phi, Rq, ph); },
                 [&](unsigned mask, int first) {
                     stage_group<T, kFbCH>(
                         b, leaf, mask, first, ph, nbuf, sc, [](bool, int, int, T, T, T) {},
@@ -1010,7 +1039,7 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, SPH_FORCE_MINB) k_forc
         walk(
             b, dy,
             [&](const NodeBox &nb) {
-                return box_overlap(boxA.plo, boxA.phi, nb.plo, nb.phi, R, ph) ||
+                return box_within(boxA.plo, boxA.phi, nb.plo, nb.phi, R, ph) ||
                        box_overlap(boxA.plo, boxA.phi, nb.slo, nb.shi, 0.f, ph);
             },
             [&](unsigned mask, int first) {
