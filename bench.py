@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-reuse", action="store_true", help="skip the tree-reuse measurement")
     ap.add_argument("--lpp", type=int, default=0, help="lanes per particle (0: autotuned)")
     ap.add_argument("--workload", default="sod", choices=sorted(WORKLOADS),
                     help="sod (the default measured configuration), sedov or cloud")
@@ -378,6 +379,24 @@ def run_ours(args):
                 "speedup_of_mixed": (value / world) / v64}
         p64.close()
 
+    # tree reuse (Sec. 4.2): leaves rebuilt every 4th step, boxes updated in
+    # between -- a separate mode, not the headline step above
+    reuse = None
+    if not args.no_reuse:
+        k_every = 4
+        prmr = S.make_params(S.PREC_MIXED, **p, flags=S.FLAG_ASYNC, lanes_per_particle=args.lpp,
+                             tree_rebuild_every=k_every)
+        with torch.cuda.stream(stream):
+            pr = S.Problem(a, prmr, device=dev, stream=stream)
+            S.check(S.sph_density_h(pr.ctx), "sph_density_h")
+            S.check(S.sph_forces(pr.ctx), "sph_forces")
+        S.check(S.sph_run(pr.ctx, 2 * k_every), "sph_run")  # both step graphs built
+        msr, _, _, _ = time_steps(S, pr, stream, torch, 4 * k_every, flush)
+        vr = n * len(msr) / (np.sum(msr) * 1e-3)
+        reuse = {"rebuild_every": k_every, "value": vr, "unit": UNIT, "ms_per_step": float(np.mean(msr)),
+                 "speedup_of_rebuild_every_step": vr / (value / world)}
+        pr.close()
+
     diag = prob.diagnostics()
     prob.close()
     serve_res = None
@@ -402,7 +421,7 @@ def run_ours(args):
                    "l2": "flushed (256 MiB write) between timed steps", "graph": "one CUDA graph per step",
                    "lanes_per_particle": int(prob.params.lanes_per_particle) or "auto"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": kernels_per_step * args.steps,
-        "clocks": clocks, "fp64_gpu": fp64, "serving": serve_res,
+        "clocks": clocks, "fp64_gpu": fp64, "tree_reuse": reuse, "serving": serve_res,
         "step_diag": {"nr_iterations": diag.nr_iterations, "nr_max": diag.nr_max, "fallback": diag.fallback,
                       "leaves": diag.leaves, "ngb_mean": diag.ngb_mean, "candidates": diag.candidates},
     }

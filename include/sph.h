@@ -94,8 +94,13 @@ typedef struct {
     int precision;         /* SPH_PREC_*                                               */
     int kernel;            /* 0 = M4 cubic spline (the only value accepted)            */
     int leaf_size;         /* particles per leaf, 8/16/32 (0: chosen by the autotuner) */
-    int lanes_per_particle;/* 1/2/4 lanes of a warp per particle (0: autotuner)        */
+    int lanes_per_particle;/* 1/2/4/8 lanes of a warp per particle (0: autotuner)      */
     unsigned flags;        /* SPH_FLAG_*                                               */
+    int tree_rebuild_every;/* sph_step/sph_run: sort and rebuild the leaves every k-th
+                              step and only update the leaf and node boxes bottom-up in
+                              between (Sec. 4.2, tree reuse); 0 or 1: every step.
+                              Results do not depend on it beyond round-off; the tree's
+                              efficiency does.  Batched steps always rebuild.       */
 } sph_params;
 
 /* Caller-owned device arrays, FP64, length n, caller's particle order.

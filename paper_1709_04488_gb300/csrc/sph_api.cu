@@ -154,7 +154,9 @@ struct sph_ctx {
     ProbDiag *diag;
     ProbStatic host_ps;
     bool have_forces;
-    cudaGraphExec_t graph;
+    int since_build;              // steps since the leaves were last built
+    cudaGraphExec_t graph;        // one step that rebuilds the leaves
+    cudaGraphExec_t graph_reuse;  // one step that keeps them
     int graph_kernels;
     cudaEvent_t ev[SPH_NSTAGES + 1];
     bool timing;
@@ -325,7 +327,9 @@ int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *st
     c->stream = (cudaStream_t)stream;
     c->lpp = lpp_of(p, n);
     c->have_forces = false;
+    c->since_build = 0;
     c->graph = nullptr;
+    c->graph_reuse = nullptr;
     c->graph_kernels = 0;
     c->timing = (p->flags & SPH_FLAG_TIMING) != 0;
     for (int k = 0; k <= SPH_NSTAGES; ++k) c->ev[k] = nullptr;
@@ -429,15 +433,22 @@ struct Marks {
     }
 };
 
-static int enqueue_density(const BatchView &b, int precision, int use_pred, cudaStream_t st, const Marks &mk)
+// rebuild: new keys, sort and leaves; otherwise the leaves of the last build
+// keep their particles (gathered again by the last permutation) and only
+// their offsets and boxes, and the nodes above them, are recomputed
+static int enqueue_density(const BatchView &b, int precision, int use_pred, cudaStream_t st, const Marks &mk,
+                           bool rebuild = true)
 {
     mk.at(SPH_STAGE_SORT, st);
-    CU(launch_domain_and_keys(b, st));
-    CU(launch_radix_sort(b, st));
+    if (rebuild) {
+        CU(launch_domain_and_keys(b, st));
+        CU(launch_radix_sort(b, st));
+    }
     CU(launch_gather(b, st));
     mk.at(SPH_STAGE_TREE, st);
     mk.done(SPH_STAGE_SORT);
-    CU(launch_build_leaves(b, precision, st));
+    if (rebuild) CU(launch_build_leaves(b, precision, st));
+    else CU(launch_update_leaves(b, precision, st));
     mk.at(SPH_STAGE_DENSITY, st);
     mk.done(SPH_STAGE_TREE);
     CU(launch_density(b, precision, use_pred, st));
@@ -449,12 +460,13 @@ static int enqueue_density(const BatchView &b, int precision, int use_pred, cuda
     return SPH_OK;
 }
 
-static int enqueue_step(const BatchView &b, int precision, double dt, cudaStream_t st, const Marks &mk)
+static int enqueue_step(const BatchView &b, int precision, double dt, cudaStream_t st, const Marks &mk,
+                        bool rebuild = true)
 {
     mk.at(SPH_STAGE_KICK_DRIFT, st);
     CU(launch_kick_drift(b, dt, st));
     mk.done(SPH_STAGE_KICK_DRIFT);
-    int rc = enqueue_density(b, precision, 1, st, mk);
+    int rc = enqueue_density(b, precision, 1, st, mk, rebuild);
     if (rc) return rc;
     CU(launch_forces(b, precision, st));
     mk.at(SPH_STAGE_CLOSE, st);
@@ -476,6 +488,15 @@ static Marks marks_of(sph_ctx *c)
 }
 
 
+
+// tree reuse cadence (sph_params.tree_rebuild_every)
+static bool next_is_rebuild(const sph_ctx *c)
+{
+    const int every = c->prm.tree_rebuild_every;
+    return every <= 1 || c->since_build + 1 >= every;
+}
+
+static void count_step(sph_ctx *c, bool rebuild) { c->since_build = rebuild ? 0 : c->since_build + 1; }
 
 static int finish_call(sph_ctx *c)
 {
@@ -503,6 +524,7 @@ int sph_density_h(sph_ctx *c)
     if (rc) return rc;
     CU(launch_kick_close(c->bv, 0, 0, c->stream));
     c->have_forces = false;
+    c->since_build = 0;
     return finish_call(c);
 }
 
@@ -528,8 +550,10 @@ int sph_step(sph_ctx *c, double dt, double *dt_used)
         return fail(SPH_EINVAL, "no CFL step yet: call sph_density_h and sph_forces first, or pass dt > 0");
     if (!std::isfinite(dt)) return fail(SPH_EINVAL, "dt must be finite");
     clear_ran(c);
-    int rc = enqueue_step(c->bv, c->prm.precision, dt, c->stream, marks_of(c));
+    const bool rebuild = next_is_rebuild(c);
+    int rc = enqueue_step(c->bv, c->prm.precision, dt, c->stream, marks_of(c), rebuild);
     if (rc) return rc;
+    count_step(c, rebuild);
     c->have_forces = true;
     if (dt_used) {
         CU(cudaMemcpyAsync(dt_used, &c->diag->dt_cur, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -538,12 +562,12 @@ int sph_step(sph_ctx *c, double dt, double *dt_used)
     return finish_call(c);
 }
 
-static int build_graph(sph_ctx *c)
+static int build_graph(sph_ctx *c, bool rebuild = true)
 {
     cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     clear_ran(c);
-    int rc = enqueue_step(c->bv, c->prm.precision, -1.0, c->stream, marks_of(c));
+    int rc = enqueue_step(c->bv, c->prm.precision, -1.0, c->stream, marks_of(c), rebuild);
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (rc) {
         if (g) cudaGraphDestroy(g);
@@ -559,11 +583,12 @@ static int build_graph(sph_ctx *c)
         cudaGraphNodeType t;
         if (cudaGraphNodeGetType(nodes[k], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kern;
     }
-    c->graph_kernels = kern;
-    e = cudaGraphInstantiate(&c->graph, g, 0);
+    cudaGraphExec_t *slot = rebuild ? &c->graph : &c->graph_reuse;
+    if (rebuild) c->graph_kernels = kern;
+    e = cudaGraphInstantiate(slot, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        c->graph = nullptr;
+        *slot = nullptr;
         return fail(SPH_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
     }
     return SPH_OK;
@@ -575,25 +600,25 @@ int sph_run(sph_ctx *c, int nsteps)
     if (nsteps < 0) return fail(SPH_EINVAL, "nsteps must be >= 0");
     if (!c->have_forces) return fail(SPH_EINVAL, "no CFL step yet: call sph_density_h and sph_forces first");
     if (nsteps == 0) return SPH_OK;
-    if (c->stream == nullptr) {
-        // the legacy default stream cannot be captured: enqueue step by step
-        for (int k = 0; k < nsteps; ++k) {
+    for (int k = 0; k < nsteps; ++k) {
+        const bool rebuild = next_is_rebuild(c);
+        cudaGraphExec_t *slot = rebuild ? &c->graph : &c->graph_reuse;
+        if (c->stream == nullptr || !*slot) {
+            // the legacy default stream cannot be captured: enqueue eagerly;
+            // otherwise one eager step first so that lazily set kernel
+            // attributes are in place, then capture this kind of step
             clear_ran(c);
-            int rc = enqueue_step(c->bv, c->prm.precision, -1.0, c->stream, marks_of(c));
+            int rc = enqueue_step(c->bv, c->prm.precision, -1.0, c->stream, marks_of(c), rebuild);
             if (rc) return rc;
+            if (c->stream != nullptr) {
+                rc = build_graph(c, rebuild);
+                if (rc) return rc;
+            }
+        } else {
+            CU(cudaGraphLaunch(*slot, c->stream));
         }
-        return finish_call(c);
+        count_step(c, rebuild);
     }
-    if (!c->graph) {
-        // one eager step first so that lazily set kernel attributes are in place
-        clear_ran(c);
-        int rc = enqueue_step(c->bv, c->prm.precision, -1.0, c->stream, marks_of(c));
-        if (rc) return rc;
-        --nsteps;
-        rc = build_graph(c);
-        if (rc) return rc;
-    }
-    for (int k = 0; k < nsteps; ++k) CU(cudaGraphLaunch(c->graph, c->stream));
     return finish_call(c);
 }
 
@@ -691,6 +716,7 @@ int sph_destroy(sph_ctx *c)
 {
     if (!c) return SPH_OK;
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->graph_reuse) cudaGraphExecDestroy(c->graph_reuse);
     for (int k = 0; k <= SPH_NSTAGES; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     delete c;

@@ -357,7 +357,7 @@ __device__ __forceinline__ float offset_f(double v) { return (float)v; }
 // box is formed in FP32 from the offsets, widened for their rounding, plus
 // the reference point rounded down (up): only these two conversions per axis
 // and leaf, by lanes 0..2, run on the FP64 pipe besides the offsets.
-template <typename T4>
+template <typename T4, bool WRAP>
 __global__ void k_leaf_props(BatchView b)
 {
     const int lane = threadIdx.x & 31;
@@ -371,9 +371,16 @@ __global__ void k_leaf_props(BatchView b)
         float lo[3], hi[3];
         if (on) {
             T4 v;
-            v.x = (decltype(v.x))(b.sx[st + lane] - c[0]);
-            v.y = (decltype(v.y))(b.sy[st + lane] - c[1]);
-            v.z = (decltype(v.z))(b.sz[st + lane] - c[2]);
+            if (WRAP) {  // a kept leaf's particles may have crossed a periodic boundary
+                const PhysParams &ph = ps.ph;
+                v.x = (decltype(v.x))min_image(b.sx[st + lane] - c[0], ph.box_len[0], ph.periodic);
+                v.y = (decltype(v.y))min_image(b.sy[st + lane] - c[1], ph.box_len[1], ph.periodic);
+                v.z = (decltype(v.z))min_image(b.sz[st + lane] - c[2], ph.box_len[2], ph.periodic);
+            } else {
+                v.x = (decltype(v.x))(b.sx[st + lane] - c[0]);
+                v.y = (decltype(v.y))(b.sy[st + lane] - c[1]);
+                v.z = (decltype(v.z))(b.sz[st + lane] - c[2]);
+            }
             v.w = ps.uniform_m ? (decltype(v.w))ps.m_uniform : (decltype(v.w))b.sm[st + lane];
             ((T4 *)b.pm)[st + lane] = v;
             const float o[3] = {offset_f(v.x), offset_f(v.y), offset_f(v.z)};
@@ -506,8 +513,21 @@ cudaError_t launch_build_leaves(const BatchView &b, int precision, cudaStream_t 
     const long long tiles = (b.ntot + kLeafTile - 1) / kLeafTile;
     k_leaf_scan<<<(unsigned)tiles, kLeafThreads, 0, st>>>(b);
     int pb = persistent_blocks(256);
-    if (precision == SPH_PREC_FP64) k_leaf_props<dbl4><<<pb, 256, 0, st>>>(b);
-    else k_leaf_props<float4><<<pb, 256, 0, st>>>(b);
+    if (precision == SPH_PREC_FP64) k_leaf_props<dbl4, false><<<pb, 256, 0, st>>>(b);
+    else k_leaf_props<float4, false><<<pb, 256, 0, st>>>(b);
+    return cudaGetLastError();
+}
+
+// Tree reuse (Sec. 4.2): the leaves of the last build keep their particles;
+// offsets, leaf boxes and node boxes are recomputed from the new positions.
+// Offsets are taken by minimum image, as a kept leaf may straddle a periodic
+// boundary after particles moved.
+cudaError_t launch_update_leaves(const BatchView &b, int precision, cudaStream_t st)
+{
+    if (b.ntot == 0) return cudaSuccess;
+    int pb = persistent_blocks(256);
+    if (precision == SPH_PREC_FP64) k_leaf_props<dbl4, true><<<pb, 256, 0, st>>>(b);
+    else k_leaf_props<float4, true><<<pb, 256, 0, st>>>(b);
     return cudaGetLastError();
 }
 

@@ -240,6 +240,7 @@ cudaError_t launch_radix_sort(const BatchView &b, cudaStream_t st);
 cudaError_t launch_gather(const BatchView &b, cudaStream_t st);
 cudaError_t launch_set_sorted_h(const BatchView &b, const double *h_in, cudaStream_t st);
 cudaError_t launch_build_leaves(const BatchView &b, int precision, cudaStream_t st);
+cudaError_t launch_update_leaves(const BatchView &b, int precision, cudaStream_t st);  // tree reuse
 cudaError_t launch_refit(const BatchView &b, int precision, cudaStream_t st);
 cudaError_t launch_density(const BatchView &b, int precision, int use_pred, cudaStream_t st);
 cudaError_t launch_forces(const BatchView &b, int precision, cudaStream_t st);

@@ -44,6 +44,7 @@ class Params(C.Structure):
         ("leaf_size", C.c_int),
         ("lanes_per_particle", C.c_int),
         ("flags", C.c_uint),
+        ("tree_rebuild_every", C.c_int),
     ]
 
 

@@ -37,15 +37,17 @@ def test_struct_layouts_match_header(S, tmp_path):
     src = tmp_path / "sizes.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "sph.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu\\n\","
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
         "sizeof(sph_params),sizeof(sph_state),sizeof(sph_diag),sizeof(sph_server_cfg),"
-        "sizeof(sph_request),sizeof(sph_result),offsetof(sph_params,flags),offsetof(sph_diag,status));return 0;}\n")
+        "sizeof(sph_request),sizeof(sph_result),offsetof(sph_params,flags),offsetof(sph_diag,status),"
+        "offsetof(sph_params,tree_rebuild_every));return 0;}\n")
     exe = tmp_path / "sizes"
     import subprocess
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     want = [C.sizeof(S.Params), C.sizeof(S.State), C.sizeof(S.Diag), C.sizeof(S.ServerCfg),
-            C.sizeof(S.Request), C.sizeof(S.Result), S.Params.flags.offset, S.Diag.status.offset]
+            C.sizeof(S.Request), C.sizeof(S.Result), S.Params.flags.offset, S.Diag.status.offset,
+            S.Params.tree_rebuild_every.offset]
     assert got == want
 
 
