@@ -82,6 +82,11 @@ void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precis
         cap = cap / kBranch + nprob + 1;
     }
     b.fallback_list = c.take<int>(n);
+    b.group_cap = 2 * n;
+    b.group_pool = c.take<int2>(b.group_cap);
+    b.leaf_gofs = c.take<int>(ml);
+    b.leaf_ngroups = c.take<int>(ml);
+    b.leaf_hcap = c.take<float>(ml);
     b.counters = c.take<int>(32);
     b.scratch64 = c.take<long long>(8);
     // zero region (kept zero by the kernels that use it)

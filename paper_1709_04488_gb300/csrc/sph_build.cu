@@ -362,13 +362,15 @@ __global__ void k_leaf_props(BatchView b)
 {
     const int lane = threadIdx.x & 31;
     const int nleaf = b.counters[0];
+    if (blockIdx.x == 0)
+        for (int p = threadIdx.x; p < b.nprob; p += blockDim.x) b.dyn[p].lists_stale = 0;
     int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
     for (int leaf = w; leaf < nleaf; leaf += nw) {
         const int st = b.leaf_start[leaf], cnt = b.leaf_start[leaf + 1] - st;
         const ProbStatic &ps = b.prob[b.leaf_pid[leaf]];
         const bool on = lane < cnt;
         const double c[3] = {b.sx[st], b.sy[st], b.sz[st]};
-        float lo[3], hi[3];
+        float lo[3], hi[3], hp = 0.f;
         if (on) {
             T4 v;
             if (WRAP) {  // a kept leaf's particles may have crossed a periodic boundary
@@ -384,6 +386,10 @@ __global__ void k_leaf_props(BatchView b)
             v.w = ps.uniform_m ? (decltype(v.w))ps.m_uniform : (decltype(v.w))b.sm[st + lane];
             ((T4 *)b.pm)[st + lane] = v;
             const float o[3] = {offset_f(v.x), offset_f(v.y), offset_f(v.z)};
+            // predicted h_max: 1.1 x the largest guessed h (the h the density
+            // solve starts from); the force pass reuses the density walk's
+            // candidates when no final h of the leaf exceeds it
+            hp = __fmul_ru(kHPredict, __double2float_ru(b.sh[st + lane]));
             for (int a = 0; a < 3; ++a) {
                 lo[a] = widen_dn(o[a], fabsf(o[a]));
                 hi[a] = widen_up(o[a], fabsf(o[a]));
@@ -398,7 +404,9 @@ __global__ void k_leaf_props(BatchView b)
             lo[a] = warp_min(lo[a]);
             hi[a] = warp_max(hi[a]);
         }
-        float bl = 0.f, bh = 0.f;
+        hp = warp_max(hp);
+        const float h2p = __fmul_ru(2.0f, hp);  // predicted sphere box: position box grown by 2 h_max
+        float bl = 0.f, bh = 0.f, sl = 0.f, sh = 0.f;
         if (lane < 3) {
             const double ca = lane == 0 ? c[0] : lane == 1 ? c[1] : c[2];
             const float cd = __double2float_rd(ca), cu = __double2float_ru(ca);
@@ -407,17 +415,23 @@ __global__ void k_leaf_props(BatchView b)
             b.leaf_cf[6 * (long long)leaf + 3 + lane] = cu;
             bl = __fadd_rd(cd, axis_of(lo, lane));
             bh = __fadd_ru(cu, axis_of(hi, lane));
+            sl = __fadd_rd(cd, __fsub_rd(axis_of(lo, lane), h2p));
+            sh = __fadd_ru(cu, __fadd_ru(axis_of(hi, lane), h2p));
         }
         const float l0 = __shfl_sync(0xffffffffu, bl, 0), l1 = __shfl_sync(0xffffffffu, bl, 1),
                     l2 = __shfl_sync(0xffffffffu, bl, 2);
         const float h0 = __shfl_sync(0xffffffffu, bh, 0), h1 = __shfl_sync(0xffffffffu, bh, 1),
                     h2 = __shfl_sync(0xffffffffu, bh, 2);
+        const float s0 = __shfl_sync(0xffffffffu, sl, 0), s1 = __shfl_sync(0xffffffffu, sl, 1),
+                    s2 = __shfl_sync(0xffffffffu, sl, 2);
+        const float t0 = __shfl_sync(0xffffffffu, sh, 0), t1 = __shfl_sync(0xffffffffu, sh, 1),
+                    t2 = __shfl_sync(0xffffffffu, sh, 2);
         if (lane == 0) {
             NodeBox nb;
-            nb.plo = make_float4(l0, l1, l2, 0.f);
+            nb.plo = make_float4(l0, l1, l2, hp);  // h_max predicted until the refit
             nb.phi = make_float4(h0, h1, h2, (float)cnt);
-            nb.slo = nb.plo;
-            nb.shi = nb.phi;
+            nb.slo = make_float4(s0, s1, s2, 0.f);
+            nb.shi = make_float4(t0, t1, t2, 0.f);
             b.nodes[0][leaf] = nb;
         }
         tree_up(b, leaf);
@@ -469,6 +483,8 @@ __global__ void k_leaf_refit(BatchView b)
         const float h0 = __shfl_sync(0xffffffffu, bh, 0), h1 = __shfl_sync(0xffffffffu, bh, 1),
                     h2 = __shfl_sync(0xffffffffu, bh, 2);
         if (lane == 0) {
+            // the density walk's recorded candidates cover h up to leaf_hcap
+            if (hm > b.leaf_hcap[leaf]) atomicOr(&b.dyn[b.leaf_pid[leaf]].lists_stale, 1);
             NodeBox &nb = b.nodes[0][leaf];
             nb.plo.w = hm;
             nb.slo = make_float4(l0, l1, l2, 0.f);

@@ -44,7 +44,8 @@ __device__ __forceinline__ void reset_counters(const BatchView &b, int mode)
 {
     const int k = threadIdx.x;
     if (blockIdx.x != 0 || k >= 32) return;
-    const bool all = k == kSlowCounter || k == kTimeoutCounter || (k >= kDensityCounter && k < kForceCounter + 4);
+    const bool all = k == kSlowCounter || k == kPoolCounter || k == kTimeoutCounter ||
+                     (k >= kDensityCounter && k < kForceCounter + 4);
     const bool forces = k == kTimeoutCounter || (k >= kForceCounter && k < kForceCounter + 4);
     if (mode == 1 ? all : forces) b.counters[k] = 0;
 }

@@ -16,10 +16,13 @@ constexpr int kMortonBits = 10;     // bits per axis of the Morton key
 constexpr int kMortonTotal = 3 * kMortonBits;
 constexpr double kPi = 3.14159265358979323846;
 // slots of BatchView::counters: 0 leaves, 1..7 nodes per level, 8 slow-path
-// count, 15 look-back timeout, 16..23 density leaf tickets (per class),
-// 24..27 force leaf tickets (per lanes per particle); the step's first
-// kernel clears 8, 15 and 16..27, a forces-only call clears 15 and 24..27
-constexpr int kSlowCounter = 8, kTimeoutCounter = 15, kDensityCounter = 16, kForceCounter = 24;
+// count, 9 groups used in the candidate-group pool, 15 look-back timeout,
+// 16..23 density leaf tickets (per class), 24..27 force leaf tickets (per
+// lanes per particle); the step's first kernel clears 8, 9, 15 and 16..27,
+// a forces-only call clears 15 and 24..27
+constexpr int kSlowCounter = 8, kPoolCounter = 9, kTimeoutCounter = 15, kDensityCounter = 16, kForceCounter = 24;
+constexpr int kMaxLeafGroups = 32;  // candidate-leaf groups recorded per leaf (one per lane)
+constexpr float kHPredict = 1.1f;   // predicted sphere boxes use 1.1 x the guessed h
 
 // Status bits kept on the device per problem (mapped to SPH_E* on the host).
 enum : unsigned {
@@ -87,6 +90,8 @@ struct ProbDyn {
     int top_level;       // highest tree level (0 = the leaves themselves)
     int node_off[kMaxLevels + 1];  // global index of this problem's first node per level
     int node_cnt[kMaxLevels + 1];  // nodes per level (level 0 = leaves)
+    int lists_stale;     // some leaf's final h exceeds what its recorded candidate groups cover
+    int pad_;
 };
 
 // 32-byte vector of four doubles (FP64 staging)
@@ -156,6 +161,13 @@ struct BatchView {
     char *zero_lo;               // [zero_lo, zero_lo + zero_bytes) holds the two above
     size_t zero_bytes;
     int *fallback_list;          // [ntot] sorted indices needing the slow path
+    // candidate-leaf groups (first leaf, ballot of the 32 siblings) the
+    // density walk visited per leaf, for the force pass to reuse
+    int2 *group_pool;            // [group_cap]
+    long long group_cap;
+    int *leaf_gofs;              // [max_leaves] first pool entry of the leaf's groups
+    int *leaf_ngroups;           // [max_leaves] group count, -1: not recorded (walk)
+    float *leaf_hcap;            // [max_leaves] largest h the recorded groups cover
     int *counters;               // [32], slots as listed at kSlowCounter
     long long *scratch64;        // [8]
 };

@@ -490,10 +490,17 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM>::WPB * 32, SPH_DENS_MINB) k_d
         // their rank among the group's hits instead of by slot, so that the
         // lists fill evenly; taken after a slot-dealt list overflowed
         bool bal = false;
+        // candidate-leaf groups of the last walk (lane k holds group k) and
+        // the walk radius they cover, kept for the force pass
+        int ng = 0, g_first = 0;
+        unsigned g_mask = 0u;
+        float Rq_last = 0.f;
         for (int attempt = 0;; ++attempt) {
             const T hs = h * (T)kListMargin;
             float Rq = warp_max((active && !fail) ? __fmul_ru(2.0f, (float)hs) : 0.f) * 1.0001f;
             const T R2 = (T(2) * hs) * (T(2) * hs);
+            Rq_last = Rq;
+            ng = 0;
             cnt = 0;
             int gcnt = 0;
             bool ovf = false;
@@ -549,11 +556,27 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM>::WPB * 32, SPH_DENS_MINB) k_d
                 nbuf = 0;
             };
             const T Rq2 = (T)Rq * (T)Rq;
+            // visit leaves within Rq (gather) or whose predicted smoothing
+            // spheres reach this leaf (what the force pass will need); stage
+            // only the former
+            bool near = false;  // this lane's last tested node is within Rq
             walk(
-                b, dy, [&](const NodeBox &nb) { return box_within(boxA.plo, boxA.phi, nb.plo, nb.phi, Rq, ph); },
+                b, dy,
+                [&](const NodeBox &nb) {
+                    near = box_within(boxA.plo, boxA.phi, nb.plo, nb.phi, Rq, ph);
+                    return near || box_overlap(boxA.plo, boxA.phi, nb.slo, nb.shi, 0.f, ph);
+                },
                 [&](unsigned mask, int first) {
+                    if (lane == ng) {
+                        g_first = first;
+                        g_mask = mask;
+                    }
+                    ++ng;
+                    // the leaf-level tests just made: stage the leaves within Rq
+                    const unsigned gm = __ballot_sync(FULL, near && ((mask >> lane) & 1u));
+                    if (gm == 0u) return;
                     stage_group<T, C::CH>(
-                        b, leaf, mask, first, ph, nbuf, sc, [](bool, int, int, T, T, T) {},
+                        b, leaf, gm, first, ph, nbuf, sc, [](bool, int, int, T, T, T) {},
                         [&](int j) { return pm[j]; },
                         [&](const V &q) { return box_dist2<T>(q, flo, fhi) < Rq2; },
                         [&](int slot, const V &q, int, int) { cand[slot] = q; }, flush);
@@ -623,6 +646,21 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM>::WPB * 32, SPH_DENS_MINB) k_d
                 break;
             }
             need = false;
+        }
+        // record the last walk's groups for the force pass (lane 0 reserves
+        // pool space); not recorded: the force pass walks for this leaf
+        {
+            int base = 0;
+            if (lane == 0) {
+                base = ng <= kMaxLeafGroups ? atomicAdd(&b.counters[kPoolCounter], ng) : -1;
+                const bool fits = base >= 0 && (long long)base + ng <= b.group_cap;
+                b.leaf_gofs[leaf] = fits ? base : 0;
+                b.leaf_ngroups[leaf] = fits ? ng : -1;
+                b.leaf_hcap[leaf] = fminf(Rq_last / 2.0002f, boxA.plo.w);
+                base = fits ? base : -1;
+            }
+            base = __shfl_sync(FULL, base, 0);
+            if (base >= 0 && lane < ng) b.group_pool[base + lane] = make_int2(g_first, (int)g_mask);
         }
         // final evaluation at the returned h, unless the sums there are kept
         T S0 = kS0, S1 = kS1;
@@ -1036,13 +1074,11 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, SPH_FORCE_MINB) k_forc
             __syncwarp();
             nbuf = 0;
         };
-        walk(
-            b, dy,
-            [&](const NodeBox &nb) {
-                return box_within(boxA.plo, boxA.phi, nb.plo, nb.phi, R, ph) ||
-                       box_overlap(boxA.plo, boxA.phi, nb.slo, nb.shi, 0.f, ph);
-            },
-            [&](unsigned mask, int first) {
+        auto node_test = [&](const NodeBox &nb) {
+            return box_within(boxA.plo, boxA.phi, nb.plo, nb.phi, R, ph) ||
+                   box_overlap(boxA.plo, boxA.phi, nb.slo, nb.shi, 0.f, ph);
+        };
+        auto visit = [&](unsigned mask, int first) {
                 if (ntab + __popc(mask) > C::TAB) {
                     test();
                     eval_lists();
@@ -1075,7 +1111,23 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, SPH_FORCE_MINB) k_forc
                     },
                     test);
                 ntab += __popc(mask);
-            });
+        };
+        // the candidate groups the density walk recorded cover every pair
+        // unless some final h outgrew them (then walk the tree again)
+        const int ngl = b.leaf_ngroups[leaf];
+        if (!dy.lists_stale && ngl >= 0) {
+            const int gofs = b.leaf_gofs[leaf];
+            for (int g = 0; g < ngl; ++g) {
+                const int2 e = b.group_pool[gofs + g];
+                const unsigned mask = (unsigned)e.y;
+                bool ok = false;
+                if ((mask >> lane) & 1u) ok = node_test(b.nodes[0][e.x + lane]);
+                const unsigned fm = __ballot_sync(FULL, ok);
+                if (fm) visit(fm, e.x);
+            }
+        } else {
+            walk(b, dy, node_test, visit);
+        }
         test();
         eval_lists();
         // combine the lanes of each particle; FP64 for the compensated sums

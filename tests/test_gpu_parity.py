@@ -324,3 +324,19 @@ def test_tree_reuse_matches_oracle(S, oracle_mod):
         assert _rms_err(_acc(g), np.stack([ref.ax, ref.ay, ref.az], 1)) < 1e-4
         # 8 steps at |v| ~ 2 integrate the acceleration differences above
         assert np.max(np.abs(g["x"] - ref.x)) < 1e-7
+
+
+@pytest.mark.parametrize("guess", [1.0, 0.5])
+def test_force_candidates_reused_or_rewalked(S, oracle_mod, guess):
+    """The force pass reuses the density walk's candidate leaves when every
+    final h stays within 1.1x the starting guess (guess = the converged h) and
+    walks the tree again otherwise (guess = half of it); both match the
+    oracle."""
+    O = oracle_mod
+    a, p = _moving_lattice(14, seed=41)
+    P, ref = _oracle(O, a, p)
+    a2 = dict(a, h=ref.h * guess)
+    g = _gpu(S, a2, p, S.PREC_MIXED).numpy()
+    assert _rel(g["rho"], ref.rho) < 1e-5
+    assert _rms_err(_acc(g), np.stack([ref.ax, ref.ay, ref.az], 1)) < 1e-4
+    assert _rms_err(g["du"], ref.du) < 1e-4
