@@ -105,6 +105,11 @@ void carve_tables(Carver &c, BatchView &b, int nprob)
     b.prob_base = c.take<long long>(nprob + 1);
 }
 
+// Up to 2^20 particles the finest two of the ten Morton levels are left
+// unsorted: the 8-level cells (1/256 of the box per axis) already hold under
+// one particle on average for such sizes, and the sort needs one pass fewer.
+int key_low_bits(long long ntot) { return ntot <= (1ll << 20) ? 6 : 0; }
+
 int key_bits_for(int nprob)
 {
     int bits = 0;
@@ -352,6 +357,7 @@ int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *st
     carve_arrays(cv, c->bv, n, 1, p->precision);
     c->bv.ntot = n;
     c->bv.key_bits = key_bits_for(1);
+    c->bv.key_lo = key_low_bits(n);
     c->bv.lpp_mask = mask_of(c->lpp);
     c->bv.any_isolated = p->periodic ? 0 : 1;
     ProbStatic &ps = c->host_ps;
@@ -788,6 +794,7 @@ int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, 
     carve_arrays(cv, b, ntot, nctx, prec);
     b.ntot = ntot;
     b.key_bits = key_bits_for(nctx);
+    b.key_lo = key_low_bits(ntot);
     b.lpp_mask = mask;
     b.dens_mask = dmask;
     b.any_isolated = b_any_isolated;

@@ -22,7 +22,10 @@ constexpr double kPi = 3.14159265358979323846;
 // a forces-only call clears 15 and 24..27
 constexpr int kSlowCounter = 8, kPoolCounter = 9, kTimeoutCounter = 15, kDensityCounter = 16, kForceCounter = 24;
 constexpr int kMaxLeafGroups = 32;  // candidate-leaf groups recorded per leaf (one per lane)
-constexpr float kHPredict = 1.1f;   // predicted sphere boxes use 1.1 x the guessed h
+#ifndef SPH_HPREDICT
+#define SPH_HPREDICT 1.1f
+#endif
+constexpr float kHPredict = SPH_HPREDICT;  // predicted sphere boxes use this x the guessed h
 
 // Status bits kept on the device per problem (mapped to SPH_E* on the host).
 enum : unsigned {
@@ -127,6 +130,7 @@ struct BatchView {
     long long ntot;              // particles over all problems
     int max_leaves;              // capacity of the leaf arrays
     int key_bits;                // bits the radix sort must order
+    int key_lo;                  // lowest key bit that is sorted (the bits below are cleared)
     int any_isolated;            // some problem is isolated (needs a bounding box)
     ProbStatic *prob;            // [nprob]
     ProbDyn *dyn;                // [nprob]
@@ -280,6 +284,7 @@ int fail(int code, const char *fmt, ...);  // records the thread's error message
 void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precision);
 void carve_tables(Carver &c, BatchView &b, int nprob);
 int key_bits_for(int nprob);
+int key_low_bits(long long ntot);  // Morton bits left unsorted (cleared) for ntot particles
 int mask_of(int lpp);
 int dens_class_bit(int lpp, int uniform_m);
 int validate(const sph_params *p);

@@ -93,6 +93,7 @@ extern "C" int sph_density_forces_noalloc(const sph_params *p, int64_t n, const 
     const int lpp = lpp_of(p, n);
     b.ntot = n;
     b.key_bits = key_bits_for(1);
+    b.key_lo = key_low_bits(n);
     b.lpp_mask = mask_of(lpp);
     b.dens_mask = dens_class_bit(lpp, 0);  // masses are not inspected here: distance-and-mass lists
     b.any_isolated = p->periodic ? 0 : 1;

@@ -183,7 +183,7 @@ __device__ __forceinline__ unsigned morton_key_code(const BatchView &b, int p, l
 }
 
 // Keys of every particle, and the digit histograms of every pass.
-__global__ void k_keys_hist(BatchView b, unsigned *hist, int passes)
+__global__ void k_keys_hist(BatchView b, unsigned long long *kout, unsigned *hist, int passes, int lo)
 {
     __shared__ unsigned h[8][256];
     for (int k = threadIdx.x; k < 8 * 256; k += blockDim.x) (&h[0][0])[k] = 0u;
@@ -194,10 +194,10 @@ __global__ void k_keys_hist(BatchView b, unsigned *hist, int passes)
         unsigned long long key = 0ull;
         if (ok) {
             int p = find_problem(b.prob_base, b.nprob, g);
-            key = ((unsigned long long)p << kMortonTotal) | morton_key_code(b, p, g);
-            b.keys[0][g] = key;
+            key = ((unsigned long long)p << kMortonTotal) | (morton_key_code(b, p, g) & ~((1u << lo) - 1u));
+            kout[g] = key;
         }
-        for (int q = 0; q < passes; ++q) warp_hist_add(h[q], (unsigned)(key >> (8 * q)) & 255u, ok);
+        for (int q = 0; q < passes; ++q) warp_hist_add(h[q], (unsigned)(key >> (lo + 8 * q)) & 255u, ok);
     }
     __syncthreads();
     for (int k = threadIdx.x; k < passes * 256; k += blockDim.x) {
@@ -343,26 +343,24 @@ cudaError_t launch_radix_sort(const BatchView &b, cudaStream_t st)
     const int items = sort_items(n);
     const long long tile_keys = (long long)kSortThreads * items;
     const int ntile = (int)((n + tile_keys - 1) / tile_keys);
-    const int passes = (b.key_bits + 7) / 8;
+    const int passes = (b.key_bits - b.key_lo + 7) / 8;
     // hist[passes][256] | tile counters[passes] | status[passes][ntile][256]
     unsigned *hist = b.hist, *ctr = b.hist + passes * 256, *status = b.hist + passes * 256 + 8;
     cudaMemsetAsync(b.hist, 0, sizeof(unsigned) * ((size_t)passes * 256 + 8 + (size_t)passes * ntile * 256), st);
     int kb = (int)((n + 255) / 256);
     int cap = dev_info().sm_count * 8;
-    k_keys_hist<<<kb < cap ? kb : cap, 256, 0, st>>>(b, hist, passes);
-    int src = 0;
+    // the passes ping-pong between the two key buffers: start in the one that
+    // leaves the sorted keys in keys[0] for the leaf builder
+    int src = passes & 1;
+    k_keys_hist<<<kb < cap ? kb : cap, 256, 0, st>>>(b, b.keys[src], hist, passes, b.key_lo);
     for (int pass = 0; pass < passes; ++pass) {
         const bool last = pass == passes - 1;
         unsigned *vdst = last ? (unsigned *)b.perm : b.vals[src ^ 1];
         auto kern = items == 1 ? k_onesweep<1> : items == 2 ? k_onesweep<2> : items == 4 ? k_onesweep<4> : k_onesweep<8>;
-        kern<<<ntile, kSortThreads, 0, st>>>(b.keys[src], b.vals[src], b.keys[src ^ 1], vdst, n, 8 * pass,
+        kern<<<ntile, kSortThreads, 0, st>>>(b.keys[src], b.vals[src], b.keys[src ^ 1], vdst, n, b.key_lo + 8 * pass,
                                              hist + pass * 256, status + (size_t)pass * ntile * 256, ctr + pass,
                                              pass == 0, (unsigned *)&b.counters[kTimeoutCounter]);
         src ^= 1;
-    }
-    if (src != 0) {
-        // leave the sorted keys in keys[0] for the leaf builder
-        cudaMemcpyAsync(b.keys[0], b.keys[1], sizeof(unsigned long long) * n, cudaMemcpyDeviceToDevice, st);
     }
     return cudaGetLastError();
 }
