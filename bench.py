@@ -77,12 +77,12 @@ def kernel_source_sha(srcs):
 PAIR_SOURCES = [os.path.join(ROOT, "paper_1709_04488_gb300", "csrc", f) for f in ("sph_pairs.cu", "sph_tuned.h")]
 
 
-def traffic_for(workload):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu
-    summary, if the kernel sources are unchanged since that capture."""
+def traffic_for(workload, kernel):
+    """DRAM bytes per launch of a pair kernel from the committed ncu summary,
+    if the kernel sources are unchanged since that capture."""
     try:
         with open(os.path.join(ROOT, "profiles", "roofline_traffic.json")) as fh:
-            rec = json.load(fh).get(workload)
+            rec = json.load(fh).get(workload, {}).get(kernel)
         if rec and rec.get("source_sha256") == kernel_source_sha(PAIR_SOURCES):
             return rec
     except Exception:
@@ -323,20 +323,23 @@ def run_ours(args):
     dens_ms, force_ms = st[S.STAGES.index("density")], st[S.STAGES.index("forces")]
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     peak, mhz = peak_fp32_tflops(sm_count)
-    if force_ms >= dens_ms:
-        kern, flops, t_ms = "k_forces", np.mean(fp) * FLOPS_FORCE_PAIR, force_ms
-    else:
-        kern, flops, t_ms = "k_density", np.mean(dp) * FLOPS_DENSITY_PAIR, dens_ms
+    per_kernel = {
+        "k_forces": {"ms": float(force_ms), "flop": float(np.mean(fp) * FLOPS_FORCE_PAIR)},
+        "k_density": {"ms": float(dens_ms), "flop": float(np.mean(dp) * FLOPS_DENSITY_PAIR)},
+    }
+    for rec in per_kernel.values():
+        rec["achieved"] = rec["flop"] / (rec["ms"] * 1e-3) / 1e12 if rec["ms"] > 0 else 0.0
+    kern = "k_forces" if force_ms >= dens_ms else "k_density"  # the dominant pair kernel
+    flops, t_ms = per_kernel[kern]["flop"], per_kernel[kern]["ms"]
     achieved = flops / (t_ms * 1e-3) / 1e12
-    tr = traffic_for(args.workload)
-    traffic = None
-    if tr and tr.get("kernel") == kern:
-        traffic = tr["dram_bytes_per_launch"]
+    tr = traffic_for(args.workload, kern)
+    traffic = tr["dram_bytes_per_launch"] if tr else None
     roof = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
             "peak_basis": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz",
             "stage_ms": {k: float(v) for k, v in zip(S.STAGES, st)},
-            "density_pairs_per_step": float(np.mean(dp)), "force_pairs_per_step": float(np.mean(fp))}
+            "density_pairs_per_step": float(np.mean(dp)), "force_pairs_per_step": float(np.mean(fp)),
+            "pair_kernels": {k: dict(v, frac=v["achieved"] / peak) for k, v in per_kernel.items()}}
 
     # end to end through the C ABI with host buffers: H2D of the step's input
     # state from pinned memory, one step, D2H of the resulting state
