@@ -138,6 +138,9 @@ typedef struct {
     int64_t leaves;        /* leaves built                                                  */
     int32_t status;        /* device-side status (SPH_OK or SPH_E*)                         */
     int32_t unconverged;   /* particles that met SPH_ENOCONV                                */
+    int32_t walk_reused;   /* 1: the last force pass took its candidate leaves from the
+                              density pass's walk; 0: it walked the tree itself            */
+    int32_t pad_;
 } sph_diag;
 
 typedef struct sph_ctx sph_ctx;

@@ -693,6 +693,7 @@ int sph_diagnostics(sph_ctx *c, sph_diag *out)
     out->leaves = d.leaves;
     out->status = status_to_code(d.status);
     out->unconverged = d.unconverged;
+    out->walk_reused = d.walk_reused;
     return SPH_OK;
 }
 

@@ -370,7 +370,7 @@ __global__ void k_leaf_props(BatchView b)
         const ProbStatic &ps = b.prob[b.leaf_pid[leaf]];
         const bool on = lane < cnt;
         const double c[3] = {b.sx[st], b.sy[st], b.sz[st]};
-        float lo[3], hi[3], hp = 0.f;
+        float lo[3], hi[3], slo_[3], shi_[3], hp = 0.f;
         if (on) {
             T4 v;
             if (WRAP) {  // a kept leaf's particles may have crossed a periodic boundary
@@ -386,26 +386,31 @@ __global__ void k_leaf_props(BatchView b)
             v.w = ps.uniform_m ? (decltype(v.w))ps.m_uniform : (decltype(v.w))b.sm[st + lane];
             ((T4 *)b.pm)[st + lane] = v;
             const float o[3] = {offset_f(v.x), offset_f(v.y), offset_f(v.z)};
-            // predicted h_max: 1.1 x the largest guessed h (the h the density
-            // solve starts from); the force pass reuses the density walk's
-            // candidates when no final h of the leaf exceeds it
+            // predicted smoothing spheres: 1.1 x the guessed h (the h the
+            // density solve starts from); the force pass reuses the density
+            // walk's candidates when no final h exceeds its prediction
             hp = __fmul_ru(kHPredict, __double2float_ru(b.sh[st + lane]));
+            const float h2 = __fmul_ru(2.0f, hp);
             for (int a = 0; a < 3; ++a) {
                 lo[a] = widen_dn(o[a], fabsf(o[a]));
                 hi[a] = widen_up(o[a], fabsf(o[a]));
+                const float mag = __fadd_ru(fabsf(o[a]), h2);
+                slo_[a] = widen_dn(__fsub_rd(o[a], h2), mag);
+                shi_[a] = widen_up(__fadd_ru(o[a], h2), mag);
             }
         } else {
             for (int a = 0; a < 3; ++a) {
-                lo[a] = INFINITY;
-                hi[a] = -INFINITY;
+                lo[a] = slo_[a] = INFINITY;
+                hi[a] = shi_[a] = -INFINITY;
             }
         }
         for (int a = 0; a < 3; ++a) {
             lo[a] = warp_min(lo[a]);
             hi[a] = warp_max(hi[a]);
+            slo_[a] = warp_min(slo_[a]);
+            shi_[a] = warp_max(shi_[a]);
         }
         hp = warp_max(hp);
-        const float h2p = __fmul_ru(2.0f, hp);  // predicted sphere box: position box grown by 2 h_max
         float bl = 0.f, bh = 0.f, sl = 0.f, sh = 0.f;
         if (lane < 3) {
             const double ca = lane == 0 ? c[0] : lane == 1 ? c[1] : c[2];
@@ -415,8 +420,8 @@ __global__ void k_leaf_props(BatchView b)
             b.leaf_cf[6 * (long long)leaf + 3 + lane] = cu;
             bl = __fadd_rd(cd, axis_of(lo, lane));
             bh = __fadd_ru(cu, axis_of(hi, lane));
-            sl = __fadd_rd(cd, __fsub_rd(axis_of(lo, lane), h2p));
-            sh = __fadd_ru(cu, __fadd_ru(axis_of(hi, lane), h2p));
+            sl = __fadd_rd(cd, axis_of(slo_, lane));
+            sh = __fadd_ru(cu, axis_of(shi_, lane));
         }
         const float l0 = __shfl_sync(0xffffffffu, bl, 0), l1 = __shfl_sync(0xffffffffu, bl, 1),
                     l2 = __shfl_sync(0xffffffffu, bl, 2);
@@ -483,8 +488,6 @@ __global__ void k_leaf_refit(BatchView b)
         const float h0 = __shfl_sync(0xffffffffu, bh, 0), h1 = __shfl_sync(0xffffffffu, bh, 1),
                     h2 = __shfl_sync(0xffffffffu, bh, 2);
         if (lane == 0) {
-            // the density walk's recorded candidates cover h up to leaf_hcap
-            if (hm > b.leaf_hcap[leaf]) atomicOr(&b.dyn[b.leaf_pid[leaf]].lists_stale, 1);
             NodeBox &nb = b.nodes[0][leaf];
             nb.plo.w = hm;
             nb.slo = make_float4(l0, l1, l2, 0.f);

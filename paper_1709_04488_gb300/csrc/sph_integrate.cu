@@ -137,6 +137,24 @@ __global__ void k_kick_close(BatchView b, int do_kick, int forces_ran, int items
                 d->steps += 1;
             }
             d->leaves = b.dyn[p].nleaf;
+            if (forces_ran) {
+                // recording the force candidates in the density walk pays only
+                // while they stay valid: after a step where they did not, walk
+                // without recording for a while (8 steps, doubling up to 256
+                // while retries keep failing), then try again
+                int reused = 0;
+                if (d->reuse_hold > 0) {
+                    --d->reuse_hold;
+                } else if (b.dyn[p].lists_stale) {
+                    const int len = d->reuse_backoff > 0 ? d->reuse_backoff : kReuseHold;
+                    d->reuse_hold = len;
+                    d->reuse_backoff = len < 256 ? 2 * len : 256;
+                } else {
+                    reused = 1;
+                    d->reuse_backoff = kReuseHold;
+                }
+                d->walk_reused = reused;
+            }
         }
     }
     const long long base = (long long)blockIdx.x * blockDim.x * items;

@@ -26,6 +26,7 @@ constexpr int kMaxLeafGroups = 32;  // candidate-leaf groups recorded per leaf (
 #define SPH_HPREDICT 1.1f
 #endif
 constexpr float kHPredict = SPH_HPREDICT;  // predicted sphere boxes use this x the guessed h
+constexpr int kReuseHold = 8;  // first hold after a step whose final h outgrew the records
 
 // Status bits kept on the device per problem (mapped to SPH_E* on the host).
 enum : unsigned {
@@ -66,7 +67,9 @@ struct ProbDiag {
     int nr_max, ngb_min, ngb_max;
     unsigned status;
     int unconverged;
-    int pad_;
+    int walk_reused;     // the last force pass reused the density walk's candidates
+    int reuse_hold;      // steps left before the density walk records candidates again
+    int reuse_backoff;   // length of the next hold (doubles while the records keep failing)
 };
 
 // Host-written description of one problem inside a batch.

@@ -474,6 +474,8 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM>::WPB * 32, SPH_DENS_MINB) k_d
         const double Lmin = ph.periodic ? fmin(ph.box_len[0], fmin(ph.box_len[1], ph.box_len[2])) : INFINITY;
         const T hbox = (T)(0.25 * Lmin);  // h beyond a quarter of the box: SPH_EBOX
         T h = active ? (T)b.sh[s] : T(1);
+        // the leaf pass predicted this particle's sphere from the same start
+        const float hpred = active ? __fmul_ru(kHPredict, __double2float_ru(b.sh[s])) : 0.f;
         if (active && !(h > T(0))) {
             double ext = ph.periodic ? fmax(ph.box_len[0], fmax(ph.box_len[1], ph.box_len[2])) : 1.0 / dy.dom_inv;
             h = (T)(ph.eta * cbrt(ext * ext * ext / (double)(ps.n > 0 ? ps.n : 1)));
@@ -491,7 +493,9 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM>::WPB * 32, SPH_DENS_MINB) k_d
         // lists fill evenly; taken after a slot-dealt list overflowed
         bool bal = false;
         // candidate-leaf groups of the last walk (lane k holds group k) and
-        // the walk radius they cover, kept for the force pass
+        // the walk radius they cover, kept for the force pass unless the
+        // recent records outgrew their h (then the force pass walks)
+        const bool record = ps.diag->reuse_hold == 0;
         int ng = 0, g_first = 0;
         unsigned g_mask = 0u;
         float Rq_last = 0.f;
@@ -564,7 +568,7 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM>::WPB * 32, SPH_DENS_MINB) k_d
                 b, dy,
                 [&](const NodeBox &nb) {
                     near = box_within(boxA.plo, boxA.phi, nb.plo, nb.phi, Rq, ph);
-                    return near || box_overlap(boxA.plo, boxA.phi, nb.slo, nb.shi, 0.f, ph);
+                    return near || (record && box_overlap(boxA.plo, boxA.phi, nb.slo, nb.shi, 0.f, ph));
                 },
                 [&](unsigned mask, int first) {
                     if (lane == ng) {
@@ -652,11 +656,11 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM>::WPB * 32, SPH_DENS_MINB) k_d
         {
             int base = 0;
             if (lane == 0) {
-                base = ng <= kMaxLeafGroups ? atomicAdd(&b.counters[kPoolCounter], ng) : -1;
+                base = record && ng <= kMaxLeafGroups ? atomicAdd(&b.counters[kPoolCounter], ng) : -1;
                 const bool fits = base >= 0 && (long long)base + ng <= b.group_cap;
                 b.leaf_gofs[leaf] = fits ? base : 0;
                 b.leaf_ngroups[leaf] = fits ? ng : -1;
-                b.leaf_hcap[leaf] = fminf(Rq_last / 2.0002f, boxA.plo.w);
+                b.leaf_hcap[leaf] = Rq_last / 2.0002f;
                 base = fits ? base : -1;
             }
             base = __shfl_sync(FULL, base, 0);
@@ -698,11 +702,16 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM>::WPB * 32, SPH_DENS_MINB) k_d
                 atomicOr(&ps.diag->status, ST_NOCONV);
                 atomicAdd(&ps.diag->unconverged, 1);
             }
+            // the recorded candidate groups cover this particle's pairs only
+            // if its final h stays within the walk radius and its prediction
+            const float hf = to_float_ru(h);
+            if (hf > hpred || hf > Rq_last / 2.0002f) atomicOr(&b.dyn[p].lists_stale, 1);
         }
         if (active && fail && sub == 0) {
             int k = atomicAdd(&b.counters[kSlowCounter], 1);
             b.fallback_list[k] = (int)s;
             b.sh[s] = (double)h;  // best guess so far
+            b.hf[s] = hpred;      // for the slow path's coverage check
         }
         // statistics (one atomic per warp per quantity)
         long long tp = warp_sum(pairs), tt = warp_sum(tested);
@@ -883,6 +892,8 @@ __global__ void __launch_bounds__(FbCfg<T>::WPB * 32) k_density_fallback(BatchVi
         sums(h);
         pairs += nn;
         if (lane == 0) {
+            const float hf = to_float_ru(h);
+            if (hf > b.hf[s] || hf > b.leaf_hcap[leaf]) atomicOr(&b.dyn[p].lists_stale, 1);
             density_epilogue<T>(b, ps, s, pi, h, S0, S1, use_pred);
             if (noconv) {
                 atomicOr(&ps.diag->status, ST_NOCONV);

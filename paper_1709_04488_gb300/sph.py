@@ -78,6 +78,8 @@ class Diag(C.Structure):
         ("leaves", C.c_int64),
         ("status", C.c_int32),
         ("unconverged", C.c_int32),
+        ("walk_reused", C.c_int32),
+        ("pad_", C.c_int32),
     ]
 
     def as_dict(self):
