@@ -64,6 +64,7 @@ class _Params(C.Structure):
         ("h_tol", C.c_double),
         ("h_max_iter", C.c_int),
         ("use_grid", C.c_int),
+        ("kernel", C.c_int),
     ]
 
 
@@ -94,6 +95,14 @@ def lib():
             fn = getattr(L, name)
             fn.restype = C.c_double
             fn.argtypes = [C.c_double, C.c_double]
+        for name in ("orc_g6", "orc_dg6"):
+            fn = getattr(L, name)
+            fn.restype = C.c_double
+            fn.argtypes = [C.c_double]
+        for name in ("orc_Wk", "orc_dWdrk", "orc_dWdhk"):
+            fn = getattr(L, name)
+            fn.restype = C.c_double
+            fn.argtypes = [C.c_int, C.c_double, C.c_double]
         PP, SP = C.POINTER(_Params), C.POINTER(_State)
         L.orc_density.restype = C.c_int
         L.orc_density.argtypes = [PP, C.c_int64, SP]
@@ -135,6 +144,7 @@ class Params:
     h_tol: float = 1e-13
     h_max_iter: int = 50
     use_grid: bool = False
+    kernel: int = 0                 # 0 = M4 cubic spline (support 2h), 1 = M6 quintic (3h)
 
     def _c(self) -> _Params:
         p = _Params()
@@ -146,6 +156,7 @@ class Params:
         p.alpha_av, p.beta_av, p.alpha_ac = self.alpha_av, self.beta_av, self.alpha_ac
         p.c_cfl, p.h_tol, p.h_max_iter = self.c_cfl, self.h_tol, int(self.h_max_iter)
         p.use_grid = int(bool(self.use_grid))
+        p.kernel = int(self.kernel)
         return p
 
 
@@ -261,6 +272,27 @@ def kernel_dWdr(r, h):
 
 def kernel_dWdh(r, h):
     return np.vectorize(lib().orc_dWdh, otypes=[np.float64])(r, h)
+
+
+def kernel_g6(q):
+    """Quintic M6 shape g(q) (W = g / (120 pi h^3), support 3h)."""
+    return np.vectorize(lib().orc_g6, otypes=[np.float64])(q)
+
+
+def kernel_dg6(q):
+    return np.vectorize(lib().orc_dg6, otypes=[np.float64])(q)
+
+
+def kernel_Wk(k, r, h):
+    return np.vectorize(lambda rr, hh: lib().orc_Wk(int(k), rr, hh), otypes=[np.float64])(r, h)
+
+
+def kernel_dWdrk(k, r, h):
+    return np.vectorize(lambda rr, hh: lib().orc_dWdrk(int(k), rr, hh), otypes=[np.float64])(r, h)
+
+
+def kernel_dWdhk(k, r, h):
+    return np.vectorize(lambda rr, hh: lib().orc_dWdhk(int(k), rr, hh), otypes=[np.float64])(r, h)
 
 
 def num_threads() -> int:

@@ -8,9 +8,11 @@
  * header or constant with the CUDA implementation.
  *
  * What it computes, in the paper's order and notation:
- *   - M4 cubic-spline kernel, support 2h (Sec. 2, kernel functions).  The paper
- *     defers the formulas to an earlier paper; we use the standard
- *     Monaghan & Lattanzio (1985) M4 spline with 3D normalisation 1/pi.
+ *   - M4 cubic-spline kernel, support 2h, or the quintic M6 spline, support
+ *     3h (Sec. 2, the two kernel functions).  The paper defers the formulas to
+ *     an earlier paper; we use the standard Monaghan & Lattanzio (1985) M4
+ *     spline with 3D normalisation 1/pi and the standard M6 quintic spline
+ *     with 3D normalisation 1/(120 pi).
  *   - Density sum, Eq. SPHRHO, and the h-rho relation, Eq. HRHO (eta = 1.2 by
  *     default), iterated to convergence by Newton-Raphson with a bisection
  *     fallback (Sec. 2.1.1; Newton-Raphson is named in Sec. 4.1 for the same
@@ -57,6 +59,7 @@ typedef struct {
     double h_tol;            /* stop when |dh|/h < h_tol */
     int h_max_iter;
     int use_grid;            /* 0 = brute force, 1 = grid prefilter (same result) */
+    int kernel;              /* 0 = M4 cubic spline (support 2h), 1 = M6 quintic (3h) */
 } orc_params;
 
 typedef struct {
@@ -109,6 +112,48 @@ double orc_dWdh(double r, double h)
 {
     double q = r / h;
     return -(3.0 * orc_f(q) + q * orc_df(q)) / (ORC_PI * h * h * h * h);
+}
+
+/* ------------------------------------------------------------------------ */
+/* M6 quintic spline, 3D, support radius 3h: W(r,h) = g(r/h) / (120 pi h^3)  */
+/* with g(q) = (3-q)^5 - 6 (2-q)^5 + 15 (1-q)^5, each term present only      */
+/* while its bracket is positive.                                            */
+/* ------------------------------------------------------------------------ */
+static double pow5(double t) { return t * t * t * t * t; }
+static double pow4(double t) { return t * t * t * t; }
+
+double orc_g6(double q)
+{
+    if (q < 0.0) q = -q;
+    if (q >= 3.0) return 0.0;
+    double g = pow5(3.0 - q);
+    if (q < 2.0) g -= 6.0 * pow5(2.0 - q);
+    if (q < 1.0) g += 15.0 * pow5(1.0 - q);
+    return g;
+}
+
+/* dg/dq */
+double orc_dg6(double q)
+{
+    if (q >= 3.0) return 0.0;
+    double d = -5.0 * pow4(3.0 - q);
+    if (q < 2.0) d += 30.0 * pow4(2.0 - q);
+    if (q < 1.0) d -= 75.0 * pow4(1.0 - q);
+    return d;
+}
+
+/* Kernel k (0 = M4, 1 = M6): support radius in units of h, normalised shape
+   F = sigma f(q) with W = F / h^3, and dF/dq. */
+static double kernel_R(int k) { return k == 1 ? 3.0 : 2.0; }
+static double kernel_F(int k, double q) { return k == 1 ? orc_g6(q) / (120.0 * ORC_PI) : orc_f(q) / ORC_PI; }
+static double kernel_dF(int k, double q) { return k == 1 ? orc_dg6(q) / (120.0 * ORC_PI) : orc_df(q) / ORC_PI; }
+
+double orc_Wk(int k, double r, double h) { return kernel_F(k, r / h) / (h * h * h); }
+double orc_dWdrk(int k, double r, double h) { return kernel_dF(k, r / h) / (h * h * h * h); }
+double orc_dWdhk(int k, double r, double h)
+{
+    double q = r / h;
+    return -(3.0 * kernel_F(k, q) + q * kernel_dF(k, q)) / (h * h * h * h);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -255,7 +300,8 @@ static int push(idlist_t *l, int64_t j)
 /*
  * All j (including i itself) with r_ij^2 < R^2, ascending in j.
  * mode "rmax_of_j": when hj != NULL the radius for pair (i,j) is
- * 2 max(h_i, h_j) (the force list); otherwise the fixed radius R.
+ * R_K max(h_i, h_j) (the force list, R_K the kernel's support in units of
+ * h); otherwise the fixed radius R.
  */
 static int gather(const orc_params *p, const orc_state *s, int64_t n, const grid_t *g,
                   int64_t i, double R, const double *hforce, idlist_t *out)
@@ -267,7 +313,7 @@ static int gather(const orc_params *p, const orc_state *s, int64_t n, const grid
             double Rj = R;
             if (hforce) {
                 double hm = hforce[i] > hforce[j] ? hforce[i] : hforce[j];
-                Rj = 2.0 * hm;
+                Rj = kernel_R(p->kernel) * hm;
             }
             if (d.r2 < Rj * Rj)
                 if (push(out, j)) return ORC_ENOMEM;
@@ -275,7 +321,7 @@ static int gather(const orc_params *p, const orc_state *s, int64_t n, const grid
         return ORC_OK;
     }
     /* grid: the query radius must cover the largest pair radius; for force
-       lists the caller passes R = 2 max_j h_j */
+       lists the caller passes R = R_K max_j h_j */
     const double Rq = R;
     const double X[3] = {s->x[i], s->y[i], s->z[i]};
     int c0[3], c1[3], full[3];
@@ -309,7 +355,7 @@ static int gather(const orc_params *p, const orc_state *s, int64_t n, const grid
                     double Rj = R;
                     if (hforce) {
                         double hm = hforce[i] > hforce[j] ? hforce[i] : hforce[j];
-                        Rj = 2.0 * hm;
+                        Rj = kernel_R(p->kernel) * hm;
                     }
                     if (d.r2 < Rj * Rj)
                         if (push(out, j)) return ORC_ENOMEM;
@@ -328,6 +374,7 @@ static int params_ok(const orc_params *p, int64_t n)
             if (!(p->box_len[a] > 0)) return 0;
     if (p->eos == 0 && !(p->gamma > 1.0)) return 0;
     if (p->eos == 1 && !(p->cs_iso > 0)) return 0;
+    if (p->kernel != 0 && p->kernel != 1) return 0;
     return 1;
 }
 
@@ -357,15 +404,15 @@ static double median_spacing_guess(const orc_params *p, const orc_state *s, int6
 static int density_at(const orc_params *p, const orc_state *s, int64_t n, const grid_t *g,
                       int64_t i, double h, idlist_t *buf, double *rho, double *drho, int32_t *nn)
 {
-    int rc = gather(p, s, n, g, i, 2.0 * h, NULL, buf);
+    int rc = gather(p, s, n, g, i, kernel_R(p->kernel) * h, NULL, buf);
     if (rc) return rc;
     kahan_t r = {0, 0}, d = {0, 0};
     for (int64_t k = 0; k < buf->n; ++k) {
         int64_t j = buf->v[k];
         sep_t sp = separation(p, s, i, j);
         double rr = sqrt(sp.r2);
-        kadd(&r, s->m[j] * orc_W(rr, h));
-        kadd(&d, s->m[j] * orc_dWdh(rr, h));
+        kadd(&r, s->m[j] * orc_Wk(p->kernel, rr, h));
+        kadd(&d, s->m[j] * orc_dWdhk(p->kernel, rr, h));
     }
     *rho = r.s;
     *drho = d.s;
@@ -447,7 +494,7 @@ static int solve_h(const orc_params *p, const orc_state *s, int64_t n, const gri
             double Lmin = p->box_len[0];
             if (p->box_len[1] < Lmin) Lmin = p->box_len[1];
             if (p->box_len[2] < Lmin) Lmin = p->box_len[2];
-            if (hn > 0.25 * Lmin) {
+            if (hn > Lmin / (2.0 * kernel_R(p->kernel))) { /* the support exceeds half the box */
                 *h_io = h;
                 *it_o = it;
                 return ORC_EBOX;
@@ -548,7 +595,7 @@ int orc_forces(const orc_params *p, int64_t n, orc_state *s)
         idlist_t buf = {0, 0, 0};
 #pragma omp for schedule(dynamic, 64)
         for (int64_t i = 0; i < n; ++i) {
-            int rc = gather(p, s, n, gp, i, 2.0 * hmax, s->h, &buf);
+            int rc = gather(p, s, n, gp, i, kernel_R(p->kernel) * hmax, s->h, &buf);
             if (rc) {
 #pragma omp critical
                 status = rc;
@@ -564,8 +611,8 @@ int orc_forces(const orc_params *p, int64_t n, orc_state *s)
                 sep_t sp = separation(p, s, i, j);
                 double r = sqrt(sp.r2);
                 double rx = sp.dx / r, ry = sp.dy / r, rz = sp.dz / r; /* r_hat_ij */
-                double gi = orc_dWdr(r, s->h[i]);                       /* grad_i W(h_i) = gi r_hat */
-                double gj = orc_dWdr(r, s->h[j]);                       /* grad_i W(h_j) = gj r_hat */
+                double gi = orc_dWdrk(p->kernel, r, s->h[i]);           /* grad_i W(h_i) = gi r_hat */
+                double gj = orc_dWdrk(p->kernel, r, s->h[j]);           /* grad_i W(h_j) = gj r_hat */
                 double Aj = s->P[j] / (s->omega[j] * s->rho[j] * s->rho[j]);
                 double mj = s->m[j];
                 /* pressure term, Eq. GRADHMOMEQN */
@@ -693,8 +740,8 @@ int64_t orc_neighbours(const orc_params *p, int64_t n, const orc_state *s, int k
     idlist_t buf = {0, 0, 0};
     int64_t total = 0;
     for (int64_t i = 0; i < n; ++i) {
-        int rc = kind == 0 ? gather(p, s, n, gp, i, 2.0 * s->h[i], NULL, &buf)
-                           : gather(p, s, n, gp, i, 2.0 * hmax, s->h, &buf);
+        int rc = kind == 0 ? gather(p, s, n, gp, i, kernel_R(p->kernel) * s->h[i], NULL, &buf)
+                           : gather(p, s, n, gp, i, kernel_R(p->kernel) * hmax, s->h, &buf);
         if (rc) {
             free(buf.v);
             if (gp) grid_free(&g);
@@ -792,7 +839,7 @@ int orc_forces_subset(const orc_params *p, int64_t n, orc_state *s, int64_t nsub
 #pragma omp for schedule(dynamic, 16)
         for (int64_t k = 0; k < nsub; ++k) {
             int64_t i = idx[k];
-            int rc = gather(p, s, n, &g, i, 2.0 * hmax, s->h, &buf);
+            int rc = gather(p, s, n, &g, i, kernel_R(p->kernel) * hmax, s->h, &buf);
             if (rc) {
 #pragma omp critical
                 status = rc;
@@ -808,8 +855,8 @@ int orc_forces_subset(const orc_params *p, int64_t n, orc_state *s, int64_t nsub
                 sep_t sp = separation(p, s, i, j);
                 double r = sqrt(sp.r2);
                 double rx = sp.dx / r, ry = sp.dy / r, rz = sp.dz / r;
-                double gi = orc_dWdr(r, s->h[i]);
-                double gj = orc_dWdr(r, s->h[j]);
+                double gi = orc_dWdrk(p->kernel, r, s->h[i]);
+                double gj = orc_dWdrk(p->kernel, r, s->h[j]);
                 double Aj = s->P[j] / (s->omega[j] * s->rho[j] * s->rho[j]);
                 double mj = s->m[j];
                 double fp = -mj * (Ai * gi + Aj * gj);
