@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-reuse", action="store_true", help="skip the tree-reuse measurement")
+    ap.add_argument("--no-m6", action="store_true", help="skip the M6 quintic-kernel measurement")
     ap.add_argument("--lpp", type=int, default=0, help="lanes per particle (0: autotuned)")
     ap.add_argument("--workload", default="sod", choices=sorted(WORKLOADS),
                     help="sod (the default measured configuration), sedov or cloud")
@@ -74,7 +75,7 @@ def kernel_source_sha(srcs):
     return h.hexdigest()
 
 
-PAIR_SOURCES = [os.path.join(ROOT, "paper_1709_04488_gb300", "csrc", f) for f in ("sph_pairs.cu", "sph_tuned.h")]
+PAIR_SOURCES = [os.path.join(ROOT, "paper_1709_04488_gb300", "csrc", f) for f in ("sph_pairs.cuh", "sph_pairs.cu", "sph_tuned.h")]
 
 
 def traffic_for(workload, kernel):
@@ -400,6 +401,26 @@ def run_ours(args):
                  "speedup_of_rebuild_every_step": vr / (value / world)}
         pr.close()
 
+    # the same workload with the M6 quintic kernel (Sec. 2; support 3h,
+    # eta = 1.0, ~113 neighbours), started from h = 1.0 x spacing
+    m6 = None
+    if not args.no_m6:
+        a6 = dict(a, h=a["h"] / 1.2)
+        prm6 = S.make_params(S.PREC_MIXED, **p, flags=S.FLAG_ASYNC, kernel=S.KERNEL_M6, eta=1.0)
+        with torch.cuda.stream(stream):
+            p6 = S.Problem(a6, prm6, device=dev, stream=stream)
+            S.check(S.sph_density_h(p6.ctx), "sph_density_h")
+            S.check(S.sph_forces(p6.ctx), "sph_forces")
+        S.check(S.sph_run(p6.ctx, 3), "sph_run")
+        ms6, _, dp6, fp6 = time_steps(S, p6, stream, torch, 10, flush)
+        v6 = n * len(ms6) / (np.sum(ms6) * 1e-3)
+        d6 = p6.diagnostics()
+        m6 = {"value": v6, "unit": UNIT, "ms_per_step": float(np.mean(ms6)), "eta": 1.0,
+              "ngb_mean": d6.ngb_mean, "fallback": d6.fallback,
+              "leaves": d6.leaves,
+              "relative_to_m4": v6 / (value / world)}
+        p6.close()
+
     diag = prob.diagnostics()
     prob.close()
     serve_res = None
@@ -424,9 +445,10 @@ def run_ours(args):
                    "l2": "flushed (256 MiB write) between timed steps", "graph": "one CUDA graph per step",
                    "lanes_per_particle": int(prob.params.lanes_per_particle) or "auto"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": kernels_per_step * args.steps,
-        "clocks": clocks, "fp64_gpu": fp64, "tree_reuse": reuse, "serving": serve_res,
+        "clocks": clocks, "fp64_gpu": fp64, "tree_reuse": reuse, "m6_kernel": m6, "serving": serve_res,
         "step_diag": {"nr_iterations": diag.nr_iterations, "nr_max": diag.nr_max, "fallback": diag.fallback,
-                      "leaves": diag.leaves, "ngb_mean": diag.ngb_mean, "candidates": diag.candidates},
+                      "leaves": diag.leaves, "ngb_mean": diag.ngb_mean, "candidates": diag.candidates,
+                      "wrap_leaves": diag.wrap_leaves},
     }
     print(json.dumps(line), flush=True)
     if world > 1:

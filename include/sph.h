@@ -13,7 +13,8 @@
  *     conductivity, Eqs. MON97ARTVISC and MON97ENERGYDISS,
  *   - the CFL time-step, Eq. SPH_DT, and the global-step leapfrog
  *     kick-drift-kick, Eqs. LFKDK1 and LFKDK2.
- * The kernel is the M4 cubic spline with support 2h (Sec. 2).
+ * The smoothing kernel is the M4 cubic spline (support 2h) or the M6
+ * quintic spline (support 3h), the two kernels of Sec. 2.
  *
  * Conventions shared by every entry point
  *   - All functions return an int status: SPH_OK (0) or a negative SPH_E*
@@ -64,6 +65,9 @@ extern "C" {
 #define SPH_PREC_MIXED 1     /* FP32 pair arithmetic; FP64 positions, centre differences, */
                              /* integration, accumulation of a and the global reductions  */
 
+#define SPH_KERNEL_M4 0      /* M4 cubic spline, support 2h (Sec. 2)                      */
+#define SPH_KERNEL_M6 1      /* M6 quintic spline, support 3h (Sec. 2)                    */
+
 #define SPH_FLAG_ASYNC 1u    /* compute calls return without synchronising the stream     */
 #define SPH_FLAG_TIMING 2u   /* record CUDA events around the stages of every step        */
 
@@ -92,7 +96,12 @@ typedef struct {
     double h_tol;          /* stop the h iteration when |dh|/h < h_tol (0: per precision)*/
     int h_max_iter;        /* iteration cap (0: 50)                                     */
     int precision;         /* SPH_PREC_*                                               */
-    int kernel;            /* 0 = M4 cubic spline (the only value accepted)            */
+    int kernel;            /* SPH_KERNEL_M4 (cubic spline, support 2h) or SPH_KERNEL_M6
+                              (quintic spline, support 3h), Sec. 2; the M6 kernel is
+                              W = g(q) / (120 pi h^3), g = (3-q)^5 - 6 (2-q)^5 + 15 (1-q)^5
+                              with each term present while its bracket is positive.
+                              With M6, eta ~ 1.0 gives ~113 neighbours.  Any other
+                              value: SPH_EINVAL.                                    */
     int leaf_size;         /* particles per leaf, 8/16/32 (0: chosen by the autotuner) */
     int lanes_per_particle;/* 1/2/4/8 lanes of a warp per particle (0: autotuner)      */
     unsigned flags;        /* SPH_FLAG_*                                               */
@@ -140,7 +149,9 @@ typedef struct {
     int32_t unconverged;   /* particles that met SPH_ENOCONV                                */
     int32_t walk_reused;   /* 1: the last force pass took its candidate leaves from the
                               density pass's walk; 0: it walked the tree itself            */
-    int32_t pad_;
+    int32_t wrap_leaves;   /* leaves of the last density + force passes whose pair vectors
+                              needed minimum-image wraps (periodic; few particles per
+                              box length)                                                  */
 } sph_diag;
 
 typedef struct sph_ctx sph_ctx;

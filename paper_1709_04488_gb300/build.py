@@ -17,8 +17,9 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsph.so")
 
-SOURCES = ["sph_sort.cu", "sph_build.cu", "sph_pairs.cu", "sph_integrate.cu", "sph_export.cu",
-           "sph_api.cu", "sph_server.cu", "sph_noalloc.cu"]
+SOURCES = ["sph_sort.cu", "sph_build.cu", "sph_pairs.cu", "sph_pairs_m6.cu", "sph_pairs_m4_wrap.cu",
+           "sph_pairs_m6_wrap.cu", "sph_integrate.cu", "sph_export.cu", "sph_api.cu", "sph_server.cu",
+           "sph_noalloc.cu"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
@@ -36,7 +37,7 @@ def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
     deps = [src, os.path.join(CSRC, "sph_internal.cuh"), os.path.join(CSRC, "sph_tuned.h"),
-            os.path.join(ROOT, "include", "sph.h")]
+            os.path.join(CSRC, "sph_pairs.cuh"), os.path.join(ROOT, "include", "sph.h")]
     t = os.path.getmtime(obj)
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 

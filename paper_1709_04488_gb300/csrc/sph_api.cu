@@ -82,12 +82,13 @@ void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precis
         cap = cap / kBranch + nprob + 1;
     }
     b.fallback_list = c.take<int>(n);
+    b.wrap_list = c.take<int>(n);
     b.group_cap = 2 * n;
     b.group_pool = c.take<int2>(b.group_cap);
     b.leaf_gofs = c.take<int>(ml);
     b.leaf_ngroups = c.take<int>(ml);
     b.leaf_hcap = c.take<float>(ml);
-    b.counters = c.take<int>(32);
+    b.counters = c.take<int>(kNumCounters);
     b.scratch64 = c.take<long long>(8);
     // zero region (kept zero by the kernels that use it)
     b.tile_state = c.take<unsigned>(leaf_tiles(n) + 2);
@@ -117,9 +118,15 @@ int key_bits_for(int nprob)
     return kMortonTotal + bits;
 }
 
-int mask_of(int lpp) { return lpp == 1 ? 1 : lpp == 2 ? 2 : lpp == 4 ? 4 : 8; }
+int mask_of(int lpp, int kernel)
+{
+    return (lpp == 1 ? 1 : lpp == 2 ? 2 : lpp == 4 ? 4 : 8) << (kernel == SPH_KERNEL_M6 ? 4 : 0);
+}
 
-int dens_class_bit(int lpp, int uniform_m) { return mask_of(lpp) << (uniform_m ? 4 : 0); }
+int dens_class_bit(int lpp, int uniform_m, int kernel)
+{
+    return (lpp == 1 ? 1 : lpp == 2 ? 2 : lpp == 4 ? 4 : 8) << ((uniform_m ? 4 : 0) + (kernel == SPH_KERNEL_M6 ? 8 : 0));
+}
 
 // Lanes per particle by problem size: a table of (largest n, lanes) rows
 // installed with sph_set_launch_table (the package's autotuner measures one
@@ -131,7 +138,9 @@ static int g_table_rows = 0;
 static long long g_table_n[kMaxTableRows];
 static int g_table_lpp[kMaxTableRows];
 
-static int choose_lpp(long long n, int precision, int requested)
+// The table and the rule are for the M4 kernel; the M6 kernel (support 3h,
+// about twice the neighbours) takes twice the lanes, at least 2 and at most 8.
+static int choose_lpp(long long n, int precision, int requested, int kernel)
 {
     int l = requested;
     if (l == 0) {
@@ -144,6 +153,8 @@ static int choose_lpp(long long n, int precision, int requested)
             }
     }
     if (l != 1 && l != 2 && l != 4 && l != 8) l = 4;
+    if (kernel == SPH_KERNEL_M6 && requested == 0) l = l >= 4 ? 8 : 2 * l;
+    if (kernel == SPH_KERNEL_M6 && l < 2) l = 2;
     if (precision == SPH_PREC_FP64) l = (l >= 4) ? 4 : 2;
     return l;
 }
@@ -183,7 +194,8 @@ namespace sph {
 int validate(const sph_params *p)
 {
     if (!p) return fail(SPH_EINVAL, "params is NULL");
-    if (p->kernel != 0) return fail(SPH_EINVAL, "kernel %d not supported (0 = M4 cubic spline)", p->kernel);
+    if (p->kernel != SPH_KERNEL_M4 && p->kernel != SPH_KERNEL_M6)
+        return fail(SPH_EINVAL, "kernel %d not supported (0 = M4 cubic spline, 1 = M6 quintic spline)", p->kernel);
     if (p->periodic != 0 && p->periodic != 1) return fail(SPH_EINVAL, "periodic must be 0 or 1");
     if (p->periodic)
         for (int a = 0; a < 3; ++a)
@@ -217,6 +229,8 @@ PhysParams phys_of(const sph_params *p)
         ph.box_lo[a] = p->box_lo[a];
         ph.box_len[a] = p->periodic ? p->box_len[a] : 0.0;
         ph.box_len_f[a] = (float)ph.box_len[a];
+        ph.box_inv[a] = p->periodic ? 1.0 / ph.box_len[a] : 0.0;
+        ph.box_inv_f[a] = p->periodic ? 1.0f / ph.box_len_f[a] : 0.f;
     }
     ph.gamma = p->gamma;
     ph.cs_iso = p->cs_iso;
@@ -227,6 +241,9 @@ PhysParams phys_of(const sph_params *p)
     ph.c_cfl = p->c_cfl;
     ph.h_tol = p->h_tol > 0 ? p->h_tol : (p->precision == SPH_PREC_FP64 ? 1e-13 : 1e-6);
     ph.h_max_iter = p->h_max_iter > 0 ? p->h_max_iter : 50;
+    ph.kernel = p->kernel;
+    ph.kr = p->kernel == SPH_KERNEL_M6 ? 3.0 : 2.0;
+    ph.kr_f = (float)ph.kr;
     return ph;
 }
 
@@ -234,13 +251,13 @@ int lpp_of(const sph_params *p, long long n)
 {
     int req = p->lanes_per_particle;
     if (req == 0 && p->leaf_size != 0) req = 32 / p->leaf_size;
-    return choose_lpp(n, p->precision, req);
+    return choose_lpp(n, p->precision, req, p->kernel);
 }
 
 int status_to_code(unsigned st)
 {
     if (st & ST_NONFINITE) return fail(SPH_ENONFINITE, "non-finite value in the results");
-    if (st & ST_BOX) return fail(SPH_EBOX, "smoothing length reached a quarter of the periodic box");
+    if (st & ST_BOX) return fail(SPH_EBOX, "kernel support (R_K h) reached half the periodic box");
     if (st & ST_TIMEOUT) return fail(SPH_ETIMEOUT, "a bounded device wait gave up");
     if (st & ST_OVERFLOW) return fail(SPH_ENOSPACE, "an internal capacity was exceeded");
     if (st & ST_NOCONV) return fail(SPH_ENOCONV, "h-rho iteration did not converge for some particles");
@@ -358,8 +375,9 @@ int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *st
     c->bv.ntot = n;
     c->bv.key_bits = key_bits_for(1);
     c->bv.key_lo = key_low_bits(n);
-    c->bv.lpp_mask = mask_of(c->lpp);
+    c->bv.lpp_mask = mask_of(c->lpp, p->kernel);
     c->bv.any_isolated = p->periodic ? 0 : 1;
+    c->bv.any_periodic = p->periodic ? 1 : 0;
     ProbStatic &ps = c->host_ps;
     memset(&ps, 0, sizeof ps);
     ps.x = state->x;
@@ -402,7 +420,7 @@ int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *st
         ps.m_uniform = mh[0];
         ps.inv_m_uniform = uni && mh[0] != 0.0 ? 1.0 / mh[0] : 0.0;
     }
-    c->bv.dens_mask = dens_class_bit(c->lpp, ps.uniform_m);
+    c->bv.dens_mask = dens_class_bit(c->lpp, ps.uniform_m, p->kernel);
     ProbDiag d0;
     memset(&d0, 0, sizeof d0);
     d0.dt_next = 0.0;
@@ -411,7 +429,7 @@ int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *st
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->diag, &d0, sizeof d0, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(c->bv.prob_base, bases, sizeof bases, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->bv.dyn, 0, sizeof(ProbDyn), c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->bv.counters, 0, 32 * sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->bv.counters, 0, kNumCounters * sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->bv.zero_lo, 0, c->bv.zero_bytes, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
@@ -694,6 +712,7 @@ int sph_diagnostics(sph_ctx *c, sph_diag *out)
     out->status = status_to_code(d.status);
     out->unconverged = d.unconverged;
     out->walk_reused = d.walk_reused;
+    out->wrap_leaves = d.wrap_leaves;
     return SPH_OK;
 }
 
@@ -777,15 +796,16 @@ int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, 
     long long ntot = 0;
     std::vector<ProbStatic> tab(nctx);
     std::vector<long long> bases(nctx + 1);
-    int mask = 0, dmask = 0, b_any_isolated = 0;
+    int mask = 0, dmask = 0, b_any_isolated = 0, b_any_periodic = 0;
     for (int k = 0; k < nctx; ++k) {
         tab[k] = ctxs[k]->host_ps;
         tab[k].base = ntot;
         bases[k] = ntot;
         ntot += ctxs[k]->n;
-        mask |= mask_of(tab[k].lpp);
-        dmask |= dens_class_bit(tab[k].lpp, tab[k].uniform_m);
+        mask |= mask_of(tab[k].lpp, tab[k].ph.kernel);
+        dmask |= dens_class_bit(tab[k].lpp, tab[k].uniform_m, tab[k].ph.kernel);
         if (!tab[k].ph.periodic) b_any_isolated = 1;
+        else b_any_periodic = 1;
     }
     bases[nctx] = ntot;
     Carver cv{(char *)workspace};
@@ -799,10 +819,11 @@ int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, 
     b.lpp_mask = mask;
     b.dens_mask = dmask;
     b.any_isolated = b_any_isolated;
+    b.any_periodic = b_any_periodic;
     CU(cudaMemcpyAsync(b.prob, tab.data(), sizeof(ProbStatic) * nctx, cudaMemcpyHostToDevice, st));
     CU(cudaMemcpyAsync(b.prob_base, bases.data(), sizeof(long long) * (nctx + 1), cudaMemcpyHostToDevice, st));
     CU(cudaMemsetAsync(b.dyn, 0, sizeof(ProbDyn) * nctx, st));
-    CU(cudaMemsetAsync(b.counters, 0, 32 * sizeof(int), st));
+    CU(cudaMemsetAsync(b.counters, 0, kNumCounters * sizeof(int), st));
     CU(cudaMemsetAsync(b.zero_lo, 0, b.zero_bytes, st));
     for (int s = 0; s < nsteps; ++s) {
         rc = enqueue_step(b, prec, -1.0, st, Marks());

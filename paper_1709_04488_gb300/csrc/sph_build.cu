@@ -351,6 +351,23 @@ __device__ __forceinline__ float axis_of(const float *v, int lane)
 __device__ __forceinline__ float offset_f(float v) { return v; }
 __device__ __forceinline__ float offset_f(double v) { return (float)v; }
 
+// Per-axis extents of a leaf's offsets from its reference point (e: this
+// lane's |offset| per axis), packed for the minimum-image test of the pair
+// kernels: 10 bits per axis in units of L_a / 2046, rounded up (1023: half
+// the box or more), as the bits of a float; 0 for isolated problems.
+__device__ __forceinline__ float leaf_ext_bits(const float (&e)[3], const PhysParams &ph)
+{
+    unsigned bits = 0u;
+    for (int a = 0; a < 3; ++a) {
+        const float m = warp_max(e[a]);
+        if (ph.periodic) {
+            const unsigned q = (unsigned)ceilf(m * (2.f * ph.box_inv_f[a]) * 1023.f * 1.00001f) + 1u;
+            bits |= (q < 1023u ? q : 1023u) << (10 * a);
+        }
+    }
+    return __uint_as_float(bits);
+}
+
 // Leaf reference point, position box and the offsets of its particles from
 // that point.  The reference point is the leaf's first particle (FP64); the
 // FP64 difference is taken before the cast to the staging precision.  The
@@ -369,28 +386,37 @@ __global__ void k_leaf_props(BatchView b)
         const int st = b.leaf_start[leaf], cnt = b.leaf_start[leaf + 1] - st;
         const ProbStatic &ps = b.prob[b.leaf_pid[leaf]];
         const bool on = lane < cnt;
-        const double c[3] = {b.sx[st], b.sy[st], b.sz[st]};
-        float lo[3], hi[3], slo_[3], shi_[3], hp = 0.f;
+        // reference point: the centre of the leaf's box (its first particle
+        // shifted by the float midpoint of the offsets from it), so that the
+        // offsets stay within half the leaf's width
+        double c[3] = {b.sx[st], b.sy[st], b.sz[st]};
+        double d[3] = {0.0, 0.0, 0.0};
+        if (on) {
+            const double x[3] = {b.sx[st + lane], b.sy[st + lane], b.sz[st + lane]};
+            for (int a = 0; a < 3; ++a)
+                d[a] = WRAP ? min_image(x[a] - c[a], ps.ph.box_len[a], ps.ph.periodic)  // (kept leaf: may
+                            : x[a] - c[a];                                               // have wrapped)
+        }
+        for (int a = 0; a < 3; ++a) {
+            const float mid = 0.5f * (warp_max(on ? (float)d[a] : -INFINITY) + warp_min(on ? (float)d[a] : INFINITY));
+            c[a] += (double)mid;
+            d[a] -= (double)mid;
+        }
+        float lo[3], hi[3], slo_[3], shi_[3], hp = 0.f, ex[3] = {0.f, 0.f, 0.f};
         if (on) {
             T4 v;
-            if (WRAP) {  // a kept leaf's particles may have crossed a periodic boundary
-                const PhysParams &ph = ps.ph;
-                v.x = (decltype(v.x))min_image(b.sx[st + lane] - c[0], ph.box_len[0], ph.periodic);
-                v.y = (decltype(v.y))min_image(b.sy[st + lane] - c[1], ph.box_len[1], ph.periodic);
-                v.z = (decltype(v.z))min_image(b.sz[st + lane] - c[2], ph.box_len[2], ph.periodic);
-            } else {
-                v.x = (decltype(v.x))(b.sx[st + lane] - c[0]);
-                v.y = (decltype(v.y))(b.sy[st + lane] - c[1]);
-                v.z = (decltype(v.z))(b.sz[st + lane] - c[2]);
-            }
+            v.x = (decltype(v.x))d[0];
+            v.y = (decltype(v.y))d[1];
+            v.z = (decltype(v.z))d[2];
             v.w = ps.uniform_m ? (decltype(v.w))ps.m_uniform : (decltype(v.w))b.sm[st + lane];
             ((T4 *)b.pm)[st + lane] = v;
             const float o[3] = {offset_f(v.x), offset_f(v.y), offset_f(v.z)};
+            for (int a = 0; a < 3; ++a) ex[a] = fabsf(o[a]);
             // predicted smoothing spheres: 1.1 x the guessed h (the h the
             // density solve starts from); the force pass reuses the density
             // walk's candidates when no final h exceeds its prediction
             hp = __fmul_ru(kHPredict, __double2float_ru(b.sh[st + lane]));
-            const float h2 = __fmul_ru(2.0f, hp);
+            const float h2 = __fmul_ru(ps.ph.kr_f, hp);  // support radius R_K h
             for (int a = 0; a < 3; ++a) {
                 lo[a] = widen_dn(o[a], fabsf(o[a]));
                 hi[a] = widen_up(o[a], fabsf(o[a]));
@@ -411,6 +437,7 @@ __global__ void k_leaf_props(BatchView b)
             shi_[a] = warp_max(shi_[a]);
         }
         hp = warp_max(hp);
+        const float ext = leaf_ext_bits(ex, ps.ph);
         float bl = 0.f, bh = 0.f, sl = 0.f, sh = 0.f;
         if (lane < 3) {
             const double ca = lane == 0 ? c[0] : lane == 1 ? c[1] : c[2];
@@ -435,7 +462,7 @@ __global__ void k_leaf_props(BatchView b)
             NodeBox nb;
             nb.plo = make_float4(l0, l1, l2, hp);  // h_max predicted until the refit
             nb.phi = make_float4(h0, h1, h2, (float)cnt);
-            nb.slo = make_float4(s0, s1, s2, 0.f);
+            nb.slo = make_float4(s0, s1, s2, ext);
             nb.shi = make_float4(t0, t1, t2, 0.f);
             b.nodes[0][leaf] = nb;
         }
@@ -456,12 +483,15 @@ __global__ void k_leaf_refit(BatchView b)
     for (int leaf = w; leaf < nleaf; leaf += nw) {
         const int st = b.leaf_start[leaf], cnt = b.leaf_start[leaf + 1] - st;
         const bool on = lane < cnt;
-        float slo[3], shi[3], hm = 0.f;
+        const PhysParams &ph = b.prob[b.leaf_pid[leaf]].ph;
+        const float kr = ph.kr_f;
+        float slo[3], shi[3], hm = 0.f, ex[3] = {0.f, 0.f, 0.f};
         if (on) {
             const T4 v = ((const T4 *)b.pm)[st + lane];
             const float o[3] = {offset_f(v.x), offset_f(v.y), offset_f(v.z)};
-            const float h = b.hf[st + lane], h2 = __fmul_ru(2.0f, h);
+            const float h = b.hf[st + lane], h2 = __fmul_ru(kr, h);
             hm = h;
+            for (int a = 0; a < 3; ++a) ex[a] = fabsf(o[a]);
             for (int a = 0; a < 3; ++a) {
                 const float mag = __fadd_ru(fabsf(o[a]), h2);
                 slo[a] = widen_dn(__fsub_rd(o[a], h2), mag);
@@ -474,6 +504,7 @@ __global__ void k_leaf_refit(BatchView b)
             }
         }
         hm = warp_max(hm);
+        const float ext = leaf_ext_bits(ex, ph);
         for (int a = 0; a < 3; ++a) {
             slo[a] = warp_min(slo[a]);
             shi[a] = warp_max(shi[a]);
@@ -490,7 +521,7 @@ __global__ void k_leaf_refit(BatchView b)
         if (lane == 0) {
             NodeBox &nb = b.nodes[0][leaf];
             nb.plo.w = hm;
-            nb.slo = make_float4(l0, l1, l2, 0.f);
+            nb.slo = make_float4(l0, l1, l2, ext);
             nb.shi = make_float4(h0, h1, h2, 0.f);
         }
         tree_up(b, leaf);

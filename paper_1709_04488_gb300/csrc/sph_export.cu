@@ -2,7 +2,8 @@
 // per-leaf tree walk retrieves the candidates (Sec. 4.2), membership is
 // decided on absolute FP64 positions with the periodic minimum image and
 // r^2 = dx*dx + dy*dy + dz*dz formed without fused multiply-add, compared
-// with (2h)*(2h) (gather list) or (2 max(h_i,h_j))^2 (force list).  Used by
+// with (R_K h)^2 (gather list) or (R_K max(h_i,h_j))^2 (force list), R_K the
+// kernel's support in units of h (2 for M4, 3 for M6).  Used by
 // the tests to compare neighbour sets bit for bit with the CPU oracle.
 #include "sph_internal.cuh"
 
@@ -64,7 +65,7 @@ __global__ void __launch_bounds__(128) k_export(BatchView b, int kind, int pass,
         const long long i = (long long)b.perm[s] - ps.base;
         float4 qlo = make_float4(__double2float_rd(xi), __double2float_rd(yi), __double2float_rd(zi), 0.f);
         float4 qhi = make_float4(__double2float_ru(xi), __double2float_ru(yi), __double2float_ru(zi), 0.f);
-        const float R = __double2float_ru(2.0 * hi) * 1.0001f;
+        const float R = __double2float_ru(ph.kr * hi) * 1.0001f;
         int n = 0;
         // walk (same structure as the pair kernels)
         const int top = d.top_level;
@@ -99,7 +100,8 @@ __global__ void __launch_bounds__(128) k_export(BatchView b, int kind, int pass,
                     double dz = min_image(__dsub_rn(zi, b.sz[j]), ph.box_len[2], ph.periodic);
                     double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
                     double hh = kind == 1 ? fmax(hi, b.sh[j]) : hi;
-                    double R2 = __dmul_rn(2.0 * hh, 2.0 * hh);
+                    const double Rk = __dmul_rn(ph.kr, hh);  // R_K h, rounded as the oracle's
+                    double R2 = __dmul_rn(Rk, Rk);
                     hit = r2 < R2 && !(kind == 1 && j == s);
                     jid = (int)((long long)b.perm[j] - ps.base);
                 }

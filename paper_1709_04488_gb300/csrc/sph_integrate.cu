@@ -22,6 +22,7 @@ __device__ void reset_diag(const BatchView &b, int p, int mode)
     d->dt_min_bits = 0x7ff0000000000000ull;  // +inf
     d->force_pairs = 0;
     if (mode == 2) return;
+    d->wrap_leaves = 0;
     d->mass = 0;
     for (int a = 0; a < 3; ++a) {
         d->mom[a] = 0;
@@ -38,15 +39,16 @@ __device__ void reset_diag(const BatchView &b, int p, int mode)
     d->unconverged = 0;
 }
 
-// Clear the per-call counters (block 0, first 32 threads): mode 1 all of a
-// step's, mode 2 those of a forces-only call.
+// Clear the per-call counters (block 0, first kNumCounters threads): mode 1
+// all of a step's, mode 2 those of a forces-only call.
 __device__ __forceinline__ void reset_counters(const BatchView &b, int mode)
 {
     const int k = threadIdx.x;
-    if (blockIdx.x != 0 || k >= 32) return;
-    const bool all = k == kSlowCounter || k == kPoolCounter || k == kTimeoutCounter ||
-                     (k >= kDensityCounter && k < kForceCounter + 4);
-    const bool forces = k == kTimeoutCounter || (k >= kForceCounter && k < kForceCounter + 4);
+    if (blockIdx.x != 0 || k >= kNumCounters) return;
+    const bool all = (k >= kSlowCounter && k <= kForceWrapList) || k >= kTimeoutCounter;
+    const bool forces = k == kForceWrapList || k == kTimeoutCounter ||
+                        (k >= kForceCounter && k < kForceCounter + kForceClasses) ||
+                        (k >= kForceWrapCounter && k < kForceWrapCounter + kForceClasses);
     if (mode == 1 ? all : forces) b.counters[k] = 0;
 }
 

@@ -16,11 +16,20 @@ constexpr int kMortonBits = 10;     // bits per axis of the Morton key
 constexpr int kMortonTotal = 3 * kMortonBits;
 constexpr double kPi = 3.14159265358979323846;
 // slots of BatchView::counters: 0 leaves, 1..7 nodes per level, 8 slow-path
-// count, 9 groups used in the candidate-group pool, 15 look-back timeout,
-// 16..23 density leaf tickets (per class), 24..27 force leaf tickets (per
-// lanes per particle); the step's first kernel clears 8, 9, 15 and 16..27,
-// a forces-only call clears 15 and 24..27
-constexpr int kSlowCounter = 8, kPoolCounter = 9, kTimeoutCounter = 15, kDensityCounter = 16, kForceCounter = 24;
+// count, 9 groups used in the candidate-group pool, 10 (11) leaves on the
+// density (force) wrap list, 15 look-back timeout, 16..31 density leaf
+// tickets (per class: lanes, equal masses, kernel), 32..39 force leaf
+// tickets (per lanes per particle and kernel), 40..55 and 56..63 the same
+// for the launches that serve the wrap lists; the step's first kernel clears
+// 8..11 and 15..63, a forces-only call 11, 15, 32..39 and 56..63
+constexpr int kNumCounters = 64;
+constexpr int kSlowCounter = 8, kPoolCounter = 9, kDensWrapList = 10, kForceWrapList = 11, kTimeoutCounter = 15;
+constexpr int kDensityCounter = 16, kForceCounter = 32, kDensityWrapCounter = 40, kForceWrapCounter = 56;
+constexpr int kDensityClasses = 16, kForceClasses = 8;
+static_assert(kDensityCounter + kDensityClasses <= kForceCounter && kForceCounter + kForceClasses <= kDensityWrapCounter &&
+                  kDensityWrapCounter + kDensityClasses <= kForceWrapCounter &&
+                  kForceWrapCounter + kForceClasses <= kNumCounters,
+              "counter slots");
 constexpr int kMaxLeafGroups = 32;  // candidate-leaf groups recorded per leaf (one per lane)
 #ifndef SPH_HPREDICT
 #define SPH_HPREDICT 1.1f
@@ -47,9 +56,13 @@ struct PhysParams {
     double alpha_av, beta_av, alpha_ac, c_cfl;
     double h_tol;
     int h_max_iter;
-    int pad_;
+    int kernel;          // SPH_KERNEL_M4 or SPH_KERNEL_M6
     float box_len_f[3];  // box_len as float (node tests run in FP32)
-    float pad2_;
+    float kr_f;          // support radius in units of h: 2 (M4) or 3 (M6)
+    double kr;
+    double box_inv[3];   // 1 / box_len (periodic), for minimum-image wraps
+    float box_inv_f[3];
+    float pad_;
 };
 
 // Per-problem diagnostics and persistent scalars; lives in the context's own
@@ -70,6 +83,8 @@ struct ProbDiag {
     int walk_reused;     // the last force pass reused the density walk's candidates
     int reuse_hold;      // steps left before the density walk records candidates again
     int reuse_backoff;   // length of the next hold (doubles while the records keep failing)
+    int wrap_leaves;     // leaves of the last passes put on the wrap list
+    int pad_;
 };
 
 // Host-written description of one problem inside a batch.
@@ -116,25 +131,26 @@ struct Vec4<double> {
     using type = dbl4;
 };
 
-// Box of a leaf or tree node: positions and smoothing spheres (pos +- 2h),
-// rounded outwards to float.
+// Box of a leaf or tree node: positions and smoothing spheres (pos +- R_K h,
+// R_K the kernel's support in units of h), rounded outwards to float.
 struct __align__(16) NodeBox {
     float4 plo;  // xyz = min position, w = h_max
     float4 phi;  // xyz = max position, w = particle count (as float)
-    float4 slo;  // xyz = min (x - 2h)
-    float4 shi;  // xyz = max (x + 2h)
+    float4 slo;  // xyz = min (x - R_K h); w (leaves, periodic) = packed offset extents (leaf_ext_bits)
+    float4 shi;  // xyz = max (x + R_K h)
 };
 
 // Batch-global scratch arrays (all carved from one workspace).
 struct BatchView {
     int nprob;
-    int lpp_mask;                // bit k set: some problem uses 2^k lanes per particle
-    int dens_mask;               // bit (k + 4 u): density class (2^k lanes, uniform masses u)
+    int lpp_mask;                // bit (k + 4 K): some problem uses 2^k lanes per particle and kernel K
+    int dens_mask;               // bit (k + 4 u + 8 K): density class (2^k lanes, uniform masses u, kernel K)
     long long ntot;              // particles over all problems
     int max_leaves;              // capacity of the leaf arrays
     int key_bits;                // bits the radix sort must order
     int key_lo;                  // lowest key bit that is sorted (the bits below are cleared)
     int any_isolated;            // some problem is isolated (needs a bounding box)
+    int any_periodic;            // some problem is periodic (wrap-list launches)
     ProbStatic *prob;            // [nprob]
     ProbDyn *dyn;                // [nprob]
     long long *prob_base;        // [nprob + 1] base offsets (for searches)
@@ -168,6 +184,7 @@ struct BatchView {
     char *zero_lo;               // [zero_lo, zero_lo + zero_bytes) holds the two above
     size_t zero_bytes;
     int *fallback_list;          // [ntot] sorted indices needing the slow path
+    int *wrap_list;              // [ntot] leaves served by the minimum-image (wrap) launches
     // candidate-leaf groups (first leaf, ballot of the 32 siblings) the
     // density walk visited per leaf, for the force pass to reuse
     int2 *group_pool;            // [group_cap]
@@ -175,7 +192,7 @@ struct BatchView {
     int *leaf_gofs;              // [max_leaves] first pool entry of the leaf's groups
     int *leaf_ngroups;           // [max_leaves] group count, -1: not recorded (walk)
     float *leaf_hcap;            // [max_leaves] largest h the recorded groups cover
-    int *counters;               // [32], slots as listed at kSlowCounter
+    int *counters;               // [kNumCounters], slots as listed at kSlowCounter
     long long *scratch64;        // [8]
 };
 
@@ -288,8 +305,8 @@ void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precis
 void carve_tables(Carver &c, BatchView &b, int nprob);
 int key_bits_for(int nprob);
 int key_low_bits(long long ntot);  // Morton bits left unsorted (cleared) for ntot particles
-int mask_of(int lpp);
-int dens_class_bit(int lpp, int uniform_m);
+int mask_of(int lpp, int kernel);
+int dens_class_bit(int lpp, int uniform_m, int kernel);
 int validate(const sph_params *p);
 PhysParams phys_of(const sph_params *p);
 int lpp_of(const sph_params *p, long long n);

@@ -59,7 +59,7 @@ __global__ void k_noalloc_init(BatchView b, ProbStatic ps)
         memset(b.dyn, 0, sizeof(ProbDyn));
         memset(ps.diag, 0, sizeof(ProbDiag));
     }
-    if (blockIdx.x == 0) b.counters[threadIdx.x] = 0;  // 32 counters
+    if (blockIdx.x == 0) b.counters[threadIdx.x] = 0;  // kNumCounters threads
 }
 
 }  // namespace
@@ -94,9 +94,10 @@ extern "C" int sph_density_forces_noalloc(const sph_params *p, int64_t n, const 
     b.ntot = n;
     b.key_bits = key_bits_for(1);
     b.key_lo = key_low_bits(n);
-    b.lpp_mask = mask_of(lpp);
-    b.dens_mask = dens_class_bit(lpp, 0);  // masses are not inspected here: distance-and-mass lists
+    b.lpp_mask = mask_of(lpp, p->kernel);
+    b.dens_mask = dens_class_bit(lpp, 0, p->kernel);  // masses are not inspected here: distance-and-mass lists
     b.any_isolated = p->periodic ? 0 : 1;
+    b.any_periodic = p->periodic ? 1 : 0;
     ProbStatic ps;
     memset(&ps, 0, sizeof ps);
     ps.x = state->x;
@@ -130,7 +131,7 @@ extern "C" int sph_density_forces_noalloc(const sph_params *p, int64_t n, const 
         e = (x);                                                                                   \
         if (e != cudaSuccess) return fail(SPH_ECUDA, "%s: %s", #x, cudaGetErrorString(e));         \
     } while (0)
-    k_noalloc_init<<<1, 32, 0, st>>>(b, ps);
+    k_noalloc_init<<<1, kNumCounters, 0, st>>>(b, ps);
     NA_TRY(cudaGetLastError());
     NA_TRY(cudaMemsetAsync(b.zero_lo, 0, b.zero_bytes, st));
     NA_TRY(launch_reset_step(b, 1, st));

@@ -17,6 +17,7 @@ OK, EINVAL, EBOX, ENOCONV, ENONFINITE, ETIMEOUT, ETOOBIG, EBUSY, EAGAIN, ECUDA, 
     0, -1, -2, -3, -4, -5, -6, -7, -8, -9, -10)
 EOS_ADIABATIC, EOS_ISOTHERMAL = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
+KERNEL_M4, KERNEL_M6 = 0, 1
 FLAG_ASYNC, FLAG_TIMING = 1, 2
 NSTAGES = 7
 STAGES = ["kick_drift", "sort", "tree", "density", "refit", "forces", "close"]
@@ -79,7 +80,7 @@ class Diag(C.Structure):
         ("status", C.c_int32),
         ("unconverged", C.c_int32),
         ("walk_reused", C.c_int32),
-        ("pad_", C.c_int32),
+        ("wrap_leaves", C.c_int32),
     ]
 
     def as_dict(self):

@@ -54,6 +54,15 @@ def test_struct_layouts_match_header(S, tmp_path):
 def test_defaults_are_the_papers(S):
     p = S.sph_params_default()
     assert p.eta == 1.2 and p.alpha_av == 1.0 and p.beta_av == 2.0 and p.c_cfl == 0.2
+    assert p.kernel == S.KERNEL_M4
+
+
+def test_constants_match_header(S):
+    txt = open(os.path.join(ROOT, "include", "sph.h")).read()
+    defs = dict(re.findall(r"#define (SPH_[A-Z0-9_]+)\s+(-?\d+)u?\b", txt))
+    for name in ("KERNEL_M4", "KERNEL_M6", "EOS_ADIABATIC", "EOS_ISOTHERMAL", "PREC_FP64", "PREC_MIXED",
+                 "FLAG_ASYNC", "FLAG_TIMING"):
+        assert int(defs["SPH_" + name]) == getattr(S, name), name
 
 
 def test_workspace_bytes_and_validation(S):
@@ -66,8 +75,11 @@ def test_workspace_bytes_and_validation(S):
     bad = S.sph_params_default()
     bad.eta = -1.0
     assert S.sph_workspace_bytes(10, bad) == 0
+    m6 = S.sph_params_default()
+    m6.kernel = S.KERNEL_M6
+    assert S.sph_workspace_bytes(1000, m6) > 0
     bad = S.sph_params_default()
-    bad.kernel = 1
+    bad.kernel = 2
     assert S.sph_workspace_bytes(10, bad) == 0
     bad = S.sph_params_default()
     bad.lanes_per_particle = 3
