@@ -45,7 +45,9 @@ LATTICE_SIDES = (12, 20, 33, 50, 80, 126)  # 1728 ... 2.0e6 particles (33: the S
 # candidate values of the compile-time shapes, in the order they are tuned
 BUILD_SPACE = {
     "SPH_FORCE_MINB": (4, 5, 6),
+    "SPH_FORCE_MINB1": (4, 5, 6),
     "SPH_DENS_MINB": (3, 4, 5),
+    "SPH_DENS_MINB1": (3, 4, 5),
     "SPH_FORCE_SB1": (4, 8, 16),
     "SPH_FORCE_LC1": (80, 96, 112),
     "SPH_DENS_LCAP1": (88, 96),

@@ -572,6 +572,7 @@ struct DCfg {
                                                    : LPP == 1 ? SPH_DENS_LCAP1 : LPP == 2 ? 64 : LPP == 4 ? 40 : 24;
     static constexpr int CH = SPH_DENS_CH;
     static constexpr int WPB = 4;
+    static constexpr int MINB = LPP == 1 ? SPH_DENS_MINB1 : SPH_DENS_MINB;  // blocks per SM the registers allow
     static constexpr int LW = UM ? 1 : 2;  // list words per entry: r (and m_j unless masses are equal)
     static constexpr size_t scratch = (sizeof(StageScratch<T>) + 31) & ~(size_t)31;
     static constexpr size_t per_warp = CH * sizeof(V) + (size_t)LCAP * 32 * LW * sizeof(T) + scratch;
@@ -958,7 +959,7 @@ __device__ __forceinline__ bool density_leaf(const BatchView &b, int leaf, unsig
 // WRAP: the launch that serves the wrap list (leaves whose pair vectors may
 // miss the minimum image); the other launch puts them there.
 template <typename T, int LPP, bool UM, int K, bool WRAP>
-__global__ void __launch_bounds__(DCfg<T, LPP, UM, K>::WPB * 32, SPH_DENS_MINB) k_density(BatchView b, int use_pred)
+__global__ void __launch_bounds__(DCfg<T, LPP, UM, K>::WPB * 32, DCfg<T, LPP, UM, K>::MINB) k_density(BatchView b, int use_pred)
 {
     using C = DCfg<T, LPP, UM, K>;
     extern __shared__ __align__(32) unsigned char smem[];
@@ -1183,6 +1184,7 @@ struct FCfg {
     static constexpr int SB = LPP == 1 ? SPH_FORCE_SB1 : SPH_FORCE_SB;
     static constexpr int TAB = SPH_FORCE_TAB;  // candidate leaves per table fill (<= 2048)
     static constexpr int WPB = 4;
+    static constexpr int MINB = LPP == 1 ? SPH_FORCE_MINB1 : SPH_FORCE_MINB;  // blocks per SM the registers allow
     static_assert(TAB <= 2048 && LC >= 2 * SB / LPP, "force list layout");
     static constexpr size_t scratch = (sizeof(StageScratch<T>) + 31) & ~(size_t)31;
     static constexpr size_t codes = ((size_t)(CH + LC * 32) * 2 + 31) & ~(size_t)31;
@@ -1456,7 +1458,7 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
 // WRAP: the launch that serves the wrap list (leaves whose pair vectors may
 // miss the minimum image); the other launch puts them there.
 template <typename T, int LPP, int K, bool WRAP>
-__global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, SPH_FORCE_MINB) k_forces(BatchView b)
+__global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, FCfg<T, LPP>::MINB) k_forces(BatchView b)
 {
     using C = FCfg<T, LPP>;
     extern __shared__ __align__(32) unsigned char smem[];
@@ -1464,6 +1466,8 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, SPH_FORCE_MINB) k_forc
     unsigned char *mine = smem + wib * C::per_warp;
     const int nleaf = WRAP ? b.counters[kForceWrapList] : b.counters[0];
     const int cls = lpp_log2(LPP) + 4 * K;
+    int last_p = -1;
+    float Rall = 0.f;  // periodic: pairs reach R_K x the problem's largest h
     for (;;) {
         int leaf = 0;
         if (lane == 0) leaf = atomicAdd(&b.counters[(WRAP ? kForceWrapCounter : kForceCounter) + cls], 1);
@@ -1473,11 +1477,11 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, SPH_FORCE_MINB) k_forc
         const int p = b.leaf_pid[leaf];
         const ProbStatic &ps = b.prob[p];
         if (ps.lpp != LPP || ps.ph.kernel != K) continue;  // leaf of a problem served by another launch
-        float Rall = 0.f;  // periodic: pairs reach R_K x the problem's largest h
-        if (ps.ph.periodic) {
+        if (ps.ph.periodic && p != last_p) {  // (consecutive leaves mostly share a problem)
             float extmax;
             problem_top_max(b, b.dyn[p], Rall, extmax);
             Rall = __fmul_ru((float)Kern<K>::R, Rall) * 1.0001f;
+            last_p = p;
         }
         if (!force_leaf<T, LPP, K, WRAP>(b, leaf, mine, Rall) && lane == 0) {
             b.wrap_list[atomicAdd(&b.counters[kForceWrapList], 1)] = leaf;
@@ -1502,7 +1506,8 @@ cudaError_t run_density(const BatchView &b, int use_pred, cudaStream_t st)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_density<T, LPP, UM, K, WRAP>, C::WPB * 32, C::smem);
         if (per_sm < 1) per_sm = 1;
     }
-    k_density<T, LPP, UM, K, WRAP><<<dev_info().sm_count * per_sm, C::WPB * 32, C::smem, st>>>(b, use_pred);
+    // the wrap-list launch serves few leaves (mostly none): one block per SM
+    k_density<T, LPP, UM, K, WRAP><<<dev_info().sm_count * (WRAP ? 1 : per_sm), C::WPB * 32, C::smem, st>>>(b, use_pred);
     return cudaGetLastError();
 }
 
@@ -1530,7 +1535,7 @@ cudaError_t run_forces(const BatchView &b, cudaStream_t st)
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forces<T, LPP, K, WRAP>, C::WPB * 32, C::smem);
     if (per_sm < 1) per_sm = 1;
-    int grid = dev_info().sm_count * per_sm;
+    int grid = dev_info().sm_count * (WRAP ? 1 : per_sm);  // (the wrap list is short)
     k_forces<T, LPP, K, WRAP><<<grid, C::WPB * 32, C::smem, st>>>(b);
     return cudaGetLastError();
 }

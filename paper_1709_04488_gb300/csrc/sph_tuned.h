@@ -6,12 +6,16 @@
 #pragma once
 
 // density: staged candidates per chunk, blocks per SM the registers are
-// sized for, list entries per lane at one lane per particle
+// sized for (at several lanes per particle, and at one), list entries per
+// lane at one lane per particle
 #ifndef SPH_DENS_CH
 #define SPH_DENS_CH 64
 #endif
 #ifndef SPH_DENS_MINB
-#define SPH_DENS_MINB 5
+#define SPH_DENS_MINB 4
+#endif
+#ifndef SPH_DENS_MINB1
+#define SPH_DENS_MINB1 5
 #endif
 #ifndef SPH_DENS_LCAP1
 #define SPH_DENS_LCAP1 96
@@ -19,12 +23,15 @@
 
 // forces: staged candidates per chunk, blocks per SM the registers are sized
 // for, table of candidate leaves, list entries per lane and candidates per
-// list-room check (at several lanes per particle, and at one)
+// list-room check (each at several lanes per particle, and at one)
 #ifndef SPH_FORCE_CH
 #define SPH_FORCE_CH 64
 #endif
 #ifndef SPH_FORCE_MINB
-#define SPH_FORCE_MINB 5
+#define SPH_FORCE_MINB 4
+#endif
+#ifndef SPH_FORCE_MINB1
+#define SPH_FORCE_MINB1 5
 #endif
 #ifndef SPH_FORCE_TAB
 #define SPH_FORCE_TAB 64
