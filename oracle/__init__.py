@@ -65,6 +65,7 @@ class _Params(C.Structure):
         ("h_max_iter", C.c_int),
         ("use_grid", C.c_int),
         ("kernel", C.c_int),
+        ("ac_signal", C.c_int),
     ]
 
 
@@ -145,6 +146,7 @@ class Params:
     h_max_iter: int = 50
     use_grid: bool = False
     kernel: int = 0                 # 0 = M4 cubic spline (support 2h), 1 = M6 quintic (3h)
+    ac_signal: int = 0              # conductivity signal speed: 0 Wadsley |v.r_hat|, 1 Price sqrt(|dP|/rho_bar)
 
     def _c(self) -> _Params:
         p = _Params()
@@ -157,6 +159,7 @@ class Params:
         p.c_cfl, p.h_tol, p.h_max_iter = self.c_cfl, self.h_tol, int(self.h_max_iter)
         p.use_grid = int(bool(self.use_grid))
         p.kernel = int(self.kernel)
+        p.ac_signal = int(self.ac_signal)
         return p
 
 

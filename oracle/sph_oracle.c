@@ -60,6 +60,8 @@ typedef struct {
     int h_max_iter;
     int use_grid;            /* 0 = brute force, 1 = grid prefilter (same result) */
     int kernel;              /* 0 = M4 cubic spline (support 2h), 1 = M6 quintic (3h) */
+    int ac_signal;           /* conductivity signal speed: 0 = Wadsley |v_ij . r_hat|,
+                                1 = Price sqrt(|P_i - P_j| / rho_bar) (Sec. 2.1.1) */
 } orc_params;
 
 typedef struct {
@@ -375,6 +377,7 @@ static int params_ok(const orc_params *p, int64_t n)
     if (p->eos == 0 && !(p->gamma > 1.0)) return 0;
     if (p->eos == 1 && !(p->cs_iso > 0)) return 0;
     if (p->kernel != 0 && p->kernel != 1) return 0;
+    if (p->ac_signal != 0 && p->ac_signal != 1) return 0;
     return 1;
 }
 
@@ -570,6 +573,15 @@ int orc_density(const orc_params *p, int64_t n, orc_state *s)
     return status;
 }
 
+/* Signal speed of the artificial conductivity (Sec. 2.1.1): Wadsley's
+   |v_ij . r_hat_ij| by default, or Price's sqrt(|P_i - P_j| / rho_bar_ij). */
+static double ac_signal_speed(const orc_params *p, const orc_state *s, int64_t i, int64_t j, double vdr,
+                              double rhobar)
+{
+    if (p->ac_signal == 1) return sqrt(fabs(s->P[i] - s->P[j]) / rhobar);
+    return fabs(vdr);
+}
+
 /*
  * Accelerations and energy rates (Eqs. GRADHMOMEQN, GRADHENEQN, MON97ARTVISC,
  * MON97ENERGYDISS) and the signal speed of Eq. SPH_DT, over j != i with
@@ -637,7 +649,7 @@ int orc_forces(const orc_params *p, int64_t n, orc_state *s)
                 kadd(&az, f * rz);
                 if (p->eos == 0) {
                     double dui = Ai * mj * vdr * gi; /* Eq. GRADHENEQN */
-                    double duac = mj / rhobar * aac * fabs(vdr) * (s->u[i] - s->u[j]) * gbar;
+                    double duac = mj / rhobar * aac * ac_signal_speed(p, s, i, j, vdr, rhobar) * (s->u[i] - s->u[j]) * gbar;
                     kadd(&du, dui + duav + duac);
                 }
             }
@@ -880,7 +892,7 @@ int orc_forces_subset(const orc_params *p, int64_t n, orc_state *s, int64_t nsub
                 kadd(&az, f * rz);
                 if (p->eos == 0) {
                     double dui = Ai * mj * vdr * gi;
-                    double duac = mj / rhobar * aac * fabs(vdr) * (s->u[i] - s->u[j]) * gbar;
+                    double duac = mj / rhobar * aac * ac_signal_speed(p, s, i, j, vdr, rhobar) * (s->u[i] - s->u[j]) * gbar;
                     kadd(&du, dui + duav + duac);
                 }
             }
