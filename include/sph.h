@@ -68,6 +68,9 @@ extern "C" {
 #define SPH_KERNEL_M4 0      /* M4 cubic spline, support 2h (Sec. 2)                      */
 #define SPH_KERNEL_M6 1      /* M6 quintic spline, support 3h (Sec. 2)                    */
 
+#define SPH_AC_WADSLEY 0     /* conductivity signal speed |v_ij . r_hat_ij| (Wadsley 2008)  */
+#define SPH_AC_PRICE 1       /* conductivity signal speed sqrt(|P_i - P_j| / rho_bar) (Price) */
+
 #define SPH_FLAG_ASYNC 1u    /* compute calls return without synchronising the stream     */
 #define SPH_FLAG_TIMING 2u   /* record CUDA events around the stages of every step        */
 
@@ -110,6 +113,9 @@ typedef struct {
                               between (Sec. 4.2, tree reuse); 0 or 1: every step.
                               Results do not depend on it beyond round-off; the tree's
                               efficiency does.  Batched steps always rebuild.       */
+    int ac_signal;         /* artificial-conductivity signal speed (Sec. 2.1.1):
+                              SPH_AC_WADSLEY |v_ij . r_hat_ij| (default) or SPH_AC_PRICE
+                              sqrt(|P_i - P_j| / rho_bar_ij).  Any other value: SPH_EINVAL */
 } sph_params;
 
 /* Caller-owned device arrays, FP64, length n, caller's particle order.

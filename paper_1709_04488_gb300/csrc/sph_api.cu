@@ -194,6 +194,8 @@ namespace sph {
 int validate(const sph_params *p)
 {
     if (!p) return fail(SPH_EINVAL, "params is NULL");
+    if (p->ac_signal != SPH_AC_WADSLEY && p->ac_signal != SPH_AC_PRICE)
+        return fail(SPH_EINVAL, "ac_signal %d not supported (0 = Wadsley, 1 = Price)", p->ac_signal);
     if (p->kernel != SPH_KERNEL_M4 && p->kernel != SPH_KERNEL_M6)
         return fail(SPH_EINVAL, "kernel %d not supported (0 = M4 cubic spline, 1 = M6 quintic spline)", p->kernel);
     if (p->periodic != 0 && p->periodic != 1) return fail(SPH_EINVAL, "periodic must be 0 or 1");
@@ -242,6 +244,7 @@ PhysParams phys_of(const sph_params *p)
     ph.h_tol = p->h_tol > 0 ? p->h_tol : (p->precision == SPH_PREC_FP64 ? 1e-13 : 1e-6);
     ph.h_max_iter = p->h_max_iter > 0 ? p->h_max_iter : 50;
     ph.kernel = p->kernel;
+    ph.ac_signal = p->ac_signal;
     ph.kr = p->kernel == SPH_KERNEL_M6 ? 3.0 : 2.0;
     ph.kr_f = (float)ph.kr;
     return ph;

@@ -62,7 +62,7 @@ struct PhysParams {
     double kr;
     double box_inv[3];   // 1 / box_len (periodic), for minimum-image wraps
     float box_inv_f[3];
-    float pad_;
+    int ac_signal;       // SPH_AC_WADSLEY or SPH_AC_PRICE
 };
 
 // Per-problem diagnostics and persistent scalars; lives in the context's own

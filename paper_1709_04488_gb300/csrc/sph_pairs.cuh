@@ -1209,6 +1209,16 @@ struct TwoSumAcc {
     }
 };
 
+// conductivity signal speed (Sec. 2.1.1): Wadsley |v_ij . r_hat| (gm1 = 0)
+// or Price sqrt(|P_i - P_j| / rho_bar), P = gm1 rho u from the staged
+// (A, rho, m, u) vectors
+template <typename T, typename V>
+__device__ __forceinline__ T ac_speed(T vdr, const V &ti, const V &tj, T gm1, T rhob_inv)
+{
+    if (gm1 > T(0)) return sqrt(gm1 * fabs(ti.y * ti.w - tj.y * tj.w) * rhob_inv);
+    return fabs(vdr);
+}
+
 template <typename V>
 __device__ __forceinline__ V ld_ro(const V *p);
 template <>
@@ -1257,6 +1267,9 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
     const int s = st + (active ? pp : 0);
     const V xi = gph[s], vi = gvc[s], ti = gth[s];
     const T alpha = (T)ph.alpha_av, beta = (T)ph.beta_av, aac = (T)ph.alpha_ac;
+    // Price conductivity: v'_sig = sqrt(|P_i - P_j| / rho_bar) with P = (gamma - 1) rho u
+    // (adiabatic); 0 selects Wadsley's |v_ij . r_hat|
+    const T gm1_price = ph.ac_signal == SPH_AC_PRICE ? (T)(ph.gamma - 1.0) : T(0);
     const bool adi = ph.eos == SPH_EOS_ADIABATIC;
     const T sigma = T(KF::sigma);
     const T hi2 = mul_rn(xi.w, xi.w), hi4 = mul_rn(hi2, hi2);
@@ -1322,7 +1335,7 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
             az.add(mul_rn(wgt, rz));
             if (adi)
                 du += a2.z * (ti.x * vdr * gi +
-                              rhob_inv * gbar * (T(-0.5) * alpha * vsig * mu * mu + aac * fabs(vdr) * (ti.w - a2.w)));
+                              rhob_inv * gbar * (T(-0.5) * alpha * vsig * mu * mu + aac * ac_speed(vdr, ti, a2, gm1_price, rhob_inv) * (ti.w - a2.w)));
             vs = vsig > vs ? vsig : vs;
         }
         pairs += cnt;

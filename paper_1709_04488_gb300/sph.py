@@ -18,6 +18,7 @@ OK, EINVAL, EBOX, ENOCONV, ENONFINITE, ETIMEOUT, ETOOBIG, EBUSY, EAGAIN, ECUDA, 
 EOS_ADIABATIC, EOS_ISOTHERMAL = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 KERNEL_M4, KERNEL_M6 = 0, 1
+AC_WADSLEY, AC_PRICE = 0, 1
 FLAG_ASYNC, FLAG_TIMING = 1, 2
 NSTAGES = 7
 STAGES = ["kick_drift", "sort", "tree", "density", "refit", "forces", "close"]
@@ -46,6 +47,7 @@ class Params(C.Structure):
         ("lanes_per_particle", C.c_int),
         ("flags", C.c_uint),
         ("tree_rebuild_every", C.c_int),
+        ("ac_signal", C.c_int),
     ]
 
 

@@ -37,17 +37,17 @@ def test_struct_layouts_match_header(S, tmp_path):
     src = tmp_path / "sizes.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "sph.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
         "sizeof(sph_params),sizeof(sph_state),sizeof(sph_diag),sizeof(sph_server_cfg),"
         "sizeof(sph_request),sizeof(sph_result),offsetof(sph_params,flags),offsetof(sph_diag,status),"
-        "offsetof(sph_params,tree_rebuild_every));return 0;}\n")
+        "offsetof(sph_params,tree_rebuild_every),offsetof(sph_params,ac_signal));return 0;}\n")
     exe = tmp_path / "sizes"
     import subprocess
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     want = [C.sizeof(S.Params), C.sizeof(S.State), C.sizeof(S.Diag), C.sizeof(S.ServerCfg),
             C.sizeof(S.Request), C.sizeof(S.Result), S.Params.flags.offset, S.Diag.status.offset,
-            S.Params.tree_rebuild_every.offset]
+            S.Params.tree_rebuild_every.offset, S.Params.ac_signal.offset]
     assert got == want
 
 
@@ -60,7 +60,7 @@ def test_defaults_are_the_papers(S):
 def test_constants_match_header(S):
     txt = open(os.path.join(ROOT, "include", "sph.h")).read()
     defs = dict(re.findall(r"#define (SPH_[A-Z0-9_]+)\s+(-?\d+)u?\b", txt))
-    for name in ("KERNEL_M4", "KERNEL_M6", "EOS_ADIABATIC", "EOS_ISOTHERMAL", "PREC_FP64", "PREC_MIXED",
+    for name in ("KERNEL_M4", "KERNEL_M6", "AC_WADSLEY", "AC_PRICE", "EOS_ADIABATIC", "EOS_ISOTHERMAL", "PREC_FP64", "PREC_MIXED",
                  "FLAG_ASYNC", "FLAG_TIMING"):
         assert int(defs["SPH_" + name]) == getattr(S, name), name
 
@@ -80,6 +80,9 @@ def test_workspace_bytes_and_validation(S):
     assert S.sph_workspace_bytes(1000, m6) > 0
     bad = S.sph_params_default()
     bad.kernel = 2
+    assert S.sph_workspace_bytes(10, bad) == 0
+    bad = S.sph_params_default()
+    bad.ac_signal = 2
     assert S.sph_workspace_bytes(10, bad) == 0
     bad = S.sph_params_default()
     bad.lanes_per_particle = 3

@@ -373,3 +373,38 @@ def test_force_candidates_reused_or_rewalked(S, oracle_mod, guess):
     assert _rel(g["rho"], ref.rho) < 1e-5
     assert _rms_err(_acc(g), np.stack([ref.ax, ref.ay, ref.az], 1)) < 1e-4
     assert _rms_err(g["du"], ref.du) < 1e-4
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_price_conductivity_matches_oracle(S, oracle_mod, prec):
+    """Price (2008) conductivity signal speed (Sec. 2.1.1) on a moving lattice
+    with a hot slab (conduction active everywhere the pressures differ)."""
+    O = oracle_mod
+    a, p = _moving_lattice(14, seed=41)
+    a["u"] = a["u"] * np.where(a["x"] < 0.5, 2.0, 1.0)
+    P, ref = _oracle(O, a, p, ac_signal=1)
+    fp64 = prec == "fp64"
+    g = _gpu(S, a, p, S.PREC_FP64 if fp64 else S.PREC_MIXED, ac_signal=S.AC_PRICE).numpy()
+    tol, atol = (1e-12, 1e-12) if fp64 else (1e-5, 1e-4)
+    assert _rel(g["rho"], ref.rho) < tol
+    ra = np.stack([ref.ax, ref.ay, ref.az], 1)
+    arms = np.sqrt(np.mean(np.sum(ra ** 2, 1)))
+    assert np.max(np.linalg.norm(_acc(g) - ra, axis=1)) < atol * arms
+    assert _rms_err(g["du"], ref.du) < atol
+    # the conduction term differs from Wadsley's
+    _, wad = _oracle(O, a, p, ac_signal=0)
+    assert _rms_err(wad.du, ref.du) > 1e-3
+
+
+def test_price_sod_steps_match_oracle(S, oracle_mod):
+    O = oracle_mod
+    a, p = ics.sod(left=(32, 16, 16), right=(16, 8, 8), width=0.25)
+    P, ref = _oracle(O, a, p, grid=True, ac_signal=1)
+    prob = _gpu(S, a, p, S.PREC_MIXED, ac_signal=S.AC_PRICE)
+    for _ in range(6):
+        dt = O.cfl_dt(P, ref)
+        assert O.step(P, ref, dt) == O.OK
+        prob.step(dt)
+    g = prob.numpy()
+    assert _rel(g["rho"], ref.rho) < 1e-5
+    assert _rms_err(g["u"], ref.u) < 1e-5
