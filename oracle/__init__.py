@@ -66,6 +66,9 @@ class _Params(C.Structure):
         ("use_grid", C.c_int),
         ("kernel", C.c_int),
         ("ac_signal", C.c_int),
+        ("av_switch", C.c_int),
+        ("alpha_min", C.c_double),
+        ("av_decay", C.c_double),
     ]
 
 
@@ -75,10 +78,11 @@ _IP = C.POINTER(C.c_int32)
 _FIELDS_D = ["x", "y", "z", "vx", "vy", "vz", "u", "m", "h",
              "rho", "omega", "P", "c", "ax", "ay", "az", "du", "vsig"]
 _FIELDS_I = ["nngb", "iters"]
+_FIELDS_A = ["alpha", "dalpha"]  # viscosity switch: alpha per particle and its rate
 
 
 class _State(C.Structure):
-    _fields_ = [(f, _DP) for f in _FIELDS_D] + [(f, _IP) for f in _FIELDS_I]
+    _fields_ = [(f, _DP) for f in _FIELDS_D] + [(f, _IP) for f in _FIELDS_I] + [(f, _DP) for f in _FIELDS_A]
 
 
 _lib = None
@@ -147,6 +151,9 @@ class Params:
     use_grid: bool = False
     kernel: int = 0                 # 0 = M4 cubic spline (support 2h), 1 = M6 quintic (3h)
     ac_signal: int = 0              # conductivity signal speed: 0 Wadsley |v.r_hat|, 1 Price sqrt(|dP|/rho_bar)
+    av_switch: int = 0              # 1: Morris & Monaghan viscosity switch (alpha per particle)
+    alpha_min: float = 0.1          # switch: floor of alpha
+    av_decay: float = 0.1           # switch: tau = h / (av_decay c)
 
     def _c(self) -> _Params:
         p = _Params()
@@ -160,6 +167,8 @@ class Params:
         p.use_grid = int(bool(self.use_grid))
         p.kernel = int(self.kernel)
         p.ac_signal = int(self.ac_signal)
+        p.av_switch = int(self.av_switch)
+        p.alpha_min, p.av_decay = self.alpha_min, self.av_decay
         return p
 
 
@@ -171,7 +180,7 @@ class State:
     def __init__(self, **arrays):
         n = len(arrays["x"])
         self.n = n
-        for f in _FIELDS_D:
+        for f in _FIELDS_D + _FIELDS_A:
             a = arrays.get(f)
             a = np.zeros(n) if a is None else np.array(a, dtype=np.float64, copy=True)
             setattr(self, f, np.ascontiguousarray(a, dtype=np.float64))
@@ -179,14 +188,14 @@ class State:
             setattr(self, f, np.zeros(n, dtype=np.int32))
 
     def copy(self) -> "State":
-        s = State(**{f: getattr(self, f) for f in _FIELDS_D})
+        s = State(**{f: getattr(self, f) for f in _FIELDS_D + _FIELDS_A})
         for f in _FIELDS_I:
             setattr(s, f, getattr(self, f).copy())
         return s
 
     def _c(self) -> _State:
         st = _State()
-        for f in _FIELDS_D:
+        for f in _FIELDS_D + _FIELDS_A:
             a = getattr(self, f)
             assert a.flags.c_contiguous and a.dtype == np.float64 and len(a) == self.n
             setattr(st, f, a.ctypes.data_as(_DP))

@@ -62,6 +62,10 @@ typedef struct {
     int kernel;              /* 0 = M4 cubic spline (support 2h), 1 = M6 quintic (3h) */
     int ac_signal;           /* conductivity signal speed: 0 = Wadsley |v_ij . r_hat|,
                                 1 = Price sqrt(|P_i - P_j| / rho_bar) (Sec. 2.1.1) */
+    int av_switch;           /* 0: constant alpha_av; 1: Morris & Monaghan (1997) switch,
+                                one alpha per particle (Sec. 2.1.1) */
+    double alpha_min;        /* switch: floor the viscosity decays to */
+    double av_decay;         /* switch: decay time tau = h / (av_decay c) */
 } orc_params;
 
 typedef struct {
@@ -71,6 +75,7 @@ typedef struct {
     double *rho, *omega, *P, *c;
     double *ax, *ay, *az, *du, *vsig;
     int32_t *nngb, *iters;
+    double *alpha, *dalpha;  /* switch: viscosity parameter per particle and its rate */
 } orc_state;
 
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_EBOX = -2, ORC_ENOCONV = -3, ORC_ENOMEM = -9 };
@@ -378,6 +383,9 @@ static int params_ok(const orc_params *p, int64_t n)
     if (p->eos == 1 && !(p->cs_iso > 0)) return 0;
     if (p->kernel != 0 && p->kernel != 1) return 0;
     if (p->ac_signal != 0 && p->ac_signal != 1) return 0;
+    if (p->av_switch != 0 && p->av_switch != 1) return 0;
+    if (p->av_switch && !(p->alpha_av > 0 && p->alpha_min >= 0 && p->alpha_min <= p->alpha_av && p->av_decay > 0))
+        return 0;
     return 1;
 }
 
@@ -573,6 +581,31 @@ int orc_density(const orc_params *p, int64_t n, orc_state *s)
     return status;
 }
 
+/* Viscosity parameters of pair (i,j): alpha_AV and beta_AV = (beta/alpha)
+   alpha_AV, the latter the pair mean of the particles' alphas under the
+   Morris & Monaghan switch. */
+static void av_pair(const orc_params *p, const orc_state *s, int64_t i, int64_t j, double *a, double *b)
+{
+    if (p->av_switch) {
+        *a = 0.5 * (s->alpha[i] + s->alpha[j]);
+        *b = p->beta_av / p->alpha_av * (*a);
+    } else {
+        *a = p->alpha_av;
+        *b = p->beta_av;
+    }
+}
+
+/* Morris & Monaghan (1997) switch: d alpha_i/dt = -(alpha_i - alpha_min)/tau_i
+   + max(-div v_i, 0) (alpha_max - alpha_i), tau_i = h_i / (av_decay c_i),
+   alpha_max = alpha_av; div v_i = -(1/(Omega_i rho_i)) sum_j m_j v_ij . grad_i W(r_ij, h_i)
+   (sumv: the sum). */
+static double av_rate(const orc_params *p, const orc_state *s, int64_t i, double sumv)
+{
+    const double divv = -sumv / (s->omega[i] * s->rho[i]);
+    const double src = divv < 0 ? -divv * (p->alpha_av - s->alpha[i]) : 0.0;
+    return -(s->alpha[i] - p->alpha_min) * p->av_decay * s->c[i] / s->h[i] + src;
+}
+
 /* Signal speed of the artificial conductivity (Sec. 2.1.1): Wadsley's
    |v_ij . r_hat_ij| by default, or Price's sqrt(|P_i - P_j| / rho_bar_ij). */
 static double ac_signal_speed(const orc_params *p, const orc_state *s, int64_t i, int64_t j, double vdr,
@@ -589,6 +622,7 @@ static double ac_signal_speed(const orc_params *p, const orc_state *s, int64_t i
  */
 int orc_forces(const orc_params *p, int64_t n, orc_state *s)
 {
+    if (p && p->av_switch && (!s->alpha || !s->dalpha)) return ORC_EINVAL;
     if (!params_ok(p, n)) return ORC_EINVAL;
     if (n == 0) return ORC_OK;
     double hmax = 0;
@@ -600,7 +634,7 @@ int orc_forces(const orc_params *p, int64_t n, orc_state *s)
         if (grid_build(&g, p, s, n, 2.0 * median_spacing_guess(p, s, n))) return ORC_ENOMEM;
         gp = &g;
     }
-    const double alpha = p->alpha_av, beta = p->beta_av, aac = p->alpha_ac;
+    const double aac = p->alpha_ac;
     int status = ORC_OK;
 #pragma omp parallel
     {
@@ -614,7 +648,7 @@ int orc_forces(const orc_params *p, int64_t n, orc_state *s)
                 continue;
             }
             const double Ai = s->P[i] / (s->omega[i] * s->rho[i] * s->rho[i]);
-            kahan_t ax = {0, 0}, ay = {0, 0}, az = {0, 0}, du = {0, 0};
+            kahan_t ax = {0, 0}, ay = {0, 0}, az = {0, 0}, du = {0, 0}, dv = {0, 0};
             double vsig = 2.0 * s->c[i]; /* no neighbour: c_i + c_i */
             int have = 0;
             for (int64_t k = 0; k < buf.n; ++k) {
@@ -633,7 +667,9 @@ int orc_forces(const orc_params *p, int64_t n, orc_state *s)
                 double vdr = vxij * rx + vyij * ry + vzij * rz; /* v_ij . r_hat_ij */
                 double gbar = 0.5 * (gi + gj);                   /* r_hat . mean grad W */
                 double rhobar = 0.5 * (s->rho[i] + s->rho[j]);
-                double fav = 0.0, duav = 0.0;
+                double fav = 0.0, duav = 0.0, alpha, beta;
+                av_pair(p, s, i, j, &alpha, &beta);
+                kadd(&dv, mj * vdr * gi); /* sum_j m_j v_ij . grad_i W(h_i) */
                 double vs = s->c[i] + s->c[j] - beta * (vdr < 0 ? vdr : 0.0);
                 if (!have || vs > vsig) vsig = vs;
                 have = 1;
@@ -658,6 +694,7 @@ int orc_forces(const orc_params *p, int64_t n, orc_state *s)
             s->az[i] = az.s;
             s->du[i] = (p->eos == 0) ? du.s : 0.0;
             s->vsig[i] = vsig;
+            if (p->av_switch) s->dalpha[i] = av_rate(p, s, i, dv.s);
         }
         free(buf.v);
     }
@@ -693,15 +730,20 @@ static double wrap(double x, double lo, double L)
 int orc_step(const orc_params *p, int64_t n, orc_state *s, double dt)
 {
     if (!params_ok(p, n) || !(dt > 0)) return ORC_EINVAL;
-    double *vh = (double *)malloc((size_t)(n > 0 ? n : 1) * 4 * sizeof(double));
+    if (p->av_switch && (!s->alpha || !s->dalpha)) return ORC_EINVAL;
+    double *vh = (double *)malloc((size_t)(n > 0 ? n : 1) * 5 * sizeof(double));
     if (!vh) return ORC_ENOMEM;
-    double *vhx = vh, *vhy = vh + n, *vhz = vh + 2 * n, *uh = vh + 3 * n;
+    double *vhx = vh, *vhy = vh + n, *vhz = vh + 2 * n, *uh = vh + 3 * n, *ah = vh + 4 * n;
     const int adi = (p->eos == 0);
     for (int64_t i = 0; i < n; ++i) {
         vhx[i] = s->vx[i] + 0.5 * s->ax[i] * dt;
         vhy[i] = s->vy[i] + 0.5 * s->ay[i] * dt;
         vhz[i] = s->vz[i] + 0.5 * s->az[i] * dt;
         uh[i] = adi ? s->u[i] + 0.5 * s->du[i] * dt : s->u[i];
+        if (p->av_switch) { /* the switch's alpha is kicked and predicted like u */
+            ah[i] = s->alpha[i] + 0.5 * s->dalpha[i] * dt;
+            s->alpha[i] = ah[i] + 0.5 * s->dalpha[i] * dt;
+        }
         s->x[i] += vhx[i] * dt;
         s->y[i] += vhy[i] * dt;
         s->z[i] += vhz[i] * dt;
@@ -723,6 +765,7 @@ int orc_step(const orc_params *p, int64_t n, orc_state *s, double dt)
         s->vy[i] = vhy[i] + 0.5 * s->ay[i] * dt;
         s->vz[i] = vhz[i] + 0.5 * s->az[i] * dt;
         if (adi) s->u[i] = uh[i] + 0.5 * s->du[i] * dt;
+        if (p->av_switch) s->alpha[i] = ah[i] + 0.5 * s->dalpha[i] * dt;
     }
     free(vh);
     return rc2 ? rc2 : rc;
@@ -839,11 +882,12 @@ int orc_forces_subset(const orc_params *p, int64_t n, orc_state *s, int64_t nsub
                       double hmax)
 {
     if (!params_ok(p, n) || nsub < 0 || !(hmax > 0)) return ORC_EINVAL;
+    if (p->av_switch && (!s->alpha || !s->dalpha)) return ORC_EINVAL;
     if (n == 0 || nsub == 0) return ORC_OK;
     grid_t g;
     memset(&g, 0, sizeof g);
     if (grid_build(&g, p, s, n, 2.0 * median_spacing_guess(p, s, n))) return ORC_ENOMEM;
-    const double alpha = p->alpha_av, beta = p->beta_av, aac = p->alpha_ac;
+    const double aac = p->alpha_ac;
     int status = ORC_OK;
 #pragma omp parallel
     {
@@ -858,7 +902,7 @@ int orc_forces_subset(const orc_params *p, int64_t n, orc_state *s, int64_t nsub
                 continue;
             }
             const double Ai = s->P[i] / (s->omega[i] * s->rho[i] * s->rho[i]);
-            kahan_t ax = {0, 0}, ay = {0, 0}, az = {0, 0}, du = {0, 0};
+            kahan_t ax = {0, 0}, ay = {0, 0}, az = {0, 0}, du = {0, 0}, dv = {0, 0};
             double vsig = 2.0 * s->c[i];
             int have = 0;
             for (int64_t q = 0; q < buf.n; ++q) {
@@ -876,7 +920,9 @@ int orc_forces_subset(const orc_params *p, int64_t n, orc_state *s, int64_t nsub
                 double vdr = vxij * rx + vyij * ry + vzij * rz;
                 double gbar = 0.5 * (gi + gj);
                 double rhobar = 0.5 * (s->rho[i] + s->rho[j]);
-                double fav = 0.0, duav = 0.0;
+                double fav = 0.0, duav = 0.0, alpha, beta;
+                av_pair(p, s, i, j, &alpha, &beta);
+                kadd(&dv, mj * vdr * gi); /* sum_j m_j v_ij . grad_i W(h_i) */
                 double vs = s->c[i] + s->c[j] - beta * (vdr < 0 ? vdr : 0.0);
                 if (!have || vs > vsig) vsig = vs;
                 have = 1;
@@ -901,6 +947,7 @@ int orc_forces_subset(const orc_params *p, int64_t n, orc_state *s, int64_t nsub
             s->az[i] = az.s;
             s->du[i] = (p->eos == 0) ? du.s : 0.0;
             s->vsig[i] = vsig;
+            if (p->av_switch) s->dalpha[i] = av_rate(p, s, i, dv.s);
         }
         free(buf.v);
     }
