@@ -71,6 +71,9 @@ extern "C" {
 #define SPH_AC_WADSLEY 0     /* conductivity signal speed |v_ij . r_hat_ij| (Wadsley 2008)  */
 #define SPH_AC_PRICE 1       /* conductivity signal speed sqrt(|P_i - P_j| / rho_bar) (Price) */
 
+#define SPH_AV_CONSTANT 0          /* viscosity alpha_av everywhere                       */
+#define SPH_AV_MORRIS_MONAGHAN 1   /* per-particle alpha, Morris & Monaghan (1997) switch  */
+
 #define SPH_FLAG_ASYNC 1u    /* compute calls return without synchronising the stream     */
 #define SPH_FLAG_TIMING 2u   /* record CUDA events around the stages of every step        */
 
@@ -116,6 +119,17 @@ typedef struct {
     int ac_signal;         /* artificial-conductivity signal speed (Sec. 2.1.1):
                               SPH_AC_WADSLEY |v_ij . r_hat_ij| (default) or SPH_AC_PRICE
                               sqrt(|P_i - P_j| / rho_bar_ij).  Any other value: SPH_EINVAL */
+    int av_switch;         /* SPH_AV_CONSTANT (alpha_av everywhere, default) or
+                              SPH_AV_MORRIS_MONAGHAN: one alpha per particle (state.alpha),
+                              d alpha/dt = -(alpha - alpha_min) av_decay c / h
+                              + max(-div v, 0) (alpha_av - alpha), integrated like u;
+                              pair (i,j) uses alpha_ij = (alpha_i + alpha_j)/2 and
+                              beta_ij = beta_av / alpha_av alpha_ij (Sec. 2.1.1 names the
+                              Morris & Monaghan 1997 switch).  Requires alpha_av > 0,
+                              0 <= alpha_min <= alpha_av, av_decay > 0 and non-NULL
+                              state.alpha, state.dalpha; not accepted by the server.  */
+    double alpha_min;      /* switch: floor alpha decays to (default 0.1)               */
+    double av_decay;       /* switch: decay rate in units of c/h (default 0.1)          */
 } sph_params;
 
 /* Caller-owned device arrays, FP64, length n, caller's particle order.
@@ -129,6 +143,9 @@ typedef struct {
     double *u, *m, *h;
     double *rho, *omega, *P, *c;
     double *ax, *ay, *az, *du, *vsig;
+    double *alpha, *dalpha; /* viscosity switch only (else may be NULL): alpha per particle
+                               (input, advanced by sph_step) and d alpha/dt (output of the
+                               force evaluation)                                          */
 } sph_state;
 
 /* Per-call diagnostics (FP64 reductions over the particles, Sec. 2.1.1

@@ -63,10 +63,11 @@ void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precis
     b.hist = c.take<unsigned>(passes * 256 + 8 + passes * nblk * 256);
     b.perm = c.take<int>(n);
     double **sd[] = {&b.sx, &b.sy, &b.sz, &b.sh, &b.sm, &b.srho, &b.somega, &b.sP, &b.sc,
-                     &b.vpx, &b.vpy, &b.vpz, &b.up};
+                     &b.vpx, &b.vpy, &b.vpz, &b.up, &b.ap};
     for (double **p : sd) *p = c.take<double>(n);
     void **st[] = {&b.pm, &b.ph, &b.vc, &b.th};
     for (void **p : st) *p = c.take<char>(v4 * n);
+    b.sal = c.take<char>(v4 / 4 * n);
     b.flag = c.take<unsigned>(n);
     const long long ml = leaves_upper_bound(n);
     b.max_leaves = (int)ml;
@@ -194,6 +195,11 @@ namespace sph {
 int validate(const sph_params *p)
 {
     if (!p) return fail(SPH_EINVAL, "params is NULL");
+    if (p->av_switch != SPH_AV_CONSTANT && p->av_switch != SPH_AV_MORRIS_MONAGHAN)
+        return fail(SPH_EINVAL, "av_switch %d not supported (0 = constant, 1 = Morris & Monaghan)", p->av_switch);
+    if (p->av_switch == SPH_AV_MORRIS_MONAGHAN &&
+        !(p->alpha_av > 0 && p->alpha_min >= 0 && p->alpha_min <= p->alpha_av && p->av_decay > 0))
+        return fail(SPH_EINVAL, "viscosity switch needs alpha_av > 0, 0 <= alpha_min <= alpha_av, av_decay > 0");
     if (p->ac_signal != SPH_AC_WADSLEY && p->ac_signal != SPH_AC_PRICE)
         return fail(SPH_EINVAL, "ac_signal %d not supported (0 = Wadsley, 1 = Price)", p->ac_signal);
     if (p->kernel != SPH_KERNEL_M4 && p->kernel != SPH_KERNEL_M6)
@@ -245,6 +251,10 @@ PhysParams phys_of(const sph_params *p)
     ph.h_max_iter = p->h_max_iter > 0 ? p->h_max_iter : 50;
     ph.kernel = p->kernel;
     ph.ac_signal = p->ac_signal;
+    ph.av_switch = p->av_switch;
+    ph.alpha_min = p->alpha_min;
+    ph.av_decay = p->av_decay;
+    ph.beta_ratio = p->alpha_av > 0 ? p->beta_av / p->alpha_av : 0.0;
     ph.kr = p->kernel == SPH_KERNEL_M6 ? 3.0 : 2.0;
     ph.kr_f = (float)ph.kr;
     return ph;
@@ -313,6 +323,8 @@ int sph_params_default(sph_params *p)
     p->h_tol = 0.0;
     p->h_max_iter = 50;
     p->precision = SPH_PREC_MIXED;
+    p->alpha_min = 0.1;
+    p->av_decay = 0.1;
     return SPH_OK;
 }
 
@@ -343,6 +355,8 @@ int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *st
                                state->ax, state->ay, state->az, state->du, state->vsig};
         for (const double *q : req)
             if (!q) return fail(SPH_EINVAL, "a state array is NULL");
+        if (p->av_switch && (!state->alpha || !state->dalpha))
+            return fail(SPH_EINVAL, "the viscosity switch needs state.alpha and state.dalpha");
     }
     size_t need = sph_workspace_bytes(n, p);
     if (!workspace || ws_bytes < need)
@@ -381,6 +395,7 @@ int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *st
     c->bv.lpp_mask = mask_of(c->lpp, p->kernel);
     c->bv.any_isolated = p->periodic ? 0 : 1;
     c->bv.any_periodic = p->periodic ? 1 : 0;
+    c->bv.any_general = (p->av_switch || p->ac_signal) ? 1 : 0;
     ProbStatic &ps = c->host_ps;
     memset(&ps, 0, sizeof ps);
     ps.x = state->x;
@@ -401,6 +416,8 @@ int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *st
     ps.az = state->az;
     ps.du = state->du;
     ps.vsig = state->vsig;
+    ps.alpha = state->alpha;
+    ps.dalpha = state->dalpha;
     ps.n = n;
     ps.base = 0;
     ps.diag = c->diag;
@@ -799,7 +816,7 @@ int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, 
     long long ntot = 0;
     std::vector<ProbStatic> tab(nctx);
     std::vector<long long> bases(nctx + 1);
-    int mask = 0, dmask = 0, b_any_isolated = 0, b_any_periodic = 0;
+    int mask = 0, dmask = 0, b_any_isolated = 0, b_any_periodic = 0, b_any_general = 0;
     for (int k = 0; k < nctx; ++k) {
         tab[k] = ctxs[k]->host_ps;
         tab[k].base = ntot;
@@ -809,6 +826,7 @@ int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, 
         dmask |= dens_class_bit(tab[k].lpp, tab[k].uniform_m, tab[k].ph.kernel);
         if (!tab[k].ph.periodic) b_any_isolated = 1;
         else b_any_periodic = 1;
+        if (tab[k].ph.av_switch || tab[k].ph.ac_signal) b_any_general = 1;
     }
     bases[nctx] = ntot;
     Carver cv{(char *)workspace};
@@ -823,6 +841,7 @@ int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, 
     b.dens_mask = dmask;
     b.any_isolated = b_any_isolated;
     b.any_periodic = b_any_periodic;
+    b.any_general = b_any_general;
     CU(cudaMemcpyAsync(b.prob, tab.data(), sizeof(ProbStatic) * nctx, cudaMemcpyHostToDevice, st));
     CU(cudaMemcpyAsync(b.prob_base, bases.data(), sizeof(long long) * (nctx + 1), cudaMemcpyHostToDevice, st));
     CU(cudaMemsetAsync(b.dyn, 0, sizeof(ProbDyn) * nctx, st));

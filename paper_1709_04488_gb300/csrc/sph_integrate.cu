@@ -109,6 +109,11 @@ __global__ void k_kick_drift(BatchView b, double dt_host)
     } else {
         b.up[g] = u;
     }
+    if (ph.av_switch) {  // the switch's alpha is kicked and predicted like u
+        const double ah = ps.alpha[i] + hdt * ps.dalpha[i];
+        ps.alpha[i] = ah;
+        b.ap[g] = ah + hdt * ps.dalpha[i];
+    }
 }
 
 __device__ __forceinline__ void add_diag(ProbDiag *d, const double *v)
@@ -195,6 +200,7 @@ __global__ void k_kick_close(BatchView b, int do_kick, int forces_ran, int items
                 u += hdt * du;
                 ps.u[i] = u;
             }
+            if (ph.av_switch) ps.alpha[i] += hdt * ps.dalpha[i];
         }
         double m = ps.m[i];
         v[0] += m;

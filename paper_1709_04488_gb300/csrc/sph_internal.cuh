@@ -63,6 +63,8 @@ struct PhysParams {
     double box_inv[3];   // 1 / box_len (periodic), for minimum-image wraps
     float box_inv_f[3];
     int ac_signal;       // SPH_AC_WADSLEY or SPH_AC_PRICE
+    int av_switch;       // SPH_AV_CONSTANT or SPH_AV_MORRIS_MONAGHAN
+    double alpha_min, av_decay, beta_ratio;  // switch: floor, decay rate (c/h), beta_av / alpha_av
 };
 
 // Per-problem diagnostics and persistent scalars; lives in the context's own
@@ -92,6 +94,7 @@ struct ProbStatic {
     // caller state arrays (original particle order)
     double *x, *y, *z, *vx, *vy, *vz, *u, *m, *h;
     double *rho, *omega, *P, *c, *ax, *ay, *az, *du, *vsig;
+    double *alpha, *dalpha;  // viscosity switch (NULL without it)
     long long n;
     long long base;  // offset of this problem in the batch-global particle index space
     ProbDiag *diag;
@@ -151,6 +154,8 @@ struct BatchView {
     int key_lo;                  // lowest key bit that is sorted (the bits below are cleared)
     int any_isolated;            // some problem is isolated (needs a bounding box)
     int any_periodic;            // some problem is periodic (wrap-list launches)
+    int any_general;             // some problem uses the viscosity switch or Price's conductivity
+                                 // (served by the wrap-list force launches)
     ProbStatic *prob;            // [nprob]
     ProbDyn *dyn;                // [nprob]
     long long *prob_base;        // [nprob + 1] base offsets (for searches)
@@ -164,11 +169,13 @@ struct BatchView {
     double *srho, *somega, *sP, *sc;
     // predicted velocity / internal energy (original order, batch-global)
     double *vpx, *vpy, *vpz, *up;
+    double *ap;  // predicted alpha of the viscosity switch (original order)
     // staging for the pair kernels (sorted order); element type float4 or double4
     void *pm;   // (offset xyz, m)
     void *ph;   // (offset xyz, h)
     void *vc;   // (v xyz, c)
     void *th;   // (P/(Omega rho^2), rho, m, u)
+    void *sal;  // alpha of the viscosity switch (T per particle)
     // leaves
     unsigned *flag;              // [ntot] leaf start flags, then leaf index (scan)
     int *leaf_start;             // [max_leaves + 1]

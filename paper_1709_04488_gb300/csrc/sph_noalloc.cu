@@ -78,6 +78,8 @@ extern "C" int sph_density_forces_noalloc(const sph_params *p, int64_t n, const 
                                state->ax, state->ay, state->az, state->du, state->vsig};
         for (const double *q : req)
             if (!q) return fail(SPH_EINVAL, "a state array is NULL");
+        if (p->av_switch && (!state->alpha || !state->dalpha))
+            return fail(SPH_EINVAL, "the viscosity switch needs state.alpha and state.dalpha");
     }
     void *base = nullptr;
     rc = scratch_for_current_device(&base);
@@ -98,6 +100,7 @@ extern "C" int sph_density_forces_noalloc(const sph_params *p, int64_t n, const 
     b.dens_mask = dens_class_bit(lpp, 0, p->kernel);  // masses are not inspected here: distance-and-mass lists
     b.any_isolated = p->periodic ? 0 : 1;
     b.any_periodic = p->periodic ? 1 : 0;
+    b.any_general = (p->av_switch || p->ac_signal) ? 1 : 0;
     ProbStatic ps;
     memset(&ps, 0, sizeof ps);
     ps.x = state->x;
@@ -118,6 +121,8 @@ extern "C" int sph_density_forces_noalloc(const sph_params *p, int64_t n, const 
     ps.az = state->az;
     ps.du = state->du;
     ps.vsig = state->vsig;
+    ps.alpha = state->alpha;
+    ps.dalpha = state->dalpha;
     ps.n = n;
     ps.base = 0;
     ps.diag = diag;

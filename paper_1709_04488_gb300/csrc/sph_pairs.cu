@@ -37,8 +37,8 @@ cudaError_t launch_forces(const BatchView &b, int precision, cudaStream_t st)
     if (b.ntot == 0) return cudaSuccess;
     cudaError_t e = force_launches_m4(b, precision, st);
     if (e == cudaSuccess) e = force_launches_m6(b, precision, st);
-    if (e == cudaSuccess && b.any_periodic) e = force_launches_m4_wrap(b, precision, st);
-    if (e == cudaSuccess && b.any_periodic) e = force_launches_m6_wrap(b, precision, st);
+    if (e == cudaSuccess && (b.any_periodic || b.any_general)) e = force_launches_m4_wrap(b, precision, st);
+    if (e == cudaSuccess && (b.any_periodic || b.any_general)) e = force_launches_m6_wrap(b, precision, st);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }

@@ -633,6 +633,7 @@ __device__ __forceinline__ void density_epilogue(const BatchView &b, const ProbS
     q.z = pi.w;
     q.w = (T)u;
     ((V *)b.th)[s] = q;
+    if (ph.av_switch) ((T *)b.sal)[s] = (T)(use_pred ? b.ap[g] : ps.alpha[i]);  // viscosity switch
     if (!(isfinite((double)rho) && isfinite((double)omega) && isfinite((double)P)))
         atomicOr(&ps.diag->status, ST_NONFINITE);
 }
@@ -1269,10 +1270,16 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
     const T alpha = (T)ph.alpha_av, beta = (T)ph.beta_av, aac = (T)ph.alpha_ac;
     // Price conductivity: v'_sig = sqrt(|P_i - P_j| / rho_bar) with P = (gamma - 1) rho u
     // (adiabatic); 0 selects Wadsley's |v_ij . r_hat|
-    const T gm1_price = ph.ac_signal == SPH_AC_PRICE ? (T)(ph.gamma - 1.0) : T(0);
+    const T gm1_price = WRAP && ph.ac_signal == SPH_AC_PRICE ? (T)(ph.gamma - 1.0) : T(0);
     const bool adi = ph.eos == SPH_EOS_ADIABATIC;
     const T sigma = T(KF::sigma);
     const T hi2 = mul_rn(xi.w, xi.w), hi4 = mul_rn(hi2, hi2);
+    // viscosity switch (served by the wrap-list launch): alpha_ij = (alpha_i + alpha_j)/2,
+    // beta_ij = beta/alpha_max alpha_ij
+    const bool sw = WRAP && ph.av_switch != 0;
+    const T* __restrict__ sal = (const T *)b.sal;
+    const T alpha_i = sw ? sal[s] : alpha, bratio = (T)ph.beta_ratio;
+    T dvs = T(0);  // sum_j m_j v_ij . grad_i W(h_i) (switch: div v)
     TwoSumAcc<T> ax{T(0), T(0)}, ay{T(0), T(0)}, az{T(0), T(0)};
     T du = T(0), vs = T(-1);
     int pairs = 0, tested = 0;
@@ -1292,11 +1299,11 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
     // table entry of a candidate leaf: its shift and first sorted index,
     // stored as ~index for an ambiguous leaf pair (whose pair vectors the
     // evaluation wraps)
-    auto fetch = [&](int e, V &tb, V &a0, V &a1, V &a2) {
+    auto fetch = [&](int e, V &tb, V &a0, V &a1, V &a2, int &j) {
         const unsigned cd = lst[e * 32 + lane];
         tb = table[cd >> 5];
         const int tv = t_as_bits(tb.w);
-        const int j = (WRAP && tv < 0 ? ~tv : tv) + (int)(cd & 31u);
+        j = (WRAP && tv < 0 ? ~tv : tv) + (int)(cd & 31u);
         a0 = ld_ro(gph + j);
         a1 = ld_ro(gvc + j);
         a2 = ld_ro(gth + j);
@@ -1305,7 +1312,8 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
         __syncwarp();
         for (int e = 0; e < cnt; ++e) {
             V tb, a0, a1, a2;
-            fetch(e, tb, a0, a1, a2);
+            int j;
+            fetch(e, tb, a0, a1, a2, j);
             // r_ij = (o_i - o_j) - D_AB: IEEE subtraction is sign-symmetric and
             // D_BA = -D_AB exactly, so particle j forms exactly -r_ij
             T rx = sub_rn(sub_rn(xi.x, a0.x), tb.x), ry = sub_rn(sub_rn(xi.y, a0.y), tb.y),
@@ -1326,8 +1334,14 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
             const T mu = vdr < T(0) ? vdr : T(0);
             const T rhob_inv = fast_div(T(2), add_rn(ti.y, a2.y));
             const T gbar = mul_rn(T(0.5), add_rn(gi, gj));
-            const T vsig = fma_rn(-beta, mu, add_rn(vi.w, a1.w));
-            const T visc = mul_rn(mul_rn(mul_rn(alpha, vsig), mu), rhob_inv);
+            T al = alpha, be = beta;
+            if (sw) {
+                al = mul_rn(T(0.5), add_rn(alpha_i, sal[j]));
+                be = mul_rn(bratio, al);
+                dvs += a2.z * vdr * gi;
+            }
+            const T vsig = fma_rn(-be, mu, add_rn(vi.w, a1.w));
+            const T visc = mul_rn(mul_rn(mul_rn(al, vsig), mu), rhob_inv);
             const T S = fma_rn(visc, gbar, -pterm);
             const T wgt = mul_rn(mul_rn(mul_rn(ti.z, a2.z), S), rinv);
             ax.add(mul_rn(wgt, rx));
@@ -1335,7 +1349,7 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
             az.add(mul_rn(wgt, rz));
             if (adi)
                 du += a2.z * (ti.x * vdr * gi +
-                              rhob_inv * gbar * (T(-0.5) * alpha * vsig * mu * mu + aac * ac_speed(vdr, ti, a2, gm1_price, rhob_inv) * (ti.w - a2.w)));
+                              rhob_inv * gbar * (T(-0.5) * al * vsig * mu * mu + aac * ac_speed(vdr, ti, a2, gm1_price, rhob_inv) * (ti.w - a2.w)));
             vs = vsig > vs ? vsig : vs;
         }
         pairs += cnt;
@@ -1437,6 +1451,7 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
     Fz = group_sum<LPP>(Fz);
     du = group_sum<LPP>(du);
     vs = group_max<LPP>(vs);
+    if (sw) dvs = group_sum<LPP>(dvs);
     // a = F / m in FP64 (m a stays F to FP64 round-off), one reciprocal
     // per particle (none for equal masses); the CFL step C h / v_sig of
     // Eq. SPH_DT in the pair precision (FP32: the FP64 pipe is much
@@ -1453,6 +1468,12 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
         ps.az[i] = a[2];
         ps.du[i] = adi ? (double)du : 0.0;
         ps.vsig[i] = (double)vsig_t;
+        if (sw) {  // Morris & Monaghan: decay towards alpha_min, growth where compressed
+            const double divv = -(double)dvs / (b.somega[s] * b.srho[s]);
+            const double ai = (double)alpha_i;
+            ps.dalpha[i] = -(ai - ph.alpha_min) * ph.av_decay * (double)vi.w / b.sh[s] +
+                           (divv < 0.0 ? -divv * (ph.alpha_av - ai) : 0.0);
+        }
         dti = (T)ph.c_cfl * (T)b.sh[s] / vsig_t;
         if (!(isfinite(a[0]) && isfinite(a[1]) && isfinite(a[2]) && isfinite(du)))
             atomicOr(&ps.diag->status, ST_NONFINITE);
@@ -1490,6 +1511,12 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, FCfg<T, LPP>::MINB) k_
         const int p = b.leaf_pid[leaf];
         const ProbStatic &ps = b.prob[p];
         if (ps.lpp != LPP || ps.ph.kernel != K) continue;  // leaf of a problem served by another launch
+        if (!WRAP && (ps.ph.av_switch || ps.ph.ac_signal)) {
+            // the viscosity switch and Price's conductivity run in the wrap-list
+            // launch only, which keeps the common path's registers for the default scheme
+            if (lane == 0) b.wrap_list[atomicAdd(&b.counters[kForceWrapList], 1)] = leaf;
+            continue;
+        }
         if (ps.ph.periodic && p != last_p) {  // (consecutive leaves mostly share a problem)
             float extmax;
             problem_top_max(b, b.dyn[p], Rall, extmax);
@@ -1548,7 +1575,8 @@ cudaError_t run_forces(const BatchView &b, cudaStream_t st)
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forces<T, LPP, K, WRAP>, C::WPB * 32, C::smem);
     if (per_sm < 1) per_sm = 1;
-    int grid = dev_info().sm_count * (WRAP ? 1 : per_sm);  // (the wrap list is short)
+    // the wrap list is short unless a problem uses the viscosity switch or Price's conductivity
+    int grid = dev_info().sm_count * (WRAP && !b.any_general ? 1 : per_sm);
     k_forces<T, LPP, K, WRAP><<<grid, C::WPB * 32, C::smem, st>>>(b);
     return cudaGetLastError();
 }

@@ -215,6 +215,7 @@ int sph_server_submit(sph_server *s, const sph_request *req, uint64_t *ticket)
             if (!p) return SPH_EINVAL;
     sph_params prm = req->params;
     prm.precision = s->cfg.precision;
+    if (prm.av_switch != SPH_AV_CONSTANT) return SPH_EINVAL;  // (per-particle alpha is not kept by the server)
     if (sph_workspace_bytes(req->n, &prm) == 0) return SPH_EINVAL;
     if (footprint(prm, req->n) > s->pool.size) return SPH_ETOOBIG;
     if ((int)s->queue.size() >= s->cfg.max_queue) return SPH_EBUSY;

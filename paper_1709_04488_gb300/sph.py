@@ -19,6 +19,7 @@ EOS_ADIABATIC, EOS_ISOTHERMAL = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 KERNEL_M4, KERNEL_M6 = 0, 1
 AC_WADSLEY, AC_PRICE = 0, 1
+AV_CONSTANT, AV_MORRIS_MONAGHAN = 0, 1
 FLAG_ASYNC, FLAG_TIMING = 1, 2
 NSTAGES = 7
 STAGES = ["kick_drift", "sort", "tree", "density", "refit", "forces", "close"]
@@ -48,11 +49,14 @@ class Params(C.Structure):
         ("flags", C.c_uint),
         ("tree_rebuild_every", C.c_int),
         ("ac_signal", C.c_int),
+        ("av_switch", C.c_int),
+        ("alpha_min", C.c_double),
+        ("av_decay", C.c_double),
     ]
 
 
 STATE_FIELDS = ["x", "y", "z", "vx", "vy", "vz", "u", "m", "h",
-                "rho", "omega", "P", "c", "ax", "ay", "az", "du", "vsig"]
+                "rho", "omega", "P", "c", "ax", "ay", "az", "du", "vsig", "alpha", "dalpha"]
 
 
 class State(C.Structure):
@@ -340,6 +344,8 @@ class Problem:
                 self.t[f] = torch.as_tensor(a, dtype=torch.float64).to(self.device).contiguous()
             else:
                 self.t[f] = torch.zeros(max(n, 1), dtype=torch.float64, device=self.device)
+        if params.av_switch and arrays.get("alpha") is None:
+            self.t["alpha"].fill_(params.alpha_av)  # the switch starts from the full viscosity
         self.state = State(**{f: self.t[f].data_ptr() for f in STATE_FIELDS})
         self.ws_bytes = sph_workspace_bytes(n, params)
         if self.ws_bytes == 0:

@@ -37,17 +37,19 @@ def test_struct_layouts_match_header(S, tmp_path):
     src = tmp_path / "sizes.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "sph.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
         "sizeof(sph_params),sizeof(sph_state),sizeof(sph_diag),sizeof(sph_server_cfg),"
         "sizeof(sph_request),sizeof(sph_result),offsetof(sph_params,flags),offsetof(sph_diag,status),"
-        "offsetof(sph_params,tree_rebuild_every),offsetof(sph_params,ac_signal));return 0;}\n")
+        "offsetof(sph_params,tree_rebuild_every),offsetof(sph_params,ac_signal),offsetof(sph_params,av_decay),"
+        "offsetof(sph_state,dalpha));return 0;}\n")
     exe = tmp_path / "sizes"
     import subprocess
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     want = [C.sizeof(S.Params), C.sizeof(S.State), C.sizeof(S.Diag), C.sizeof(S.ServerCfg),
             C.sizeof(S.Request), C.sizeof(S.Result), S.Params.flags.offset, S.Diag.status.offset,
-            S.Params.tree_rebuild_every.offset, S.Params.ac_signal.offset]
+            S.Params.tree_rebuild_every.offset, S.Params.ac_signal.offset, S.Params.av_decay.offset,
+            S.State.dalpha.offset]
     assert got == want
 
 
@@ -60,7 +62,7 @@ def test_defaults_are_the_papers(S):
 def test_constants_match_header(S):
     txt = open(os.path.join(ROOT, "include", "sph.h")).read()
     defs = dict(re.findall(r"#define (SPH_[A-Z0-9_]+)\s+(-?\d+)u?\b", txt))
-    for name in ("KERNEL_M4", "KERNEL_M6", "AC_WADSLEY", "AC_PRICE", "EOS_ADIABATIC", "EOS_ISOTHERMAL", "PREC_FP64", "PREC_MIXED",
+    for name in ("KERNEL_M4", "KERNEL_M6", "AC_WADSLEY", "AC_PRICE", "AV_CONSTANT", "AV_MORRIS_MONAGHAN", "EOS_ADIABATIC", "EOS_ISOTHERMAL", "PREC_FP64", "PREC_MIXED",
                  "FLAG_ASYNC", "FLAG_TIMING"):
         assert int(defs["SPH_" + name]) == getattr(S, name), name
 
@@ -84,6 +86,12 @@ def test_workspace_bytes_and_validation(S):
     bad = S.sph_params_default()
     bad.ac_signal = 2
     assert S.sph_workspace_bytes(10, bad) == 0
+    sw = S.sph_params_default()
+    sw.av_switch = S.AV_MORRIS_MONAGHAN
+    assert sw.alpha_min == 0.1 and sw.av_decay == 0.1
+    assert S.sph_workspace_bytes(10, sw) > 0
+    sw.alpha_min = 2.0  # above alpha_av
+    assert S.sph_workspace_bytes(10, sw) == 0
     bad = S.sph_params_default()
     bad.lanes_per_particle = 3
     assert S.sph_workspace_bytes(10, bad) == 0
