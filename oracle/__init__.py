@@ -69,6 +69,8 @@ class _Params(C.Structure):
         ("av_switch", C.c_int),
         ("alpha_min", C.c_double),
         ("av_decay", C.c_double),
+        ("gravity", C.c_int),
+        ("G", C.c_double),
     ]
 
 
@@ -78,7 +80,7 @@ _IP = C.POINTER(C.c_int32)
 _FIELDS_D = ["x", "y", "z", "vx", "vy", "vz", "u", "m", "h",
              "rho", "omega", "P", "c", "ax", "ay", "az", "du", "vsig"]
 _FIELDS_I = ["nngb", "iters"]
-_FIELDS_A = ["alpha", "dalpha"]  # viscosity switch: alpha per particle and its rate
+_FIELDS_A = ["alpha", "dalpha", "zeta"]  # viscosity switch: alpha and its rate; gravity: zeta
 
 
 class _State(C.Structure):
@@ -108,6 +110,14 @@ def lib():
             fn = getattr(L, name)
             fn.restype = C.c_double
             fn.argtypes = [C.c_int, C.c_double, C.c_double]
+        for name in ("orc_gmass", "orc_gpsi"):
+            fn = getattr(L, name)
+            fn.restype = C.c_double
+            fn.argtypes = [C.c_double]
+        for name in ("orc_gforce", "orc_gpot", "orc_gdphidh"):
+            fn = getattr(L, name)
+            fn.restype = C.c_double
+            fn.argtypes = [C.c_double, C.c_double]
         PP, SP = C.POINTER(_Params), C.POINTER(_State)
         L.orc_density.restype = C.c_int
         L.orc_density.argtypes = [PP, C.c_int64, SP]
@@ -115,6 +125,8 @@ def lib():
         L.orc_forces.argtypes = [PP, C.c_int64, SP]
         L.orc_step.restype = C.c_int
         L.orc_step.argtypes = [PP, C.c_int64, SP, C.c_double]
+        L.orc_gravity_energy.restype = C.c_double
+        L.orc_gravity_energy.argtypes = [PP, C.c_int64, SP]
         L.orc_cfl_dt.restype = C.c_double
         L.orc_cfl_dt.argtypes = [PP, C.c_int64, SP]
         L.orc_neighbours.restype = C.c_int64
@@ -154,6 +166,8 @@ class Params:
     av_switch: int = 0              # 1: Morris & Monaghan viscosity switch (alpha per particle)
     alpha_min: float = 0.1          # switch: floor of alpha
     av_decay: float = 0.1           # switch: tau = h / (av_decay c)
+    gravity: int = 0                # 1: self-gravity (isolated, M4), Eq. SPHSELFGRAV
+    G: float = 1.0                  # gravitational constant
 
     def _c(self) -> _Params:
         p = _Params()
@@ -169,6 +183,7 @@ class Params:
         p.ac_signal = int(self.ac_signal)
         p.av_switch = int(self.av_switch)
         p.alpha_min, p.av_decay = self.alpha_min, self.av_decay
+        p.gravity, p.G = int(self.gravity), self.G
         return p
 
 
@@ -293,6 +308,30 @@ def kernel_g6(q):
 
 def kernel_dg6(q):
     return np.vectorize(lib().orc_dg6, otypes=[np.float64])(q)
+
+
+def grav_mass(q):
+    """Enclosed mass fraction M(q) of the M4 kernel (phi' = M / r^2)."""
+    return np.vectorize(lib().orc_gmass, otypes=[np.float64])(q)
+
+
+def grav_force(r, h):
+    """Softened gravitational force kernel phi'(r, h), Eq. GRAVFORCEKERNEL (G = 1)."""
+    return np.vectorize(lib().orc_gforce, otypes=[np.float64])(r, h)
+
+
+def grav_pot(r, h):
+    """Softened potential phi(r, h) (-> -1/r beyond 2h)."""
+    return np.vectorize(lib().orc_gpot, otypes=[np.float64])(r, h)
+
+
+def grav_dphidh(r, h):
+    return np.vectorize(lib().orc_gdphidh, otypes=[np.float64])(r, h)
+
+
+def gravity_energy(p: Params, s: State) -> float:
+    """(G/2) sum_i sum_j m_i m_j (phi(r_ij,h_i) + phi(r_ij,h_j))/2 with the state's h."""
+    return lib().orc_gravity_energy(C.byref(p._c()), s.n, C.byref(s._c()))
 
 
 def kernel_Wk(k, r, h):

@@ -66,6 +66,8 @@ typedef struct {
                                 one alpha per particle (Sec. 2.1.1) */
     double alpha_min;        /* switch: floor the viscosity decays to */
     double av_decay;         /* switch: decay time tau = h / (av_decay c) */
+    int gravity;             /* 1: self-gravity, Eq. SPHSELFGRAV (isolated, M4 kernel) */
+    double G;                /* gravitational constant */
 } orc_params;
 
 typedef struct {
@@ -76,6 +78,7 @@ typedef struct {
     double *ax, *ay, *az, *du, *vsig;
     int32_t *nngb, *iters;
     double *alpha, *dalpha;  /* switch: viscosity parameter per particle and its rate */
+    double *zeta;            /* gravity: zeta of Eq. GRADHZETA (written by the density solve) */
 } orc_state;
 
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_EBOX = -2, ORC_ENOCONV = -3, ORC_ENOMEM = -9 };
@@ -161,6 +164,39 @@ double orc_dWdhk(int k, double r, double h)
 {
     double q = r / h;
     return -(3.0 * kernel_F(k, q) + q * kernel_dF(k, q)) / (h * h * h * h);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Softened gravity of the M4 kernel (Eqs. GRAVFORCEKERNEL, GRADHZETA).      */
+/* The enclosed mass fraction of a unit-mass kernel, M(q) = 4 int_0^q f s^2 ds,*/
+/* gives phi'(r,h) = M(q)/r^2; the potential phi(r,h) = psi(q)/h with        */
+/* psi' = M/q^2 and psi = -1/q beyond q = 2; dphi/dh = -(psi + M/q)/h^2.     */
+/* (Integrals of the cubic spline, written out piecewise.)                   */
+/* ------------------------------------------------------------------------ */
+double orc_gmass(double q)
+{
+    if (q >= 2.0) return 1.0;
+    double q3 = q * q * q;
+    if (q < 1.0) return 4.0 * (q3 / 3.0 - 0.3 * q3 * q * q + 0.125 * q3 * q3);
+    return 4.0 * (2.0 * q3 / 3.0 - 0.75 * q3 * q + 0.3 * q3 * q * q - q3 * q3 / 24.0 - 1.0 / 60.0);
+}
+
+double orc_gpsi(double q)
+{
+    if (q >= 2.0) return -1.0 / q;
+    double q2 = q * q;
+    if (q < 1.0) return 2.0 * q2 / 3.0 - 0.3 * q2 * q2 + 0.1 * q2 * q2 * q - 1.4;
+    return 4.0 * q2 / 3.0 - q2 * q + 0.3 * q2 * q2 - q2 * q2 * q / 30.0 + 1.0 / (15.0 * q) - 1.6;
+}
+
+/* phi'(r,h), phi(r,h) and dphi/dh at fixed r (G = 1) */
+double orc_gforce(double r, double h) { return orc_gmass(r / h) / (r * r); }
+double orc_gpot(double r, double h) { return orc_gpsi(r / h) / h; }
+double orc_gdphidh(double r, double h)
+{
+    double q = r / h;
+    double mq = q > 0 ? orc_gmass(q) / q : 0.0; /* M(q)/q -> 0 as q -> 0 */
+    return -(orc_gpsi(q) + mq) / (h * h);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -386,6 +422,8 @@ static int params_ok(const orc_params *p, int64_t n)
     if (p->av_switch != 0 && p->av_switch != 1) return 0;
     if (p->av_switch && !(p->alpha_av > 0 && p->alpha_min >= 0 && p->alpha_min <= p->alpha_av && p->av_decay > 0))
         return 0;
+    if (p->gravity != 0 && p->gravity != 1) return 0;
+    if (p->gravity && (p->periodic || p->kernel != 0 || !(p->G > 0))) return 0;
     return 1;
 }
 
@@ -544,9 +582,53 @@ static void eos(const orc_params *p, double rho, double u, double *P, double *c)
  * h is read as the starting guess (<= 0: a default guess) and overwritten.
  * Returns ORC_ENOCONV if any particle failed to converge.
  */
+/* zeta_i of Eq. GRADHZETA: (dh/drho) sum_j m_j dphi/dh (r_ij, h_i) over the
+   gather list at the final h (self included), dh/drho = -h/(3 rho). */
+static double gravity_zeta(const orc_params *p, const orc_state *s, int64_t i, const idlist_t *buf, double rho)
+{
+    kahan_t z = {0, 0};
+    for (int64_t k = 0; k < buf->n; ++k) {
+        int64_t j = buf->v[k];
+        sep_t sp = separation(p, s, i, j);
+        kadd(&z, s->m[j] * orc_gdphidh(sqrt(sp.r2), s->h[i]));
+    }
+    return -s->h[i] / (3.0 * rho) * z.s;
+}
+
+/* Long-range part of Eq. SPHSELFGRAV for particle i: -G sum_{j != i} m_j
+   (phi'(r_ij,h_i) + phi'(r_ij,h_j))/2 r_hat_ij, by direct summation over
+   every particle (isolated problems). */
+static void gravity_direct(const orc_params *p, const orc_state *s, int64_t n, int64_t i, kahan_t *ax, kahan_t *ay,
+                           kahan_t *az)
+{
+    for (int64_t j = 0; j < n; ++j) {
+        if (j == i) continue;
+        sep_t sp = separation(p, s, i, j);
+        double r = sqrt(sp.r2);
+        double f = -p->G * s->m[j] * 0.5 * (orc_gforce(r, s->h[i]) + orc_gforce(r, s->h[j])) / r;
+        kadd(ax, f * sp.dx);
+        kadd(ay, f * sp.dy);
+        kadd(az, f * sp.dz);
+    }
+}
+
+/* Gravitational potential energy (G/2) sum_i sum_j m_i m_j (phi(r_ij,h_i) +
+   phi(r_ij,h_j))/2, self terms included, with the current h. */
+double orc_gravity_energy(const orc_params *p, int64_t n, const orc_state *s)
+{
+    kahan_t e = {0, 0};
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) {
+            double r = i == j ? 0.0 : sqrt(separation(p, s, i, j).r2);
+            kadd(&e, s->m[i] * s->m[j] * 0.5 * (orc_gpot(r, s->h[i]) + orc_gpot(r, s->h[j])));
+        }
+    return 0.5 * p->G * e.s;
+}
+
 int orc_density(const orc_params *p, int64_t n, orc_state *s)
 {
     if (!params_ok(p, n)) return ORC_EINVAL;
+    if (p->gravity && !s->zeta) return ORC_EINVAL;
     if (n == 0) return ORC_OK;
     grid_t g;
     memset(&g, 0, sizeof g);
@@ -567,6 +649,7 @@ int orc_density(const orc_params *p, int64_t n, orc_state *s)
             s->rho[i] = rho;
             /* Omega = 1 - (dh/drho) sum m dW/dh with dh/drho = -h/(3 rho) */
             s->omega[i] = 1.0 + s->h[i] / (3.0 * rho) * drho;
+            if (p->gravity) s->zeta[i] = gravity_zeta(p, s, i, &buf, rho);
             eos(p, rho, s->u[i], &s->P[i], &s->c[i]);
             if (s->nngb) s->nngb[i] = nn;
             if (s->iters) s->iters[i] = it;
@@ -623,6 +706,7 @@ static double ac_signal_speed(const orc_params *p, const orc_state *s, int64_t i
 int orc_forces(const orc_params *p, int64_t n, orc_state *s)
 {
     if (p && p->av_switch && (!s->alpha || !s->dalpha)) return ORC_EINVAL;
+    if (p && p->gravity && !s->zeta) return ORC_EINVAL;
     if (!params_ok(p, n)) return ORC_EINVAL;
     if (n == 0) return ORC_OK;
     double hmax = 0;
@@ -663,6 +747,8 @@ int orc_forces(const orc_params *p, int64_t n, orc_state *s)
                 double mj = s->m[j];
                 /* pressure term, Eq. GRADHMOMEQN */
                 double fp = -mj * (Ai * gi + Aj * gj);
+                if (p->gravity) /* zeta term of Eq. SPHSELFGRAV */
+                    fp -= 0.5 * p->G * mj * (s->zeta[i] / s->omega[i] * gi + s->zeta[j] / s->omega[j] * gj);
                 double vxij = s->vx[i] - s->vx[j], vyij = s->vy[i] - s->vy[j], vzij = s->vz[i] - s->vz[j];
                 double vdr = vxij * rx + vyij * ry + vzij * rz; /* v_ij . r_hat_ij */
                 double gbar = 0.5 * (gi + gj);                   /* r_hat . mean grad W */
@@ -689,6 +775,7 @@ int orc_forces(const orc_params *p, int64_t n, orc_state *s)
                     kadd(&du, dui + duav + duac);
                 }
             }
+            if (p->gravity) gravity_direct(p, s, n, i, &ax, &ay, &az);
             s->ax[i] = ax.s;
             s->ay[i] = ay.s;
             s->az[i] = az.s;
@@ -857,6 +944,7 @@ int orc_density_subset(const orc_params *p, int64_t n, orc_state *s, int64_t nsu
             int rc = solve_h(p, s, n, &g, i, &buf, &s->h[i], &rho, &drho, &nn, &it);
             s->rho[i] = rho;
             s->omega[i] = 1.0 + s->h[i] / (3.0 * rho) * drho;
+            if (p->gravity) s->zeta[i] = gravity_zeta(p, s, i, &buf, rho);
             eos(p, rho, s->u[i], &s->P[i], &s->c[i]);
             if (s->nngb) s->nngb[i] = nn;
             if (s->iters) s->iters[i] = it;
@@ -916,6 +1004,8 @@ int orc_forces_subset(const orc_params *p, int64_t n, orc_state *s, int64_t nsub
                 double Aj = s->P[j] / (s->omega[j] * s->rho[j] * s->rho[j]);
                 double mj = s->m[j];
                 double fp = -mj * (Ai * gi + Aj * gj);
+                if (p->gravity) /* zeta term of Eq. SPHSELFGRAV */
+                    fp -= 0.5 * p->G * mj * (s->zeta[i] / s->omega[i] * gi + s->zeta[j] / s->omega[j] * gj);
                 double vxij = s->vx[i] - s->vx[j], vyij = s->vy[i] - s->vy[j], vzij = s->vz[i] - s->vz[j];
                 double vdr = vxij * rx + vyij * ry + vzij * rz;
                 double gbar = 0.5 * (gi + gj);
@@ -942,6 +1032,7 @@ int orc_forces_subset(const orc_params *p, int64_t n, orc_state *s, int64_t nsub
                     kadd(&du, dui + duav + duac);
                 }
             }
+            if (p->gravity) gravity_direct(p, s, n, i, &ax, &ay, &az);
             s->ax[i] = ax.s;
             s->ay[i] = ay.s;
             s->az[i] = az.s;
