@@ -130,6 +130,13 @@ typedef struct {
                               state.alpha, state.dalpha; not accepted by the server.  */
     double alpha_min;      /* switch: floor alpha decays to (default 0.1)               */
     double av_decay;       /* switch: decay rate in units of c/h (default 0.1)          */
+    int gravity;           /* 1: self-gravity, Eq. SPHSELFGRAV (Sec. 2.1.2): the kernel-
+                              softened attraction -G sum_j m_j (phi'(r,h_i)+phi'(r,h_j))/2
+                              r_hat over every particle of the problem (direct summation,
+                              O(n^2)) plus the zeta term of Eq. GRADHZETA over the
+                              neighbours.  Isolated problems and the M4 kernel only
+                              (SPH_EINVAL otherwise).                                    */
+    double G;              /* gravitational constant (gravity; must be > 0)            */
 } sph_params;
 
 /* Caller-owned device arrays, FP64, length n, caller's particle order.

@@ -68,6 +68,7 @@ void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precis
     void **st[] = {&b.pm, &b.ph, &b.vc, &b.th};
     for (void **p : st) *p = c.take<char>(v4 * n);
     b.sal = c.take<char>(v4 / 4 * n);
+    b.szg = c.take<char>(v4 / 4 * n);
     b.flag = c.take<unsigned>(n);
     const long long ml = leaves_upper_bound(n);
     b.max_leaves = (int)ml;
@@ -200,6 +201,9 @@ int validate(const sph_params *p)
     if (p->av_switch == SPH_AV_MORRIS_MONAGHAN &&
         !(p->alpha_av > 0 && p->alpha_min >= 0 && p->alpha_min <= p->alpha_av && p->av_decay > 0))
         return fail(SPH_EINVAL, "viscosity switch needs alpha_av > 0, 0 <= alpha_min <= alpha_av, av_decay > 0");
+    if (p->gravity != 0 && p->gravity != 1) return fail(SPH_EINVAL, "gravity must be 0 or 1");
+    if (p->gravity && (p->periodic || p->kernel != SPH_KERNEL_M4 || !(p->G > 0)))
+        return fail(SPH_EINVAL, "self-gravity needs an isolated problem, the M4 kernel and G > 0");
     if (p->ac_signal != SPH_AC_WADSLEY && p->ac_signal != SPH_AC_PRICE)
         return fail(SPH_EINVAL, "ac_signal %d not supported (0 = Wadsley, 1 = Price)", p->ac_signal);
     if (p->kernel != SPH_KERNEL_M4 && p->kernel != SPH_KERNEL_M6)
@@ -255,6 +259,8 @@ PhysParams phys_of(const sph_params *p)
     ph.alpha_min = p->alpha_min;
     ph.av_decay = p->av_decay;
     ph.beta_ratio = p->alpha_av > 0 ? p->beta_av / p->alpha_av : 0.0;
+    ph.gravity = p->gravity;
+    ph.G = p->G;
     ph.kr = p->kernel == SPH_KERNEL_M6 ? 3.0 : 2.0;
     ph.kr_f = (float)ph.kr;
     return ph;
@@ -395,7 +401,9 @@ int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *st
     c->bv.lpp_mask = mask_of(c->lpp, p->kernel);
     c->bv.any_isolated = p->periodic ? 0 : 1;
     c->bv.any_periodic = p->periodic ? 1 : 0;
-    c->bv.any_general = (p->av_switch || p->ac_signal) ? 1 : 0;
+    c->bv.any_general = (p->av_switch || p->ac_signal || p->gravity) ? 1 : 0;
+    c->bv.any_gravity = p->gravity ? 1 : 0;
+    c->bv.grav_blocks = p->gravity ? gravity_blocks(n) : 0;
     ProbStatic &ps = c->host_ps;
     memset(&ps, 0, sizeof ps);
     ps.x = state->x;
@@ -816,7 +824,8 @@ int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, 
     long long ntot = 0;
     std::vector<ProbStatic> tab(nctx);
     std::vector<long long> bases(nctx + 1);
-    int mask = 0, dmask = 0, b_any_isolated = 0, b_any_periodic = 0, b_any_general = 0;
+    int mask = 0, dmask = 0, b_any_isolated = 0, b_any_periodic = 0, b_any_general = 0, b_any_gravity = 0;
+    long long grav_blocks = 0;
     for (int k = 0; k < nctx; ++k) {
         tab[k] = ctxs[k]->host_ps;
         tab[k].base = ntot;
@@ -826,7 +835,10 @@ int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, 
         dmask |= dens_class_bit(tab[k].lpp, tab[k].uniform_m, tab[k].ph.kernel);
         if (!tab[k].ph.periodic) b_any_isolated = 1;
         else b_any_periodic = 1;
-        if (tab[k].ph.av_switch || tab[k].ph.ac_signal) b_any_general = 1;
+        if (tab[k].ph.av_switch || tab[k].ph.ac_signal || tab[k].ph.gravity) b_any_general = 1;
+        if (tab[k].ph.gravity) b_any_gravity = 1;
+        tab[k].gblk0 = (int)grav_blocks;
+        if (tab[k].ph.gravity) grav_blocks += gravity_blocks(ctxs[k]->n);
     }
     bases[nctx] = ntot;
     Carver cv{(char *)workspace};
@@ -842,6 +854,8 @@ int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, 
     b.any_isolated = b_any_isolated;
     b.any_periodic = b_any_periodic;
     b.any_general = b_any_general;
+    b.any_gravity = b_any_gravity;
+    b.grav_blocks = grav_blocks;
     CU(cudaMemcpyAsync(b.prob, tab.data(), sizeof(ProbStatic) * nctx, cudaMemcpyHostToDevice, st));
     CU(cudaMemcpyAsync(b.prob_base, bases.data(), sizeof(long long) * (nctx + 1), cudaMemcpyHostToDevice, st));
     CU(cudaMemsetAsync(b.dyn, 0, sizeof(ProbDyn) * nctx, st));

@@ -65,6 +65,9 @@ struct PhysParams {
     int ac_signal;       // SPH_AC_WADSLEY or SPH_AC_PRICE
     int av_switch;       // SPH_AV_CONSTANT or SPH_AV_MORRIS_MONAGHAN
     double alpha_min, av_decay, beta_ratio;  // switch: floor, decay rate (c/h), beta_av / alpha_av
+    int gravity;         // self-gravity (isolated, M4)
+    int pad3_;
+    double G;
 };
 
 // Per-problem diagnostics and persistent scalars; lives in the context's own
@@ -100,6 +103,8 @@ struct ProbStatic {
     ProbDiag *diag;
     int lpp;         // lanes per particle in the pair kernels (leaf size = 32 / lpp)
     int uniform_m;   // all masses equal (m_uniform): neighbour lists keep distances only
+    int gblk0;       // gravity: the problem's first block of the direct-sum launch
+    int pad4_;
     double m_uniform;
     double inv_m_uniform;  // 1 / m_uniform (0 unless uniform_m)
     PhysParams ph;
@@ -154,8 +159,10 @@ struct BatchView {
     int key_lo;                  // lowest key bit that is sorted (the bits below are cleared)
     int any_isolated;            // some problem is isolated (needs a bounding box)
     int any_periodic;            // some problem is periodic (wrap-list launches)
-    int any_general;             // some problem uses the viscosity switch or Price's conductivity
-                                 // (served by the wrap-list force launches)
+    int any_general;             // some problem uses the viscosity switch, Price's conductivity or
+                                 // gravity (served by the wrap-list launches)
+    int any_gravity;             // some problem has self-gravity (direct-sum launch)
+    long long grav_blocks;       // blocks of the direct-sum launch (all gravity problems)
     ProbStatic *prob;            // [nprob]
     ProbDyn *dyn;                // [nprob]
     long long *prob_base;        // [nprob + 1] base offsets (for searches)
@@ -176,6 +183,7 @@ struct BatchView {
     void *vc;   // (v xyz, c)
     void *th;   // (P/(Omega rho^2), rho, m, u)
     void *sal;  // alpha of the viscosity switch (T per particle)
+    void *szg;  // gravity: G zeta / (2 Omega) (T per particle), the zeta term's weight
     // leaves
     unsigned *flag;              // [ntot] leaf start flags, then leaf index (scan)
     int *leaf_start;             // [max_leaves + 1]
@@ -287,6 +295,8 @@ cudaError_t launch_update_leaves(const BatchView &b, int precision, cudaStream_t
 cudaError_t launch_refit(const BatchView &b, int precision, cudaStream_t st);
 cudaError_t launch_density(const BatchView &b, int precision, int use_pred, cudaStream_t st);
 cudaError_t launch_forces(const BatchView &b, int precision, cudaStream_t st);
+void launch_gravity(const BatchView &b, int precision, cudaStream_t st);  // direct-sum self-gravity
+long long gravity_blocks(long long n);
 cudaError_t launch_kick_drift(const BatchView &b, double dt_host, cudaStream_t st);  // also selects dt, resets diagnostics
 cudaError_t launch_kick_close(const BatchView &b, int do_kick, int forces_ran, cudaStream_t st);
 cudaError_t launch_reset_step(const BatchView &b, int mode, cudaStream_t st);  // mode 1 full, 2 forces only

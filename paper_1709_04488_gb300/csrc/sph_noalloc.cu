@@ -100,7 +100,9 @@ extern "C" int sph_density_forces_noalloc(const sph_params *p, int64_t n, const 
     b.dens_mask = dens_class_bit(lpp, 0, p->kernel);  // masses are not inspected here: distance-and-mass lists
     b.any_isolated = p->periodic ? 0 : 1;
     b.any_periodic = p->periodic ? 1 : 0;
-    b.any_general = (p->av_switch || p->ac_signal) ? 1 : 0;
+    b.any_general = (p->av_switch || p->ac_signal || p->gravity) ? 1 : 0;
+    b.any_gravity = p->gravity ? 1 : 0;
+    b.grav_blocks = p->gravity ? gravity_blocks(n) : 0;
     ProbStatic ps;
     memset(&ps, 0, sizeof ps);
     ps.x = state->x;

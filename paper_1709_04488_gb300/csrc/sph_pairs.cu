@@ -24,8 +24,8 @@ cudaError_t launch_density(const BatchView &b, int precision, int use_pred, cuda
     if (b.ntot == 0) return cudaSuccess;
     cudaError_t e = density_launches_m4(b, precision, use_pred, st);
     if (e == cudaSuccess) e = density_launches_m6(b, precision, use_pred, st);
-    if (e == cudaSuccess && b.any_periodic) e = density_launches_m4_wrap(b, precision, use_pred, st);
-    if (e == cudaSuccess && b.any_periodic) e = density_launches_m6_wrap(b, precision, use_pred, st);
+    if (e == cudaSuccess && (b.any_periodic || b.any_gravity)) e = density_launches_m4_wrap(b, precision, use_pred, st);
+    if (e == cudaSuccess && (b.any_periodic || b.any_gravity)) e = density_launches_m6_wrap(b, precision, use_pred, st);
     if (e != cudaSuccess) return e;
     if (precision == SPH_PREC_FP64) run_density_fallback<double>(b, use_pred, st);
     else run_density_fallback<float>(b, use_pred, st);
@@ -40,6 +40,7 @@ cudaError_t launch_forces(const BatchView &b, int precision, cudaStream_t st)
     if (e == cudaSuccess && (b.any_periodic || b.any_general)) e = force_launches_m4_wrap(b, precision, st);
     if (e == cudaSuccess && (b.any_periodic || b.any_general)) e = force_launches_m6_wrap(b, precision, st);
     if (e != cudaSuccess) return e;
+    launch_gravity(b, precision, st);  // adds the long-range attraction to a
     return cudaGetLastError();
 }
 

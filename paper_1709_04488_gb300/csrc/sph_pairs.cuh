@@ -111,6 +111,30 @@ __device__ __forceinline__ double kern_sigma(int k)
     return k == SPH_KERNEL_M6 ? Kern<SPH_KERNEL_M6>::sigma : Kern<SPH_KERNEL_M4>::sigma;
 }
 
+// Softened gravity of the M4 kernel (Eqs. GRAVFORCEKERNEL, GRADHZETA): the
+// enclosed mass fraction M(q) = 4 int_0^q f s^2 ds of a unit-mass kernel
+// (phi' = M / r^2) and the potential shape psi (phi = psi(q)/h, psi' = M/q^2,
+// -1/q from q = 2 on).  zeta needs psi + M/q (= -h^2 dphi/dh), which vanishes
+// from q = 2 on and is psi(0) = -7/5 at q = 0.
+template <typename T>
+__device__ __forceinline__ T grav_mass(T q)
+{
+    const T q3 = q * q * q;
+    if (q >= T(2)) return T(1);
+    if (q < T(1)) return T(4) * q3 * (T(1.0 / 3.0) + q * q * (T(-0.3) + T(0.125) * q));
+    return T(4) * (q3 * (T(2.0 / 3.0) + q * (T(-0.75) + q * (T(0.3) - q * T(1.0 / 24.0)))) - T(1.0 / 60.0));
+}
+template <typename T>
+__device__ __forceinline__ T grav_psi_plus_mq(T q)
+{
+    if (q >= T(2)) return T(0);
+    const T q2 = q * q;
+    T psi;
+    if (q < T(1)) psi = q2 * (T(2.0 / 3.0) + q2 * (T(-0.3) + T(0.1) * q)) - T(1.4);
+    else psi = q2 * (T(4.0 / 3.0) + q * (T(-1) + q * (T(0.3) - q * T(1.0 / 30.0)))) + T(1.0 / 15.0) / q - T(1.6);
+    return psi + (q > T(0) ? grav_mass(q) / q : T(0));
+}
+
 template <typename T>
 __device__ __forceinline__ T rsqrt_t(T x);
 template <>
@@ -583,7 +607,7 @@ struct DCfg {
 template <typename T>
 __device__ __forceinline__ void density_epilogue(const BatchView &b, const ProbStatic &ps, long long s,
                                                  typename Vec4<T>::type pi, T h, T S0, T S1, int use_pred,
-                                                 T sigma)
+                                                 T sigma, T Z = T(0))
 {
     using V = typename Vec4<T>::type;
     const PhysParams &ph = ps.ph;
@@ -634,6 +658,9 @@ __device__ __forceinline__ void density_epilogue(const BatchView &b, const ProbS
     q.w = (T)u;
     ((V *)b.th)[s] = q;
     if (ph.av_switch) ((T *)b.sal)[s] = (T)(use_pred ? b.ap[g] : ps.alpha[i]);  // viscosity switch
+    // gravity: zeta = dh/drho sum_j m_j dphi/dh = Z / (3 rho h) (Z = sum_j m_j (psi + M/q)),
+    // kept as the weight G zeta / (2 Omega) of the force pass's zeta term
+    if (ph.gravity) ((T *)b.szg)[s] = (T)(0.5 * ph.G) * Z / (T(3) * rho * h * omega);
     if (!(isfinite((double)rho) && isfinite((double)omega) && isfinite((double)P)))
         atomicOr(&ps.diag->status, ST_NONFINITE);
 }
@@ -917,8 +944,17 @@ __device__ __forceinline__ bool density_leaf(const BatchView &b, int leaf, unsig
             if (sub == 0) pairs += rn;
         }
     }
+    T Z = T(0);  // gravity (wrap-list launch): sum_j m_j (psi + M/q) at the final h
+    if (WRAP && ph.gravity) {
+        if (fin) {
+            const T hinv = T(1) / h;
+            for (int e = 0; e < cnt; ++e)
+                Z += (UM ? mu_all : lm[e * 32 + lane]) * grav_psi_plus_mq(lr[e * 32 + lane] * hinv);
+        }
+        Z = group_sum<LPP>(Z);
+    }
     if (fin && sub == 0) {
-        density_epilogue<T>(b, ps, s, pi, h, S0, S1, use_pred, sigma);
+        density_epilogue<T>(b, ps, s, pi, h, S0, S1, use_pred, sigma, Z);
         if (noconv) {
             atomicOr(&ps.diag->status, ST_NOCONV);
             atomicAdd(&ps.diag->unconverged, 1);
@@ -976,6 +1012,10 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM, K>::WPB * 32, DCfg<T, LPP, UM
         if (WRAP) leaf = b.wrap_list[leaf];
         const ProbStatic &ps = b.prob[b.leaf_pid[leaf]];
         if (ps.lpp != LPP || (ps.uniform_m != 0) != UM || ps.ph.kernel != K) continue;  // another launch's
+        if (!WRAP && ps.ph.gravity) {  // gravity's zeta runs in the wrap-list launch only
+            if (lane == 0) b.wrap_list[atomicAdd(&b.counters[kDensWrapList], 1)] = leaf;
+            continue;
+        }
         if (!density_leaf<T, LPP, UM, K, WRAP>(b, leaf, mine, use_pred) && lane == 0) {
             b.wrap_list[atomicAdd(&b.counters[kDensWrapList], 1)] = leaf;
             atomicAdd(&ps.diag->wrap_leaves, 1);
@@ -1092,9 +1132,11 @@ __global__ void __launch_bounds__(FbCfg<T>::WPB * 32) k_density_fallback(BatchVi
             direct = __any_sync(FULL, ovf);
             __syncwarp();
         };
+        T Z = T(0);  // gravity: sum_j m_j (psi + M/q)
         auto sums = [&](T hh) {
             S0 = T(0);
             S1 = T(0);
+            Z = T(0);
             nn = 0;
             const T hinv = T(1) / hh;
             if (!direct) {
@@ -1104,6 +1146,7 @@ __global__ void __launch_bounds__(FbCfg<T>::WPB * 32) k_density_fallback(BatchVi
                     T mj = fm[e * 32 + lane];
                     S0 += mj * f;
                     S1 += mj * qq * df;
+                    if (ph.gravity) Z += mj * grav_psi_plus_mq(qq);
                     nn += qq < KR;
                 }
             } else {
@@ -1114,12 +1157,14 @@ __global__ void __launch_bounds__(FbCfg<T>::WPB * 32) k_density_fallback(BatchVi
                         kern_fdf(kk, qq, f, df);
                         S0 += mj * f;
                         S1 += mj * qq * df;
+                        if (ph.gravity) Z += mj * grav_psi_plus_mq(qq);
                         ++nn;
                     }
                 });
             }
             S0 = warp_sum(S0);
             S1 = warp_sum(S1);
+            Z = warp_sum(Z);
             nn = warp_sum(nn);
         };
         build();
@@ -1149,7 +1194,7 @@ __global__ void __launch_bounds__(FbCfg<T>::WPB * 32) k_density_fallback(BatchVi
         if (lane == 0) {
             const float hf = to_float_ru(h);
             if (hf > b.hf[s] || hf > b.leaf_hcap[leaf]) atomicOr(&b.dyn[p].lists_stale, 1);
-            density_epilogue<T>(b, ps, s, pi, h, S0, S1, use_pred, sigma);
+            density_epilogue<T>(b, ps, s, pi, h, S0, S1, use_pred, sigma, Z);
             if (noconv) {
                 atomicOr(&ps.diag->status, ST_NOCONV);
                 atomicAdd(&ps.diag->unconverged, 1);
@@ -1280,6 +1325,11 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
     const T* __restrict__ sal = (const T *)b.sal;
     const T alpha_i = sw ? sal[s] : alpha, bratio = (T)ph.beta_ratio;
     T dvs = T(0);  // sum_j m_j v_ij . grad_i W(h_i) (switch: div v)
+    // gravity (wrap-list launch): the zeta term of Eq. SPHSELFGRAV has the pressure
+    // term's form, with P/(Omega rho^2) + G zeta/(2 Omega) per particle
+    const bool grav = WRAP && ph.gravity != 0;
+    const T* __restrict__ szg = (const T *)b.szg;
+    const T Ai_g = grav ? add_rn(ti.x, szg[s]) : ti.x;
     TwoSumAcc<T> ax{T(0), T(0)}, ay{T(0), T(0)}, az{T(0), T(0)};
     T du = T(0), vs = T(-1);
     int pairs = 0, tested = 0;
@@ -1328,7 +1378,7 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
             const T hj2 = mul_rn(a0.w, a0.w);
             const T gi = mul_rn(mul_rn(sigma, KF::df(qi)), hi4);
             const T gj = mul_rn(mul_rn(sigma, KF::df(qj)), mul_rn(hj2, hj2));
-            const T pterm = add_rn(mul_rn(ti.x, gi), mul_rn(a2.x, gj));
+            const T pterm = add_rn(mul_rn(Ai_g, gi), mul_rn(grav ? add_rn(a2.x, szg[j]) : a2.x, gj));
             const T vx = sub_rn(vi.x, a1.x), vy = sub_rn(vi.y, a1.y), vz = sub_rn(vi.z, a1.z);
             const T vdr = mul_rn(fma_rn(vz, rz, fma_rn(vy, ry, mul_rn(vx, rx))), rinv);
             const T mu = vdr < T(0) ? vdr : T(0);
@@ -1511,9 +1561,9 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, FCfg<T, LPP>::MINB) k_
         const int p = b.leaf_pid[leaf];
         const ProbStatic &ps = b.prob[p];
         if (ps.lpp != LPP || ps.ph.kernel != K) continue;  // leaf of a problem served by another launch
-        if (!WRAP && (ps.ph.av_switch || ps.ph.ac_signal)) {
-            // the viscosity switch and Price's conductivity run in the wrap-list
-            // launch only, which keeps the common path's registers for the default scheme
+        if (!WRAP && (ps.ph.av_switch || ps.ph.ac_signal || ps.ph.gravity)) {
+            // the viscosity switch, Price's conductivity and gravity's zeta term run in the
+            // wrap-list launch only, which keeps the common path's registers for the default scheme
             if (lane == 0) b.wrap_list[atomicAdd(&b.counters[kForceWrapList], 1)] = leaf;
             continue;
         }
@@ -1546,8 +1596,9 @@ cudaError_t run_density(const BatchView &b, int use_pred, cudaStream_t st)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_density<T, LPP, UM, K, WRAP>, C::WPB * 32, C::smem);
         if (per_sm < 1) per_sm = 1;
     }
-    // the wrap-list launch serves few leaves (mostly none): one block per SM
-    k_density<T, LPP, UM, K, WRAP><<<dev_info().sm_count * (WRAP ? 1 : per_sm), C::WPB * 32, C::smem, st>>>(b, use_pred);
+    // the wrap-list launch serves few leaves (mostly none) unless a problem has gravity
+    k_density<T, LPP, UM, K, WRAP><<<dev_info().sm_count * (WRAP && !b.any_gravity ? 1 : per_sm), C::WPB * 32, C::smem,
+                                     st>>>(b, use_pred);
     return cudaGetLastError();
 }
 

@@ -52,6 +52,8 @@ class Params(C.Structure):
         ("av_switch", C.c_int),
         ("alpha_min", C.c_double),
         ("av_decay", C.c_double),
+        ("gravity", C.c_int),
+        ("G", C.c_double),
     ]
 
 
