@@ -38,6 +38,8 @@ WORKLOAD = WORKLOADS["sod"]
 # algorithmic flops per in-range pair, counted from the kernels' source
 FLOPS_DENSITY_PAIR = 19   # per pair per Newton-Raphson pass (q, f, f', two accumulations)
 FLOPS_FORCE_PAIR = 101    # per ordered pair (pressure, viscosity, conduction, energy, TwoSum-compensated m a)
+FLOPS_GRAVITY_PAIR = 38   # per ordered pair beyond the softening (r, 1/r^3 weight, TwoSum-compensated F)
+GRAVITY_N = 65536         # self-gravity measurement: isolated cloud of this many particles
 
 
 def parse():
@@ -50,6 +52,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-reuse", action="store_true", help="skip the tree-reuse measurement")
     ap.add_argument("--no-m6", action="store_true", help="skip the M6 quintic-kernel measurement")
+    ap.add_argument("--no-gravity", action="store_true", help="skip the self-gravity measurement")
     ap.add_argument("--lpp", type=int, default=0, help="lanes per particle (0: autotuned)")
     ap.add_argument("--workload", default="sod", choices=sorted(WORKLOADS),
                     help="sod (the default measured configuration), sedov or cloud")
@@ -421,6 +424,29 @@ def run_ours(args):
               "relative_to_m4": v6 / (value / world)}
         p6.close()
 
+    # self-gravity (Sec. 2.1.2) on an isolated cloud: the direct-sum kernel
+    # is a dense pair loop, timed as its own stage
+    grav = None
+    if not args.no_gravity:
+        from paper_1709_04488_gb300 import ics
+        ag, pg = ics.cloud(GRAVITY_N, seed=4)
+        prmg = S.make_params(S.PREC_MIXED, **pg, flags=S.FLAG_ASYNC | S.FLAG_TIMING, gravity=1, G=1.0)
+        with torch.cuda.stream(stream):
+            pgr = S.Problem(ag, prmg, device=dev, stream=stream)
+            S.check(S.sph_density_h(pgr.ctx), "sph_density_h")
+            S.check(S.sph_forces(pgr.ctx), "sph_forces")
+        S.check(S.sph_run(pgr.ctx, 3), "sph_run")
+        msg, stg, _, _ = time_steps(S, pgr, stream, torch, 5, flush, stage=True)
+        gst = np.mean(np.array(stg), axis=0)
+        g_ms = float(gst[S.STAGES.index("gravity")])
+        gflop = GRAVITY_N * (GRAVITY_N - 1) * FLOPS_GRAVITY_PAIR
+        g_ach = gflop / (g_ms * 1e-3) / 1e12
+        grav = {"workload": f"cloud_{GRAVITY_N}: isolated, isothermal, G=1, direct summation",
+                "ms_per_step": float(np.mean(msg)), "value": GRAVITY_N * len(msg) / (np.sum(msg) * 1e-3),
+                "unit": UNIT, "k_gravity": {"ms": g_ms, "flop": float(gflop), "achieved": g_ach,
+                                            "frac": g_ach / peak, "unit": "TFLOP/s"}}
+        pgr.close()
+
     diag = prob.diagnostics()
     prob.close()
     serve_res = None
@@ -445,7 +471,7 @@ def run_ours(args):
                    "l2": "flushed (256 MiB write) between timed steps", "graph": "one CUDA graph per step",
                    "lanes_per_particle": int(prob.params.lanes_per_particle) or "auto"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": kernels_per_step * args.steps,
-        "clocks": clocks, "fp64_gpu": fp64, "tree_reuse": reuse, "m6_kernel": m6, "serving": serve_res,
+        "clocks": clocks, "fp64_gpu": fp64, "tree_reuse": reuse, "m6_kernel": m6, "gravity": grav, "serving": serve_res,
         "step_diag": {"nr_iterations": diag.nr_iterations, "nr_max": diag.nr_max, "fallback": diag.fallback,
                       "leaves": diag.leaves, "ngb_mean": diag.ngb_mean, "candidates": diag.candidates,
                       "wrap_leaves": diag.wrap_leaves},

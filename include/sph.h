@@ -84,8 +84,9 @@ extern "C" {
 #define SPH_STAGE_DENSITY 3      /* density / h solve (incl. the slow path)      */
 #define SPH_STAGE_REFIT 4        /* smoothing-sphere boxes                       */
 #define SPH_STAGE_FORCES 5       /* accelerations, du/dt, signal speeds          */
-#define SPH_STAGE_CLOSE 6        /* closing half kick, reductions, CFL step      */
-#define SPH_NSTAGES 7
+#define SPH_STAGE_GRAVITY 6      /* direct-sum self-gravity (problems with gravity) */
+#define SPH_STAGE_CLOSE 7        /* closing half kick, reductions, CFL step      */
+#define SPH_NSTAGES 8
 
 typedef struct {
     int periodic;          /* 1: periodic box [box_lo, box_lo + box_len) per axis; 0: isolated */

@@ -50,7 +50,7 @@ DevInfo dev_info()
 
 // ---- workspace layout -------------------------------------------------------
 // Carve the per-step scratch arrays for `ntot` particles over `nprob` problems.
-void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precision)
+void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precision, int grav_chunks)
 {
     const long long n = ntot > 0 ? ntot : 1;
     const size_t v4 = precision == SPH_PREC_FP64 ? sizeof(dbl4) : sizeof(float4);
@@ -69,6 +69,7 @@ void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precis
     for (void **p : st) *p = c.take<char>(v4 * n);
     b.sal = c.take<char>(v4 / 4 * n);
     b.szg = c.take<char>(v4 / 4 * n);
+    b.gpart = grav_chunks > 1 ? c.take<double>(3LL * grav_chunks * n) : nullptr;
     b.flag = c.take<unsigned>(n);
     const long long ml = leaves_upper_bound(n);
     b.max_leaves = (int)ml;
@@ -342,7 +343,7 @@ size_t sph_workspace_bytes(int64_t n, const sph_params *p)
     BatchView b;
     memset(&b, 0, sizeof b);
     carve_tables(c, b, 1);
-    carve_arrays(c, b, n, 1, p->precision);
+    carve_arrays(c, b, n, 1, p->precision, p->gravity ? gravity_chunks(n) : 0);
     return c.off + 256;
 }
 
@@ -394,7 +395,7 @@ int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *st
     c->diag = cv.take<ProbDiag>(1);
     memset(&c->bv, 0, sizeof c->bv);
     carve_tables(cv, c->bv, 1);
-    carve_arrays(cv, c->bv, n, 1, p->precision);
+    carve_arrays(cv, c->bv, n, 1, p->precision, p->gravity ? gravity_chunks(n) : 0);
     c->bv.ntot = n;
     c->bv.key_bits = key_bits_for(1);
     c->bv.key_lo = key_low_bits(n);
@@ -404,6 +405,7 @@ int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *st
     c->bv.any_general = (p->av_switch || p->ac_signal || p->gravity) ? 1 : 0;
     c->bv.any_gravity = p->gravity ? 1 : 0;
     c->bv.grav_blocks = p->gravity ? gravity_blocks(n) : 0;
+    c->bv.grav_split = p->gravity && gravity_chunks(n) > 1;
     ProbStatic &ps = c->host_ps;
     memset(&ps, 0, sizeof ps);
     ps.x = state->x;
@@ -431,6 +433,7 @@ int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *st
     ps.diag = c->diag;
     ps.lpp = c->lpp;
     ps.ph = phys_of(p);
+    ps.gchunks = p->gravity ? gravity_chunks(n) : 0;
     // equal masses (the usual SPH set-up; masses never change) let the
     // density lists keep distances only
     if (n > 0) {
@@ -526,8 +529,12 @@ static int enqueue_step(const BatchView &b, int precision, double dt, cudaStream
     int rc = enqueue_density(b, precision, 1, st, mk, rebuild);
     if (rc) return rc;
     CU(launch_forces(b, precision, st));
-    mk.at(SPH_STAGE_CLOSE, st);
+    mk.at(SPH_STAGE_GRAVITY, st);
     mk.done(SPH_STAGE_FORCES);
+    launch_gravity(b, precision, st);  // adds the long-range attraction to a
+    CU(cudaGetLastError());
+    mk.at(SPH_STAGE_CLOSE, st);
+    if (b.any_gravity) mk.done(SPH_STAGE_GRAVITY);
     CU(launch_kick_close(b, 1, 1, st));
     mk.at(SPH_NSTAGES, st);
     mk.done(SPH_STAGE_CLOSE);
@@ -593,8 +600,12 @@ int sph_forces(sph_ctx *c)
     CU(launch_reset_step(c->bv, 2, c->stream));
     mk.at(SPH_STAGE_FORCES, c->stream);
     CU(launch_forces(c->bv, c->prm.precision, c->stream));
-    mk.at(SPH_STAGE_CLOSE, c->stream);
+    mk.at(SPH_STAGE_GRAVITY, c->stream);
     mk.done(SPH_STAGE_FORCES);
+    launch_gravity(c->bv, c->prm.precision, c->stream);
+    CU(cudaGetLastError());
+    mk.at(SPH_STAGE_CLOSE, c->stream);
+    if (c->bv.any_gravity) mk.done(SPH_STAGE_GRAVITY);
     CU(launch_kick_close(c->bv, 0, 1, c->stream));
     c->have_forces = true;
     return finish_call(c);
@@ -799,12 +810,16 @@ size_t sph_batch_workspace_bytes(sph_ctx *const *ctxs, int nctx)
 {
     if (batch_check(ctxs, nctx) != SPH_OK) return 0;
     long long ntot = 0;
-    for (int k = 0; k < nctx; ++k) ntot += ctxs[k]->n;
+    int gch = 0;
+    for (int k = 0; k < nctx; ++k) {
+        ntot += ctxs[k]->n;
+        if (ctxs[k]->prm.gravity && gravity_chunks(ctxs[k]->n) > gch) gch = gravity_chunks(ctxs[k]->n);
+    }
     Carver c{nullptr};
     BatchView b;
     memset(&b, 0, sizeof b);
     carve_tables(c, b, nctx);
-    carve_arrays(c, b, ntot, nctx, ctxs[0]->prm.precision);
+    carve_arrays(c, b, ntot, nctx, ctxs[0]->prm.precision, gch);
     return c.off + 256;
 }
 
@@ -826,6 +841,7 @@ int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, 
     std::vector<long long> bases(nctx + 1);
     int mask = 0, dmask = 0, b_any_isolated = 0, b_any_periodic = 0, b_any_general = 0, b_any_gravity = 0;
     long long grav_blocks = 0;
+    int gch = 0;
     for (int k = 0; k < nctx; ++k) {
         tab[k] = ctxs[k]->host_ps;
         tab[k].base = ntot;
@@ -838,14 +854,16 @@ int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, 
         if (tab[k].ph.av_switch || tab[k].ph.ac_signal || tab[k].ph.gravity) b_any_general = 1;
         if (tab[k].ph.gravity) b_any_gravity = 1;
         tab[k].gblk0 = (int)grav_blocks;
+        tab[k].gchunks = tab[k].ph.gravity ? gravity_chunks(ctxs[k]->n) : 0;
         if (tab[k].ph.gravity) grav_blocks += gravity_blocks(ctxs[k]->n);
+        if (tab[k].gchunks > gch) gch = tab[k].gchunks;
     }
     bases[nctx] = ntot;
     Carver cv{(char *)workspace};
     BatchView b;
     memset(&b, 0, sizeof b);
     carve_tables(cv, b, nctx);
-    carve_arrays(cv, b, ntot, nctx, prec);
+    carve_arrays(cv, b, ntot, nctx, prec, gch);
     b.ntot = ntot;
     b.key_bits = key_bits_for(nctx);
     b.key_lo = key_low_bits(ntot);
@@ -856,6 +874,7 @@ int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, 
     b.any_general = b_any_general;
     b.any_gravity = b_any_gravity;
     b.grav_blocks = grav_blocks;
+    b.grav_split = gch > 1;
     CU(cudaMemcpyAsync(b.prob, tab.data(), sizeof(ProbStatic) * nctx, cudaMemcpyHostToDevice, st));
     CU(cudaMemcpyAsync(b.prob_base, bases.data(), sizeof(long long) * (nctx + 1), cudaMemcpyHostToDevice, st));
     CU(cudaMemsetAsync(b.dyn, 0, sizeof(ProbDyn) * nctx, st));

@@ -104,7 +104,7 @@ struct ProbStatic {
     int lpp;         // lanes per particle in the pair kernels (leaf size = 32 / lpp)
     int uniform_m;   // all masses equal (m_uniform): neighbour lists keep distances only
     int gblk0;       // gravity: the problem's first block of the direct-sum launch
-    int pad4_;
+    int gchunks;     // gravity: ranges the partners are split into (one block per range and 256 particles)
     double m_uniform;
     double inv_m_uniform;  // 1 / m_uniform (0 unless uniform_m)
     PhysParams ph;
@@ -163,6 +163,8 @@ struct BatchView {
                                  // gravity (served by the wrap-list launches)
     int any_gravity;             // some problem has self-gravity (direct-sum launch)
     long long grav_blocks;       // blocks of the direct-sum launch (all gravity problems)
+    int grav_split;              // some gravity problem splits its partners (partial sums to reduce)
+    double *gpart;               // gravity: partial forces [chunk][ntot][3] of split problems
     ProbStatic *prob;            // [nprob]
     ProbDyn *dyn;                // [nprob]
     long long *prob_base;        // [nprob + 1] base offsets (for searches)
@@ -296,7 +298,8 @@ cudaError_t launch_refit(const BatchView &b, int precision, cudaStream_t st);
 cudaError_t launch_density(const BatchView &b, int precision, int use_pred, cudaStream_t st);
 cudaError_t launch_forces(const BatchView &b, int precision, cudaStream_t st);
 void launch_gravity(const BatchView &b, int precision, cudaStream_t st);  // direct-sum self-gravity
-long long gravity_blocks(long long n);
+long long gravity_blocks(long long n);  // blocks of one problem (particle blocks x partner ranges)
+int gravity_chunks(long long n);        // partner ranges of one problem
 cudaError_t launch_kick_drift(const BatchView &b, double dt_host, cudaStream_t st);  // also selects dt, resets diagnostics
 cudaError_t launch_kick_close(const BatchView &b, int do_kick, int forces_ran, cudaStream_t st);
 cudaError_t launch_reset_step(const BatchView &b, int mode, cudaStream_t st);  // mode 1 full, 2 forces only
@@ -318,7 +321,7 @@ struct Carver {
     }
 };
 int fail(int code, const char *fmt, ...);  // records the thread's error message, returns code
-void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precision);
+void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precision, int grav_chunks = 0);
 void carve_tables(Carver &c, BatchView &b, int nprob);
 int key_bits_for(int nprob);
 int key_low_bits(long long ntot);  // Morton bits left unsorted (cleared) for ntot particles

@@ -90,7 +90,7 @@ extern "C" int sph_density_forces_noalloc(const sph_params *p, int64_t n, const 
     BatchView b;
     memset(&b, 0, sizeof b);
     carve_tables(c, b, 1);
-    carve_arrays(c, b, n, 1, p->precision);
+    carve_arrays(c, b, n, 1, p->precision, p->gravity ? gravity_chunks(n) : 0);
     if (c.off > kNoAllocBytes) return fail(SPH_ENOSPACE, "fixed scratch too small for %lld particles", (long long)n);
     const int lpp = lpp_of(p, n);
     b.ntot = n;
@@ -103,6 +103,7 @@ extern "C" int sph_density_forces_noalloc(const sph_params *p, int64_t n, const 
     b.any_general = (p->av_switch || p->ac_signal || p->gravity) ? 1 : 0;
     b.any_gravity = p->gravity ? 1 : 0;
     b.grav_blocks = p->gravity ? gravity_blocks(n) : 0;
+    b.grav_split = p->gravity && gravity_chunks(n) > 1;
     ProbStatic ps;
     memset(&ps, 0, sizeof ps);
     ps.x = state->x;
@@ -130,6 +131,7 @@ extern "C" int sph_density_forces_noalloc(const sph_params *p, int64_t n, const 
     ps.diag = diag;
     ps.lpp = lpp;
     ps.ph = phys_of(p);
+    ps.gchunks = p->gravity ? gravity_chunks(n) : 0;
     cudaStream_t st = (cudaStream_t)stream;
     const int prec = p->precision;
     cudaError_t e;
@@ -149,6 +151,8 @@ extern "C" int sph_density_forces_noalloc(const sph_params *p, int64_t n, const 
     NA_TRY(launch_density(b, prec, 0, st));
     NA_TRY(launch_refit(b, prec, st));
     NA_TRY(launch_forces(b, prec, st));
+    launch_gravity(b, prec, st);
+    NA_TRY(cudaGetLastError());
     NA_TRY(launch_kick_close(b, 0, 1, st));
     if (p->flags & SPH_FLAG_ASYNC) return SPH_OK;
     NA_TRY(cudaStreamSynchronize(st));

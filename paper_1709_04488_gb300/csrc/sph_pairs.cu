@@ -40,7 +40,6 @@ cudaError_t launch_forces(const BatchView &b, int precision, cudaStream_t st)
     if (e == cudaSuccess && (b.any_periodic || b.any_general)) e = force_launches_m4_wrap(b, precision, st);
     if (e == cudaSuccess && (b.any_periodic || b.any_general)) e = force_launches_m6_wrap(b, precision, st);
     if (e != cudaSuccess) return e;
-    launch_gravity(b, precision, st);  // adds the long-range attraction to a
     return cudaGetLastError();
 }
 

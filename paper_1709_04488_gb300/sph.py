@@ -21,8 +21,8 @@ KERNEL_M4, KERNEL_M6 = 0, 1
 AC_WADSLEY, AC_PRICE = 0, 1
 AV_CONSTANT, AV_MORRIS_MONAGHAN = 0, 1
 FLAG_ASYNC, FLAG_TIMING = 1, 2
-NSTAGES = 7
-STAGES = ["kick_drift", "sort", "tree", "density", "refit", "forces", "close"]
+NSTAGES = 8
+STAGES = ["kick_drift", "sort", "tree", "density", "refit", "forces", "gravity", "close"]
 
 _DP = C.POINTER(C.c_double)
 
