@@ -19,6 +19,11 @@ Parity status per function (see the pins in ``tests/test_oracle_pins.py``):
   forces (viscosity, conductivity) ..... pinned (pairwise antisymmetry, energy balance,
                                          v=0 and uniform-u special cases)
   KDK step ............................. pinned (free translation, Sod analytic window)
+  self-gravity (direct sum, zeta) ....... pinned (enclosed mass by quadrature, phi' = dphi/dr,
+                                         momentum, gravity = -grad E_pot)
+  gravity tree walk (KD tree, theta) .... pinned (dumbbell fields = the closed-form series
+                                         through the quadrupole; error order (l/d)^3 vs
+                                         (l/d)^2; theta -> 0 is the direct sum)
   neighbour lists ...................... pinned (scipy cKDTree on the same points)
 """
 from __future__ import annotations
@@ -71,6 +76,8 @@ class _Params(C.Structure):
         ("av_decay", C.c_double),
         ("gravity", C.c_int),
         ("G", C.c_double),
+        ("grav_theta", C.c_double),
+        ("grav_leaf", C.c_int),
     ]
 
 
@@ -137,6 +144,11 @@ def lib():
         L.orc_density_subset.argtypes = [PP, C.c_int64, SP, C.c_int64, C.POINTER(C.c_int64)]
         L.orc_forces_subset.restype = C.c_int
         L.orc_forces_subset.argtypes = [PP, C.c_int64, SP, C.c_int64, C.POINTER(C.c_int64), C.c_double]
+        L.orc_gravity_accel.restype = C.c_int
+        L.orc_gravity_accel.argtypes = [PP, C.c_int64, SP, _DP, _DP, _DP]
+        L.orc_multipole_accel.restype = None
+        L.orc_multipole_accel.argtypes = [C.c_int64, _DP, _DP, _DP, _DP, C.c_double, C.c_double, C.c_double,
+                                          C.c_int, _DP]
         L.orc_num_threads.restype = C.c_int
         L.orc_set_num_threads.argtypes = [C.c_int]
         _lib = L
@@ -168,6 +180,8 @@ class Params:
     av_decay: float = 0.1           # switch: tau = h / (av_decay c)
     gravity: int = 0                # 1: self-gravity (isolated, M4), Eq. SPHSELFGRAV
     G: float = 1.0                  # gravitational constant
+    grav_theta: float = 0.0         # gravity: tree opening angle theta_MAX (0: direct summation)
+    grav_leaf: int = 8              # gravity tree: N_LEAF
 
     def _c(self) -> _Params:
         p = _Params()
@@ -184,6 +198,7 @@ class Params:
         p.av_switch = int(self.av_switch)
         p.alpha_min, p.av_decay = self.alpha_min, self.av_decay
         p.gravity, p.G = int(self.gravity), self.G
+        p.grav_theta, p.grav_leaf = float(self.grav_theta), int(self.grav_leaf)
         return p
 
 
@@ -332,6 +347,28 @@ def grav_dphidh(r, h):
 def gravity_energy(p: Params, s: State) -> float:
     """(G/2) sum_i sum_j m_i m_j (phi(r_ij,h_i) + phi(r_ij,h_j))/2 with the state's h."""
     return lib().orc_gravity_energy(C.byref(p._c()), s.n, C.byref(s._c()))
+
+
+def gravity_accel(p: Params, s: State):
+    """Long-range gravitational accelerations alone (tree walk when
+    p.grav_theta > 0, else the direct sum) with the state's h: (gx, gy, gz)."""
+    g = [np.zeros(s.n) for _ in range(3)]
+    rc = lib().orc_gravity_accel(C.byref(p._c()), s.n, C.byref(s._c()),
+                                 *[a.ctypes.data_as(_DP) for a in g])
+    if rc != OK:
+        raise ValueError(f"orc_gravity_accel: {rc}")
+    return tuple(g)
+
+
+def multipole_accel(x, y, z, m, point, quad=True):
+    """Acceleration (G = 1) at `point` from the points' multipole expansion
+    about their centre of mass: monopole, plus the quadrupole if `quad`."""
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z, m)]
+    out = np.zeros(3)
+    lib().orc_multipole_accel(len(arrs[0]), *[a.ctypes.data_as(_DP) for a in arrs],
+                              float(point[0]), float(point[1]), float(point[2]), int(bool(quad)),
+                              out.ctypes.data_as(_DP))
+    return out
 
 
 def kernel_Wk(k, r, h):

@@ -68,6 +68,9 @@ typedef struct {
     double av_decay;         /* switch: decay time tau = h / (av_decay c) */
     int gravity;             /* 1: self-gravity, Eq. SPHSELFGRAV (isolated, M4 kernel) */
     double G;                /* gravitational constant */
+    double grav_theta;       /* gravity: opening angle theta_MAX of the tree walk (Sec. 4.2);
+                                0 = direct summation over every pair */
+    int grav_leaf;           /* gravity tree: N_LEAF, most particles in a leaf cell */
 } orc_params;
 
 typedef struct {
@@ -424,6 +427,8 @@ static int params_ok(const orc_params *p, int64_t n)
         return 0;
     if (p->gravity != 0 && p->gravity != 1) return 0;
     if (p->gravity && (p->periodic || p->kernel != 0 || !(p->G > 0))) return 0;
+    if (p->gravity && !(p->grav_theta >= 0.0 && p->grav_theta <= 1.0)) return 0;
+    if (p->gravity && p->grav_theta > 0 && p->grav_leaf < 1) return 0;
     return 1;
 }
 
@@ -595,21 +600,256 @@ static double gravity_zeta(const orc_params *p, const orc_state *s, int64_t i, c
     return -s->h[i] / (3.0 * rho) * z.s;
 }
 
-/* Long-range part of Eq. SPHSELFGRAV for particle i: -G sum_{j != i} m_j
-   (phi'(r_ij,h_i) + phi'(r_ij,h_j))/2 r_hat_ij, by direct summation over
-   every particle (isolated problems). */
+/* One term of the long-range part of Eq. SPHSELFGRAV: the acceleration of i
+   by j, -G m_j (phi'(r_ij,h_i) + phi'(r_ij,h_j))/2 r_hat_ij. */
+static void gravity_pair(const orc_params *p, const orc_state *s, int64_t i, int64_t j, kahan_t *ax, kahan_t *ay,
+                         kahan_t *az)
+{
+    sep_t sp = separation(p, s, i, j);
+    double r = sqrt(sp.r2);
+    double f = -p->G * s->m[j] * 0.5 * (orc_gforce(r, s->h[i]) + orc_gforce(r, s->h[j])) / r;
+    kadd(ax, f * sp.dx);
+    kadd(ay, f * sp.dy);
+    kadd(az, f * sp.dz);
+}
+
+/* The long-range part for particle i by direct summation over every particle
+   (isolated problems). */
 static void gravity_direct(const orc_params *p, const orc_state *s, int64_t n, int64_t i, kahan_t *ax, kahan_t *ay,
                            kahan_t *az)
 {
-    for (int64_t j = 0; j < n; ++j) {
-        if (j == i) continue;
-        sep_t sp = separation(p, s, i, j);
-        double r = sqrt(sp.r2);
-        double f = -p->G * s->m[j] * 0.5 * (orc_gforce(r, s->h[i]) + orc_gforce(r, s->h[j])) / r;
-        kadd(ax, f * sp.dx);
-        kadd(ay, f * sp.dy);
-        kadd(az, f * sp.dz);
+    for (int64_t j = 0; j < n; ++j)
+        if (j != i) gravity_pair(p, s, i, j, ax, ay, az);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gravity tree (Sec. 4.2): a KD tree built top-down, each cell split at the */
+/* median particle position along its most elongated axis until a cell holds */
+/* at most N_LEAF particles.  Each cell keeps its mass, centre of mass,      */
+/* quadrupole moment about the centre of mass, particle box, largest h and   */
+/* size l_c.  The walk from the root uses a cell's multipole (monopole plus  */
+/* quadrupole) when the geometric criterion |r_i - r_c|^2 >= l_c^2/theta^2   */
+/* holds and no pair with the cell is softened; otherwise the cell is opened, */
+/* and a leaf that is opened contributes its particles by the pair term.     */
+/* Readings: r_c is the centre of mass (the expansion centre) and l_c the    */
+/* largest distance from it to a corner of the cell's particle box; a cell is */
+/* also opened while r_i is within 2 max(h_i, h_max of the cell) of its box, */
+/* since the expansion is of the unsoftened 1/r.                             */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t first, count; /* particles idx[first, first + count) */
+    int left, right;      /* children, -1 for a leaf */
+    double mass, com[3];
+    double quad[6];       /* Q_xx, Q_xy, Q_xz, Q_yy, Q_yz, Q_zz: sum m (3 d_a d_b - |d|^2 delta_ab) */
+    double lo[3], hi[3], hmax, lc2;
+} kdcell_t;
+
+typedef struct {
+    kdcell_t *cell;
+    int ncell, cap;
+    int64_t *idx;
+} kdtree_t;
+
+/* mass, centre of mass and quadrupole of the points idx[first, first+count)
+   (idx NULL: the points first .. first+count-1) */
+static void point_moments(const double *x, const double *y, const double *z, const double *m, const int64_t *idx,
+                          int64_t first, int64_t count, double *mass, double com[3], double q[6])
+{
+    kahan_t M = {0, 0}, cx = {0, 0}, cy = {0, 0}, cz = {0, 0};
+    for (int64_t k = first; k < first + count; ++k) {
+        int64_t j = idx ? idx[k] : k;
+        kadd(&M, m[j]);
+        kadd(&cx, m[j] * x[j]);
+        kadd(&cy, m[j] * y[j]);
+        kadd(&cz, m[j] * z[j]);
     }
+    *mass = M.s;
+    com[0] = cx.s / M.s;
+    com[1] = cy.s / M.s;
+    com[2] = cz.s / M.s;
+    kahan_t Q[6];
+    memset(Q, 0, sizeof Q);
+    for (int64_t k = first; k < first + count; ++k) {
+        int64_t j = idx ? idx[k] : k;
+        double d[3] = {x[j] - com[0], y[j] - com[1], z[j] - com[2]};
+        double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        kadd(&Q[0], m[j] * (3.0 * d[0] * d[0] - d2));
+        kadd(&Q[1], m[j] * (3.0 * d[0] * d[1]));
+        kadd(&Q[2], m[j] * (3.0 * d[0] * d[2]));
+        kadd(&Q[3], m[j] * (3.0 * d[1] * d[1] - d2));
+        kadd(&Q[4], m[j] * (3.0 * d[1] * d[2]));
+        kadd(&Q[5], m[j] * (3.0 * d[2] * d[2] - d2));
+    }
+    for (int a = 0; a < 6; ++a) q[a] = Q[a].s;
+}
+
+/* Acceleration at r (relative to the centre of mass) of mass M with
+   quadrupole Q: the potential -G (M/|r| + r.Q.r / (2|r|^5)) gives
+   -G M r/|r|^3 + G (Q r/|r|^5 - (5/2)(r.Q.r) r/|r|^7); quad = 0 keeps the
+   monopole only. */
+static void multipole_accel(double G, double M, const double q[6], const double r[3], int quad, double out[3])
+{
+    double r2 = r[0] * r[0] + r[1] * r[1] + r[2] * r[2];
+    double rinv = 1.0 / sqrt(r2);
+    double rinv3 = rinv * rinv * rinv;
+    for (int a = 0; a < 3; ++a) out[a] = -G * M * r[a] * rinv3;
+    if (!quad) return;
+    double Qr[3] = {q[0] * r[0] + q[1] * r[1] + q[2] * r[2], q[1] * r[0] + q[3] * r[1] + q[4] * r[2],
+                    q[2] * r[0] + q[4] * r[1] + q[5] * r[2]};
+    double rQr = r[0] * Qr[0] + r[1] * Qr[1] + r[2] * Qr[2];
+    double rinv5 = rinv3 * rinv * rinv, rinv7 = rinv5 * rinv * rinv;
+    for (int a = 0; a < 3; ++a) out[a] += G * (Qr[a] * rinv5 - 2.5 * rQr * r[a] * rinv7);
+}
+
+/* the acceleration that points (x, y, z, m)[0..n) exert at (px, py, pz) by
+   their multipole expansion about their centre of mass (G = 1) */
+void orc_multipole_accel(int64_t n, const double *x, const double *y, const double *z, const double *m, double px,
+                         double py, double pz, int quad, double *out)
+{
+    double M, com[3], q[6];
+    point_moments(x, y, z, m, NULL, 0, n, &M, com, q);
+    double r[3] = {px - com[0], py - com[1], pz - com[2]};
+    multipole_accel(1.0, M, q, r, quad, out);
+}
+
+static const double *kd_sort_coord; /* the tree is built by one thread */
+static int kd_cmp(const void *a, const void *b)
+{
+    int64_t i = *(const int64_t *)a, j = *(const int64_t *)b;
+    double u = kd_sort_coord[i], v = kd_sort_coord[j];
+    if (u < v) return -1;
+    if (u > v) return 1;
+    return (i > j) - (i < j); /* equal coordinates: by particle id */
+}
+
+static int kd_build(kdtree_t *t, const orc_state *s, int64_t first, int64_t count, int nleaf)
+{
+    if (t->ncell == t->cap) {
+        int cap = t->cap ? 2 * t->cap : 64;
+        kdcell_t *c = (kdcell_t *)realloc(t->cell, sizeof(kdcell_t) * cap);
+        if (!c) return -1;
+        t->cell = c;
+        t->cap = cap;
+    }
+    int id = t->ncell++;
+    kdcell_t *c = &t->cell[id];
+    c->first = first;
+    c->count = count;
+    c->left = c->right = -1;
+    const double *X[3] = {s->x, s->y, s->z};
+    c->hmax = 0.0;
+    for (int a = 0; a < 3; ++a) c->lo[a] = c->hi[a] = X[a][t->idx[first]];
+    for (int64_t k = first; k < first + count; ++k) {
+        int64_t j = t->idx[k];
+        for (int a = 0; a < 3; ++a) {
+            if (X[a][j] < c->lo[a]) c->lo[a] = X[a][j];
+            if (X[a][j] > c->hi[a]) c->hi[a] = X[a][j];
+        }
+        if (s->h[j] > c->hmax) c->hmax = s->h[j];
+    }
+    point_moments(s->x, s->y, s->z, s->m, t->idx, first, count, &c->mass, c->com, c->quad);
+    c->lc2 = 0.0;
+    for (int k = 0; k < 8; ++k) {
+        double d2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+            double d = ((k >> a) & 1 ? c->hi[a] : c->lo[a]) - c->com[a];
+            d2 += d * d;
+        }
+        if (d2 > c->lc2) c->lc2 = d2;
+    }
+    if (count <= nleaf) return 0;
+    int ax = 0; /* most elongated axis */
+    for (int a = 1; a < 3; ++a)
+        if (c->hi[a] - c->lo[a] > c->hi[ax] - c->lo[ax]) ax = a;
+    kd_sort_coord = X[ax];
+    qsort(t->idx + first, (size_t)count, sizeof(int64_t), kd_cmp);
+    int64_t nl = count / 2; /* the median splits the cell */
+    int l = t->ncell;
+    if (kd_build(t, s, first, nl, nleaf)) return -1;
+    int r = t->ncell;
+    if (kd_build(t, s, first + nl, count - nl, nleaf)) return -1;
+    t->cell[id].left = l; /* (t->cell may have moved) */
+    t->cell[id].right = r;
+    return 0;
+}
+
+static void kd_free(kdtree_t *t)
+{
+    free(t->cell);
+    free(t->idx);
+    memset(t, 0, sizeof *t);
+}
+
+static int gravity_tree_build(const orc_params *p, const orc_state *s, int64_t n, kdtree_t *t)
+{
+    memset(t, 0, sizeof *t);
+    if (!(p->gravity && p->grav_theta > 0) || n == 0) return 0;
+    t->idx = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    if (!t->idx) return -1;
+    for (int64_t i = 0; i < n; ++i) t->idx[i] = i;
+    if (kd_build(t, s, 0, n, p->grav_leaf)) {
+        kd_free(t);
+        return -1;
+    }
+    return 0;
+}
+
+static void gravity_tree_walk(const orc_params *p, const orc_state *s, const kdtree_t *t, int c, int64_t i,
+                              kahan_t *ax, kahan_t *ay, kahan_t *az)
+{
+    const kdcell_t *C = &t->cell[c];
+    const double ri[3] = {s->x[i], s->y[i], s->z[i]};
+    double r[3], d2 = 0.0, g2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        r[a] = ri[a] - C->com[a];
+        d2 += r[a] * r[a];
+        double g = ri[a] < C->lo[a] ? C->lo[a] - ri[a] : (ri[a] > C->hi[a] ? ri[a] - C->hi[a] : 0.0);
+        g2 += g * g;
+    }
+    const double soft = 2.0 * (s->h[i] > C->hmax ? s->h[i] : C->hmax);
+    if (d2 >= C->lc2 / (p->grav_theta * p->grav_theta) && g2 >= soft * soft) {
+        double acc[3];
+        multipole_accel(p->G, C->mass, C->quad, r, 1, acc);
+        kadd(ax, acc[0]);
+        kadd(ay, acc[1]);
+        kadd(az, acc[2]);
+        return;
+    }
+    if (C->left < 0) {
+        for (int64_t k = C->first; k < C->first + C->count; ++k)
+            if (t->idx[k] != i) gravity_pair(p, s, i, t->idx[k], ax, ay, az);
+        return;
+    }
+    gravity_tree_walk(p, s, t, C->left, i, ax, ay, az);
+    gravity_tree_walk(p, s, t, C->right, i, ax, ay, az);
+}
+
+/* long-range gravity of particle i: the tree walk when theta_MAX > 0, else
+   the direct sum */
+static void gravity_long_range(const orc_params *p, const orc_state *s, int64_t n, const kdtree_t *t, int64_t i,
+                               kahan_t *ax, kahan_t *ay, kahan_t *az)
+{
+    if (p->grav_theta > 0) gravity_tree_walk(p, s, t, 0, i, ax, ay, az);
+    else gravity_direct(p, s, n, i, ax, ay, az);
+}
+
+/* The long-range accelerations alone (no zeta term, no hydrodynamics) for
+   every particle, with the current h. */
+int orc_gravity_accel(const orc_params *p, int64_t n, const orc_state *s, double *gx, double *gy, double *gz)
+{
+    if (!params_ok(p, n) || !p->gravity) return ORC_EINVAL;
+    kdtree_t t;
+    if (gravity_tree_build(p, s, n, &t)) return ORC_ENOMEM;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+        kahan_t ax = {0, 0}, ay = {0, 0}, az = {0, 0};
+        gravity_long_range(p, s, n, &t, i, &ax, &ay, &az);
+        gx[i] = ax.s;
+        gy[i] = ay.s;
+        gz[i] = az.s;
+    }
+    kd_free(&t);
+    return ORC_OK;
 }
 
 /* Gravitational potential energy (G/2) sum_i sum_j m_i m_j (phi(r_ij,h_i) +
@@ -718,6 +958,11 @@ int orc_forces(const orc_params *p, int64_t n, orc_state *s)
         if (grid_build(&g, p, s, n, 2.0 * median_spacing_guess(p, s, n))) return ORC_ENOMEM;
         gp = &g;
     }
+    kdtree_t kt;
+    if (gravity_tree_build(p, s, n, &kt)) {
+        if (gp) grid_free(&g);
+        return ORC_ENOMEM;
+    }
     const double aac = p->alpha_ac;
     int status = ORC_OK;
 #pragma omp parallel
@@ -775,7 +1020,7 @@ int orc_forces(const orc_params *p, int64_t n, orc_state *s)
                     kadd(&du, dui + duav + duac);
                 }
             }
-            if (p->gravity) gravity_direct(p, s, n, i, &ax, &ay, &az);
+            if (p->gravity) gravity_long_range(p, s, n, &kt, i, &ax, &ay, &az);
             s->ax[i] = ax.s;
             s->ay[i] = ay.s;
             s->az[i] = az.s;
@@ -786,6 +1031,7 @@ int orc_forces(const orc_params *p, int64_t n, orc_state *s)
         free(buf.v);
     }
     if (gp) grid_free(&g);
+    kd_free(&kt);
     return status;
 }
 
@@ -975,6 +1221,11 @@ int orc_forces_subset(const orc_params *p, int64_t n, orc_state *s, int64_t nsub
     grid_t g;
     memset(&g, 0, sizeof g);
     if (grid_build(&g, p, s, n, 2.0 * median_spacing_guess(p, s, n))) return ORC_ENOMEM;
+    kdtree_t kt;
+    if (gravity_tree_build(p, s, n, &kt)) {
+        grid_free(&g);
+        return ORC_ENOMEM;
+    }
     const double aac = p->alpha_ac;
     int status = ORC_OK;
 #pragma omp parallel
@@ -1032,7 +1283,7 @@ int orc_forces_subset(const orc_params *p, int64_t n, orc_state *s, int64_t nsub
                     kadd(&du, dui + duav + duac);
                 }
             }
-            if (p->gravity) gravity_direct(p, s, n, i, &ax, &ay, &az);
+            if (p->gravity) gravity_long_range(p, s, n, &kt, i, &ax, &ay, &az);
             s->ax[i] = ax.s;
             s->ay[i] = ay.s;
             s->az[i] = az.s;
@@ -1043,5 +1294,6 @@ int orc_forces_subset(const orc_params *p, int64_t n, orc_state *s, int64_t nsub
         free(buf.v);
     }
     grid_free(&g);
+    kd_free(&kt);
     return status;
 }
