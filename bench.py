@@ -40,6 +40,8 @@ FLOPS_DENSITY_PAIR = 19   # per pair per Newton-Raphson pass (q, f, f', two accu
 FLOPS_FORCE_PAIR = 101    # per ordered pair (pressure, viscosity, conduction, energy, TwoSum-compensated m a)
 FLOPS_GRAVITY_PAIR = 38   # per ordered pair beyond the softening (r, 1/r^3 weight, TwoSum-compensated F)
 GRAVITY_N = 65536         # self-gravity measurement: isolated cloud of this many particles
+GRAVITY_TREE_N = 1_000_000  # the tree walk's larger cloud
+GRAVITY_THETA = 0.5       # opening angle of the tree-walk measurements
 
 
 def parse():
@@ -446,6 +448,24 @@ def run_ours(args):
                 "unit": UNIT, "k_gravity": {"ms": g_ms, "flop": float(gflop), "achieved": g_ach,
                                             "frac": g_ach / peak, "unit": "TFLOP/s"}}
         pgr.close()
+        # the tree walk (Sec. 4.2) at the same size and at a size the direct
+        # sum cannot reach
+        grav["tree"] = []
+        for nt in (GRAVITY_N, GRAVITY_TREE_N):
+            at, pt = ics.cloud(nt, seed=4)
+            prmt = S.make_params(S.PREC_MIXED, **pt, flags=S.FLAG_ASYNC | S.FLAG_TIMING, gravity=1, G=1.0,
+                                 grav_theta=GRAVITY_THETA)
+            with torch.cuda.stream(stream):
+                ptr = S.Problem(at, prmt, device=dev, stream=stream)
+                S.check(S.sph_density_h(ptr.ctx), "sph_density_h")
+                S.check(S.sph_forces(ptr.ctx), "sph_forces")
+            S.check(S.sph_run(ptr.ctx, 3), "sph_run")
+            mst, stt, _, _ = time_steps(S, ptr, stream, torch, 5, flush, stage=True)
+            grav["tree"].append({"workload": f"cloud_{nt}: isolated, isothermal, G=1, tree walk theta={GRAVITY_THETA}",
+                                 "ms_per_step": float(np.mean(mst)), "value": nt * len(mst) / (np.sum(mst) * 1e-3),
+                                 "unit": UNIT,
+                                 "gravity_stage_ms": float(np.mean(np.array(stt), axis=0)[S.STAGES.index("gravity")])})
+            ptr.close()
 
     diag = prob.diagnostics()
     prob.close()

@@ -133,11 +133,19 @@ typedef struct {
     double av_decay;       /* switch: decay rate in units of c/h (default 0.1)          */
     int gravity;           /* 1: self-gravity, Eq. SPHSELFGRAV (Sec. 2.1.2): the kernel-
                               softened attraction -G sum_j m_j (phi'(r,h_i)+phi'(r,h_j))/2
-                              r_hat over every particle of the problem (direct summation,
-                              O(n^2)) plus the zeta term of Eq. GRADHZETA over the
-                              neighbours.  Isolated problems and the M4 kernel only
-                              (SPH_EINVAL otherwise).                                    */
+                              r_hat over every particle of the problem plus the zeta term
+                              of Eq. GRADHZETA over the neighbours.  Isolated problems and
+                              the M4 kernel only (SPH_EINVAL otherwise).                 */
     double G;              /* gravitational constant (gravity; must be > 0)            */
+    double grav_theta;     /* gravity: 0 (default) sums the attraction directly over
+                              every pair, O(n^2); 0 < theta <= 1 walks the tree instead
+                              (Sec. 4.2): a node is used through its monopole and
+                              quadrupole moments when the squared distance from its
+                              centre of mass to the leaf's box is at least l^2/theta^2
+                              (l: distance from the centre of mass to the node box's
+                              farthest corner) and no pair with it is softened (boxes
+                              at least 2 max h apart); other nodes are opened, opened
+                              leaves summed pair by pair.  Outside [0, 1]: SPH_EINVAL. */
 } sph_params;
 
 /* Caller-owned device arrays, FP64, length n, caller's particle order.

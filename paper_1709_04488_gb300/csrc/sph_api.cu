@@ -50,7 +50,7 @@ DevInfo dev_info()
 
 // ---- workspace layout -------------------------------------------------------
 // Carve the per-step scratch arrays for `ntot` particles over `nprob` problems.
-void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precision, int grav_chunks)
+void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precision, int grav_chunks, int grav_tree)
 {
     const long long n = ntot > 0 ? ntot : 1;
     const size_t v4 = precision == SPH_PREC_FP64 ? sizeof(dbl4) : sizeof(float4);
@@ -82,6 +82,7 @@ void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precis
     for (int l = 0; l <= kMaxLevels; ++l) {
         b.node_cap[l] = (int)cap;
         b.nodes[l] = c.take<NodeBox>(cap);
+        b.gnode[l] = grav_tree ? (void *)c.take<char>(5 * v4 * cap) : nullptr;
         cap = cap / kBranch + nprob + 1;
     }
     b.fallback_list = c.take<int>(n);
@@ -203,6 +204,8 @@ int validate(const sph_params *p)
         !(p->alpha_av > 0 && p->alpha_min >= 0 && p->alpha_min <= p->alpha_av && p->av_decay > 0))
         return fail(SPH_EINVAL, "viscosity switch needs alpha_av > 0, 0 <= alpha_min <= alpha_av, av_decay > 0");
     if (p->gravity != 0 && p->gravity != 1) return fail(SPH_EINVAL, "gravity must be 0 or 1");
+    if (p->gravity && !(p->grav_theta >= 0.0 && p->grav_theta <= 1.0))
+        return fail(SPH_EINVAL, "grav_theta must lie in [0, 1]");
     if (p->gravity && (p->periodic || p->kernel != SPH_KERNEL_M4 || !(p->G > 0)))
         return fail(SPH_EINVAL, "self-gravity needs an isolated problem, the M4 kernel and G > 0");
     if (p->ac_signal != SPH_AC_WADSLEY && p->ac_signal != SPH_AC_PRICE)
@@ -262,6 +265,7 @@ PhysParams phys_of(const sph_params *p)
     ph.beta_ratio = p->alpha_av > 0 ? p->beta_av / p->alpha_av : 0.0;
     ph.gravity = p->gravity;
     ph.G = p->G;
+    ph.grav_theta = p->grav_theta;
     ph.kr = p->kernel == SPH_KERNEL_M6 ? 3.0 : 2.0;
     ph.kr_f = (float)ph.kr;
     return ph;
@@ -343,7 +347,8 @@ size_t sph_workspace_bytes(int64_t n, const sph_params *p)
     BatchView b;
     memset(&b, 0, sizeof b);
     carve_tables(c, b, 1);
-    carve_arrays(c, b, n, 1, p->precision, p->gravity ? gravity_chunks(n) : 0);
+    carve_arrays(c, b, n, 1, p->precision, p->gravity ? gravity_chunks(n, p->grav_theta) : 0,
+                 p->gravity && p->grav_theta > 0);
     return c.off + 256;
 }
 
@@ -395,7 +400,8 @@ int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *st
     c->diag = cv.take<ProbDiag>(1);
     memset(&c->bv, 0, sizeof c->bv);
     carve_tables(cv, c->bv, 1);
-    carve_arrays(cv, c->bv, n, 1, p->precision, p->gravity ? gravity_chunks(n) : 0);
+    carve_arrays(cv, c->bv, n, 1, p->precision, p->gravity ? gravity_chunks(n, p->grav_theta) : 0,
+                 p->gravity && p->grav_theta > 0);
     c->bv.ntot = n;
     c->bv.key_bits = key_bits_for(1);
     c->bv.key_lo = key_low_bits(n);
@@ -404,8 +410,9 @@ int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *st
     c->bv.any_periodic = p->periodic ? 1 : 0;
     c->bv.any_general = (p->av_switch || p->ac_signal || p->gravity) ? 1 : 0;
     c->bv.any_gravity = p->gravity ? 1 : 0;
-    c->bv.grav_blocks = p->gravity ? gravity_blocks(n) : 0;
-    c->bv.grav_split = p->gravity && gravity_chunks(n) > 1;
+    c->bv.grav_blocks = p->gravity ? gravity_blocks(n, p->grav_theta) : 0;
+    c->bv.grav_split = p->gravity && gravity_chunks(n, p->grav_theta) > 1;
+    c->bv.any_grav_tree = p->gravity && p->grav_theta > 0;
     ProbStatic &ps = c->host_ps;
     memset(&ps, 0, sizeof ps);
     ps.x = state->x;
@@ -433,7 +440,7 @@ int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *st
     ps.diag = c->diag;
     ps.lpp = c->lpp;
     ps.ph = phys_of(p);
-    ps.gchunks = p->gravity ? gravity_chunks(n) : 0;
+    ps.gchunks = p->gravity ? gravity_chunks(n, p->grav_theta) : 0;
     // equal masses (the usual SPH set-up; masses never change) let the
     // density lists keep distances only
     if (n > 0) {
@@ -810,16 +817,18 @@ size_t sph_batch_workspace_bytes(sph_ctx *const *ctxs, int nctx)
 {
     if (batch_check(ctxs, nctx) != SPH_OK) return 0;
     long long ntot = 0;
-    int gch = 0;
+    int gch = 0, gtree = 0;
     for (int k = 0; k < nctx; ++k) {
+        const sph_params &q = ctxs[k]->prm;
         ntot += ctxs[k]->n;
-        if (ctxs[k]->prm.gravity && gravity_chunks(ctxs[k]->n) > gch) gch = gravity_chunks(ctxs[k]->n);
+        if (q.gravity && gravity_chunks(ctxs[k]->n, q.grav_theta) > gch) gch = gravity_chunks(ctxs[k]->n, q.grav_theta);
+        if (q.gravity && q.grav_theta > 0) gtree = 1;
     }
     Carver c{nullptr};
     BatchView b;
     memset(&b, 0, sizeof b);
     carve_tables(c, b, nctx);
-    carve_arrays(c, b, ntot, nctx, ctxs[0]->prm.precision, gch);
+    carve_arrays(c, b, ntot, nctx, ctxs[0]->prm.precision, gch, gtree);
     return c.off + 256;
 }
 
@@ -841,7 +850,7 @@ int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, 
     std::vector<long long> bases(nctx + 1);
     int mask = 0, dmask = 0, b_any_isolated = 0, b_any_periodic = 0, b_any_general = 0, b_any_gravity = 0;
     long long grav_blocks = 0;
-    int gch = 0;
+    int gch = 0, gtree = 0;
     for (int k = 0; k < nctx; ++k) {
         tab[k] = ctxs[k]->host_ps;
         tab[k].base = ntot;
@@ -854,8 +863,9 @@ int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, 
         if (tab[k].ph.av_switch || tab[k].ph.ac_signal || tab[k].ph.gravity) b_any_general = 1;
         if (tab[k].ph.gravity) b_any_gravity = 1;
         tab[k].gblk0 = (int)grav_blocks;
-        tab[k].gchunks = tab[k].ph.gravity ? gravity_chunks(ctxs[k]->n) : 0;
-        if (tab[k].ph.gravity) grav_blocks += gravity_blocks(ctxs[k]->n);
+        tab[k].gchunks = tab[k].ph.gravity ? gravity_chunks(ctxs[k]->n, tab[k].ph.grav_theta) : 0;
+        if (tab[k].ph.gravity) grav_blocks += gravity_blocks(ctxs[k]->n, tab[k].ph.grav_theta);
+        if (tab[k].ph.gravity && tab[k].ph.grav_theta > 0) gtree = 1;
         if (tab[k].gchunks > gch) gch = tab[k].gchunks;
     }
     bases[nctx] = ntot;
@@ -863,7 +873,7 @@ int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, 
     BatchView b;
     memset(&b, 0, sizeof b);
     carve_tables(cv, b, nctx);
-    carve_arrays(cv, b, ntot, nctx, prec, gch);
+    carve_arrays(cv, b, ntot, nctx, prec, gch, gtree);
     b.ntot = ntot;
     b.key_bits = key_bits_for(nctx);
     b.key_lo = key_low_bits(ntot);
@@ -875,6 +885,7 @@ int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, 
     b.any_gravity = b_any_gravity;
     b.grav_blocks = grav_blocks;
     b.grav_split = gch > 1;
+    b.any_grav_tree = gtree;
     CU(cudaMemcpyAsync(b.prob, tab.data(), sizeof(ProbStatic) * nctx, cudaMemcpyHostToDevice, st));
     CU(cudaMemcpyAsync(b.prob_base, bases.data(), sizeof(long long) * (nctx + 1), cudaMemcpyHostToDevice, st));
     CU(cudaMemsetAsync(b.dyn, 0, sizeof(ProbDyn) * nctx, st));

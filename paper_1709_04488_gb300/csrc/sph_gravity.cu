@@ -187,12 +187,356 @@ __global__ void __launch_bounds__(256) k_gravity_reduce(BatchView b)
     ps.az[io] += Gm * fz;
 }
 
+// ---------------------------------------------------------------------------
+// Gravity tree walk (Sec. 4.2) over the leaves and 32-ary nodes the pair
+// kernels use.  Each node carries its mass, centre of mass (relative to the
+// key-domain corner), quadrupole Q_ab = sum m (3 d_a d_b - |d|^2 delta_ab)
+// about the centre of mass, particle box, h_max and l^2, l the distance from
+// the centre of mass to the box's farthest corner.  Moments are formed in FP64
+// (leaves from the sorted particles, nodes bottom-up from their children by
+// the parallel-axis shift) and stored in the staging precision; boxes are
+// rounded outwards.
+// ---------------------------------------------------------------------------
+constexpr int kTreeThreads = 128;
+
+__device__ __forceinline__ float4 ldcg4(const float4 *p) { return __ldcg(p); }
+__device__ __forceinline__ dbl4 ldcg4(const dbl4 *p)
+{
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+    const double2 a = __ldcg(q), c = __ldcg(q + 1);
+    dbl4 r;
+    r.x = a.x;
+    r.y = a.y;
+    r.z = c.x;
+    r.w = c.y;
+    return r;
+}
+
+__device__ __forceinline__ float rd_t(double v, float) { return __double2float_rd(v); }
+__device__ __forceinline__ float ru_t(double v, float) { return __double2float_ru(v); }
+__device__ __forceinline__ double rd_t(double v, double) { return v; }
+__device__ __forceinline__ double ru_t(double v, double) { return v; }
+
+template <typename V4>
+__device__ __forceinline__ V4 mk4(double x, double y, double z, double w)
+{
+    V4 r;
+    r.x = x;
+    r.y = y;
+    r.z = z;
+    r.w = w;
+    return r;
+}
+
+// Moments of one warp's set (one entry per lane; M = 0 where a lane holds
+// nothing): centre of mass com, Q about it, box [lo, hi], h_max; written by
+// lane 0 to node g.  `q` is the entry's own quadrupole about its own centre
+// (zero for particles).
+template <typename T>
+__device__ void form_node(double M, const double (&x)[3], const double (&q)[6], const double (&lo)[3],
+                          const double (&hi)[3], double hm, typename Vec4<T>::type *g)
+{
+    using V4 = typename Vec4<T>::type;
+    const double Mt = warp_sum(M);
+    double c[3];
+    for (int a = 0; a < 3; ++a) c[a] = warp_sum(M * x[a]) / Mt;
+    const double d[3] = {M > 0 ? x[0] - c[0] : 0.0, M > 0 ? x[1] - c[1] : 0.0, M > 0 ? x[2] - c[2] : 0.0};
+    const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const double Q[6] = {warp_sum(q[0] + M * (3.0 * d[0] * d[0] - d2)), warp_sum(q[1] + M * (3.0 * d[0] * d[1])),
+                         warp_sum(q[2] + M * (3.0 * d[0] * d[2])), warp_sum(q[3] + M * (3.0 * d[1] * d[1] - d2)),
+                         warp_sum(q[4] + M * (3.0 * d[1] * d[2])), warp_sum(q[5] + M * (3.0 * d[2] * d[2] - d2))};
+    double L[3], H[3];
+    for (int a = 0; a < 3; ++a) {
+        L[a] = warp_min(lo[a]);
+        H[a] = warp_max(hi[a]);
+    }
+    const double hmax = warp_max(hm);
+    double l2 = 0.0;  // farthest corner of the box from the centre of mass
+    for (int a = 0; a < 3; ++a) {
+        const double e = fmax(c[a] - L[a], H[a] - c[a]);
+        l2 += e * e;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        const T t = T(0);
+        g[0] = mk4<V4>(c[0], c[1], c[2], Mt);
+        g[1] = mk4<V4>(Q[0], Q[1], Q[2], Q[3]);
+        g[2] = mk4<V4>(Q[4], Q[5], ru_t(l2, t), ru_t(hmax, t));
+        g[3] = mk4<V4>(rd_t(L[0], t), rd_t(L[1], t), rd_t(L[2], t), 0.0);
+        g[4] = mk4<V4>(ru_t(H[0], t), ru_t(H[1], t), ru_t(H[2], t), 0.0);
+    }
+}
+
+// Leaf moments from the sorted FP64 particles, then the nodes above: the warp
+// whose arrival completes a node's children forms it (the arrival counters
+// are the tree build's, zero between kernels, and are cleared again here).
+template <typename T>
+__global__ void __launch_bounds__(256) k_grav_moments(BatchView b)
+{
+    using V4 = typename Vec4<T>::type;
+    const int lane = threadIdx.x & 31;
+    const int nleaf = b.counters[0];
+    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int leaf = w0; leaf < nleaf; leaf += nw) {
+        const int p = b.leaf_pid[leaf];
+        const ProbStatic &ps = b.prob[p];
+        if (!(ps.ph.gravity && ps.ph.grav_theta > 0)) continue;
+        const ProbDyn &d = b.dyn[p];
+        const int st = b.leaf_start[leaf], cnt = b.leaf_start[leaf + 1] - st;
+        double M = 0.0, x[3] = {0.0, 0.0, 0.0}, lo[3], hi[3], hm = 0.0;
+        const double q0[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        if (lane < cnt) {
+            const int i = st + lane;
+            x[0] = b.sx[i] - d.dom_lo[0];
+            x[1] = b.sy[i] - d.dom_lo[1];
+            x[2] = b.sz[i] - d.dom_lo[2];
+            M = b.sm[i];
+            hm = b.sh[i];
+            for (int a = 0; a < 3; ++a) lo[a] = hi[a] = x[a];
+        } else {
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = INFINITY;
+                hi[a] = -INFINITY;
+            }
+        }
+        form_node<T>(M, x, q0, lo, hi, hm, (V4 *)b.gnode[0] + 5LL * leaf);
+        // upwards
+        int k = leaf - d.node_off[0];
+        for (int lvl = 0; lvl < d.top_level; ++lvl) {
+            const int parent = k / kBranch;
+            const int nch = min(kBranch, d.node_cnt[lvl] - parent * kBranch);
+            int *ctr = b.node_ctr[lvl + 1] + d.node_off[lvl + 1] + parent;
+            int old = 0;
+            if (lane == 0) {
+                __threadfence();  // this warp's node before its arrival
+                old = atomicAdd(ctr, 1);
+            }
+            old = __shfl_sync(0xffffffffu, old, 0);
+            if (old != nch - 1) break;
+            if (lane == 0) *ctr = 0;
+            __threadfence();
+            double Mc = 0.0, xc[3] = {0.0, 0.0, 0.0}, qc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0}, lc[3], hc[3], hmc = 0.0;
+            if (lane < nch) {
+                const V4 *g = (const V4 *)b.gnode[lvl] + 5LL * (d.node_off[lvl] + parent * kBranch + lane);
+                const V4 A = ldcg4(g), B = ldcg4(g + 1), C = ldcg4(g + 2), L = ldcg4(g + 3), H = ldcg4(g + 4);
+                Mc = A.w;
+                xc[0] = A.x;
+                xc[1] = A.y;
+                xc[2] = A.z;
+                qc[0] = B.x;
+                qc[1] = B.y;
+                qc[2] = B.z;
+                qc[3] = B.w;
+                qc[4] = C.x;
+                qc[5] = C.y;
+                hmc = C.w;
+                lc[0] = L.x;
+                lc[1] = L.y;
+                lc[2] = L.z;
+                hc[0] = H.x;
+                hc[1] = H.y;
+                hc[2] = H.z;
+            } else {
+                for (int a = 0; a < 3; ++a) {
+                    lc[a] = INFINITY;
+                    hc[a] = -INFINITY;
+                }
+            }
+            form_node<T>(Mc, xc, qc, lc, hc, hmc, (V4 *)b.gnode[lvl + 1] + 5LL * (d.node_off[lvl + 1] + parent));
+            k = parent;
+        }
+    }
+}
+
+// Acceleration (per unit G) at offset r from a node's centre of mass:
+// -M r/|r|^3 + Q r/|r|^5 - (5/2)(r.Q.r) r/|r|^7.
+template <typename T>
+__device__ __forceinline__ void multipole_acc(T rx, T ry, T rz, T M, const T (&Q)[6], TwoSumAcc<T> &ax,
+                                              TwoSumAcc<T> &ay, TwoSumAcc<T> &az)
+{
+    const T r2 = rx * rx + ry * ry + rz * rz;
+    const T rinv = rsqrt_t(r2), rinv2 = rinv * rinv, rinv3 = rinv2 * rinv, rinv5 = rinv3 * rinv2;
+    const T qx = Q[0] * rx + Q[1] * ry + Q[2] * rz;
+    const T qy = Q[1] * rx + Q[3] * ry + Q[4] * rz;
+    const T qz = Q[2] * rx + Q[4] * ry + Q[5] * rz;
+    const T rqr = rx * qx + ry * qy + rz * qz;
+    const T k = -M * rinv3 - T(2.5) * rqr * rinv5 * rinv2;
+    ax.add(k * rx + qx * rinv5);
+    ay.add(k * ry + qy * rinv5);
+    az.add(k * rz + qz * rinv5);
+}
+
+// One warp per leaf of a problem with grav_theta > 0.  The walk classifies the
+// children of each visited node, one per lane: used through its multipole
+// (the opening criterion holds for the whole leaf box and no pair with it is
+// softened), opened, or absent.  Used nodes and the particles of opened
+// leaves are staged in shared memory and summed at once; with several lanes
+// per particle each lane takes every lpp-th staged entry and the lanes'
+// sums are added in a fixed order at the end.
+template <typename T>
+__global__ void __launch_bounds__(kTreeThreads) k_gravity_tree(BatchView b)
+{
+    using V4 = typename Vec4<T>::type;
+    using P = typename GravVec<T>::P;
+    using H = typename GravVec<T>::H;
+    constexpr int kW = kTreeThreads / 32;
+    __shared__ P s_p[kW][32];  // partner (x, m) or node (com, M)
+    __shared__ H s_h[kW][32];  // partner (h, 1/h)
+    __shared__ T s_q[kW][32][6];  // node Q
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const int nleaf = b.counters[0];
+    const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int leaf = w0; leaf < nleaf; leaf += nw) {
+        const int p = b.leaf_pid[leaf];
+        const ProbStatic &ps = b.prob[p];
+        if (!(ps.ph.gravity && ps.ph.grav_theta > 0)) continue;
+        const ProbDyn &d = b.dyn[p];
+        const double *ref = d.dom_lo;
+        const int lpp = ps.lpp, S = kBranch / lpp;
+        const int pi = lane % S, sub = lane / S;
+        const int st = b.leaf_start[leaf], cnt = b.leaf_start[leaf + 1] - st;
+        const V4 *gl = (const V4 *)b.gnode[0] + 5LL * leaf;
+        const V4 GL = gl[3], GH = gl[4];
+        const T hleaf = gl[2].w;
+        const T blo[3] = {GL.x, GL.y, GL.z}, bhi[3] = {GH.x, GH.y, GH.z};
+        // this lane's particle (lanes beyond the leaf sit at its box corner)
+        T xi = blo[0], yi = blo[1], zi = blo[2], hi = T(1), hinv = T(1);
+        if (pi < cnt) {
+            const int i = st + pi;
+            xi = (T)(b.sx[i] - ref[0]);
+            yi = (T)(b.sy[i] - ref[1]);
+            zi = (T)(b.sz[i] - ref[2]);
+            hi = (T)b.sh[i];
+            hinv = T(1) / hi;
+        }
+        const T th2 = (T)(ps.ph.grav_theta * ps.ph.grav_theta);
+        TwoSumAcc<T> ax{T(0), T(0)}, ay{T(0), T(0)}, az{T(0), T(0)};
+        // classify node g of level `lvl`, stage it when it is used; returns 1 used, 2 opened
+        auto visit = [&](int level, int first, int count) -> unsigned {
+            const int c = first + lane;
+            int cls = 0;
+            V4 A, B, C;
+            if (lane < count) {
+                const V4 *g = (const V4 *)b.gnode[level] + 5LL * c;
+                A = g[0];
+                B = g[1];
+                C = g[2];
+                const V4 L = g[3], U = g[4];
+                const T cm[3] = {A.x, A.y, A.z}, nl[3] = {L.x, L.y, L.z}, nh[3] = {U.x, U.y, U.z};
+                T d2 = T(0), g2 = T(0);
+                for (int a = 0; a < 3; ++a) {
+                    const T da = fmax(fmax(blo[a] - cm[a], cm[a] - bhi[a]), T(0));
+                    const T ga = fmax(fmax(nl[a] - bhi[a], blo[a] - nh[a]), T(0));
+                    d2 += da * da;
+                    g2 += ga * ga;
+                }
+                const T soft = T(2) * fmax(hleaf, C.w);
+                cls = (th2 > T(0) && d2 * th2 >= C.z && g2 >= soft * soft) ? 1 : 2;
+            }
+            const unsigned um = __ballot_sync(0xffffffffu, cls == 1);
+            if (um) {  // sum the used nodes
+                if (cls == 1) {
+                    const int slot = __popc(um & ((1u << lane) - 1u));
+                    P e;
+                    e.x = A.x;
+                    e.y = A.y;
+                    e.z = A.z;
+                    e.w = A.w;
+                    s_p[wi][slot] = e;
+                    s_q[wi][slot][0] = B.x;
+                    s_q[wi][slot][1] = B.y;
+                    s_q[wi][slot][2] = B.z;
+                    s_q[wi][slot][3] = B.w;
+                    s_q[wi][slot][4] = C.x;
+                    s_q[wi][slot][5] = C.y;
+                }
+                __syncwarp();
+                const int nu = __popc(um);
+                for (int e = sub; e < nu; e += lpp) {
+                    const P q = s_p[wi][e];
+                    const T Q[6] = {s_q[wi][e][0], s_q[wi][e][1], s_q[wi][e][2],
+                                    s_q[wi][e][3], s_q[wi][e][4], s_q[wi][e][5]};
+                    multipole_acc(xi - q.x, yi - q.y, zi - q.z, q.w, Q, ax, ay, az);
+                }
+                __syncwarp();
+            }
+            return __ballot_sync(0xffffffffu, cls == 2);
+        };
+        // sum the particles of the opened leaves first + bits of om, pair by pair
+        auto direct = [&](unsigned om, int first) {
+            while (om) {
+                const int c = __ffs(om) - 1;
+                om &= om - 1u;
+                const int L = first + c, ls = b.leaf_start[L], lc = b.leaf_start[L + 1] - ls;
+                if (lane < lc) {
+                    const int j = ls + lane;
+                    P e;
+                    H f;
+                    e.x = (T)(b.sx[j] - ref[0]);
+                    e.y = (T)(b.sy[j] - ref[1]);
+                    e.z = (T)(b.sz[j] - ref[2]);
+                    e.w = (T)b.sm[j];
+                    f.x = (T)b.sh[j];
+                    f.y = T(1) / f.x;
+                    s_p[wi][lane] = e;
+                    s_h[wi][lane] = f;
+                }
+                __syncwarp();
+                for (int e = sub; e < lc; e += lpp) grav_pair(xi, yi, zi, T(1), hi, hinv, s_p[wi][e], s_h[wi][e], ax, ay, az);
+                __syncwarp();
+            }
+        };
+        const int top = d.top_level;
+        unsigned mask[kMaxLevels + 1];
+        int base[kMaxLevels + 1];
+        {
+            const unsigned om = visit(top, d.node_off[top], d.node_cnt[top]);
+            if (top == 0) direct(om, d.node_off[0]);
+            mask[top] = om;
+            base[top] = 0;
+        }
+        int lvl = top;
+        while (top > 0) {
+            const unsigned m = mask[lvl];
+            if (m == 0u) {
+                if (++lvl > top) break;
+                continue;
+            }
+            const int c = __ffs(m) - 1;
+            mask[lvl] = m & (m - 1u);
+            const int node = base[lvl] + c;
+            const int cnt_ch = min(kBranch, d.node_cnt[lvl - 1] - node * kBranch);
+            const unsigned om = visit(lvl - 1, d.node_off[lvl - 1] + node * kBranch, cnt_ch);
+            if (lvl == 1) {
+                direct(om, d.node_off[0] + node * kBranch);
+                continue;
+            }
+            --lvl;
+            base[lvl] = node * kBranch;
+            mask[lvl] = om;
+        }
+        // the lanes of each particle add their sums in a fixed order
+        double gx = (double)ax.s + (double)ax.c, gy = (double)ay.s + (double)ay.c, gz = (double)az.s + (double)az.c;
+        for (int o = S; o < kBranch; o <<= 1) {
+            gx += __shfl_xor_sync(0xffffffffu, gx, o);
+            gy += __shfl_xor_sync(0xffffffffu, gy, o);
+            gz += __shfl_xor_sync(0xffffffffu, gz, o);
+        }
+        if (sub == 0 && pi < cnt) {
+            const long long io = (long long)b.perm[st + pi] - ps.base;
+            ps.ax[io] += ps.ph.G * gx;
+            ps.ay[io] += ps.ph.G * gy;
+            ps.az[io] += ps.ph.G * gz;
+        }
+    }
+}
+
 }  // namespace
 
 // C partner ranges for N particles: enough blocks to fill the GPU (about 8 per
 // SM), at most 16 ranges and at least 4096 partners per range.
-int gravity_chunks(long long n)
+int gravity_chunks(long long n, double theta)
 {
+    if (theta > 0) return 0;  // the tree walk serves this problem
     const long long ib = (n + 2 * kGravThreads - 1) / (2 * kGravThreads);
     long long c = ib > 0 ? (1216 + ib - 1) / ib : 1;
     if (c > 16) c = 16;
@@ -200,18 +544,31 @@ int gravity_chunks(long long n)
     return c < 1 ? 1 : (int)c;
 }
 
-long long gravity_blocks(long long n)
+long long gravity_blocks(long long n, double theta)
 {
-    return (n + 2 * kGravThreads - 1) / (2 * kGravThreads) * gravity_chunks(n);
+    return (n + 2 * kGravThreads - 1) / (2 * kGravThreads) * gravity_chunks(n, theta);
 }
 
 void launch_gravity(const BatchView &b, int precision, cudaStream_t st)
 {
-    if (!b.any_gravity || b.grav_blocks <= 0) return;
-    if (precision == SPH_PREC_FP64) k_gravity<double><<<(unsigned)b.grav_blocks, kGravThreads, 0, st>>>(b);
-    else k_gravity<float><<<(unsigned)b.grav_blocks, kGravThreads, 0, st>>>(b);
+    if (!b.any_gravity) return;
+    if (b.grav_blocks > 0) {
+        if (precision == SPH_PREC_FP64) k_gravity<double><<<(unsigned)b.grav_blocks, kGravThreads, 0, st>>>(b);
+        else k_gravity<float><<<(unsigned)b.grav_blocks, kGravThreads, 0, st>>>(b);
+    }
     if (b.grav_split)
         k_gravity_reduce<<<(unsigned)((b.ntot + 255) / 256), 256, 0, st>>>(b);
+    if (b.any_grav_tree) {
+        static int sms = 0;
+        if (!sms) sms = dev_info().sm_count;
+        if (precision == SPH_PREC_FP64) {
+            k_grav_moments<double><<<sms * 8, 256, 0, st>>>(b);
+            k_gravity_tree<double><<<sms * 8, kTreeThreads, 0, st>>>(b);
+        } else {
+            k_grav_moments<float><<<sms * 8, 256, 0, st>>>(b);
+            k_gravity_tree<float><<<sms * 8, kTreeThreads, 0, st>>>(b);
+        }
+    }
 }
 
 }  // namespace sph

@@ -68,6 +68,7 @@ struct PhysParams {
     int gravity;         // self-gravity (isolated, M4)
     int pad3_;
     double G;
+    double grav_theta;   // gravity: tree opening angle (0: direct summation)
 };
 
 // Per-problem diagnostics and persistent scalars; lives in the context's own
@@ -164,7 +165,12 @@ struct BatchView {
     int any_gravity;             // some problem has self-gravity (direct-sum launch)
     long long grav_blocks;       // blocks of the direct-sum launch (all gravity problems)
     int grav_split;              // some gravity problem splits its partners (partial sums to reduce)
+    int any_grav_tree;           // some gravity problem walks the tree (grav_theta > 0)
     double *gpart;               // gravity: partial forces [chunk][ntot][3] of split problems
+    // gravity tree: five Vec4 per node of each level (centre of mass relative
+    // to the key-domain corner and mass; Q_xx, Q_xy, Q_xz, Q_yy; Q_yz, Q_zz,
+    // l^2, h_max; box min; box max), element type float4 or dbl4
+    void *gnode[kMaxLevels + 1];
     ProbStatic *prob;            // [nprob]
     ProbDyn *dyn;                // [nprob]
     long long *prob_base;        // [nprob + 1] base offsets (for searches)
@@ -298,8 +304,9 @@ cudaError_t launch_refit(const BatchView &b, int precision, cudaStream_t st);
 cudaError_t launch_density(const BatchView &b, int precision, int use_pred, cudaStream_t st);
 cudaError_t launch_forces(const BatchView &b, int precision, cudaStream_t st);
 void launch_gravity(const BatchView &b, int precision, cudaStream_t st);  // direct-sum self-gravity
-long long gravity_blocks(long long n);  // blocks of one problem (particle blocks x partner ranges)
-int gravity_chunks(long long n);        // partner ranges of one problem
+// direct-sum launch of one problem (none when it walks the tree, theta > 0):
+long long gravity_blocks(long long n, double theta);  // blocks (particle blocks x partner ranges)
+int gravity_chunks(long long n, double theta);        // partner ranges
 cudaError_t launch_kick_drift(const BatchView &b, double dt_host, cudaStream_t st);  // also selects dt, resets diagnostics
 cudaError_t launch_kick_close(const BatchView &b, int do_kick, int forces_ran, cudaStream_t st);
 cudaError_t launch_reset_step(const BatchView &b, int mode, cudaStream_t st);  // mode 1 full, 2 forces only
@@ -321,7 +328,8 @@ struct Carver {
     }
 };
 int fail(int code, const char *fmt, ...);  // records the thread's error message, returns code
-void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precision, int grav_chunks = 0);
+void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precision, int grav_chunks = 0,
+                  int grav_tree = 0);
 void carve_tables(Carver &c, BatchView &b, int nprob);
 int key_bits_for(int nprob);
 int key_low_bits(long long ntot);  // Morton bits left unsorted (cleared) for ntot particles

@@ -90,7 +90,8 @@ extern "C" int sph_density_forces_noalloc(const sph_params *p, int64_t n, const 
     BatchView b;
     memset(&b, 0, sizeof b);
     carve_tables(c, b, 1);
-    carve_arrays(c, b, n, 1, p->precision, p->gravity ? gravity_chunks(n) : 0);
+    carve_arrays(c, b, n, 1, p->precision, p->gravity ? gravity_chunks(n, p->grav_theta) : 0,
+                 p->gravity && p->grav_theta > 0);
     if (c.off > kNoAllocBytes) return fail(SPH_ENOSPACE, "fixed scratch too small for %lld particles", (long long)n);
     const int lpp = lpp_of(p, n);
     b.ntot = n;
@@ -102,8 +103,9 @@ extern "C" int sph_density_forces_noalloc(const sph_params *p, int64_t n, const 
     b.any_periodic = p->periodic ? 1 : 0;
     b.any_general = (p->av_switch || p->ac_signal || p->gravity) ? 1 : 0;
     b.any_gravity = p->gravity ? 1 : 0;
-    b.grav_blocks = p->gravity ? gravity_blocks(n) : 0;
-    b.grav_split = p->gravity && gravity_chunks(n) > 1;
+    b.grav_blocks = p->gravity ? gravity_blocks(n, p->grav_theta) : 0;
+    b.grav_split = p->gravity && gravity_chunks(n, p->grav_theta) > 1;
+    b.any_grav_tree = p->gravity && p->grav_theta > 0;
     ProbStatic ps;
     memset(&ps, 0, sizeof ps);
     ps.x = state->x;
@@ -131,7 +133,7 @@ extern "C" int sph_density_forces_noalloc(const sph_params *p, int64_t n, const 
     ps.diag = diag;
     ps.lpp = lpp;
     ps.ph = phys_of(p);
-    ps.gchunks = p->gravity ? gravity_chunks(n) : 0;
+    ps.gchunks = p->gravity ? gravity_chunks(n, p->grav_theta) : 0;
     cudaStream_t st = (cudaStream_t)stream;
     const int prec = p->precision;
     cudaError_t e;

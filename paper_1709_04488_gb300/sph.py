@@ -54,6 +54,7 @@ class Params(C.Structure):
         ("av_decay", C.c_double),
         ("gravity", C.c_int),
         ("G", C.c_double),
+        ("grav_theta", C.c_double),
     ]
 
 
