@@ -39,6 +39,7 @@ WORKLOAD = WORKLOADS["sod"]
 FLOPS_DENSITY_PAIR = 19   # per pair per Newton-Raphson pass (q, f, f', two accumulations)
 FLOPS_FORCE_PAIR = 101    # per ordered pair (pressure, viscosity, conduction, energy, TwoSum-compensated m a)
 FLOPS_GRAVITY_PAIR = 38   # per ordered pair beyond the softening (r, 1/r^3 weight, TwoSum-compensated F)
+FLOPS_GRAVITY_NODE = 64   # per (particle, node) multipole term (r, powers of 1/r, Q r, r.Q.r, TwoSum-compensated a)
 GRAVITY_N = 65536         # self-gravity measurement: isolated cloud of this many particles
 GRAVITY_TREE_N = 1_000_000  # the tree walk's larger cloud
 GRAVITY_THETA = 0.5       # opening angle of the tree-walk measurements
@@ -461,10 +462,15 @@ def run_ours(args):
                 S.check(S.sph_forces(ptr.ctx), "sph_forces")
             S.check(S.sph_run(ptr.ctx, 3), "sph_run")
             mst, stt, _, _ = time_steps(S, ptr, stream, torch, 5, flush, stage=True)
+            gms = float(np.mean(np.array(stt), axis=0)[S.STAGES.index("gravity")])
+            dg = ptr.diagnostics()
+            tflop = dg.grav_pairs * FLOPS_GRAVITY_PAIR + dg.grav_nodes * FLOPS_GRAVITY_NODE
             grav["tree"].append({"workload": f"cloud_{nt}: isolated, isothermal, G=1, tree walk theta={GRAVITY_THETA}",
                                  "ms_per_step": float(np.mean(mst)), "value": nt * len(mst) / (np.sum(mst) * 1e-3),
-                                 "unit": UNIT,
-                                 "gravity_stage_ms": float(np.mean(np.array(stt), axis=0)[S.STAGES.index("gravity")])})
+                                 "unit": UNIT, "gravity_stage_ms": gms,
+                                 "pairs_per_particle": dg.grav_pairs / nt, "nodes_per_particle": dg.grav_nodes / nt,
+                                 "achieved_tflops": tflop / (gms * 1e-3) / 1e12,
+                                 "frac": tflop / (gms * 1e-3) / 1e12 / peak})
             ptr.close()
 
     diag = prob.diagnostics()

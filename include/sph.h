@@ -191,6 +191,8 @@ typedef struct {
     int32_t wrap_leaves;   /* leaves of the last density + force passes whose pair vectors
                               needed minimum-image wraps (periodic; few particles per
                               box length)                                                  */
+    int64_t grav_pairs;    /* gravity tree walk, last force pass: (i,j) pair terms summed  */
+    int64_t grav_nodes;    /* gravity tree walk, last force pass: (i,node) multipole terms */
 } sph_diag;
 
 typedef struct sph_ctx sph_ctx;

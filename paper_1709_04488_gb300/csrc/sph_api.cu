@@ -70,6 +70,8 @@ void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precis
     b.sal = c.take<char>(v4 / 4 * n);
     b.szg = c.take<char>(v4 / 4 * n);
     b.gpart = grav_chunks > 1 ? c.take<double>(3LL * grav_chunks * n) : nullptr;
+    b.gpos = grav_tree ? (void *)c.take<char>(v4 * n) : nullptr;
+    b.gh = grav_tree ? (void *)c.take<char>(v4 / 2 * n) : nullptr;
     b.flag = c.take<unsigned>(n);
     const long long ml = leaves_upper_bound(n);
     b.max_leaves = (int)ml;
@@ -759,6 +761,8 @@ int sph_diagnostics(sph_ctx *c, sph_diag *out)
     out->unconverged = d.unconverged;
     out->walk_reused = d.walk_reused;
     out->wrap_leaves = d.wrap_leaves;
+    out->grav_pairs = d.grav_pairs;
+    out->grav_nodes = d.grav_nodes;
     return SPH_OK;
 }
 

@@ -198,6 +198,7 @@ __global__ void __launch_bounds__(256) k_gravity_reduce(BatchView b)
 // rounded outwards.
 // ---------------------------------------------------------------------------
 constexpr int kTreeThreads = 128;
+constexpr int kTreeStage = 128;  // partner particles staged per warp at once
 
 __device__ __forceinline__ float4 ldcg4(const float4 *p) { return __ldcg(p); }
 __device__ __forceinline__ dbl4 ldcg4(const dbl4 *p)
@@ -292,6 +293,19 @@ __global__ void __launch_bounds__(256) k_grav_moments(BatchView b)
             M = b.sm[i];
             hm = b.sh[i];
             for (int a = 0; a < 3; ++a) lo[a] = hi[a] = x[a];
+            // the walk's copy of the particle in the staging precision
+            using P = typename GravVec<T>::P;
+            using H = typename GravVec<T>::H;
+            P e;
+            H f;
+            e.x = (T)x[0];
+            e.y = (T)x[1];
+            e.z = (T)x[2];
+            e.w = (T)M;
+            f.x = (T)hm;
+            f.y = T(1) / f.x;
+            ((P *)b.gpos)[i] = e;
+            ((H *)b.gh)[i] = f;
         } else {
             for (int a = 0; a < 3; ++a) {
                 lo[a] = INFINITY;
@@ -379,9 +393,10 @@ __global__ void __launch_bounds__(kTreeThreads) k_gravity_tree(BatchView b)
     using P = typename GravVec<T>::P;
     using H = typename GravVec<T>::H;
     constexpr int kW = kTreeThreads / 32;
-    __shared__ P s_p[kW][32];  // partner (x, m) or node (com, M)
-    __shared__ H s_h[kW][32];  // partner (h, 1/h)
-    __shared__ T s_q[kW][32][6];  // node Q
+    __shared__ P s_p[kW][kTreeStage];  // partner (x, m) or node (com, M)
+    __shared__ H s_h[kW][kTreeStage];  // partner (h, 1/h)
+    __shared__ T s_q[kW][32][6];       // node Q
+    __shared__ int s_off[kW][32], s_st[kW][32];  // opened leaves: first staged entry, first particle
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
     const int nleaf = b.counters[0];
     const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
@@ -390,7 +405,6 @@ __global__ void __launch_bounds__(kTreeThreads) k_gravity_tree(BatchView b)
         const ProbStatic &ps = b.prob[p];
         if (!(ps.ph.gravity && ps.ph.grav_theta > 0)) continue;
         const ProbDyn &d = b.dyn[p];
-        const double *ref = d.dom_lo;
         const int lpp = ps.lpp, S = kBranch / lpp;
         const int pi = lane % S, sub = lane / S;
         const int st = b.leaf_start[leaf], cnt = b.leaf_start[leaf + 1] - st;
@@ -401,13 +415,15 @@ __global__ void __launch_bounds__(kTreeThreads) k_gravity_tree(BatchView b)
         // this lane's particle (lanes beyond the leaf sit at its box corner)
         T xi = blo[0], yi = blo[1], zi = blo[2], hi = T(1), hinv = T(1);
         if (pi < cnt) {
-            const int i = st + pi;
-            xi = (T)(b.sx[i] - ref[0]);
-            yi = (T)(b.sy[i] - ref[1]);
-            zi = (T)(b.sz[i] - ref[2]);
-            hi = (T)b.sh[i];
-            hinv = T(1) / hi;
+            const P e = ((const P *)b.gpos)[st + pi];
+            const H f = ((const H *)b.gh)[st + pi];
+            xi = e.x;
+            yi = e.y;
+            zi = e.z;
+            hi = f.x;
+            hinv = f.y;
         }
+        long long npair = 0, nnode = 0;  // terms this lane summed
         const T th2 = (T)(ps.ph.grav_theta * ps.ph.grav_theta);
         TwoSumAcc<T> ax{T(0), T(0)}, ay{T(0), T(0)}, az{T(0), T(0)};
         // classify node g of level `lvl`, stage it when it is used; returns 1 used, 2 opened
@@ -451,6 +467,7 @@ __global__ void __launch_bounds__(kTreeThreads) k_gravity_tree(BatchView b)
                 }
                 __syncwarp();
                 const int nu = __popc(um);
+                if (pi < cnt) nnode += (nu - sub + lpp - 1) / lpp;
                 for (int e = sub; e < nu; e += lpp) {
                     const P q = s_p[wi][e];
                     const T Q[6] = {s_q[wi][e][0], s_q[wi][e][1], s_q[wi][e][2],
@@ -461,27 +478,35 @@ __global__ void __launch_bounds__(kTreeThreads) k_gravity_tree(BatchView b)
             }
             return __ballot_sync(0xffffffffu, cls == 2);
         };
-        // sum the particles of the opened leaves first + bits of om, pair by pair
+        // sum the particles of the opened leaves first + bits of om pair by
+        // pair, staged kTreeStage at a time across leaves
         auto direct = [&](unsigned om, int first) {
-            while (om) {
-                const int c = __ffs(om) - 1;
-                om &= om - 1u;
-                const int L = first + c, ls = b.leaf_start[L], lc = b.leaf_start[L + 1] - ls;
-                if (lane < lc) {
-                    const int j = ls + lane;
-                    P e;
-                    H f;
-                    e.x = (T)(b.sx[j] - ref[0]);
-                    e.y = (T)(b.sy[j] - ref[1]);
-                    e.z = (T)(b.sz[j] - ref[2]);
-                    e.w = (T)b.sm[j];
-                    f.x = (T)b.sh[j];
-                    f.y = T(1) / f.x;
-                    s_p[wi][lane] = e;
-                    s_h[wi][lane] = f;
+            if (!om) return;
+            const bool op = (om >> lane) & 1u;
+            const int ls = op ? b.leaf_start[first + lane] : 0;
+            const int lc = op ? b.leaf_start[first + lane + 1] - ls : 0;
+            const int inc = warp_incl_scan<int>(lc);
+            const int total = __shfl_sync(0xffffffffu, inc, 31);
+            s_off[wi][lane] = inc - lc;
+            s_st[wi][lane] = ls;
+            __syncwarp();
+            for (int cb = 0; cb < total; cb += kTreeStage) {
+                const int nst = min(kTreeStage, total - cb);
+                for (int e = lane; e < nst; e += 32) {
+                    const int f = cb + e;
+                    int lo = 0, hi2 = 31;  // last opened leaf whose first entry is <= f
+                    while (lo < hi2) {
+                        const int mid = (lo + hi2 + 1) >> 1;
+                        if (s_off[wi][mid] <= f) lo = mid;
+                        else hi2 = mid - 1;
+                    }
+                    const int j = s_st[wi][lo] + (f - s_off[wi][lo]);
+                    s_p[wi][e] = ((const P *)b.gpos)[j];
+                    s_h[wi][e] = ((const H *)b.gh)[j];
                 }
                 __syncwarp();
-                for (int e = sub; e < lc; e += lpp) grav_pair(xi, yi, zi, T(1), hi, hinv, s_p[wi][e], s_h[wi][e], ax, ay, az);
+                if (pi < cnt) npair += (nst - sub + lpp - 1) / lpp;
+                for (int e = sub; e < nst; e += lpp) grav_pair(xi, yi, zi, T(1), hi, hinv, s_p[wi][e], s_h[wi][e], ax, ay, az);
                 __syncwarp();
             }
         };
@@ -526,6 +551,13 @@ __global__ void __launch_bounds__(kTreeThreads) k_gravity_tree(BatchView b)
             ps.ax[io] += ps.ph.G * gx;
             ps.ay[io] += ps.ph.G * gy;
             ps.az[io] += ps.ph.G * gz;
+        }
+        // self pairs (r = 0) add nothing and are not counted
+        npair = warp_sum(npair) - cnt;
+        nnode = warp_sum(nnode);
+        if (lane == 0) {
+            atomicAdd((unsigned long long *)&ps.diag->grav_pairs, (unsigned long long)npair);
+            atomicAdd((unsigned long long *)&ps.diag->grav_nodes, (unsigned long long)nnode);
         }
     }
 }

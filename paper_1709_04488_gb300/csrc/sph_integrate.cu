@@ -21,6 +21,7 @@ __device__ void reset_diag(const BatchView &b, int p, int mode)
     ProbDiag *d = b.prob[p].diag;
     d->dt_min_bits = 0x7ff0000000000000ull;  // +inf
     d->force_pairs = 0;
+    d->grav_pairs = d->grav_nodes = 0;
     if (mode == 2) return;
     d->wrap_leaves = 0;
     d->mass = 0;

@@ -91,6 +91,7 @@ struct ProbDiag {
     int reuse_backoff;   // length of the next hold (doubles while the records keep failing)
     int wrap_leaves;     // leaves of the last passes put on the wrap list
     int pad_;
+    long long grav_pairs, grav_nodes;  // gravity tree walk: pair and multipole terms
 };
 
 // Host-written description of one problem inside a batch.
@@ -171,6 +172,8 @@ struct BatchView {
     // to the key-domain corner and mass; Q_xx, Q_xy, Q_xz, Q_yy; Q_yz, Q_zz,
     // l^2, h_max; box min; box max), element type float4 or dbl4
     void *gnode[kMaxLevels + 1];
+    void *gpos;                  // gravity tree: (x - corner, m) per sorted particle, Vec4
+    void *gh;                    // gravity tree: (h, 1/h) per sorted particle, float2 or double2
     ProbStatic *prob;            // [nprob]
     ProbDyn *dyn;                // [nprob]
     long long *prob_base;        // [nprob + 1] base offsets (for searches)

@@ -90,6 +90,8 @@ class Diag(C.Structure):
         ("unconverged", C.c_int32),
         ("walk_reused", C.c_int32),
         ("wrap_leaves", C.c_int32),
+        ("grav_pairs", C.c_int64),
+        ("grav_nodes", C.c_int64),
     ]
 
     def as_dict(self):

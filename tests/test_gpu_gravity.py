@@ -185,7 +185,9 @@ def _gpu_gravity(S, a, p, prec, theta, lpp=0):
     prob = S.Problem(a, S.make_params(prec, **p, **GR, grav_theta=theta, lanes_per_particle=lpp))
     prob.density_h()
     prob.forces()
-    return prob.numpy()
+    out = prob.numpy()
+    out["diag"] = prob.diagnostics()
+    return out
 
 
 @pytest.mark.parametrize("prec,lpp", [("mixed", 0), ("mixed", 1), ("mixed", 4), ("fp64", 0)])
@@ -200,6 +202,9 @@ def test_tree_with_tiny_theta_is_the_direct_sum(S, oracle_mod, prec, lpp):
     ra = _acc({"ax": ref.ax, "ay": ref.ay, "az": ref.az})
     arms = np.sqrt(np.mean(np.sum(ra ** 2, 1)))
     assert np.max(np.linalg.norm(_acc(g) - ra, axis=1)) < (1e-12 if fp64 else 1e-4) * arms
+    # every other particle once: as a pair term or as a one-particle leaf's monopole
+    n = len(a["x"])
+    assert g["diag"].grav_pairs + g["diag"].grav_nodes == n * (n - 1)
 
 
 @pytest.mark.parametrize("prec,theta", [("mixed", 0.5), ("fp64", 0.5), ("fp64", 1.0), ("mixed", 0.3)])
