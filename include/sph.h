@@ -146,6 +146,9 @@ typedef struct {
                               farthest corner) and no pair with it is softened (boxes
                               at least 2 max h apart); other nodes are opened, opened
                               leaves summed pair by pair.  Outside [0, 1]: SPH_EINVAL. */
+    double c_grav;         /* gravity: acceleration condition of Eq. SPH_DTACCEL, the
+                              step is also at most c_grav sqrt(h_i / |a_i|) (default 0.5;
+                              must be > 0 with gravity)                                   */
 } sph_params;
 
 /* Caller-owned device arrays, FP64, length n, caller's particle order.

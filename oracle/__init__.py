@@ -78,6 +78,7 @@ class _Params(C.Structure):
         ("G", C.c_double),
         ("grav_theta", C.c_double),
         ("grav_leaf", C.c_int),
+        ("c_grav", C.c_double),
     ]
 
 
@@ -182,6 +183,7 @@ class Params:
     G: float = 1.0                  # gravitational constant
     grav_theta: float = 0.0         # gravity: tree opening angle theta_MAX (0: direct summation)
     grav_leaf: int = 8              # gravity tree: N_LEAF
+    c_grav: float = 0.5             # gravity: acceleration time-step condition multiplier
 
     def _c(self) -> _Params:
         p = _Params()
@@ -199,6 +201,7 @@ class Params:
         p.alpha_min, p.av_decay = self.alpha_min, self.av_decay
         p.gravity, p.G = int(self.gravity), self.G
         p.grav_theta, p.grav_leaf = float(self.grav_theta), int(self.grav_leaf)
+        p.c_grav = float(self.c_grav)
         return p
 
 

@@ -71,6 +71,7 @@ typedef struct {
     double grav_theta;       /* gravity: opening angle theta_MAX of the tree walk (Sec. 4.2);
                                 0 = direct summation over every pair */
     int grav_leaf;           /* gravity tree: N_LEAF, most particles in a leaf cell */
+    double c_grav;           /* gravity: acceleration condition multiplier, Eq. SPH_DTACCEL */
 } orc_params;
 
 typedef struct {
@@ -429,6 +430,7 @@ static int params_ok(const orc_params *p, int64_t n)
     if (p->gravity && (p->periodic || p->kernel != 0 || !(p->G > 0))) return 0;
     if (p->gravity && !(p->grav_theta >= 0.0 && p->grav_theta <= 1.0)) return 0;
     if (p->gravity && p->grav_theta > 0 && p->grav_leaf < 1) return 0;
+    if (p->gravity && !(p->c_grav > 0)) return 0;
     return 1;
 }
 
@@ -1035,13 +1037,23 @@ int orc_forces(const orc_params *p, int64_t n, orc_state *s)
     return status;
 }
 
-/* Global CFL time-step, Eq. SPH_DT: C_CFL * min_i h_i / v_sig,i. */
+/* Global time-step: the CFL condition of Eq. SPH_DT, C_CFL * min_i h_i /
+   v_sig,i, and with gravity the acceleration condition of Eq. SPH_DTACCEL,
+   read as C_GRAV sqrt(h_i / |a_i|) (the printed h_i / sqrt(|a_i|) is not a
+   time). */
 double orc_cfl_dt(const orc_params *p, int64_t n, const orc_state *s)
 {
     double dt = INFINITY;
     for (int64_t i = 0; i < n; ++i) {
         double d = p->c_cfl * s->h[i] / s->vsig[i];
         if (d < dt) dt = d;
+        if (p->gravity) {
+            double a = sqrt(s->ax[i] * s->ax[i] + s->ay[i] * s->ay[i] + s->az[i] * s->az[i]);
+            if (a > 0) {
+                double g = p->c_grav * sqrt(s->h[i] / a);
+                if (g < dt) dt = g;
+            }
+        }
     }
     return dt;
 }

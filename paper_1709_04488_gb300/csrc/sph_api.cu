@@ -208,6 +208,7 @@ int validate(const sph_params *p)
     if (p->gravity != 0 && p->gravity != 1) return fail(SPH_EINVAL, "gravity must be 0 or 1");
     if (p->gravity && !(p->grav_theta >= 0.0 && p->grav_theta <= 1.0))
         return fail(SPH_EINVAL, "grav_theta must lie in [0, 1]");
+    if (p->gravity && !(p->c_grav > 0)) return fail(SPH_EINVAL, "c_grav must be > 0");
     if (p->gravity && (p->periodic || p->kernel != SPH_KERNEL_M4 || !(p->G > 0)))
         return fail(SPH_EINVAL, "self-gravity needs an isolated problem, the M4 kernel and G > 0");
     if (p->ac_signal != SPH_AC_WADSLEY && p->ac_signal != SPH_AC_PRICE)
@@ -268,6 +269,7 @@ PhysParams phys_of(const sph_params *p)
     ph.gravity = p->gravity;
     ph.G = p->G;
     ph.grav_theta = p->grav_theta;
+    ph.c_grav = p->c_grav;
     ph.kr = p->kernel == SPH_KERNEL_M6 ? 3.0 : 2.0;
     ph.kr_f = (float)ph.kr;
     return ph;
@@ -337,6 +339,7 @@ int sph_params_default(sph_params *p)
     p->h_max_iter = 50;
     p->precision = SPH_PREC_MIXED;
     p->alpha_min = 0.1;
+    p->c_grav = 0.5;
     p->av_decay = 0.1;
     return SPH_OK;
 }

@@ -562,6 +562,34 @@ __global__ void __launch_bounds__(kTreeThreads) k_gravity_tree(BatchView b)
     }
 }
 
+// Acceleration condition of Eq. SPH_DTACCEL for the problems with gravity,
+// once the long-range part has been added: dt_i = c_grav sqrt(h_i / |a_i|)
+// joins the CFL minimum of the force pass.
+__global__ void __launch_bounds__(256) k_grav_dt(BatchView b)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int p = -1;
+    double dt = INFINITY;
+    if (g < b.ntot) {
+        p = find_problem(b.prob_base, b.nprob, g);
+        const ProbStatic &ps = b.prob[p];
+        if (ps.ph.gravity) {
+            const long long i = g - ps.base;
+            const double a2 = ps.ax[i] * ps.ax[i] + ps.ay[i] * ps.ay[i] + ps.az[i] * ps.az[i];
+            if (a2 > 0) dt = ps.ph.c_grav * sqrt(ps.h[i] / sqrt(a2));
+        }
+    }
+    // one atomic per warp when the warp lies in one problem
+    const int p0 = __shfl_sync(0xffffffffu, p, 0);
+    if (__all_sync(0xffffffffu, p == p0)) {
+        dt = warp_min(dt);
+        if ((threadIdx.x & 31) == 0 && p0 >= 0 && dt < INFINITY)
+            atomicMin(&b.prob[p0].diag->dt_min_bits, (unsigned long long)__double_as_longlong(dt));
+    } else if (p >= 0 && dt < INFINITY) {
+        atomicMin(&b.prob[p].diag->dt_min_bits, (unsigned long long)__double_as_longlong(dt));
+    }
+}
+
 }  // namespace
 
 // C partner ranges for N particles: enough blocks to fill the GPU (about 8 per
@@ -601,6 +629,7 @@ void launch_gravity(const BatchView &b, int precision, cudaStream_t st)
             k_gravity_tree<float><<<sms * 8, kTreeThreads, 0, st>>>(b);
         }
     }
+    if (b.ntot > 0) k_grav_dt<<<(unsigned)((b.ntot + 255) / 256), 256, 0, st>>>(b);
 }
 
 }  // namespace sph

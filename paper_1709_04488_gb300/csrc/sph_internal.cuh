@@ -69,6 +69,7 @@ struct PhysParams {
     int pad3_;
     double G;
     double grav_theta;   // gravity: tree opening angle (0: direct summation)
+    double c_grav;       // gravity: acceleration time-step condition's multiplier
 };
 
 // Per-problem diagnostics and persistent scalars; lives in the context's own

@@ -55,6 +55,7 @@ class Params(C.Structure):
         ("gravity", C.c_int),
         ("G", C.c_double),
         ("grav_theta", C.c_double),
+        ("c_grav", C.c_double),
     ]
 
 

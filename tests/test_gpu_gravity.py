@@ -276,8 +276,29 @@ def test_tree_steps_track_the_direct_sum(S, oracle_mod):
     assert np.max(np.abs(g["rho"] / ref.rho - 1.0)) < 1e-3
 
 
+@pytest.mark.parametrize("prec,theta", [("mixed", 0.0), ("fp64", 0.0), ("fp64", 0.5)])
+def test_step_of_a_cold_clump_is_the_acceleration_condition(S, oracle_mod, prec, theta):
+    """Cold gas (c = 0): the next step is C_GRAV min sqrt(h/|a|) of Eq.
+    SPH_DTACCEL, from the accelerations with the long-range part added."""
+    O = oracle_mod
+    a, p = ics.cloud(2000, seed=92)
+    a["u"][:] = 0.0
+    for c in ("vx", "vy", "vz"):
+        a[c][:] = 0.0
+    p = dict(p, eos="adiabatic", gamma=5.0 / 3.0)
+    fp64 = prec == "fp64"
+    prob = _gpu(S, a, p, S.PREC_FP64 if fp64 else S.PREC_MIXED, **GR, grav_theta=theta)
+    g = prob.numpy()
+    dt = prob.diagnostics().dt_next
+    an = np.linalg.norm(_acc(g), axis=1)
+    assert dt == pytest.approx(0.5 * np.min(np.sqrt(g["h"] / an)), rel=1e-14)
+    if theta == 0.0:
+        P, ref = _oracle(O, a, p, **GR)
+        assert dt == pytest.approx(O.cfl_dt(P, ref), rel=1e-12 if fp64 else 1e-4)
+
+
 def test_gravity_rejected_for_periodic_or_m6(S):
     for kw in (dict(periodic=True), dict(periodic=False, kernel=1), dict(periodic=False, grav_theta=1.5),
-               dict(periodic=False, grav_theta=-0.1)):
+               dict(periodic=False, grav_theta=-0.1), dict(periodic=False, c_grav=0.0)):
         p = S.make_params(S.PREC_MIXED, gravity=1, G=1.0, **kw)
         assert S.sph_workspace_bytes(100, p) == 0

@@ -99,3 +99,29 @@ def test_gravity_needs_an_isolated_m4_problem(oracle_mod):
     t = O.State(**b)
     assert O.density(O.Params(**dict(q, gravity=1, kernel=1)), t) == O.EINVAL
     assert O.density(O.Params(**dict(q, gravity=1, G=0.0)), t) == O.EINVAL
+
+
+def test_acceleration_condition_sets_the_step_of_a_cold_clump(oracle_mod):
+    """Eq. SPH_DTACCEL: with no pressure (u = 0, so c = 0 and the CFL step is
+    unbounded) the step is C_GRAV min sqrt(h/|a|): every acceleration of a
+    cold static clump is proportional to G, so 4G halves the step, and
+    C_CFL plays no part; hot gas under weak gravity keeps the CFL step."""
+    O = oracle_mod
+    a, p = _cold_clump(500, seed=63)
+    dts = {}
+    for G, ccfl in ((1.0, 0.2), (4.0, 0.2), (1.0, 0.05)):
+        P = O.Params(**dict(p, G=G), use_grid=True, c_cfl=ccfl)
+        s = O.State(**a)
+        assert O.density(P, s) == O.OK and O.forces(P, s) == O.OK
+        dts[(G, ccfl)] = O.cfl_dt(P, s)
+    assert np.isfinite(dts[(1.0, 0.2)])
+    assert dts[(4.0, 0.2)] == pytest.approx(dts[(1.0, 0.2)] / 2, rel=1e-12)
+    assert dts[(1.0, 0.05)] == dts[(1.0, 0.2)]
+    b, q = ics.cloud(500, seed=64)
+    P0 = O.Params(**q, use_grid=True)
+    P1 = O.Params(**dict(q, gravity=1, G=1e-6), use_grid=True)
+    s0, s1 = O.State(**b), O.State(**b)
+    for P, s in ((P0, s0), (P1, s1)):
+        assert O.density(P, s) == O.OK and O.forces(P, s) == O.OK
+    assert O.cfl_dt(P1, s1) == pytest.approx(O.cfl_dt(P0, s0), rel=1e-9)
+    assert O.density(O.Params(**dict(q, gravity=1, c_grav=0.0)), O.State(**b)) == O.EINVAL
