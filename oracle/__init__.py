@@ -145,6 +145,8 @@ def lib():
         L.orc_density_subset.argtypes = [PP, C.c_int64, SP, C.c_int64, C.POINTER(C.c_int64)]
         L.orc_forces_subset.restype = C.c_int
         L.orc_forces_subset.argtypes = [PP, C.c_int64, SP, C.c_int64, C.POINTER(C.c_int64), C.c_double]
+        L.orc_block_step.restype = C.c_int
+        L.orc_block_step.argtypes = [PP, C.c_int64, SP, _IP, _IP, C.c_int, C.c_int, _DP, C.POINTER(C.c_int64)]
         L.orc_gravity_accel.restype = C.c_int
         L.orc_gravity_accel.argtypes = [PP, C.c_int64, SP, _DP, _DP, _DP]
         L.orc_multipole_accel.restype = None
@@ -350,6 +352,20 @@ def grav_dphidh(r, h):
 def gravity_energy(p: Params, s: State) -> float:
     """(G/2) sum_i sum_j m_i m_j (phi(r_ij,h_i) + phi(r_ij,h_j))/2 with the state's h."""
     return lib().orc_gravity_energy(C.byref(p._c()), s.n, C.byref(s._c()))
+
+
+def block_step(p: Params, s: State, level, ngb_maxlev, L: int, dl: int = 2):
+    """One block step (Sec. 2.1.4) from one synchronisation to the next:
+    returns (status, Delta t_MAX, force passes, particle force evaluations).
+    `level` and `ngb_maxlev` (int32, length n, zeros before the first call)
+    are updated in place."""
+    for a in (level, ngb_maxlev):
+        assert a.dtype == np.int32 and a.flags.c_contiguous and len(a) == s.n
+    dtmax = C.c_double(0.0)
+    counts = (C.c_int64 * 2)()
+    rc = lib().orc_block_step(C.byref(p._c()), s.n, C.byref(s._c()), level.ctypes.data_as(_IP),
+                              ngb_maxlev.ctypes.data_as(_IP), int(L), int(dl), C.byref(dtmax), counts)
+    return rc, dtmax.value, counts[0], counts[1]
 
 
 def gravity_accel(p: Params, s: State):

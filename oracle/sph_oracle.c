@@ -940,12 +940,28 @@ static double ac_signal_speed(const orc_params *p, const orc_state *s, int64_t i
     return fabs(vdr);
 }
 
+/* Block time-steps (Sec. 2.1.4): the level of every particle, the largest
+   level among each particle's force neighbours (recorded by the force pass),
+   and, during a block step, which particles end their step now. */
+typedef struct {
+    int32_t *level;
+    int32_t *ngb_maxlev;
+    const uint8_t *active; /* NULL: every particle */
+} orc_block_t;
+
+static int forces_impl(const orc_params *p, int64_t n, orc_state *s, const orc_block_t *blk);
+
 /*
  * Accelerations and energy rates (Eqs. GRADHMOMEQN, GRADHENEQN, MON97ARTVISC,
  * MON97ENERGYDISS) and the signal speed of Eq. SPH_DT, over j != i with
  * r_ij < 2 max(h_i, h_j).  Needs h, rho, Omega, P, c from orc_density.
  */
-int orc_forces(const orc_params *p, int64_t n, orc_state *s)
+int orc_forces(const orc_params *p, int64_t n, orc_state *s) { return forces_impl(p, n, s, NULL); }
+
+/* With block time-steps only the active particles (blk->active) get new
+   accelerations and rates; each of them also records the largest level
+   among its force neighbours. */
+static int forces_impl(const orc_params *p, int64_t n, orc_state *s, const orc_block_t *blk)
 {
     if (p && p->av_switch && (!s->alpha || !s->dalpha)) return ORC_EINVAL;
     if (p && p->gravity && !s->zeta) return ORC_EINVAL;
@@ -972,6 +988,7 @@ int orc_forces(const orc_params *p, int64_t n, orc_state *s)
         idlist_t buf = {0, 0, 0};
 #pragma omp for schedule(dynamic, 64)
         for (int64_t i = 0; i < n; ++i) {
+            if (blk && blk->active && !blk->active[i]) continue;
             int rc = gather(p, s, n, gp, i, kernel_R(p->kernel) * hmax, s->h, &buf);
             if (rc) {
 #pragma omp critical
@@ -982,9 +999,11 @@ int orc_forces(const orc_params *p, int64_t n, orc_state *s)
             kahan_t ax = {0, 0}, ay = {0, 0}, az = {0, 0}, du = {0, 0}, dv = {0, 0};
             double vsig = 2.0 * s->c[i]; /* no neighbour: c_i + c_i */
             int have = 0;
+            int32_t maxlev = -1; /* no neighbour */
             for (int64_t k = 0; k < buf.n; ++k) {
                 int64_t j = buf.v[k];
                 if (j == i) continue;
+                if (blk && blk->level[j] > maxlev) maxlev = blk->level[j];
                 sep_t sp = separation(p, s, i, j);
                 double r = sqrt(sp.r2);
                 double rx = sp.dx / r, ry = sp.dy / r, rz = sp.dz / r; /* r_hat_ij */
@@ -1029,6 +1048,7 @@ int orc_forces(const orc_params *p, int64_t n, orc_state *s)
             s->du[i] = (p->eos == 0) ? du.s : 0.0;
             s->vsig[i] = vsig;
             if (p->av_switch) s->dalpha[i] = av_rate(p, s, i, dv.s);
+            if (blk) blk->ngb_maxlev[i] = maxlev;
         }
         free(buf.v);
     }
@@ -1114,6 +1134,225 @@ int orc_step(const orc_params *p, int64_t n, orc_state *s, double dt)
     }
     free(vh);
     return rc2 ? rc2 : rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hierarchical block time-steps (Sec. 2.1.4) with the Saitoh & Makino       */
+/* (2009) limiter in its predictive and reactive parts.                      */
+/*                                                                           */
+/* One call advances every particle from one synchronisation point to the   */
+/* next, Delta t_MAX later.  Levels l = 0 .. L give steps Delta t_MAX / 2^l;  */
+/* time is counted in ticks of Delta t_MAX / 2^L.  Readings of the paper:    */
+/*  - Delta t_MAX = min(max_i dt_i, 2^L min_i dt_i), dt_i the step of Eq.     */
+/*    SPH_DT (and Eq. SPH_DTACCEL with gravity), so that every particle fits  */
+/*    a level; a particle takes the lowest level whose step is <= its dt_i.   */
+/*  - Each particle runs its own kick-drift-kick: a half kick with its       */
+/*    acceleration when its step starts, every particle drifts with its half */
+/*    step velocity at every tick where some particle ends its step, and     */
+/*    the particles whose step ends there (active) get new h-independent     */
+/*    forces from the positions of all particles and the predicted           */
+/*    v = v_half + a (t - t_mid) and u of all particles, then the closing    */
+/*    half kick.  The density solve runs for all particles at every such     */
+/*    tick (the paper does not say whether inactive particles keep their     */
+/*    old h; re-solving keeps them consistent with the drifted positions).   */
+/*  - A new step's level may rise freely but fall by one level only, and    */
+/*    only where the tick is a multiple of the longer step (Sec. 2.1.4).     */
+/*  - Predictive limiter: a new level is at least (largest level among the  */
+/*    force neighbours at the last force pass) - dl, i.e. a step at most     */
+/*    2^dl times the shortest neighbour's.  Reactive limiter: an active      */
+/*    particle on level l lifts every inactive force neighbour below l - dl  */
+/*    to l - dl; that neighbour's step then ends at the next tick that is a  */
+/*    multiple of its new step, and its opening half kick is corrected to    */
+/*    the shortened step (v_half += a (dt' - dt)/2).                         */
+/* ------------------------------------------------------------------------ */
+static int level_of(double dt, double dtmax, int L)
+{
+    int l = 0;
+    while (l < L && ldexp(dtmax, -l) > dt) ++l;
+    return l;
+}
+
+static double particle_dt(const orc_params *p, const orc_state *s, int64_t i)
+{
+    double d = p->c_cfl * s->h[i] / s->vsig[i];
+    if (p->gravity) {
+        double a = sqrt(s->ax[i] * s->ax[i] + s->ay[i] * s->ay[i] + s->az[i] * s->az[i]);
+        if (a > 0) {
+            double g = p->c_grav * sqrt(s->h[i] / a);
+            if (g < d) d = g;
+        }
+    }
+    return d;
+}
+
+/* The lifted level l - dl that active particle i asks of each inactive
+   force neighbour below it (the reactive part), as a maximum per particle. */
+static int reactive_requests(const orc_params *p, int64_t n, const orc_state *s, const int32_t *level,
+                             const uint8_t *active, int dl, int32_t *req)
+{
+    double hmax = 0;
+    for (int64_t j = 0; j < n; ++j) hmax = s->h[j] > hmax ? s->h[j] : hmax;
+    grid_t g;
+    memset(&g, 0, sizeof g);
+    const grid_t *gp = NULL;
+    if (p->use_grid) {
+        if (grid_build(&g, p, s, n, 2.0 * median_spacing_guess(p, s, n))) return ORC_ENOMEM;
+        gp = &g;
+    }
+    idlist_t buf = {0, 0, 0};
+    int rc = ORC_OK;
+    for (int64_t i = 0; i < n && rc == ORC_OK; ++i) {
+        if (!active[i]) continue;
+        rc = gather(p, s, n, gp, i, kernel_R(p->kernel) * hmax, s->h, &buf);
+        for (int64_t k = 0; rc == ORC_OK && k < buf.n; ++k) {
+            int64_t j = buf.v[k];
+            if (j == i || active[j]) continue;
+            if (level[j] < level[i] - dl && level[i] - dl > req[j]) req[j] = level[i] - dl;
+        }
+    }
+    free(buf.v);
+    if (gp) grid_free(&g);
+    return rc;
+}
+
+/*
+ * One block step of the whole system.  Needs a, du/dt, v_sig (and h) from a
+ * force evaluation of every particle at the start, as orc_step does;
+ * level[] and ngb_maxlev[] carry the levels and the neighbours' largest
+ * levels from one call to the next (zero before the first).  L = largest
+ * level, dl = limiter gap in levels (steps within a factor 2^dl of the
+ * neighbours').  Writes Delta t_MAX to *dtmax_out, and to counts[0] the
+ * force passes and to counts[1] the particle force evaluations they made.
+ */
+int orc_block_step(const orc_params *p, int64_t n, orc_state *s, int32_t *level, int32_t *ngb_maxlev, int L, int dl,
+                   double *dtmax_out, int64_t *counts)
+{
+    if (!params_ok(p, n) || L < 0 || L > 30 || dl < 1) return ORC_EINVAL;
+    if (p->av_switch && (!s->alpha || !s->dalpha)) return ORC_EINVAL;
+    if (p->gravity && !s->zeta) return ORC_EINVAL;
+    if (n == 0) return ORC_OK;
+    const int adi = (p->eos == 0);
+    const int64_t N = (int64_t)1 << L;
+    double dmin = INFINITY, dmax = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        double d = particle_dt(p, s, i);
+        if (d < dmin) dmin = d;
+        if (d > dmax) dmax = d;
+    }
+    const double dtmax = dmax < ldexp(dmin, L) ? dmax : ldexp(dmin, L);
+    const double tau = ldexp(dtmax, -L);
+    *dtmax_out = dtmax;
+    double *w = (double *)malloc((size_t)n * 5 * sizeof(double));
+    int64_t *t0 = (int64_t *)malloc((size_t)n * 2 * sizeof(int64_t));
+    uint8_t *act = (uint8_t *)malloc((size_t)n);
+    int32_t *req = (int32_t *)malloc((size_t)n * sizeof(int32_t));
+    if (!w || !t0 || !act || !req) {
+        free(w);
+        free(t0);
+        free(act);
+        free(req);
+        return ORC_ENOMEM;
+    }
+    double *vhx = w, *vhy = w + n, *vhz = w + 2 * n, *uh = w + 3 * n, *ah = w + 4 * n;
+    int64_t *t1 = t0 + n;
+    /* levels of the new steps and the opening half kicks */
+    for (int64_t i = 0; i < n; ++i) {
+        int l = level_of(particle_dt(p, s, i), dtmax, L);
+        if (l < ngb_maxlev[i] - dl) l = ngb_maxlev[i] - dl; /* predictive limiter */
+        level[i] = l;
+        t0[i] = 0;
+        t1[i] = N >> l;
+        const double hd = 0.5 * (double)t1[i] * tau;
+        vhx[i] = s->vx[i] + s->ax[i] * hd;
+        vhy[i] = s->vy[i] + s->ay[i] * hd;
+        vhz[i] = s->vz[i] + s->az[i] * hd;
+        uh[i] = adi ? s->u[i] + s->du[i] * hd : s->u[i];
+        ah[i] = p->av_switch ? s->alpha[i] + s->dalpha[i] * hd : 0.0;
+    }
+    int64_t k = 0, npass = 0, nevals = 0;
+    int rc = ORC_OK;
+    orc_block_t blk = {level, ngb_maxlev, act};
+    while (k < N) {
+        int64_t kn = N;
+        for (int64_t i = 0; i < n; ++i)
+            if (t1[i] < kn) kn = t1[i];
+        const double dk = (double)(kn - k) * tau;
+        for (int64_t i = 0; i < n; ++i) { /* drift every particle to tick kn */
+            s->x[i] += vhx[i] * dk;
+            s->y[i] += vhy[i] * dk;
+            s->z[i] += vhz[i] * dk;
+            if (p->periodic) {
+                s->x[i] = wrap(s->x[i], p->box_lo[0], p->box_len[0]);
+                s->y[i] = wrap(s->y[i], p->box_lo[1], p->box_len[1]);
+                s->z[i] = wrap(s->z[i], p->box_lo[2], p->box_len[2]);
+            }
+        }
+        k = kn;
+        for (int64_t i = 0; i < n; ++i) { /* active set and the predicted v, u, alpha */
+            act[i] = t1[i] == k;
+            nevals += act[i];
+            const double dp = (double)(2 * k - t0[i] - t1[i]) * 0.5 * tau; /* t - t_mid */
+            s->vx[i] = vhx[i] + s->ax[i] * dp;
+            s->vy[i] = vhy[i] + s->ay[i] * dp;
+            s->vz[i] = vhz[i] + s->az[i] * dp;
+            if (adi) s->u[i] = uh[i] + s->du[i] * dp;
+            if (p->av_switch) s->alpha[i] = ah[i] + s->dalpha[i] * dp;
+            req[i] = -1;
+        }
+        rc = orc_density(p, n, s);
+        if (rc != ORC_OK && rc != ORC_ENOCONV) break;
+        int rc2 = forces_impl(p, n, s, &blk);
+        if (rc2 == ORC_OK) rc2 = reactive_requests(p, n, s, level, act, dl, req);
+        if (rc2) {
+            rc = rc2;
+            break;
+        }
+        ++npass;
+        for (int64_t i = 0; i < n; ++i) {
+            if (act[i]) { /* closing half kick, then the next step */
+                const double hd = 0.5 * (double)(t1[i] - t0[i]) * tau;
+                s->vx[i] = vhx[i] + s->ax[i] * hd;
+                s->vy[i] = vhy[i] + s->ay[i] * hd;
+                s->vz[i] = vhz[i] + s->az[i] * hd;
+                if (adi) s->u[i] = uh[i] + s->du[i] * hd;
+                if (p->av_switch) s->alpha[i] = ah[i] + s->dalpha[i] * hd;
+                if (k == N) continue;
+                int l = level_of(particle_dt(p, s, i), dtmax, L);
+                if (l < ngb_maxlev[i] - dl) l = ngb_maxlev[i] - dl;
+                if (l < level[i]) /* down one level, and only where synchronised */
+                    l = (k % (N >> (level[i] - 1)) == 0) ? level[i] - 1 : level[i];
+                level[i] = l;
+                t0[i] = k;
+                t1[i] = k + (N >> l);
+                const double hn = 0.5 * (double)(N >> l) * tau;
+                vhx[i] = s->vx[i] + s->ax[i] * hn;
+                vhy[i] = s->vy[i] + s->ay[i] * hn;
+                vhz[i] = s->vz[i] + s->az[i] * hn;
+                uh[i] = adi ? s->u[i] + s->du[i] * hn : s->u[i];
+                if (p->av_switch) ah[i] = s->alpha[i] + s->dalpha[i] * hn;
+            } else if (req[i] > level[i]) { /* reactive limiter: end the step early */
+                const int64_t st = N >> req[i];
+                const int64_t ke = (k / st + 1) * st; /* next tick on the new level's grid */
+                if (ke < t1[i]) {
+                    const double corr = 0.5 * (double)(ke - t1[i]) * tau;
+                    vhx[i] += s->ax[i] * corr;
+                    vhy[i] += s->ay[i] * corr;
+                    vhz[i] += s->az[i] * corr;
+                    if (adi) uh[i] += s->du[i] * corr;
+                    if (p->av_switch) ah[i] += s->dalpha[i] * corr;
+                    t1[i] = ke;
+                    level[i] = req[i];
+                }
+            }
+        }
+    }
+    counts[0] = npass;
+    counts[1] = nevals;
+    free(w);
+    free(t0);
+    free(act);
+    free(req);
+    return rc;
 }
 
 /*
