@@ -149,6 +149,12 @@ typedef struct {
     double c_grav;         /* gravity: acceleration condition of Eq. SPH_DTACCEL, the
                               step is also at most c_grav sqrt(h_i / |a_i|) (default 0.5;
                               must be > 0 with gravity)                                   */
+    int block_levels;      /* hierarchical block time-steps (Sec. 2.1.4) for
+                              sph_block_step: largest level L, 0..20 (0 = none, the
+                              default).  Not with gravity (SPH_EINVAL).                  */
+    int block_gap;         /* block steps: limiter gap in levels (Saitoh & Makino):
+                              a particle's step is at most 2^gap times its shortest
+                              neighbour's (default 2; 1..20)                              */
 } sph_params;
 
 /* Caller-owned device arrays, FP64, length n, caller's particle order.
@@ -240,6 +246,29 @@ int sph_step(sph_ctx *ctx, double dt, double *dt_used);
 /* Take nsteps steps with the CFL time-step without host round trips (one
  * captured CUDA graph replayed nsteps times). */
 int sph_run(sph_ctx *ctx, int nsteps);
+
+/* One hierarchical block step (Sec. 2.1.4) of a context set up with
+ * block_levels = L > 0: every particle goes from one synchronisation point to
+ * the next, Delta t_MAX = min(max_i dt_i, 2^L min_i dt_i) later (dt_i the CFL
+ * step of the last force evaluation).  A particle on level l steps by
+ * Delta t_MAX / 2^l with its own kick-drift-kick; at every tick where some
+ * particle's step ends all particles drift, every h and density is solved at
+ * the drifted positions, and the particles whose step ends take forces (with
+ * the predicted v and u of all), the closing half kick and the level and
+ * opening half kick of their next step.  Levels rise freely and fall by one
+ * at a time where synchronised; Saitoh & Makino's limiter keeps each step
+ * within 2^block_gap of the neighbours' (predictive: from the neighbours'
+ * largest level at the last force pass; reactive: particles that take forces
+ * shorten the steps of slower neighbours, which then end at the next tick of
+ * their new level).  Needs a force evaluation first; leaves every particle
+ * synchronised with fresh forces.  Writes Delta t_MAX to *dtmax and the
+ * number of particle force evaluations to *evals (either may be NULL).
+ * Synchronises (one host round trip per tick where a step ends). */
+int sph_block_step(sph_ctx *ctx, double *dtmax, int64_t *evals);
+
+/* Copy each particle's time-step level (int32, caller's order) into the
+ * device array levels (n entries). */
+int sph_block_levels(sph_ctx *ctx, int32_t *levels);
 
 /* Wait for the context's queued work and report the device-side status. */
 int sph_sync(sph_ctx *ctx);

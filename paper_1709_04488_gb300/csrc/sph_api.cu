@@ -50,7 +50,8 @@ DevInfo dev_info()
 
 // ---- workspace layout -------------------------------------------------------
 // Carve the per-step scratch arrays for `ntot` particles over `nprob` problems.
-void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precision, int grav_chunks, int grav_tree)
+void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precision, int grav_chunks, int grav_tree,
+                  int block)
 {
     const long long n = ntot > 0 ? ntot : 1;
     const size_t v4 = precision == SPH_PREC_FP64 ? sizeof(dbl4) : sizeof(float4);
@@ -72,6 +73,10 @@ void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precis
     b.gpart = grav_chunks > 1 ? c.take<double>(3LL * grav_chunks * n) : nullptr;
     b.gpos = grav_tree ? (void *)c.take<char>(v4 * n) : nullptr;
     b.gh = grav_tree ? (void *)c.take<char>(v4 / 2 * n) : nullptr;
+    int **bi[] = {&b.blev, &b.bnml, &b.breq, &b.bt0, &b.bt1};
+    for (int **p : bi) *p = block ? c.take<int>(n) : nullptr;
+    b.bvh = block ? c.take<double>(5 * n) : nullptr;
+    b.slev = block ? (void *)c.take<char>(v4 / 4 * n) : nullptr;
     b.flag = c.take<unsigned>(n);
     const long long ml = leaves_upper_bound(n);
     b.max_leaves = (int)ml;
@@ -209,6 +214,11 @@ int validate(const sph_params *p)
     if (p->gravity && !(p->grav_theta >= 0.0 && p->grav_theta <= 1.0))
         return fail(SPH_EINVAL, "grav_theta must lie in [0, 1]");
     if (p->gravity && !(p->c_grav > 0)) return fail(SPH_EINVAL, "c_grav must be > 0");
+    if (p->block_levels < 0 || p->block_levels > 20) return fail(SPH_EINVAL, "block_levels must lie in [0, 20]");
+    if (p->block_levels > 0 && (p->block_gap < 1 || p->block_gap > 20))
+        return fail(SPH_EINVAL, "block_gap must lie in [1, 20]");
+    if (p->block_levels > 0 && p->gravity)
+        return fail(SPH_EINVAL, "block time-steps are not available with gravity");
     if (p->gravity && (p->periodic || p->kernel != SPH_KERNEL_M4 || !(p->G > 0)))
         return fail(SPH_EINVAL, "self-gravity needs an isolated problem, the M4 kernel and G > 0");
     if (p->ac_signal != SPH_AC_WADSLEY && p->ac_signal != SPH_AC_PRICE)
@@ -270,6 +280,8 @@ PhysParams phys_of(const sph_params *p)
     ph.G = p->G;
     ph.grav_theta = p->grav_theta;
     ph.c_grav = p->c_grav;
+    ph.block = p->block_levels;
+    ph.block_gap = p->block_gap;
     ph.kr = p->kernel == SPH_KERNEL_M6 ? 3.0 : 2.0;
     ph.kr_f = (float)ph.kr;
     return ph;
@@ -340,6 +352,7 @@ int sph_params_default(sph_params *p)
     p->precision = SPH_PREC_MIXED;
     p->alpha_min = 0.1;
     p->c_grav = 0.5;
+    p->block_gap = 2;
     p->av_decay = 0.1;
     return SPH_OK;
 }
@@ -353,7 +366,7 @@ size_t sph_workspace_bytes(int64_t n, const sph_params *p)
     memset(&b, 0, sizeof b);
     carve_tables(c, b, 1);
     carve_arrays(c, b, n, 1, p->precision, p->gravity ? gravity_chunks(n, p->grav_theta) : 0,
-                 p->gravity && p->grav_theta > 0);
+                 p->gravity && p->grav_theta > 0, p->block_levels > 0);
     return c.off + 256;
 }
 
@@ -406,7 +419,7 @@ int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *st
     memset(&c->bv, 0, sizeof c->bv);
     carve_tables(cv, c->bv, 1);
     carve_arrays(cv, c->bv, n, 1, p->precision, p->gravity ? gravity_chunks(n, p->grav_theta) : 0,
-                 p->gravity && p->grav_theta > 0);
+                 p->gravity && p->grav_theta > 0, p->block_levels > 0);
     c->bv.ntot = n;
     c->bv.key_bits = key_bits_for(1);
     c->bv.key_lo = key_low_bits(n);
@@ -474,6 +487,10 @@ int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *st
     if (e == cudaSuccess) e = cudaMemsetAsync(c->bv.dyn, 0, sizeof(ProbDyn), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->bv.counters, 0, kNumCounters * sizeof(int), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->bv.zero_lo, 0, c->bv.zero_bytes, c->stream);
+    if (e == cudaSuccess && c->bv.blev) {  // block steps: level 0, no neighbour levels yet
+        e = cudaMemsetAsync(c->bv.blev, 0, sizeof(int) * (size_t)(n > 0 ? n : 1), c->stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->bv.bnml, 0, sizeof(int) * (size_t)(n > 0 ? n : 1), c->stream);
+    }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) {
         delete c;
@@ -589,6 +606,73 @@ int sph_sync(sph_ctx *c)
     unsigned st = 0;
     CU(cudaMemcpy(&st, &c->diag->status, sizeof st, cudaMemcpyDeviceToHost));
     return status_to_code(st);
+}
+
+int sph_block_step(sph_ctx *c, double *dtmax_out, int64_t *evals_out)
+{
+    if (!c) return fail(SPH_EINVAL, "ctx is NULL");
+    const int L = c->prm.block_levels;
+    if (L <= 0 || !c->bv.blev) return fail(SPH_EINVAL, "the context was set up without block_levels");
+    if (!c->have_forces) return fail(SPH_EINVAL, "sph_block_step needs a force evaluation first");
+    if (c->n == 0) return SPH_OK;
+    clear_ran(c);
+    BatchView b = c->bv;
+    b.block_on = 1;
+    b.any_general = 1;  // the active particles' forces run in the wrap-list launch
+    const int prec = c->prm.precision;
+    cudaStream_t st = c->stream;
+    const long long N = 1LL << L;
+    // Delta t_MAX: the largest step, or 2^L times the smallest if that is less
+    CU(launch_block_dt(b, st));
+    unsigned long long bits[2];
+    CU(cudaMemcpyAsync(bits, b.scratch64, sizeof bits, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    double dmin, dmax;
+    memcpy(&dmin, &bits[0], sizeof dmin);
+    memcpy(&dmax, &bits[1], sizeof dmax);
+    if (!(dmin > 0) || !(dmin < INFINITY)) return fail(SPH_ENONFINITE, "no finite positive time-step");
+    const double dtmax = dmax < ldexp(dmin, L) ? dmax : ldexp(dmin, L);
+    const double tau = ldexp(dtmax, -L);
+    CU(launch_block_open(b, dtmax, tau, L, st));
+    long long k = 0, next = 0;
+    CU(cudaMemcpyAsync(&next, b.scratch64 + 2, sizeof next, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    while (k < N) {
+        if (next <= k || next > N) return fail(SPH_ECUDA, "block step: bad next tick %lld after %lld", next, k);
+        CU(launch_reset_step(b, 1, st));
+        CU(launch_block_drift(b, k, next, tau, st));
+        int rc = enqueue_density(b, prec, 1, st, Marks(), true);
+        if (rc) return rc;
+        CU(launch_block_stage(b, prec, next, st));
+        CU(launch_forces(b, prec, st));
+        CU(launch_block_kick(b, next, dtmax, tau, L, st));
+        k = next;
+        unsigned status = 0;
+        CU(cudaMemcpyAsync(&next, b.scratch64 + 2, sizeof next, cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(&status, &c->diag->status, sizeof status, cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        if (status) return status_to_code(status);
+    }
+    CU(launch_kick_close(b, 0, 1, st));  // conservation sums of the synchronised state
+    CU(launch_block_finish(b, dtmax, st));
+    long long evals = 0;
+    CU(cudaMemcpyAsync(&evals, b.scratch64 + 3, sizeof evals, cudaMemcpyDeviceToHost, st));
+    int rc = sph_sync(c);
+    if (dtmax_out) *dtmax_out = dtmax;
+    if (evals_out) *evals_out = evals;
+    c->have_forces = true;
+    c->since_build = 0;
+    return rc;
+}
+
+int sph_block_levels(sph_ctx *c, int32_t *levels)
+{
+    if (!c || !levels) return fail(SPH_EINVAL, "NULL argument");
+    if (!c->bv.blev) return fail(SPH_EINVAL, "the context was set up without block_levels");
+    if (c->n == 0) return SPH_OK;
+    CU(cudaMemcpyAsync(levels, c->bv.blev, sizeof(int32_t) * (size_t)c->n, cudaMemcpyDeviceToDevice, c->stream));
+    CU(cudaStreamSynchronize(c->stream));
+    return SPH_OK;
 }
 
 int sph_density_h(sph_ctx *c)

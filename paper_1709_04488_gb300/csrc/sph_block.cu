@@ -1,0 +1,268 @@
+// Hierarchical block time-steps (Sec. 2.1.4) with the Saitoh & Makino
+// limiter, for one problem per context.  One block step takes every particle
+// from one synchronisation point to the next, Delta t_MAX later: levels
+// l = 0 .. L step by Delta t_MAX / 2^l, and time is counted in ticks of
+// Delta t_MAX / 2^L.  At every tick where some particle's step ends, all
+// particles drift with their half-step velocities, every particle's h and
+// density are solved at the drifted positions, and the particles whose step
+// ends (the active ones) take new forces from the predicted v and u of all,
+// the closing half kick and the opening half kick of their next step.  The
+// force pass of the wrap-list launch serves them: it records the largest
+// level among each active particle's neighbours (the predictive limiter) and
+// lifts inactive neighbours more than block_gap levels below (the reactive
+// one).  Every rule is taken on integer levels and ticks, so both precisions
+// make the same decisions from the same step lengths.
+//
+// The kick, drift and prediction arithmetic is written with explicit
+// rounding, operation for operation as the reference formulas state it.
+#include "sph_internal.cuh"
+
+namespace sph {
+
+namespace {
+
+constexpr int kBlockThreads = 256;
+
+__device__ __forceinline__ unsigned long long dbits(double v)
+{
+    return (unsigned long long)__double_as_longlong(v);  // positive doubles order as integers
+}
+
+// lowest level l <= L whose step Delta t_MAX / 2^l is at most dt
+__device__ __forceinline__ int level_of(double dt, double dtmax, int L)
+{
+    int l = 0;
+    while (l < L && ldexp(dtmax, -l) > dt) ++l;
+    return l;
+}
+
+// the CFL step of Eq. SPH_DT from the last force evaluation
+__device__ __forceinline__ double particle_dt(const ProbStatic &ps, long long i)
+{
+    return __ddiv_rn(__dmul_rn(ps.ph.c_cfl, ps.h[i]), ps.vsig[i]);
+}
+
+__device__ __forceinline__ double kick(double v, double a, double d) { return __dadd_rn(v, __dmul_rn(a, d)); }
+
+// half of `ticks` ticks of length tau
+__device__ __forceinline__ double half_ticks(long long ticks, double tau)
+{
+    return __dmul_rn(__dmul_rn(0.5, (double)ticks), tau);
+}
+
+__global__ void k_block_init(BatchView b)
+{
+    b.scratch64[0] = (long long)dbits(INFINITY);  // smallest step
+    b.scratch64[1] = 0;                           // largest step
+    b.scratch64[2] = 0x7fffffffffffffffLL;        // next tick where a step ends
+    b.scratch64[3] = 0;                           // particle force evaluations
+}
+
+__global__ void __launch_bounds__(kBlockThreads) k_block_dt(BatchView b)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double lo = INFINITY, hi = 0.0;
+    if (g < b.ntot) {
+        const ProbStatic &ps = b.prob[0];
+        lo = hi = particle_dt(ps, g - ps.base);
+    }
+    lo = warp_min(lo);
+    hi = warp_max(hi);
+    if ((threadIdx.x & 31) == 0) {
+        if (lo < INFINITY) atomicMin((unsigned long long *)&b.scratch64[0], dbits(lo));
+        atomicMax((unsigned long long *)&b.scratch64[1], dbits(hi));
+    }
+}
+
+__device__ __forceinline__ void next_event(const BatchView &b, long long t)
+{
+    const long long m = warp_min(t);
+    if ((threadIdx.x & 31) == 0) atomicMin((unsigned long long *)&b.scratch64[2], (unsigned long long)m);
+}
+
+// each particle's opening step: level from its CFL step, raised to within
+// block_gap of its neighbours' largest level, and the opening half kick
+__global__ void __launch_bounds__(kBlockThreads) k_block_open(BatchView b, double dtmax, double tau, int L)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long t1 = 0x7fffffffffffffffLL;
+    if (g < b.ntot) {
+        const ProbStatic &ps = b.prob[0];
+        const long long i = g - ps.base;
+        int l = level_of(particle_dt(ps, i), dtmax, L);
+        const int lim = b.bnml[g] - ps.ph.block_gap;
+        if (l < lim) l = lim;
+        b.blev[g] = l;
+        b.bt0[g] = 0;
+        b.bt1[g] = (int)((1LL << L) >> l);
+        t1 = b.bt1[g];
+        const double hd = half_ticks(t1, tau);
+        const long long n = b.ntot;
+        b.bvh[g] = kick(ps.vx[i], ps.ax[i], hd);
+        b.bvh[n + g] = kick(ps.vy[i], ps.ay[i], hd);
+        b.bvh[2 * n + g] = kick(ps.vz[i], ps.az[i], hd);
+        b.bvh[3 * n + g] = ps.ph.eos == SPH_EOS_ADIABATIC ? kick(ps.u[i], ps.du[i], hd) : ps.u[i];
+        b.bvh[4 * n + g] = ps.ph.av_switch ? kick(ps.alpha[i], ps.dalpha[i], hd) : 0.0;
+    }
+    next_event(b, t1);
+}
+
+// drift every particle from tick k0 to tick k1, mark the particles whose
+// step ends at k1, predict v, u and alpha at k1 for the force pass
+__global__ void __launch_bounds__(kBlockThreads) k_block_drift(BatchView b, long long k0, long long k1, double tau)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool due = false;
+    if (g < b.ntot) {
+        const ProbStatic &ps = b.prob[0];
+        const PhysParams &ph = ps.ph;
+        const long long i = g - ps.base, n = b.ntot;
+        const double dk = __dmul_rn((double)(k1 - k0), tau);
+        double *X[3] = {ps.x, ps.y, ps.z};
+        const double *A[3] = {ps.ax, ps.ay, ps.az};
+        double *VP[3] = {b.vpx, b.vpy, b.vpz};
+        const int t0 = b.bt0[g], t1 = b.bt1[g];
+        const double dp = __dmul_rn(__dmul_rn((double)(2 * k1 - t0 - t1), 0.5), tau);  // t - t_mid
+        for (int a = 0; a < 3; ++a) {
+            const double vh = b.bvh[a * n + g];
+            double x = __dadd_rn(X[a][i], __dmul_rn(vh, dk));
+            if (ph.periodic) {
+                const double lo = ph.box_lo[a], Lb = ph.box_len[a];
+                if (x >= lo + Lb) x -= Lb;
+                else if (x < lo) x += Lb;
+            }
+            X[a][i] = x;
+            VP[a][g] = kick(vh, A[a][i], dp);
+        }
+        b.up[g] = ph.eos == SPH_EOS_ADIABATIC ? kick(b.bvh[3 * n + g], ps.du[i], dp) : ps.u[i];
+        if (ph.av_switch) b.ap[g] = kick(b.bvh[4 * n + g], ps.dalpha[i], dp);
+        b.breq[g] = -1;
+        due = t1 == k1;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, due);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd((unsigned long long *)&b.scratch64[3], (unsigned long long)__popc(m));
+}
+
+// sorted staging of the levels for the force pass: +(level + 1) where the
+// step ends at tick k, -(level + 1) elsewhere
+template <typename T>
+__global__ void __launch_bounds__(kBlockThreads) k_block_stage(BatchView b, long long k)
+{
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= b.ntot) return;
+    const int g = b.perm[s];
+    const T v = (T)(b.blev[g] + 1);
+    ((T *)b.slev)[s] = b.bt1[g] == k ? v : -v;
+}
+
+// after the force pass at tick k: closing half kick of the active particles
+// and, before the end of the block, the level and opening half kick of their
+// next step; inactive particles lifted by the reactive limiter end their
+// step at the next tick of their new level's grid
+__global__ void __launch_bounds__(kBlockThreads) k_block_kick(BatchView b, long long k, double dtmax, double tau, int L)
+{
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    long long tnext = 0x7fffffffffffffffLL;
+    if (g < b.ntot) {
+        const ProbStatic &ps = b.prob[0];
+        const PhysParams &ph = ps.ph;
+        const long long i = g - ps.base, n = b.ntot, N = 1LL << L;
+        const bool adi = ph.eos == SPH_EOS_ADIABATIC;
+        const double *A[3] = {ps.ax, ps.ay, ps.az};
+        double *V[3] = {ps.vx, ps.vy, ps.vz};
+        int t0 = b.bt0[g], t1 = b.bt1[g], lev = b.blev[g];
+        if (t1 == k) {
+            const double hd = half_ticks(t1 - t0, tau);
+            for (int a = 0; a < 3; ++a) V[a][i] = kick(b.bvh[a * n + g], A[a][i], hd);
+            if (adi) ps.u[i] = kick(b.bvh[3 * n + g], ps.du[i], hd);
+            if (ph.av_switch) ps.alpha[i] = kick(b.bvh[4 * n + g], ps.dalpha[i], hd);
+            if (k < N) {
+                int l = level_of(particle_dt(ps, i), dtmax, L);
+                const int lim = b.bnml[g] - ph.block_gap;
+                if (l < lim) l = lim;
+                if (l < lev)  // down one level, and only where synchronised
+                    l = (k % (N >> (lev - 1)) == 0) ? lev - 1 : lev;
+                lev = l;
+                t0 = (int)k;
+                t1 = (int)(k + (N >> l));
+                const double hn = half_ticks(N >> l, tau);
+                for (int a = 0; a < 3; ++a) b.bvh[a * n + g] = kick(V[a][i], A[a][i], hn);
+                b.bvh[3 * n + g] = adi ? kick(ps.u[i], ps.du[i], hn) : ps.u[i];
+                if (ph.av_switch) b.bvh[4 * n + g] = kick(ps.alpha[i], ps.dalpha[i], hn);
+            }
+        } else {
+            const int rq = b.breq[g];
+            if (rq > lev) {
+                const long long stp = N >> rq;
+                const long long ke = (k / stp + 1) * stp;  // next tick on the new level's grid
+                if (ke < t1) {
+                    const double corr = half_ticks(ke - t1, tau);
+                    for (int a = 0; a < 3; ++a) b.bvh[a * n + g] = kick(b.bvh[a * n + g], A[a][i], corr);
+                    if (adi) b.bvh[3 * n + g] = kick(b.bvh[3 * n + g], ps.du[i], corr);
+                    if (ph.av_switch) b.bvh[4 * n + g] = kick(b.bvh[4 * n + g], ps.dalpha[i], corr);
+                    t1 = (int)ke;
+                    lev = rq;
+                }
+            }
+        }
+        b.bt0[g] = t0;
+        b.bt1[g] = t1;
+        b.blev[g] = lev;
+        if (t1 > k) tnext = t1;
+    }
+    next_event(b, tnext);
+}
+
+__global__ void k_block_next_reset(BatchView b) { b.scratch64[2] = 0x7fffffffffffffffLL; }
+
+__global__ void k_block_finish(BatchView b, double dtmax)
+{
+    ProbDiag *d = b.prob[0].diag;
+    d->time += dtmax;
+    d->steps += 1;
+}
+
+inline unsigned blocks_for(long long n) { return (unsigned)((n + kBlockThreads - 1) / kBlockThreads); }
+
+}  // namespace
+
+cudaError_t launch_block_dt(const BatchView &b, cudaStream_t st)
+{
+    k_block_init<<<1, 1, 0, st>>>(b);
+    k_block_dt<<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_open(const BatchView &b, double dtmax, double tau, int L, cudaStream_t st)
+{
+    k_block_open<<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b, dtmax, tau, L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_drift(const BatchView &b, long long k0, long long k1, double tau, cudaStream_t st)
+{
+    k_block_drift<<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b, k0, k1, tau);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_stage(const BatchView &b, int precision, long long k, cudaStream_t st)
+{
+    if (precision == SPH_PREC_FP64) k_block_stage<double><<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b, k);
+    else k_block_stage<float><<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b, k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_kick(const BatchView &b, long long k, double dtmax, double tau, int L, cudaStream_t st)
+{
+    k_block_next_reset<<<1, 1, 0, st>>>(b);  // the next event is a fresh minimum over the updated steps
+    k_block_kick<<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b, k, dtmax, tau, L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_finish(const BatchView &b, double dtmax, cudaStream_t st)
+{
+    k_block_finish<<<1, 1, 0, st>>>(b, dtmax);
+    return cudaGetLastError();
+}
+
+}  // namespace sph

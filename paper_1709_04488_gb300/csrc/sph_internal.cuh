@@ -70,6 +70,8 @@ struct PhysParams {
     double G;
     double grav_theta;   // gravity: tree opening angle (0: direct summation)
     double c_grav;       // gravity: acceleration time-step condition's multiplier
+    int block;           // hierarchical block time-steps: largest level L (0: global steps)
+    int block_gap;       // block steps: limiter gap dl in levels
 };
 
 // Per-problem diagnostics and persistent scalars; lives in the context's own
@@ -173,6 +175,14 @@ struct BatchView {
     // to the key-domain corner and mass; Q_xx, Q_xy, Q_xz, Q_yy; Q_yz, Q_zz,
     // l^2, h_max; box min; box max), element type float4 or dbl4
     void *gnode[kMaxLevels + 1];
+    // block time-steps (single problem): per particle, original order
+    int block_on;                // this launch set is a tick of a block step
+    int *blev;                   // level
+    int *bnml;                   // largest level among the force neighbours at the last force pass (-1: none)
+    int *breq;                   // reactive limiter: level asked of an inactive particle (-1: none)
+    int *bt0, *bt1;              // current step's first and last tick
+    double *bvh;                 // half-step velocity x, y, z, u and alpha ([5][n])
+    void *slev;                  // sorted: +(level + 1) if the particle ends its step now, else -(level + 1)
     void *gpos;                  // gravity tree: (x - corner, m) per sorted particle, Vec4
     void *gh;                    // gravity tree: (h, 1/h) per sorted particle, float2 or double2
     ProbStatic *prob;            // [nprob]
@@ -312,6 +322,14 @@ void launch_gravity(const BatchView &b, int precision, cudaStream_t st);  // dir
 long long gravity_blocks(long long n, double theta);  // blocks (particle blocks x partner ranges)
 int gravity_chunks(long long n, double theta);        // partner ranges
 cudaError_t launch_kick_drift(const BatchView &b, double dt_host, cudaStream_t st);  // also selects dt, resets diagnostics
+// block time-steps (sph_block.cu); scratch64: [0] smallest and [1] largest
+// step (ordered bits), [2] next tick where a step ends, [3] force evaluations
+cudaError_t launch_block_dt(const BatchView &b, cudaStream_t st);
+cudaError_t launch_block_open(const BatchView &b, double dtmax, double tau, int L, cudaStream_t st);
+cudaError_t launch_block_drift(const BatchView &b, long long k0, long long k1, double tau, cudaStream_t st);
+cudaError_t launch_block_stage(const BatchView &b, int precision, long long k, cudaStream_t st);
+cudaError_t launch_block_kick(const BatchView &b, long long k, double dtmax, double tau, int L, cudaStream_t st);
+cudaError_t launch_block_finish(const BatchView &b, double dtmax, cudaStream_t st);
 cudaError_t launch_kick_close(const BatchView &b, int do_kick, int forces_ran, cudaStream_t st);
 cudaError_t launch_reset_step(const BatchView &b, int mode, cudaStream_t st);  // mode 1 full, 2 forces only
 cudaError_t launch_neighbour_export(const BatchView &b, int kind, const double *h_in, long long *offsets,
@@ -333,7 +351,7 @@ struct Carver {
 };
 int fail(int code, const char *fmt, ...);  // records the thread's error message, returns code
 void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precision, int grav_chunks = 0,
-                  int grav_tree = 0);
+                  int grav_tree = 0, int block = 0);
 void carve_tables(Carver &c, BatchView &b, int nprob);
 int key_bits_for(int nprob);
 int key_low_bits(long long ntot);  // Morton bits left unsorted (cleared) for ntot particles

@@ -1330,6 +1330,17 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
     const bool grav = WRAP && ph.gravity != 0;
     const T* __restrict__ szg = (const T *)b.szg;
     const T Ai_g = grav ? add_rn(ti.x, szg[s]) : ti.x;
+    // block time-steps (wrap-list launch): only the particles whose step ends
+    // now (staged level + 1 > 0) take forces; they record the largest level
+    // among their neighbours and lift inactive neighbours more than
+    // block_gap levels below them (Saitoh & Makino's limiter)
+    const bool blk = WRAP && b.block_on;
+    const T* __restrict__ slev = (const T *)b.slev;
+    const T li1 = blk ? slev[s] : T(0);
+    const bool due = blk ? (active && li1 > T(0)) : active;
+    if (blk && !__any_sync(FULL, due)) return true;  // no particle of this leaf ends its step now
+    const T lgap = (T)ph.block_gap;
+    T mlev = T(0);
     TwoSumAcc<T> ax{T(0), T(0)}, ay{T(0), T(0)}, az{T(0), T(0)};
     T du = T(0), vs = T(-1);
     int pairs = 0, tested = 0;
@@ -1401,6 +1412,11 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
                 du += a2.z * (ti.x * vdr * gi +
                               rhob_inv * gbar * (T(-0.5) * al * vsig * mu * mu + aac * ac_speed(vdr, ti, a2, gm1_price, rhob_inv) * (ti.w - a2.w)));
             vs = vsig > vs ? vsig : vs;
+            if (blk) {
+                const T lj = slev[j], aj = fabs(lj);
+                mlev = aj > mlev ? aj : mlev;
+                if (due && lj < T(0) && aj < li1 - lgap) atomicMax(&b.breq[b.perm[j]], (int)(li1 - lgap) - 1);
+            }
         }
         pairs += cnt;
         cnt = 0;
@@ -1502,14 +1518,16 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
     du = group_sum<LPP>(du);
     vs = group_max<LPP>(vs);
     if (sw) dvs = group_sum<LPP>(dvs);
+    if (blk) mlev = group_max<LPP>(mlev);
     // a = F / m in FP64 (m a stays F to FP64 round-off), one reciprocal
     // per particle (none for equal masses); the CFL step C h / v_sig of
     // Eq. SPH_DT in the pair precision (FP32: the FP64 pipe is much
     // narrower than the FP32 one on this part)
     T dti = tinf<T>();
-    if (active && sub == 0) {
+    if (due && sub == 0) {
         long long g = b.perm[s];
         long long i = g - ps.base;
+        if (blk) b.bnml[g] = (int)mlev - 1;
         const double minv = ps.uniform_m ? ps.inv_m_uniform : 1.0 / ps.m[i];
         double a[3] = {Fx * minv, Fy * minv, Fz * minv};
         const T vsig_t = vs < T(0) ? T(2) * vi.w : vs;
@@ -1561,7 +1579,7 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, FCfg<T, LPP>::MINB) k_
         const int p = b.leaf_pid[leaf];
         const ProbStatic &ps = b.prob[p];
         if (ps.lpp != LPP || ps.ph.kernel != K) continue;  // leaf of a problem served by another launch
-        if (!WRAP && (ps.ph.av_switch || ps.ph.ac_signal || ps.ph.gravity)) {
+        if (!WRAP && (ps.ph.av_switch || ps.ph.ac_signal || ps.ph.gravity || b.block_on)) {
             // the viscosity switch, Price's conductivity and gravity's zeta term run in the
             // wrap-list launch only, which keeps the common path's registers for the default scheme
             if (lane == 0) b.wrap_list[atomicAdd(&b.counters[kForceWrapList], 1)] = leaf;

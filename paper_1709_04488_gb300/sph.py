@@ -56,6 +56,8 @@ class Params(C.Structure):
         ("G", C.c_double),
         ("grav_theta", C.c_double),
         ("c_grav", C.c_double),
+        ("block_levels", C.c_int),
+        ("block_gap", C.c_int),
     ]
 
 
@@ -160,6 +162,8 @@ def lib():
             "sph_forces": (i, [vp]),
             "sph_step": (i, [vp, d, C.POINTER(d)]),
             "sph_run": (i, [vp, i]),
+            "sph_block_step": (i, [vp, C.POINTER(d), C.POINTER(i64)]),
+            "sph_block_levels": (i, [vp, vp]),
             "sph_sync": (i, [vp]),
             "sph_diagnostics": (i, [vp, C.POINTER(Diag)]),
             "sph_neighbours": (i, [vp, i, vp, vp, vp, i64, C.POINTER(i64)]),
@@ -263,6 +267,18 @@ def sph_step_nowait(ctx, dt: float) -> int:
 
 def sph_run(ctx, nsteps: int) -> int:
     return lib().sph_run(ctx, int(nsteps))
+
+
+def sph_block_step(ctx):
+    """One block step: (status, Delta t_MAX, particle force evaluations)."""
+    dtmax = C.c_double(0.0)
+    evals = C.c_int64(0)
+    rc = lib().sph_block_step(ctx, C.byref(dtmax), C.byref(evals))
+    return rc, dtmax.value, evals.value
+
+
+def sph_block_levels(ctx, levels_ptr) -> int:
+    return lib().sph_block_levels(ctx, levels_ptr)
 
 
 def sph_sync(ctx) -> int:
@@ -373,6 +389,20 @@ class Problem:
 
     def run(self, nsteps: int, allow=()):
         return check(sph_run(self.ctx, nsteps), "sph_run", allow)
+
+    def block_step(self, allow=()):
+        """One hierarchical block step (needs block_levels > 0 in the
+        params): returns (Delta t_MAX, particle force evaluations)."""
+        rc, dtmax, evals = sph_block_step(self.ctx)
+        check(rc, "sph_block_step", allow)
+        return dtmax, evals
+
+    def levels(self):
+        """Each particle's time-step level (numpy int32, caller's order)."""
+        torch = self.torch
+        lv = torch.zeros(self.n, dtype=torch.int32, device=self.device)
+        check(sph_block_levels(self.ctx, lv.data_ptr()), "sph_block_levels")
+        return lv.cpu().numpy()
 
     def sync(self, allow=()):
         return check(sph_sync(self.ctx), "sph_sync", allow)

@@ -1,0 +1,103 @@
+"""GPU parity of hierarchical block time-steps (Sec. 2.1.4) with the Saitoh &
+Makino limiter against the FP64 oracle's block step: the same levels and
+force evaluations (every decision is taken on integer levels from the same
+step lengths), and the state after one block step within the path's
+tolerance (FP64 path 1e-10 of the scale, mixed 5e-4 -- several drifts,
+density solves and kicks compound the per-evaluation 1e-4)."""
+import numpy as np
+import pytest
+
+from paper_1709_04488_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1709_04488_gb300 import build as b
+    b.build()
+    from paper_1709_04488_gb300 import sph
+    return sph
+
+
+def _oracle_block(O, a, p, L, dl=2, blocks=1):
+    P = O.Params(**p, use_grid=True)
+    s = O.State(**a)
+    assert O.density(P, s) == O.OK and O.forces(P, s) == O.OK
+    lv = np.zeros(s.n, np.int32)
+    nm = np.zeros(s.n, np.int32)
+    out = []
+    for _ in range(blocks):
+        rc, dtmax, passes, evals = O.block_step(P, s, lv, nm, L, dl)
+        assert rc == O.OK
+        out.append((dtmax, evals))
+    return s, lv, out
+
+
+def _gpu_block(S, a, p, prec, L, dl=2, blocks=1):
+    prob = S.Problem(a, S.make_params(prec, **p, block_levels=L, block_gap=dl))
+    prob.density_h()
+    prob.forces()
+    out = [prob.block_step() for _ in range(blocks)]
+    return prob, out
+
+
+def _scale_err(g, ref, f):
+    r = getattr(ref, f)
+    return np.max(np.abs(g[f] - r)) / max(np.max(np.abs(r)), 1e-300)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_sedov_block_step_matches_oracle(S, oracle_mod, prec):
+    O = oracle_mod
+    a, p = ics.sedov(16)
+    L = 5
+    ref, lv_ref, oo = _oracle_block(O, a, p, L)
+    fp64 = prec == "fp64"
+    prob, go = _gpu_block(S, a, p, S.PREC_FP64 if fp64 else S.PREC_MIXED, L)
+    lv = prob.levels()
+    assert np.array_equal(lv, lv_ref)
+    assert go[0][0] == pytest.approx(oo[0][0], rel=1e-12 if fp64 else 1e-5)
+    assert go[0][1] == oo[0][1]  # the same particle force evaluations
+    assert lv.max() >= 3 and go[0][1] < len(a["x"]) * 2 ** L / 4
+    g = prob.numpy()
+    tol = 1e-10 if fp64 else 5e-4
+    for f in ("vx", "vy", "vz", "u"):
+        assert _scale_err(g, ref, f) < tol, f
+    L_box = np.asarray(p["box_len"])
+    for k, f in enumerate(("x", "y", "z")):
+        d = np.abs(g[f] - getattr(ref, f))
+        d = np.minimum(d, L_box[k] - d)
+        assert np.max(d) < (1e-10 if fp64 else 1e-6), f
+    assert np.max(np.abs(g["rho"] / ref.rho - 1.0)) < (1e-10 if fp64 else 1e-4)
+
+
+def test_two_block_steps_and_limiter_history(S, oracle_mod):
+    """The neighbours' largest levels carry from one block step to the next
+    (the predictive limiter at the second block's start)."""
+    O = oracle_mod
+    a, p = ics.sedov(14, seed=5)
+    ref, lv_ref, oo = _oracle_block(O, a, p, 4, blocks=2)
+    prob, go = _gpu_block(S, a, p, S.PREC_FP64, 4, blocks=2)
+    assert np.array_equal(prob.levels(), lv_ref)
+    assert [e for _, e in go] == [e for _, e in oo]
+    g = prob.numpy()
+    for f in ("vx", "u"):
+        assert _scale_err(g, ref, f) < 1e-9, f
+
+
+def test_block_step_rejections(S):
+    import torch
+    a, p = ics.lattice(6, seed=2)
+    prob = S.Problem(a, S.make_params(S.PREC_MIXED, **p))
+    prob.density_h()
+    prob.forces()
+    rc, _, _ = S.sph_block_step(prob.ctx)
+    assert rc == S.EINVAL  # set up without block_levels
+    b, q = ics.cloud(500, seed=3)
+    assert S.sph_workspace_bytes(500, S.make_params(S.PREC_MIXED, **q, gravity=1, block_levels=3)) == 0
+    assert S.sph_workspace_bytes(500, S.make_params(S.PREC_MIXED, **q, block_levels=21)) == 0
+    assert S.sph_workspace_bytes(500, S.make_params(S.PREC_MIXED, **q, block_levels=3, block_gap=0)) == 0
