@@ -43,6 +43,8 @@ FLOPS_GRAVITY_NODE = 64   # per (particle, node) multipole term (r, powers of 1/
 GRAVITY_N = 65536         # self-gravity measurement: isolated cloud of this many particles
 GRAVITY_TREE_N = 1_000_000  # the tree walk's larger cloud
 GRAVITY_THETA = 0.5       # opening angle of the tree-walk measurements
+BLOCK_SEDOV_SIDE = 64     # block time-step measurement: Sedov blast on 64^3 particles
+BLOCK_LEVELS = 6
 
 
 def parse():
@@ -56,6 +58,7 @@ def parse():
     ap.add_argument("--no-reuse", action="store_true", help="skip the tree-reuse measurement")
     ap.add_argument("--no-m6", action="store_true", help="skip the M6 quintic-kernel measurement")
     ap.add_argument("--no-gravity", action="store_true", help="skip the self-gravity measurement")
+    ap.add_argument("--no-block", action="store_true", help="skip the block time-step measurement")
     ap.add_argument("--lpp", type=int, default=0, help="lanes per particle (0: autotuned)")
     ap.add_argument("--workload", default="sod", choices=sorted(WORKLOADS),
                     help="sod (the default measured configuration), sedov or cloud")
@@ -473,6 +476,48 @@ def run_ours(args):
                                  "frac": tflop / (gms * 1e-3) / 1e12 / peak})
             ptr.close()
 
+    # hierarchical block time-steps (Sec. 2.1.4) on a Sedov blast, the
+    # paper's block time-step test: one block step against the global steps
+    # of the smallest CFL step over the same simulated time
+    blk = None
+    if not args.no_block:
+        from paper_1709_04488_gb300 import ics
+        ab, pb_ = ics.sedov(BLOCK_SEDOV_SIDE)
+        nb = len(ab["x"])
+        with torch.cuda.stream(stream):
+            pbk = S.Problem(ab, S.make_params(S.PREC_MIXED, **pb_, block_levels=BLOCK_LEVELS), device=dev,
+                            stream=stream)
+            S.check(S.sph_density_h(pbk.ctx), "sph_density_h")
+            S.check(S.sph_forces(pbk.ctx), "sph_forces")
+            pgl = S.Problem(ab, S.make_params(S.PREC_MIXED, **pb_, flags=S.FLAG_ASYNC), device=dev, stream=stream)
+            S.check(S.sph_density_h(pgl.ctx), "sph_density_h")
+            S.check(S.sph_forces(pgl.ctx), "sph_forces")
+        dt_glob = pgl.diagnostics().dt_next
+        S.check(S.sph_run(pgl.ctx, 3), "sph_run")
+        msgl, _, _, _ = time_steps(S, pgl, stream, torch, 5, flush)
+        pbk.block_step()  # warm-up block; the timed one starts from the same state as the global steps
+        pbk.close()
+        with torch.cuda.stream(stream):
+            pbk = S.Problem(ab, S.make_params(S.PREC_MIXED, **pb_, block_levels=BLOCK_LEVELS), device=dev,
+                            stream=stream)
+            S.check(S.sph_density_h(pbk.ctx), "sph_density_h")
+            S.check(S.sph_forces(pbk.ctx), "sph_forces")
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        dtmax, evals = pbk.block_step()
+        torch.cuda.synchronize(dev)
+        blk_ms = (time.perf_counter() - t0) * 1e3
+        lv = pbk.levels()
+        glob_equiv = float(np.mean(msgl)) * dtmax / dt_glob
+        blk = {"workload": f"sedov_{nb}: {BLOCK_LEVELS} levels, limiter gap 2",
+               "block_ms": blk_ms, "dt_max": dtmax, "force_evaluations": int(evals),
+               "evaluations_global": int(nb * round(dtmax / dt_glob)), "levels": np.bincount(lv).tolist(),
+               "global_ms_per_step": float(np.mean(msgl)), "global_dt": dt_glob,
+               "global_ms_same_time": glob_equiv, "speedup": glob_equiv / blk_ms,
+               "timing": "host wall clock around one block step (one host round trip per tick)"}
+        pbk.close()
+        pgl.close()
+
     diag = prob.diagnostics()
     prob.close()
     serve_res = None
@@ -497,7 +542,7 @@ def run_ours(args):
                    "l2": "flushed (256 MiB write) between timed steps", "graph": "one CUDA graph per step",
                    "lanes_per_particle": int(prob.params.lanes_per_particle) or "auto"},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": kernels_per_step * args.steps,
-        "clocks": clocks, "fp64_gpu": fp64, "tree_reuse": reuse, "m6_kernel": m6, "gravity": grav, "serving": serve_res,
+        "clocks": clocks, "fp64_gpu": fp64, "tree_reuse": reuse, "m6_kernel": m6, "gravity": grav, "block_steps": blk, "serving": serve_res,
         "step_diag": {"nr_iterations": diag.nr_iterations, "nr_max": diag.nr_max, "fallback": diag.fallback,
                       "leaves": diag.leaves, "ngb_mean": diag.ngb_mean, "candidates": diag.candidates,
                       "wrap_leaves": diag.wrap_leaves},
