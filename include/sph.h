@@ -252,10 +252,11 @@ int sph_run(sph_ctx *ctx, int nsteps);
  * the next, Delta t_MAX = min(max_i dt_i, 2^L min_i dt_i) later (dt_i the CFL
  * step of the last force evaluation).  A particle on level l steps by
  * Delta t_MAX / 2^l with its own kick-drift-kick; at every tick where some
- * particle's step ends all particles drift, every h and density is solved at
- * the drifted positions, and the particles whose step ends take forces (with
- * the predicted v and u of all), the closing half kick and the level and
- * opening half kick of their next step.  Levels rise freely and fall by one
+ * particle's step ends all particles drift, and the particles whose step ends
+ * get a new h and density and forces (from the positions and predicted v and
+ * u of all), the closing half kick and the level and opening half kick of
+ * their next step; the others keep the h, rho, omega, P and c of their last
+ * solve.  Levels rise freely and fall by one
  * at a time where synchronised; Saitoh & Makino's limiter keeps each step
  * within 2^block_gap of the neighbours' (predictive: from the neighbours'
  * largest level at the last force pass; reactive: particles that take forces

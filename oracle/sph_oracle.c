@@ -1149,12 +1149,11 @@ int orc_step(const orc_params *p, int64_t n, orc_state *s, double dt)
 /*  - Each particle runs its own kick-drift-kick: a half kick with its       */
 /*    acceleration when its step starts, every particle drifts with its half */
 /*    step velocity at every tick where some particle ends its step, and     */
-/*    the particles whose step ends there (active) get new h-independent     */
+/*    the particles whose step ends there (active) get a new h, density and  */
 /*    forces from the positions of all particles and the predicted           */
 /*    v = v_half + a (t - t_mid) and u of all particles, then the closing    */
-/*    half kick.  The density solve runs for all particles at every such     */
-/*    tick (the paper does not say whether inactive particles keep their     */
-/*    old h; re-solving keeps them consistent with the drifted positions).   */
+/*    half kick.  Inactive particles keep the h, rho, Omega, P and c of      */
+/*    their last solve (only the active particles' density is solved).      */
 /*  - A new step's level may rise freely but fall by one level only, and    */
 /*    only where the tick is a multiple of the longer step (Sec. 2.1.4).     */
 /*  - Predictive limiter: a new level is at least (largest level among the  */
@@ -1165,6 +1164,8 @@ int orc_step(const orc_params *p, int64_t n, orc_state *s, double dt)
 /*    multiple of its new step, and its opening half kick is corrected to    */
 /*    the shortened step (v_half += a (dt' - dt)/2).                         */
 /* ------------------------------------------------------------------------ */
+int orc_density_subset(const orc_params *p, int64_t n, orc_state *s, int64_t nsub, const int64_t *idx);
+
 static int level_of(double dt, double dtmax, int L)
 {
     int l = 0;
@@ -1246,11 +1247,13 @@ int orc_block_step(const orc_params *p, int64_t n, orc_state *s, int32_t *level,
     int64_t *t0 = (int64_t *)malloc((size_t)n * 2 * sizeof(int64_t));
     uint8_t *act = (uint8_t *)malloc((size_t)n);
     int32_t *req = (int32_t *)malloc((size_t)n * sizeof(int32_t));
-    if (!w || !t0 || !act || !req) {
+    int64_t *aidx = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    if (!w || !t0 || !act || !req || !aidx) {
         free(w);
         free(t0);
         free(act);
         free(req);
+        free(aidx);
         return ORC_ENOMEM;
     }
     double *vhx = w, *vhy = w + n, *vhz = w + 2 * n, *uh = w + 3 * n, *ah = w + 4 * n;
@@ -1299,7 +1302,10 @@ int orc_block_step(const orc_params *p, int64_t n, orc_state *s, int32_t *level,
             if (p->av_switch) s->alpha[i] = ah[i] + s->dalpha[i] * dp;
             req[i] = -1;
         }
-        rc = orc_density(p, n, s);
+        int64_t na = 0;
+        for (int64_t i = 0; i < n; ++i)
+            if (act[i]) aidx[na++] = i;
+        rc = orc_density_subset(p, n, s, na, aidx);
         if (rc != ORC_OK && rc != ORC_ENOCONV) break;
         int rc2 = forces_impl(p, n, s, &blk);
         if (rc2 == ORC_OK) rc2 = reactive_requests(p, n, s, level, act, dl, req);
@@ -1352,6 +1358,7 @@ int orc_block_step(const orc_params *p, int64_t n, orc_state *s, int32_t *level,
     free(t0);
     free(act);
     free(req);
+    free(aidx);
     return rc;
 }
 

@@ -641,9 +641,13 @@ int sph_block_step(sph_ctx *c, double *dtmax_out, int64_t *evals_out)
         if (next <= k || next > N) return fail(SPH_ECUDA, "block step: bad next tick %lld after %lld", next, k);
         CU(launch_reset_step(b, 1, st));
         CU(launch_block_drift(b, k, next, tau, st));
-        int rc = enqueue_density(b, prec, 1, st, Marks(), true);
-        if (rc) return rc;
-        CU(launch_block_stage(b, prec, next, st));
+        CU(launch_domain_and_keys(b, st));
+        CU(launch_radix_sort(b, st));
+        CU(launch_gather(b, st));
+        CU(launch_block_stage(b, prec, next, st));  // which sorted particles end their step now
+        CU(launch_build_leaves(b, prec, st));
+        CU(launch_density(b, prec, 1, st));  // solves the active particles, restages the others
+        CU(launch_refit(b, prec, st));
         CU(launch_forces(b, prec, st));
         CU(launch_block_kick(b, next, dtmax, tau, L, st));
         k = next;

@@ -3,10 +3,11 @@
 // from one synchronisation point to the next, Delta t_MAX later: levels
 // l = 0 .. L step by Delta t_MAX / 2^l, and time is counted in ticks of
 // Delta t_MAX / 2^L.  At every tick where some particle's step ends, all
-// particles drift with their half-step velocities, every particle's h and
-// density are solved at the drifted positions, and the particles whose step
-// ends (the active ones) take new forces from the predicted v and u of all,
-// the closing half kick and the opening half kick of their next step.  The
+// particles drift with their half-step velocities, and the particles whose
+// step ends (the active ones) get a new h and density and new forces from
+// the positions and predicted v and u of all, the closing half kick and the
+// opening half kick of their next step; the others keep the h, density,
+// pressure and sound speed of their last solve.  The
 // force pass of the wrap-list launch serves them: it records the largest
 // level among each active particle's neighbours (the predictive limiter) and
 // lifts inactive neighbours more than block_gap levels below (the reactive

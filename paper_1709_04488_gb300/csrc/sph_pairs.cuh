@@ -611,23 +611,35 @@ __device__ __forceinline__ void density_epilogue(const BatchView &b, const ProbS
 {
     using V = typename Vec4<T>::type;
     const PhysParams &ph = ps.ph;
-    T hinv = T(1) / h;
-    T hinv3 = hinv * hinv * hinv;
-    T rho = sigma * S0 * hinv3;
-    T drho = -sigma * hinv3 * hinv * (T(3) * S0 + S1);
-    T omega = T(1) + h / (T(3) * rho) * drho;
     long long g = b.perm[s];
     long long i = g - ps.base;
     double u = use_pred ? b.up[g] : ps.u[i];
     double v[3] = {use_pred ? b.vpx[g] : ps.vx[i], use_pred ? b.vpy[g] : ps.vy[i],
                    use_pred ? b.vpz[g] : ps.vz[i]};
-    T P, c;
-    if (ph.eos == SPH_EOS_ISOTHERMAL) {
-        c = (T)ph.cs_iso;
-        P = c * c * rho;
+    T hinv, rho, omega, P, c;
+    // block time-steps: a particle whose step does not end now keeps the h,
+    // rho, Omega, P and c of its last solve (restaged here for the force pass)
+    const bool keep = b.block_on && ((const T *)b.slev)[s] < T(0);
+    if (keep) {
+        h = (T)ps.h[i];
+        hinv = T(1) / h;
+        rho = (T)ps.rho[i];
+        omega = (T)ps.omega[i];
+        P = (T)ps.P[i];
+        c = (T)ps.c[i];
     } else {
-        P = (T)(ph.gamma - 1.0) * rho * (T)u;
-        c = sqrt((T)ph.gamma * P / rho);
+        hinv = T(1) / h;
+        T hinv3 = hinv * hinv * hinv;
+        rho = sigma * S0 * hinv3;
+        T drho = -sigma * hinv3 * hinv * (T(3) * S0 + S1);
+        omega = T(1) + h / (T(3) * rho) * drho;
+        if (ph.eos == SPH_EOS_ISOTHERMAL) {
+            c = (T)ph.cs_iso;
+            P = c * c * rho;
+        } else {
+            P = (T)(ph.gamma - 1.0) * rho * (T)u;
+            c = sqrt((T)ph.gamma * P / rho);
+        }
     }
     T A = P / (omega * rho * rho);
     b.sh[s] = (double)h;
@@ -636,11 +648,13 @@ __device__ __forceinline__ void density_epilogue(const BatchView &b, const ProbS
     b.somega[s] = (double)omega;
     b.sP[s] = (double)P;
     b.sc[s] = (double)c;
-    ps.h[i] = (double)h;
-    ps.rho[i] = (double)rho;
-    ps.omega[i] = (double)omega;
-    ps.P[i] = (double)P;
-    ps.c[i] = (double)c;
+    if (!keep) {
+        ps.h[i] = (double)h;
+        ps.rho[i] = (double)rho;
+        ps.omega[i] = (double)omega;
+        ps.P[i] = (double)P;
+        ps.c[i] = (double)c;
+    }
     V q;
     q.x = pi.x;
     q.y = pi.y;
@@ -696,6 +710,12 @@ __device__ __forceinline__ bool density_leaf(const BatchView &b, int leaf, unsig
     const long long s = st + (active ? pp : 0);
     const V pi = pm[s];
     const T mi = pi.w;
+    // block time-steps: a leaf none of whose particles ends its step now is
+    // only restaged from the particles' last solve
+    if (b.block_on && !__any_sync(FULL, active && ((const T *)b.slev)[s] > T(0))) {
+        if (active && sub == 0) density_epilogue<T>(b, ps, s, pi, T(1), T(0), T(0), use_pred, sigma);
+        return true;
+    }
     V flo, fhi;
     frame_box<V, T>(pi, active, flo, fhi);
     const float halfL = ph.periodic ? half_box(ph) : INFINITY;
@@ -955,7 +975,7 @@ __device__ __forceinline__ bool density_leaf(const BatchView &b, int leaf, unsig
     }
     if (fin && sub == 0) {
         density_epilogue<T>(b, ps, s, pi, h, S0, S1, use_pred, sigma, Z);
-        if (noconv) {
+        if (noconv && !(b.block_on && ((const T *)b.slev)[s] < T(0))) {  // (a kept solve is not this one)
             atomicOr(&ps.diag->status, ST_NOCONV);
             atomicAdd(&ps.diag->unconverged, 1);
         }
