@@ -151,7 +151,9 @@ typedef struct {
                               must be > 0 with gravity)                                   */
     int block_levels;      /* hierarchical block time-steps (Sec. 2.1.4) for
                               sph_block_step: largest level L, 0..20 (0 = none, the
-                              default).  Not with gravity (SPH_EINVAL).                  */
+                              default).  With gravity the long range and the zeta
+                              term follow the same active set, and the acceleration
+                              condition enters each particle's step.                    */
     int block_gap;         /* block steps: limiter gap in levels (Saitoh & Makino):
                               a particle's step is at most 2^gap times its shortest
                               neighbour's (default 2; 1..20)                              */

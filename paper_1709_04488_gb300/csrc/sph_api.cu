@@ -76,6 +76,7 @@ void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precis
     int **bi[] = {&b.blev, &b.bnml, &b.breq, &b.bt0, &b.bt1};
     for (int **p : bi) *p = block ? c.take<int>(n) : nullptr;
     b.bvh = block ? c.take<double>(5 * n) : nullptr;
+    b.bzeta = block ? c.take<double>(n) : nullptr;
     b.slev = block ? (void *)c.take<char>(v4 / 4 * n) : nullptr;
     b.flag = c.take<unsigned>(n);
     const long long ml = leaves_upper_bound(n);
@@ -217,8 +218,6 @@ int validate(const sph_params *p)
     if (p->block_levels < 0 || p->block_levels > 20) return fail(SPH_EINVAL, "block_levels must lie in [0, 20]");
     if (p->block_levels > 0 && (p->block_gap < 1 || p->block_gap > 20))
         return fail(SPH_EINVAL, "block_gap must lie in [1, 20]");
-    if (p->block_levels > 0 && p->gravity)
-        return fail(SPH_EINVAL, "block time-steps are not available with gravity");
     if (p->gravity && (p->periodic || p->kernel != SPH_KERNEL_M4 || !(p->G > 0)))
         return fail(SPH_EINVAL, "self-gravity needs an isolated problem, the M4 kernel and G > 0");
     if (p->ac_signal != SPH_AC_WADSLEY && p->ac_signal != SPH_AC_PRICE)
@@ -649,6 +648,8 @@ int sph_block_step(sph_ctx *c, double *dtmax_out, int64_t *evals_out)
         CU(launch_density(b, prec, 1, st));  // solves the active particles, restages the others
         CU(launch_refit(b, prec, st));
         CU(launch_forces(b, prec, st));
+        launch_gravity(b, prec, st);  // the long range of the active particles
+        CU(cudaGetLastError());
         CU(launch_block_kick(b, next, dtmax, tau, L, st));
         k = next;
         unsigned status = 0;

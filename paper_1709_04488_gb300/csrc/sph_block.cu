@@ -37,10 +37,21 @@ __device__ __forceinline__ int level_of(double dt, double dtmax, int L)
     return l;
 }
 
-// the CFL step of Eq. SPH_DT from the last force evaluation
+// the CFL step of Eq. SPH_DT from the last force evaluation and, with
+// gravity, the acceleration condition of Eq. SPH_DTACCEL
 __device__ __forceinline__ double particle_dt(const ProbStatic &ps, long long i)
 {
-    return __ddiv_rn(__dmul_rn(ps.ph.c_cfl, ps.h[i]), ps.vsig[i]);
+    double d = __ddiv_rn(__dmul_rn(ps.ph.c_cfl, ps.h[i]), ps.vsig[i]);
+    if (ps.ph.gravity) {
+        const double a2 = __dadd_rn(__dadd_rn(__dmul_rn(ps.ax[i], ps.ax[i]), __dmul_rn(ps.ay[i], ps.ay[i])),
+                                    __dmul_rn(ps.az[i], ps.az[i]));
+        const double a = __dsqrt_rn(a2);
+        if (a > 0) {
+            const double gdt = __dmul_rn(ps.ph.c_grav, __dsqrt_rn(__ddiv_rn(ps.h[i], a)));
+            if (gdt < d) d = gdt;
+        }
+    }
+    return d;
 }
 
 __device__ __forceinline__ double kick(double v, double a, double d) { return __dadd_rn(v, __dmul_rn(a, d)); }

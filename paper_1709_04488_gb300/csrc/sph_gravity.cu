@@ -138,6 +138,7 @@ __global__ void __launch_bounds__(kGravThreads) k_gravity(BatchView b)
         }
     }
     auto store = [&](long long i, const TwoSumAcc<T> &ax, const TwoSumAcc<T> &ay, const TwoSumAcc<T> &az) {
+        if (b.block_on && ((const T *)b.slev)[i] < T(0)) return;  // block step: not this particle's force pass
         if (C > 1) {  // partial of range ch, layout [ch][axis][ntot]
             double *g = b.gpart + (long long)ch * 3 * b.ntot + i;
             g[0] = (double)ax.s + (double)ax.c;
@@ -157,10 +158,12 @@ __global__ void __launch_bounds__(kGravThreads) k_gravity(BatchView b)
 }
 
 // Sum the partials of split problems in range order: a_i += G/m_i sum_ch F_i,ch.
+template <typename T>
 __global__ void __launch_bounds__(256) k_gravity_reduce(BatchView b)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= b.ntot) return;
+    if (b.block_on && ((const T *)b.slev)[i] < T(0)) return;  // block step: not this particle's force pass
     int p = 0;  // problem of particle i: the last one whose base is <= i
     for (int lo = 0, hi = b.nprob - 1; lo <= hi;) {
         const int mid = (lo + hi) >> 1;
@@ -408,6 +411,9 @@ __global__ void __launch_bounds__(kTreeThreads) k_gravity_tree(BatchView b)
         const int lpp = ps.lpp, S = kBranch / lpp;
         const int pi = lane % S, sub = lane / S;
         const int st = b.leaf_start[leaf], cnt = b.leaf_start[leaf + 1] - st;
+        // block step: only the particles whose step ends take the long range
+        const bool due = pi < cnt && (!b.block_on || ((const T *)b.slev)[st + pi] > T(0));
+        if (!__any_sync(0xffffffffu, due)) continue;
         const V4 *gl = (const V4 *)b.gnode[0] + 5LL * leaf;
         const V4 GL = gl[3], GH = gl[4];
         const T hleaf = gl[2].w;
@@ -546,7 +552,7 @@ __global__ void __launch_bounds__(kTreeThreads) k_gravity_tree(BatchView b)
             gy += __shfl_xor_sync(0xffffffffu, gy, o);
             gz += __shfl_xor_sync(0xffffffffu, gz, o);
         }
-        if (sub == 0 && pi < cnt) {
+        if (sub == 0 && due) {
             const long long io = (long long)b.perm[st + pi] - ps.base;
             ps.ax[io] += ps.ph.G * gx;
             ps.ay[io] += ps.ph.G * gy;
@@ -616,8 +622,10 @@ void launch_gravity(const BatchView &b, int precision, cudaStream_t st)
         if (precision == SPH_PREC_FP64) k_gravity<double><<<(unsigned)b.grav_blocks, kGravThreads, 0, st>>>(b);
         else k_gravity<float><<<(unsigned)b.grav_blocks, kGravThreads, 0, st>>>(b);
     }
-    if (b.grav_split)
-        k_gravity_reduce<<<(unsigned)((b.ntot + 255) / 256), 256, 0, st>>>(b);
+    if (b.grav_split) {
+        if (precision == SPH_PREC_FP64) k_gravity_reduce<double><<<(unsigned)((b.ntot + 255) / 256), 256, 0, st>>>(b);
+        else k_gravity_reduce<float><<<(unsigned)((b.ntot + 255) / 256), 256, 0, st>>>(b);
+    }
     if (b.any_grav_tree) {
         static int sms = 0;
         if (!sms) sms = dev_info().sm_count;

@@ -182,6 +182,7 @@ struct BatchView {
     int *breq;                   // reactive limiter: level asked of an inactive particle (-1: none)
     int *bt0, *bt1;              // current step's first and last tick
     double *bvh;                 // half-step velocity x, y, z, u and alpha ([5][n])
+    double *bzeta;               // gravity: the zeta term's weight G zeta / (2 Omega) of the last solve
     void *slev;                  // sorted: +(level + 1) if the particle ends its step now, else -(level + 1)
     void *gpos;                  // gravity tree: (x - corner, m) per sorted particle, Vec4
     void *gh;                    // gravity tree: (h, 1/h) per sorted particle, float2 or double2

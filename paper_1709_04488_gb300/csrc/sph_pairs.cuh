@@ -674,7 +674,15 @@ __device__ __forceinline__ void density_epilogue(const BatchView &b, const ProbS
     if (ph.av_switch) ((T *)b.sal)[s] = (T)(use_pred ? b.ap[g] : ps.alpha[i]);  // viscosity switch
     // gravity: zeta = dh/drho sum_j m_j dphi/dh = Z / (3 rho h) (Z = sum_j m_j (psi + M/q)),
     // kept as the weight G zeta / (2 Omega) of the force pass's zeta term
-    if (ph.gravity) ((T *)b.szg)[s] = (T)(0.5 * ph.G) * Z / (T(3) * rho * h * omega);
+    if (ph.gravity) {
+        if (keep) {
+            ((T *)b.szg)[s] = (T)b.bzeta[g];
+        } else {
+            const T wz = (T)(0.5 * ph.G) * Z / (T(3) * rho * h * omega);
+            ((T *)b.szg)[s] = wz;
+            if (b.bzeta) b.bzeta[g] = (double)wz;  // block-step contexts keep it for the ticks that do not solve
+        }
+    }
     if (!(isfinite((double)rho) && isfinite((double)omega) && isfinite((double)P)))
         atomicOr(&ps.diag->status, ST_NONFINITE);
 }

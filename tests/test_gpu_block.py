@@ -89,6 +89,34 @@ def test_two_block_steps_and_limiter_history(S, oracle_mod):
         assert _scale_err(g, ref, f) < 1e-9, f
 
 
+def _gravity_block_case(n=3000, seed=93):
+    a, p = ics.cloud(n, seed=seed)
+    rng = np.random.default_rng(seed)
+    a["m"] = a["m"] * rng.uniform(0.7, 1.3, n)
+    return a, dict(p, gravity=1, G=3.0)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_gravity_block_step_matches_oracle(S, oracle_mod, prec):
+    """Self-gravity inside block steps: the acceleration condition enters the
+    levels, the long-range sum and the zeta term follow the active set."""
+    O = oracle_mod
+    a, p = _gravity_block_case()
+    L = 4
+    ref, lv_ref, oo = _oracle_block(O, a, p, L)
+    fp64 = prec == "fp64"
+    prob, go = _gpu_block(S, a, p, S.PREC_FP64 if fp64 else S.PREC_MIXED, L)
+    lv = prob.levels()
+    assert np.array_equal(lv, lv_ref)
+    assert go[0][1] == oo[0][1] and lv.max() > lv.min()
+    g = prob.numpy()
+    tol = 1e-10 if fp64 else 5e-4
+    for f in ("vx", "vy", "vz"):
+        assert _scale_err(g, ref, f) < tol, f
+    for f in ("x", "y", "z"):
+        assert np.max(np.abs(g[f] - getattr(ref, f))) < (1e-10 if fp64 else 1e-6), f
+
+
 def test_block_step_rejections(S):
     import torch
     a, p = ics.lattice(6, seed=2)
@@ -98,6 +126,6 @@ def test_block_step_rejections(S):
     rc, _, _ = S.sph_block_step(prob.ctx)
     assert rc == S.EINVAL  # set up without block_levels
     b, q = ics.cloud(500, seed=3)
-    assert S.sph_workspace_bytes(500, S.make_params(S.PREC_MIXED, **q, gravity=1, block_levels=3)) == 0
+    assert S.sph_workspace_bytes(500, S.make_params(S.PREC_MIXED, **q, gravity=1, G=1.0, block_levels=3)) > 0
     assert S.sph_workspace_bytes(500, S.make_params(S.PREC_MIXED, **q, block_levels=21)) == 0
     assert S.sph_workspace_bytes(500, S.make_params(S.PREC_MIXED, **q, block_levels=3, block_gap=0)) == 0

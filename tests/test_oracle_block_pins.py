@@ -29,11 +29,14 @@ def _block(O, P, s, L, dl=2):
     return lv, dtmax, passes, evals
 
 
-@pytest.mark.parametrize("kw", [{}, dict(av_switch=1)])
+@pytest.mark.parametrize("kw", [{}, dict(av_switch=1), dict(gravity=1, G=1.0)])
 def test_one_level_is_the_global_step(oracle_mod, kw):
     O = oracle_mod
-    a, p = ics.sod(left=(32, 16, 16), right=(16, 8, 8), width=0.25)
-    if kw:
+    if kw.get("gravity"):
+        a, p = ics.cloud(1500, seed=9)
+    else:
+        a, p = ics.sod(left=(32, 16, 16), right=(16, 8, 8), width=0.25)
+    if kw.get("av_switch"):
         a["alpha"] = np.full(len(a["x"]), 0.3)
     P, s = _ready(O, a, p, **kw)
     g = s.copy()
@@ -41,7 +44,7 @@ def test_one_level_is_the_global_step(oracle_mod, kw):
     assert O.step(P, g, dt) == O.OK
     lv, dtmax, passes, evals = _block(O, P, s, 0)
     assert dtmax == dt and passes == 1 and evals == s.n and np.all(lv == 0)
-    for f in ("x", "y", "z", "vx", "vy", "vz", "u", "h", "rho", "ax", "du", "vsig") + (("alpha",) if kw else ()):
+    for f in ("x", "y", "z", "vx", "vy", "vz", "u", "h", "rho", "ax", "du", "vsig") + (("alpha",) if "av_switch" in kw else ()):
         assert np.array_equal(getattr(s, f), getattr(g, f)), f
 
 
