@@ -39,7 +39,7 @@ WORKLOAD = WORKLOADS["sod"]
 FLOPS_DENSITY_PAIR = 19   # per pair per Newton-Raphson pass (q, f, f', two accumulations)
 FLOPS_FORCE_PAIR = 101    # per ordered pair (pressure, viscosity, conduction, energy, TwoSum-compensated m a)
 FLOPS_GRAVITY_PAIR = 38   # per ordered pair beyond the softening (r, 1/r^3 weight, TwoSum-compensated F)
-FLOPS_GRAVITY_NODE = 64   # per (particle, node) multipole term (r, powers of 1/r, Q r, r.Q.r, TwoSum-compensated a)
+FLOPS_GRAVITY_NODE = 49   # per (particle, node) multipole term (r, powers of 1/r, Q r, r.Q.r, the three sums)
 GRAVITY_N = 65536         # self-gravity measurement: isolated cloud of this many particles
 GRAVITY_TREE_N = 1_000_000  # the tree walk's larger cloud
 GRAVITY_THETA = 0.5       # opening angle of the tree-walk measurements

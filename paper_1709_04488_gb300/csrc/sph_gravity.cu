@@ -365,10 +365,10 @@ __global__ void __launch_bounds__(256) k_grav_moments(BatchView b)
 }
 
 // Acceleration (per unit G) at offset r from a node's centre of mass:
-// -M r/|r|^3 + Q r/|r|^5 - (5/2)(r.Q.r) r/|r|^7.
+// -M r/|r|^3 + Q r/|r|^5 - (5/2)(r.Q.r) r/|r|^7, added to plain sums (the
+// expansion's own error, ~theta^3, is far above their rounding).
 template <typename T>
-__device__ __forceinline__ void multipole_acc(T rx, T ry, T rz, T M, const T (&Q)[6], TwoSumAcc<T> &ax,
-                                              TwoSumAcc<T> &ay, TwoSumAcc<T> &az)
+__device__ __forceinline__ void multipole_acc(T rx, T ry, T rz, T M, const T (&Q)[6], T &ax, T &ay, T &az)
 {
     const T r2 = rx * rx + ry * ry + rz * rz;
     const T rinv = rsqrt_t(r2), rinv2 = rinv * rinv, rinv3 = rinv2 * rinv, rinv5 = rinv3 * rinv2;
@@ -377,9 +377,9 @@ __device__ __forceinline__ void multipole_acc(T rx, T ry, T rz, T M, const T (&Q
     const T qz = Q[2] * rx + Q[4] * ry + Q[5] * rz;
     const T rqr = rx * qx + ry * qy + rz * qz;
     const T k = -M * rinv3 - T(2.5) * rqr * rinv5 * rinv2;
-    ax.add(k * rx + qx * rinv5);
-    ay.add(k * ry + qy * rinv5);
-    az.add(k * rz + qz * rinv5);
+    ax += k * rx + qx * rinv5;
+    ay += k * ry + qy * rinv5;
+    az += k * rz + qz * rinv5;
 }
 
 // One warp per leaf of a problem with grav_theta > 0.  The walk classifies the
@@ -431,7 +431,8 @@ __global__ void __launch_bounds__(kTreeThreads) k_gravity_tree(BatchView b)
         }
         long long npair = 0, nnode = 0;  // terms this lane summed
         const T th2 = (T)(ps.ph.grav_theta * ps.ph.grav_theta);
-        TwoSumAcc<T> ax{T(0), T(0)}, ay{T(0), T(0)}, az{T(0), T(0)};
+        TwoSumAcc<T> ax{T(0), T(0)}, ay{T(0), T(0)}, az{T(0), T(0)};  // pair terms
+        T mx = T(0), my = T(0), mz = T(0);                              // multipole terms
         // classify node g of level `lvl`, stage it when it is used; returns 1 used, 2 opened
         auto visit = [&](int level, int first, int count) -> unsigned {
             const int c = first + lane;
@@ -478,7 +479,7 @@ __global__ void __launch_bounds__(kTreeThreads) k_gravity_tree(BatchView b)
                     const P q = s_p[wi][e];
                     const T Q[6] = {s_q[wi][e][0], s_q[wi][e][1], s_q[wi][e][2],
                                     s_q[wi][e][3], s_q[wi][e][4], s_q[wi][e][5]};
-                    multipole_acc(xi - q.x, yi - q.y, zi - q.z, q.w, Q, ax, ay, az);
+                    multipole_acc(xi - q.x, yi - q.y, zi - q.z, q.w, Q, mx, my, mz);
                 }
                 __syncwarp();
             }
@@ -546,7 +547,8 @@ __global__ void __launch_bounds__(kTreeThreads) k_gravity_tree(BatchView b)
             mask[lvl] = om;
         }
         // the lanes of each particle add their sums in a fixed order
-        double gx = (double)ax.s + (double)ax.c, gy = (double)ay.s + (double)ay.c, gz = (double)az.s + (double)az.c;
+        double gx = (double)ax.s + (double)ax.c + (double)mx, gy = (double)ay.s + (double)ay.c + (double)my,
+               gz = (double)az.s + (double)az.c + (double)mz;
         for (int o = S; o < kBranch; o <<= 1) {
             gx += __shfl_xor_sync(0xffffffffu, gx, o);
             gy += __shfl_xor_sync(0xffffffffu, gy, o);
