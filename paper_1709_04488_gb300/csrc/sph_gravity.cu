@@ -1,11 +1,13 @@
 // Self-gravity, long-range part of Eq. SPHSELFGRAV (Sec. 2.1.2): the
 // kernel-softened attraction
 //   g_i = -G sum_{j != i} m_j (phi'(r_ij,h_i) + phi'(r_ij,h_j))/2 r_hat_ij,
-// phi'(r,h) = M(r/h)/r^2 (Eq. GRAVFORCEKERNEL), by direct summation over every
-// particle of the problem.  The zeta term of the same equation runs in the
-// force pass with the neighbours.
+// phi'(r,h) = M(r/h)/r^2 (Eq. GRAVFORCEKERNEL), either by direct summation over
+// every particle of the problem (grav_theta = 0, k_gravity below) or by the
+// tree walk of Sec. 4.2 (k_grav_moments, k_gravity_tree further down).  The
+// zeta term of the same equation runs in the force pass with the neighbours.
+// During a block step only the particles whose step ends take the long range.
 //
-// Two particles per thread, sorted order; the blocks of a problem cover only
+// Direct sum: two particles per thread, sorted order; the blocks of a problem cover only
 // that problem's particles (each problem's first block is precomputed on the
 // host), and the partner particles stream through shared memory in tiles.
 // A problem too small to fill the GPU with one block per 256 particles splits
