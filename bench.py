@@ -516,6 +516,19 @@ def run_ours(args):
                "global_ms_same_time": glob_equiv, "speedup": glob_equiv / blk_ms,
                "timing": "host wall clock around one block step (one host round trip per tick)"}
         pbk.close()
+        # the same with the leaves kept and refitted between ticks (rebuilt every 4th)
+        with torch.cuda.stream(stream):
+            pbr = S.Problem(ab, S.make_params(S.PREC_MIXED, **pb_, block_levels=BLOCK_LEVELS, tree_rebuild_every=4),
+                            device=dev, stream=stream)
+            S.check(S.sph_density_h(pbr.ctx), "sph_density_h")
+            S.check(S.sph_forces(pbr.ctx), "sph_forces")
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        pbr.block_step()
+        torch.cuda.synchronize(dev)
+        blk["tree_reuse_4"] = {"block_ms": (time.perf_counter() - t0) * 1e3}
+        blk["tree_reuse_4"]["speedup"] = glob_equiv / blk["tree_reuse_4"]["block_ms"]
+        pbr.close()
         pgl.close()
         # self-gravity (tree walk) with block steps on the isolated cloud, the
         # combination of the paper's collapse benchmark

@@ -264,7 +264,8 @@ int sph_run(sph_ctx *ctx, int nsteps);
  * largest level at the last force pass; reactive: particles that take forces
  * shorten the steps of slower neighbours, which then end at the next tick of
  * their new level).  Needs a force evaluation first; leaves every particle
- * synchronised with fresh forces.  Writes Delta t_MAX to *dtmax and the
+ * synchronised with fresh forces.  tree_rebuild_every applies between ticks
+ * as between global steps.  Writes Delta t_MAX to *dtmax and the
  * number of particle force evaluations to *evals (either may be NULL).
  * Synchronises (one host round trip per tick where a step ends). */
 int sph_block_step(sph_ctx *ctx, double *dtmax, int64_t *evals);

@@ -636,15 +636,22 @@ int sph_block_step(sph_ctx *c, double *dtmax_out, int64_t *evals_out)
     long long k = 0, next = 0;
     CU(cudaMemcpyAsync(&next, b.scratch64 + 2, sizeof next, cudaMemcpyDeviceToHost, st));
     CU(cudaStreamSynchronize(st));
-    while (k < N) {
+    // tree reuse (Sec. 4.2) between ticks as between global steps: sort and
+    // build on every tree_rebuild_every-th tick, refit the kept leaves between
+    const int every = c->prm.tree_rebuild_every > 1 ? c->prm.tree_rebuild_every : 1;
+    for (int tick = 0; k < N; ++tick) {
         if (next <= k || next > N) return fail(SPH_ECUDA, "block step: bad next tick %lld after %lld", next, k);
+        const bool rebuild = tick % every == 0;
         CU(launch_reset_step(b, 1, st));
         CU(launch_block_drift(b, k, next, tau, st));
-        CU(launch_domain_and_keys(b, st));
-        CU(launch_radix_sort(b, st));
+        if (rebuild) {
+            CU(launch_domain_and_keys(b, st));
+            CU(launch_radix_sort(b, st));
+        }
         CU(launch_gather(b, st));
         CU(launch_block_stage(b, prec, next, st));  // which sorted particles end their step now
-        CU(launch_build_leaves(b, prec, st));
+        if (rebuild) CU(launch_build_leaves(b, prec, st));
+        else CU(launch_update_leaves(b, prec, st));
         CU(launch_density(b, prec, 1, st));  // solves the active particles, restages the others
         CU(launch_refit(b, prec, st));
         CU(launch_forces(b, prec, st));
@@ -666,7 +673,7 @@ int sph_block_step(sph_ctx *c, double *dtmax_out, int64_t *evals_out)
     if (dtmax_out) *dtmax_out = dtmax;
     if (evals_out) *evals_out = evals;
     c->have_forces = true;
-    c->since_build = 0;
+    c->since_build = every;  // the next global step rebuilds
     return rc;
 }
 

@@ -75,6 +75,23 @@ def test_sedov_block_step_matches_oracle(S, oracle_mod, prec):
     assert np.max(np.abs(g["rho"] / ref.rho - 1.0)) < (1e-10 if fp64 else 1e-4)
 
 
+def test_block_step_with_tree_reuse_matches_oracle(S, oracle_mod):
+    """Leaves kept and refitted between ticks (tree_rebuild_every = 4): the
+    same neighbour sets, so the same levels and evaluations as the oracle."""
+    O = oracle_mod
+    a, p = ics.sedov(16)
+    ref, lv_ref, oo = _oracle_block(O, a, p, 5)
+    prob = S.Problem(a, S.make_params(S.PREC_FP64, **p, block_levels=5, tree_rebuild_every=4))
+    prob.density_h()
+    prob.forces()
+    dtmax, evals = prob.block_step()
+    assert np.array_equal(prob.levels(), lv_ref) and evals == oo[0][1]
+    g = prob.numpy()
+    for f in ("vx", "vy", "vz", "u"):
+        assert _scale_err(g, ref, f) < 1e-10, f
+    prob.step(-1.0)  # a global step after the block (it rebuilds the leaves)
+
+
 def test_two_block_steps_and_limiter_history(S, oracle_mod):
     """The neighbours' largest levels carry from one block step to the next
     (the predictive limiter at the second block's start)."""
