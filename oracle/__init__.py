@@ -88,7 +88,9 @@ _IP = C.POINTER(C.c_int32)
 _FIELDS_D = ["x", "y", "z", "vx", "vy", "vz", "u", "m", "h",
              "rho", "omega", "P", "c", "ax", "ay", "az", "du", "vsig"]
 _FIELDS_I = ["nngb", "iters"]
-_FIELDS_A = ["alpha", "dalpha", "zeta"]  # viscosity switch: alpha and its rate; gravity: zeta
+# viscosity switch: alpha and its rate (Morris & Monaghan); gravity: zeta;
+# Cullen & Dehnen: div v of the last force evaluation and the limiter xi
+_FIELDS_A = ["alpha", "dalpha", "zeta", "cd_divv", "cd_xi"]
 
 
 class _State(C.Structure):
@@ -147,6 +149,8 @@ def lib():
         L.orc_forces_subset.argtypes = [PP, C.c_int64, SP, C.c_int64, C.POINTER(C.c_int64), C.c_double]
         L.orc_block_step.restype = C.c_int
         L.orc_block_step.argtypes = [PP, C.c_int64, SP, _IP, _IP, C.c_int, C.c_int, _DP, C.POINTER(C.c_int64)]
+        L.orc_cd_update.restype = None
+        L.orc_cd_update.argtypes = [PP, C.c_int64, SP, _DP, C.c_double]
         L.orc_gravity_accel.restype = C.c_int
         L.orc_gravity_accel.argtypes = [PP, C.c_int64, SP, _DP, _DP, _DP]
         L.orc_multipole_accel.restype = None
@@ -178,7 +182,7 @@ class Params:
     use_grid: bool = False
     kernel: int = 0                 # 0 = M4 cubic spline (support 2h), 1 = M6 quintic (3h)
     ac_signal: int = 0              # conductivity signal speed: 0 Wadsley |v.r_hat|, 1 Price sqrt(|dP|/rho_bar)
-    av_switch: int = 0              # 1: Morris & Monaghan viscosity switch (alpha per particle)
+    av_switch: int = 0              # 1: Morris & Monaghan, 2: Cullen & Dehnen viscosity switch (alpha per particle)
     alpha_min: float = 0.1          # switch: floor of alpha
     av_decay: float = 0.1           # switch: tau = h / (av_decay c)
     gravity: int = 0                # 1: self-gravity (isolated, M4), Eq. SPHSELFGRAV
@@ -366,6 +370,13 @@ def block_step(p: Params, s: State, level, ngb_maxlev, L: int, dl: int = 2):
     rc = lib().orc_block_step(C.byref(p._c()), s.n, C.byref(s._c()), level.ctypes.data_as(_IP),
                               ngb_maxlev.ctypes.data_as(_IP), int(L), int(dl), C.byref(dtmax), counts)
     return rc, dtmax.value, counts[0], counts[1]
+
+
+def cd_update(p: Params, s: State, d_old, dt: float) -> None:
+    """The Cullen & Dehnen alpha update after a step of dt, d_old being div v
+    at the step's start (the state holds the new div v, xi, h and v_sig)."""
+    d = np.ascontiguousarray(d_old, dtype=np.float64)
+    lib().orc_cd_update(C.byref(p._c()), s.n, C.byref(s._c()), d.ctypes.data_as(_DP), float(dt))
 
 
 def gravity_accel(p: Params, s: State):

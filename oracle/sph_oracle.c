@@ -63,7 +63,8 @@ typedef struct {
     int ac_signal;           /* conductivity signal speed: 0 = Wadsley |v_ij . r_hat|,
                                 1 = Price sqrt(|P_i - P_j| / rho_bar) (Sec. 2.1.1) */
     int av_switch;           /* 0: constant alpha_av; 1: Morris & Monaghan (1997) switch,
-                                one alpha per particle (Sec. 2.1.1) */
+                                one alpha per particle (Sec. 2.1.1); 2: Cullen & Dehnen
+                                (2010) switch (Sec. 2.1.1 names both) */
     double alpha_min;        /* switch: floor the viscosity decays to */
     double av_decay;         /* switch: decay time tau = h / (av_decay c) */
     int gravity;             /* 1: self-gravity, Eq. SPHSELFGRAV (isolated, M4 kernel) */
@@ -83,6 +84,8 @@ typedef struct {
     int32_t *nngb, *iters;
     double *alpha, *dalpha;  /* switch: viscosity parameter per particle and its rate */
     double *zeta;            /* gravity: zeta of Eq. GRADHZETA (written by the density solve) */
+    double *cd_divv;         /* Cullen & Dehnen: div v of the last force evaluation (in: the one before) */
+    double *cd_xi;           /* Cullen & Dehnen: the limiter xi of the last force evaluation */
 } orc_state;
 
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_EBOX = -2, ORC_ENOCONV = -3, ORC_ENOMEM = -9 };
@@ -423,7 +426,7 @@ static int params_ok(const orc_params *p, int64_t n)
     if (p->eos == 1 && !(p->cs_iso > 0)) return 0;
     if (p->kernel != 0 && p->kernel != 1) return 0;
     if (p->ac_signal != 0 && p->ac_signal != 1) return 0;
-    if (p->av_switch != 0 && p->av_switch != 1) return 0;
+    if (p->av_switch < 0 || p->av_switch > 2) return 0;
     if (p->av_switch && !(p->alpha_av > 0 && p->alpha_min >= 0 && p->alpha_min <= p->alpha_av && p->av_decay > 0))
         return 0;
     if (p->gravity != 0 && p->gravity != 1) return 0;
@@ -931,6 +934,56 @@ static double av_rate(const orc_params *p, const orc_state *s, int64_t i, double
     return -(s->alpha[i] - p->alpha_min) * p->av_decay * s->c[i] / s->h[i] + src;
 }
 
+/* Cullen & Dehnen (2010) switch, as stated here (Sec. 2.1.1 names it; the
+   equations are the published ones, with two readings marked):
+   - the velocity gradient V_i = -(1/(Omega_i rho_i)) sum_j m_j v_ij (x) grad_i W(r_ij, h_i),
+     D_i = tr V_i = div v_i, S_i = sym(V_i) - D_i/3 I, the traceless shear;
+   - R_i = (1/rho_i) sum_j sign(D_j) m_j W(r_ij, h_i), self included, with the
+     signs of the previous force evaluation (reading: one pass), sign(0) = +1;
+   - xi_i = q^2 / (q^2 + tr(S_i S_i^T)), q = 2 (1 - R_i)^4 D_i (0 when both vanish);
+   - the step applies, with dD/dt = (D_new - D_old)/dt (reading: the time
+     derivative by finite differences between force evaluations),
+     A_i = xi_i max(-dD/dt, 0), alpha_loc = alpha_max h^2 A / (v_sig^2 + h^2 A),
+     alpha <- alpha_loc if alpha < alpha_loc, else alpha_loc + (alpha - alpha_loc)
+     exp(-dt/tau) with tau = h / (2 av_decay v_sig); alpha_max = alpha_av. */
+typedef struct {
+    kahan_t g[9]; /* sum_j m_j v_ij,a grad_b W */
+    kahan_t r;    /* sum_j sign(D_j) m_j W */
+} cd_sums_t;
+
+static void cd_finish(const orc_params *p, const orc_state *s, int64_t i, const cd_sums_t *c, double *D, double *xi)
+{
+    const double f = -1.0 / (s->omega[i] * s->rho[i]);
+    double V[9];
+    for (int k = 0; k < 9; ++k) V[k] = f * c->g[k].s;
+    const double d = V[0] + V[4] + V[8];
+    double ss = 0.0;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double sab = 0.5 * (V[3 * a + b] + V[3 * b + a]) - (a == b ? d / 3.0 : 0.0);
+            ss += sab * sab;
+        }
+    const double R = c->r.s / s->rho[i];
+    const double om = 1.0 - R, q = 2.0 * om * om * om * om * d;
+    *D = d;
+    *xi = (q * q + ss) > 0 ? q * q / (q * q + ss) : 0.0;
+    (void)p;
+}
+
+/* the Cullen & Dehnen update of alpha after a step of dt (D_old: div v at the step's start) */
+void orc_cd_update(const orc_params *p, int64_t n, orc_state *s, const double *d_old, double dt)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        const double ddot = (s->cd_divv[i] - d_old[i]) / dt;
+        const double A = s->cd_xi[i] * (ddot < 0 ? -ddot : 0.0);
+        const double h2A = s->h[i] * s->h[i] * A;
+        const double vs = s->vsig[i];
+        const double aloc = h2A > 0 ? p->alpha_av * h2A / (vs * vs + h2A) : 0.0;
+        if (s->alpha[i] < aloc) s->alpha[i] = aloc;
+        else s->alpha[i] = aloc + (s->alpha[i] - aloc) * exp(-dt * 2.0 * p->av_decay * vs / s->h[i]);
+    }
+}
+
 /* Signal speed of the artificial conductivity (Sec. 2.1.1): Wadsley's
    |v_ij . r_hat_ij| by default, or Price's sqrt(|P_i - P_j| / rho_bar_ij). */
 static double ac_signal_speed(const orc_params *p, const orc_state *s, int64_t i, int64_t j, double vdr,
@@ -963,7 +1016,8 @@ int orc_forces(const orc_params *p, int64_t n, orc_state *s) { return forces_imp
    among its force neighbours. */
 static int forces_impl(const orc_params *p, int64_t n, orc_state *s, const orc_block_t *blk)
 {
-    if (p && p->av_switch && (!s->alpha || !s->dalpha)) return ORC_EINVAL;
+    if (p && p->av_switch == 1 && (!s->alpha || !s->dalpha)) return ORC_EINVAL;
+    if (p && p->av_switch == 2 && (!s->alpha || !s->cd_divv || !s->cd_xi)) return ORC_EINVAL;
     if (p && p->gravity && !s->zeta) return ORC_EINVAL;
     if (!params_ok(p, n)) return ORC_EINVAL;
     if (n == 0) return ORC_OK;
@@ -983,6 +1037,21 @@ static int forces_impl(const orc_params *p, int64_t n, orc_state *s, const orc_b
     }
     const double aac = p->alpha_ac;
     int status = ORC_OK;
+    /* Cullen & Dehnen: the previous div v (its signs enter R) and the new one */
+    double *dprev = NULL, *dnew = NULL;
+    if (p->av_switch == 2) {
+        dprev = (double *)malloc(sizeof(double) * (size_t)n);
+        dnew = (double *)malloc(sizeof(double) * (size_t)n);
+        if (!dprev || !dnew) {
+            free(dprev);
+            free(dnew);
+            kd_free(&kt);
+            grid_free(&g);
+            return ORC_ENOMEM;
+        }
+        memcpy(dprev, s->cd_divv, sizeof(double) * (size_t)n);
+        memcpy(dnew, s->cd_divv, sizeof(double) * (size_t)n);
+    }
 #pragma omp parallel
     {
         idlist_t buf = {0, 0, 0};
@@ -997,6 +1066,8 @@ static int forces_impl(const orc_params *p, int64_t n, orc_state *s, const orc_b
             }
             const double Ai = s->P[i] / (s->omega[i] * s->rho[i] * s->rho[i]);
             kahan_t ax = {0, 0}, ay = {0, 0}, az = {0, 0}, du = {0, 0}, dv = {0, 0};
+            cd_sums_t cds;
+            memset(&cds, 0, sizeof cds);
             double vsig = 2.0 * s->c[i]; /* no neighbour: c_i + c_i */
             int have = 0;
             int32_t maxlev = -1; /* no neighbour */
@@ -1022,6 +1093,12 @@ static int forces_impl(const orc_params *p, int64_t n, orc_state *s, const orc_b
                 double fav = 0.0, duav = 0.0, alpha, beta;
                 av_pair(p, s, i, j, &alpha, &beta);
                 kadd(&dv, mj * vdr * gi); /* sum_j m_j v_ij . grad_i W(h_i) */
+                if (p->av_switch == 2) {
+                    const double vv[3] = {vxij, vyij, vzij}, rh[3] = {rx, ry, rz};
+                    for (int a2 = 0; a2 < 3; ++a2)
+                        for (int b2 = 0; b2 < 3; ++b2) kadd(&cds.g[3 * a2 + b2], mj * vv[a2] * rh[b2] * gi);
+                    kadd(&cds.r, (dprev[j] < 0 ? -1.0 : 1.0) * mj * orc_Wk(p->kernel, r, s->h[i]));
+                }
                 double vs = s->c[i] + s->c[j] - beta * (vdr < 0 ? vdr : 0.0);
                 if (!have || vs > vsig) vsig = vs;
                 have = 1;
@@ -1047,13 +1124,20 @@ static int forces_impl(const orc_params *p, int64_t n, orc_state *s, const orc_b
             s->az[i] = az.s;
             s->du[i] = (p->eos == 0) ? du.s : 0.0;
             s->vsig[i] = vsig;
-            if (p->av_switch) s->dalpha[i] = av_rate(p, s, i, dv.s);
+            if (p->av_switch == 1) s->dalpha[i] = av_rate(p, s, i, dv.s);
+            if (p->av_switch == 2) {
+                kadd(&cds.r, (dprev[i] < 0 ? -1.0 : 1.0) * s->m[i] * orc_Wk(p->kernel, 0.0, s->h[i])); /* self */
+                cd_finish(p, s, i, &cds, &dnew[i], &s->cd_xi[i]);
+            }
             if (blk) blk->ngb_maxlev[i] = maxlev;
         }
         free(buf.v);
     }
     if (gp) grid_free(&g);
     kd_free(&kt);
+    if (dnew) memcpy(s->cd_divv, dnew, sizeof(double) * (size_t)n);
+    free(dprev);
+    free(dnew);
     return status;
 }
 
@@ -1095,7 +1179,8 @@ static double wrap(double x, double lo, double L)
 int orc_step(const orc_params *p, int64_t n, orc_state *s, double dt)
 {
     if (!params_ok(p, n) || !(dt > 0)) return ORC_EINVAL;
-    if (p->av_switch && (!s->alpha || !s->dalpha)) return ORC_EINVAL;
+    if (p->av_switch == 1 && (!s->alpha || !s->dalpha)) return ORC_EINVAL;
+    if (p->av_switch == 2 && (!s->alpha || !s->cd_divv || !s->cd_xi)) return ORC_EINVAL;
     double *vh = (double *)malloc((size_t)(n > 0 ? n : 1) * 5 * sizeof(double));
     if (!vh) return ORC_ENOMEM;
     double *vhx = vh, *vhy = vh + n, *vhz = vh + 2 * n, *uh = vh + 3 * n, *ah = vh + 4 * n;
@@ -1105,7 +1190,7 @@ int orc_step(const orc_params *p, int64_t n, orc_state *s, double dt)
         vhy[i] = s->vy[i] + 0.5 * s->ay[i] * dt;
         vhz[i] = s->vz[i] + 0.5 * s->az[i] * dt;
         uh[i] = adi ? s->u[i] + 0.5 * s->du[i] * dt : s->u[i];
-        if (p->av_switch) { /* the switch's alpha is kicked and predicted like u */
+        if (p->av_switch == 1) { /* the switch's alpha is kicked and predicted like u */
             ah[i] = s->alpha[i] + 0.5 * s->dalpha[i] * dt;
             s->alpha[i] = ah[i] + 0.5 * s->dalpha[i] * dt;
         }
@@ -1123,14 +1208,27 @@ int orc_step(const orc_params *p, int64_t n, orc_state *s, double dt)
         s->vz[i] = vhz[i] + 0.5 * s->az[i] * dt;
         if (adi) s->u[i] = uh[i] + 0.5 * s->du[i] * dt;
     }
+    double *d_old = NULL; /* Cullen & Dehnen: div v at the step's start */
+    if (p->av_switch == 2) {
+        d_old = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+        if (!d_old) {
+            free(vh);
+            return ORC_ENOMEM;
+        }
+        memcpy(d_old, s->cd_divv, sizeof(double) * (size_t)n);
+    }
     int rc = orc_density(p, n, s);
     int rc2 = (rc == ORC_OK || rc == ORC_ENOCONV) ? orc_forces(p, n, s) : rc;
+    if (d_old) {
+        if (rc2 == ORC_OK) orc_cd_update(p, n, s, d_old, dt);
+        free(d_old);
+    }
     for (int64_t i = 0; i < n; ++i) {
         s->vx[i] = vhx[i] + 0.5 * s->ax[i] * dt;
         s->vy[i] = vhy[i] + 0.5 * s->ay[i] * dt;
         s->vz[i] = vhz[i] + 0.5 * s->az[i] * dt;
         if (adi) s->u[i] = uh[i] + 0.5 * s->du[i] * dt;
-        if (p->av_switch) s->alpha[i] = ah[i] + 0.5 * s->dalpha[i] * dt;
+        if (p->av_switch == 1) s->alpha[i] = ah[i] + 0.5 * s->dalpha[i] * dt;
     }
     free(vh);
     return rc2 ? rc2 : rc;
@@ -1229,7 +1327,9 @@ int orc_block_step(const orc_params *p, int64_t n, orc_state *s, int32_t *level,
                    double *dtmax_out, int64_t *counts)
 {
     if (!params_ok(p, n) || L < 0 || L > 30 || dl < 1) return ORC_EINVAL;
-    if (p->av_switch && (!s->alpha || !s->dalpha)) return ORC_EINVAL;
+    if (p->av_switch == 2) return ORC_EINVAL; /* (not combined with block steps) */
+    if (p->av_switch == 1 && (!s->alpha || !s->dalpha)) return ORC_EINVAL;
+    if (p->av_switch == 2 && (!s->alpha || !s->cd_divv || !s->cd_xi)) return ORC_EINVAL;
     if (p->gravity && !s->zeta) return ORC_EINVAL;
     if (n == 0) return ORC_OK;
     const int adi = (p->eos == 0);
@@ -1270,7 +1370,7 @@ int orc_block_step(const orc_params *p, int64_t n, orc_state *s, int32_t *level,
         vhy[i] = s->vy[i] + s->ay[i] * hd;
         vhz[i] = s->vz[i] + s->az[i] * hd;
         uh[i] = adi ? s->u[i] + s->du[i] * hd : s->u[i];
-        ah[i] = p->av_switch ? s->alpha[i] + s->dalpha[i] * hd : 0.0;
+        ah[i] = p->av_switch == 1 ? s->alpha[i] + s->dalpha[i] * hd : 0.0;
     }
     int64_t k = 0, npass = 0, nevals = 0;
     int rc = ORC_OK;
@@ -1299,7 +1399,7 @@ int orc_block_step(const orc_params *p, int64_t n, orc_state *s, int32_t *level,
             s->vy[i] = vhy[i] + s->ay[i] * dp;
             s->vz[i] = vhz[i] + s->az[i] * dp;
             if (adi) s->u[i] = uh[i] + s->du[i] * dp;
-            if (p->av_switch) s->alpha[i] = ah[i] + s->dalpha[i] * dp;
+            if (p->av_switch == 1) s->alpha[i] = ah[i] + s->dalpha[i] * dp;
             req[i] = -1;
         }
         int64_t na = 0;
@@ -1321,7 +1421,7 @@ int orc_block_step(const orc_params *p, int64_t n, orc_state *s, int32_t *level,
                 s->vy[i] = vhy[i] + s->ay[i] * hd;
                 s->vz[i] = vhz[i] + s->az[i] * hd;
                 if (adi) s->u[i] = uh[i] + s->du[i] * hd;
-                if (p->av_switch) s->alpha[i] = ah[i] + s->dalpha[i] * hd;
+                if (p->av_switch == 1) s->alpha[i] = ah[i] + s->dalpha[i] * hd;
                 if (k == N) continue;
                 int l = level_of(particle_dt(p, s, i), dtmax, L);
                 if (l < ngb_maxlev[i] - dl) l = ngb_maxlev[i] - dl;
@@ -1335,7 +1435,7 @@ int orc_block_step(const orc_params *p, int64_t n, orc_state *s, int32_t *level,
                 vhy[i] = s->vy[i] + s->ay[i] * hn;
                 vhz[i] = s->vz[i] + s->az[i] * hn;
                 uh[i] = adi ? s->u[i] + s->du[i] * hn : s->u[i];
-                if (p->av_switch) ah[i] = s->alpha[i] + s->dalpha[i] * hn;
+                if (p->av_switch == 1) ah[i] = s->alpha[i] + s->dalpha[i] * hn;
             } else if (req[i] > level[i]) { /* reactive limiter: end the step early */
                 const int64_t st = N >> req[i];
                 const int64_t ke = (k / st + 1) * st; /* next tick on the new level's grid */
@@ -1345,7 +1445,7 @@ int orc_block_step(const orc_params *p, int64_t n, orc_state *s, int32_t *level,
                     vhy[i] += s->ay[i] * corr;
                     vhz[i] += s->az[i] * corr;
                     if (adi) uh[i] += s->du[i] * corr;
-                    if (p->av_switch) ah[i] += s->dalpha[i] * corr;
+                    if (p->av_switch == 1) ah[i] += s->dalpha[i] * corr;
                     t1[i] = ke;
                     level[i] = req[i];
                 }
@@ -1474,7 +1574,8 @@ int orc_forces_subset(const orc_params *p, int64_t n, orc_state *s, int64_t nsub
                       double hmax)
 {
     if (!params_ok(p, n) || nsub < 0 || !(hmax > 0)) return ORC_EINVAL;
-    if (p->av_switch && (!s->alpha || !s->dalpha)) return ORC_EINVAL;
+    if (p->av_switch == 1 && (!s->alpha || !s->dalpha)) return ORC_EINVAL;
+    if (p->av_switch == 2 && (!s->alpha || !s->cd_divv || !s->cd_xi)) return ORC_EINVAL;
     if (n == 0 || nsub == 0) return ORC_OK;
     grid_t g;
     memset(&g, 0, sizeof g);
@@ -1486,6 +1587,21 @@ int orc_forces_subset(const orc_params *p, int64_t n, orc_state *s, int64_t nsub
     }
     const double aac = p->alpha_ac;
     int status = ORC_OK;
+    /* Cullen & Dehnen: the previous div v (its signs enter R) and the new one */
+    double *dprev = NULL, *dnew = NULL;
+    if (p->av_switch == 2) {
+        dprev = (double *)malloc(sizeof(double) * (size_t)n);
+        dnew = (double *)malloc(sizeof(double) * (size_t)n);
+        if (!dprev || !dnew) {
+            free(dprev);
+            free(dnew);
+            kd_free(&kt);
+            grid_free(&g);
+            return ORC_ENOMEM;
+        }
+        memcpy(dprev, s->cd_divv, sizeof(double) * (size_t)n);
+        memcpy(dnew, s->cd_divv, sizeof(double) * (size_t)n);
+    }
 #pragma omp parallel
     {
         idlist_t buf = {0, 0, 0};
@@ -1500,6 +1616,8 @@ int orc_forces_subset(const orc_params *p, int64_t n, orc_state *s, int64_t nsub
             }
             const double Ai = s->P[i] / (s->omega[i] * s->rho[i] * s->rho[i]);
             kahan_t ax = {0, 0}, ay = {0, 0}, az = {0, 0}, du = {0, 0}, dv = {0, 0};
+            cd_sums_t cds;
+            memset(&cds, 0, sizeof cds);
             double vsig = 2.0 * s->c[i];
             int have = 0;
             for (int64_t q = 0; q < buf.n; ++q) {
@@ -1522,6 +1640,12 @@ int orc_forces_subset(const orc_params *p, int64_t n, orc_state *s, int64_t nsub
                 double fav = 0.0, duav = 0.0, alpha, beta;
                 av_pair(p, s, i, j, &alpha, &beta);
                 kadd(&dv, mj * vdr * gi); /* sum_j m_j v_ij . grad_i W(h_i) */
+                if (p->av_switch == 2) {
+                    const double vv[3] = {vxij, vyij, vzij}, rh[3] = {rx, ry, rz};
+                    for (int a2 = 0; a2 < 3; ++a2)
+                        for (int b2 = 0; b2 < 3; ++b2) kadd(&cds.g[3 * a2 + b2], mj * vv[a2] * rh[b2] * gi);
+                    kadd(&cds.r, (dprev[j] < 0 ? -1.0 : 1.0) * mj * orc_Wk(p->kernel, r, s->h[i]));
+                }
                 double vs = s->c[i] + s->c[j] - beta * (vdr < 0 ? vdr : 0.0);
                 if (!have || vs > vsig) vsig = vs;
                 have = 1;
@@ -1547,11 +1671,18 @@ int orc_forces_subset(const orc_params *p, int64_t n, orc_state *s, int64_t nsub
             s->az[i] = az.s;
             s->du[i] = (p->eos == 0) ? du.s : 0.0;
             s->vsig[i] = vsig;
-            if (p->av_switch) s->dalpha[i] = av_rate(p, s, i, dv.s);
+            if (p->av_switch == 1) s->dalpha[i] = av_rate(p, s, i, dv.s);
+            if (p->av_switch == 2) {
+                kadd(&cds.r, (dprev[i] < 0 ? -1.0 : 1.0) * s->m[i] * orc_Wk(p->kernel, 0.0, s->h[i])); /* self */
+                cd_finish(p, s, i, &cds, &dnew[i], &s->cd_xi[i]);
+            }
         }
         free(buf.v);
     }
     grid_free(&g);
     kd_free(&kt);
+    if (dnew) memcpy(s->cd_divv, dnew, sizeof(double) * (size_t)n);
+    free(dprev);
+    free(dnew);
     return status;
 }
