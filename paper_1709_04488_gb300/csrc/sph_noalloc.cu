@@ -6,7 +6,7 @@
 // host that owns every byte of device memory through its own pool (so that a
 // raw allocation would bypass its accounting or fail once the pool has
 // reserved the free memory), a plug-in called back from such a host, or a
-// real-time loop that must not enter the driver's allocator can still call
+// real-time loop that must not enter the CUDA allocator can still call
 // this with its own input and output arrays.  The price is a fixed scratch
 // area that every GPU using the library keeps until the process exits, and a
 // cap on the problem size.
