@@ -97,6 +97,35 @@ def test_workspace_bytes_and_validation(S):
     assert S.sph_workspace_bytes(10, bad) == 0
 
 
+def test_gravity_and_block_step_parameters(S):
+    """Defaults (direct summation, c_grav 0.5, no block steps, gap 2) and the
+    host-side validation of the self-gravity and block-step parameters; the
+    workspace grows by the tree walk's and the block steps' arrays."""
+    p = S.sph_params_default()
+    assert p.gravity == 0 and p.grav_theta == 0.0 and p.c_grav == 0.5
+    assert p.block_levels == 0 and p.block_gap == 2
+
+    def iso(**kw):
+        q = S.make_params(S.PREC_MIXED, periodic=False, **kw)
+        return S.sph_workspace_bytes(20000, q)
+
+    direct = iso(gravity=1, G=1.0)
+    tree = iso(gravity=1, G=1.0, grav_theta=0.5)
+    assert 0 < direct and 0 < tree and tree != direct
+    assert iso(gravity=1, G=0.0) == 0
+    assert iso(gravity=1, G=1.0, grav_theta=1.01) == 0
+    assert iso(gravity=1, G=1.0, grav_theta=-0.5) == 0
+    assert iso(gravity=1, G=1.0, c_grav=0.0) == 0
+    assert iso(gravity=1, G=1.0, kernel=S.KERNEL_M6) == 0
+    assert S.sph_workspace_bytes(20000, S.make_params(S.PREC_MIXED, gravity=1, G=1.0)) == 0  # periodic
+    plain = iso()
+    blk = iso(block_levels=6)
+    assert blk > plain
+    assert iso(block_levels=21) == 0 and iso(block_levels=-1) == 0
+    assert iso(block_levels=4, block_gap=0) == 0
+    assert iso(block_levels=4, gravity=1, G=1.0, grav_theta=0.5) > 0
+
+
 def test_setup_rejects_bad_arguments_without_a_gpu(S):
     p = S.sph_params_default()
     st = S.State()
