@@ -1,12 +1,16 @@
-"""Benchmark of the GB300 SPH hot path: one KDK step of the 3D Sod shock tube
-(128x16x16 | 64x8x8 = 36864 particles, periodic [0,1)x[0,1/8)^2, gamma 1.4),
-FP32 pair arithmetic with FP64 positions, integration and reductions.
+"""Benchmark of the GB300 SPH hot path on the largest single-GPU
+configuration: the isolated turbulent cloud of 8e6 particles (rho ~ 1/(1 +
+r^2/a^2), a = 0.1, radius 1, isothermal, Mach-5 velocity field with P(k) ~
+k^-4), FP32 pair arithmetic with FP64 positions, integration and reductions.
 
 One step = kick-drift, Morton sort, leaf/tree build, density/h Newton-Raphson
 solve, forces with viscosity and conductivity, closing kick and the FP64
 reductions (every row of the hot path), replayed as one captured CUDA graph.
+The roofline's ceiling is the FP32 fused multiply-add throughput measured in
+the same run (the pair arithmetic is bound by that pipe).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload cloud|sedov|sod]
 
 Prints one JSON line.  Under torchrun (N > 1) every rank steps its own replica
 of the problem (independent problems, no data-path collective); the timing is
@@ -34,7 +38,22 @@ WORKLOADS = {
     "sedov": "sedov3d_1e6: 100^3 jittered lattice, periodic unit cube, E=1 on 64 central particles, gamma=5/3, CFL KDK steps",
     "cloud": "cloud_8e6: isolated sphere rho ~ 1/(1+r^2/a^2), a=0.1, isothermal, Mach-5 k^-4 velocity field, CFL KDK steps",
 }
-WORKLOAD = WORKLOADS["sod"]
+DEFAULT_WORKLOAD = "cloud"  # the largest configuration that fits one GPU
+# down-sampled copies of each workload the CPU oracle is timed on (same
+# generator and seed): particles at all host threads, particles at one thread
+ORACLE_SAMPLES = {"cloud": (200_000, 50_000), "sedov": (59 ** 3, 37 ** 3), "sod": (36864, 36864)}
+FULL_N = {"cloud": 8_000_000, "sedov": 1_000_000, "sod": 36864}
+
+
+def sample_ics(name, n):
+    """The workload's generator at n particles (n is ignored for Sod, whose
+    36864 particles the oracle steps in full)."""
+    from paper_1709_04488_gb300 import ics
+    if name == "cloud":
+        return ics.cloud(n, seed=4)
+    if name == "sedov":
+        return ics.sedov(int(round(n ** (1.0 / 3.0))))
+    return ics.sod()
 # algorithmic flops per in-range pair, counted from the kernels' source
 FLOPS_DENSITY_PAIR = 19   # per pair per Newton-Raphson pass (q, f, f', two accumulations)
 FLOPS_FORCE_PAIR = 101    # per ordered pair (pressure, viscosity, conduction, energy, TwoSum-compensated m a)
@@ -60,16 +79,17 @@ def parse():
     ap.add_argument("--no-gravity", action="store_true", help="skip the self-gravity measurement")
     ap.add_argument("--no-block", action="store_true", help="skip the block time-step measurement")
     ap.add_argument("--lpp", type=int, default=0, help="lanes per particle (0: autotuned)")
-    ap.add_argument("--workload", default="sod", choices=sorted(WORKLOADS),
-                    help="sod (the default measured configuration), sedov or cloud")
-    ap.add_argument("--serve", type=int, default=150,
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS),
+                    help="cloud (8e6, the default: the largest single-GPU configuration), sedov (1e6) or sod (36864)")
+    ap.add_argument("--no-sod", action="store_true", help="skip the Sod-36864 side measurement")
+    ap.add_argument("--serve", type=int, default=2000,
                     help="requests in the serving measurement (0 skips it)")
-    ap.add_argument("--serve-load", type=float, nargs="*", default=[0.7],
+    ap.add_argument("--serve-load", type=float, nargs="*", default=[0.5, 0.7, 0.9],
                     help="offered loads as fractions of the saturated batched throughput")
     return ap.parse_args()
 
 
-def workload(name="sod"):
+def workload(name=DEFAULT_WORKLOAD):
     from paper_1709_04488_gb300 import ics
     return {"sod": ics.sod, "sedov": ics.sedov, "cloud": ics.cloud}[name]()
 
@@ -124,23 +144,43 @@ def dist_env():
     return rank, world, local
 
 
-def oracle_sample(seconds=12.0, max_steps=50):
-    """The oracle as it stands, stepping the same workload on the host cores
-    until about `seconds` have passed; returns (updates/s, cores, steps, n)."""
+def oracle_sample(name, threads=0, warm=1, steps=1):
+    """The oracle as it stands on a down-sampled copy of workload `name`: one
+    untimed density + force evaluation (and `warm` untimed KDK steps), then
+    `steps` timed KDK steps with the CFL step.  threads = 0 uses every host
+    thread.  Returns (updates/s, threads used, particles, mean neighbours)."""
     import oracle as O
-    a, p = workload()
+    n_all, n_one = ORACLE_SAMPLES[name]
+    a, p = sample_ics(name, n_all if threads == 0 else n_one)
+    O.set_num_threads(threads if threads > 0 else (os.cpu_count() or 1))
     P = O.Params(**p, use_grid=True)
     s = O.State(**a)
-    t0 = time.perf_counter()
     assert O.density(P, s) == O.OK and O.forces(P, s) == O.OK
-    t_setup = time.perf_counter() - t0
-    steps = 0
-    t0 = time.perf_counter()
-    while steps < max_steps and (steps == 0 or time.perf_counter() - t0 < seconds):
+    for _ in range(warm):
         assert O.step(P, s, O.cfl_dt(P, s)) == O.OK
-        steps += 1
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        assert O.step(P, s, O.cfl_dt(P, s)) == O.OK
     dt = time.perf_counter() - t0
-    return s.n * steps / dt, O.num_threads(), steps, s.n, t_setup
+    return s.n * steps / dt, O.num_threads(), s.n, float(np.mean(s.nngb))
+
+
+def cpu_baselines(name, ngb_full, n_full):
+    """The oracle's per-pair cost on the down-sampled copies, at every host
+    thread and at one, extrapolated to the full workload by the ratio of
+    mean neighbour counts (Sod is timed in full, not extrapolated)."""
+    out = []
+    for threads in (0, 1):
+        v, cores, ns, ngb = oracle_sample(name, threads, warm=0 if threads == 1 else 1)
+        extrap = ns != n_full
+        val = v * (ngb / ngb_full if extrap and ngb_full > 0 else 1.0)
+        out.append({"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                    "extrapolated": extrap,
+                    "sample": (f"one KDK step of a {ns}-particle copy of the workload (same generator and seed, "
+                               f"grid prefilter, mean {ngb:.1f} neighbours) after one untimed evaluation"
+                               + (f"; per-pair cost x the full workload's {ngb_full:.1f} neighbours per particle"
+                                  if extrap else ""))})
+    return out
 
 
 def run_reference(args):
@@ -148,7 +188,10 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle as O
-    a, p = workload()
+    name = args.workload
+    n_all, _ = ORACLE_SAMPLES[name]
+    a, p = sample_ics(name, n_all)
+    O.set_num_threads(os.cpu_count() or 1)
     P = O.Params(**p, use_grid=True)
     s = O.State(**a)
     assert O.density(P, s) == O.OK and O.forces(P, s) == O.OK
@@ -159,15 +202,17 @@ def run_reference(args):
         assert O.step(P, s, O.cfl_dt(P, s)) == O.OK
     el = time.perf_counter() - t0
     v = s.n * args.steps / el
+    sample = (f"{args.steps} timed KDK steps of a {s.n}-particle copy of the workload (same generator and seed, "
+              f"grid prefilter) after {args.warmup} untimed; the per-particle rate of that copy, not extrapolated")
+    if s.n == FULL_N[name]:
+        sample = f"{args.steps} timed KDK steps of the full {s.n}-particle workload after {args.warmup} untimed"
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": "fp64 CPU oracle (grid prefilter)"},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
-                         "sample": f"{args.steps} timed KDK steps of the full {s.n}-particle workload "
-                                   f"after {args.warmup} untimed"},
+        "config": {"workload": WORKLOADS[name], "precision": "fp64 CPU oracle (grid prefilter)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -228,16 +273,15 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def peak_fp32_tflops(sm_count):
-    """FP32 ALU roof: SMs x 128 FP32 lanes x 2 flop (FMA) x max SM clock
-    (measured max clock if recorded, else the part's 2070 MHz)."""
-    mhz = 2070.0
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            mhz = float(json.load(fh).get("sm_max_mhz", mhz))
-    except Exception:
-        pass
-    return sm_count * 128 * 2 * mhz * 1e6 / 1e12, mhz
+def measure_peaks(S, stream, local):
+    """FP32 and FP64 fused multiply-add ceilings of this GPU (sph_alu_peak),
+    with the SM clock sampled while the FP32 chains run."""
+    S.sph_alu_peak(S.PREC_MIXED, 20.0, stream.cuda_stream)  # warm the clocks
+    with Clocks(local) as clk:
+        f32, ms32 = S.sph_alu_peak(S.PREC_MIXED, 400.0, stream.cuda_stream)
+    f64, ms64 = S.sph_alu_peak(S.PREC_FP64, 200.0, stream.cuda_stream)
+    return {"fp32_tflops": f32, "fp32_launch_ms": ms32, "fp64_tflops": f64, "fp64_launch_ms": ms64,
+            "clocks": clk.summary()}
 
 
 def time_steps(S, prob, stream, torch, K, flush, stage=False):
@@ -331,8 +375,8 @@ def run_ours(args):
     _, stages, dp, fp = time_steps(S, prob, stream, torch, min(args.steps, 20), flush, stage=True)
     st = np.mean(np.array(stages), axis=0)
     dens_ms, force_ms = st[S.STAGES.index("density")], st[S.STAGES.index("forces")]
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak, mhz = peak_fp32_tflops(sm_count)
+    peaks = measure_peaks(S, stream, local)
+    peak = peaks["fp32_tflops"]
     per_kernel = {
         "k_forces": {"ms": float(force_ms), "flop": float(np.mean(fp) * FLOPS_FORCE_PAIR)},
         "k_density": {"ms": float(dens_ms), "flop": float(np.mean(dp) * FLOPS_DENSITY_PAIR)},
@@ -346,7 +390,9 @@ def run_ours(args):
     traffic = tr["dram_bytes_per_launch"] if tr else None
     roof = {"bound": "alu", "kernel": kern, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic,
-            "peak_basis": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz",
+            "peak_basis": (f"measured in this run: FP32 fused multiply-add chains on every SM (sph_alu_peak), "
+                           f"SM clock {peaks['clocks']['sm_mhz']} MHz median while they ran"),
+            "peaks": peaks, "timing": "CUDA events the library records on its stream around each stage",
             "stage_ms": {k: float(v) for k, v in zip(S.STAGES, st)},
             "density_pairs_per_step": float(np.mean(dp)), "force_pairs_per_step": float(np.mean(fp)),
             "pair_kernels": {k: dict(v, frac=v["achieved"] / peak) for k, v in per_kernel.items()}}
@@ -564,6 +610,22 @@ def run_ours(args):
 
     diag = prob.diagnostics()
     prob.close()
+    # the Sod shock tube (36864 particles) as a side measurement
+    sod = None
+    if not args.no_sod and args.workload != "sod":
+        asd, psd = workload("sod")
+        prms = S.make_params(S.PREC_MIXED, **psd, flags=S.FLAG_ASYNC)
+        with torch.cuda.stream(stream):
+            psod = S.Problem(asd, prms, device=dev, stream=stream)
+            S.check(S.sph_density_h(psod.ctx), "sph_density_h")
+            S.check(S.sph_forces(psod.ctx), "sph_forces")
+        S.sph_step_kernel_count(psod.ctx)
+        S.check(S.sph_run(psod.ctx, 3), "sph_run")
+        mss, _, _, _ = time_steps(S, psod, stream, torch, 50, flush)
+        nsd = len(asd["x"])
+        sod = {"workload": WORKLOADS["sod"], "value": nsd * len(mss) / (np.sum(mss) * 1e-3), "unit": UNIT,
+               "ms_per_step": float(np.mean(mss)), "steps": len(mss)}
+        psod.close()
     serve_res = None
     if args.serve > 0 and rank == 0:
         free, _ = torch.cuda.mem_get_info(dev)
@@ -572,20 +634,21 @@ def run_ours(args):
         if world > 1:
             dist.destroy_process_group()
         return
-    cpu = None
-    if not args.no_cpu_baseline and world == 1 and args.workload == "sod":
-        v, cores, steps, nn, _ = oracle_sample()
-        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": f"{steps} KDK steps of the full {nn}-particle workload (grid prefilter)"}
+    cpu, cpu_one = None, None
+    if not args.no_cpu_baseline and world == 1:
+        cpu, cpu_one = cpu_baselines(args.workload, float(diag.ngb_mean), n)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "particles": n, "precision": "mixed (FP32 pairs, FP64 state)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                   "l2": "flushed (256 MiB write) between timed steps", "graph": "one CUDA graph per step",
+                   "l2": "flushed (256 MiB write) between timed steps" + (
+                       "; the step's inputs are also larger than L2" if n * 8 * 9 > (129 << 20) else ""),
+                   "graph": "one CUDA graph per step",
                    "lanes_per_particle": int(prob.params.lanes_per_particle) or "auto"},
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": kernels_per_step * args.steps,
+        "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_1thread": cpu_one, "e2e": e2e,
+        "gpu_launches": kernels_per_step * args.steps, "sod": sod,
         "clocks": clocks, "fp64_gpu": fp64, "tree_reuse": reuse, "m6_kernel": m6, "gravity": grav, "block_steps": blk, "serving": serve_res,
         "step_diag": {"nr_iterations": diag.nr_iterations, "nr_max": diag.nr_max, "fallback": diag.fallback,
                       "leaves": diag.leaves, "ngb_mean": diag.ngb_mean, "candidates": diag.candidates,

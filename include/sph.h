@@ -329,7 +329,7 @@ typedef struct {
     int64_t n;             /* particles                                    */
     const double *x, *y, *z, *vx, *vy, *vz, *u, *m, *h; /* host arrays, copied at submit */
     sph_params params;     /* per-request physics (precision/flags ignored) */
-    int nsteps;            /* CFL steps to take                            */
+    int nsteps;            /* CFL steps to take (>= 1; else SPH_EINVAL)     */
     double arrival;        /* arrival time on the server's clock (seconds) */
 } sph_request;
 
@@ -370,7 +370,12 @@ int sph_server_destroy(sph_server *s);
  *   - Allocates nothing: no cudaMalloc/cudaFree, no allocating library call.
  *     Its scratch memory is a fixed 16 MiB array compiled into the library,
  *     which every GPU that loads the library holds until the process exits.
- *   - n is at most 32768; larger n returns SPH_EINVAL with a message.
+ *   - n is at most 32768; larger n returns SPH_EINVAL with a message.  With
+ *     self-gravity the scratch also holds the long-range sum's buffers, so
+ *     the largest n is smaller: 30240 (mixed precision, direct sum), 27840
+ *     (FP64, direct sum), 24960 (FP64, tree walk); the mixed tree walk takes
+ *     32768.  A call beyond its limit returns SPH_ENOSPACE, before touching
+ *     the device, with a message naming the largest n that fits.
  *   - The caller passes the particle arrays (inputs and outputs as in
  *     sph_state) and the stream; p as for sph_setup (SPH_FLAG_ASYNC skips the
  *     final synchronisation, and then no status is reported).
@@ -393,6 +398,18 @@ int sph_density_forces_noalloc(const sph_params *p, int64_t n, const sph_state *
  * FP64 path clamps lanes to 2 or 4.  No counterpart in the paper: the
  * package's autotuner measures the table on the GPU and installs it. */
 int sph_set_launch_table(const int64_t *n_max, const int32_t *lanes, int rows);
+
+/* ---- hardware ceiling of the pair kernels ------------------------------ */
+/* Measured fused multiply-add throughput of the current device: independent
+ * FP32 (precision SPH_PREC_MIXED) or FP64 (SPH_PREC_FP64) chains on every SM,
+ * 2 flop per fused multiply-add, one launch of about target_ms milliseconds
+ * (0 < target_ms <= 10000) after short calibration launches, timed with CUDA
+ * events on stream.  Writes TFLOP/s to *tflops and the timed launch's
+ * duration to *ms (may be NULL).  Synchronises the stream.  Allocates no
+ * device memory.  The pair arithmetic of the density and force passes is
+ * bound by this pipe (no dense contraction), so it is the ceiling their
+ * roofline fraction is taken against; the paper has no counterpart. */
+int sph_alu_peak(int precision, double target_ms, double *tflops, double *ms, void *stream);
 
 /* Message describing the calling thread's last error ("" if none). */
 const char *sph_last_error(void);

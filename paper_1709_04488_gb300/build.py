@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libsph.so")
 
 SOURCES = ["sph_sort.cu", "sph_build.cu", "sph_pairs.cu", "sph_pairs_m6.cu", "sph_pairs_m4_wrap.cu",
            "sph_pairs_m6_wrap.cu", "sph_gravity.cu", "sph_block.cu", "sph_integrate.cu", "sph_export.cu", "sph_api.cu", "sph_server.cu",
-           "sph_noalloc.cu"]
+           "sph_noalloc.cu", "sph_peak.cu"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",

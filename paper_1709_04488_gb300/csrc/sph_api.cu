@@ -998,6 +998,10 @@ int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, 
         rc = enqueue_step(b, prec, -1.0, st, Marks());
         if (rc) return rc;
     }
+    // the batch sorted every context's particles in its own layout: a later
+    // sph_step of one context alone must rebuild its leaves first
+    if (nsteps > 0)
+        for (int k = 0; k < nctx; ++k) ctxs[k]->since_build = ctxs[k]->prm.tree_rebuild_every;
     CU(cudaStreamSynchronize(st));
     int worst = SPH_OK;
     for (int k = 0; k < nctx; ++k) {

@@ -18,9 +18,12 @@ namespace {
 
 using namespace sph;
 
-// Largest problem the fixed scratch holds, and its size: the workspace layout
-// of the FP64 path (the larger of the two precisions) for this many
-// particles, plus the persistent diagnostics record, rounded up.
+// Largest problem the fixed scratch holds, and its size.  16 MiB holds the
+// workspace layout of either precision for 32768 particles without
+// self-gravity (14.3 MiB for the FP64 layout), plus the diagnostics record.
+// Self-gravity adds the long-range sum's buffers (partial sums of split
+// partner ranges, the tree walk's copies), so with gravity the largest n is
+// smaller; noalloc_max_n() finds it for the caller's parameters.
 constexpr long long kNoAllocMaxN = 32768;
 constexpr size_t kNoAllocBytes = (size_t)16 << 20;
 constexpr int kMaxDevices = 64;
@@ -49,6 +52,32 @@ int scratch_for_current_device(void **out)
     return SPH_OK;
 }
 
+// Bytes of the fixed scratch one call of n particles with parameters p uses.
+size_t noalloc_bytes(const sph_params *p, long long n)
+{
+    Carver c{nullptr};
+    c.take<ProbDiag>(1);
+    BatchView b;
+    memset(&b, 0, sizeof b);
+    carve_tables(c, b, 1);
+    carve_arrays(c, b, n, 1, p->precision, p->gravity ? gravity_chunks(n, p->grav_theta) : 0,
+                 p->gravity && p->grav_theta > 0);
+    return c.off;
+}
+
+// Largest n (<= kNoAllocMaxN) whose layout fits the fixed scratch for p.
+long long noalloc_max_n(const sph_params *p)
+{
+    if (noalloc_bytes(p, kNoAllocMaxN) <= kNoAllocBytes) return kNoAllocMaxN;
+    long long lo = 0, hi = kNoAllocMaxN;  // fits(lo), !fits(hi)
+    while (hi - lo > 1) {
+        const long long mid = (lo + hi) / 2;
+        if (noalloc_bytes(p, mid) <= kNoAllocBytes) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // Writes the problem table and clears everything a call must find at zero.
 __global__ void k_noalloc_init(BatchView b, ProbStatic ps)
 {
@@ -71,6 +100,11 @@ extern "C" int sph_density_forces_noalloc(const sph_params *p, int64_t n, const 
     if (n < 0 || n > kNoAllocMaxN)
         return fail(SPH_EINVAL, "n = %lld: the allocation-free entry point takes at most %lld particles",
                     (long long)n, kNoAllocMaxN);
+    if (noalloc_bytes(p, n) > kNoAllocBytes)
+        return fail(SPH_ENOSPACE,
+                    "n = %lld does not fit the allocation-free entry point's fixed scratch with these "
+                    "parameters (self-gravity needs extra buffers): at most %lld particles",
+                    (long long)n, noalloc_max_n(p));
     if (!state) return fail(SPH_EINVAL, "state is NULL");
     if (n > 0) {
         const double *req[] = {state->x, state->y, state->z, state->vx, state->vy, state->vz, state->u,
@@ -92,7 +126,8 @@ extern "C" int sph_density_forces_noalloc(const sph_params *p, int64_t n, const 
     carve_tables(c, b, 1);
     carve_arrays(c, b, n, 1, p->precision, p->gravity ? gravity_chunks(n, p->grav_theta) : 0,
                  p->gravity && p->grav_theta > 0);
-    if (c.off > kNoAllocBytes) return fail(SPH_ENOSPACE, "fixed scratch too small for %lld particles", (long long)n);
+    if (c.off > kNoAllocBytes)  // (checked above; kept as a guard on the layout)
+        return fail(SPH_ENOSPACE, "fixed scratch too small for %lld particles", (long long)n);
     const int lpp = lpp_of(p, n);
     b.ntot = n;
     b.key_bits = key_bits_for(1);

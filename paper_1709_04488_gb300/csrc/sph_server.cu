@@ -208,7 +208,7 @@ int sph_server_create(sph_server **out, const sph_server_cfg *cfg)
 int sph_server_submit(sph_server *s, const sph_request *req, uint64_t *ticket)
 {
     if (!s || !req || !ticket) return SPH_EINVAL;
-    if (req->n < 0 || req->nsteps < 0) return SPH_EINVAL;
+    if (req->n < 0 || req->nsteps < 1) return SPH_EINVAL;  // (a request asks for at least one step)
     const double *in[9] = {req->x, req->y, req->z, req->vx, req->vy, req->vz, req->u, req->m, req->h};
     if (req->n > 0)
         for (const double *p : in)

@@ -114,15 +114,31 @@ def sedov(n_side: int = 100, seed: int = 3, E: float = 1.0, u0: float = 1e-5,
 
 def _cloud_radii(n, a, R, rng):
     # invert M(<r)/M = (r - a atan(r/a)) / (R - a atan(R/a)) by bisection
+    # (in cache-sized chunks; every element takes the same 60 halvings)
     target = rng.uniform(0.0, 1.0, n) * (R - a * math.atan(R / a))
-    lo = np.zeros(n)
-    hi = np.full(n, R)
-    for _ in range(60):
-        mid = 0.5 * (lo + hi)
-        f = mid - a * np.arctan(mid / a)
-        lo = np.where(f < target, mid, lo)
-        hi = np.where(f < target, hi, mid)
-    return 0.5 * (lo + hi)
+    out = np.empty(n)
+    chunk = 1 << 16
+    mid = np.empty(chunk)
+    f = np.empty(chunk)
+    below = np.empty(chunk, dtype=bool)
+    for c0 in range(0, n, chunk):
+        t = target[c0:c0 + chunk]
+        m = len(t)
+        lo = np.zeros(m)
+        hi = np.full(m, R)
+        md, fm, bl = mid[:m], f[:m], below[:m]
+        for _ in range(60):
+            np.add(lo, hi, out=md)
+            md *= 0.5
+            np.divide(md, a, out=fm)
+            np.arctan(fm, out=fm)
+            fm *= a
+            np.subtract(md, fm, out=fm)
+            np.less(fm, t, out=bl)
+            np.copyto(lo, md, where=bl)
+            np.copyto(hi, md, where=~bl)
+        out[c0:c0 + m] = 0.5 * (lo + hi)
+    return out
 
 
 def _random_field(ngrid, kmin, kmax, rng):
@@ -139,22 +155,28 @@ def _random_field(ngrid, kmin, kmax, rng):
     return comps
 
 
-def _trilinear(field, pos, lo, L):
-    ng = field.shape[0]
-    s = (pos - lo) / L * ng - 0.5
-    i0 = np.floor(s).astype(np.int64)
-    f = s - i0
-    out = np.zeros(len(pos))
-    for dz in (0, 1):
-        for dy in (0, 1):
-            for dx in (0, 1):
-                w = ((f[:, 0] if dx else 1 - f[:, 0]) * (f[:, 1] if dy else 1 - f[:, 1]) *
-                     (f[:, 2] if dz else 1 - f[:, 2]))
-                ix = (i0[:, 0] + dx) % ng
-                iy = (i0[:, 1] + dy) % ng
-                iz = (i0[:, 2] + dz) % ng
-                out += w * field[iz, iy, ix]
-    return out
+def _trilinear(fields, pos, lo, L):
+    # the same weights and cells serve every field; one gather per corner
+    # fetches the values of all fields at that node
+    ng = fields[0].shape[0]
+    F = np.stack([fd.ravel() for fd in fields], axis=1)
+    out = np.zeros((len(pos), len(fields)))
+    chunk = 1 << 18
+    for c0 in range(0, len(pos), chunk):
+        s = (pos[c0:c0 + chunk] - lo) / L * ng - 0.5
+        i0 = np.floor(s).astype(np.int64)
+        f = s - i0
+        o = out[c0:c0 + chunk]
+        for dz in (0, 1):
+            for dy in (0, 1):
+                for dx in (0, 1):
+                    w = ((f[:, 0] if dx else 1 - f[:, 0]) * (f[:, 1] if dy else 1 - f[:, 1]) *
+                         (f[:, 2] if dz else 1 - f[:, 2]))
+                    ix = (i0[:, 0] + dx) % ng
+                    iy = (i0[:, 1] + dy) % ng
+                    iz = (i0[:, 2] + dz) % ng
+                    o += w[:, None] * F[(iz * ng + iy) * ng + ix]
+    return [out[:, k].copy() for k in range(len(fields))]
 
 
 def cloud(n: int = 8_000_000, seed: int = 4, a: float = 0.1, R: float = 1.0, mach: float = 5.0,
@@ -166,7 +188,7 @@ def cloud(n: int = 8_000_000, seed: int = 4, a: float = 0.1, R: float = 1.0, mac
     st = np.sqrt(1.0 - mu ** 2)
     pos = np.stack([r * st * np.cos(phi), r * st * np.sin(phi), r * mu], axis=1)
     vf = _random_field(ngrid, kmin, kmax, rng)
-    v = np.stack([_trilinear(c, pos, -1.0, 2.0) for c in vf], axis=1)
+    v = np.stack(_trilinear(vf, pos, -1.0, 2.0), axis=1)
     v -= v.mean(axis=0)
     v *= mach * cs / math.sqrt(np.mean(np.sum(v ** 2, axis=1)))
     m = np.full(n, 1.0 / n)

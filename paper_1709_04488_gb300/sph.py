@@ -182,6 +182,7 @@ def lib():
             "sph_last_error": (C.c_char_p, []),
             "sph_version": (C.c_char_p, []),
             "sph_set_launch_table": (i, [C.POINTER(i64), C.POINTER(C.c_int32), i]),
+            "sph_alu_peak": (i, [i, d, C.POINTER(d), C.POINTER(d), vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -331,6 +332,15 @@ def sph_batch_step(ctxs, nsteps: int, ws_ptr: int, ws_bytes: int) -> int:
 
 
 # ---- helper: problem state held in PyTorch device memory ----------------------
+def sph_alu_peak(precision: int, target_ms: float, stream: int = 0):
+    """Measured fused multiply-add throughput (TFLOP/s, launch ms) of the
+    current device: FP32 for PREC_MIXED, FP64 for PREC_FP64."""
+    tf, ms = C.c_double(0.0), C.c_double(0.0)
+    check(lib().sph_alu_peak(int(precision), float(target_ms), C.byref(tf), C.byref(ms), C.c_void_p(stream)),
+          "sph_alu_peak")
+    return tf.value, ms.value
+
+
 def make_params(precision: int = PREC_MIXED, **kw) -> Params:
     """sph_params from keyword arguments (names as in sph_params; 'eos' may be
     'adiabatic'/'isothermal'; box tuples accepted)."""

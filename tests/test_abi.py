@@ -158,3 +158,29 @@ def test_launch_table_validation(S):
         import json
         rows = json.load(open(S.TUNING_PATH))["lpp_table"]
         assert call(rows) == S.OK
+
+
+def test_noalloc_limits_per_option_without_a_gpu(S):
+    """The allocation-free entry point rejects, before touching the device, a
+    problem whose layout does not fit its fixed scratch: n > 32768 with
+    SPH_EINVAL, and self-gravity problems above their smaller limits with
+    SPH_ENOSPACE naming the largest n that fits (checked one particle on
+    either side of the limit)."""
+    import ctypes as C
+    st = S.State()  # NULL arrays: a call that passes the size checks stops at SPH_EINVAL
+
+    def call(n, prec, **kw):
+        p = S.make_params(prec, **kw)
+        return S.lib().sph_density_forces_noalloc(C.byref(p), n, C.byref(st), None)
+
+    assert call(32769, S.PREC_MIXED) == S.EINVAL
+    assert call(32768, S.PREC_MIXED) == S.EINVAL and "NULL" in S.last_error()
+    assert call(32768, S.PREC_FP64) == S.EINVAL and "NULL" in S.last_error()
+    grav = dict(periodic=False, gravity=1, G=1.0)
+    for prec, kw, limit in [(S.PREC_MIXED, grav, 30240), (S.PREC_FP64, grav, 27840),
+                            (S.PREC_FP64, dict(grav, grav_theta=0.5), 24960)]:
+        assert call(32768, prec, **kw) == S.ENOSPACE
+        assert f"at most {limit} particles" in S.last_error()
+        assert call(limit + 1, prec, **kw) == S.ENOSPACE
+        assert call(limit, prec, **kw) == S.EINVAL and "NULL" in S.last_error()
+    assert call(32768, S.PREC_MIXED, **dict(grav, grav_theta=0.5)) == S.EINVAL
