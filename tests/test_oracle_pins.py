@@ -90,6 +90,34 @@ def test_lattice_density_neighbours_and_offset(oracle_mod):
     assert np.all(np.abs(s.h * 16 - 1.2) < 0.01)
 
 
+def test_lattice_values_from_integer_shells(oracle_mod):
+    """The perfect-lattice solution computed independently of the oracle's
+    neighbour search, periodic images and Newton-Raphson iteration: on the
+    integer lattice (spacing 1, m = 1) rho(h) = sum_n W(|n|, h) over n in Z^3,
+    and Eq. HRHO is solved for h by bracketing root finding.  The oracle's h
+    and rho on a 16^3 periodic lattice equal it to FP64 rounding, i.e.
+    h / spacing = 1.199670..., rho / rho0 = 1.000825... (a 0.08 % offset)."""
+    O = oracle_mod
+    from scipy.optimize import brentq
+    r = np.arange(-3, 4)
+    X, Y, Z = np.meshgrid(r, r, r, indexing="ij")
+    dist = np.sqrt(X ** 2 + Y ** 2 + Z ** 2).ravel()
+    dist = dist[dist < 2.5]  # every point that can lie inside 2h for h < 1.25
+
+    def rho_of(h):
+        return float(np.sum([O.kernel_W(d, h) for d in dist]))
+
+    h_ref = brentq(lambda h: rho_of(h) - (1.2 / h) ** 3, 1.0, 1.25, xtol=1e-15, rtol=1e-15)
+    rho_ref = rho_of(h_ref)
+    assert abs(h_ref - 1.199670) < 5e-7 and abs(rho_ref - 1.000825) < 5e-7
+    a, p = ics.lattice(16, jitter=0.0)
+    P = O.Params(**p)
+    s = _state(O, a)
+    assert O.density(P, s) == O.OK
+    assert np.max(np.abs(s.h * 16 / h_ref - 1.0)) < 1e-13
+    assert np.max(np.abs(s.rho / rho_ref - 1.0)) < 1e-13
+
+
 def test_density_solution_satisfies_hrho(oracle_mod):
     """After the iteration, h and rho satisfy Eq. HRHO to the tolerance and
     rho is the density sum at the returned h (jittered lattice, cold start)."""
