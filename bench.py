@@ -82,6 +82,11 @@ def parse():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS),
                     help="cloud (8e6, the default: the largest single-GPU configuration), sedov (1e6) or sod (36864)")
     ap.add_argument("--no-sod", action="store_true", help="skip the Sod-36864 side measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-path measurement")
+    ap.add_argument("--batch-problems", type=int, default=64, help="problems in the batched-path measurement")
+    ap.add_argument("--particles", type=int, default=0,
+                    help="scale the cloud or Sedov workload down to about this many particles (profiling runs; "
+                         "0: the configuration's size)")
     ap.add_argument("--serve", type=int, default=2000,
                     help="requests in the serving measurement (0 skips it)")
     ap.add_argument("--serve-load", type=float, nargs="*", default=[0.5, 0.7, 0.9],
@@ -89,8 +94,14 @@ def parse():
     return ap.parse_args()
 
 
-def workload(name=DEFAULT_WORKLOAD):
+def workload(name=DEFAULT_WORKLOAD, particles=0):
+    """The configuration's generator; particles > 0 scales the cloud (and the
+    Sedov lattice, to the nearest cube) down for profiling runs."""
     from paper_1709_04488_gb300 import ics
+    if particles > 0 and name == "cloud":
+        return ics.cloud(particles)
+    if particles > 0 and name == "sedov":
+        return ics.sedov(int(round(particles ** (1.0 / 3.0))))
     return {"sod": ics.sod, "sedov": ics.sedov, "cloud": ics.cloud}[name]()
 
 
@@ -333,6 +344,72 @@ def serving(nreq, loads, pool_bytes):
     return out
 
 
+def batched_measurement(S, torch, dev, stream, flush, peak, nprob, steps=10):
+    from paper_1709_04488_gb300 import serve
+    reqs = serve.make_requests(nprob, seed=7, n_min=1e3, n_max=2e5, nsteps=steps)
+    probs = []
+    with torch.cuda.stream(stream):
+        for r in reqs:
+            pr = S.Problem(r["arrays"], S.make_params(S.PREC_MIXED, **r["params"], flags=S.FLAG_ASYNC),
+                           device=dev, stream=stream)
+            S.check(S.sph_density_h(pr.ctx), "sph_density_h")
+            S.check(S.sph_forces(pr.ctx), "sph_forces")
+            probs.append(pr)
+    ntot = sum(pr.n for pr in probs)
+    batch = S.Batch(probs, flags=S.FLAG_TIMING)
+    batch.run(3)  # the first step is captured
+    assert batch.sync() == [S.OK] * len(probs)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    stages = []
+    for k in range(steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev[k][0].record(stream)
+        batch.run(1)
+        ev[k][1].record(stream)
+        stream.synchronize()
+        stages.append(batch.stage_times())
+    st = batch.sync()
+    assert st == [S.OK] * len(probs), st
+    ms = [a.elapsed_time(b) for a, b in ev]
+    dp = sum(pr.diagnostics().density_pairs for pr in probs)
+    fp = sum(pr.diagnostics().force_pairs for pr in probs)
+    sm = np.mean(np.array(stages), axis=0)
+    dens_ms, force_ms = float(sm[S.STAGES.index("density")]), float(sm[S.STAGES.index("forces")])
+    pk = {"k_forces": {"ms": force_ms, "flop": float(fp * FLOPS_FORCE_PAIR)},
+          "k_density": {"ms": dens_ms, "flop": float(dp * FLOPS_DENSITY_PAIR)}}
+    for rec in pk.values():
+        rec["achieved"] = rec["flop"] / (rec["ms"] * 1e-3) / 1e12 if rec["ms"] > 0 else 0.0
+        rec["frac"] = rec["achieved"] / peak
+    kern = "k_forces" if force_ms >= dens_ms else "k_density"
+    value = ntot * steps / (np.sum(ms) * 1e-3)
+    out = {"workload": f"{nprob} problems (lattice, Sod, Sedov; 1e3..2e5 particles, log-uniform; seed 7), "
+                       f"{ntot} particles in all",
+           "problems": nprob, "particles": ntot, "steps": steps, "value": value, "unit": UNIT,
+           "ms_per_step": float(np.mean(ms)), "kernels_per_step": batch.kernel_count(),
+           "graph": "one captured graph per batched step (tables resident)",
+           "roofline": {"bound": "alu", "kernel": kern, "achieved": pk[kern]["achieved"], "peak": peak,
+                        "unit": "TFLOP/s", "frac": pk[kern]["frac"], "stage_ms": dict(zip(S.STAGES, sm.tolist())),
+                        "pair_kernels": pk}}
+    batch.close()
+    # the same problems stepped one after another (each its own graph)
+    for pr in probs:
+        S.sph_step_kernel_count(pr.ctx)  # builds each problem's step graph
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for pr in probs:
+        S.check(S.sph_run(pr.ctx, steps), "sph_run")
+    e1.record(stream)
+    stream.synchronize()
+    seq = ntot * steps / (e0.elapsed_time(e1) * 1e-3)
+    out["one_by_one"] = {"value": seq, "unit": UNIT}
+    out["speedup_of_batching"] = value / seq
+    for pr in probs:
+        pr.close()
+    return out
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -346,7 +423,7 @@ def run_ours(args):
         B.build()
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
-    a, p = workload(args.workload)
+    a, p = workload(args.workload, args.particles)
     n = len(a["x"])
     prm = S.make_params(S.PREC_MIXED, **p, flags=S.FLAG_ASYNC | S.FLAG_TIMING, lanes_per_particle=args.lpp)
     with torch.cuda.stream(stream):
@@ -455,6 +532,14 @@ def run_ours(args):
         reuse = {"rebuild_every": k_every, "value": vr, "unit": UNIT, "ms_per_step": float(np.mean(msr)),
                  "speedup_of_rebuild_every_step": vr / (value / world)}
         pr.close()
+
+    # the batched path: many independent problems of uneven sizes (the
+    # serving configuration's mix: lattice, Sod and Sedov problems of 1e3 to
+    # 2e5 particles) stepped by one resident batch whose step is a captured
+    # graph, against the same problems stepped one after another
+    batched = None
+    if not args.no_batch:
+        batched = batched_measurement(S, torch, dev, stream, flush, peak, args.batch_problems)
 
     # the same workload with the M6 quintic kernel (Sec. 2; support 3h,
     # eta = 1.0, ~113 neighbours), started from h = 1.0 x spacing
@@ -641,7 +726,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload], "particles": n, "precision": "mixed (FP32 pairs, FP64 state)",
+        "config": {"workload": WORKLOADS[args.workload] + (f" (scaled to {n} particles)" if args.particles else ""),
+                   "particles": n, "precision": "mixed (FP32 pairs, FP64 state)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "flushed (256 MiB write) between timed steps" + (
                        "; the step's inputs are also larger than L2" if n * 8 * 9 > (129 << 20) else ""),
@@ -649,7 +735,7 @@ def run_ours(args):
                    "lanes_per_particle": int(prob.params.lanes_per_particle) or "auto"},
         "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_1thread": cpu_one, "e2e": e2e,
         "gpu_launches": kernels_per_step * args.steps, "sod": sod,
-        "clocks": clocks, "fp64_gpu": fp64, "tree_reuse": reuse, "m6_kernel": m6, "gravity": grav, "block_steps": blk, "serving": serve_res,
+        "clocks": clocks, "batched": batched, "fp64_gpu": fp64, "tree_reuse": reuse, "m6_kernel": m6, "gravity": grav, "block_steps": blk, "serving": serve_res,
         "step_diag": {"nr_iterations": diag.nr_iterations, "nr_max": diag.nr_max, "fallback": diag.fallback,
                       "leaves": diag.leaves, "ngb_mean": diag.ngb_mean, "candidates": diag.candidates,
                       "wrap_leaves": diag.wrap_leaves},

@@ -312,8 +312,38 @@ size_t sph_batch_workspace_bytes(sph_ctx *const *ctxs, int nctx);
  * over all problems (work lists of (problem, leaf) items).  Every problem's
  * result equals the result of stepping it alone.  All contexts must use the
  * same precision and stream; workspace is caller-owned device memory of at
- * least sph_batch_workspace_bytes(). */
+ * least sph_batch_workspace_bytes().  Synchronises; returns the first error
+ * among the contexts (each context's own status: sph_sync or
+ * sph_diagnostics).  A later sph_step of one context alone rebuilds its
+ * leaves first. */
 int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, size_t ws_bytes);
+
+/* A resident batch of contexts (the batched path of the many-problem
+ * workloads): the problem tables are uploaded once at creation, and one
+ * batched step (every kernel once over all problems: persistent work-queue
+ * launches over (problem, leaf) items for the density and force passes) is
+ * captured as a CUDA graph on the first sph_batch_run and replayed after
+ * that, with no host round trip between steps.  The contexts must have a
+ * force evaluation, share precision and a non-default stream, and stay alive
+ * and unchanged in size while the batch exists; workspace as for
+ * sph_batch_step, reserved for the batch until sph_batch_destroy.
+ * flags: SPH_FLAG_TIMING records CUDA events around the stages of each step
+ * (sph_batch_stage_times).  Every problem's result equals stepping it alone.
+ * No counterpart in the paper (its batches are OpenMP loops over one
+ * problem's cells); the work unit, a leaf cell, is the paper's. */
+typedef struct sph_batch sph_batch;
+int sph_batch_create(sph_batch **out, sph_ctx *const *ctxs, int nctx, void *workspace, size_t ws_bytes,
+                     unsigned flags);
+/* Enqueue nsteps batched CFL steps (graph replays; asynchronous). */
+int sph_batch_run(sph_batch *b, int nsteps);
+/* Wait for the batch's work; writes each context's status to status[k]
+ * (nctx entries, may be NULL) and returns the first error among them. */
+int sph_batch_sync(sph_batch *b, int *status);
+/* Stage durations (ms, SPH_NSTAGES doubles) of the last batched step. */
+int sph_batch_stage_times(sph_batch *b, double *ms);
+/* Kernel launches in one captured batched step (after the first run). */
+int sph_batch_kernel_count(sph_batch *b, int *kernels);
+int sph_batch_destroy(sph_batch *b);
 
 /* ---- serving: continuous batching of independent runs ------------------ */
 typedef struct {

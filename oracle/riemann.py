@@ -145,3 +145,29 @@ def isothermal_star(rhoL, uL, rhoR, uR, cs):
     fL, _ = fk(r, rhoL)
     fR, _ = fk(r, rhoR)
     return r, 0.5 * (uL + uR) + 0.5 * (fR - fL)
+
+
+# the classic Sod states of the shock-tube configuration (rho, u, P | rho, u, P, gamma)
+SOD = (1.0, 0.0, 1.0, 0.125, 0.0, 0.1, 1.4)
+
+
+def sod_window(t: float, hmax: float):
+    """Stretch of the periodic Sod tube where the solution at time t is the
+    single Riemann problem at x0 = 0.5: right of the mirror problem's
+    rarefaction head (the box's second discontinuity at x = 0 sends it to
+    x = c_L t) and left of the contact, each edge moved inwards by 2 hmax."""
+    ws = wave_speeds(*SOD)
+    lo = max(0.25, -ws["left"][0] * t) + 2.0 * hmax
+    hi = min(0.67, 0.5 + ws["contact"] * t) - 2.0 * hmax
+    return lo, hi
+
+
+def sod_l1(x, rho, vx, P, t: float, hmax: float):
+    """L1 errors (1/N) sum_i |q_i - q(x_i, t)| of rho, v_x and P against the
+    exact solution over the particles inside sod_window(t, hmax) (the L1
+    form of the paper's shock-tube comparison, Sec. 6.2)."""
+    lo, hi = sod_window(t, hmax)
+    sel = (x >= lo) & (x <= hi)
+    r, u, p = sample((x[sel] - 0.5) / t, *SOD)
+    return (float(np.mean(np.abs(rho[sel] - r))), float(np.mean(np.abs(vx[sel] - u))),
+            float(np.mean(np.abs(P[sel] - p))), int(np.sum(sel)))

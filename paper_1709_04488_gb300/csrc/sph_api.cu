@@ -935,11 +935,12 @@ size_t sph_batch_workspace_bytes(sph_ctx *const *ctxs, int nctx)
     return c.off + 256;
 }
 
-int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, size_t ws_bytes)
+// The batch-global view of nctx contexts laid out in workspace: problem
+// tables (uploaded on st), scratch arrays, launch classes.
+static int batch_view(sph_ctx *const *ctxs, int nctx, void *workspace, size_t ws_bytes, BatchView &b)
 {
     int rc = batch_check(ctxs, nctx);
     if (rc) return rc;
-    if (nsteps < 0) return fail(SPH_EINVAL, "nsteps must be >= 0");
     for (int k = 0; k < nctx; ++k)
         if (!ctxs[k]->have_forces)
             return fail(SPH_EINVAL, "batch context %d has no force evaluation yet", k);
@@ -973,7 +974,6 @@ int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, 
     }
     bases[nctx] = ntot;
     Carver cv{(char *)workspace};
-    BatchView b;
     memset(&b, 0, sizeof b);
     carve_tables(cv, b, nctx);
     carve_arrays(cv, b, ntot, nctx, prec, gch, gtree);
@@ -994,23 +994,192 @@ int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, 
     CU(cudaMemsetAsync(b.dyn, 0, sizeof(ProbDyn) * nctx, st));
     CU(cudaMemsetAsync(b.counters, 0, kNumCounters * sizeof(int), st));
     CU(cudaMemsetAsync(b.zero_lo, 0, b.zero_bytes, st));
-    for (int s = 0; s < nsteps; ++s) {
-        rc = enqueue_step(b, prec, -1.0, st, Marks());
-        if (rc) return rc;
-    }
-    // the batch sorted every context's particles in its own layout: a later
-    // sph_step of one context alone must rebuild its leaves first
-    if (nsteps > 0)
-        for (int k = 0; k < nctx; ++k) ctxs[k]->since_build = ctxs[k]->prm.tree_rebuild_every;
+    // the host copies of the tables are read before this returns
     CU(cudaStreamSynchronize(st));
+    return SPH_OK;
+}
+
+// the contexts' own step bookkeeping after batched steps: their particles
+// were sorted in the batch's layout, so a later step of one context alone
+// must rebuild its leaves first
+static void after_batch_steps(sph_ctx *const *ctxs, int nctx)
+{
+    for (int k = 0; k < nctx; ++k) ctxs[k]->since_build = ctxs[k]->prm.tree_rebuild_every;
+}
+
+// each context's device status, and the first error among them
+static int batch_statuses(sph_ctx *const *ctxs, int nctx, int *status)
+{
     int worst = SPH_OK;
     for (int k = 0; k < nctx; ++k) {
         unsigned s = 0;
         CU(cudaMemcpy(&s, &ctxs[k]->diag->status, sizeof s, cudaMemcpyDeviceToHost));
-        int code = status_to_code(s);
+        const int code = status_to_code(s);
+        if (status) status[k] = code;
         if (code != SPH_OK && worst == SPH_OK) worst = code;
     }
     return worst;
+}
+
+int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, size_t ws_bytes)
+{
+    if (nsteps < 0) return fail(SPH_EINVAL, "nsteps must be >= 0");
+    BatchView b;
+    int rc = batch_view(ctxs, nctx, workspace, ws_bytes, b);
+    if (rc) return rc;
+    const int prec = ctxs[0]->prm.precision;
+    cudaStream_t st = ctxs[0]->stream;
+    for (int s = 0; s < nsteps; ++s) {
+        rc = enqueue_step(b, prec, -1.0, st, Marks());
+        if (rc) return rc;
+    }
+    if (nsteps > 0) after_batch_steps(ctxs, nctx);
+    CU(cudaStreamSynchronize(st));
+    return batch_statuses(ctxs, nctx, nullptr);
+}
+
+}  // extern "C"
+
+// ---- resident batch: tables uploaded once, the step captured as a graph ----
+struct sph_batch {
+    std::vector<sph_ctx *> ctxs;
+    BatchView b;
+    int prec = SPH_PREC_MIXED;
+    cudaStream_t st = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graph_kernels = 0;
+    bool timing = false;
+    cudaEvent_t ev[SPH_NSTAGES + 1] = {};
+    bool stage_ran[SPH_NSTAGES] = {};
+};
+
+static Marks marks_of(sph_batch *bt)
+{
+    Marks m;
+    if (bt->timing) {
+        m.ev = bt->ev;
+        m.ran = bt->stage_ran;
+    }
+    return m;
+}
+
+static int batch_build_graph(sph_batch *bt)
+{
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(bt->st, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_step(bt->b, bt->prec, -1.0, bt->st, marks_of(bt));
+    cudaError_t e = cudaStreamEndCapture(bt->st, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(SPH_ECUDA, "batch graph capture failed: %s", cudaGetErrorString(e));
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    if (nn) cudaGraphGetNodes(g, nodes.data(), &nn);
+    int kern = 0;
+    for (size_t k = 0; k < nn; ++k) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nodes[k], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kern;
+    }
+    e = cudaGraphInstantiate(&bt->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        bt->graph = nullptr;
+        return fail(SPH_ECUDA, "batch graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+    bt->graph_kernels = kern;
+    return SPH_OK;
+}
+
+extern "C" {
+
+int sph_batch_create(sph_batch **out, sph_ctx *const *ctxs, int nctx, void *workspace, size_t ws_bytes,
+                     unsigned flags)
+{
+    if (!out) return fail(SPH_EINVAL, "out is NULL");
+    *out = nullptr;
+    BatchView b;
+    int rc = batch_view(ctxs, nctx, workspace, ws_bytes, b);
+    if (rc) return rc;
+    if (ctxs[0]->stream == nullptr)
+        return fail(SPH_EINVAL, "a resident batch needs a non-default stream (its step is captured as a graph)");
+    sph_batch *bt = new sph_batch();
+    bt->ctxs.assign(ctxs, ctxs + nctx);
+    bt->b = b;
+    bt->prec = ctxs[0]->prm.precision;
+    bt->st = ctxs[0]->stream;
+    bt->timing = (flags & SPH_FLAG_TIMING) != 0;
+    if (bt->timing)
+        for (int k = 0; k <= SPH_NSTAGES; ++k)
+            if (cudaEventCreate(&bt->ev[k]) != cudaSuccess) {
+                for (int j = 0; j < k; ++j) cudaEventDestroy(bt->ev[j]);
+                delete bt;
+                return fail(SPH_ECUDA, "cudaEventCreate failed");
+            }
+    *out = bt;
+    return SPH_OK;
+}
+
+int sph_batch_run(sph_batch *bt, int nsteps)
+{
+    if (!bt) return fail(SPH_EINVAL, "batch is NULL");
+    if (nsteps < 0) return fail(SPH_EINVAL, "nsteps must be >= 0");
+    for (int s = 0; s < nsteps; ++s) {
+        if (!bt->graph) {
+            // one eager step first (lazily set kernel attributes), then capture
+            int rc = enqueue_step(bt->b, bt->prec, -1.0, bt->st, marks_of(bt));
+            if (rc) return rc;
+            rc = batch_build_graph(bt);
+            if (rc) return rc;
+        } else {
+            CU(cudaGraphLaunch(bt->graph, bt->st));
+        }
+    }
+    if (nsteps > 0) after_batch_steps(bt->ctxs.data(), (int)bt->ctxs.size());
+    return SPH_OK;
+}
+
+int sph_batch_sync(sph_batch *bt, int *status)
+{
+    if (!bt) return fail(SPH_EINVAL, "batch is NULL");
+    CU(cudaStreamSynchronize(bt->st));
+    return batch_statuses(bt->ctxs.data(), (int)bt->ctxs.size(), status);
+}
+
+int sph_batch_stage_times(sph_batch *bt, double *ms)
+{
+    if (!bt || !ms) return fail(SPH_EINVAL, "NULL argument");
+    if (!bt->timing) return fail(SPH_EINVAL, "batch was created without SPH_FLAG_TIMING");
+    CU(cudaStreamSynchronize(bt->st));
+    for (int k = 0; k < SPH_NSTAGES; ++k) {
+        ms[k] = 0.0;
+        if (!bt->stage_ran[k]) continue;
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, bt->ev[k], bt->ev[k + 1]) == cudaSuccess) ms[k] = t;
+        else cudaGetLastError();
+    }
+    return SPH_OK;
+}
+
+int sph_batch_kernel_count(sph_batch *bt, int *kernels)
+{
+    if (!bt || !kernels) return fail(SPH_EINVAL, "NULL argument");
+    if (!bt->graph) return fail(SPH_EINVAL, "no step captured yet: call sph_batch_run first");
+    *kernels = bt->graph_kernels;
+    return SPH_OK;
+}
+
+int sph_batch_destroy(sph_batch *bt)
+{
+    if (!bt) return SPH_OK;
+    if (bt->graph) cudaGraphExecDestroy(bt->graph);
+    if (bt->timing)
+        for (int k = 0; k <= SPH_NSTAGES; ++k)
+            if (bt->ev[k]) cudaEventDestroy(bt->ev[k]);
+    delete bt;
+    return SPH_OK;
 }
 
 }  // extern "C"

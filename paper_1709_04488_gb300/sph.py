@@ -183,6 +183,12 @@ def lib():
             "sph_version": (C.c_char_p, []),
             "sph_set_launch_table": (i, [C.POINTER(i64), C.POINTER(C.c_int32), i]),
             "sph_alu_peak": (i, [i, d, C.POINTER(d), C.POINTER(d), vp]),
+            "sph_batch_create": (i, [C.POINTER(vp), C.POINTER(vp), i, vp, C.c_size_t, C.c_uint]),
+            "sph_batch_run": (i, [vp, i]),
+            "sph_batch_sync": (i, [vp, C.POINTER(i)]),
+            "sph_batch_stage_times": (i, [vp, C.POINTER(d)]),
+            "sph_batch_kernel_count": (i, [vp, C.POINTER(i)]),
+            "sph_batch_destroy": (i, [vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -329,6 +335,56 @@ def sph_batch_workspace_bytes(ctxs) -> int:
 def sph_batch_step(ctxs, nsteps: int, ws_ptr: int, ws_bytes: int) -> int:
     arr = (C.c_void_p * len(ctxs))(*[c.value for c in ctxs])
     return lib().sph_batch_step(arr, len(ctxs), int(nsteps), C.c_void_p(ws_ptr), int(ws_bytes))
+
+
+class Batch:
+    """A resident batch of Problems (sph_batch_*): tables uploaded once, the
+    batched step captured as a CUDA graph on the first run.  The problems
+    must share precision and a non-default stream and have a force
+    evaluation."""
+
+    def __init__(self, problems, flags: int = 0):
+        import torch
+        self.problems = list(problems)
+        self.stream = self.problems[0].stream
+        self._arr = (C.c_void_p * len(self.problems))(*[p.ctx.value for p in self.problems])
+        self.ws_bytes = int(lib().sph_batch_workspace_bytes(self._arr, len(self.problems)))
+        if self.ws_bytes == 0:
+            raise SPHError(EINVAL, "sph_batch_workspace_bytes")
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.problems[0].device)
+        self.h = C.c_void_p()
+        check(lib().sph_batch_create(C.byref(self.h), self._arr, len(self.problems), C.c_void_p(self.ws.data_ptr()),
+                                     self.ws_bytes, int(flags)), "sph_batch_create")
+
+    def run(self, nsteps: int):
+        check(lib().sph_batch_run(self.h, int(nsteps)), "sph_batch_run")
+
+    def sync(self):
+        """Per-problem statuses (list) after waiting for the batch's work."""
+        st = (C.c_int * len(self.problems))()
+        lib().sph_batch_sync(self.h, st)
+        return list(st)
+
+    def stage_times(self):
+        ms = (C.c_double * NSTAGES)()
+        check(lib().sph_batch_stage_times(self.h, ms), "sph_batch_stage_times")
+        return list(ms)
+
+    def kernel_count(self) -> int:
+        k = C.c_int(0)
+        check(lib().sph_batch_kernel_count(self.h, C.byref(k)), "sph_batch_kernel_count")
+        return k.value
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().sph_batch_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ---- helper: problem state held in PyTorch device memory ----------------------

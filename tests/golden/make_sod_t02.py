@@ -1,0 +1,53 @@
+"""Writes sod_t02_oracle_l1.json: the FP64 CPU oracle's L1 errors against the
+exact Riemann solution for the 3D Sod shock tube of 36864 particles (the
+configuration's 128x16x16 | 64x8x8 lattices, gamma = 1.4) run to t = 0.2
+with the CFL step (the last step shortened to end at 0.2), over the window
+of oracle.riemann.sod_window (paper Sec. 6.2, the adiabatic shock tube and
+its L1 comparison).  Calls only oracle/ (and the seeded initial conditions).
+
+    python tests/golden/make_sod_t02.py
+"""
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+import oracle as O  # noqa: E402
+from oracle import riemann  # noqa: E402
+from paper_1709_04488_gb300 import ics  # noqa: E402
+
+
+def main():
+    O.build()
+    a, p = ics.sod()
+    P = O.Params(**p, use_grid=True)
+    s = O.State(**a)
+    assert O.density(P, s) == O.OK and O.forces(P, s) == O.OK
+    t, steps, t0 = 0.0, 0, time.time()
+    T = 0.2
+    while t < T * (1 - 1e-12):
+        dt = min(O.cfl_dt(P, s), T - t)
+        assert O.step(P, s, dt) == O.OK
+        t += dt
+        steps += 1
+    lo, hi = riemann.sod_window(T, 0.0)
+    inwin = (s.x >= lo) & (s.x <= hi)
+    hmax = float(np.max(s.h[inwin]))
+    l1 = riemann.sod_l1(s.x, s.rho, s.vx, s.P, T, hmax)
+    out = {"source": "FP64 CPU oracle (oracle/sph_oracle.c), Sec. 6.2 Sod shock tube in 3D, 36864 particles",
+           "t": T, "steps": steps, "hmax_window": hmax, "window": riemann.sod_window(T, hmax),
+           "l1_rho": l1[0], "l1_vx": l1[1], "l1_P": l1[2], "particles_in_window": l1[3],
+           "seconds": time.time() - t0, "threads": O.num_threads()}
+    with open(os.path.join(HERE, "sod_t02_oracle_l1.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

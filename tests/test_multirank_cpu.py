@@ -6,6 +6,7 @@ import os
 import socket
 import sys
 
+import numpy as np
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -58,3 +59,67 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.reduce_max_ms(7.0, 1) == 7.0
     assert bench.replica_value(1000, 5, 1, 10.0) == pytest.approx(5e5)
+
+
+def _oracle_worker(rank, world, port, q):
+    """Each rank steps its own problem (a lattice with a rank-dependent jitter
+    seed) through the oracle, times it, and the ranks gather their results
+    and times over gloo, as bench.py's replicas do over NCCL."""
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import time
+    import torch.distributed as dist
+    import bench
+    import oracle as O
+    from paper_1709_04488_gb300 import ics
+    O.set_num_threads(1)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    a, p = ics.lattice(8, seed=10 + rank)
+    P = O.Params(**p)
+    s = O.State(**a)
+    t0 = time.perf_counter()
+    assert O.density(P, s) == O.OK and O.forces(P, s) == O.OK
+    for _ in range(3):
+        assert O.step(P, s, O.cfl_dt(P, s)) == O.OK
+    ms = 1e3 * (time.perf_counter() - t0)
+    slowest = bench.reduce_max_ms(ms, world, dist, torch.device("cpu"))
+    mine = {"rank": rank, "ms": ms, "x": s.x.copy(), "vx": s.vx.copy(), "rho": s.rho.copy()}
+    allr = [None] * world
+    dist.all_gather_object(allr, mine)
+    if rank == 0:
+        q.put((allr, slowest, bench.replica_value(s.n, 4, world, slowest)))
+    dist.destroy_process_group()
+
+
+def test_two_ranks_step_their_own_problems_through_the_oracle(oracle_mod):
+    """Gathered per-rank results equal the same problems stepped in one
+    process (bit for bit: the oracle's sums do not depend on the process),
+    the timing is the slowest rank's, and the whole-job value counts both
+    ranks' particle updates (one evaluation and three steps each)."""
+    O = oracle_mod
+    from paper_1709_04488_gb300 import ics
+    ctx = torch.multiprocessing.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_oracle_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    allr, slowest, value = q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [r["rank"] for r in allr] == [0, 1]
+    assert slowest == max(r["ms"] for r in allr)
+    assert value == pytest.approx(2 * 512 * 4 / (slowest * 1e-3))
+    for r in allr:
+        a, p = ics.lattice(8, seed=10 + r["rank"])
+        P = O.Params(**p)
+        s = O.State(**a)
+        assert O.density(P, s) == O.OK and O.forces(P, s) == O.OK
+        for _ in range(3):
+            assert O.step(P, s, O.cfl_dt(P, s)) == O.OK
+        assert np.array_equal(r["x"], s.x) and np.array_equal(r["vx"], s.vx)
+        assert np.array_equal(r["rho"], s.rho)
+    # the two ranks stepped different problems
+    assert not np.array_equal(allr[0]["x"], allr[1]["x"])
