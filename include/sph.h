@@ -321,9 +321,9 @@ int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, 
 /* A resident batch of contexts (the batched path of the many-problem
  * workloads): the problem tables are uploaded once at creation, and one
  * batched step (every kernel once over all problems: persistent work-queue
- * launches over (problem, leaf) items for the density and force passes) is
- * captured as a CUDA graph on the first sph_batch_run and replayed after
- * that, with no host round trip between steps.  The contexts must have a
+ * launches over (problem, leaf) items for the density and force passes)
+ * runs eagerly the first time, is captured as a CUDA graph the second time
+ * and replayed after that, with no host round trip between steps.  The contexts must have a
  * force evaluation, share precision and a non-default stream, and stay alive
  * and unchanged in size while the batch exists; workspace as for
  * sph_batch_step, reserved for the batch until sph_batch_destroy.
@@ -341,7 +341,7 @@ int sph_batch_run(sph_batch *b, int nsteps);
 int sph_batch_sync(sph_batch *b, int *status);
 /* Stage durations (ms, SPH_NSTAGES doubles) of the last batched step. */
 int sph_batch_stage_times(sph_batch *b, double *ms);
-/* Kernel launches in one captured batched step (after the first run). */
+/* Kernel launches in one captured batched step (after the second step). */
 int sph_batch_kernel_count(sph_batch *b, int *kernels);
 int sph_batch_destroy(sph_batch *b);
 

@@ -994,8 +994,8 @@ static int batch_view(sph_ctx *const *ctxs, int nctx, void *workspace, size_t ws
     CU(cudaMemsetAsync(b.dyn, 0, sizeof(ProbDyn) * nctx, st));
     CU(cudaMemsetAsync(b.counters, 0, kNumCounters * sizeof(int), st));
     CU(cudaMemsetAsync(b.zero_lo, 0, b.zero_bytes, st));
-    // the host copies of the tables are read before this returns
-    CU(cudaStreamSynchronize(st));
+    // (copies from pageable host memory are staged before cudaMemcpyAsync
+    // returns, so the local tables may go out of scope)
     return SPH_OK;
 }
 
@@ -1048,6 +1048,7 @@ struct sph_batch {
     cudaStream_t st = nullptr;
     cudaGraphExec_t graph = nullptr;
     int graph_kernels = 0;
+    int eager = 0;  // steps enqueued before the capture
     bool timing = false;
     cudaEvent_t ev[SPH_NSTAGES + 1] = {};
     bool stage_ran[SPH_NSTAGES] = {};
@@ -1127,15 +1128,19 @@ int sph_batch_run(sph_batch *bt, int nsteps)
     if (!bt) return fail(SPH_EINVAL, "batch is NULL");
     if (nsteps < 0) return fail(SPH_EINVAL, "nsteps must be >= 0");
     for (int s = 0; s < nsteps; ++s) {
-        if (!bt->graph) {
-            // one eager step first (lazily set kernel attributes), then capture
+        if (!bt->graph && bt->eager == 0) {
+            // the first step runs eagerly (it sets the kernels' lazily set
+            // attributes); a batch that takes one step only is never captured
             int rc = enqueue_step(bt->b, bt->prec, -1.0, bt->st, marks_of(bt));
             if (rc) return rc;
-            rc = batch_build_graph(bt);
-            if (rc) return rc;
-        } else {
-            CU(cudaGraphLaunch(bt->graph, bt->st));
+            ++bt->eager;
+            continue;
         }
+        if (!bt->graph) {
+            int rc = batch_build_graph(bt);
+            if (rc) return rc;
+        }
+        CU(cudaGraphLaunch(bt->graph, bt->st));
     }
     if (nsteps > 0) after_batch_steps(bt->ctxs.data(), (int)bt->ctxs.size());
     return SPH_OK;

@@ -108,6 +108,8 @@ struct sph_server {
     double clock = 0.0;
     std::chrono::steady_clock::time_point t0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    void *staging = nullptr;      // pinned host memory for retiring requests' states
+    size_t staging_bytes = 0;
 };
 
 static size_t footprint(const sph_params &p, long long n)
@@ -164,26 +166,59 @@ static int admit(sph_server *s, Req *r)
     return SPH_OK;
 }
 
-static void retire(sph_server *s, Req *r)
+// Copy the final states of the finished requests back: every array goes
+// through the server's pinned staging buffer with cudaMemcpyAsync (one copy
+// per array), then one synchronisation for all of them.
+static void retire_all(sph_server *s, const std::vector<Req *> &done)
 {
+    if (done.empty()) return;
     cudaStream_t st = (cudaStream_t)s->cfg.stream;
-    double *src[9] = {r->st.x, r->st.y, r->st.z, r->st.vx, r->st.vy, r->st.vz, r->st.u, r->st.m, r->st.h};
-    cudaStreamSynchronize(st);
-    for (int k = 0; k < 9; ++k)
-        if (r->n > 0) cudaMemcpy(r->host[k].data(), src[k], sizeof(double) * r->n, cudaMemcpyDeviceToHost);
-    r->rho.resize(r->n);
-    if (r->n > 0) cudaMemcpy(r->rho.data(), r->st.rho, sizeof(double) * r->n, cudaMemcpyDeviceToHost);
-    sph_diag d;
-    if (sph_diagnostics(r->ctx, &d) == SPH_OK) {
-        r->t_sim = d.time;
-        if (d.status != SPH_OK && r->status == SPH_OK) r->status = d.status;
+    size_t need = 0;
+    for (Req *r : done) need += 10 * sizeof(double) * (size_t)(r->n > 0 ? r->n : 0);
+    if (need > s->staging_bytes) {
+        if (s->staging) cudaFreeHost(s->staging);
+        s->staging = nullptr;
+        s->staging_bytes = 0;
+        if (cudaHostAlloc(&s->staging, need, cudaHostAllocDefault) == cudaSuccess) s->staging_bytes = need;
+        else s->staging = nullptr;
     }
-    sph_destroy(r->ctx);
-    r->ctx = nullptr;
-    s->pool.release(r->mem, r->mem_bytes);
-    r->mem = nullptr;
-    r->state = DONE;
-    r->completed = s->clock;
+    double *stage = (double *)s->staging;
+    size_t off = 0;
+    for (Req *r : done) {
+        double *src[10] = {r->st.x, r->st.y, r->st.z, r->st.vx, r->st.vy, r->st.vz, r->st.u, r->st.m, r->st.h, r->st.rho};
+        r->rho.resize(r->n);
+        for (int k = 0; k < 10; ++k) {
+            if (r->n <= 0) continue;
+            double *dst = k < 9 ? r->host[k].data() : r->rho.data();
+            if (stage) {
+                cudaMemcpyAsync(stage + off, src[k], sizeof(double) * r->n, cudaMemcpyDeviceToHost, st);
+                off += (size_t)r->n;
+            } else {
+                cudaMemcpyAsync(dst, src[k], sizeof(double) * r->n, cudaMemcpyDeviceToHost, st);
+            }
+        }
+    }
+    cudaStreamSynchronize(st);
+    off = 0;
+    for (Req *r : done) {
+        for (int k = 0; k < 10 && stage; ++k) {
+            if (r->n <= 0) continue;
+            double *dst = k < 9 ? r->host[k].data() : r->rho.data();
+            memcpy(dst, stage + off, sizeof(double) * r->n);
+            off += (size_t)r->n;
+        }
+        sph_diag d;
+        if (sph_diagnostics(r->ctx, &d) == SPH_OK) {
+            r->t_sim = d.time;
+            if (d.status != SPH_OK && r->status == SPH_OK) r->status = d.status;
+        }
+        sph_destroy(r->ctx);
+        r->ctx = nullptr;
+        s->pool.release(r->mem, r->mem_bytes);
+        r->mem = nullptr;
+        r->state = DONE;
+        r->completed = s->clock;
+    }
 }
 
 extern "C" {
@@ -270,23 +305,32 @@ int sph_server_run(sph_server *s, double until, int virtual_clock)
             }
             continue;
         }
-        // one batched step over every resident problem
+        // one batched step over every resident problem; each request takes
+        // its own problem's status (one failing problem fails no other)
         std::vector<sph_ctx *> ctxs;
         ctxs.reserve(s->active.size());
         for (Req *r : s->active) ctxs.push_back(r->ctx);
+        std::vector<int> status(ctxs.size(), SPH_OK);
         size_t bw = sph_batch_workspace_bytes(ctxs.data(), (int)ctxs.size());
         void *bmem = bw ? s->pool.alloc(bw) : nullptr;
-        int rc;
         if (bmem) {
-            rc = sph_batch_step(ctxs.data(), (int)ctxs.size(), 1, bmem, bw);
+            sph_batch *bt = nullptr;
+            int rc = sph_batch_create(&bt, ctxs.data(), (int)ctxs.size(), bmem, bw, 0);
+            if (rc == SPH_OK) rc = sph_batch_run(bt, 1);
+            if (bt) {
+                sph_batch_sync(bt, status.data());
+                sph_batch_destroy(bt);
+            }
+            if (rc != SPH_OK)
+                for (int &v : status)
+                    if (v == SPH_OK) v = rc;
             s->pool.release(bmem, bw);
         } else {
-            rc = SPH_OK;  // no contiguous room: step the problems one by one
-            for (sph_ctx *c : ctxs) {
-                int r2 = sph_step(c, -1.0, nullptr);
-                if (r2 != SPH_OK && rc == SPH_OK) rc = r2;
+            // no contiguous room: step the problems one by one
+            for (size_t k = 0; k < ctxs.size(); ++k) {
+                const int r2 = sph_step(ctxs[k], -1.0, nullptr);
+                status[k] = r2 != SPH_OK ? r2 : sph_sync(ctxs[k]);
             }
-            cudaStreamSynchronize(st);
         }
         cudaEventRecord(s->ev1, st);
         cudaEventSynchronize(s->ev1);
@@ -294,13 +338,16 @@ int sph_server_run(sph_server *s, double until, int virtual_clock)
         cudaEventElapsedTime(&ms, s->ev0, s->ev1);
         if (virtual_clock) s->clock += 1e-3 * ms;
         else s->clock = std::max(s->clock, wall_now(s));
-        std::vector<Req *> keep;
-        for (Req *r : s->active) {
+        std::vector<Req *> keep, done;
+        for (size_t k = 0; k < s->active.size(); ++k) {
+            Req *r = s->active[k];
             r->steps_done += 1;
-            if (rc != SPH_OK && r->status == SPH_OK) r->status = rc;
-            if (r->steps_done >= r->nsteps) retire(s, r);
+            if (status[k] != SPH_OK && r->status == SPH_OK) r->status = status[k];
+            // a failed request stops here; the others go on
+            if (r->steps_done >= r->nsteps || r->status != SPH_OK) done.push_back(r);
             else keep.push_back(r);
         }
+        retire_all(s, done);
         s->active.swap(keep);
     }
 }
@@ -336,6 +383,7 @@ int sph_server_destroy(sph_server *s)
     }
     if (s->ev0) cudaEventDestroy(s->ev0);
     if (s->ev1) cudaEventDestroy(s->ev1);
+    if (s->staging) cudaFreeHost(s->staging);
     delete s;
     return SPH_OK;
 }

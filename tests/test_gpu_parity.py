@@ -408,3 +408,26 @@ def test_price_sod_steps_match_oracle(S, oracle_mod):
     g = prob.numpy()
     assert _rel(g["rho"], ref.rho) < 1e-5
     assert _rms_err(g["u"], ref.u) < 1e-5
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_energy_balance_matches_oracle(S, oracle_mod, prec):
+    """The energy rate sum_i m_i (v_i . a_i + du_i/dt) vanishes pair by pair
+    (pressure, viscosity and conduction terms each; Sec. 2.1.1, adiabatic
+    gas).  The GPU's FP64 reduction of it (sph_diag.dEdt) equals the oracle's
+    value to the rounding of the pair terms: within 1e-7 (mixed) or 1e-12
+    (FP64) of sum_i m_i (|v_i . a_i| + |du_i/dt|)."""
+    O = oracle_mod
+    a, p = _moving_lattice()
+    P, ref = _oracle(O, a, p)
+    pr = S.PREC_MIXED if prec == "mixed" else S.PREC_FP64
+    prob = _gpu(S, a, p, pr)
+    g = prob.numpy()
+    d = prob.diagnostics()
+    va = a["vx"] * g["ax"] + a["vy"] * g["ay"] + a["vz"] * g["az"]
+    scale = float(np.sum(a["m"] * (np.abs(va) + np.abs(g["du"]))))
+    ref_rate = O.diagnostics(P, ref)["dEdt"]
+    tol = 1e-7 if prec == "mixed" else 1e-12
+    assert abs(ref_rate) < 1e-12 * scale        # the oracle's own balance
+    assert abs(d.dEdt - ref_rate) < tol * scale
+    assert abs(float(np.sum(a["m"] * (va + g["du"])))) < tol * scale

@@ -89,3 +89,40 @@ def test_too_big_and_busy(S):
         srv.submit(reqs[0]["arrays"], reqs[0]["params"], 1, 0.0)
     assert e.value.code == S.ETOOBIG
     srv.close()
+
+
+def test_one_failing_request_fails_alone(S):
+    """A request that cannot converge (four isolated particles) is served
+    beside three healthy ones: it comes back with an error status, and the
+    healthy ones finish with SPH_OK and the same bits as each run alone (each
+    request takes its own problem's status, not the batch's)."""
+    from paper_1709_04488_gb300 import serve
+    reqs = serve.make_requests(3, seed=17, n_min=1e3, n_max=8e3, nsteps=3)
+    rng = np.random.default_rng(0)
+    bad = {k: rng.uniform(0, 1, 4) for k in ("x", "y", "z")}
+    bad.update(vx=np.zeros(4), vy=np.zeros(4), vz=np.zeros(4), u=np.ones(4), m=np.ones(4), h=np.full(4, 0.1))
+    srv = serve.Server(1 << 30, max_slots=8)
+    tickets = [srv.submit(r["arrays"], r["params"], r["nsteps"], 0.0) for r in reqs[:2]]
+    tb = srv.submit(bad, {"periodic": False, "box_lo": (0.0, 0.0, 0.0), "box_len": (0.0, 0.0, 0.0),
+                          "eos": "adiabatic", "gamma": 5.0 / 3.0}, 3, 0.0)
+    tickets.append(srv.submit(reqs[2]["arrays"], reqs[2]["params"], reqs[2]["nsteps"], 0.0))
+    srv.run(virtual_clock=True)
+    ob = srv.poll(tb, 4)
+    assert ob is not None and ob["status"] != S.OK
+    for r, tk in zip(reqs, tickets):
+        o = srv.poll(tk, len(r["arrays"]["x"]), want_state=True)
+        assert o is not None and o["status"] == S.OK and o["steps_done"] == r["nsteps"]
+        ref = _alone(S, r)
+        for f in ("x", "vx", "u", "h", "rho"):
+            assert np.array_equal(o[f], ref[f]), f
+    srv.close()
+
+
+def test_zero_step_request_is_rejected(S):
+    from paper_1709_04488_gb300 import serve
+    reqs = serve.make_requests(1, seed=19, n_min=1e3, n_max=1e3, nsteps=1)
+    srv = serve.Server(1 << 28, max_slots=4)
+    with pytest.raises(S.SPHError) as e:
+        srv.submit(reqs[0]["arrays"], reqs[0]["params"], 0, 0.0)
+    assert e.value.code == S.EINVAL
+    srv.close()
