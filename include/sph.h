@@ -73,6 +73,7 @@ extern "C" {
 
 #define SPH_AV_CONSTANT 0          /* viscosity alpha_av everywhere                       */
 #define SPH_AV_MORRIS_MONAGHAN 1   /* per-particle alpha, Morris & Monaghan (1997) switch  */
+#define SPH_AV_CULLEN_DEHNEN 2     /* per-particle alpha, Cullen & Dehnen (2010) switch    */
 
 #define SPH_FLAG_ASYNC 1u    /* compute calls return without synchronising the stream     */
 #define SPH_FLAG_TIMING 2u   /* record CUDA events around the stages of every step        */
@@ -128,7 +129,20 @@ typedef struct {
                               beta_ij = beta_av / alpha_av alpha_ij (Sec. 2.1.1 names the
                               Morris & Monaghan 1997 switch).  Requires alpha_av > 0,
                               0 <= alpha_min <= alpha_av, av_decay > 0 and non-NULL
-                              state.alpha, state.dalpha; not accepted by the server.  */
+                              state.alpha, state.dalpha; not accepted by the server.
+                              SPH_AV_CULLEN_DEHNEN: alpha per particle from a shock
+                              indicator (Cullen & Dehnen 2010): the force pass forms the
+                              velocity gradient V = -(1/(Omega rho)) sum_j m_j v_ij (x)
+                              grad_i W(h_i), D = tr V, the traceless shear S, R = (1/rho)
+                              sum_j sign(D_j) m_j W(r_ij, h_i) (self included, signs of
+                              the previous evaluation), xi = q^2/(q^2 + tr S S^T) with
+                              q = 2 (1-R)^4 D; each step then sets A = xi max(-dD/dt, 0)
+                              (dD/dt between the step's two force evaluations),
+                              alpha_loc = alpha_av h^2 A / (v_sig^2 + h^2 A), and alpha =
+                              alpha_loc where alpha < alpha_loc, else it decays towards it
+                              with time constant h / (2 av_decay v_sig).  state.dalpha
+                              holds D (input: the previous evaluation's, 0 at the start;
+                              output: this one's).  Not with block time-steps.        */
     double alpha_min;      /* switch: floor alpha decays to (default 0.1)               */
     double av_decay;       /* switch: decay rate in units of c/h (default 0.1)          */
     int gravity;           /* 1: self-gravity, Eq. SPHSELFGRAV (Sec. 2.1.2): the kernel-
@@ -398,14 +412,13 @@ int sph_server_destroy(sph_server *s);
  * own pool, or a plug-in or real-time loop called from such a host.  The paper
  * has no counterpart: this is a property of the library, not of the method.
  *   - Allocates nothing: no cudaMalloc/cudaFree, no allocating library call.
- *     Its scratch memory is a fixed 16 MiB array compiled into the library,
+ *     Its scratch memory is a fixed 24 MiB array compiled into the library,
  *     which every GPU that loads the library holds until the process exits.
- *   - n is at most 32768; larger n returns SPH_EINVAL with a message.  With
- *     self-gravity the scratch also holds the long-range sum's buffers, so
- *     the largest n is smaller: 30240 (mixed precision, direct sum), 27840
- *     (FP64, direct sum), 24960 (FP64, tree walk); the mixed tree walk takes
- *     32768.  A call beyond its limit returns SPH_ENOSPACE, before touching
- *     the device, with a message naming the largest n that fits.
+ *   - n is at most 32768, whatever the options (precision, kernel,
+ *     self-gravity by direct sum or tree walk; the FP64 tree walk's layout,
+ *     the largest, takes about 22 MiB); larger n returns SPH_EINVAL with a
+ *     message.  (A layout that did not fit would return SPH_ENOSPACE, before
+ *     touching the device, naming the largest n that fits.)
  *   - The caller passes the particle arrays (inputs and outputs as in
  *     sph_state) and the stream; p as for sph_setup (SPH_FLAG_ASYNC skips the
  *     final synchronisation, and then no status is reported).

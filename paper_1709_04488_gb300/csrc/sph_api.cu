@@ -69,6 +69,9 @@ void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precis
     void **st[] = {&b.pm, &b.ph, &b.vc, &b.th};
     for (void **p : st) *p = c.take<char>(v4 * n);
     b.sal = c.take<char>(v4 / 4 * n);
+    b.scd = c.take<char>(v4 / 4 * n);
+    b.cdold = c.take<double>(n);
+    b.cdxi = c.take<double>(n);
     b.szg = c.take<char>(v4 / 4 * n);
     b.gpart = grav_chunks > 1 ? c.take<double>(3LL * grav_chunks * n) : nullptr;
     b.gpos = grav_tree ? (void *)c.take<char>(v4 * n) : nullptr;
@@ -206,11 +209,17 @@ namespace sph {
 int validate(const sph_params *p)
 {
     if (!p) return fail(SPH_EINVAL, "params is NULL");
-    if (p->av_switch != SPH_AV_CONSTANT && p->av_switch != SPH_AV_MORRIS_MONAGHAN)
-        return fail(SPH_EINVAL, "av_switch %d not supported (0 = constant, 1 = Morris & Monaghan)", p->av_switch);
+    if (p->av_switch != SPH_AV_CONSTANT && p->av_switch != SPH_AV_MORRIS_MONAGHAN &&
+        p->av_switch != SPH_AV_CULLEN_DEHNEN)
+        return fail(SPH_EINVAL, "av_switch %d not supported (0 = constant, 1 = Morris & Monaghan, 2 = Cullen & Dehnen)",
+                    p->av_switch);
     if (p->av_switch == SPH_AV_MORRIS_MONAGHAN &&
         !(p->alpha_av > 0 && p->alpha_min >= 0 && p->alpha_min <= p->alpha_av && p->av_decay > 0))
         return fail(SPH_EINVAL, "viscosity switch needs alpha_av > 0, 0 <= alpha_min <= alpha_av, av_decay > 0");
+    if (p->av_switch == SPH_AV_CULLEN_DEHNEN && !(p->alpha_av > 0 && p->av_decay > 0))
+        return fail(SPH_EINVAL, "the Cullen & Dehnen switch needs alpha_av > 0 and av_decay > 0");
+    if (p->av_switch == SPH_AV_CULLEN_DEHNEN && p->block_levels > 0)
+        return fail(SPH_EINVAL, "the Cullen & Dehnen switch is not combined with block time-steps");
     if (p->gravity != 0 && p->gravity != 1) return fail(SPH_EINVAL, "gravity must be 0 or 1");
     if (p->gravity && !(p->grav_theta >= 0.0 && p->grav_theta <= 1.0))
         return fail(SPH_EINVAL, "grav_theta must lie in [0, 1]");
@@ -427,6 +436,7 @@ int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *st
     c->bv.any_periodic = p->periodic ? 1 : 0;
     c->bv.any_general = (p->av_switch || p->ac_signal || p->gravity) ? 1 : 0;
     c->bv.any_gravity = p->gravity ? 1 : 0;
+    c->bv.any_cd = p->av_switch == SPH_AV_CULLEN_DEHNEN ? 1 : 0;
     c->bv.grav_blocks = p->gravity ? gravity_blocks(n, p->grav_theta) : 0;
     c->bv.grav_split = p->gravity && gravity_chunks(n, p->grav_theta) > 1;
     c->bv.any_grav_tree = p->gravity && p->grav_theta > 0;
@@ -953,6 +963,7 @@ static int batch_view(sph_ctx *const *ctxs, int nctx, void *workspace, size_t ws
     std::vector<ProbStatic> tab(nctx);
     std::vector<long long> bases(nctx + 1);
     int mask = 0, dmask = 0, b_any_isolated = 0, b_any_periodic = 0, b_any_general = 0, b_any_gravity = 0;
+    int b_any_cd = 0;
     long long grav_blocks = 0;
     int gch = 0, gtree = 0;
     for (int k = 0; k < nctx; ++k) {
@@ -966,6 +977,7 @@ static int batch_view(sph_ctx *const *ctxs, int nctx, void *workspace, size_t ws
         else b_any_periodic = 1;
         if (tab[k].ph.av_switch || tab[k].ph.ac_signal || tab[k].ph.gravity) b_any_general = 1;
         if (tab[k].ph.gravity) b_any_gravity = 1;
+        if (tab[k].ph.av_switch == SPH_AV_CULLEN_DEHNEN) b_any_cd = 1;
         tab[k].gblk0 = (int)grav_blocks;
         tab[k].gchunks = tab[k].ph.gravity ? gravity_chunks(ctxs[k]->n, tab[k].ph.grav_theta) : 0;
         if (tab[k].ph.gravity) grav_blocks += gravity_blocks(ctxs[k]->n, tab[k].ph.grav_theta);
@@ -986,6 +998,7 @@ static int batch_view(sph_ctx *const *ctxs, int nctx, void *workspace, size_t ws
     b.any_periodic = b_any_periodic;
     b.any_general = b_any_general;
     b.any_gravity = b_any_gravity;
+    b.any_cd = b_any_cd;
     b.grav_blocks = grav_blocks;
     b.grav_split = gch > 1;
     b.any_grav_tree = gtree;

@@ -49,7 +49,8 @@ __device__ __forceinline__ void reset_counters(const BatchView &b, int mode)
     const bool all = (k >= kSlowCounter && k <= kForceWrapList) || k >= kTimeoutCounter;
     const bool forces = k == kForceWrapList || k == kTimeoutCounter ||
                         (k >= kForceCounter && k < kForceCounter + kForceClasses) ||
-                        (k >= kForceWrapCounter && k < kForceWrapCounter + kForceClasses);
+                        (k >= kForceWrapCounter && k < kForceWrapCounter + kForceClasses) ||
+                        (k >= kForceCdCounter && k < kForceCdCounter + kForceClasses);
     if (mode == 1 ? all : forces) b.counters[k] = 0;
 }
 
@@ -110,7 +111,7 @@ __global__ void k_kick_drift(BatchView b, double dt_host)
     } else {
         b.up[g] = u;
     }
-    if (ph.av_switch) {  // the switch's alpha is kicked and predicted like u
+    if (ph.av_switch == SPH_AV_MORRIS_MONAGHAN) {  // the switch's alpha is kicked and predicted like u
         const double ah = ps.alpha[i] + hdt * ps.dalpha[i];
         ps.alpha[i] = ah;
         b.ap[g] = ah + hdt * ps.dalpha[i];
@@ -201,7 +202,19 @@ __global__ void k_kick_close(BatchView b, int do_kick, int forces_ran, int items
                 u += hdt * du;
                 ps.u[i] = u;
             }
-            if (ph.av_switch) ps.alpha[i] += hdt * ps.dalpha[i];
+            if (ph.av_switch == SPH_AV_MORRIS_MONAGHAN) ps.alpha[i] += hdt * ps.dalpha[i];
+            if (ph.av_switch == SPH_AV_CULLEN_DEHNEN && forces_ran) {
+                // Cullen & Dehnen: A = xi max(-dD/dt, 0) with dD/dt between the
+                // step's two force evaluations; alpha rises to alpha_loc at once
+                // and decays towards it on h / (2 av_decay v_sig)
+                const double dt = 2.0 * hdt;
+                const double ddot = (ps.dalpha[i] - b.cdold[g]) / dt;
+                const double Aa = b.cdxi[g] * (ddot < 0.0 ? -ddot : 0.0);
+                const double h = ps.h[i], h2A = h * h * Aa, vs = ps.vsig[i];
+                const double aloc = h2A > 0.0 ? ph.alpha_av * h2A / (vs * vs + h2A) : 0.0;
+                const double al = ps.alpha[i];
+                ps.alpha[i] = al < aloc ? aloc : aloc + (al - aloc) * exp(-dt * 2.0 * ph.av_decay * vs / h);
+            }
         }
         double m = ps.m[i];
         v[0] += m;

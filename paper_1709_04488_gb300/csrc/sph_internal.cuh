@@ -20,15 +20,18 @@ constexpr double kPi = 3.14159265358979323846;
 // density (force) wrap list, 15 look-back timeout, 16..31 density leaf
 // tickets (per class: lanes, equal masses, kernel), 32..39 force leaf
 // tickets (per lanes per particle and kernel), 40..55 and 56..63 the same
-// for the launches that serve the wrap lists; the step's first kernel clears
-// 8..11 and 15..63, a forces-only call 11, 15, 32..39 and 56..63
-constexpr int kNumCounters = 64;
+// for the launches that serve the wrap lists, 64..71 the force tickets of the
+// Cullen & Dehnen launches; the step's first kernel clears 8..11 and 15..71,
+// a forces-only call 11, 15, 32..39 and 56..71
+constexpr int kNumCounters = 72;
 constexpr int kSlowCounter = 8, kPoolCounter = 9, kDensWrapList = 10, kForceWrapList = 11, kTimeoutCounter = 15;
-constexpr int kDensityCounter = 16, kForceCounter = 32, kDensityWrapCounter = 40, kForceWrapCounter = 56;
+constexpr int kDensityCounter = 16, kForceCounter = 32, kDensityWrapCounter = 40, kForceWrapCounter = 56,
+              kForceCdCounter = 64;
 constexpr int kDensityClasses = 16, kForceClasses = 8;
 static_assert(kDensityCounter + kDensityClasses <= kForceCounter && kForceCounter + kForceClasses <= kDensityWrapCounter &&
                   kDensityWrapCounter + kDensityClasses <= kForceWrapCounter &&
-                  kForceWrapCounter + kForceClasses <= kNumCounters,
+                  kForceWrapCounter + kForceClasses <= kForceCdCounter &&
+                  kForceCdCounter + kForceClasses <= kNumCounters,
               "counter slots");
 constexpr int kMaxLeafGroups = 32;  // candidate-leaf groups recorded per leaf (one per lane)
 #ifndef SPH_HPREDICT
@@ -167,6 +170,7 @@ struct BatchView {
     int any_general;             // some problem uses the viscosity switch, Price's conductivity or
                                  // gravity (served by the wrap-list launches)
     int any_gravity;             // some problem has self-gravity (direct-sum launch)
+    int any_cd;                  // some problem uses the Cullen & Dehnen switch (its own force launches)
     long long grav_blocks;       // blocks of the direct-sum launch (all gravity problems)
     int grav_split;              // some gravity problem splits its partners (partial sums to reduce)
     int any_grav_tree;           // some gravity problem walks the tree (grav_theta > 0)
@@ -206,6 +210,9 @@ struct BatchView {
     void *vc;   // (v xyz, c)
     void *th;   // (P/(Omega rho^2), rho, m, u)
     void *sal;  // alpha of the viscosity switch (T per particle)
+    void *scd;  // Cullen & Dehnen: div v of the previous force evaluation (T per sorted particle)
+    double *cdold, *cdxi;  // Cullen & Dehnen (original order, batch-global): div v before this
+                           // evaluation and the limiter xi of this one, for the step's alpha update
     void *szg;  // gravity: G zeta / (2 Omega) (T per particle), the zeta term's weight
     // leaves
     unsigned *flag;              // [ntot] leaf start flags, then leaf index (scan)

@@ -18,14 +18,14 @@ namespace {
 
 using namespace sph;
 
-// Largest problem the fixed scratch holds, and its size.  16 MiB holds the
-// workspace layout of either precision for 32768 particles without
-// self-gravity (14.3 MiB for the FP64 layout), plus the diagnostics record.
-// Self-gravity adds the long-range sum's buffers (partial sums of split
-// partner ranges, the tree walk's copies), so with gravity the largest n is
-// smaller; noalloc_max_n() finds it for the caller's parameters.
+// Largest problem the fixed scratch holds, and its size.  24 MiB holds the
+// workspace layout of every option for 32768 particles: the FP64 layout
+// (15 MiB) plus self-gravity's buffers (partial sums of split partner
+// ranges, the tree walk's copies; the FP64 tree walk's layout is the
+// largest, 22 MiB), plus the diagnostics record.  noalloc_max_n() finds the
+// largest n for a layout that would not fit (a guard: none does now).
 constexpr long long kNoAllocMaxN = 32768;
-constexpr size_t kNoAllocBytes = (size_t)16 << 20;
+constexpr size_t kNoAllocBytes = (size_t)24 << 20;
 constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
@@ -138,6 +138,7 @@ extern "C" int sph_density_forces_noalloc(const sph_params *p, int64_t n, const 
     b.any_periodic = p->periodic ? 1 : 0;
     b.any_general = (p->av_switch || p->ac_signal || p->gravity) ? 1 : 0;
     b.any_gravity = p->gravity ? 1 : 0;
+    b.any_cd = p->av_switch == SPH_AV_CULLEN_DEHNEN ? 1 : 0;
     b.grav_blocks = p->gravity ? gravity_blocks(n, p->grav_theta) : 0;
     b.grav_split = p->gravity && gravity_chunks(n, p->grav_theta) > 1;
     b.any_grav_tree = p->gravity && p->grav_theta > 0;

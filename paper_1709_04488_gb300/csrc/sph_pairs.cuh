@@ -671,7 +671,9 @@ __device__ __forceinline__ void density_epilogue(const BatchView &b, const ProbS
     q.z = pi.w;
     q.w = (T)u;
     ((V *)b.th)[s] = q;
-    if (ph.av_switch) ((T *)b.sal)[s] = (T)(use_pred ? b.ap[g] : ps.alpha[i]);  // viscosity switch
+    if (ph.av_switch)  // viscosity switch (Morris & Monaghan's alpha is kicked and predicted like u)
+        ((T *)b.sal)[s] = (T)(use_pred && ph.av_switch == SPH_AV_MORRIS_MONAGHAN ? b.ap[g] : ps.alpha[i]);
+    if (ph.av_switch == SPH_AV_CULLEN_DEHNEN) ((T *)b.scd)[s] = (T)ps.dalpha[i];  // the previous div v
     // gravity: zeta = dh/drho sum_j m_j dphi/dh = Z / (3 rho h) (Z = sum_j m_j (psi + M/q)),
     // kept as the weight G zeta / (2 Omega) of the force pass's zeta term
     if (ph.gravity) {
@@ -1315,7 +1317,7 @@ __device__ __forceinline__ dbl4 ld_ro<dbl4>(const dbl4 *p)
 // list and its pair vectors are wrapped where they may miss the minimum
 // image.  Returns false (writing nothing) when the plain launch meets an
 // ambiguous leaf pair.
-template <typename T, int LPP, int K, bool WRAP>
+template <typename T, int LPP, int K, bool WRAP, bool CD>
 __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigned char *mine, float Rall)
 {
     using C = FCfg<T, LPP>;
@@ -1353,6 +1355,13 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
     const T* __restrict__ sal = (const T *)b.sal;
     const T alpha_i = sw ? sal[s] : alpha, bratio = (T)ph.beta_ratio;
     T dvs = T(0);  // sum_j m_j v_ij . grad_i W(h_i) (switch: div v)
+    // Cullen & Dehnen (its own launch, so that the other options keep their
+    // registers): the gradient sums G_ab = sum_j m_j v_ij,a grad_i,b W(h_i)
+    // and the signed density sum_j sign(D_j) m_j W(r_ij, h_i)
+    constexpr bool cdw = CD;
+    const T* __restrict__ scd = (const T *)b.scd;
+    T cg[9] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+    T cr = T(0);
     // gravity (wrap-list launch): the zeta term of Eq. SPHSELFGRAV has the pressure
     // term's form, with P/(Omega rho^2) + G zeta/(2 Omega) per particle
     const bool grav = WRAP && ph.gravity != 0;
@@ -1428,6 +1437,23 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
                 al = mul_rn(T(0.5), add_rn(alpha_i, sal[j]));
                 be = mul_rn(bratio, al);
                 dvs += a2.z * vdr * gi;
+            }
+            if (cdw) {
+                const T mg = a2.z * gi * rinv;
+                cg[0] += mg * vx * rx;
+                cg[1] += mg * vx * ry;
+                cg[2] += mg * vx * rz;
+                cg[3] += mg * vy * rx;
+                cg[4] += mg * vy * ry;
+                cg[5] += mg * vy * rz;
+                cg[6] += mg * vz * rx;
+                cg[7] += mg * vz * ry;
+                cg[8] += mg * vz * rz;
+                if (qi < T(KF::R)) {
+                    T f, df;
+                    KF::fdf(qi, f, df);
+                    cr += (scd[j] < T(0) ? -a2.z : a2.z) * f;
+                }
             }
             const T vsig = fma_rn(-be, mu, add_rn(vi.w, a1.w));
             const T visc = mul_rn(mul_rn(mul_rn(al, vsig), mu), rhob_inv);
@@ -1546,6 +1572,11 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
     du = group_sum<LPP>(du);
     vs = group_max<LPP>(vs);
     if (sw) dvs = group_sum<LPP>(dvs);
+    if (cdw) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) cg[k] = group_sum<LPP>(cg[k]);
+        cr = group_sum<LPP>(cr);
+    }
     if (blk) mlev = group_max<LPP>(mlev);
     // a = F / m in FP64 (m a stays F to FP64 round-off), one reciprocal
     // per particle (none for equal masses); the CFL step C h / v_sig of
@@ -1564,11 +1595,32 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
         ps.az[i] = a[2];
         ps.du[i] = adi ? (double)du : 0.0;
         ps.vsig[i] = (double)vsig_t;
-        if (sw) {  // Morris & Monaghan: decay towards alpha_min, growth where compressed
+        if (sw && !cdw) {  // Morris & Monaghan: decay towards alpha_min, growth where compressed
             const double divv = -(double)dvs / (b.somega[s] * b.srho[s]);
             const double ai = (double)alpha_i;
             ps.dalpha[i] = -(ai - ph.alpha_min) * ph.av_decay * (double)vi.w / b.sh[s] +
                            (divv < 0.0 ? -divv * (ph.alpha_av - ai) : 0.0);
+        }
+        if (cdw) {  // Cullen & Dehnen: velocity gradient, shear, signed density, limiter
+            const double rho_i = b.srho[s], f = -1.0 / (b.somega[s] * rho_i);
+            double V[9];
+            for (int k = 0; k < 9; ++k) V[k] = f * (double)cg[k];
+            const double dv = V[0] + V[4] + V[8];
+            double ss = 0.0;
+            for (int p2 = 0; p2 < 3; ++p2)
+                for (int q2 = 0; q2 < 3; ++q2) {
+                    const double sab = 0.5 * (V[3 * p2 + q2] + V[3 * q2 + p2]) - (p2 == q2 ? dv / 3.0 : 0.0);
+                    ss += sab * sab;
+                }
+            const double hinv_i = (double)xi.w, w0 = Kern<K>::sigma * hinv_i * hinv_i * hinv_i;
+            T f0, df0;
+            KF::fdf(T(0), f0, df0);
+            const double self = (ps.dalpha[i] < 0.0 ? -1.0 : 1.0) * (double)ti.z * (double)f0;
+            const double R = ((double)cr + self) * w0 / rho_i;
+            const double om = 1.0 - R, qq = 2.0 * om * om * om * om * dv;
+            b.cdold[g] = ps.dalpha[i];
+            b.cdxi[g] = (qq * qq + ss) > 0.0 ? qq * qq / (qq * qq + ss) : 0.0;
+            ps.dalpha[i] = dv;
         }
         dti = (T)ph.c_cfl * (T)b.sh[s] / vsig_t;
         if (!(isfinite(a[0]) && isfinite(a[1]) && isfinite(a[2]) && isfinite(du)))
@@ -1587,7 +1639,7 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
 
 // WRAP: the launch that serves the wrap list (leaves whose pair vectors may
 // miss the minimum image); the other launch puts them there.
-template <typename T, int LPP, int K, bool WRAP>
+template <typename T, int LPP, int K, bool WRAP, bool CD>
 __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, FCfg<T, LPP>::MINB) k_forces(BatchView b)
 {
     using C = FCfg<T, LPP>;
@@ -1600,13 +1652,14 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, FCfg<T, LPP>::MINB) k_
     float Rall = 0.f;  // periodic: pairs reach R_K x the problem's largest h
     for (;;) {
         int leaf = 0;
-        if (lane == 0) leaf = atomicAdd(&b.counters[(WRAP ? kForceWrapCounter : kForceCounter) + cls], 1);
+        if (lane == 0) leaf = atomicAdd(&b.counters[(CD ? kForceCdCounter : WRAP ? kForceWrapCounter : kForceCounter) + cls], 1);
         leaf = __shfl_sync(FULL, leaf, 0);
         if (leaf >= nleaf) break;
         if (WRAP) leaf = b.wrap_list[leaf];
         const int p = b.leaf_pid[leaf];
         const ProbStatic &ps = b.prob[p];
         if (ps.lpp != LPP || ps.ph.kernel != K) continue;  // leaf of a problem served by another launch
+        if (WRAP && (ps.ph.av_switch == SPH_AV_CULLEN_DEHNEN) != CD) continue;  // (the switch's own launch)
         if (!WRAP && (ps.ph.av_switch || ps.ph.ac_signal || ps.ph.gravity || b.block_on)) {
             // the viscosity switch, Price's conductivity and gravity's zeta term run in the
             // wrap-list launch only, which keeps the common path's registers for the default scheme
@@ -1619,7 +1672,7 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, FCfg<T, LPP>::MINB) k_
             Rall = __fmul_ru((float)Kern<K>::R, Rall) * 1.0001f;
             last_p = p;
         }
-        if (!force_leaf<T, LPP, K, WRAP>(b, leaf, mine, Rall) && lane == 0) {
+        if (!force_leaf<T, LPP, K, WRAP, CD>(b, leaf, mine, Rall) && lane == 0) {
             b.wrap_list[atomicAdd(&b.counters[kForceWrapList], 1)] = leaf;
             atomicAdd(&ps.diag->wrap_leaves, 1);
         }
@@ -1660,22 +1713,26 @@ void run_density_fallback(const BatchView &b, int use_pred, cudaStream_t st)
     k_density_fallback<T><<<dev_info().sm_count * 4, C::WPB * 32, C::smem, st>>>(b, use_pred);
 }
 
-template <typename T, int LPP, int K, bool WRAP>
+template <typename T, int LPP, int K, bool WRAP, bool CD = false>
 cudaError_t run_forces(const BatchView &b, cudaStream_t st)
 {
     using C = FCfg<T, LPP>;
     static bool init = false;
     if (!init) {
-        set_smem(k_forces<T, LPP, K, WRAP>, C::smem);
+        set_smem(k_forces<T, LPP, K, WRAP, CD>, C::smem);
         init = true;
     }
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forces<T, LPP, K, WRAP>, C::WPB * 32, C::smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forces<T, LPP, K, WRAP, CD>, C::WPB * 32, C::smem);
     if (per_sm < 1) per_sm = 1;
     // the wrap list is short unless a problem uses the viscosity switch or Price's conductivity
     int grid = dev_info().sm_count * (WRAP && !b.any_general ? 1 : per_sm);
-    k_forces<T, LPP, K, WRAP><<<grid, C::WPB * 32, C::smem, st>>>(b);
-    return cudaGetLastError();
+    k_forces<T, LPP, K, WRAP, CD><<<grid, C::WPB * 32, C::smem, st>>>(b);
+    cudaError_t e = cudaGetLastError();
+    // the Cullen & Dehnen problems' leaves on the wrap list: their own launch
+    if constexpr (WRAP && !CD)
+        if (e == cudaSuccess && b.any_cd) e = run_forces<T, LPP, K, true, true>(b, st);
+    return e;
 }
 
 // The density launches of kernel K: one per class (lanes per particle, equal

@@ -69,11 +69,19 @@ def _block(nx, ny, nz, lo, hi):
 
 
 def sod(left=(128, 16, 16), right=(64, 8, 8), rho=(1.0, 0.125), P=(1.0, 0.1),
-        gamma: float = 1.4, length: float = 1.0, width: float = 0.125):
-    """Shock tube split at x = length/2 in a periodic box length x width x width."""
+        gamma: float = 1.4, length: float = 1.0, width: float = 0.125, jitter: float = 0.0, seed: int = 1):
+    """Shock tube split at x = length/2 in a periodic box length x width x width.
+    jitter > 0 moves every particle by a uniform random offset of up to
+    jitter x its lattice spacing per axis (seeded; none by default)."""
     Lb = (length, width, width)
     pl = _block(*left, (0.0, 0.0, 0.0), (0.5 * length, width, width))
     pr = _block(*right, (0.5 * length, 0.0, 0.0), (length, width, width))
+    if jitter > 0:
+        rng = np.random.default_rng(seed)
+        dl = np.array([0.5 * length / left[0], width / left[1], width / left[2]])
+        dr = np.array([0.5 * length / right[0], width / right[1], width / right[2]])
+        pl = pl + rng.uniform(-jitter, jitter, pl.shape) * dl
+        pr = pr + rng.uniform(-jitter, jitter, pr.shape) * dr
     vol = 0.5 * length * width * width
     ml = rho[0] * vol / pl.shape[0]
     mr = rho[1] * vol / pr.shape[0]

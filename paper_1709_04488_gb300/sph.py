@@ -19,7 +19,7 @@ EOS_ADIABATIC, EOS_ISOTHERMAL = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 KERNEL_M4, KERNEL_M6 = 0, 1
 AC_WADSLEY, AC_PRICE = 0, 1
-AV_CONSTANT, AV_MORRIS_MONAGHAN = 0, 1
+AV_CONSTANT, AV_MORRIS_MONAGHAN, AV_CULLEN_DEHNEN = 0, 1, 2
 FLAG_ASYNC, FLAG_TIMING = 1, 2
 NSTAGES = 8
 STAGES = ["kick_drift", "sort", "tree", "density", "refit", "forces", "gravity", "close"]

@@ -93,7 +93,10 @@ def run(prec_name, large):
         eo = energy({f: getattr(r, f) for f in ("vx", "vy", "vz", "u")}, r.m) / energy(r0, r.m) - 1.0
         de.append(abs(eg - eo))
     g = prob.numpy()
+    # (the step's forces act on the predicted velocities, which the state
+    # does not keep: the dE/dt balance is checked on single evaluations)
     rows["Sod 36864, after 5 steps"] = errors(g, r, {"vx": g["vx"], "vy": g["vy"], "vz": g["vz"]})
+    rows["Sod 36864, after 5 steps"].pop("dEdt_residual")
     rows["Sod 36864, after 5 steps"]["energy_change_per_step"] = float(max(de))
     prob.close()
     if large and prec == S.PREC_MIXED:

@@ -161,11 +161,11 @@ def test_launch_table_validation(S):
 
 
 def test_noalloc_limits_per_option_without_a_gpu(S):
-    """The allocation-free entry point rejects, before touching the device, a
-    problem whose layout does not fit its fixed scratch: n > 32768 with
-    SPH_EINVAL, and self-gravity problems above their smaller limits with
-    SPH_ENOSPACE naming the largest n that fits (checked one particle on
-    either side of the limit)."""
+    """The allocation-free entry point rejects, before touching the device,
+    n > 32768 with SPH_EINVAL; at n = 32768 every option's layout (either
+    precision, either kernel, either viscosity switch, self-gravity by
+    direct sum or tree walk) fits its fixed scratch, so the call passes the
+    size checks and stops at the NULL state arrays."""
     import ctypes as C
     st = S.State()  # NULL arrays: a call that passes the size checks stops at SPH_EINVAL
 
@@ -173,14 +173,21 @@ def test_noalloc_limits_per_option_without_a_gpu(S):
         p = S.make_params(prec, **kw)
         return S.lib().sph_density_forces_noalloc(C.byref(p), n, C.byref(st), None)
 
-    assert call(32769, S.PREC_MIXED) == S.EINVAL
-    assert call(32768, S.PREC_MIXED) == S.EINVAL and "NULL" in S.last_error()
-    assert call(32768, S.PREC_FP64) == S.EINVAL and "NULL" in S.last_error()
+    assert call(32769, S.PREC_MIXED) == S.EINVAL and "32768" in S.last_error()
     grav = dict(periodic=False, gravity=1, G=1.0)
-    for prec, kw, limit in [(S.PREC_MIXED, grav, 30240), (S.PREC_FP64, grav, 27840),
-                            (S.PREC_FP64, dict(grav, grav_theta=0.5), 24960)]:
-        assert call(32768, prec, **kw) == S.ENOSPACE
-        assert f"at most {limit} particles" in S.last_error()
-        assert call(limit + 1, prec, **kw) == S.ENOSPACE
-        assert call(limit, prec, **kw) == S.EINVAL and "NULL" in S.last_error()
-    assert call(32768, S.PREC_MIXED, **dict(grav, grav_theta=0.5)) == S.EINVAL
+    for prec in (S.PREC_MIXED, S.PREC_FP64):
+        for kw in (dict(), dict(kernel=S.KERNEL_M6, eta=1.0), dict(av_switch=2), grav, dict(grav, grav_theta=0.5)):
+            assert call(32768, prec, **kw) == S.EINVAL and "NULL" in S.last_error(), (prec, kw)
+
+
+def test_cullen_dehnen_switch_parameters(S):
+    """av_switch = 2 (Cullen & Dehnen) is accepted with alpha_av > 0 and
+    av_decay > 0, and refused with block time-steps or an unknown value."""
+    def ws(**kw):
+        return S.sph_workspace_bytes(4096, S.make_params(S.PREC_MIXED, **kw))
+    assert S.AV_CULLEN_DEHNEN == 2
+    assert ws(av_switch=2) > 0
+    assert ws(av_switch=2, av_decay=0.0) == 0
+    assert ws(av_switch=2, alpha_av=0.0) == 0
+    assert ws(av_switch=2, block_levels=3) == 0
+    assert ws(av_switch=3) == 0

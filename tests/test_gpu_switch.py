@@ -155,3 +155,80 @@ def test_switch_rejected_without_alpha_arrays_and_by_the_server(S):
     with pytest.raises(S.SPHError) as e:
         srv.submit(a, dict(p, **SW), nsteps=1, arrival=0.0)
     assert e.value.code == S.EINVAL
+
+
+# ---- the Cullen & Dehnen (2010) switch (av_switch = 2) ----------------------
+CD = dict(av_switch=2, av_decay=0.1)
+
+
+def _cd_inputs(seed=61, n_side=14):
+    """A cold jittered lattice with a compressive, sheared velocity field
+    plus noise (the compression steepens as the particles coast, so
+    d(div v)/dt < 0), alpha per particle, and the previous evaluation's div v
+    with both signs (it sets the signs in R)."""
+    a, p = ics.lattice(n_side, seed=seed)
+    p = dict(p, periodic=False)
+    rng = np.random.default_rng(seed)
+    x0 = {c: a[c] - 0.5 for c in ("x", "y", "z")}
+    a["vx"] = -0.8 * x0["x"] + 0.5 * x0["y"] + rng.normal(0.0, 0.05, len(a["x"]))
+    a["vy"] = -0.8 * x0["y"] + rng.normal(0.0, 0.05, len(a["x"]))
+    a["vz"] = 0.3 * x0["z"] + rng.normal(0.0, 0.05, len(a["x"]))
+    a["u"] = np.full(len(a["x"]), 1e-3)  # a cold gas: alpha_loc is not swamped by the sound speed
+    a["alpha"] = rng.uniform(0.02, 0.8, len(a["x"]))
+    a["dalpha"] = rng.normal(-0.5, 1.0, len(a["x"]))  # the previous div v
+    return a, p
+
+
+def _cd_oracle_state(O, a):
+    s = O.State(**{k: v for k, v in a.items() if k != "dalpha"})
+    s.cd_divv[:] = a["dalpha"]
+    return s
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_cullen_dehnen_evaluation_matches_oracle(S, oracle_mod, prec):
+    """One density/h solve and force evaluation: the accelerations and rates
+    with alpha_ij = (alpha_i + alpha_j)/2, and the new div v (written to
+    state.dalpha), against the oracle's (its cd_divv)."""
+    O = oracle_mod
+    a, p = _cd_inputs()
+    P = O.Params(**p, use_grid=True, **CD)
+    ref = _cd_oracle_state(O, a)
+    assert O.density(P, ref) == O.OK and O.forces(P, ref) == O.OK
+    fp64 = prec == "fp64"
+    g = _gpu(S, a, p, S.PREC_FP64 if fp64 else S.PREC_MIXED, **CD).numpy()
+    tol = 1e-12 if fp64 else 1e-4
+    ra = np.stack([ref.ax, ref.ay, ref.az], 1)
+    arms = np.sqrt(np.mean(np.sum(ra ** 2, 1)))
+    assert np.max(np.linalg.norm(_acc(g) - ra, axis=1)) < tol * arms
+    assert _rms_err(g["du"], ref.du) < tol
+    assert _rms_err(g["dalpha"], ref.cd_divv) < tol
+    # alpha is only read by an evaluation
+    assert np.array_equal(g["alpha"], a["alpha"])
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_cullen_dehnen_steps_match_oracle(S, oracle_mod, prec):
+    """Three KDK steps with the oracle's time-steps: alpha from the switch's
+    update (A = xi max(-dD/dt, 0), alpha_loc, decay), div v and the state
+    against the oracle; the limiter xi and the rise and decay branches are
+    all exercised by the mixed compression and shear."""
+    O = oracle_mod
+    a, p = _cd_inputs(seed=62)
+    P = O.Params(**p, use_grid=True, **CD)
+    ref = _cd_oracle_state(O, a)
+    assert O.density(P, ref) == O.OK and O.forces(P, ref) == O.OK
+    fp64 = prec == "fp64"
+    prob = _gpu(S, a, p, S.PREC_FP64 if fp64 else S.PREC_MIXED, **CD)
+    for _ in range(3):
+        dt = O.cfl_dt(P, ref)
+        assert O.step(P, ref, dt) == O.OK
+        prob.step(dt)
+    g = prob.numpy()
+    tol = 1e-10 if fp64 else 1e-4
+    assert np.max(np.abs(g["alpha"] - ref.alpha)) < tol * np.max(ref.alpha)
+    assert np.any(ref.alpha > a["alpha"]) and np.any(ref.alpha < a["alpha"])  # both branches taken
+    assert _rms_err(g["dalpha"], ref.cd_divv) < tol
+    ra = np.stack([ref.ax, ref.ay, ref.az], 1)
+    assert np.max(np.linalg.norm(_acc(g) - ra, axis=1)) < tol * np.sqrt(np.mean(np.sum(ra ** 2, 1)))
+    assert np.max(np.abs(g["rho"] / ref.rho - 1.0)) < (1e-10 if fp64 else 1e-5)

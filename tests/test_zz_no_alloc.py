@@ -107,8 +107,3 @@ def test_noalloc_rejects_too_many_particles(S):
     rc = S.sph_density_forces_noalloc(S.make_params(S.PREC_MIXED), n, st, 0)
     assert rc == S.EINVAL
     assert "32768" in S.last_error()
-    # self-gravity in FP64 leaves room for fewer particles: SPH_ENOSPACE
-    prm = S.make_params(S.PREC_FP64, periodic=False, gravity=1, G=1.0)
-    rc = S.sph_density_forces_noalloc(prm, 32768, st, 0)
-    assert rc == S.ENOSPACE
-    assert "at most 27840 particles" in S.last_error()
