@@ -504,16 +504,28 @@ __device__ __forceinline__ void stage_group(const BatchView &b, int A, unsigned 
     sc.dz[lane] = Dz;
     __syncwarp();
     const unsigned below = (1u << lane) - 1u;
+    // the particles are loaded one chunk of 32 ahead: a chunk's load (an L2
+    // round trip) overlaps the filtering, storing and flushing of the chunk
+    // before it (flush() leaves the scratch and the loaded arrays alone)
+    V qn{};
+    int kn = 0, idxn = 0;
+    if (lane < tot) {
+        kn = owner_of(sc, lane);
+        idxn = lane - sc.first[kn];
+        qn = load(sc.start[kn] + idxn);
+    }
     for (int e0 = 0; e0 < tot; e0 += 32) {
-        if (nbuf > CH - 32) flush();
         const int e = e0 + lane;
+        V q = qn;
+        const int k = kn, idx = idxn;
+        if (e + 32 < tot) {
+            kn = owner_of(sc, e + 32);
+            idxn = e + 32 - sc.first[kn];
+            qn = load(sc.start[kn] + idxn);
+        }
+        if (nbuf > CH - 32) flush();
         bool ok = false;
-        V q;
-        int k = 0, idx = 0;
         if (e < tot) {
-            k = owner_of(sc, e);
-            idx = e - sc.first[k];
-            q = load(sc.start[k] + idx);
             q.x += sc.dx[k];
             q.y += sc.dy[k];
             q.z += sc.dz[k];
