@@ -56,6 +56,7 @@ def sample_ics(name, n):
     return ics.sod()
 # algorithmic flops per in-range pair, counted from the kernels' source
 FLOPS_DENSITY_PAIR = 19   # per pair per Newton-Raphson pass (q, f, f', two accumulations)
+FLOPS_DENSITY_DIST = 9    # per in-range pair, once: the separation (3), r^2 (5), r (1)
 FLOPS_FORCE_PAIR = 101    # per ordered pair (pressure, viscosity, conduction, energy, TwoSum-compensated m a)
 FLOPS_GRAVITY_PAIR = 38   # per ordered pair beyond the softening (r, 1/r^3 weight, TwoSum-compensated F)
 FLOPS_GRAVITY_NODE = 49   # per (particle, node) multipole term (r, powers of 1/r, Q r, r.Q.r, the three sums)
@@ -301,6 +302,7 @@ def time_steps(S, prob, stream, torch, K, flush, stage=False):
     pair counters of each step."""
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     stages, dens_pairs, force_pairs = [], [], []
+    dist_pairs = []  # in-range (i, j) pairs of the density lists (each distance formed once)
     for k in range(K):
         with torch.cuda.stream(stream):
             flush.zero_()
@@ -313,8 +315,10 @@ def time_steps(S, prob, stream, torch, K, flush, stage=False):
             d = prob.diagnostics()
             dens_pairs.append(d.density_pairs)
             force_pairs.append(d.force_pairs)
+            dist_pairs.append(d.ngb_mean * prob.n)
     stream.synchronize()
     ms = [a.elapsed_time(b) for a, b in ev]
+    time_steps.dist_pairs = dist_pairs
     return ms, stages, dens_pairs, force_pairs
 
 
@@ -373,11 +377,12 @@ def batched_measurement(S, torch, dev, stream, flush, peak, nprob, steps=10):
     assert st == [S.OK] * len(probs), st
     ms = [a.elapsed_time(b) for a, b in ev]
     dp = sum(pr.diagnostics().density_pairs for pr in probs)
+    dd = sum(pr.diagnostics().ngb_mean * pr.n for pr in probs)
     fp = sum(pr.diagnostics().force_pairs for pr in probs)
     sm = np.mean(np.array(stages), axis=0)
     dens_ms, force_ms = float(sm[S.STAGES.index("density")]), float(sm[S.STAGES.index("forces")])
     pk = {"k_forces": {"ms": force_ms, "flop": float(fp * FLOPS_FORCE_PAIR)},
-          "k_density": {"ms": dens_ms, "flop": float(dp * FLOPS_DENSITY_PAIR)}}
+          "k_density": {"ms": dens_ms, "flop": float(dp * FLOPS_DENSITY_PAIR + dd * FLOPS_DENSITY_DIST)}}
     for rec in pk.values():
         rec["achieved"] = rec["flop"] / (rec["ms"] * 1e-3) / 1e12 if rec["ms"] > 0 else 0.0
         rec["frac"] = rec["achieved"] / peak
@@ -456,7 +461,8 @@ def run_ours(args):
     peak = peaks["fp32_tflops"]
     per_kernel = {
         "k_forces": {"ms": float(force_ms), "flop": float(np.mean(fp) * FLOPS_FORCE_PAIR)},
-        "k_density": {"ms": float(dens_ms), "flop": float(np.mean(dp) * FLOPS_DENSITY_PAIR)},
+        "k_density": {"ms": float(dens_ms), "flop": float(np.mean(dp) * FLOPS_DENSITY_PAIR +
+                                                          np.mean(time_steps.dist_pairs) * FLOPS_DENSITY_DIST)},
     }
     for rec in per_kernel.values():
         rec["achieved"] = rec["flop"] / (rec["ms"] * 1e-3) / 1e12 if rec["ms"] > 0 else 0.0

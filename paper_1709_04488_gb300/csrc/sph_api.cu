@@ -70,6 +70,7 @@ void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precis
     for (void **p : st) *p = c.take<char>(v4 * n);
     b.sal = c.take<char>(v4 / 4 * n);
     b.scd = c.take<char>(v4 / 4 * n);
+    b.divv = c.take<float>(n);
     b.cdold = c.take<double>(n);
     b.cdxi = c.take<double>(n);
     b.szg = c.take<char>(v4 / 4 * n);
@@ -1007,6 +1008,12 @@ static int batch_view(sph_ctx *const *ctxs, int nctx, void *workspace, size_t ws
     CU(cudaMemsetAsync(b.dyn, 0, sizeof(ProbDyn) * nctx, st));
     CU(cudaMemsetAsync(b.counters, 0, kNumCounters * sizeof(int), st));
     CU(cudaMemsetAsync(b.zero_lo, 0, b.zero_bytes, st));
+    // each problem's div v from its last force pass (the next step's h
+    // prediction) moves into the batch's layout
+    for (int k = 0; k < nctx; ++k)
+        if (ctxs[k]->n > 0)
+            CU(cudaMemcpyAsync(b.divv + bases[k], ctxs[k]->bv.divv, sizeof(float) * ctxs[k]->n,
+                               cudaMemcpyDeviceToDevice, st));
     // (copies from pageable host memory are staged before cudaMemcpyAsync
     // returns, so the local tables may go out of scope)
     return SPH_OK;
@@ -1014,10 +1021,17 @@ static int batch_view(sph_ctx *const *ctxs, int nctx, void *workspace, size_t ws
 
 // the contexts' own step bookkeeping after batched steps: their particles
 // were sorted in the batch's layout, so a later step of one context alone
-// must rebuild its leaves first
-static void after_batch_steps(sph_ctx *const *ctxs, int nctx)
+// must rebuild its leaves first; div v (the h prediction) goes back to each
+// context
+static void after_batch_steps(sph_ctx *const *ctxs, int nctx, const BatchView &b, cudaStream_t st)
 {
-    for (int k = 0; k < nctx; ++k) ctxs[k]->since_build = ctxs[k]->prm.tree_rebuild_every;
+    long long base = 0;
+    for (int k = 0; k < nctx; ++k) {
+        ctxs[k]->since_build = ctxs[k]->prm.tree_rebuild_every;
+        if (ctxs[k]->n > 0)
+            cudaMemcpyAsync(ctxs[k]->bv.divv, b.divv + base, sizeof(float) * ctxs[k]->n, cudaMemcpyDeviceToDevice, st);
+        base += ctxs[k]->n;
+    }
 }
 
 // each context's device status, and the first error among them
@@ -1046,7 +1060,7 @@ int sph_batch_step(sph_ctx *const *ctxs, int nctx, int nsteps, void *workspace, 
         rc = enqueue_step(b, prec, -1.0, st, Marks());
         if (rc) return rc;
     }
-    if (nsteps > 0) after_batch_steps(ctxs, nctx);
+    if (nsteps > 0) after_batch_steps(ctxs, nctx, b, st);
     CU(cudaStreamSynchronize(st));
     return batch_statuses(ctxs, nctx, nullptr);
 }
@@ -1155,7 +1169,7 @@ int sph_batch_run(sph_batch *bt, int nsteps)
         }
         CU(cudaGraphLaunch(bt->graph, bt->st));
     }
-    if (nsteps > 0) after_batch_steps(bt->ctxs.data(), (int)bt->ctxs.size());
+    if (nsteps > 0) after_batch_steps(bt->ctxs.data(), (int)bt->ctxs.size(), bt->b, bt->st);
     return SPH_OK;
 }
 

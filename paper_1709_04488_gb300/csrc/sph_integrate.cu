@@ -103,6 +103,12 @@ __global__ void k_kick_drift(BatchView b, double dt_host)
         X[k][i] = x;
         VP[k][g] = vh + hdt * a[k];
     }
+    // the h iteration starts from the continuity equation's prediction,
+    // h exp(div v dt / 3) (h ~ rho^-1/3), bounded to a factor 1.25
+    if (b.divv) {
+        const float e = (float)(dt * (1.0 / 3.0)) * b.divv[g];
+        ps.h[i] *= (double)expf(fminf(fmaxf(e, -0.223f), 0.223f));  // (a starting guess: FP32 is enough)
+    }
     double u = ps.u[i];
     if (ph.eos == SPH_EOS_ADIABATIC) {
         double uh = u + hdt * ps.du[i];

@@ -211,6 +211,7 @@ struct BatchView {
     void *th;   // (P/(Omega rho^2), rho, m, u)
     void *sal;  // alpha of the viscosity switch (T per particle)
     void *scd;  // Cullen & Dehnen: div v of the previous force evaluation (T per sorted particle)
+    float *divv;  // div v of the last force pass (original order, batch-global): the h prediction
     double *cdold, *cdxi;  // Cullen & Dehnen (original order, batch-global): div v before this
                            // evaluation and the limiter xi of this one, for the step's alpha update
     void *szg;  // gravity: G zeta / (2 Omega) (T per particle), the zeta term's weight

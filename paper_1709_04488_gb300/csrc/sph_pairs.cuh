@@ -1448,8 +1448,8 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
             if (sw) {
                 al = mul_rn(T(0.5), add_rn(alpha_i, sal[j]));
                 be = mul_rn(bratio, al);
-                dvs += a2.z * vdr * gi;
             }
+            dvs += a2.z * vdr * gi;  // (div v: the switch's source, and the next step's h prediction)
             if (cdw) {
                 const T mg = a2.z * gi * rinv;
                 cg[0] += mg * vx * rx;
@@ -1583,7 +1583,7 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
     Fz = group_sum<LPP>(Fz);
     du = group_sum<LPP>(du);
     vs = group_max<LPP>(vs);
-    if (sw) dvs = group_sum<LPP>(dvs);
+    dvs = group_sum<LPP>(dvs);
     if (cdw) {
 #pragma unroll
         for (int k = 0; k < 9; ++k) cg[k] = group_sum<LPP>(cg[k]);
@@ -1607,6 +1607,10 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
         ps.az[i] = a[2];
         ps.du[i] = adi ? (double)du : 0.0;
         ps.vsig[i] = (double)vsig_t;
+        // div v = -(1/(Omega rho)) sum_j m_j v_ij . grad_i W(h_i): the next
+        // step starts its h iteration from h exp(div v dt / 3) (continuity,
+        // with h ~ rho^-1/3)
+        b.divv[g] = (float)(-(double)dvs / (b.somega[s] * b.srho[s]));
         if (sw && !cdw) {  // Morris & Monaghan: decay towards alpha_min, growth where compressed
             const double divv = -(double)dvs / (b.somega[s] * b.srho[s]);
             const double ai = (double)alpha_i;
