@@ -105,7 +105,7 @@ void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precis
     b.leaf_ngroups = c.take<int>(ml);
     b.leaf_hcap = c.take<float>(ml);
     b.counters = c.take<int>(kNumCounters);
-    b.scratch64 = c.take<long long>(8);
+    b.scratch64 = c.take<long long>(16);
     // zero region (kept zero by the kernels that use it)
     b.tile_state = c.take<unsigned>(leaf_tiles(n) + 2);
     b.zero_lo = (char *)b.tile_state;
@@ -194,6 +194,7 @@ struct sph_ctx {
     int since_build;              // steps since the leaves were last built
     cudaGraphExec_t graph;        // one step that rebuilds the leaves
     cudaGraphExec_t graph_reuse;  // one step that keeps them
+    cudaGraphExec_t block_graph;  // one block step, its ticks a device-driven loop
     int graph_kernels;
     cudaEvent_t ev[SPH_NSTAGES + 1];
     bool timing;
@@ -309,6 +310,7 @@ int status_to_code(unsigned st)
     if (st & ST_BOX) return fail(SPH_EBOX, "kernel support (R_K h) reached half the periodic box");
     if (st & ST_TIMEOUT) return fail(SPH_ETIMEOUT, "a bounded device wait gave up");
     if (st & ST_OVERFLOW) return fail(SPH_ENOSPACE, "an internal capacity was exceeded");
+    if (st & ST_SCHEDULE) return fail(SPH_ECUDA, "block step: the next event tick does not follow the current one");
     if (st & ST_NOCONV) return fail(SPH_ENOCONV, "h-rho iteration did not converge for some particles");
     return SPH_OK;
 }
@@ -413,6 +415,7 @@ int sph_setup(sph_ctx **out, const sph_params *p, int64_t n, const sph_state *st
     c->since_build = 0;
     c->graph = nullptr;
     c->graph_reuse = nullptr;
+    c->block_graph = nullptr;
     c->graph_kernels = 0;
     c->timing = (p->flags & SPH_FLAG_TIMING) != 0;
     for (int k = 0; k <= SPH_NSTAGES; ++k) c->ev[k] = nullptr;
@@ -607,6 +610,215 @@ static int finish_call(sph_ctx *c)
     return sph_sync(c);
 }
 
+// ---- block time-steps (Sec. 2.1.4) -----------------------------------------
+// One block step: Delta t_MAX and the opening kicks, then one tick per event
+// (a tick where some particle's step ends), then the conservation sums.  The
+// schedule lives on the device; on a capturable stream the ticks are the body
+// of a graph loop (a conditional while node) whose condition the last kernel
+// of each tick sets, so no host round trip separates them.
+
+static BatchView block_view(const sph_ctx *c)
+{
+    BatchView b = c->bv;
+    b.block_on = 1;
+    b.any_general = 1;  // the active particles' forces run in the wrap-list launch
+    return b;
+}
+
+static int block_every(const sph_ctx *c) { return c->prm.tree_rebuild_every > 1 ? c->prm.tree_rebuild_every : 1; }
+
+// tree reuse between ticks as between global steps: sort and build on every
+// tree_rebuild_every-th tick, refit the kept leaves between
+static int enqueue_block_leaves(const BatchView &b, int prec, bool rebuild, cudaStream_t st)
+{
+    if (rebuild) {
+        CU(launch_domain_and_keys(b, st));
+        CU(launch_radix_sort(b, st));
+    }
+    CU(launch_gather(b, st));
+    CU(launch_block_stage(b, prec, st));  // which sorted particles end their step now
+    if (rebuild) CU(launch_build_leaves(b, prec, st));
+    else CU(launch_update_leaves(b, prec, st));
+    return SPH_OK;
+}
+
+static int enqueue_block_passes(const BatchView &b, int prec, int L, bool use_cond, cudaGraphConditionalHandle loop,
+                                cudaStream_t st)
+{
+    CU(launch_density(b, prec, 1, st));  // solves the active particles, restages the others
+    CU(launch_refit(b, prec, st));
+    CU(launch_forces(b, prec, st));
+    launch_gravity(b, prec, st);  // the long range of the active particles
+    CU(cudaGetLastError());
+    CU(launch_block_kick(b, L, st));
+    CU(launch_block_tick_end(b, L, use_cond, loop, st));
+    return SPH_OK;
+}
+
+// the legacy default stream: the host reads the loop flag after every tick
+static int block_step_eager(sph_ctx *c, const BatchView &b)
+{
+    const int L = c->prm.block_levels, prec = c->prm.precision, every = block_every(c);
+    cudaStream_t st = c->stream;
+    CU(launch_block_dt(b, L, st));
+    CU(launch_block_open(b, L, st));
+    CU(launch_block_gate(b, L, false, 0, st));
+    for (int tick = 0;; ++tick) {
+        long long go = 0;
+        CU(cudaMemcpyAsync(&go, b.scratch64 + 9, sizeof go, cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        if (!go) break;
+        CU(launch_block_tick_begin(b, every, false, 0, st));
+        CU(launch_reset_step(b, 1, st));
+        CU(launch_block_drift(b, st));
+        int rc = enqueue_block_leaves(b, prec, tick % every == 0, st);
+        if (rc) return rc;
+        rc = enqueue_block_passes(b, prec, L, false, 0, st);
+        if (rc) return rc;
+    }
+    CU(launch_kick_close(b, 0, 1, st));  // conservation sums of the synchronised state
+    CU(launch_block_finish(b, st));
+    return SPH_OK;
+}
+
+// adds a conditional node of `type` after the capture's current dependencies
+// and makes it the stream's only dependency; returns its body graphs
+static int add_conditional(cudaStream_t s, cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                           unsigned size, cudaGraph_t **bodies)
+{
+    cudaStreamCaptureStatus cs;
+    unsigned long long id = 0;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    CU(cudaStreamGetCaptureInfo(s, &cs, &id, &g, &deps, nullptr, &nd));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = type;
+    np.conditional.size = size;
+    cudaGraphNode_t node = nullptr;
+    CU(cudaGraphAddNode(&node, g, deps, nullptr, nd, &np));
+    CU(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    *bodies = np.conditional.phGraph_out;
+    return SPH_OK;
+}
+
+static int capture_graph(cudaStream_t s, cudaGraph_t *g_out)
+{
+    cudaStreamCaptureStatus cs;
+    unsigned long long id = 0;
+    CU(cudaStreamGetCaptureInfo(s, &cs, &id, g_out, nullptr, nullptr, nullptr));
+    return SPH_OK;
+}
+
+// ends a capture into a conditional body (the graph stays its node's)
+static int end_body_capture(cudaStream_t s, int rc)
+{
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (rc) return rc;
+    CU(e);
+    return SPH_OK;
+}
+
+// one tick into the loop body (stream s2; s3 captures the branches)
+static int capture_tick(const sph_ctx *c, const BatchView &b, cudaGraphConditionalHandle loop, cudaStream_t s2,
+                        cudaStream_t s3)
+{
+    const int L = c->prm.block_levels, prec = c->prm.precision, every = block_every(c);
+    cudaGraphConditionalHandle rb = 0;
+    if (every > 1) {
+        cudaGraph_t body = nullptr;
+        int rc = capture_graph(s2, &body);
+        if (rc) return rc;
+        CU(cudaGraphConditionalHandleCreate(&rb, body, 0, 0));
+    }
+    CU(launch_block_tick_begin(b, every, every > 1, rb, s2));
+    CU(launch_reset_step(b, 1, s2));
+    CU(launch_block_drift(b, s2));
+    if (every > 1) {
+        cudaGraph_t *br = nullptr;
+        int rc = add_conditional(s2, rb, cudaGraphCondTypeIf, 2, &br);  // [0] rebuild, [1] keep the leaves
+        if (rc) return rc;
+        for (int k = 0; k < 2; ++k) {
+            CU(cudaStreamBeginCaptureToGraph(s3, br[k], nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+            rc = end_body_capture(s3, enqueue_block_leaves(b, prec, k == 0, s3));
+            if (rc) return rc;
+        }
+    } else {
+        int rc = enqueue_block_leaves(b, prec, true, s2);
+        if (rc) return rc;
+    }
+    return enqueue_block_passes(b, prec, L, true, loop, s2);
+}
+
+static int capture_block(const sph_ctx *c, const BatchView &b, cudaStream_t s2, cudaStream_t s3)
+{
+    const int L = c->prm.block_levels;
+    cudaStream_t st = c->stream;
+    cudaGraph_t g = nullptr;
+    int rc = capture_graph(st, &g);
+    if (rc) return rc;
+    cudaGraphConditionalHandle loop = 0;
+    CU(cudaGraphConditionalHandleCreate(&loop, g, 0, cudaGraphCondAssignDefault));
+    CU(launch_block_dt(b, L, st));
+    CU(launch_block_open(b, L, st));
+    CU(launch_block_gate(b, L, true, loop, st));
+    cudaGraph_t *body = nullptr;
+    rc = add_conditional(st, loop, cudaGraphCondTypeWhile, 1, &body);
+    if (rc) return rc;
+    CU(cudaStreamBeginCaptureToGraph(s2, body[0], nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    rc = end_body_capture(s2, capture_tick(c, b, loop, s2, s3));
+    if (rc) return rc;
+    CU(launch_kick_close(b, 0, 1, st));  // conservation sums of the synchronised state
+    CU(launch_block_finish(b, st));
+    return SPH_OK;
+}
+
+static int build_block_graph(sph_ctx *c, const BatchView &b)
+{
+    cudaStream_t s2 = nullptr, s3 = nullptr;
+    CU(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+    cudaError_t e = cudaStreamCreateWithFlags(&s3, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaStreamDestroy(s2);
+        return fail(SPH_ECUDA, "stream creation failed: %s", cudaGetErrorString(e));
+    }
+    int rc = SPH_OK;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        rc = capture_block(c, b, s2, s3);
+        for (cudaStream_t s : {s3, s2}) {  // a capture left open by a failure
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+                cudaGraph_t gb = nullptr;
+                cudaStreamEndCapture(s, &gb);
+            }
+        }
+        e = cudaStreamEndCapture(c->stream, &g);
+    }
+    cudaStreamDestroy(s2);
+    cudaStreamDestroy(s3);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return rc;
+    }
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return fail(SPH_ECUDA, "block-step graph capture failed: %s", cudaGetErrorString(e));
+    }
+    e = cudaGraphInstantiate(&c->block_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        c->block_graph = nullptr;
+        return fail(SPH_ECUDA, "block-step graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+    return SPH_OK;
+}
+
 extern "C" {
 
 int sph_sync(sph_ctx *c)
@@ -626,65 +838,28 @@ int sph_block_step(sph_ctx *c, double *dtmax_out, int64_t *evals_out)
     if (!c->have_forces) return fail(SPH_EINVAL, "sph_block_step needs a force evaluation first");
     if (c->n == 0) return SPH_OK;
     clear_ran(c);
-    BatchView b = c->bv;
-    b.block_on = 1;
-    b.any_general = 1;  // the active particles' forces run in the wrap-list launch
-    const int prec = c->prm.precision;
+    const BatchView b = block_view(c);
     cudaStream_t st = c->stream;
-    const long long N = 1LL << L;
-    // Delta t_MAX: the largest step, or 2^L times the smallest if that is less
-    CU(launch_block_dt(b, st));
-    unsigned long long bits[2];
-    CU(cudaMemcpyAsync(bits, b.scratch64, sizeof bits, cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-    double dmin, dmax;
-    memcpy(&dmin, &bits[0], sizeof dmin);
-    memcpy(&dmax, &bits[1], sizeof dmax);
-    if (!(dmin > 0) || !(dmin < INFINITY)) return fail(SPH_ENONFINITE, "no finite positive time-step");
-    const double dtmax = dmax < ldexp(dmin, L) ? dmax : ldexp(dmin, L);
-    const double tau = ldexp(dtmax, -L);
-    CU(launch_block_open(b, dtmax, tau, L, st));
-    long long k = 0, next = 0;
-    CU(cudaMemcpyAsync(&next, b.scratch64 + 2, sizeof next, cudaMemcpyDeviceToHost, st));
-    CU(cudaStreamSynchronize(st));
-    // tree reuse (Sec. 4.2) between ticks as between global steps: sort and
-    // build on every tree_rebuild_every-th tick, refit the kept leaves between
-    const int every = c->prm.tree_rebuild_every > 1 ? c->prm.tree_rebuild_every : 1;
-    for (int tick = 0; k < N; ++tick) {
-        if (next <= k || next > N) return fail(SPH_ECUDA, "block step: bad next tick %lld after %lld", next, k);
-        const bool rebuild = tick % every == 0;
-        CU(launch_reset_step(b, 1, st));
-        CU(launch_block_drift(b, k, next, tau, st));
-        if (rebuild) {
-            CU(launch_domain_and_keys(b, st));
-            CU(launch_radix_sort(b, st));
+    if (st == nullptr) {
+        int rc = block_step_eager(c, b);  // the legacy default stream cannot be captured
+        if (rc) return rc;
+    } else {
+        if (!c->block_graph) {
+            int rc = build_block_graph(c, b);
+            if (rc) return rc;
         }
-        CU(launch_gather(b, st));
-        CU(launch_block_stage(b, prec, next, st));  // which sorted particles end their step now
-        if (rebuild) CU(launch_build_leaves(b, prec, st));
-        else CU(launch_update_leaves(b, prec, st));
-        CU(launch_density(b, prec, 1, st));  // solves the active particles, restages the others
-        CU(launch_refit(b, prec, st));
-        CU(launch_forces(b, prec, st));
-        launch_gravity(b, prec, st);  // the long range of the active particles
-        CU(cudaGetLastError());
-        CU(launch_block_kick(b, next, dtmax, tau, L, st));
-        k = next;
-        unsigned status = 0;
-        CU(cudaMemcpyAsync(&next, b.scratch64 + 2, sizeof next, cudaMemcpyDeviceToHost, st));
-        CU(cudaMemcpyAsync(&status, &c->diag->status, sizeof status, cudaMemcpyDeviceToHost, st));
-        CU(cudaStreamSynchronize(st));
-        if (status) return status_to_code(status);
+        CU(cudaGraphLaunch(c->block_graph, st));
     }
-    CU(launch_kick_close(b, 0, 1, st));  // conservation sums of the synchronised state
-    CU(launch_block_finish(b, dtmax, st));
-    long long evals = 0;
+    long long evals = 0, dbits = 0;
     CU(cudaMemcpyAsync(&evals, b.scratch64 + 3, sizeof evals, cudaMemcpyDeviceToHost, st));
+    CU(cudaMemcpyAsync(&dbits, b.scratch64 + 6, sizeof dbits, cudaMemcpyDeviceToHost, st));
     int rc = sph_sync(c);
+    double dtmax;
+    memcpy(&dtmax, &dbits, sizeof dtmax);
     if (dtmax_out) *dtmax_out = dtmax;
     if (evals_out) *evals_out = evals;
     c->have_forces = true;
-    c->since_build = every;  // the next global step rebuilds
+    c->since_build = c->prm.tree_rebuild_every > 1 ? c->prm.tree_rebuild_every : 1;  // the next global step rebuilds
     return rc;
 }
 
@@ -908,6 +1083,7 @@ int sph_destroy(sph_ctx *c)
     if (!c) return SPH_OK;
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->graph_reuse) cudaGraphExecDestroy(c->graph_reuse);
+    if (c->block_graph) cudaGraphExecDestroy(c->block_graph);
     for (int k = 0; k <= SPH_NSTAGES; ++k)
         if (c->ev[k]) cudaEventDestroy(c->ev[k]);
     delete c;

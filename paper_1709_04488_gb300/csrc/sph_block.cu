@@ -16,6 +16,11 @@
 //
 // The kick, drift and prediction arithmetic is written with explicit
 // rounding, operation for operation as the reference formulas state it.
+//
+// The schedule lives on the device (Delta t_MAX, the tick length, the current
+// and next event ticks), so the host can enqueue the ticks as the body of a
+// graph loop whose condition the last kernel of each tick sets: no host round
+// trip between ticks.
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -62,12 +67,17 @@ __device__ __forceinline__ double half_ticks(long long ticks, double tau)
     return __dmul_rn(__dmul_rn(0.5, (double)ticks), tau);
 }
 
+__device__ __forceinline__ double bits_d(long long v) { return __longlong_as_double(v); }
+
 __global__ void k_block_init(BatchView b)
 {
     b.scratch64[0] = (long long)dbits(INFINITY);  // smallest step
     b.scratch64[1] = 0;                           // largest step
     b.scratch64[2] = 0x7fffffffffffffffLL;        // next tick where a step ends
     b.scratch64[3] = 0;                           // particle force evaluations
+    b.scratch64[4] = 0;                           // the block starts at tick 0
+    b.scratch64[8] = 0;                           // ticks taken
+    b.scratch64[9] = 0;
 }
 
 __global__ void __launch_bounds__(kBlockThreads) k_block_dt(BatchView b)
@@ -86,6 +96,23 @@ __global__ void __launch_bounds__(kBlockThreads) k_block_dt(BatchView b)
     }
 }
 
+// Delta t_MAX: the largest step, or 2^L times the smallest if that is less;
+// no finite positive step leaves Delta t_MAX = 0 and a non-finite status
+__global__ void k_block_plan(BatchView b, int L)
+{
+    const double dmin = bits_d(b.scratch64[0]), dmax = bits_d(b.scratch64[1]);
+    double dtmax = 0.0, tau = 0.0;
+    if (dmin > 0 && dmin < INFINITY) {
+        const double cap = ldexp(dmin, L);
+        dtmax = dmax < cap ? dmax : cap;
+        tau = ldexp(dtmax, -L);
+    } else {
+        atomicOr(&b.prob[0].diag->status, ST_NONFINITE);
+    }
+    b.scratch64[6] = __double_as_longlong(dtmax);
+    b.scratch64[7] = __double_as_longlong(tau);
+}
+
 __device__ __forceinline__ void next_event(const BatchView &b, long long t)
 {
     const long long m = warp_min(t);
@@ -94,11 +121,12 @@ __device__ __forceinline__ void next_event(const BatchView &b, long long t)
 
 // each particle's opening step: level from its CFL step, raised to within
 // block_gap of its neighbours' largest level, and the opening half kick
-__global__ void __launch_bounds__(kBlockThreads) k_block_open(BatchView b, double dtmax, double tau, int L)
+__global__ void __launch_bounds__(kBlockThreads) k_block_open(BatchView b, int L)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const double dtmax = bits_d(b.scratch64[6]), tau = bits_d(b.scratch64[7]);
     long long t1 = 0x7fffffffffffffffLL;
-    if (g < b.ntot) {
+    if (g < b.ntot && dtmax > 0) {
         const ProbStatic &ps = b.prob[0];
         const long long i = g - ps.base;
         int l = level_of(particle_dt(ps, i), dtmax, L);
@@ -119,11 +147,53 @@ __global__ void __launch_bounds__(kBlockThreads) k_block_open(BatchView b, doubl
     next_event(b, t1);
 }
 
+// the loop's gate before the first tick: the first event tick must lie in
+// (0, 2^L] and nothing may have failed
+__global__ void k_block_gate(BatchView b, int L, int use_cond, cudaGraphConditionalHandle cond)
+{
+    ProbDiag *d = b.prob[0].diag;
+    const long long N = 1LL << L, next = b.scratch64[2];
+    bool go = d->status == 0;
+    if (go && !(next > 0 && next <= N)) {
+        atomicOr(&d->status, ST_SCHEDULE);
+        go = false;
+    }
+    b.scratch64[9] = go ? 1 : 0;
+    if (use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
+}
+
+// a tick starts: it advances to the next event tick; with tree reuse, the
+// branch condition says whether this tick sorts and builds the leaves
+__global__ void k_block_tick_begin(BatchView b, int every, int use_cond, cudaGraphConditionalHandle cond)
+{
+    b.scratch64[5] = b.scratch64[2];
+    if (use_cond) cudaGraphSetConditional(cond, b.scratch64[8] % every == 0 ? 1u : 0u);
+}
+
+// a tick ends: the next one follows unless the block is complete or a
+// status is set; the next event tick must lie after this one
+__global__ void k_block_tick_end(BatchView b, int L, int use_cond, cudaGraphConditionalHandle cond)
+{
+    ProbDiag *d = b.prob[0].diag;
+    const long long N = 1LL << L, k1 = b.scratch64[5], next = b.scratch64[2];
+    b.scratch64[4] = k1;
+    b.scratch64[8] += 1;
+    bool go = d->status == 0 && k1 < N;
+    if (go && !(next > k1 && next <= N)) {
+        atomicOr(&d->status, ST_SCHEDULE);
+        go = false;
+    }
+    b.scratch64[9] = go ? 1 : 0;
+    if (use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
+}
+
 // drift every particle from tick k0 to tick k1, mark the particles whose
 // step ends at k1, predict v, u and alpha at k1 for the force pass
-__global__ void __launch_bounds__(kBlockThreads) k_block_drift(BatchView b, long long k0, long long k1, double tau)
+__global__ void __launch_bounds__(kBlockThreads) k_block_drift(BatchView b)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long k0 = b.scratch64[4], k1 = b.scratch64[5];
+    const double tau = bits_d(b.scratch64[7]);
     bool due = false;
     if (g < b.ntot) {
         const ProbStatic &ps = b.prob[0];
@@ -158,10 +228,11 @@ __global__ void __launch_bounds__(kBlockThreads) k_block_drift(BatchView b, long
 // sorted staging of the levels for the force pass: +(level + 1) where the
 // step ends at tick k, -(level + 1) elsewhere
 template <typename T>
-__global__ void __launch_bounds__(kBlockThreads) k_block_stage(BatchView b, long long k)
+__global__ void __launch_bounds__(kBlockThreads) k_block_stage(BatchView b)
 {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= b.ntot) return;
+    const long long k = b.scratch64[5];
     const int g = b.perm[s];
     const T v = (T)(b.blev[g] + 1);
     ((T *)b.slev)[s] = b.bt1[g] == k ? v : -v;
@@ -171,9 +242,11 @@ __global__ void __launch_bounds__(kBlockThreads) k_block_stage(BatchView b, long
 // and, before the end of the block, the level and opening half kick of their
 // next step; inactive particles lifted by the reactive limiter end their
 // step at the next tick of their new level's grid
-__global__ void __launch_bounds__(kBlockThreads) k_block_kick(BatchView b, long long k, double dtmax, double tau, int L)
+__global__ void __launch_bounds__(kBlockThreads) k_block_kick(BatchView b, int L)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long k = b.scratch64[5];
+    const double dtmax = bits_d(b.scratch64[6]), tau = bits_d(b.scratch64[7]);
     long long tnext = 0x7fffffffffffffffLL;
     if (g < b.ntot) {
         const ProbStatic &ps = b.prob[0];
@@ -227,10 +300,11 @@ __global__ void __launch_bounds__(kBlockThreads) k_block_kick(BatchView b, long 
 
 __global__ void k_block_next_reset(BatchView b) { b.scratch64[2] = 0x7fffffffffffffffLL; }
 
-__global__ void k_block_finish(BatchView b, double dtmax)
+__global__ void k_block_finish(BatchView b)
 {
     ProbDiag *d = b.prob[0].diag;
-    d->time += dtmax;
+    if (d->status) return;  // a failed block leaves the clock where it was
+    d->time += bits_d(b.scratch64[6]);
     d->steps += 1;
 }
 
@@ -238,42 +312,64 @@ inline unsigned blocks_for(long long n) { return (unsigned)((n + kBlockThreads -
 
 }  // namespace
 
-cudaError_t launch_block_dt(const BatchView &b, cudaStream_t st)
+cudaError_t launch_block_dt(const BatchView &b, int L, cudaStream_t st)
 {
     k_block_init<<<1, 1, 0, st>>>(b);
     k_block_dt<<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b);
+    k_block_plan<<<1, 1, 0, st>>>(b, L);
     return cudaGetLastError();
 }
 
-cudaError_t launch_block_open(const BatchView &b, double dtmax, double tau, int L, cudaStream_t st)
+cudaError_t launch_block_open(const BatchView &b, int L, cudaStream_t st)
 {
-    k_block_open<<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b, dtmax, tau, L);
+    k_block_open<<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b, L);
     return cudaGetLastError();
 }
 
-cudaError_t launch_block_drift(const BatchView &b, long long k0, long long k1, double tau, cudaStream_t st)
+cudaError_t launch_block_gate(const BatchView &b, int L, bool use_cond, cudaGraphConditionalHandle cond,
+                              cudaStream_t st)
 {
-    k_block_drift<<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b, k0, k1, tau);
+    k_block_gate<<<1, 1, 0, st>>>(b, L, use_cond ? 1 : 0, cond);
     return cudaGetLastError();
 }
 
-cudaError_t launch_block_stage(const BatchView &b, int precision, long long k, cudaStream_t st)
+cudaError_t launch_block_tick_begin(const BatchView &b, int every, bool use_cond, cudaGraphConditionalHandle cond,
+                                    cudaStream_t st)
 {
-    if (precision == SPH_PREC_FP64) k_block_stage<double><<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b, k);
-    else k_block_stage<float><<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b, k);
+    k_block_tick_begin<<<1, 1, 0, st>>>(b, every > 1 ? every : 1, use_cond ? 1 : 0, cond);
     return cudaGetLastError();
 }
 
-cudaError_t launch_block_kick(const BatchView &b, long long k, double dtmax, double tau, int L, cudaStream_t st)
+cudaError_t launch_block_drift(const BatchView &b, cudaStream_t st)
+{
+    k_block_drift<<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_stage(const BatchView &b, int precision, cudaStream_t st)
+{
+    if (precision == SPH_PREC_FP64) k_block_stage<double><<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b);
+    else k_block_stage<float><<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_kick(const BatchView &b, int L, cudaStream_t st)
 {
     k_block_next_reset<<<1, 1, 0, st>>>(b);  // the next event is a fresh minimum over the updated steps
-    k_block_kick<<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b, k, dtmax, tau, L);
+    k_block_kick<<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b, L);
     return cudaGetLastError();
 }
 
-cudaError_t launch_block_finish(const BatchView &b, double dtmax, cudaStream_t st)
+cudaError_t launch_block_tick_end(const BatchView &b, int L, bool use_cond, cudaGraphConditionalHandle cond,
+                                  cudaStream_t st)
 {
-    k_block_finish<<<1, 1, 0, st>>>(b, dtmax);
+    k_block_tick_end<<<1, 1, 0, st>>>(b, L, use_cond ? 1 : 0, cond);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_finish(const BatchView &b, cudaStream_t st)
+{
+    k_block_finish<<<1, 1, 0, st>>>(b);
     return cudaGetLastError();
 }
 

@@ -47,6 +47,7 @@ enum : unsigned {
     ST_NONFINITE = 4u,
     ST_TIMEOUT = 8u,
     ST_OVERFLOW = 16u,  // internal capacity exceeded (e.g. neighbour export)
+    ST_SCHEDULE = 32u,  // block step: the next event tick is not after the current one
 };
 
 // Physics parameters of one problem as the kernels read them.
@@ -239,7 +240,7 @@ struct BatchView {
     int *leaf_ngroups;           // [max_leaves] group count, -1: not recorded (walk)
     float *leaf_hcap;            // [max_leaves] largest h the recorded groups cover
     int *counters;               // [kNumCounters], slots as listed at kSlowCounter
-    long long *scratch64;        // [8]
+    long long *scratch64;        // [16]
 };
 
 // ---------------------------------------------------------------------------
@@ -331,14 +332,25 @@ void launch_gravity(const BatchView &b, int precision, cudaStream_t st);  // dir
 long long gravity_blocks(long long n, double theta);  // blocks (particle blocks x partner ranges)
 int gravity_chunks(long long n, double theta);        // partner ranges
 cudaError_t launch_kick_drift(const BatchView &b, double dt_host, cudaStream_t st);  // also selects dt, resets diagnostics
-// block time-steps (sph_block.cu); scratch64: [0] smallest and [1] largest
-// step (ordered bits), [2] next tick where a step ends, [3] force evaluations
-cudaError_t launch_block_dt(const BatchView &b, cudaStream_t st);
-cudaError_t launch_block_open(const BatchView &b, double dtmax, double tau, int L, cudaStream_t st);
-cudaError_t launch_block_drift(const BatchView &b, long long k0, long long k1, double tau, cudaStream_t st);
-cudaError_t launch_block_stage(const BatchView &b, int precision, long long k, cudaStream_t st);
-cudaError_t launch_block_kick(const BatchView &b, long long k, double dtmax, double tau, int L, cudaStream_t st);
-cudaError_t launch_block_finish(const BatchView &b, double dtmax, cudaStream_t st);
+// block time-steps (sph_block.cu).  Every quantity a tick needs lives on the
+// device, so that the ticks can run as a loop of a captured graph; scratch64:
+// [0] smallest and [1] largest step (ordered bits), [2] next tick where a
+// step ends, [3] force evaluations, [4] the current tick k0, [5] the tick k1
+// being advanced to, [6] Delta t_MAX and [7] the tick length (bits), [8]
+// ticks taken, [9] 1 while another tick follows.  `cond` is the graph's loop
+// (or branch) condition handle, set only when `use_cond` is true.
+cudaError_t launch_block_dt(const BatchView &b, int L, cudaStream_t st);  // also plans Delta t_MAX
+cudaError_t launch_block_open(const BatchView &b, int L, cudaStream_t st);
+cudaError_t launch_block_gate(const BatchView &b, int L, bool use_cond, cudaGraphConditionalHandle cond,
+                              cudaStream_t st);
+cudaError_t launch_block_tick_begin(const BatchView &b, int every, bool use_cond, cudaGraphConditionalHandle cond,
+                                    cudaStream_t st);
+cudaError_t launch_block_drift(const BatchView &b, cudaStream_t st);
+cudaError_t launch_block_stage(const BatchView &b, int precision, cudaStream_t st);
+cudaError_t launch_block_kick(const BatchView &b, int L, cudaStream_t st);
+cudaError_t launch_block_tick_end(const BatchView &b, int L, bool use_cond, cudaGraphConditionalHandle cond,
+                                  cudaStream_t st);
+cudaError_t launch_block_finish(const BatchView &b, cudaStream_t st);
 cudaError_t launch_kick_close(const BatchView &b, int do_kick, int forces_ran, cudaStream_t st);
 cudaError_t launch_reset_step(const BatchView &b, int mode, cudaStream_t st);  // mode 1 full, 2 forces only
 cudaError_t launch_neighbour_export(const BatchView &b, int kind, const double *h_in, long long *offsets,

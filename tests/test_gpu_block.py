@@ -134,6 +134,65 @@ def test_gravity_block_step_matches_oracle(S, oracle_mod, prec):
         assert np.max(np.abs(g[f] - getattr(ref, f))) < (1e-10 if fp64 else 1e-6), f
 
 
+def _stepped(S, a, p, stream, blocks, **kw):
+    prob = S.Problem(a, S.make_params(S.PREC_MIXED, **p, **kw), stream=stream)
+    prob.density_h()
+    prob.forces()
+    out = [prob.block_step() for _ in range(blocks)]
+    g = prob.numpy()
+    g["levels"] = prob.levels()
+    d = prob.diagnostics()
+    prob.close()
+    return out, g, d
+
+
+@pytest.mark.parametrize("case", ["sedov", "sedov_reuse", "gravity"])
+def test_graph_loop_equals_host_driven_ticks(S, case):
+    """On a capturable stream the ticks of a block step run as the loop of
+    one captured graph (a conditional while node; with tree reuse a
+    conditional branch picks rebuild or refit), with no host round trip
+    between them; on the legacy default stream the host reads the loop flag
+    after every tick.  Both enqueue the same kernels in the same order, so
+    two consecutive blocks (the second replays the graph) agree bit for
+    bit: levels, evaluations, Delta t_MAX and the whole state."""
+    import torch
+    if case == "gravity":
+        a, p = _gravity_block_case(2000, seed=95)
+        kw = dict(block_levels=4)
+    else:
+        a, p = ics.sedov(14, seed=5)
+        kw = dict(block_levels=5, tree_rebuild_every=3 if case == "sedov_reuse" else 1)
+    host, gh, dh = _stepped(S, a, p, None, 2, **kw)
+    graph, gg, dg = _stepped(S, a, p, torch.cuda.Stream(), 2, **kw)
+    assert host == graph
+    assert host[0][1] < len(a["x"]) * 2 ** kw["block_levels"]  # fewer evaluations than global steps
+    assert dh.steps == dg.steps and dh.time == dg.time and dh.status == dg.status == S.OK
+    for f in gh:
+        assert np.array_equal(gh[f], gg[f]), f
+
+
+def test_graph_loop_reports_a_failed_block(S):
+    """A block that cannot start (four isolated particles: no finite
+    positive time-step) ends on the device in both forms: the same error,
+    and the clock does not advance."""
+    import torch
+    rng = np.random.default_rng(0)
+    bad = {k: rng.uniform(0, 1, 4) for k in ("x", "y", "z")}
+    bad.update(vx=np.zeros(4), vy=np.zeros(4), vz=np.zeros(4), u=np.ones(4), m=np.ones(4), h=np.full(4, 0.1))
+    codes = []
+    for stream in (None, torch.cuda.Stream()):
+        prob = S.Problem(bad, S.make_params(S.PREC_MIXED, periodic=False, block_levels=3, flags=S.FLAG_ASYNC),
+                         stream=stream)
+        prob.density_h()
+        prob.forces()
+        prob.sync(allow=(S.ENOCONV,))
+        rc, _, _ = S.sph_block_step(prob.ctx)
+        codes.append(rc)
+        assert prob.diagnostics().steps == 0 and prob.diagnostics().time == 0.0
+        prob.close()
+    assert codes[0] == codes[1] and codes[0] in (S.ENONFINITE, S.ENOCONV), codes
+
+
 def test_block_step_rejections(S):
     import torch
     a, p = ics.lattice(6, seed=2)
