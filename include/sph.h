@@ -281,8 +281,20 @@ int sph_run(sph_ctx *ctx, int nsteps);
  * synchronised with fresh forces.  tree_rebuild_every applies between ticks
  * as between global steps.  Writes Delta t_MAX to *dtmax and the
  * number of particle force evaluations to *evals (either may be NULL).
- * Synchronises (one host round trip per tick where a step ends). */
+ * The schedule lives on the device: on a stream that can be captured, the
+ * first call captures one CUDA graph whose ticks are a conditional while
+ * loop (no host round trip between ticks) and later calls replay it; on the
+ * legacy default stream the host reads a loop flag after every tick.  In a
+ * tick the pair kernels serve tasks of a leaf's particles whose step ends
+ * (up to 4 with 8 lanes each in FP32 pairs, 8 with 4 lanes in FP64) rather
+ * than whole leaves.  Synchronises once at the end. */
 int sph_block_step(sph_ctx *ctx, double *dtmax, int64_t *evals);
+
+/* Capture the block step's graph now (see sph_block_step), so that the first
+ * sph_block_step does not include the capture; nothing runs.  SPH_OK on the
+ * legacy default stream, where nothing is captured.  SPH_EINVAL: ctx NULL or
+ * set up without block_levels; SPH_ECUDA: capture or instantiation failed. */
+int sph_block_prepare(sph_ctx *ctx);
 
 /* Copy each particle's time-step level (int32, caller's order) into the
  * device array levels (n entries). */

@@ -82,6 +82,7 @@ void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precis
     b.bvh = block ? c.take<double>(5 * n) : nullptr;
     b.bzeta = block ? c.take<double>(n) : nullptr;
     b.slev = block ? (void *)c.take<char>(v4 / 4 * n) : nullptr;
+    b.btask = block ? c.take<int>(n) : nullptr;
     b.flag = c.take<unsigned>(n);
     const long long ml = leaves_upper_bound(n);
     b.max_leaves = (int)ml;
@@ -622,6 +623,11 @@ static BatchView block_view(const sph_ctx *c)
     BatchView b = c->bv;
     b.block_on = 1;
     b.any_general = 1;  // the active particles' forces run in the wrap-list launch
+    // the pair kernels serve tasks of up to 32 / block_lanes particles whose
+    // step ends, block_lanes lanes each
+    b.block_lanes = c->prm.precision == SPH_PREC_FP64 ? kBlockLanesF64 : kBlockLanesF32;
+    b.lpp_mask = mask_of(b.block_lanes, c->prm.kernel);
+    b.dens_mask = dens_class_bit(b.block_lanes, c->host_ps.uniform_m, c->prm.kernel);
     return b;
 }
 
@@ -639,6 +645,7 @@ static int enqueue_block_leaves(const BatchView &b, int prec, bool rebuild, cuda
     CU(launch_block_stage(b, prec, st));  // which sorted particles end their step now
     if (rebuild) CU(launch_build_leaves(b, prec, st));
     else CU(launch_update_leaves(b, prec, st));
+    CU(launch_block_tasks(b, prec, st));
     return SPH_OK;
 }
 
@@ -861,6 +868,14 @@ int sph_block_step(sph_ctx *c, double *dtmax_out, int64_t *evals_out)
     c->have_forces = true;
     c->since_build = c->prm.tree_rebuild_every > 1 ? c->prm.tree_rebuild_every : 1;  // the next global step rebuilds
     return rc;
+}
+
+int sph_block_prepare(sph_ctx *c)
+{
+    if (!c) return fail(SPH_EINVAL, "ctx is NULL");
+    if (c->prm.block_levels <= 0 || !c->bv.blev) return fail(SPH_EINVAL, "the context was set up without block_levels");
+    if (c->stream == nullptr || c->block_graph || c->n == 0) return SPH_OK;
+    return build_block_graph(c, block_view(c));
 }
 
 int sph_block_levels(sph_ctx *c, int32_t *levels)

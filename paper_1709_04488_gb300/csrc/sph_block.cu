@@ -167,6 +167,7 @@ __global__ void k_block_gate(BatchView b, int L, int use_cond, cudaGraphConditio
 __global__ void k_block_tick_begin(BatchView b, int every, int use_cond, cudaGraphConditionalHandle cond)
 {
     b.scratch64[5] = b.scratch64[2];
+    b.counters[kBlockTasks] = 0;
     if (use_cond) cudaGraphSetConditional(cond, b.scratch64[8] % every == 0 ? 1u : 0u);
 }
 
@@ -236,6 +237,29 @@ __global__ void __launch_bounds__(kBlockThreads) k_block_stage(BatchView b)
     const int g = b.perm[s];
     const T v = (T)(b.blev[g] + 1);
     ((T *)b.slev)[s] = b.bt1[g] == k ? v : -v;
+}
+
+// the tick's tasks for the pair kernels: each leaf with particles whose step
+// ends now gives one task per 32 / block_lanes of them (in sorted order), so
+// that a task's block_lanes lanes per particle and its box (of those
+// particles only) keep the pair kernels' latency short when few particles
+// of a leaf are due
+template <typename T>
+__global__ void __launch_bounds__(kBlockThreads) k_block_tasks(BatchView b)
+{
+    const int lane = threadIdx.x & 31;
+    const int nleaf = b.counters[0];
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int leaf = w; leaf < nleaf; leaf += nw) {
+        const int st = b.leaf_start[leaf], n = b.leaf_start[leaf + 1] - st;  // (n <= 32)
+        const bool due = lane < n && ((const T *)b.slev)[st + (lane < n ? lane : 0)] > T(0);
+        const int d = __popc(__ballot_sync(0xffffffffu, due));
+        const int size = 32 / b.block_lanes, nt = (d + size - 1) / size;
+        int base = 0;
+        if (lane == 0 && nt > 0) base = atomicAdd(&b.counters[kBlockTasks], nt);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (lane < nt) b.btask[base + lane] = (leaf << 5) | (lane * size);
+    }
 }
 
 // after the force pass at tick k: closing half kick of the active particles
@@ -350,6 +374,14 @@ cudaError_t launch_block_stage(const BatchView &b, int precision, cudaStream_t s
 {
     if (precision == SPH_PREC_FP64) k_block_stage<double><<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b);
     else k_block_stage<float><<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_tasks(const BatchView &b, int precision, cudaStream_t st)
+{
+    const unsigned grid = (unsigned)dev_info().sm_count * 4;
+    if (precision == SPH_PREC_FP64) k_block_tasks<double><<<grid, kBlockThreads, 0, st>>>(b);
+    else k_block_tasks<float><<<grid, kBlockThreads, 0, st>>>(b);
     return cudaGetLastError();
 }
 

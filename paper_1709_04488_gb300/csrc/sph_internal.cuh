@@ -25,6 +25,12 @@ constexpr double kPi = 3.14159265358979323846;
 // a forces-only call 11, 15, 32..39 and 56..71
 constexpr int kNumCounters = 72;
 constexpr int kSlowCounter = 8, kPoolCounter = 9, kDensWrapList = 10, kForceWrapList = 11, kTimeoutCounter = 15;
+// block-step ticks: counter 12 holds the number of tasks (a leaf and up to
+// 32 / block_lanes of its particles whose step ends now, served with
+// block_lanes lanes each by the pair kernels); cleared by each tick's first
+// kernel.  block_lanes: 8 in FP32 pairs, 4 in FP64 (the lanes the FP64
+// kernels are built for)
+constexpr int kBlockTasks = 12, kBlockLanesF32 = 8, kBlockLanesF64 = 4;
 constexpr int kDensityCounter = 16, kForceCounter = 32, kDensityWrapCounter = 40, kForceWrapCounter = 56,
               kForceCdCounter = 64;
 constexpr int kDensityClasses = 16, kForceClasses = 8;
@@ -182,6 +188,7 @@ struct BatchView {
     void *gnode[kMaxLevels + 1];
     // block time-steps (single problem): per particle, original order
     int block_on;                // this launch set is a tick of a block step
+    int block_lanes;             // lanes per particle of the tick's pair kernels
     int *blev;                   // level
     int *bnml;                   // largest level among the force neighbours at the last force pass (-1: none)
     int *breq;                   // reactive limiter: level asked of an inactive particle (-1: none)
@@ -189,6 +196,7 @@ struct BatchView {
     double *bvh;                 // half-step velocity x, y, z, u and alpha ([5][n])
     double *bzeta;               // gravity: the zeta term's weight G zeta / (2 Omega) of the last solve
     void *slev;                  // sorted: +(level + 1) if the particle ends its step now, else -(level + 1)
+    int *btask;                  // tasks of this tick: leaf << 5 | ordinal of its first due particle
     void *gpos;                  // gravity tree: (x - corner, m) per sorted particle, Vec4
     void *gh;                    // gravity tree: (h, 1/h) per sorted particle, float2 or double2
     ProbStatic *prob;            // [nprob]
@@ -347,6 +355,7 @@ cudaError_t launch_block_tick_begin(const BatchView &b, int every, bool use_cond
                                     cudaStream_t st);
 cudaError_t launch_block_drift(const BatchView &b, cudaStream_t st);
 cudaError_t launch_block_stage(const BatchView &b, int precision, cudaStream_t st);
+cudaError_t launch_block_tasks(const BatchView &b, int precision, cudaStream_t st);  // after the leaves
 cudaError_t launch_block_kick(const BatchView &b, int L, cudaStream_t st);
 cudaError_t launch_block_tick_end(const BatchView &b, int L, bool use_cond, cudaGraphConditionalHandle cond,
                                   cudaStream_t st);

@@ -22,6 +22,11 @@ cudaError_t force_launches_m4(const BatchView &b, int precision, cudaStream_t st
 cudaError_t launch_density(const BatchView &b, int precision, int use_pred, cudaStream_t st)
 {
     if (b.ntot == 0) return cudaSuccess;
+    if (b.block_on) {  // block-step tick: the particles that keep their solve first
+        const unsigned grid = (unsigned)((b.ntot + 255) / 256);
+        if (precision == SPH_PREC_FP64) k_block_restage<double><<<grid, 256, 0, st>>>(b, use_pred);
+        else k_block_restage<float><<<grid, 256, 0, st>>>(b, use_pred);
+    }
     cudaError_t e = density_launches_m4(b, precision, use_pred, st);
     if (e == cudaSuccess) e = density_launches_m6(b, precision, use_pred, st);
     if (e == cudaSuccess && (b.any_periodic || b.any_gravity)) e = density_launches_m4_wrap(b, precision, use_pred, st);
@@ -35,8 +40,11 @@ cudaError_t launch_density(const BatchView &b, int precision, int use_pred, cuda
 cudaError_t launch_forces(const BatchView &b, int precision, cudaStream_t st)
 {
     if (b.ntot == 0) return cudaSuccess;
-    cudaError_t e = force_launches_m4(b, precision, st);
-    if (e == cudaSuccess) e = force_launches_m6(b, precision, st);
+    cudaError_t e = cudaSuccess;
+    if (!b.block_on) {  // (block-step ticks: the wrap-list launch serves the tasks)
+        e = force_launches_m4(b, precision, st);
+        if (e == cudaSuccess) e = force_launches_m6(b, precision, st);
+    }
     if (e == cudaSuccess && (b.any_periodic || b.any_general)) e = force_launches_m4_wrap(b, precision, st);
     if (e == cudaSuccess && (b.any_periodic || b.any_general)) e = force_launches_m6_wrap(b, precision, st);
     if (e != cudaSuccess) return e;

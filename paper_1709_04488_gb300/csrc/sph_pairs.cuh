@@ -615,6 +615,46 @@ struct DCfg {
     static constexpr size_t smem = WPB * per_warp;
 };
 
+// Block-step tasks (k0 >= 0): the lane group pp serves the (k0 + pp)-th
+// particle of the leaf whose step ends now; returns its position in the
+// leaf and whether there is one.  k0 < 0: the whole leaf, position pp.
+template <typename T>
+__device__ __forceinline__ bool task_member(const BatchView &b, int st, int nA, int k0, int pp, int &pos)
+{
+    const int lane = threadIdx.x & 31;
+    if (k0 < 0) {
+        pos = pp;
+        return pp < nA;
+    }
+    const unsigned dm = __ballot_sync(FULL, lane < nA && ((const T *)b.slev)[st + (lane < nA ? lane : 0)] > T(0));
+    const int ord = k0 + pp;
+    const bool on = ord < __popc(dm);
+    pos = on ? (int)__fns(dm, 0u, ord + 1) : 0;
+    return on;
+}
+
+// A task's position box (its particles only) in absolute float coordinates,
+// from their offsets x (staged, leaf frame) as the leaf build forms the
+// leaf's: each offset widened for its one rounding, plus the leaf's
+// reference point rounded down (up).  w of plo: hmax.
+__device__ __forceinline__ float task_widen_dn(float v) { return __fsub_rd(v, fabsf(v) * 2.4e-7f); }
+__device__ __forceinline__ float task_widen_up(float v) { return __fadd_ru(v, fabsf(v) * 2.4e-7f); }
+
+template <typename V>
+__device__ __forceinline__ void task_box(const BatchView &b, int leaf, const V &x, bool on, float hmax, NodeBox &box)
+{
+    const float o[3] = {(float)x.x, (float)x.y, (float)x.z};
+    float lo[3], hi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = warp_min(on ? task_widen_dn(o[a]) : INFINITY);
+        hi[a] = warp_max(on ? task_widen_up(o[a]) : -INFINITY);
+    }
+    const float *cf = b.leaf_cf + 6LL * leaf;  // reference point rounded down (0..2) and up (3..5)
+    box.plo = make_float4(__fadd_rd(cf[0], lo[0]), __fadd_rd(cf[1], lo[1]), __fadd_rd(cf[2], lo[2]), hmax);
+    box.phi = make_float4(__fadd_ru(cf[3], hi[0]), __fadd_ru(cf[4], hi[1]), __fadd_ru(cf[5], hi[2]), box.phi.w);
+}
+
 // Outputs of the density solve for sorted particle s (one lane per particle).
 template <typename T>
 __device__ __forceinline__ void density_epilogue(const BatchView &b, const ProbStatic &ps, long long s,
@@ -706,7 +746,7 @@ __device__ __forceinline__ void density_epilogue(const BatchView &b, const ProbS
 // false, having written nothing, when the plain variant meets an ambiguous
 // leaf pair.
 template <typename T, int LPP, bool UM, int K, bool WRAP>
-__device__ __forceinline__ bool density_leaf(const BatchView &b, int leaf, unsigned char *mine, int use_pred)
+__device__ __forceinline__ bool density_leaf(const BatchView &b, int leaf, int k0, unsigned char *mine, int use_pred)
 {
     using C = DCfg<T, LPP, UM, K>;
     using KF = Kern<K>;
@@ -727,17 +767,15 @@ __device__ __forceinline__ bool density_leaf(const BatchView &b, int leaf, unsig
     const int st = b.leaf_start[leaf], nA = b.leaf_start[leaf + 1] - st;
     const ProbDyn &dy = b.dyn[p];
     const PhysParams &ph = ps.ph;
-    const NodeBox boxA = b.nodes[0][leaf];
-    const bool active = pp < nA;
-    const long long s = st + (active ? pp : 0);
+    NodeBox boxA = b.nodes[0][leaf];
+    int pos;
+    const bool active = task_member<T>(b, st, nA, k0, pp, pos);
+    const long long s = st + (active ? pos : 0);
     const V pi = pm[s];
     const T mi = pi.w;
-    // block time-steps: a leaf none of whose particles ends its step now is
-    // only restaged from the particles' last solve
-    if (b.block_on && !__any_sync(FULL, active && ((const T *)b.slev)[s] > T(0))) {
-        if (active && sub == 0) density_epilogue<T>(b, ps, s, pi, T(1), T(0), T(0), use_pred, sigma);
-        return true;
-    }
+    // a block-step task walks from the box of its own particles (the others
+    // of the leaf keep their last solve, restaged by k_block_restage)
+    if (k0 >= 0) task_box(b, leaf, pi, active, boxA.plo.w, boxA);
     V flo, fhi;
     frame_box<V, T>(pi, active, flo, fhi);
     const float halfL = ph.periodic ? half_box(ph) : INFINITY;
@@ -770,7 +808,7 @@ __device__ __forceinline__ bool density_leaf(const BatchView &b, int leaf, unsig
     // candidate-leaf groups of the last walk (lane k holds group k) and
     // the walk radius they cover, kept for the force pass unless the
     // recent records outgrew their h (then the force pass walks)
-    const bool record = ps.diag->reuse_hold == 0;
+    const bool record = k0 < 0 && ps.diag->reuse_hold == 0;
     int ng = 0, g_first = 0;
     unsigned g_mask = 0u;
     float Rq_last = 0.f;
@@ -942,8 +980,9 @@ __device__ __forceinline__ bool density_leaf(const BatchView &b, int leaf, unsig
     }
     if (!WRAP && to_wrap) return false;  // nothing written yet
     // record the last walk's groups for the force pass (lane 0 reserves
-    // pool space); not recorded: the force pass walks for this leaf
-    {
+    // pool space); not recorded: the force pass walks for this leaf (a
+    // block-step task records nothing: its force pass always walks)
+    if (k0 < 0) {
         int base = 0;
         if (lane == 0) {
             base = record && ng <= kMaxLeafGroups ? atomicAdd(&b.counters[kPoolCounter], ng) : -1;
@@ -1044,22 +1083,25 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM, K>::WPB * 32, DCfg<T, LPP, UM
     extern __shared__ __align__(32) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     unsigned char *mine = smem + wib * C::per_warp;
-    const int nleaf = WRAP ? b.counters[kDensWrapList] : b.counters[0];
+    // block-step ticks serve tasks (leaf << 5 | first due ordinal) instead of leaves
+    const bool tasks = b.block_on != 0;
+    const int nleaf = WRAP ? b.counters[kDensWrapList] : tasks ? b.counters[kBlockTasks] : b.counters[0];
     const int cls = lpp_log2(LPP) + (UM ? 4 : 0) + 8 * K;
     for (;;) {
-        int leaf = 0;
-        if (lane == 0) leaf = atomicAdd(&b.counters[(WRAP ? kDensityWrapCounter : kDensityCounter) + cls], 1);
-        leaf = __shfl_sync(FULL, leaf, 0);
-        if (leaf >= nleaf) break;
-        if (WRAP) leaf = b.wrap_list[leaf];
+        int item = 0;
+        if (lane == 0) item = atomicAdd(&b.counters[(WRAP ? kDensityWrapCounter : kDensityCounter) + cls], 1);
+        item = __shfl_sync(FULL, item, 0);
+        if (item >= nleaf) break;
+        item = WRAP ? b.wrap_list[item] : tasks ? b.btask[item] : item;
+        const int leaf = tasks ? item >> 5 : item, k0 = tasks ? item & 31 : -1;
         const ProbStatic &ps = b.prob[b.leaf_pid[leaf]];
-        if (ps.lpp != LPP || (ps.uniform_m != 0) != UM || ps.ph.kernel != K) continue;  // another launch's
+        if ((tasks ? b.block_lanes : ps.lpp) != LPP || (ps.uniform_m != 0) != UM || ps.ph.kernel != K) continue;
         if (!WRAP && ps.ph.gravity) {  // gravity's zeta runs in the wrap-list launch only
-            if (lane == 0) b.wrap_list[atomicAdd(&b.counters[kDensWrapList], 1)] = leaf;
+            if (lane == 0) b.wrap_list[atomicAdd(&b.counters[kDensWrapList], 1)] = item;
             continue;
         }
-        if (!density_leaf<T, LPP, UM, K, WRAP>(b, leaf, mine, use_pred) && lane == 0) {
-            b.wrap_list[atomicAdd(&b.counters[kDensWrapList], 1)] = leaf;
+        if (!density_leaf<T, LPP, UM, K, WRAP>(b, leaf, k0, mine, use_pred) && lane == 0) {
+            b.wrap_list[atomicAdd(&b.counters[kDensWrapList], 1)] = item;
             atomicAdd(&ps.diag->wrap_leaves, 1);
         }
     }
@@ -1330,7 +1372,7 @@ __device__ __forceinline__ dbl4 ld_ro<dbl4>(const dbl4 *p)
 // image.  Returns false (writing nothing) when the plain launch meets an
 // ambiguous leaf pair.
 template <typename T, int LPP, int K, bool WRAP, bool CD>
-__device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigned char *mine, float Rall)
+__device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, int k0, unsigned char *mine, float Rall)
 {
     using C = FCfg<T, LPP>;
     using KF = Kern<K>;
@@ -1350,10 +1392,14 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
     const int st = b.leaf_start[leaf], nA = b.leaf_start[leaf + 1] - st;
     const ProbDyn &dy = b.dyn[p];
     const PhysParams &ph = ps.ph;
-    const NodeBox boxA = b.nodes[0][leaf];
-    const bool active = pp < nA;
-    const int s = st + (active ? pp : 0);
+    NodeBox boxA = b.nodes[0][leaf];
+    int pos;
+    const bool active = task_member<T>(b, st, nA, k0, pp, pos);
+    const int s = st + (active ? pos : 0);
     const V xi = gph[s], vi = gvc[s], ti = gth[s];
+    // a block-step task walks from the box of its own particles, whose
+    // largest h sets the gather reach
+    if (k0 >= 0) task_box(b, leaf, xi, active, warp_max(active ? b.hf[s] : 0.f), boxA);
     const T alpha = (T)ph.alpha_av, beta = (T)ph.beta_av, aac = (T)ph.alpha_ac;
     // Price conductivity: v'_sig = sqrt(|P_i - P_j| / rho_bar) with P = (gamma - 1) rho u
     // (adiabatic); 0 selects Wadsley's |v_ij . r_hat|
@@ -1493,7 +1539,7 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
     // pair vector's the pair sits at q = R_K, where f' and the force vanish
     auto test = [&]() {
         __syncwarp();  // staged candidates visible to every lane
-        const int self = tA >= 0 ? ((tA << 5) | pp) : -1;
+        const int self = tA >= 0 ? ((tA << 5) | pos) : -1;
         for (int k0 = 0; k0 < nbuf; k0 += C::SB) {
             if (__any_sync(FULL, cnt > C::LC - C::SB / LPP)) eval_lists();
             const int ke = k0 + C::SB < nbuf ? k0 + C::SB : nbuf;
@@ -1559,7 +1605,7 @@ __device__ __forceinline__ bool force_leaf(const BatchView &b, int leaf, unsigne
     };
     // the candidate groups the density walk recorded cover every pair
     // unless some final h outgrew them (then walk the tree again)
-    const int ngl = b.leaf_ngroups[leaf];
+    const int ngl = k0 < 0 ? b.leaf_ngroups[leaf] : -1;
     if (!dy.lists_stale && ngl >= 0) {
         const int gofs = b.leaf_gofs[leaf];
         for (int g = 0; g < ngl; ++g) {
@@ -1662,19 +1708,23 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, FCfg<T, LPP>::MINB) k_
     extern __shared__ __align__(32) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     unsigned char *mine = smem + wib * C::per_warp;
-    const int nleaf = WRAP ? b.counters[kForceWrapList] : b.counters[0];
+    // block-step ticks: the wrap-list launch serves the tick's tasks (leaf
+    // << 5 | first due ordinal) directly; the common launch does not run
+    const bool tasks = WRAP && b.block_on;
+    const int nleaf = tasks ? b.counters[kBlockTasks] : WRAP ? b.counters[kForceWrapList] : b.counters[0];
     const int cls = lpp_log2(LPP) + 4 * K;
     int last_p = -1;
     float Rall = 0.f;  // periodic: pairs reach R_K x the problem's largest h
     for (;;) {
-        int leaf = 0;
-        if (lane == 0) leaf = atomicAdd(&b.counters[(CD ? kForceCdCounter : WRAP ? kForceWrapCounter : kForceCounter) + cls], 1);
-        leaf = __shfl_sync(FULL, leaf, 0);
-        if (leaf >= nleaf) break;
-        if (WRAP) leaf = b.wrap_list[leaf];
+        int item = 0;
+        if (lane == 0) item = atomicAdd(&b.counters[(CD ? kForceCdCounter : WRAP ? kForceWrapCounter : kForceCounter) + cls], 1);
+        item = __shfl_sync(FULL, item, 0);
+        if (item >= nleaf) break;
+        if (WRAP) item = tasks ? b.btask[item] : b.wrap_list[item];
+        const int leaf = tasks ? item >> 5 : item, k0 = tasks ? item & 31 : -1;
         const int p = b.leaf_pid[leaf];
         const ProbStatic &ps = b.prob[p];
-        if (ps.lpp != LPP || ps.ph.kernel != K) continue;  // leaf of a problem served by another launch
+        if ((tasks ? b.block_lanes : ps.lpp) != LPP || ps.ph.kernel != K) continue;  // served by another launch
         if (WRAP && (ps.ph.av_switch == SPH_AV_CULLEN_DEHNEN) != CD) continue;  // (the switch's own launch)
         if (!WRAP && (ps.ph.av_switch || ps.ph.ac_signal || ps.ph.gravity || b.block_on)) {
             // the viscosity switch, Price's conductivity and gravity's zeta term run in the
@@ -1688,7 +1738,7 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, FCfg<T, LPP>::MINB) k_
             Rall = __fmul_ru((float)Kern<K>::R, Rall) * 1.0001f;
             last_p = p;
         }
-        if (!force_leaf<T, LPP, K, WRAP, CD>(b, leaf, mine, Rall) && lane == 0) {
+        if (!force_leaf<T, LPP, K, WRAP, CD>(b, leaf, k0, mine, Rall) && lane == 0) {
             b.wrap_list[atomicAdd(&b.counters[kForceWrapList], 1)] = leaf;
             atomicAdd(&ps.diag->wrap_leaves, 1);
         }
@@ -1727,6 +1777,18 @@ void run_density_fallback(const BatchView &b, int use_pred, cudaStream_t st)
         init = true;
     }
     k_density_fallback<T><<<dev_info().sm_count * 4, C::WPB * 32, C::smem, st>>>(b, use_pred);
+}
+
+// Block-step ticks: every particle whose step does not end now keeps the h,
+// rho, Omega, P and c of its last solve; restaged here (with its drifted
+// offsets and predicted v, u) for the force pass.
+template <typename T>
+__global__ void __launch_bounds__(256) k_block_restage(BatchView b, int use_pred)
+{
+    using V = typename Vec4<T>::type;
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= b.ntot || ((const T *)b.slev)[s] > T(0)) return;
+    density_epilogue<T>(b, b.prob[0], s, ((const V *)b.pm)[s], T(1), T(0), T(0), use_pred, T(0));
 }
 
 template <typename T, int LPP, int K, bool WRAP, bool CD = false>

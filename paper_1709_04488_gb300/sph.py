@@ -164,6 +164,7 @@ def lib():
             "sph_run": (i, [vp, i]),
             "sph_block_step": (i, [vp, C.POINTER(d), C.POINTER(i64)]),
             "sph_block_levels": (i, [vp, vp]),
+            "sph_block_prepare": (i, [vp]),
             "sph_sync": (i, [vp]),
             "sph_diagnostics": (i, [vp, C.POINTER(Diag)]),
             "sph_neighbours": (i, [vp, i, vp, vp, vp, i64, C.POINTER(i64)]),
@@ -282,6 +283,11 @@ def sph_block_step(ctx):
     evals = C.c_int64(0)
     rc = lib().sph_block_step(ctx, C.byref(dtmax), C.byref(evals))
     return rc, dtmax.value, evals.value
+
+
+def sph_block_prepare(ctx) -> int:
+    """Capture the block step's graph now (nothing runs)."""
+    return lib().sph_block_prepare(ctx)
 
 
 def sph_block_levels(ctx, levels_ptr) -> int:
@@ -462,6 +468,10 @@ class Problem:
         rc, dtmax, evals = sph_block_step(self.ctx)
         check(rc, "sph_block_step", allow)
         return dtmax, evals
+
+    def block_prepare(self):
+        """Capture the block step's graph ahead of the first block step."""
+        check(sph_block_prepare(self.ctx), "sph_block_prepare")
 
     def levels(self):
         """Each particle's time-step level (numpy int32, caller's order)."""

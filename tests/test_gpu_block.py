@@ -138,6 +138,8 @@ def _stepped(S, a, p, stream, blocks, **kw):
     prob = S.Problem(a, S.make_params(S.PREC_MIXED, **p, **kw), stream=stream)
     prob.density_h()
     prob.forces()
+    if stream is not None:
+        prob.block_prepare()  # the graph captured ahead of the first block
     out = [prob.block_step() for _ in range(blocks)]
     g = prob.numpy()
     g["levels"] = prob.levels()
