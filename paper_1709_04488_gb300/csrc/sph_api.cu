@@ -633,32 +633,33 @@ static BatchView block_view(const sph_ctx *c)
 
 static int block_every(const sph_ctx *c) { return c->prm.tree_rebuild_every > 1 ? c->prm.tree_rebuild_every : 1; }
 
-// tree reuse between ticks as between global steps: sort and build on every
-// tree_rebuild_every-th tick, refit the kept leaves between
+// the tick's drift and leaves.  Tree reuse (Sec. 4.2) between ticks as
+// between global steps: sort and build on every tree_rebuild_every-th tick;
+// between, the order and the leaves are kept (the drift runs in sorted order
+// with the gather) and the leaves refitted
 static int enqueue_block_leaves(const BatchView &b, int prec, bool rebuild, cudaStream_t st)
 {
     if (rebuild) {
+        CU(launch_block_drift(b, st));
         CU(launch_domain_and_keys(b, st));
         CU(launch_radix_sort(b, st));
     }
-    CU(launch_gather(b, st));
-    CU(launch_block_stage(b, prec, st));  // which sorted particles end their step now
+    CU(launch_block_gather(b, prec, !rebuild, st));  // (also which particles end their step now)
     if (rebuild) CU(launch_build_leaves(b, prec, st));
     else CU(launch_update_leaves(b, prec, st));
-    CU(launch_block_tasks(b, prec, st));
     return SPH_OK;
 }
 
 static int enqueue_block_passes(const BatchView &b, int prec, int L, bool use_cond, cudaGraphConditionalHandle loop,
                                 cudaStream_t st)
 {
-    CU(launch_density(b, prec, 1, st));  // solves the active particles, restages the others
+    CU(launch_block_tasks(b, prec, st));  // (and the restaging of the particles that keep their solve)
+    CU(launch_density(b, prec, 1, st));  // solves the particles whose step ends
     CU(launch_refit(b, prec, st));
     CU(launch_forces(b, prec, st));
     launch_gravity(b, prec, st);  // the long range of the active particles
     CU(cudaGetLastError());
-    CU(launch_block_kick(b, L, st));
-    CU(launch_block_tick_end(b, L, use_cond, loop, st));
+    CU(launch_block_kick(b, L, use_cond, loop, st));  // (its last block ends the tick, opens the next)
     return SPH_OK;
 }
 
@@ -670,14 +671,12 @@ static int block_step_eager(sph_ctx *c, const BatchView &b)
     CU(launch_block_dt(b, L, st));
     CU(launch_block_open(b, L, st));
     CU(launch_block_gate(b, L, false, 0, st));
-    for (int tick = 0;; ++tick) {
+    for (long long tick = 0;; ++tick) {
         long long go = 0;
         CU(cudaMemcpyAsync(&go, b.scratch64 + 9, sizeof go, cudaMemcpyDeviceToHost, st));
         CU(cudaStreamSynchronize(st));
         if (!go) break;
-        CU(launch_block_tick_begin(b, every, false, 0, st));
-        CU(launch_reset_step(b, 1, st));
-        CU(launch_block_drift(b, st));
+        if (tick >= (1LL << L)) return fail(SPH_ECUDA, "block step: more than 2^L ticks");
         int rc = enqueue_block_leaves(b, prec, tick % every == 0, st);
         if (rc) return rc;
         rc = enqueue_block_passes(b, prec, L, false, 0, st);
@@ -741,9 +740,7 @@ static int capture_tick(const sph_ctx *c, const BatchView &b, cudaGraphCondition
         if (rc) return rc;
         CU(cudaGraphConditionalHandleCreate(&rb, body, 0, 0));
     }
-    CU(launch_block_tick_begin(b, every, every > 1, rb, s2));
-    CU(launch_reset_step(b, 1, s2));
-    CU(launch_block_drift(b, s2));
+    if (every > 1) CU(launch_block_tick_begin(b, every, rb, s2));
     if (every > 1) {
         cudaGraph_t *br = nullptr;
         int rc = add_conditional(s2, rb, cudaGraphCondTypeIf, 2, &br);  // [0] rebuild, [1] keep the leaves

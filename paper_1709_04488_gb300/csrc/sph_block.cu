@@ -78,6 +78,7 @@ __global__ void k_block_init(BatchView b)
     b.scratch64[4] = 0;                           // the block starts at tick 0
     b.scratch64[8] = 0;                           // ticks taken
     b.scratch64[9] = 0;
+    b.scratch64[10] = 0;                          // kick blocks done
 }
 
 __global__ void __launch_bounds__(kBlockThreads) k_block_dt(BatchView b)
@@ -116,7 +117,10 @@ __global__ void k_block_plan(BatchView b, int L)
 __device__ __forceinline__ void next_event(const BatchView &b, long long t)
 {
     const long long m = warp_min(t);
-    if ((threadIdx.x & 31) == 0) atomicMin((unsigned long long *)&b.scratch64[2], (unsigned long long)m);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin((unsigned long long *)&b.scratch64[2], (unsigned long long)m);
+        __threadfence();  // (before the block reports itself done)
+    }
 }
 
 // each particle's opening step: level from its CFL step, raised to within
@@ -147,126 +151,123 @@ __global__ void __launch_bounds__(kBlockThreads) k_block_open(BatchView b, int L
     next_event(b, t1);
 }
 
+// A tick opens (all threads of one block): the step's counters and
+// diagnostics are cleared, the tick advances to the next event tick, whose
+// slot then collects a fresh minimum over the updated steps.
+__device__ __forceinline__ void open_tick(const BatchView &b)
+{
+    const int k = threadIdx.x;
+    if (k < kNumCounters) reset_counter(b, 1, k);
+    if (k < b.nprob) reset_diag(b, k, 1);
+    if (k == 0) {
+        b.scratch64[5] = *(volatile long long *)&b.scratch64[2];  // (in L2: other blocks' minima)
+        b.scratch64[2] = 0x7fffffffffffffffLL;
+        b.counters[kBlockTasks] = 0;
+    }
+}
+
 // the loop's gate before the first tick: the first event tick must lie in
-// (0, 2^L] and nothing may have failed
-__global__ void k_block_gate(BatchView b, int L, int use_cond, cudaGraphConditionalHandle cond)
+// (0, 2^L] and nothing may have failed; opens the first tick
+__global__ void __launch_bounds__(128) k_block_gate(BatchView b, int L, int use_cond, cudaGraphConditionalHandle cond)
 {
-    ProbDiag *d = b.prob[0].diag;
-    const long long N = 1LL << L, next = b.scratch64[2];
-    bool go = d->status == 0;
-    if (go && !(next > 0 && next <= N)) {
-        atomicOr(&d->status, ST_SCHEDULE);
-        go = false;
-    }
-    b.scratch64[9] = go ? 1 : 0;
-    if (use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
-}
-
-// a tick starts: it advances to the next event tick; with tree reuse, the
-// branch condition says whether this tick sorts and builds the leaves
-__global__ void k_block_tick_begin(BatchView b, int every, int use_cond, cudaGraphConditionalHandle cond)
-{
-    b.scratch64[5] = b.scratch64[2];
-    b.counters[kBlockTasks] = 0;
-    if (use_cond) cudaGraphSetConditional(cond, b.scratch64[8] % every == 0 ? 1u : 0u);
-}
-
-// a tick ends: the next one follows unless the block is complete or a
-// status is set; the next event tick must lie after this one
-__global__ void k_block_tick_end(BatchView b, int L, int use_cond, cudaGraphConditionalHandle cond)
-{
-    ProbDiag *d = b.prob[0].diag;
-    const long long N = 1LL << L, k1 = b.scratch64[5], next = b.scratch64[2];
-    b.scratch64[4] = k1;
-    b.scratch64[8] += 1;
-    bool go = d->status == 0 && k1 < N;
-    if (go && !(next > k1 && next <= N)) {
-        atomicOr(&d->status, ST_SCHEDULE);
-        go = false;
-    }
-    b.scratch64[9] = go ? 1 : 0;
-    if (use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
-}
-
-// drift every particle from tick k0 to tick k1, mark the particles whose
-// step ends at k1, predict v, u and alpha at k1 for the force pass
-__global__ void __launch_bounds__(kBlockThreads) k_block_drift(BatchView b)
-{
-    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long k0 = b.scratch64[4], k1 = b.scratch64[5];
-    const double tau = bits_d(b.scratch64[7]);
-    bool due = false;
-    if (g < b.ntot) {
-        const ProbStatic &ps = b.prob[0];
-        const PhysParams &ph = ps.ph;
-        const long long i = g - ps.base, n = b.ntot;
-        const double dk = __dmul_rn((double)(k1 - k0), tau);
-        double *X[3] = {ps.x, ps.y, ps.z};
-        const double *A[3] = {ps.ax, ps.ay, ps.az};
-        double *VP[3] = {b.vpx, b.vpy, b.vpz};
-        const int t0 = b.bt0[g], t1 = b.bt1[g];
-        const double dp = __dmul_rn(__dmul_rn((double)(2 * k1 - t0 - t1), 0.5), tau);  // t - t_mid
-        for (int a = 0; a < 3; ++a) {
-            const double vh = b.bvh[a * n + g];
-            double x = __dadd_rn(X[a][i], __dmul_rn(vh, dk));
-            if (ph.periodic) {
-                const double lo = ph.box_lo[a], Lb = ph.box_len[a];
-                if (x >= lo + Lb) x -= Lb;
-                else if (x < lo) x += Lb;
-            }
-            X[a][i] = x;
-            VP[a][g] = kick(vh, A[a][i], dp);
+    __shared__ int go_s;
+    if (threadIdx.x == 0) {
+        ProbDiag *d = b.prob[0].diag;
+        const long long N = 1LL << L, next = b.scratch64[2];
+        bool go = d->status == 0;
+        if (go && !(next > 0 && next <= N)) {
+            atomicOr(&d->status, ST_SCHEDULE);
+            go = false;
         }
-        b.up[g] = ph.eos == SPH_EOS_ADIABATIC ? kick(b.bvh[3 * n + g], ps.du[i], dp) : ps.u[i];
-        if (ph.av_switch) b.ap[g] = kick(b.bvh[4 * n + g], ps.dalpha[i], dp);
-        b.breq[g] = -1;
-        due = t1 == k1;
+        b.scratch64[9] = go ? 1 : 0;
+        if (use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
+        go_s = go;
     }
+    __syncthreads();
+    if (go_s) open_tick(b);
+}
+
+// graph form with tree reuse: whether this tick sorts and builds the leaves
+__global__ void k_block_tick_begin(BatchView b, int every, cudaGraphConditionalHandle cond)
+{
+    cudaGraphSetConditional(cond, b.scratch64[8] % every == 0 ? 1u : 0u);
+}
+
+// drift particle g (original order) from tick k0 to tick k1 and predict
+// its v, u and alpha at k1 for the force pass; true if its step ends at k1
+__device__ __forceinline__ bool drift_one(const BatchView &b, long long g, long long k0, long long k1, double tau)
+{
+    const ProbStatic &ps = b.prob[0];
+    const PhysParams &ph = ps.ph;
+    const long long i = g - ps.base, n = b.ntot;
+    const double dk = __dmul_rn((double)(k1 - k0), tau);
+    double *X[3] = {ps.x, ps.y, ps.z};
+    const double *A[3] = {ps.ax, ps.ay, ps.az};
+    double *VP[3] = {b.vpx, b.vpy, b.vpz};
+    const int t0 = b.bt0[g], t1 = b.bt1[g];
+    const double dp = __dmul_rn(__dmul_rn((double)(2 * k1 - t0 - t1), 0.5), tau);  // t - t_mid
+    for (int a = 0; a < 3; ++a) {
+        const double vh = b.bvh[a * n + g];
+        double x = __dadd_rn(X[a][i], __dmul_rn(vh, dk));
+        if (ph.periodic) {
+            const double lo = ph.box_lo[a], Lb = ph.box_len[a];
+            if (x >= lo + Lb) x -= Lb;
+            else if (x < lo) x += Lb;
+        }
+        X[a][i] = x;
+        VP[a][g] = kick(vh, A[a][i], dp);
+    }
+    b.up[g] = ph.eos == SPH_EOS_ADIABATIC ? kick(b.bvh[3 * n + g], ps.du[i], dp) : ps.u[i];
+    if (ph.av_switch) b.ap[g] = kick(b.bvh[4 * n + g], ps.dalpha[i], dp);
+    b.breq[g] = -1;
+    return t1 == k1;
+}
+
+__device__ __forceinline__ void count_due(const BatchView &b, bool due)
+{
     const unsigned m = __ballot_sync(0xffffffffu, due);
     if ((threadIdx.x & 31) == 0 && m) atomicAdd((unsigned long long *)&b.scratch64[3], (unsigned long long)__popc(m));
 }
 
-// sorted staging of the levels for the force pass: +(level + 1) where the
-// step ends at tick k, -(level + 1) elsewhere
-template <typename T>
-__global__ void __launch_bounds__(kBlockThreads) k_block_stage(BatchView b)
+// drift every particle (original order), ahead of a new sort
+__global__ void __launch_bounds__(kBlockThreads) k_block_drift(BatchView b)
 {
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= b.ntot) return;
-    const long long k = b.scratch64[5];
-    const int g = b.perm[s];
-    const T v = (T)(b.blev[g] + 1);
-    ((T *)b.slev)[s] = b.bt1[g] == k ? v : -v;
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool due = g < b.ntot && drift_one(b, g, b.scratch64[4], b.scratch64[5], bits_d(b.scratch64[7]));
+    count_due(b, due);
 }
 
-// the tick's tasks for the pair kernels: each leaf with particles whose step
-// ends now gives one task per 32 / block_lanes of them (in sorted order), so
-// that a task's block_lanes lanes per particle and its box (of those
-// particles only) keep the pair kernels' latency short when few particles
-// of a leaf are due
-template <typename T>
-__global__ void __launch_bounds__(kBlockThreads) k_block_tasks(BatchView b)
+// sorted particle s: (with DRIFT, its drift first, when the leaves are kept
+// and so is the order) the gather of position, mass and h into sorted order
+// and the staging of its level for the force pass: +(level + 1) where the
+// step ends at tick k1, -(level + 1) elsewhere
+template <typename T, bool DRIFT>
+__global__ void __launch_bounds__(kBlockThreads) k_block_gather(BatchView b)
 {
-    const int lane = threadIdx.x & 31;
-    const int nleaf = b.counters[0];
-    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-    for (int leaf = w; leaf < nleaf; leaf += nw) {
-        const int st = b.leaf_start[leaf], n = b.leaf_start[leaf + 1] - st;  // (n <= 32)
-        const bool due = lane < n && ((const T *)b.slev)[st + (lane < n ? lane : 0)] > T(0);
-        const int d = __popc(__ballot_sync(0xffffffffu, due));
-        const int size = 32 / b.block_lanes, nt = (d + size - 1) / size;
-        int base = 0;
-        if (lane == 0 && nt > 0) base = atomicAdd(&b.counters[kBlockTasks], nt);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (lane < nt) b.btask[base + lane] = (leaf << 5) | (lane * size);
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long k1 = b.scratch64[5];
+    bool due = false;
+    if (s < b.ntot) {
+        const ProbStatic &ps = b.prob[0];
+        const long long g = b.perm[s], i = g - ps.base;
+        if (DRIFT) due = drift_one(b, g, b.scratch64[4], k1, bits_d(b.scratch64[7]));
+        b.sx[s] = ps.x[i];
+        b.sy[s] = ps.y[i];
+        b.sz[s] = ps.z[i];
+        b.sm[s] = ps.m[i];
+        b.sh[s] = ps.h[i];
+        const T v = (T)(b.blev[g] + 1);
+        ((T *)b.slev)[s] = b.bt1[g] == k1 ? v : -v;
     }
+    if (DRIFT) count_due(b, due);
 }
 
 // after the force pass at tick k: closing half kick of the active particles
 // and, before the end of the block, the level and opening half kick of their
 // next step; inactive particles lifted by the reactive limiter end their
 // step at the next tick of their new level's grid
-__global__ void __launch_bounds__(kBlockThreads) k_block_kick(BatchView b, int L)
+__global__ void __launch_bounds__(kBlockThreads) k_block_kick(BatchView b, int L, int use_cond,
+                                                              cudaGraphConditionalHandle cond)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long k = b.scratch64[5];
@@ -320,9 +321,36 @@ __global__ void __launch_bounds__(kBlockThreads) k_block_kick(BatchView b, int L
         if (t1 > k) tnext = t1;
     }
     next_event(b, tnext);
+    // the last block to finish ends the tick: the next one follows unless the
+    // block is complete or a status is set; the next event tick must lie
+    // after this one (read past L1: the other blocks' minima are in L2)
+    __shared__ int last_s, go_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last_s = atomicAdd((unsigned long long *)&b.scratch64[10], 1ull) == (unsigned long long)gridDim.x - 1ull;
+    }
+    __syncthreads();
+    if (!last_s) return;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        ProbDiag *d = b.prob[0].diag;
+        const long long N = 1LL << L, next = *(volatile long long *)&b.scratch64[2];
+        b.scratch64[10] = 0;
+        b.scratch64[4] = k;
+        b.scratch64[8] += 1;
+        bool go = *(volatile unsigned *)&d->status == 0 && k < N && b.scratch64[8] < N;
+        if (go && !(next > k && next <= N)) {
+            atomicOr(&d->status, ST_SCHEDULE);
+            go = false;
+        }
+        b.scratch64[9] = go ? 1 : 0;
+        if (use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
+        go_s = go;
+    }
+    __syncthreads();
+    if (go_s) open_tick(b);
 }
-
-__global__ void k_block_next_reset(BatchView b) { b.scratch64[2] = 0x7fffffffffffffffLL; }
 
 __global__ void k_block_finish(BatchView b)
 {
@@ -353,14 +381,14 @@ cudaError_t launch_block_open(const BatchView &b, int L, cudaStream_t st)
 cudaError_t launch_block_gate(const BatchView &b, int L, bool use_cond, cudaGraphConditionalHandle cond,
                               cudaStream_t st)
 {
-    k_block_gate<<<1, 1, 0, st>>>(b, L, use_cond ? 1 : 0, cond);
+    k_block_gate<<<1, 128, 0, st>>>(b, L, use_cond ? 1 : 0, cond);
     return cudaGetLastError();
 }
 
-cudaError_t launch_block_tick_begin(const BatchView &b, int every, bool use_cond, cudaGraphConditionalHandle cond,
+cudaError_t launch_block_tick_begin(const BatchView &b, int every, cudaGraphConditionalHandle cond,
                                     cudaStream_t st)
 {
-    k_block_tick_begin<<<1, 1, 0, st>>>(b, every > 1 ? every : 1, use_cond ? 1 : 0, cond);
+    k_block_tick_begin<<<1, 1, 0, st>>>(b, every > 1 ? every : 1, cond);
     return cudaGetLastError();
 }
 
@@ -370,32 +398,23 @@ cudaError_t launch_block_drift(const BatchView &b, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_block_stage(const BatchView &b, int precision, cudaStream_t st)
+cudaError_t launch_block_gather(const BatchView &b, int precision, bool drift, cudaStream_t st)
 {
-    if (precision == SPH_PREC_FP64) k_block_stage<double><<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b);
-    else k_block_stage<float><<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b);
+    const unsigned grid = blocks_for(b.ntot);
+    if (precision == SPH_PREC_FP64) {
+        if (drift) k_block_gather<double, true><<<grid, kBlockThreads, 0, st>>>(b);
+        else k_block_gather<double, false><<<grid, kBlockThreads, 0, st>>>(b);
+    } else {
+        if (drift) k_block_gather<float, true><<<grid, kBlockThreads, 0, st>>>(b);
+        else k_block_gather<float, false><<<grid, kBlockThreads, 0, st>>>(b);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_block_tasks(const BatchView &b, int precision, cudaStream_t st)
+cudaError_t launch_block_kick(const BatchView &b, int L, bool use_cond, cudaGraphConditionalHandle cond,
+                             cudaStream_t st)
 {
-    const unsigned grid = (unsigned)dev_info().sm_count * 4;
-    if (precision == SPH_PREC_FP64) k_block_tasks<double><<<grid, kBlockThreads, 0, st>>>(b);
-    else k_block_tasks<float><<<grid, kBlockThreads, 0, st>>>(b);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_block_kick(const BatchView &b, int L, cudaStream_t st)
-{
-    k_block_next_reset<<<1, 1, 0, st>>>(b);  // the next event is a fresh minimum over the updated steps
-    k_block_kick<<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b, L);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_block_tick_end(const BatchView &b, int L, bool use_cond, cudaGraphConditionalHandle cond,
-                                  cudaStream_t st)
-{
-    k_block_tick_end<<<1, 1, 0, st>>>(b, L, use_cond ? 1 : 0, cond);
+    k_block_kick<<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b, L, use_cond ? 1 : 0, cond);
     return cudaGetLastError();
 }
 

@@ -16,44 +16,6 @@ constexpr int kRedThreads = 256;
 
 constexpr int kCloseItems = 8;  // most particles per thread in the closing kernel
 
-__device__ void reset_diag(const BatchView &b, int p, int mode)
-{
-    ProbDiag *d = b.prob[p].diag;
-    d->dt_min_bits = 0x7ff0000000000000ull;  // +inf
-    d->force_pairs = 0;
-    d->grav_pairs = d->grav_nodes = 0;
-    if (mode == 2) return;
-    d->wrap_leaves = 0;
-    d->mass = 0;
-    for (int a = 0; a < 3; ++a) {
-        d->mom[a] = 0;
-        d->fsum[a] = 0;
-    }
-    d->energy = 0;
-    d->dEdt = 0;
-    d->nr_iter = d->density_pairs = d->candidates = d->fallback = 0;
-    d->ngb_sum = 0;
-    d->nr_max = 0;
-    d->ngb_min = 0x7fffffff;
-    d->ngb_max = 0;
-    d->status = 0;
-    d->unconverged = 0;
-}
-
-// Clear the per-call counters (block 0, first kNumCounters threads): mode 1
-// all of a step's, mode 2 those of a forces-only call.
-__device__ __forceinline__ void reset_counters(const BatchView &b, int mode)
-{
-    const int k = threadIdx.x;
-    if (blockIdx.x != 0 || k >= kNumCounters) return;
-    const bool all = (k >= kSlowCounter && k <= kForceWrapList) || k >= kTimeoutCounter;
-    const bool forces = k == kForceWrapList || k == kTimeoutCounter ||
-                        (k >= kForceCounter && k < kForceCounter + kForceClasses) ||
-                        (k >= kForceWrapCounter && k < kForceWrapCounter + kForceClasses) ||
-                        (k >= kForceCdCounter && k < kForceCdCounter + kForceClasses);
-    if (mode == 1 ? all : forces) b.counters[k] = 0;
-}
-
 __global__ void k_reset_step(BatchView b, int mode)
 {
     int p = blockIdx.x * blockDim.x + threadIdx.x;

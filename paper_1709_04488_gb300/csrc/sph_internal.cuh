@@ -345,25 +345,74 @@ cudaError_t launch_kick_drift(const BatchView &b, double dt_host, cudaStream_t s
 // [0] smallest and [1] largest step (ordered bits), [2] next tick where a
 // step ends, [3] force evaluations, [4] the current tick k0, [5] the tick k1
 // being advanced to, [6] Delta t_MAX and [7] the tick length (bits), [8]
-// ticks taken, [9] 1 while another tick follows.  `cond` is the graph's loop
-// (or branch) condition handle, set only when `use_cond` is true.
+// ticks taken, [9] 1 while another tick follows, [10] blocks of the kick
+// launch done.  `cond` is the graph's loop condition handle, set only when
+// `use_cond` is true.
 cudaError_t launch_block_dt(const BatchView &b, int L, cudaStream_t st);  // also plans Delta t_MAX
 cudaError_t launch_block_open(const BatchView &b, int L, cudaStream_t st);
 cudaError_t launch_block_gate(const BatchView &b, int L, bool use_cond, cudaGraphConditionalHandle cond,
-                              cudaStream_t st);
-cudaError_t launch_block_tick_begin(const BatchView &b, int every, bool use_cond, cudaGraphConditionalHandle cond,
+                              cudaStream_t st);  // (opens the first tick)
+// graph form with tree reuse: sets the branch condition (rebuild this tick)
+cudaError_t launch_block_tick_begin(const BatchView &b, int every, cudaGraphConditionalHandle cond,
                                     cudaStream_t st);
-cudaError_t launch_block_drift(const BatchView &b, cudaStream_t st);
-cudaError_t launch_block_stage(const BatchView &b, int precision, cudaStream_t st);
-cudaError_t launch_block_tasks(const BatchView &b, int precision, cudaStream_t st);  // after the leaves
-cudaError_t launch_block_kick(const BatchView &b, int L, cudaStream_t st);
-cudaError_t launch_block_tick_end(const BatchView &b, int L, bool use_cond, cudaGraphConditionalHandle cond,
-                                  cudaStream_t st);
+cudaError_t launch_block_drift(const BatchView &b, cudaStream_t st);  // ahead of a sort
+// the sorted gather and the staging of the levels (drift: the tick's drift
+// too, when the order is kept)
+cudaError_t launch_block_gather(const BatchView &b, int precision, bool drift, cudaStream_t st);
+cudaError_t launch_block_tasks(const BatchView &b, int precision, cudaStream_t st);  // after the leaves (sph_pairs.cu)
+// the tick's kicks; its last block ends the tick (loop flag [9], the loop
+// condition when use_cond) and opens the next one
+cudaError_t launch_block_kick(const BatchView &b, int L, bool use_cond, cudaGraphConditionalHandle cond,
+                             cudaStream_t st);
 cudaError_t launch_block_finish(const BatchView &b, cudaStream_t st);
 cudaError_t launch_kick_close(const BatchView &b, int do_kick, int forces_ran, cudaStream_t st);
 cudaError_t launch_reset_step(const BatchView &b, int mode, cudaStream_t st);  // mode 1 full, 2 forces only
 cudaError_t launch_neighbour_export(const BatchView &b, int kind, const double *h_in, long long *offsets,
                                     int *idx, long long cap, long long *total_dev, cudaStream_t st);
+
+// Reset of one problem's per-call diagnostics: mode 1 a whole step's, mode 2
+// those of a forces-only call.
+__device__ __forceinline__ void reset_diag(const BatchView &b, int p, int mode)
+{
+    ProbDiag *d = b.prob[p].diag;
+    d->dt_min_bits = 0x7ff0000000000000ull;  // +inf
+    d->force_pairs = 0;
+    d->grav_pairs = d->grav_nodes = 0;
+    if (mode == 2) return;
+    d->wrap_leaves = 0;
+    d->mass = 0;
+    for (int a = 0; a < 3; ++a) {
+        d->mom[a] = 0;
+        d->fsum[a] = 0;
+    }
+    d->energy = 0;
+    d->dEdt = 0;
+    d->nr_iter = d->density_pairs = d->candidates = d->fallback = 0;
+    d->ngb_sum = 0;
+    d->nr_max = 0;
+    d->ngb_min = 0x7fffffff;
+    d->ngb_max = 0;
+    d->status = 0;
+    d->unconverged = 0;
+}
+
+// Clear per-call counter k (k < kNumCounters): mode 1 all of a step's,
+// mode 2 those of a forces-only call.
+__device__ __forceinline__ void reset_counter(const BatchView &b, int mode, int k)
+{
+    const bool all = (k >= kSlowCounter && k <= kForceWrapList) || k >= kTimeoutCounter;
+    const bool forces = k == kForceWrapList || k == kTimeoutCounter ||
+                        (k >= kForceCounter && k < kForceCounter + kForceClasses) ||
+                        (k >= kForceWrapCounter && k < kForceWrapCounter + kForceClasses) ||
+                        (k >= kForceCdCounter && k < kForceCdCounter + kForceClasses);
+    if (mode == 1 ? all : forces) b.counters[k] = 0;
+}
+
+// the counters of a step or forces-only call (block 0, its first kNumCounters threads)
+__device__ __forceinline__ void reset_counters(const BatchView &b, int mode)
+{
+    if (blockIdx.x == 0 && threadIdx.x < kNumCounters) reset_counter(b, mode, threadIdx.x);
+}
 
 // ---- host helpers shared by the entry points (sph_api.cu) -----------------
 // Bump allocator over a workspace (base == nullptr measures the size).

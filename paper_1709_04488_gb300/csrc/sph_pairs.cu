@@ -22,18 +22,25 @@ cudaError_t force_launches_m4(const BatchView &b, int precision, cudaStream_t st
 cudaError_t launch_density(const BatchView &b, int precision, int use_pred, cudaStream_t st)
 {
     if (b.ntot == 0) return cudaSuccess;
-    if (b.block_on) {  // block-step tick: the particles that keep their solve first
-        const unsigned grid = (unsigned)((b.ntot + 255) / 256);
-        if (precision == SPH_PREC_FP64) k_block_restage<double><<<grid, 256, 0, st>>>(b, use_pred);
-        else k_block_restage<float><<<grid, 256, 0, st>>>(b, use_pred);
+    cudaError_t e = cudaSuccess;
+    if (!b.block_on) {  // (block-step ticks: the wrap-list launch serves the tasks)
+        e = density_launches_m4(b, precision, use_pred, st);
+        if (e == cudaSuccess) e = density_launches_m6(b, precision, use_pred, st);
     }
-    cudaError_t e = density_launches_m4(b, precision, use_pred, st);
-    if (e == cudaSuccess) e = density_launches_m6(b, precision, use_pred, st);
-    if (e == cudaSuccess && (b.any_periodic || b.any_gravity)) e = density_launches_m4_wrap(b, precision, use_pred, st);
-    if (e == cudaSuccess && (b.any_periodic || b.any_gravity)) e = density_launches_m6_wrap(b, precision, use_pred, st);
+    const bool wrap = b.any_periodic || b.any_gravity || b.block_on;
+    if (e == cudaSuccess && wrap) e = density_launches_m4_wrap(b, precision, use_pred, st);
+    if (e == cudaSuccess && wrap) e = density_launches_m6_wrap(b, precision, use_pred, st);
     if (e != cudaSuccess) return e;
     if (precision == SPH_PREC_FP64) run_density_fallback<double>(b, use_pred, st);
     else run_density_fallback<float>(b, use_pred, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_tasks(const BatchView &b, int precision, cudaStream_t st)
+{
+    const unsigned grid = (unsigned)dev_info().sm_count * 4;
+    if (precision == SPH_PREC_FP64) k_block_tasks<double><<<grid, 256, 0, st>>>(b, 1);
+    else k_block_tasks<float><<<grid, 256, 0, st>>>(b, 1);
     return cudaGetLastError();
 }
 

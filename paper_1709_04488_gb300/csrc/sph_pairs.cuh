@@ -1083,16 +1083,17 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM, K>::WPB * 32, DCfg<T, LPP, UM
     extern __shared__ __align__(32) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     unsigned char *mine = smem + wib * C::per_warp;
-    // block-step ticks serve tasks (leaf << 5 | first due ordinal) instead of leaves
-    const bool tasks = b.block_on != 0;
-    const int nleaf = WRAP ? b.counters[kDensWrapList] : tasks ? b.counters[kBlockTasks] : b.counters[0];
+    // block-step ticks: the wrap-list launch serves the tick's tasks (leaf <<
+    // 5 | first due ordinal) directly; the common launch does not run
+    const bool tasks = WRAP && b.block_on;
+    const int nleaf = tasks ? b.counters[kBlockTasks] : WRAP ? b.counters[kDensWrapList] : b.counters[0];
     const int cls = lpp_log2(LPP) + (UM ? 4 : 0) + 8 * K;
     for (;;) {
         int item = 0;
         if (lane == 0) item = atomicAdd(&b.counters[(WRAP ? kDensityWrapCounter : kDensityCounter) + cls], 1);
         item = __shfl_sync(FULL, item, 0);
         if (item >= nleaf) break;
-        item = WRAP ? b.wrap_list[item] : tasks ? b.btask[item] : item;
+        if (WRAP) item = tasks ? b.btask[item] : b.wrap_list[item];
         const int leaf = tasks ? item >> 5 : item, k0 = tasks ? item & 31 : -1;
         const ProbStatic &ps = b.prob[b.leaf_pid[leaf]];
         if ((tasks ? b.block_lanes : ps.lpp) != LPP || (ps.uniform_m != 0) != UM || ps.ph.kernel != K) continue;
@@ -1761,9 +1762,10 @@ cudaError_t run_density(const BatchView &b, int use_pred, cudaStream_t st)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_density<T, LPP, UM, K, WRAP>, C::WPB * 32, C::smem);
         if (per_sm < 1) per_sm = 1;
     }
-    // the wrap-list launch serves few leaves (mostly none) unless a problem has gravity
-    k_density<T, LPP, UM, K, WRAP><<<dev_info().sm_count * (WRAP && !b.any_gravity ? 1 : per_sm), C::WPB * 32, C::smem,
-                                     st>>>(b, use_pred);
+    // the wrap-list launch serves few leaves (mostly none) unless a problem
+    // has gravity or the launch is a block-step tick's
+    k_density<T, LPP, UM, K, WRAP><<<dev_info().sm_count * (WRAP && !b.any_gravity && !b.block_on ? 1 : per_sm),
+                                     C::WPB * 32, C::smem, st>>>(b, use_pred);
     return cudaGetLastError();
 }
 
@@ -1779,16 +1781,32 @@ void run_density_fallback(const BatchView &b, int use_pred, cudaStream_t st)
     k_density_fallback<T><<<dev_info().sm_count * 4, C::WPB * 32, C::smem, st>>>(b, use_pred);
 }
 
-// Block-step ticks: every particle whose step does not end now keeps the h,
-// rho, Omega, P and c of its last solve; restaged here (with its drifted
-// offsets and predicted v, u) for the force pass.
+// Block-step ticks, after the leaves: each leaf with particles whose step
+// ends now gives one task per 32 / block_lanes of them (in sorted order), so
+// that a task's block_lanes lanes per particle and its box (of those
+// particles only) keep the pair kernels' latency short when few particles of
+// a leaf are due; the leaf's other particles keep the h, rho, Omega, P and c
+// of their last solve and are restaged here (with their drifted offsets and
+// predicted v, u) for the force pass.  One warp per leaf (<= 32 particles).
 template <typename T>
-__global__ void __launch_bounds__(256) k_block_restage(BatchView b, int use_pred)
+__global__ void __launch_bounds__(256) k_block_tasks(BatchView b, int use_pred)
 {
     using V = typename Vec4<T>::type;
-    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= b.ntot || ((const T *)b.slev)[s] > T(0)) return;
-    density_epilogue<T>(b, b.prob[0], s, ((const V *)b.pm)[s], T(1), T(0), T(0), use_pred, T(0));
+    const int lane = threadIdx.x & 31;
+    const int nleaf = b.counters[0];
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int leaf = w; leaf < nleaf; leaf += nw) {
+        const int st = b.leaf_start[leaf], n = b.leaf_start[leaf + 1] - st;
+        const long long s = st + (lane < n ? lane : 0);
+        const bool due = lane < n && ((const T *)b.slev)[s] > T(0);
+        const int d = __popc(__ballot_sync(FULL, due));
+        const int size = 32 / b.block_lanes, nt = (d + size - 1) / size;
+        int base = 0;
+        if (lane == 0 && nt > 0) base = atomicAdd(&b.counters[kBlockTasks], nt);
+        base = __shfl_sync(FULL, base, 0);
+        if (lane < nt) b.btask[base + lane] = (leaf << 5) | (lane * size);
+        if (lane < n && !due) density_epilogue<T>(b, b.prob[0], s, ((const V *)b.pm)[s], T(1), T(0), T(0), use_pred, T(0));
+    }
 }
 
 template <typename T, int LPP, int K, bool WRAP, bool CD = false>

@@ -1,9 +1,14 @@
 """GPU parity of hierarchical block time-steps (Sec. 2.1.4) with the Saitoh &
 Makino limiter against the FP64 oracle's block step: the same levels and
 force evaluations (every decision is taken on integer levels from the same
-step lengths), and the state after one block step within the path's
-tolerance (FP64 path 1e-10 of the scale, mixed 5e-4 -- several drifts,
-density solves and kicks compound the per-evaluation 1e-4)."""
+step lengths), and the state after a block step within the norms of one
+evaluation: mixed rho 1e-5 relative, a 1e-4 of rms |a|, v and u 1e-5 of
+their largest magnitude; FP64 1e-12 relative.  Measured on the Sedov blast
+of 16^3 (mixed / FP64, largest over the particles): after one block of 1
+level (2 ticks) rho 3.4e-7 / 1.9e-14, a 7.0e-6 / 2.5e-13 of rms; after 5
+levels (32 ticks) rho 3.4e-7 / 5.5e-14, a 6.8e-6 / 1.4e-12, v 2.8e-7 /
+8.7e-14, u 9.9e-8 / 6.8e-14 -- the error does not grow with the ticks
+beyond the FP64 force sums' 1e-12 (bounded at 1e-11 after 32 ticks)."""
 import numpy as np
 import pytest
 
@@ -50,11 +55,18 @@ def _scale_err(g, ref, f):
     return np.max(np.abs(g[f] - r)) / max(np.max(np.abs(r)), 1e-300)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_sedov_block_step_matches_oracle(S, oracle_mod, prec):
+def _a_err(g, ref):
+    ra = np.stack([ref.ax, ref.ay, ref.az], 1)
+    ga = np.stack([g["ax"], g["ay"], g["az"]], 1)
+    return np.max(np.linalg.norm(ga - ra, axis=1)) / np.sqrt(np.mean(np.sum(ra ** 2, 1)))
+
+
+@pytest.mark.parametrize("prec,L", [("fp64", 1), ("mixed", 1), ("fp64", 5), ("mixed", 5)])
+def test_sedov_block_step_matches_oracle(S, oracle_mod, prec, L):
+    """One level (two ticks) and five levels (32 ticks) at the norms of one
+    evaluation (FP64 forces after 32 ticks: 1e-11, see the module notes)."""
     O = oracle_mod
     a, p = ics.sedov(16)
-    L = 5
     ref, lv_ref, oo = _oracle_block(O, a, p, L)
     fp64 = prec == "fp64"
     prob, go = _gpu_block(S, a, p, S.PREC_FP64 if fp64 else S.PREC_MIXED, L)
@@ -62,17 +74,19 @@ def test_sedov_block_step_matches_oracle(S, oracle_mod, prec):
     assert np.array_equal(lv, lv_ref)
     assert go[0][0] == pytest.approx(oo[0][0], rel=1e-12 if fp64 else 1e-5)
     assert go[0][1] == oo[0][1]  # the same particle force evaluations
-    assert lv.max() >= 3 and go[0][1] < len(a["x"]) * 2 ** L / 4
+    if L == 5:
+        assert lv.max() >= 3 and go[0][1] < len(a["x"]) * 2 ** L / 4
     g = prob.numpy()
-    tol = 1e-10 if fp64 else 5e-4
+    tol = 1e-12 if fp64 else 1e-5
     for f in ("vx", "vy", "vz", "u"):
         assert _scale_err(g, ref, f) < tol, f
     L_box = np.asarray(p["box_len"])
     for k, f in enumerate(("x", "y", "z")):
         d = np.abs(g[f] - getattr(ref, f))
         d = np.minimum(d, L_box[k] - d)
-        assert np.max(d) < (1e-10 if fp64 else 1e-6), f
-    assert np.max(np.abs(g["rho"] / ref.rho - 1.0)) < (1e-10 if fp64 else 1e-4)
+        assert np.max(d) < (1e-12 if fp64 else 1e-6), f
+    assert np.max(np.abs(g["rho"] / ref.rho - 1.0)) < (1e-12 if fp64 else 1e-5)
+    assert _a_err(g, ref) < ((1e-12 if L == 1 else 1e-11) if fp64 else 1e-4)
 
 
 def test_block_step_with_tree_reuse_matches_oracle(S, oracle_mod):
