@@ -37,7 +37,7 @@ def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
     deps = [src, os.path.join(CSRC, "sph_internal.cuh"), os.path.join(CSRC, "sph_tuned.h"),
-            os.path.join(CSRC, "sph_pairs.cuh"), os.path.join(ROOT, "include", "sph.h")]
+            os.path.join(CSRC, "sph_pairs.cuh"), os.path.join(CSRC, "sph_leaf.cuh"), os.path.join(ROOT, "include", "sph.h")]
     t = os.path.getmtime(obj)
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 

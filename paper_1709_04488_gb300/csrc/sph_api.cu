@@ -643,17 +643,18 @@ static int enqueue_block_leaves(const BatchView &b, int prec, bool rebuild, cuda
         CU(launch_block_drift(b, st));
         CU(launch_domain_and_keys(b, st));
         CU(launch_radix_sort(b, st));
+        CU(launch_block_gather(b, prec, st));  // (also which particles end their step now)
+        CU(launch_build_leaves(b, prec, st));
+        CU(launch_block_tasks(b, prec, st));  // (and the restaging of the particles that keep their solve)
+    } else {
+        CU(launch_block_leaf_tick(b, prec, st));  // drift, gather, leaf boxes, tasks and restaging
     }
-    CU(launch_block_gather(b, prec, !rebuild, st));  // (also which particles end their step now)
-    if (rebuild) CU(launch_build_leaves(b, prec, st));
-    else CU(launch_update_leaves(b, prec, st));
     return SPH_OK;
 }
 
 static int enqueue_block_passes(const BatchView &b, int prec, int L, bool use_cond, cudaGraphConditionalHandle loop,
                                 cudaStream_t st)
 {
-    CU(launch_block_tasks(b, prec, st));  // (and the restaging of the particles that keep their solve)
     CU(launch_density(b, prec, 1, st));  // solves the particles whose step ends
     CU(launch_refit(b, prec, st));
     CU(launch_forces(b, prec, st));

@@ -22,6 +22,7 @@
 // graph loop whose condition the last kernel of each tick sets: no host round
 // trip between ticks.
 #include "sph_internal.cuh"
+#include "sph_leaf.cuh"
 
 namespace sph {
 
@@ -59,7 +60,6 @@ __device__ __forceinline__ double particle_dt(const ProbStatic &ps, long long i)
     return d;
 }
 
-__device__ __forceinline__ double kick(double v, double a, double d) { return __dadd_rn(v, __dmul_rn(a, d)); }
 
 // half of `ticks` ticks of length tau
 __device__ __forceinline__ double half_ticks(long long ticks, double tau)
@@ -142,11 +142,11 @@ __global__ void __launch_bounds__(kBlockThreads) k_block_open(BatchView b, int L
         t1 = b.bt1[g];
         const double hd = half_ticks(t1, tau);
         const long long n = b.ntot;
-        b.bvh[g] = kick(ps.vx[i], ps.ax[i], hd);
-        b.bvh[n + g] = kick(ps.vy[i], ps.ay[i], hd);
-        b.bvh[2 * n + g] = kick(ps.vz[i], ps.az[i], hd);
-        b.bvh[3 * n + g] = ps.ph.eos == SPH_EOS_ADIABATIC ? kick(ps.u[i], ps.du[i], hd) : ps.u[i];
-        b.bvh[4 * n + g] = ps.ph.av_switch ? kick(ps.alpha[i], ps.dalpha[i], hd) : 0.0;
+        b.bvh[g] = block_kick(ps.vx[i], ps.ax[i], hd);
+        b.bvh[n + g] = block_kick(ps.vy[i], ps.ay[i], hd);
+        b.bvh[2 * n + g] = block_kick(ps.vz[i], ps.az[i], hd);
+        b.bvh[3 * n + g] = ps.ph.eos == SPH_EOS_ADIABATIC ? block_kick(ps.u[i], ps.du[i], hd) : ps.u[i];
+        b.bvh[4 * n + g] = ps.ph.av_switch ? block_kick(ps.alpha[i], ps.dalpha[i], hd) : 0.0;
     }
     next_event(b, t1);
 }
@@ -193,36 +193,6 @@ __global__ void k_block_tick_begin(BatchView b, int every, cudaGraphConditionalH
     cudaGraphSetConditional(cond, b.scratch64[8] % every == 0 ? 1u : 0u);
 }
 
-// drift particle g (original order) from tick k0 to tick k1 and predict
-// its v, u and alpha at k1 for the force pass; true if its step ends at k1
-__device__ __forceinline__ bool drift_one(const BatchView &b, long long g, long long k0, long long k1, double tau)
-{
-    const ProbStatic &ps = b.prob[0];
-    const PhysParams &ph = ps.ph;
-    const long long i = g - ps.base, n = b.ntot;
-    const double dk = __dmul_rn((double)(k1 - k0), tau);
-    double *X[3] = {ps.x, ps.y, ps.z};
-    const double *A[3] = {ps.ax, ps.ay, ps.az};
-    double *VP[3] = {b.vpx, b.vpy, b.vpz};
-    const int t0 = b.bt0[g], t1 = b.bt1[g];
-    const double dp = __dmul_rn(__dmul_rn((double)(2 * k1 - t0 - t1), 0.5), tau);  // t - t_mid
-    for (int a = 0; a < 3; ++a) {
-        const double vh = b.bvh[a * n + g];
-        double x = __dadd_rn(X[a][i], __dmul_rn(vh, dk));
-        if (ph.periodic) {
-            const double lo = ph.box_lo[a], Lb = ph.box_len[a];
-            if (x >= lo + Lb) x -= Lb;
-            else if (x < lo) x += Lb;
-        }
-        X[a][i] = x;
-        VP[a][g] = kick(vh, A[a][i], dp);
-    }
-    b.up[g] = ph.eos == SPH_EOS_ADIABATIC ? kick(b.bvh[3 * n + g], ps.du[i], dp) : ps.u[i];
-    if (ph.av_switch) b.ap[g] = kick(b.bvh[4 * n + g], ps.dalpha[i], dp);
-    b.breq[g] = -1;
-    return t1 == k1;
-}
-
 __device__ __forceinline__ void count_due(const BatchView &b, bool due)
 {
     const unsigned m = __ballot_sync(0xffffffffu, due);
@@ -237,20 +207,17 @@ __global__ void __launch_bounds__(kBlockThreads) k_block_drift(BatchView b)
     count_due(b, due);
 }
 
-// sorted particle s: (with DRIFT, its drift first, when the leaves are kept
-// and so is the order) the gather of position, mass and h into sorted order
-// and the staging of its level for the force pass: +(level + 1) where the
-// step ends at tick k1, -(level + 1) elsewhere
-template <typename T, bool DRIFT>
+// sorted particle s (after a new sort): the gather of position, mass and h
+// into sorted order and the staging of its level for the force pass:
+// +(level + 1) where the step ends at tick k1, -(level + 1) elsewhere
+template <typename T>
 __global__ void __launch_bounds__(kBlockThreads) k_block_gather(BatchView b)
 {
     const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long k1 = b.scratch64[5];
-    bool due = false;
     if (s < b.ntot) {
         const ProbStatic &ps = b.prob[0];
         const long long g = b.perm[s], i = g - ps.base;
-        if (DRIFT) due = drift_one(b, g, b.scratch64[4], k1, bits_d(b.scratch64[7]));
         b.sx[s] = ps.x[i];
         b.sy[s] = ps.y[i];
         b.sz[s] = ps.z[i];
@@ -259,7 +226,6 @@ __global__ void __launch_bounds__(kBlockThreads) k_block_gather(BatchView b)
         const T v = (T)(b.blev[g] + 1);
         ((T *)b.slev)[s] = b.bt1[g] == k1 ? v : -v;
     }
-    if (DRIFT) count_due(b, due);
 }
 
 // after the force pass at tick k: closing half kick of the active particles
@@ -283,9 +249,9 @@ __global__ void __launch_bounds__(kBlockThreads) k_block_kick(BatchView b, int L
         int t0 = b.bt0[g], t1 = b.bt1[g], lev = b.blev[g];
         if (t1 == k) {
             const double hd = half_ticks(t1 - t0, tau);
-            for (int a = 0; a < 3; ++a) V[a][i] = kick(b.bvh[a * n + g], A[a][i], hd);
-            if (adi) ps.u[i] = kick(b.bvh[3 * n + g], ps.du[i], hd);
-            if (ph.av_switch) ps.alpha[i] = kick(b.bvh[4 * n + g], ps.dalpha[i], hd);
+            for (int a = 0; a < 3; ++a) V[a][i] = block_kick(b.bvh[a * n + g], A[a][i], hd);
+            if (adi) ps.u[i] = block_kick(b.bvh[3 * n + g], ps.du[i], hd);
+            if (ph.av_switch) ps.alpha[i] = block_kick(b.bvh[4 * n + g], ps.dalpha[i], hd);
             if (k < N) {
                 int l = level_of(particle_dt(ps, i), dtmax, L);
                 const int lim = b.bnml[g] - ph.block_gap;
@@ -296,9 +262,9 @@ __global__ void __launch_bounds__(kBlockThreads) k_block_kick(BatchView b, int L
                 t0 = (int)k;
                 t1 = (int)(k + (N >> l));
                 const double hn = half_ticks(N >> l, tau);
-                for (int a = 0; a < 3; ++a) b.bvh[a * n + g] = kick(V[a][i], A[a][i], hn);
-                b.bvh[3 * n + g] = adi ? kick(ps.u[i], ps.du[i], hn) : ps.u[i];
-                if (ph.av_switch) b.bvh[4 * n + g] = kick(ps.alpha[i], ps.dalpha[i], hn);
+                for (int a = 0; a < 3; ++a) b.bvh[a * n + g] = block_kick(V[a][i], A[a][i], hn);
+                b.bvh[3 * n + g] = adi ? block_kick(ps.u[i], ps.du[i], hn) : ps.u[i];
+                if (ph.av_switch) b.bvh[4 * n + g] = block_kick(ps.alpha[i], ps.dalpha[i], hn);
             }
         } else {
             const int rq = b.breq[g];
@@ -307,9 +273,9 @@ __global__ void __launch_bounds__(kBlockThreads) k_block_kick(BatchView b, int L
                 const long long ke = (k / stp + 1) * stp;  // next tick on the new level's grid
                 if (ke < t1) {
                     const double corr = half_ticks(ke - t1, tau);
-                    for (int a = 0; a < 3; ++a) b.bvh[a * n + g] = kick(b.bvh[a * n + g], A[a][i], corr);
-                    if (adi) b.bvh[3 * n + g] = kick(b.bvh[3 * n + g], ps.du[i], corr);
-                    if (ph.av_switch) b.bvh[4 * n + g] = kick(b.bvh[4 * n + g], ps.dalpha[i], corr);
+                    for (int a = 0; a < 3; ++a) b.bvh[a * n + g] = block_kick(b.bvh[a * n + g], A[a][i], corr);
+                    if (adi) b.bvh[3 * n + g] = block_kick(b.bvh[3 * n + g], ps.du[i], corr);
+                    if (ph.av_switch) b.bvh[4 * n + g] = block_kick(b.bvh[4 * n + g], ps.dalpha[i], corr);
                     t1 = (int)ke;
                     lev = rq;
                 }
@@ -398,16 +364,11 @@ cudaError_t launch_block_drift(const BatchView &b, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_block_gather(const BatchView &b, int precision, bool drift, cudaStream_t st)
+cudaError_t launch_block_gather(const BatchView &b, int precision, cudaStream_t st)
 {
     const unsigned grid = blocks_for(b.ntot);
-    if (precision == SPH_PREC_FP64) {
-        if (drift) k_block_gather<double, true><<<grid, kBlockThreads, 0, st>>>(b);
-        else k_block_gather<double, false><<<grid, kBlockThreads, 0, st>>>(b);
-    } else {
-        if (drift) k_block_gather<float, true><<<grid, kBlockThreads, 0, st>>>(b);
-        else k_block_gather<float, false><<<grid, kBlockThreads, 0, st>>>(b);
-    }
+    if (precision == SPH_PREC_FP64) k_block_gather<double><<<grid, kBlockThreads, 0, st>>>(b);
+    else k_block_gather<float><<<grid, kBlockThreads, 0, st>>>(b);
     return cudaGetLastError();
 }
 

@@ -356,10 +356,11 @@ cudaError_t launch_block_gate(const BatchView &b, int L, bool use_cond, cudaGrap
 cudaError_t launch_block_tick_begin(const BatchView &b, int every, cudaGraphConditionalHandle cond,
                                     cudaStream_t st);
 cudaError_t launch_block_drift(const BatchView &b, cudaStream_t st);  // ahead of a sort
-// the sorted gather and the staging of the levels (drift: the tick's drift
-// too, when the order is kept)
-cudaError_t launch_block_gather(const BatchView &b, int precision, bool drift, cudaStream_t st);
+// after a new sort: the sorted gather and the staging of the levels
+cudaError_t launch_block_gather(const BatchView &b, int precision, cudaStream_t st);
 cudaError_t launch_block_tasks(const BatchView &b, int precision, cudaStream_t st);  // after the leaves (sph_pairs.cu)
+// a tick that keeps the order and the leaves: drift, gather, leaf boxes and tasks in one pass (sph_pairs.cu)
+cudaError_t launch_block_leaf_tick(const BatchView &b, int precision, cudaStream_t st);
 // the tick's kicks; its last block ends the tick (loop flag [9], the loop
 // condition when use_cond) and opens the next one
 cudaError_t launch_block_kick(const BatchView &b, int L, bool use_cond, cudaGraphConditionalHandle cond,

@@ -44,6 +44,14 @@ cudaError_t launch_block_tasks(const BatchView &b, int precision, cudaStream_t s
     return cudaGetLastError();
 }
 
+cudaError_t launch_block_leaf_tick(const BatchView &b, int precision, cudaStream_t st)
+{
+    const unsigned grid = (unsigned)dev_info().sm_count * 8;
+    if (precision == SPH_PREC_FP64) k_block_leaf_tick<double, dbl4><<<grid, 256, 0, st>>>(b, 1);
+    else k_block_leaf_tick<float, float4><<<grid, 256, 0, st>>>(b, 1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_forces(const BatchView &b, int precision, cudaStream_t st)
 {
     if (b.ntot == 0) return cudaSuccess;

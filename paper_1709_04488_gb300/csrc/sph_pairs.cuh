@@ -25,6 +25,7 @@
 //              which keeps sum_i m_i a_i near FP64 round-off.
 #pragma once
 #include "sph_internal.cuh"
+#include "sph_leaf.cuh"
 #include "sph_tuned.h"
 
 namespace sph {
@@ -1786,12 +1787,27 @@ void run_density_fallback(const BatchView &b, int use_pred, cudaStream_t st)
 // that a task's block_lanes lanes per particle and its box (of those
 // particles only) keep the pair kernels' latency short when few particles of
 // a leaf are due; the leaf's other particles keep the h, rho, Omega, P and c
-// of their last solve and are restaged here (with their drifted offsets and
-// predicted v, u) for the force pass.  One warp per leaf (<= 32 particles).
+// of their last solve and are restaged (with their drifted offsets and
+// predicted v, u) for the force pass.  One warp per leaf (<= 32 particles),
+// lane = position in the leaf.
+template <typename T>
+__device__ __forceinline__ void block_tasks_one(const BatchView &b, int leaf, int n, long long s, bool due, int use_pred)
+{
+    using V = typename Vec4<T>::type;
+    const int lane = threadIdx.x & 31;
+    const int d = __popc(__ballot_sync(FULL, due));
+    const int size = 32 / b.block_lanes, nt = (d + size - 1) / size;
+    int base = 0;
+    if (lane == 0 && nt > 0) base = atomicAdd(&b.counters[kBlockTasks], nt);
+    base = __shfl_sync(FULL, base, 0);
+    if (lane < nt) b.btask[base + lane] = (leaf << 5) | (lane * size);
+    if (lane < n && !due) density_epilogue<T>(b, b.prob[0], s, ((const V *)b.pm)[s], T(1), T(0), T(0), use_pred, T(0));
+}
+
+// the tasks of a tick that built its leaves
 template <typename T>
 __global__ void __launch_bounds__(256) k_block_tasks(BatchView b, int use_pred)
 {
-    using V = typename Vec4<T>::type;
     const int lane = threadIdx.x & 31;
     const int nleaf = b.counters[0];
     const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
@@ -1799,13 +1815,47 @@ __global__ void __launch_bounds__(256) k_block_tasks(BatchView b, int use_pred)
         const int st = b.leaf_start[leaf], n = b.leaf_start[leaf + 1] - st;
         const long long s = st + (lane < n ? lane : 0);
         const bool due = lane < n && ((const T *)b.slev)[s] > T(0);
-        const int d = __popc(__ballot_sync(FULL, due));
-        const int size = 32 / b.block_lanes, nt = (d + size - 1) / size;
-        int base = 0;
-        if (lane == 0 && nt > 0) base = atomicAdd(&b.counters[kBlockTasks], nt);
-        base = __shfl_sync(FULL, base, 0);
-        if (lane < nt) b.btask[base + lane] = (leaf << 5) | (lane * size);
-        if (lane < n && !due) density_epilogue<T>(b, b.prob[0], s, ((const V *)b.pm)[s], T(1), T(0), T(0), use_pred, T(0));
+        block_tasks_one<T>(b, leaf, n, s, due, use_pred);
+    }
+}
+
+// A tick that keeps the order and the leaves (tree reuse, Sec. 4.2), one
+// warp per leaf: the drift of its particles, their gather into sorted order
+// and the staging of their levels, the leaf's offsets and boxes and the tree
+// above it (as the leaf pass does for kept leaves), then its tasks and the
+// restaging of its particles that keep their solve: one pass instead of four.
+template <typename T, typename T4>
+__global__ void __launch_bounds__(256) k_block_leaf_tick(BatchView b, int use_pred)
+{
+    const int lane = threadIdx.x & 31;
+    const int nleaf = b.counters[0];
+    if (blockIdx.x == 0)
+        for (int p = threadIdx.x; p < b.nprob; p += blockDim.x) b.dyn[p].lists_stale = 0;
+    const long long k0 = b.scratch64[4], k1 = b.scratch64[5];
+    const double tau = __longlong_as_double(b.scratch64[7]);
+    const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+    for (int leaf = w; leaf < nleaf; leaf += nw) {
+        const int st = b.leaf_start[leaf], n = b.leaf_start[leaf + 1] - st;
+        const long long s = st + (lane < n ? lane : 0);
+        bool due = false;
+        if (lane < n) {
+            const ProbStatic &ps = b.prob[0];
+            const long long g = b.perm[s], i = g - ps.base;
+            due = drift_one(b, g, k0, k1, tau);
+            b.sx[s] = ps.x[i];
+            b.sy[s] = ps.y[i];
+            b.sz[s] = ps.z[i];
+            b.sm[s] = ps.m[i];
+            b.sh[s] = ps.h[i];
+            const T v = (T)(b.blev[g] + 1);
+            ((T *)b.slev)[s] = due ? v : -v;
+        }
+        const unsigned dm = __ballot_sync(FULL, due);
+        if (lane == 0 && dm) atomicAdd((unsigned long long *)&b.scratch64[3], (unsigned long long)__popc(dm));
+        __syncwarp();  // the leaf's gathered particles visible to the whole warp
+        leaf_props_one<T4, true>(b, leaf);
+        __syncwarp();
+        block_tasks_one<T>(b, leaf, n, s, due, use_pred);
     }
 }
 
