@@ -613,21 +613,27 @@ static int finish_call(sph_ctx *c)
 
 // ---- block time-steps (Sec. 2.1.4) -----------------------------------------
 // One block step: Delta t_MAX and the opening kicks, then one tick per event
-// (a tick where some particle's step ends), then the conservation sums.  The
-// schedule lives on the device; on a capturable stream the ticks are the body
-// of a graph loop (a conditional while node) whose condition the last kernel
-// of each tick sets, so no host round trip separates them.
+// (a tick where some particle's step ends) before 2^L, then the last tick at
+// 2^L (every particle due), then the conservation sums.  The schedule lives
+// on the device; on a capturable stream the ticks before 2^L are the body of
+// a graph loop (a conditional while node) and the last tick a conditional
+// branch, whose conditions the last block of each tick's kick sets, so no
+// host round trip separates the ticks.
 
-static BatchView block_view(const sph_ctx *c)
+// tasks: the ticks before 2^L, whose pair kernels serve tasks of up to 32 /
+// block_lanes particles whose step ends, block_lanes lanes each; else the
+// last tick, whose pair kernels serve whole leaves (as a global step's do)
+static BatchView block_view(const sph_ctx *c, bool tasks = true)
 {
     BatchView b = c->bv;
     b.block_on = 1;
+    b.block_tasks = tasks ? 1 : 0;
     b.any_general = 1;  // the active particles' forces run in the wrap-list launch
-    // the pair kernels serve tasks of up to 32 / block_lanes particles whose
-    // step ends, block_lanes lanes each
     b.block_lanes = c->prm.precision == SPH_PREC_FP64 ? kBlockLanesF64 : kBlockLanesF32;
-    b.lpp_mask = mask_of(b.block_lanes, c->prm.kernel);
-    b.dens_mask = dens_class_bit(b.block_lanes, c->host_ps.uniform_m, c->prm.kernel);
+    if (tasks) {
+        b.lpp_mask = mask_of(b.block_lanes, c->prm.kernel);
+        b.dens_mask = dens_class_bit(b.block_lanes, c->host_ps.uniform_m, c->prm.kernel);
+    }
     return b;
 }
 
@@ -653,34 +659,50 @@ static int enqueue_block_leaves(const BatchView &b, int prec, bool rebuild, cuda
 }
 
 static int enqueue_block_passes(const BatchView &b, int prec, int L, bool use_cond, cudaGraphConditionalHandle loop,
-                                cudaStream_t st)
+                                cudaGraphConditionalHandle fin, cudaStream_t st)
 {
     CU(launch_density(b, prec, 1, st));  // solves the particles whose step ends
     CU(launch_refit(b, prec, st));
     CU(launch_forces(b, prec, st));
     launch_gravity(b, prec, st);  // the long range of the active particles
     CU(cudaGetLastError());
-    CU(launch_block_kick(b, L, use_cond, loop, st));  // (its last block ends the tick, opens the next)
+    CU(launch_block_kick(b, L, use_cond, loop, fin, st));  // (its last block ends the tick, opens the next)
     return SPH_OK;
 }
 
-// the legacy default stream: the host reads the loop flag after every tick
-static int block_step_eager(sph_ctx *c, const BatchView &b)
+// the last tick (2^L, every particle due): sort and leaves built afresh (the
+// next block starts from them), whole leaves in the pair kernels
+static int enqueue_block_last(const BatchView &bl, int prec, int L, cudaStream_t st)
+{
+    CU(launch_block_drift(bl, st));
+    CU(launch_domain_and_keys(bl, st));
+    CU(launch_radix_sort(bl, st));
+    CU(launch_block_gather(bl, prec, st));
+    CU(launch_build_leaves(bl, prec, st));
+    return enqueue_block_passes(bl, prec, L, false, 0, 0, st);
+}
+
+// the legacy default stream: the host reads the flags after every tick
+static int block_step_eager(sph_ctx *c, const BatchView &b, const BatchView &bl)
 {
     const int L = c->prm.block_levels, prec = c->prm.precision, every = block_every(c);
     cudaStream_t st = c->stream;
     CU(launch_block_dt(b, L, st));
     CU(launch_block_open(b, L, st));
-    CU(launch_block_gate(b, L, false, 0, st));
+    CU(launch_block_gate(b, L, false, 0, 0, st));
+    long long fl[3] = {0, 0, 0};  // [9] loop, [10], [11] last tick
     for (long long tick = 0;; ++tick) {
-        long long go = 0;
-        CU(cudaMemcpyAsync(&go, b.scratch64 + 9, sizeof go, cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(fl, b.scratch64 + 9, sizeof fl, cudaMemcpyDeviceToHost, st));
         CU(cudaStreamSynchronize(st));
-        if (!go) break;
+        if (!fl[0]) break;
         if (tick >= (1LL << L)) return fail(SPH_ECUDA, "block step: more than 2^L ticks");
         int rc = enqueue_block_leaves(b, prec, tick % every == 0, st);
         if (rc) return rc;
-        rc = enqueue_block_passes(b, prec, L, false, 0, st);
+        rc = enqueue_block_passes(b, prec, L, false, 0, 0, st);
+        if (rc) return rc;
+    }
+    if (fl[2]) {
+        int rc = enqueue_block_last(bl, prec, L, st);
         if (rc) return rc;
     }
     CU(launch_kick_close(b, 0, 1, st));  // conservation sums of the synchronised state
@@ -730,8 +752,8 @@ static int end_body_capture(cudaStream_t s, int rc)
 }
 
 // one tick into the loop body (stream s2; s3 captures the branches)
-static int capture_tick(const sph_ctx *c, const BatchView &b, cudaGraphConditionalHandle loop, cudaStream_t s2,
-                        cudaStream_t s3)
+static int capture_tick(const sph_ctx *c, const BatchView &b, cudaGraphConditionalHandle loop,
+                        cudaGraphConditionalHandle fin, cudaStream_t s2, cudaStream_t s3)
 {
     const int L = c->prm.block_levels, prec = c->prm.precision, every = block_every(c);
     cudaGraphConditionalHandle rb = 0;
@@ -755,33 +777,39 @@ static int capture_tick(const sph_ctx *c, const BatchView &b, cudaGraphCondition
         int rc = enqueue_block_leaves(b, prec, true, s2);
         if (rc) return rc;
     }
-    return enqueue_block_passes(b, prec, L, true, loop, s2);
+    return enqueue_block_passes(b, prec, L, true, loop, fin, s2);
 }
 
-static int capture_block(const sph_ctx *c, const BatchView &b, cudaStream_t s2, cudaStream_t s3)
+static int capture_block(const sph_ctx *c, const BatchView &b, const BatchView &bl, cudaStream_t s2, cudaStream_t s3)
 {
-    const int L = c->prm.block_levels;
+    const int L = c->prm.block_levels, prec = c->prm.precision;
     cudaStream_t st = c->stream;
     cudaGraph_t g = nullptr;
     int rc = capture_graph(st, &g);
     if (rc) return rc;
-    cudaGraphConditionalHandle loop = 0;
+    cudaGraphConditionalHandle loop = 0, fin = 0;
     CU(cudaGraphConditionalHandleCreate(&loop, g, 0, cudaGraphCondAssignDefault));
+    CU(cudaGraphConditionalHandleCreate(&fin, g, 0, cudaGraphCondAssignDefault));
     CU(launch_block_dt(b, L, st));
     CU(launch_block_open(b, L, st));
-    CU(launch_block_gate(b, L, true, loop, st));
+    CU(launch_block_gate(b, L, true, loop, fin, st));
     cudaGraph_t *body = nullptr;
     rc = add_conditional(st, loop, cudaGraphCondTypeWhile, 1, &body);
     if (rc) return rc;
     CU(cudaStreamBeginCaptureToGraph(s2, body[0], nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    rc = end_body_capture(s2, capture_tick(c, b, loop, s2, s3));
+    rc = end_body_capture(s2, capture_tick(c, b, loop, fin, s2, s3));
+    if (rc) return rc;
+    rc = add_conditional(st, fin, cudaGraphCondTypeIf, 1, &body);  // the last tick
+    if (rc) return rc;
+    CU(cudaStreamBeginCaptureToGraph(s2, body[0], nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    rc = end_body_capture(s2, enqueue_block_last(bl, prec, L, s2));
     if (rc) return rc;
     CU(launch_kick_close(b, 0, 1, st));  // conservation sums of the synchronised state
     CU(launch_block_finish(b, st));
     return SPH_OK;
 }
 
-static int build_block_graph(sph_ctx *c, const BatchView &b)
+static int build_block_graph(sph_ctx *c, const BatchView &b, const BatchView &bl)
 {
     cudaStream_t s2 = nullptr, s3 = nullptr;
     CU(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
@@ -794,7 +822,7 @@ static int build_block_graph(sph_ctx *c, const BatchView &b)
     cudaGraph_t g = nullptr;
     e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        rc = capture_block(c, b, s2, s3);
+        rc = capture_block(c, b, bl, s2, s3);
         for (cudaStream_t s : {s3, s2}) {  // a capture left open by a failure
             cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
             if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
@@ -843,14 +871,14 @@ int sph_block_step(sph_ctx *c, double *dtmax_out, int64_t *evals_out)
     if (!c->have_forces) return fail(SPH_EINVAL, "sph_block_step needs a force evaluation first");
     if (c->n == 0) return SPH_OK;
     clear_ran(c);
-    const BatchView b = block_view(c);
+    const BatchView b = block_view(c), bl = block_view(c, false);
     cudaStream_t st = c->stream;
     if (st == nullptr) {
-        int rc = block_step_eager(c, b);  // the legacy default stream cannot be captured
+        int rc = block_step_eager(c, b, bl);  // the legacy default stream cannot be captured
         if (rc) return rc;
     } else {
         if (!c->block_graph) {
-            int rc = build_block_graph(c, b);
+            int rc = build_block_graph(c, b, bl);
             if (rc) return rc;
         }
         CU(cudaGraphLaunch(c->block_graph, st));
@@ -873,7 +901,7 @@ int sph_block_prepare(sph_ctx *c)
     if (!c) return fail(SPH_EINVAL, "ctx is NULL");
     if (c->prm.block_levels <= 0 || !c->bv.blev) return fail(SPH_EINVAL, "the context was set up without block_levels");
     if (c->stream == nullptr || c->block_graph || c->n == 0) return SPH_OK;
-    return build_block_graph(c, block_view(c));
+    return build_block_graph(c, block_view(c), block_view(c, false));
 }
 
 int sph_block_levels(sph_ctx *c, int32_t *levels)

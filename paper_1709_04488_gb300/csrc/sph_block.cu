@@ -79,6 +79,7 @@ __global__ void k_block_init(BatchView b)
     b.scratch64[8] = 0;                           // ticks taken
     b.scratch64[9] = 0;
     b.scratch64[10] = 0;                          // kick blocks done
+    b.scratch64[11] = 0;
 }
 
 __global__ void __launch_bounds__(kBlockThreads) k_block_dt(BatchView b)
@@ -166,23 +167,37 @@ __device__ __forceinline__ void open_tick(const BatchView &b)
     }
 }
 
-// the loop's gate before the first tick: the first event tick must lie in
-// (0, 2^L] and nothing may have failed; opens the first tick
-__global__ void __launch_bounds__(128) k_block_gate(BatchView b, int L, int use_cond, cudaGraphConditionalHandle cond)
+// after a tick (or before the first): the next tick opens if nothing failed
+// and the next event tick lies after the current one and at most 2^L; the
+// ticks before 2^L run as the loop, the tick at 2^L (every particle due)
+// after it
+__device__ __forceinline__ void schedule_next(const BatchView &b, long long k, long long N, int use_cond,
+                                              cudaGraphConditionalHandle cond, cudaGraphConditionalHandle fin,
+                                              int *go_s)
+{
+    ProbDiag *d = b.prob[0].diag;
+    const long long next = *(volatile long long *)&b.scratch64[2];
+    bool go = *(volatile unsigned *)&d->status == 0 && k < N && b.scratch64[8] < N;
+    if (go && !(next > k && next <= N)) {
+        atomicOr(&d->status, ST_SCHEDULE);
+        go = false;
+    }
+    const bool loop = go && next < N, last = go && next == N;
+    b.scratch64[9] = loop ? 1 : 0;
+    b.scratch64[11] = last ? 1 : 0;
+    if (use_cond) {
+        cudaGraphSetConditional(cond, loop ? 1u : 0u);
+        cudaGraphSetConditional(fin, last ? 1u : 0u);
+    }
+    *go_s = go;
+}
+
+// the loop's gate before the first tick; opens the first tick
+__global__ void __launch_bounds__(128) k_block_gate(BatchView b, int L, int use_cond, cudaGraphConditionalHandle cond,
+                                                    cudaGraphConditionalHandle fin)
 {
     __shared__ int go_s;
-    if (threadIdx.x == 0) {
-        ProbDiag *d = b.prob[0].diag;
-        const long long N = 1LL << L, next = b.scratch64[2];
-        bool go = d->status == 0;
-        if (go && !(next > 0 && next <= N)) {
-            atomicOr(&d->status, ST_SCHEDULE);
-            go = false;
-        }
-        b.scratch64[9] = go ? 1 : 0;
-        if (use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
-        go_s = go;
-    }
+    if (threadIdx.x == 0) schedule_next(b, 0, 1LL << L, use_cond, cond, fin, &go_s);
     __syncthreads();
     if (go_s) open_tick(b);
 }
@@ -233,7 +248,8 @@ __global__ void __launch_bounds__(kBlockThreads) k_block_gather(BatchView b)
 // next step; inactive particles lifted by the reactive limiter end their
 // step at the next tick of their new level's grid
 __global__ void __launch_bounds__(kBlockThreads) k_block_kick(BatchView b, int L, int use_cond,
-                                                              cudaGraphConditionalHandle cond)
+                                                              cudaGraphConditionalHandle cond,
+                                                              cudaGraphConditionalHandle fin)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long k = b.scratch64[5];
@@ -300,19 +316,10 @@ __global__ void __launch_bounds__(kBlockThreads) k_block_kick(BatchView b, int L
     if (!last_s) return;
     if (threadIdx.x == 0) {
         __threadfence();
-        ProbDiag *d = b.prob[0].diag;
-        const long long N = 1LL << L, next = *(volatile long long *)&b.scratch64[2];
         b.scratch64[10] = 0;
         b.scratch64[4] = k;
         b.scratch64[8] += 1;
-        bool go = *(volatile unsigned *)&d->status == 0 && k < N && b.scratch64[8] < N;
-        if (go && !(next > k && next <= N)) {
-            atomicOr(&d->status, ST_SCHEDULE);
-            go = false;
-        }
-        b.scratch64[9] = go ? 1 : 0;
-        if (use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
-        go_s = go;
+        schedule_next(b, k, 1LL << L, use_cond, cond, fin, &go_s);
     }
     __syncthreads();
     if (go_s) open_tick(b);
@@ -345,9 +352,9 @@ cudaError_t launch_block_open(const BatchView &b, int L, cudaStream_t st)
 }
 
 cudaError_t launch_block_gate(const BatchView &b, int L, bool use_cond, cudaGraphConditionalHandle cond,
-                              cudaStream_t st)
+                              cudaGraphConditionalHandle fin, cudaStream_t st)
 {
-    k_block_gate<<<1, 128, 0, st>>>(b, L, use_cond ? 1 : 0, cond);
+    k_block_gate<<<1, 128, 0, st>>>(b, L, use_cond ? 1 : 0, cond, fin);
     return cudaGetLastError();
 }
 
@@ -373,9 +380,9 @@ cudaError_t launch_block_gather(const BatchView &b, int precision, cudaStream_t 
 }
 
 cudaError_t launch_block_kick(const BatchView &b, int L, bool use_cond, cudaGraphConditionalHandle cond,
-                             cudaStream_t st)
+                             cudaGraphConditionalHandle fin, cudaStream_t st)
 {
-    k_block_kick<<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b, L, use_cond ? 1 : 0, cond);
+    k_block_kick<<<blocks_for(b.ntot), kBlockThreads, 0, st>>>(b, L, use_cond ? 1 : 0, cond, fin);
     return cudaGetLastError();
 }
 

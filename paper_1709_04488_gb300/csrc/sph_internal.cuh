@@ -188,7 +188,8 @@ struct BatchView {
     void *gnode[kMaxLevels + 1];
     // block time-steps (single problem): per particle, original order
     int block_on;                // this launch set is a tick of a block step
-    int block_lanes;             // lanes per particle of the tick's pair kernels
+    int block_tasks;             // the pair kernels serve the tick's tasks (else whole leaves: the block's last tick)
+    int block_lanes;             // lanes per particle of the tick's pair kernels (tasks)
     int *blev;                   // level
     int *bnml;                   // largest level among the force neighbours at the last force pass (-1: none)
     int *breq;                   // reactive limiter: level asked of an inactive particle (-1: none)
@@ -345,13 +346,14 @@ cudaError_t launch_kick_drift(const BatchView &b, double dt_host, cudaStream_t s
 // [0] smallest and [1] largest step (ordered bits), [2] next tick where a
 // step ends, [3] force evaluations, [4] the current tick k0, [5] the tick k1
 // being advanced to, [6] Delta t_MAX and [7] the tick length (bits), [8]
-// ticks taken, [9] 1 while another tick follows, [10] blocks of the kick
-// launch done.  `cond` is the graph's loop condition handle, set only when
-// `use_cond` is true.
+// ticks taken, [9] 1 while another tick of the loop follows, [10] blocks of
+// the kick launch done, [11] 1 when the block's last tick (every particle
+// due, at 2^L) follows.  `cond`/`fin` are the graph's loop and last-tick
+// condition handles, set only when `use_cond` is true.
 cudaError_t launch_block_dt(const BatchView &b, int L, cudaStream_t st);  // also plans Delta t_MAX
 cudaError_t launch_block_open(const BatchView &b, int L, cudaStream_t st);
 cudaError_t launch_block_gate(const BatchView &b, int L, bool use_cond, cudaGraphConditionalHandle cond,
-                              cudaStream_t st);  // (opens the first tick)
+                              cudaGraphConditionalHandle fin, cudaStream_t st);  // (opens the first tick)
 // graph form with tree reuse: sets the branch condition (rebuild this tick)
 cudaError_t launch_block_tick_begin(const BatchView &b, int every, cudaGraphConditionalHandle cond,
                                     cudaStream_t st);
@@ -361,10 +363,10 @@ cudaError_t launch_block_gather(const BatchView &b, int precision, cudaStream_t 
 cudaError_t launch_block_tasks(const BatchView &b, int precision, cudaStream_t st);  // after the leaves (sph_pairs.cu)
 // a tick that keeps the order and the leaves: drift, gather, leaf boxes and tasks in one pass (sph_pairs.cu)
 cudaError_t launch_block_leaf_tick(const BatchView &b, int precision, cudaStream_t st);
-// the tick's kicks; its last block ends the tick (loop flag [9], the loop
-// condition when use_cond) and opens the next one
+// the tick's kicks; its last block ends the tick (flags [9], [11], the
+// conditions when use_cond) and opens the next one
 cudaError_t launch_block_kick(const BatchView &b, int L, bool use_cond, cudaGraphConditionalHandle cond,
-                             cudaStream_t st);
+                             cudaGraphConditionalHandle fin, cudaStream_t st);
 cudaError_t launch_block_finish(const BatchView &b, cudaStream_t st);
 cudaError_t launch_kick_close(const BatchView &b, int do_kick, int forces_ran, cudaStream_t st);
 cudaError_t launch_reset_step(const BatchView &b, int mode, cudaStream_t st);  // mode 1 full, 2 forces only

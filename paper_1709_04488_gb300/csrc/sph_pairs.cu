@@ -23,11 +23,12 @@ cudaError_t launch_density(const BatchView &b, int precision, int use_pred, cuda
 {
     if (b.ntot == 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-    if (!b.block_on) {  // (block-step ticks: the wrap-list launch serves the tasks)
+    const bool tasks = b.block_on && b.block_tasks;
+    if (!tasks) {  // (block-step ticks with tasks: the wrap-list launch serves them)
         e = density_launches_m4(b, precision, use_pred, st);
         if (e == cudaSuccess) e = density_launches_m6(b, precision, use_pred, st);
     }
-    const bool wrap = b.any_periodic || b.any_gravity || b.block_on;
+    const bool wrap = b.any_periodic || b.any_gravity || tasks;
     if (e == cudaSuccess && wrap) e = density_launches_m4_wrap(b, precision, use_pred, st);
     if (e == cudaSuccess && wrap) e = density_launches_m6_wrap(b, precision, use_pred, st);
     if (e != cudaSuccess) return e;
@@ -56,7 +57,7 @@ cudaError_t launch_forces(const BatchView &b, int precision, cudaStream_t st)
 {
     if (b.ntot == 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
-    if (!b.block_on) {  // (block-step ticks: the wrap-list launch serves the tasks)
+    if (!(b.block_on && b.block_tasks)) {  // (block-step ticks with tasks: the wrap-list launch serves them)
         e = force_launches_m4(b, precision, st);
         if (e == cudaSuccess) e = force_launches_m6(b, precision, st);
     }

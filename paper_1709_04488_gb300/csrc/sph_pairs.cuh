@@ -1086,7 +1086,7 @@ __global__ void __launch_bounds__(DCfg<T, LPP, UM, K>::WPB * 32, DCfg<T, LPP, UM
     unsigned char *mine = smem + wib * C::per_warp;
     // block-step ticks: the wrap-list launch serves the tick's tasks (leaf <<
     // 5 | first due ordinal) directly; the common launch does not run
-    const bool tasks = WRAP && b.block_on;
+    const bool tasks = WRAP && b.block_on && b.block_tasks;
     const int nleaf = tasks ? b.counters[kBlockTasks] : WRAP ? b.counters[kDensWrapList] : b.counters[0];
     const int cls = lpp_log2(LPP) + (UM ? 4 : 0) + 8 * K;
     for (;;) {
@@ -1712,7 +1712,7 @@ __global__ void __launch_bounds__(FCfg<T, LPP>::WPB * 32, FCfg<T, LPP>::MINB) k_
     unsigned char *mine = smem + wib * C::per_warp;
     // block-step ticks: the wrap-list launch serves the tick's tasks (leaf
     // << 5 | first due ordinal) directly; the common launch does not run
-    const bool tasks = WRAP && b.block_on;
+    const bool tasks = WRAP && b.block_on && b.block_tasks;
     const int nleaf = tasks ? b.counters[kBlockTasks] : WRAP ? b.counters[kForceWrapList] : b.counters[0];
     const int cls = lpp_log2(LPP) + 4 * K;
     int last_p = -1;
@@ -1765,7 +1765,7 @@ cudaError_t run_density(const BatchView &b, int use_pred, cudaStream_t st)
     }
     // the wrap-list launch serves few leaves (mostly none) unless a problem
     // has gravity or the launch is a block-step tick's
-    k_density<T, LPP, UM, K, WRAP><<<dev_info().sm_count * (WRAP && !b.any_gravity && !b.block_on ? 1 : per_sm),
+    k_density<T, LPP, UM, K, WRAP><<<dev_info().sm_count * (WRAP && !b.any_gravity && !(b.block_on && b.block_tasks) ? 1 : per_sm),
                                      C::WPB * 32, C::smem, st>>>(b, use_pred);
     return cudaGetLastError();
 }
