@@ -334,26 +334,44 @@ def time_steps(S, prob, stream, torch, K, flush, stage=False):
     return ms, stages, dens_pairs, force_pairs
 
 
-def serving(nreq, loads, pool_bytes):
+def serving(nreq, loads, pool_bytes, rank=0, world=1, dist=None):
     """Serving configuration: requests of 1e3..2e5 particles (lattice, Sod or
     Sedov, seeded), 10 steps each.  First all requests arrive at t = 0 (the
     saturated batched throughput), then Poisson arrivals at the given loads
-    (wall clock); latency = completion - arrival."""
+    (wall clock); latency = completion - arrival.  With several GPUs (one
+    rank each) every rank builds the same stream and serves the requests
+    routed to it (serve.route: the GPU whose queue empties first), and the
+    ranks' records are gathered (host bookkeeping only)."""
     from paper_1709_04488_gb300 import serve
     reqs = serve.make_requests(nreq, seed=5, n_min=1e3, n_max=2e5, nsteps=10)
     work = sum(len(r["arrays"]["x"]) * r["nsteps"] for r in reqs)
-    recs, span = serve.run_stream(reqs, np.zeros(nreq), pool_bytes)
-    assert all(r["status"] == 0 for r in recs), [r["status"] for r in recs]
+
+    def share(arr, rate):
+        route = serve.route(reqs, arr, world, rate=rate)
+        mine = [i for i in range(nreq) if route[i] == rank]
+        recs, span = serve.run_stream([reqs[i] for i in mine], arr[mine], pool_bytes)
+        got = [(span, [r["latency"] for r in recs], [r["status"] for r in recs])]
+        if world > 1:
+            got = [None] * world
+            dist.all_gather_object(got, (span, [r["latency"] for r in recs], [r["status"] for r in recs]))
+        spans = [g[0] for g in got]
+        lat = np.array([x for g in got for x in g[1]])
+        st = [x for g in got for x in g[2]]
+        assert all(x == 0 for x in st), st
+        return max(spans), lat
+
+    span, _ = share(np.zeros(nreq), 1.0e8)
     sat = work / span
     out = {"requests": nreq, "particle_steps": work, "saturated_updates_per_s": sat,
            "saturated_makespan_s": span, "loads": []}
+    if world > 1:
+        out["gpus"] = world
+        out["routing"] = "each request to the GPU whose queue empties first (shared cost model, no exchange)"
     mean_work = work / nreq
     for load in loads:
         rate = load * sat / mean_work
         arr = serve.poisson_arrivals(nreq, rate, seed=6)
-        recs, span = serve.run_stream(reqs, arr, pool_bytes)
-        assert all(r["status"] == 0 for r in recs)
-        lat = np.array([r["latency"] for r in recs])
+        span, lat = share(arr, sat / world)
         out["loads"].append({"load": load, "arrival_rate_per_s": rate, "p50_s": float(np.percentile(lat, 50)),
                              "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
                              "updates_per_s": work / span, "makespan_s": span})
@@ -747,9 +765,9 @@ def run_ours(args):
                "ms_per_step": float(np.mean(mss)), "steps": len(mss)}
         psod.close()
     serve_res = None
-    if args.serve > 0 and rank == 0:
+    if args.serve > 0:
         free, _ = torch.cuda.mem_get_info(dev)
-        serve_res = serving(args.serve, args.serve_load, int(0.8 * free))
+        serve_res = serving(args.serve, args.serve_load, int(0.8 * free), rank, world, dist if world > 1 else None)
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()

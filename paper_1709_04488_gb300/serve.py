@@ -121,6 +121,27 @@ class Server:
             pass
 
 
+def route(reqs, arrivals, nranks: int, rate: float = 1.0e8):
+    """Multi-GPU serving (one process per GPU): each request goes to the GPU
+    whose queue empties first by a cost model every rank shares (its
+    particle-steps at `rate` particle-updates/s per GPU, queues taken in
+    arrival order, ties to the lowest rank), so every rank computes the same
+    assignment from the same request stream and nothing is exchanged on the
+    data path.  Returns the rank of each request."""
+    if nranks < 1:
+        raise ValueError("nranks must be >= 1")
+    arrivals = np.asarray(arrivals, dtype=np.float64)
+    order = np.argsort(arrivals, kind="stable")
+    free = np.zeros(nranks)  # time at which each GPU's queue empties
+    out = np.zeros(len(reqs), dtype=np.int64)
+    for i in order:
+        start = np.maximum(free, arrivals[i])
+        r = int(np.argmin(start))
+        free[r] = start[r] + len(reqs[i]["arrays"]["x"]) * reqs[i]["nsteps"] / rate
+        out[i] = r
+    return out
+
+
 def run_stream(reqs, arrivals, pool_bytes: int, max_slots: int = 256, virtual_clock: bool = False):
     """Submit every request with its arrival time, drive the loop until all are
     done; returns per-request records and the makespan on the server clock."""

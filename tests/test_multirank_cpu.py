@@ -123,3 +123,61 @@ def test_two_ranks_step_their_own_problems_through_the_oracle(oracle_mod):
         assert np.array_equal(r["rho"], s.rho)
     # the two ranks stepped different problems
     assert not np.array_equal(allr[0]["x"], allr[1]["x"])
+
+
+def test_route_covers_and_balances_requests():
+    """Multi-GPU serving: every request goes to exactly one GPU, the same
+    stream routes the same way every time, saturated queues are balanced
+    within one request's work, and with arrivals spread out a request goes
+    to an idle GPU."""
+    from paper_1709_04488_gb300 import serve
+    reqs = serve.make_requests(40, seed=3, n_min=1e3, n_max=2e4, nsteps=10)
+    work = np.array([len(r["arrays"]["x"]) * r["nsteps"] for r in reqs], dtype=float)
+    for nr in (1, 2, 3, 4):
+        rt = serve.route(reqs, np.zeros(len(reqs)), nr)
+        assert rt.min() >= 0 and rt.max() < nr
+        assert np.array_equal(rt, serve.route(reqs, np.zeros(len(reqs)), nr))
+        load = np.array([work[rt == r].sum() for r in range(nr)])
+        assert load.max() - load.min() <= work.max()
+    # arrivals far apart (each request done before the next arrives): all on GPU 0
+    rt = serve.route(reqs, np.arange(len(reqs)) * 10.0, 3)
+    assert np.all(rt == 0)
+    with pytest.raises(ValueError):
+        serve.route(reqs, np.zeros(len(reqs)), 0)
+
+
+def _route_worker(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+    from paper_1709_04488_gb300 import serve
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    reqs = serve.make_requests(30, seed=4, n_min=1e3, n_max=2e4, nsteps=10)
+    arr = serve.poisson_arrivals(30, 50.0, seed=6)
+    rt = serve.route(reqs, arr, world, rate=2e6)
+    mine = [i for i in range(len(reqs)) if rt[i] == rank]
+    allr = [None] * world
+    dist.all_gather_object(allr, (rank, rt.tolist(), mine))
+    if rank == 0:
+        q.put(allr)
+    dist.destroy_process_group()
+
+
+def test_two_ranks_route_the_same_stream_the_same_way():
+    """Each rank routes the shared request stream by itself: the two
+    assignments agree, and the ranks' shares partition the requests."""
+    ctx = torch.multiprocessing.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_route_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    allr = q.get(timeout=300)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert allr[0][1] == allr[1][1]
+    shares = [set(a[2]) for a in allr]
+    assert shares[0].isdisjoint(shares[1]) and shares[0] | shares[1] == set(range(30))
+    assert len(shares[0]) > 0 and len(shares[1]) > 0
