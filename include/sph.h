@@ -278,8 +278,10 @@ int sph_run(sph_ctx *ctx, int nsteps);
  * largest level at the last force pass; reactive: particles that take forces
  * shorten the steps of slower neighbours, which then end at the next tick of
  * their new level).  Needs a force evaluation first; leaves every particle
- * synchronised with fresh forces.  tree_rebuild_every applies between ticks
- * as between global steps.  Writes Delta t_MAX to *dtmax and the
+ * synchronised with fresh forces.  Tree reuse (tree_rebuild_every = k > 1):
+ * the block starts from the context's leaves, the ticks at multiples of k
+ * sort and build afresh and the others keep and refit them; the last tick
+ * (2^L) always builds them.  Writes Delta t_MAX to *dtmax and the
  * number of particle force evaluations to *evals (either may be NULL).
  * The schedule lives on the device: on a stream that can be captured, the
  * first call captures one CUDA graph whose ticks are a conditional while

@@ -639,6 +639,18 @@ static BatchView block_view(const sph_ctx *c, bool tasks = true)
 
 static int block_every(const sph_ctx *c) { return c->prm.tree_rebuild_every > 1 ? c->prm.tree_rebuild_every : 1; }
 
+// With tree reuse the block starts from the context's leaves (those of the
+// last build or refit: the previous block's last tick, a global step, the
+// density solve), and the ticks k > 0 with k a multiple of
+// tree_rebuild_every sort and build afresh; every tick does without reuse.
+// A cadence of at least 2^L ticks never rebuilds inside the loop.
+static bool block_loop_rebuilds(const sph_ctx *c) { return block_every(c) < (1 << c->prm.block_levels); }
+static bool block_tick_rebuilds(const sph_ctx *c, long long tick)
+{
+    const int every = block_every(c);
+    return every == 1 || (tick > 0 && tick % every == 0 && block_loop_rebuilds(c));
+}
+
 // the tick's drift and leaves.  Tree reuse (Sec. 4.2) between ticks as
 // between global steps: sort and build on every tree_rebuild_every-th tick;
 // between, the order and the leaves are kept (the drift runs in sorted order
@@ -685,7 +697,7 @@ static int enqueue_block_last(const BatchView &bl, int prec, int L, cudaStream_t
 // the legacy default stream: the host reads the flags after every tick
 static int block_step_eager(sph_ctx *c, const BatchView &b, const BatchView &bl)
 {
-    const int L = c->prm.block_levels, prec = c->prm.precision, every = block_every(c);
+    const int L = c->prm.block_levels, prec = c->prm.precision;
     cudaStream_t st = c->stream;
     CU(launch_block_dt(b, L, st));
     CU(launch_block_open(b, L, st));
@@ -696,7 +708,7 @@ static int block_step_eager(sph_ctx *c, const BatchView &b, const BatchView &bl)
         CU(cudaStreamSynchronize(st));
         if (!fl[0]) break;
         if (tick >= (1LL << L)) return fail(SPH_ECUDA, "block step: more than 2^L ticks");
-        int rc = enqueue_block_leaves(b, prec, tick % every == 0, st);
+        int rc = enqueue_block_leaves(b, prec, block_tick_rebuilds(c, tick), st);
         if (rc) return rc;
         rc = enqueue_block_passes(b, prec, L, false, 0, 0, st);
         if (rc) return rc;
@@ -756,15 +768,16 @@ static int capture_tick(const sph_ctx *c, const BatchView &b, cudaGraphCondition
                         cudaGraphConditionalHandle fin, cudaStream_t s2, cudaStream_t s3)
 {
     const int L = c->prm.block_levels, prec = c->prm.precision, every = block_every(c);
+    const bool branch = every > 1 && block_loop_rebuilds(c);  // some ticks rebuild, others keep
     cudaGraphConditionalHandle rb = 0;
-    if (every > 1) {
+    if (branch) {
         cudaGraph_t body = nullptr;
         int rc = capture_graph(s2, &body);
         if (rc) return rc;
         CU(cudaGraphConditionalHandleCreate(&rb, body, 0, 0));
+        CU(launch_block_tick_begin(b, every, rb, s2));
     }
-    if (every > 1) CU(launch_block_tick_begin(b, every, rb, s2));
-    if (every > 1) {
+    if (branch) {
         cudaGraph_t *br = nullptr;
         int rc = add_conditional(s2, rb, cudaGraphCondTypeIf, 2, &br);  // [0] rebuild, [1] keep the leaves
         if (rc) return rc;
@@ -774,7 +787,7 @@ static int capture_tick(const sph_ctx *c, const BatchView &b, cudaGraphCondition
             if (rc) return rc;
         }
     } else {
-        int rc = enqueue_block_leaves(b, prec, true, s2);
+        int rc = enqueue_block_leaves(b, prec, every == 1, s2);
         if (rc) return rc;
     }
     return enqueue_block_passes(b, prec, L, true, loop, fin, s2);
@@ -873,6 +886,13 @@ int sph_block_step(sph_ctx *c, double *dtmax_out, int64_t *evals_out)
     clear_ran(c);
     const BatchView b = block_view(c), bl = block_view(c, false);
     cudaStream_t st = c->stream;
+    if (block_every(c) > 1 && c->since_build >= block_every(c)) {
+        // the context's leaves do not hold its particles (a batch moved them): build them first
+        CU(launch_domain_and_keys(c->bv, st));
+        CU(launch_radix_sort(c->bv, st));
+        CU(launch_gather(c->bv, st));
+        CU(launch_build_leaves(c->bv, c->prm.precision, st));
+    }
     if (st == nullptr) {
         int rc = block_step_eager(c, b, bl);  // the legacy default stream cannot be captured
         if (rc) return rc;
@@ -892,7 +912,7 @@ int sph_block_step(sph_ctx *c, double *dtmax_out, int64_t *evals_out)
     if (dtmax_out) *dtmax_out = dtmax;
     if (evals_out) *evals_out = evals;
     c->have_forces = true;
-    c->since_build = c->prm.tree_rebuild_every > 1 ? c->prm.tree_rebuild_every : 1;  // the next global step rebuilds
+    c->since_build = 0;  // the last tick built the leaves
     return rc;
 }
 

@@ -203,9 +203,11 @@ __global__ void __launch_bounds__(128) k_block_gate(BatchView b, int L, int use_
 }
 
 // graph form with tree reuse: whether this tick sorts and builds the leaves
+// (the ticks k > 0 with k a multiple of tree_rebuild_every)
 __global__ void k_block_tick_begin(BatchView b, int every, cudaGraphConditionalHandle cond)
 {
-    cudaGraphSetConditional(cond, b.scratch64[8] % every == 0 ? 1u : 0u);
+    const long long k = b.scratch64[8];
+    cudaGraphSetConditional(cond, k > 0 && k % every == 0 ? 1u : 0u);
 }
 
 __device__ __forceinline__ void count_due(const BatchView &b, bool due)
