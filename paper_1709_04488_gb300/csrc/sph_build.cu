@@ -280,6 +280,10 @@ __global__ void k_leaf_props(BatchView b)
 template <typename T4>
 __global__ void k_leaf_refit(BatchView b)
 {
+    // a block-step tick with tasks: unless some particle's final h outgrew
+    // the prediction the leaf pass boxed it with (lists_stale), those boxes
+    // already hold every smoothing sphere (the kept particles' h unchanged)
+    if (b.block_on && b.block_tasks && !*(volatile int *)&b.dyn[0].lists_stale) return;
     const int lane = threadIdx.x & 31;
     const int nleaf = b.counters[0];
     int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
