@@ -79,6 +79,9 @@ def parse():
     ap.add_argument("--no-m6", action="store_true", help="skip the M6 quintic-kernel measurement")
     ap.add_argument("--no-gravity", action="store_true", help="skip the self-gravity measurement")
     ap.add_argument("--no-block", action="store_true", help="skip the block time-step measurement")
+    ap.add_argument("--block-probe", action="store_true",
+                    help="only one block step of the Sedov blast (64^3, 6 levels, tree kept for the block) on the "
+                         "legacy default stream (its ticks launched one by one, for profiling): prints its time")
     ap.add_argument("--lpp", type=int, default=0, help="lanes per particle (0: autotuned)")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS),
                     help="cloud (8e6, the default: the largest single-GPU configuration), sedov (1e6) or sod (36864)")
@@ -798,8 +801,34 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def block_probe():
+    """One block step of the block-step measurement's Sedov blast, its ticks
+    host-driven on the legacy default stream so that a profiler sees every
+    kernel launch of every tick."""
+    import torch
+    from paper_1709_04488_gb300 import build as B
+    from paper_1709_04488_gb300 import ics
+    from paper_1709_04488_gb300 import sph as S
+    if not os.path.exists(S.LIB_PATH):
+        B.build()
+    a, p = ics.sedov(BLOCK_SEDOV_SIDE)
+    prob = S.Problem(a, S.make_params(S.PREC_MIXED, **p, block_levels=BLOCK_LEVELS,
+                                      tree_rebuild_every=2 ** BLOCK_LEVELS), stream=None)
+    prob.density_h()
+    prob.forces()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    dtmax, evals = prob.block_step()
+    torch.cuda.synchronize()
+    print(json.dumps({"probe": "block_step", "block_ms": (time.perf_counter() - t0) * 1e3, "dt_max": dtmax,
+                      "force_evaluations": int(evals), "levels": np.bincount(prob.levels()).tolist()}))
+    prob.close()
+
+
 def main():
     args = parse()
+    if args.block_probe:
+        return block_probe()
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -136,3 +136,46 @@ def test_alone_step_with_tree_reuse_after_batched_steps(S, oracle_mod):
     ra = np.stack([ref.ax, ref.ay, ref.az], 1)
     ga = np.stack([g["ax"], g["ay"], g["az"]], 1)
     assert np.max(np.linalg.norm(ga - ra, axis=1)) < 1e-4 * np.sqrt(np.mean(np.sum(ra ** 2, 1)))
+
+
+def test_block_step_with_tree_reuse_after_batched_steps(S, oracle_mod):
+    """A block step with tree reuse starts from the context's leaves; after a
+    batched step (which sorts the problems in the batch's layout) it builds
+    them first, and matches the oracle's block step from the same state."""
+    import torch
+    O = oracle_mod
+    st = torch.cuda.Stream()
+    a, p = ics.sedov(12, seed=15)
+    prob = S.Problem(a, S.make_params(S.PREC_FP64, **p, block_levels=4, tree_rebuild_every=4, flags=S.FLAG_ASYNC),
+                     stream=st)
+    prob.density_h()
+    prob.forces()
+    prob.sync()
+    b_, q_ = _moving_lattice(9, seed=16)
+    other = S.Problem(b_, S.make_params(S.PREC_FP64, **q_, flags=S.FLAG_ASYNC), stream=st)
+    other.density_h()
+    other.forces()
+    other.sync()
+    dt = prob.diagnostics().dt_next
+    wb = S.sph_batch_workspace_bytes([prob.ctx, other.ctx])
+    ws = torch.empty(wb, dtype=torch.uint8, device="cuda")
+    S.check(S.sph_batch_step([prob.ctx, other.ctx], 1, ws.data_ptr(), wb), "sph_batch_step")
+    # the oracle takes the same KDK step (its forces, like the GPU's, from the predicted v)
+    P = O.Params(**p, use_grid=True)
+    ref = O.State(**a)
+    assert O.density(P, ref) == O.OK and O.forces(P, ref) == O.OK
+    assert O.step(P, ref, dt) == O.OK
+    lv = np.zeros(ref.n, np.int32)
+    nm = np.zeros(ref.n, np.int32)
+    rc, dtmax, passes, evals = O.block_step(P, ref, lv, nm, 4, 2)
+    assert rc == O.OK
+    # the GPU context from the same state: its forces were evaluated by the batched step
+    dt_g, ev_g = prob.block_step()
+    assert ev_g == evals and np.array_equal(prob.levels(), lv)
+    assert dt_g == pytest.approx(dtmax, rel=1e-12)
+    g = prob.numpy()
+    for f in ("vx", "vy", "vz", "u"):
+        r = getattr(ref, f)
+        assert np.max(np.abs(g[f] - r)) < 1e-11 * np.max(np.abs(r)), f
+    prob.close()
+    other.close()
