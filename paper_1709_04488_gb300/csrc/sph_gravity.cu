@@ -403,33 +403,61 @@ __global__ void __launch_bounds__(kTreeThreads) k_gravity_tree(BatchView b)
     __shared__ T s_q[kW][32][6];       // node Q
     __shared__ int s_off[kW][32], s_st[kW][32];  // opened leaves: first staged entry, first particle
     const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
-    const int nleaf = b.counters[0];
+    // the walk's query: a leaf (its box the opening criterion's), or in a
+    // block-step tick a task of the particles whose step ends (up to S =
+    // 32 / block_lanes of a leaf, their own box), so that the few queries
+    // of a tick walk in short, parallel pieces.  (For a whole step the
+    // leaves are faster: the multipole terms per particle hardly fall with
+    // the smaller boxes, and the walks multiply.)
+    const bool blk = b.block_on && b.block_tasks;
+    const int nitem = blk ? b.counters[kBlockTasks] : b.counters[0];
     const int w0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
-    for (int leaf = w0; leaf < nleaf; leaf += nw) {
+    for (int item = w0; item < nitem; item += nw) {
+        int leaf = item, k0 = 0;
+        if (blk) {
+            const int t = b.btask[item];
+            leaf = t >> 5;
+            k0 = t & 31;
+        }
         const int p = b.leaf_pid[leaf];
         const ProbStatic &ps = b.prob[p];
         if (!(ps.ph.gravity && ps.ph.grav_theta > 0)) continue;
         const ProbDyn &d = b.dyn[p];
-        const int lpp = ps.lpp, S = kBranch / lpp;
+        const int lpp = blk ? b.block_lanes : ps.lpp, S = kBranch / lpp;
         const int pi = lane % S, sub = lane / S;
-        const int st = b.leaf_start[leaf], cnt = b.leaf_start[leaf + 1] - st;
-        // block step: only the particles whose step ends take the long range
-        const bool due = pi < cnt && (!b.block_on || ((const T *)b.slev)[st + pi] > T(0));
+        const int st = b.leaf_start[leaf], cnt_leaf = b.leaf_start[leaf + 1] - st;
+        // the particles of the leaf that take the long range now (block
+        // step: those whose step ends), and this task's share of them
+        const unsigned dm = __ballot_sync(0xffffffffu, lane < cnt_leaf &&
+                                          (!b.block_on || ((const T *)b.slev)[st + (lane < cnt_leaf ? lane : 0)] > T(0)));
+        const int nd = __popc(dm), cnt = min(S, max(nd - k0, 0));
+        const bool due = pi < cnt;
         if (!__any_sync(0xffffffffu, due)) continue;
-        const V4 *gl = (const V4 *)b.gnode[0] + 5LL * leaf;
-        const V4 GL = gl[3], GH = gl[4];
-        const T hleaf = gl[2].w;
-        const T blo[3] = {GL.x, GL.y, GL.z}, bhi[3] = {GH.x, GH.y, GH.z};
-        // this lane's particle (lanes beyond the leaf sit at its box corner)
-        T xi = blo[0], yi = blo[1], zi = blo[2], hi = T(1), hinv = T(1);
-        if (pi < cnt) {
-            const P e = ((const P *)b.gpos)[st + pi];
-            const H f = ((const H *)b.gh)[st + pi];
-            xi = e.x;
-            yi = e.y;
-            zi = e.z;
-            hi = f.x;
-            hinv = f.y;
+        const int pos = due ? (int)__fns(dm, 0u, k0 + pi + 1) : 0;
+        // this lane's particle (lanes beyond the task take its first)
+        const P e = ((const P *)b.gpos)[st + (due ? pos : (int)__fns(dm, 0u, k0 + 1))];
+        const H f = ((const H *)b.gh)[st + (due ? pos : (int)__fns(dm, 0u, k0 + 1))];
+        const T xi = e.x, yi = e.y, zi = e.z, hi = f.x, hinv = f.y;
+        // the query's box and largest h: the leaf's, or the task's
+        T blo[3], bhi[3], hleaf;
+        if (blk) {
+            blo[0] = warp_min(xi);
+            blo[1] = warp_min(yi);
+            blo[2] = warp_min(zi);
+            bhi[0] = warp_max(xi);
+            bhi[1] = warp_max(yi);
+            bhi[2] = warp_max(zi);
+            hleaf = warp_max(hi);
+        } else {
+            const V4 *gl = (const V4 *)b.gnode[0] + 5LL * leaf;
+            const V4 GL = gl[3], GH = gl[4];
+            blo[0] = GL.x;
+            blo[1] = GL.y;
+            blo[2] = GL.z;
+            bhi[0] = GH.x;
+            bhi[1] = GH.y;
+            bhi[2] = GH.z;
+            hleaf = gl[2].w;
         }
         long long npair = 0, nnode = 0;  // terms this lane summed
         const T th2 = (T)(ps.ph.grav_theta * ps.ph.grav_theta);
@@ -557,7 +585,7 @@ __global__ void __launch_bounds__(kTreeThreads) k_gravity_tree(BatchView b)
             gz += __shfl_xor_sync(0xffffffffu, gz, o);
         }
         if (sub == 0 && due) {
-            const long long io = (long long)b.perm[st + pi] - ps.base;
+            const long long io = (long long)b.perm[st + pos] - ps.base;
             ps.ax[io] += ps.ph.G * gx;
             ps.ay[io] += ps.ph.G * gy;
             ps.az[io] += ps.ph.G * gz;
