@@ -181,3 +181,52 @@ def test_two_ranks_route_the_same_stream_the_same_way():
     shares = [set(a[2]) for a in allr]
     assert shares[0].isdisjoint(shares[1]) and shares[0] | shares[1] == set(range(30))
     assert len(shares[0]) > 0 and len(shares[1]) > 0
+
+
+def _serving_worker(rank, world, port, q):
+    """bench.py's serving leg on two gloo ranks, with the GPU server replaced
+    by a stand-in that finishes each request at its arrival plus its work at
+    a fixed rate (the routing and the gathering of the ranks' records run as
+    they do on GPUs)."""
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+    import bench
+    from paper_1709_04488_gb300 import serve
+
+    def fake_run_stream(reqs, arrivals, pool_bytes, **kw):
+        t, recs = 0.0, []
+        for r, a in sorted(zip(reqs, arrivals), key=lambda x: x[1]):
+            t = max(t, a) + len(r["arrays"]["x"]) * r["nsteps"] / 1e8
+            recs.append({"status": 0, "latency": t - a})
+        return recs, t
+
+    serve.run_stream = fake_run_stream
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    out = bench.serving(12, [0.5], 0, rank, world, dist)
+    q.put((rank, out))
+    dist.destroy_process_group()
+
+
+def test_serving_leg_routes_and_gathers_across_ranks():
+    """Every rank serves its routed share; the whole job's saturated
+    throughput is all the work over the slowest rank's makespan, and the
+    latency percentiles cover every request of the stream."""
+    ctx = torch.multiprocessing.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_serving_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = dict(q.get(timeout=600) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    out = got[0]
+    assert out == got[1]  # the gathered records are the same on every rank
+    assert out["requests"] == 12 and out["gpus"] == 2
+    assert out["saturated_updates_per_s"] == pytest.approx(out["particle_steps"] / out["saturated_makespan_s"])
+    # two GPUs at 1e8 each: the routed saturated stream takes about half the work time of one
+    assert out["saturated_makespan_s"] < 0.75 * out["particle_steps"] / 1e8
+    assert len(out["loads"]) == 1 and out["loads"][0]["p99_s"] >= out["loads"][0]["p50_s"] > 0
