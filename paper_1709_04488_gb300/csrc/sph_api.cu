@@ -98,6 +98,7 @@ void carve_arrays(Carver &c, BatchView &b, long long ntot, int nprob, int precis
         b.gnode[l] = grav_tree ? (void *)c.take<char>(5 * v4 * cap) : nullptr;
         cap = cap / kBranch + nprob + 1;
     }
+    b.ggrp = grav_tree ? (void *)c.take<char>(5 * v4 * 8 * (long long)b.node_cap[1]) : nullptr;
     b.fallback_list = c.take<int>(n);
     b.wrap_list = c.take<int>(n);
     b.group_cap = 2 * n;

@@ -272,6 +272,60 @@ __device__ void form_node(double M, const double (&x)[3], const double (&q)[6], 
     }
 }
 
+// The same over each group of four lanes (the level-1 node's leaves 4g ..
+// 4g+3 in lanes 4g .. 4g+3): lane 4g writes group g to g_base + 5 g; empty
+// groups (no mass) are written with M = 0 and are never visited.
+template <typename T>
+__device__ void form_groups(double M, const double (&x)[3], const double (&q)[6], const double (&lo)[3],
+                            const double (&hi)[3], double hm, typename Vec4<T>::type *g_base)
+{
+    using V4 = typename Vec4<T>::type;
+    auto gsum = [](double v) {
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        return v + __shfl_xor_sync(0xffffffffu, v, 2);
+    };
+    auto gmin = [](double v) {
+        v = fmin(v, __shfl_xor_sync(0xffffffffu, v, 1));
+        return fmin(v, __shfl_xor_sync(0xffffffffu, v, 2));
+    };
+    auto gmax = [](double v) {
+        v = fmax(v, __shfl_xor_sync(0xffffffffu, v, 1));
+        return fmax(v, __shfl_xor_sync(0xffffffffu, v, 2));
+    };
+    const double Mt = gsum(M);
+    double c[3];
+    for (int a = 0; a < 3; ++a) {
+        const double s = gsum(M * x[a]);
+        c[a] = Mt > 0 ? s / Mt : 0.0;
+    }
+    const double d[3] = {M > 0 ? x[0] - c[0] : 0.0, M > 0 ? x[1] - c[1] : 0.0, M > 0 ? x[2] - c[2] : 0.0};
+    const double d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const double Q[6] = {gsum(q[0] + M * (3.0 * d[0] * d[0] - d2)), gsum(q[1] + M * (3.0 * d[0] * d[1])),
+                         gsum(q[2] + M * (3.0 * d[0] * d[2])), gsum(q[3] + M * (3.0 * d[1] * d[1] - d2)),
+                         gsum(q[4] + M * (3.0 * d[1] * d[2])), gsum(q[5] + M * (3.0 * d[2] * d[2] - d2))};
+    double L[3], H[3];
+    for (int a = 0; a < 3; ++a) {
+        L[a] = gmin(lo[a]);
+        H[a] = gmax(hi[a]);
+    }
+    const double hmax = gmax(hm);
+    double l2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double e = Mt > 0 ? fmax(c[a] - L[a], H[a] - c[a]) : 0.0;
+        l2 += e * e;
+    }
+    const int lane = threadIdx.x & 31;
+    if ((lane & 3) == 0) {
+        const T t = T(0);
+        V4 *g = g_base + 5 * (lane >> 2);
+        g[0] = mk4<V4>(c[0], c[1], c[2], Mt);
+        g[1] = mk4<V4>(Q[0], Q[1], Q[2], Q[3]);
+        g[2] = mk4<V4>(Q[4], Q[5], ru_t(l2, t), ru_t(hmax, t));
+        g[3] = mk4<V4>(rd_t(Mt > 0 ? L[0] : 0.0, t), rd_t(Mt > 0 ? L[1] : 0.0, t), rd_t(Mt > 0 ? L[2] : 0.0, t), 0.0);
+        g[4] = mk4<V4>(ru_t(Mt > 0 ? H[0] : 0.0, t), ru_t(Mt > 0 ? H[1] : 0.0, t), ru_t(Mt > 0 ? H[2] : 0.0, t), 0.0);
+    }
+}
+
 // Leaf moments from the sorted FP64 particles, then the nodes above: the warp
 // whose arrival completes a node's children forms it (the arrival counters
 // are the tree build's, zero between kernels, and are cleared again here).
@@ -360,6 +414,8 @@ __global__ void __launch_bounds__(256) k_grav_moments(BatchView b)
                     hc[a] = -INFINITY;
                 }
             }
+            if (lvl == 0)  // a level-1 node: also its groups of four leaves
+                form_groups<T>(Mc, xc, qc, lc, hc, hmc, (V4 *)b.ggrp + 40LL * (d.node_off[1] + parent));
             form_node<T>(Mc, xc, qc, lc, hc, hmc, (V4 *)b.gnode[lvl + 1] + 5LL * (d.node_off[lvl + 1] + parent));
             k = parent;
         }
@@ -464,12 +520,11 @@ __global__ void __launch_bounds__(kTreeThreads) k_gravity_tree(BatchView b)
         TwoSumAcc<T> ax{T(0), T(0)}, ay{T(0), T(0)}, az{T(0), T(0)};  // pair terms
         T mx = T(0), my = T(0), mz = T(0);                              // multipole terms
         // classify node g of level `lvl`, stage it when it is used; returns 1 used, 2 opened
-        auto visit = [&](int level, int first, int count) -> unsigned {
-            const int c = first + lane;
+        auto visit = [&](const V4 *nodes, int count, unsigned filter) -> unsigned {
             int cls = 0;
             V4 A, B, C;
-            if (lane < count) {
-                const V4 *g = (const V4 *)b.gnode[level] + 5LL * c;
+            if (lane < count && ((filter >> lane) & 1u)) {
+                const V4 *g = nodes + 5LL * lane;
                 A = g[0];
                 B = g[1];
                 C = g[2];
@@ -551,7 +606,7 @@ __global__ void __launch_bounds__(kTreeThreads) k_gravity_tree(BatchView b)
         unsigned mask[kMaxLevels + 1];
         int base[kMaxLevels + 1];
         {
-            const unsigned om = visit(top, d.node_off[top], d.node_cnt[top]);
+            const unsigned om = visit((const V4 *)b.gnode[top] + 5LL * d.node_off[top], d.node_cnt[top], ~0u);
             if (top == 0) direct(om, d.node_off[0]);
             mask[top] = om;
             base[top] = 0;
@@ -567,11 +622,19 @@ __global__ void __launch_bounds__(kTreeThreads) k_gravity_tree(BatchView b)
             mask[lvl] = m & (m - 1u);
             const int node = base[lvl] + c;
             const int cnt_ch = min(kBranch, d.node_cnt[lvl - 1] - node * kBranch);
-            const unsigned om = visit(lvl - 1, d.node_off[lvl - 1] + node * kBranch, cnt_ch);
             if (lvl == 1) {
+                // a level-1 node's leaves: its groups of four first (used
+                // whole where the criterion allows), then the leaves of the
+                // groups it opens
+                const unsigned og = visit((const V4 *)b.ggrp + 40LL * (d.node_off[1] + node), (cnt_ch + 3) >> 2, ~0u);
+                unsigned lf = 0u;
+                for (unsigned m = og; m; m &= m - 1u) lf |= 0xfu << (4 * (__ffs(m) - 1));
+                const unsigned om =
+                    lf ? visit((const V4 *)b.gnode[0] + 5LL * (d.node_off[0] + node * kBranch), cnt_ch, lf) : 0u;
                 direct(om, d.node_off[0] + node * kBranch);
                 continue;
             }
+            const unsigned om = visit((const V4 *)b.gnode[lvl - 1] + 5LL * (d.node_off[lvl - 1] + node * kBranch), cnt_ch, ~0u);
             --lvl;
             base[lvl] = node * kBranch;
             mask[lvl] = om;

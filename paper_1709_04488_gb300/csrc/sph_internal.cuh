@@ -186,6 +186,7 @@ struct BatchView {
     // to the key-domain corner and mass; Q_xx, Q_xy, Q_xz, Q_yy; Q_yz, Q_zz,
     // l^2, h_max; box min; box max), element type float4 or dbl4
     void *gnode[kMaxLevels + 1];
+    void *ggrp;                  // gravity tree: per level-1 node, its 8 groups of 4 leaves (five Vec4 each)
     // block time-steps (single problem): per particle, original order
     int block_on;                // this launch set is a tick of a block step
     int block_tasks;             // the pair kernels serve the tick's tasks (else whole leaves: the block's last tick)
