@@ -11,7 +11,7 @@
 // in-range candidates so that the arithmetic runs without divergence.
 //
 //  k_density   Eqs. SPHRHO, HRHO, OMEGA: Newton-Raphson on
-//              F(h) = rho(h) - m (eta/h)^3 over the cached list of (r, m_j)
+//              F(h) = rho(h) - m (eta/h)^3 over the cached list of (r^2, m_j)
 //              with the same bracketing fallback as the oracle; the list is
 //              rebuilt if h outgrows it.  Particles whose list overflows, or
 //              that need too many rebuilds, go to k_density_fallback, which
@@ -610,7 +610,7 @@ struct DCfg {
     static constexpr int CH = SPH_DENS_CH;
     static constexpr int WPB = 4;
     static constexpr int MINB = LPP == 1 ? SPH_DENS_MINB1 : SPH_DENS_MINB;  // blocks per SM the registers allow
-    static constexpr int LW = UM ? 1 : 2;  // list words per entry: r (and m_j unless masses are equal)
+    static constexpr int LW = UM ? 1 : 2;  // list words per entry: r^2 (and m_j unless masses are equal)
     static constexpr size_t scratch = (sizeof(StageScratch<T>) + 31) & ~(size_t)31;
     static constexpr size_t per_warp = CH * sizeof(V) + (size_t)LCAP * 32 * LW * sizeof(T) + scratch;
     static constexpr size_t smem = WPB * per_warp;
@@ -757,7 +757,7 @@ __device__ __forceinline__ bool density_leaf(const BatchView &b, int leaf, int k
     using V = typename C::V;
     const int lane = threadIdx.x & 31;
     V *cand = reinterpret_cast<V *>(mine);
-    T *lr = reinterpret_cast<T *>(mine + C::CH * sizeof(V));
+    T *lr = reinterpret_cast<T *>(mine + C::CH * sizeof(V));  // r_ij^2 per entry
     T *lm = lr + C::LCAP * 32;  // used only when masses differ
     StageScratch<T> &sc = *reinterpret_cast<StageScratch<T> *>(lr + C::LCAP * 32 * C::LW);
     const int pp = lane / LPP, sub = lane % LPP;
@@ -836,7 +836,7 @@ __device__ __forceinline__ bool density_leaf(const BatchView &b, int leaf, int k
                     T r2 = dx * dx + dyy * dyy + dz * dz;
                     if (active && !fail && r2 < R2) {
                         if (cnt < C::LCAP) {
-                            lr[cnt * 32 + lane] = sqrt(r2);
+                            lr[cnt * 32 + lane] = r2;  // (its root where the lists are read: off the append path)
                             if (!UM) lm[cnt * 32 + lane] = c.w;
                             ++cnt;
                         } else {
@@ -849,14 +849,14 @@ __device__ __forceinline__ bool density_leaf(const BatchView &b, int leaf, int k
                 for (int k0 = 0; k0 < nbuf; k0 += LPP) {
                     const int k = k0 + sub;
                     bool hit = false;
-                    T r = T(0), mj = T(0);
+                    T r = T(0), mj = T(0);  // (r: r_ij^2)
                     if (k < nbuf) {
                         V c = cand[k];
                         T dx = pi.x - c.x, dyy = pi.y - c.y, dz = pi.z - c.z;
                         if (wrap2) wrap3s<T>(sc, dx, dyy, dz);
                         T r2 = dx * dx + dyy * dyy + dz * dz;
                         hit = active && !fail && r2 < R2;
-                        r = sqrt(r2);
+                        r = r2;
                         mj = c.w;
                     }
                     const unsigned gm = (__ballot_sync(FULL, hit) >> (pp * LPP)) & ((1u << LPP) - 1u);
@@ -933,7 +933,7 @@ __device__ __forceinline__ bool density_leaf(const BatchView &b, int leaf, int k
             if (go) {
                 const T hinv = T(1) / h;
                 for (int e = 0; e < cnt; ++e) {
-                    T q = lr[e * 32 + lane] * hinv;
+                    T q = sqrt(lr[e * 32 + lane]) * hinv;
                     T mj = UM ? mu_all : lm[e * 32 + lane];
                     T f, df;
                     KF::fdf(q, f, df);
@@ -1007,7 +1007,7 @@ __device__ __forceinline__ bool density_leaf(const BatchView &b, int leaf, int k
         if (redo) {
             const T hinv = T(1) / h;
             for (int e = 0; e < cnt; ++e) {
-                T q = lr[e * 32 + lane] * hinv;
+                T q = sqrt(lr[e * 32 + lane]) * hinv;
                 T mj = UM ? mu_all : lm[e * 32 + lane];
                 T f, df;
                 KF::fdf(q, f, df);
@@ -1031,7 +1031,7 @@ __device__ __forceinline__ bool density_leaf(const BatchView &b, int leaf, int k
         if (fin) {
             const T hinv = T(1) / h;
             for (int e = 0; e < cnt; ++e)
-                Z += (UM ? mu_all : lm[e * 32 + lane]) * grav_psi_plus_mq(lr[e * 32 + lane] * hinv);
+                Z += (UM ? mu_all : lm[e * 32 + lane]) * grav_psi_plus_mq(sqrt(lr[e * 32 + lane]) * hinv);
         }
         Z = group_sum<LPP>(Z);
     }
