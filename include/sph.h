@@ -288,8 +288,9 @@ int sph_run(sph_ctx *ctx, int nsteps);
  * loop (no host round trip between ticks) and later calls replay it; on the
  * legacy default stream the host reads a loop flag after every tick.  In a
  * tick the pair kernels serve tasks of a leaf's particles whose step ends
- * (up to 4 with 8 lanes each in FP32 pairs, 8 with 4 lanes in FP64) rather
- * than whole leaves.  Synchronises once at the end. */
+ * rather than whole leaves: one particle with a whole warp in FP32 pairs
+ * with the M4 kernel, up to 4 with 8 lanes each with M6 or self-gravity, 8
+ * with 4 lanes in FP64.  Synchronises once at the end. */
 int sph_block_step(sph_ctx *ctx, double *dtmax, int64_t *evals);
 
 /* Capture the block step's graph now (see sph_block_step), so that the first

@@ -630,7 +630,9 @@ static BatchView block_view(const sph_ctx *c, bool tasks = true)
     b.block_on = 1;
     b.block_tasks = tasks ? 1 : 0;
     b.any_general = 1;  // the active particles' forces run in the wrap-list launch
-    b.block_lanes = c->prm.precision == SPH_PREC_FP64 ? kBlockLanesF64 : kBlockLanesF32;
+    b.block_lanes = c->prm.precision == SPH_PREC_FP64                    ? kBlockLanesF64
+                    : c->prm.kernel == SPH_KERNEL_M6 || c->prm.gravity ? kBlockLanesF32Walk
+                                                                       : kBlockLanesF32;
     if (tasks) {
         b.lpp_mask = mask_of(b.block_lanes, c->prm.kernel);
         b.dens_mask = dens_class_bit(b.block_lanes, c->host_ps.uniform_m, c->prm.kernel);

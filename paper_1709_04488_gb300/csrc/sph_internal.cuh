@@ -28,9 +28,12 @@ constexpr int kSlowCounter = 8, kPoolCounter = 9, kDensWrapList = 10, kForceWrap
 // block-step ticks: counter 12 holds the number of tasks (a leaf and up to
 // 32 / block_lanes of its particles whose step ends now, served with
 // block_lanes lanes each by the pair kernels); cleared by each tick's first
-// kernel.  block_lanes: 8 in FP32 pairs, 4 in FP64 (the lanes the FP64
+// kernel.  block_lanes: a whole warp per particle in FP32 pairs with the M4
+// kernel (the tick's time is its slowest task's, and a warp shares that
+// particle's candidates 32 ways); 8 with M6 or self-gravity (whose tree walk
+// per task costs more than the lanes save); 4 in FP64 (the lanes the FP64
 // kernels are built for)
-constexpr int kBlockTasks = 12, kBlockLanesF32 = 8, kBlockLanesF64 = 4;
+constexpr int kBlockTasks = 12, kBlockLanesF32 = 32, kBlockLanesF32Walk = 8, kBlockLanesF64 = 4;
 constexpr int kDensityCounter = 16, kForceCounter = 32, kDensityWrapCounter = 40, kForceWrapCounter = 56,
               kForceCdCounter = 64;
 constexpr int kDensityClasses = 16, kForceClasses = 8;

@@ -33,6 +33,8 @@ namespace sph {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
+// class index of a lanes-per-particle count; 32 (block-step tasks, one
+// particle per warp) shares 8's slot: a tick launches only its tasks' class
 __host__ __device__ constexpr int lpp_log2(int l) { return l == 1 ? 0 : l == 2 ? 1 : l == 4 ? 2 : 3; }
 constexpr double kListMargin = 1.03;  // list radius = R_K h * margin (R_K: support in units of h)
 
@@ -859,7 +861,7 @@ __device__ __forceinline__ bool density_leaf(const BatchView &b, int leaf, int k
                         r = r2;
                         mj = c.w;
                     }
-                    const unsigned gm = (__ballot_sync(FULL, hit) >> (pp * LPP)) & ((1u << LPP) - 1u);
+                    const unsigned gm = (__ballot_sync(FULL, hit) >> (pp * LPP)) & (LPP == 32 ? FULL : (1u << (LPP & 31)) - 1u);
                     if (hit) {
                         const int e = gcnt + __popc(gm & below);
                         if (e < C::LCAP * LPP) {
@@ -1876,7 +1878,8 @@ cudaError_t run_forces(const BatchView &b, cudaStream_t st)
     k_forces<T, LPP, K, WRAP, CD><<<grid, C::WPB * 32, C::smem, st>>>(b);
     cudaError_t e = cudaGetLastError();
     // the Cullen & Dehnen problems' leaves on the wrap list: their own launch
-    if constexpr (WRAP && !CD)
+    // (never with block steps, the only users of whole-warp particles)
+    if constexpr (WRAP && !CD && LPP != 32)
         if (e == cudaSuccess && b.any_cd) e = run_forces<T, LPP, K, true, true>(b, st);
     return e;
 }
@@ -1906,7 +1909,16 @@ cudaError_t density_classes(const BatchView &b, int precision, int use_pred, cud
                 [[fallthrough]];  // (M6 never runs one lane per particle)
             case 1: e = um ? run_density<float, 2, true, K, WRAP>(b, use_pred, st) : run_density<float, 2, false, K, WRAP>(b, use_pred, st); break;
             case 2: e = um ? run_density<float, 4, true, K, WRAP>(b, use_pred, st) : run_density<float, 4, false, K, WRAP>(b, use_pred, st); break;
-            default: e = um ? run_density<float, 8, true, K, WRAP>(b, use_pred, st) : run_density<float, 8, false, K, WRAP>(b, use_pred, st); break;
+            default:
+                // block-step tasks of one particle with a whole warp (M4, FP32)
+                if constexpr (K == SPH_KERNEL_M4 && WRAP) {
+                    if (b.block_on && b.block_tasks && b.block_lanes == 32) {
+                        e = um ? run_density<float, 32, true, K, WRAP>(b, use_pred, st) : run_density<float, 32, false, K, WRAP>(b, use_pred, st);
+                        break;
+                    }
+                }
+                e = um ? run_density<float, 8, true, K, WRAP>(b, use_pred, st) : run_density<float, 8, false, K, WRAP>(b, use_pred, st);
+                break;
             }
         }
         if (e != cudaSuccess) return e;
@@ -1935,7 +1947,15 @@ cudaError_t force_classes(const BatchView &b, int precision, cudaStream_t st)
                 [[fallthrough]];
             case 1: e = run_forces<float, 2, K, WRAP>(b, st); break;
             case 2: e = run_forces<float, 4, K, WRAP>(b, st); break;
-            default: e = run_forces<float, 8, K, WRAP>(b, st); break;
+            default:
+                if constexpr (K == SPH_KERNEL_M4 && WRAP) {
+                    if (b.block_on && b.block_tasks && b.block_lanes == 32) {
+                        e = run_forces<float, 32, K, WRAP>(b, st);
+                        break;
+                    }
+                }
+                e = run_forces<float, 8, K, WRAP>(b, st);
+                break;
             }
         }
         if (e != cudaSuccess) return e;
