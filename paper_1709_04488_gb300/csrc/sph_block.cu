@@ -266,13 +266,34 @@ __global__ void __launch_bounds__(kBlockThreads) k_block_kick(BatchView b, int L
         double *V[3] = {ps.vx, ps.vy, ps.vz};
         int t0 = b.bt0[g], t1 = b.bt1[g], lev = b.blev[g];
         if (t1 == k) {
+            // every input first (the stores below could alias them for the
+            // compiler: one memory round trip each), the kicked v, u and
+            // alpha kept for the next half kick
+            const bool sw = ph.av_switch != 0, more = k < N;
             const double hd = half_ticks(t1 - t0, tau);
-            for (int a = 0; a < 3; ++a) V[a][i] = block_kick(b.bvh[a * n + g], A[a][i], hd);
-            if (adi) ps.u[i] = block_kick(b.bvh[3 * n + g], ps.du[i], hd);
-            if (ph.av_switch) ps.alpha[i] = block_kick(b.bvh[4 * n + g], ps.dalpha[i], hd);
-            if (k < N) {
-                int l = level_of(particle_dt(ps, i), dtmax, L);
-                const int lim = b.bnml[g] - ph.block_gap;
+            const double vh[3] = {b.bvh[g], b.bvh[n + g], b.bvh[2 * n + g]};
+            const double acc[3] = {A[0][i], A[1][i], A[2][i]};
+            const double uh = b.bvh[3 * n + g], du = adi ? ps.du[i] : 0.0;
+            const double ah = sw ? b.bvh[4 * n + g] : 0.0, da = sw ? ps.dalpha[i] : 0.0;
+            double u = adi ? 0.0 : ps.u[i];
+            const double dt = more ? particle_dt(ps, i) : 0.0;
+            const int nml = more ? b.bnml[g] : 0;
+            double v[3], al = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                v[a] = block_kick(vh[a], acc[a], hd);
+                V[a][i] = v[a];
+            }
+            if (adi) {
+                u = block_kick(uh, du, hd);
+                ps.u[i] = u;
+            }
+            if (sw) {
+                al = block_kick(ah, da, hd);
+                ps.alpha[i] = al;
+            }
+            if (more) {
+                int l = level_of(dt, dtmax, L);
+                const int lim = nml - ph.block_gap;
                 if (l < lim) l = lim;
                 if (l < lev)  // down one level, and only where synchronised
                     l = (k % (N >> (lev - 1)) == 0) ? lev - 1 : lev;
@@ -280,9 +301,9 @@ __global__ void __launch_bounds__(kBlockThreads) k_block_kick(BatchView b, int L
                 t0 = (int)k;
                 t1 = (int)(k + (N >> l));
                 const double hn = half_ticks(N >> l, tau);
-                for (int a = 0; a < 3; ++a) b.bvh[a * n + g] = block_kick(V[a][i], A[a][i], hn);
-                b.bvh[3 * n + g] = adi ? block_kick(ps.u[i], ps.du[i], hn) : ps.u[i];
-                if (ph.av_switch) b.bvh[4 * n + g] = block_kick(ps.alpha[i], ps.dalpha[i], hn);
+                for (int a = 0; a < 3; ++a) b.bvh[a * n + g] = block_kick(v[a], acc[a], hn);
+                b.bvh[3 * n + g] = adi ? block_kick(u, du, hn) : u;
+                if (sw) b.bvh[4 * n + g] = block_kick(al, da, hn);
             }
         } else {
             const int rq = b.breq[g];

@@ -216,31 +216,40 @@ __device__ __forceinline__ void leaf_props_one(const BatchView &b, int leaf)
 __device__ __forceinline__ double block_kick(double v, double a, double d) { return __dadd_rn(v, __dmul_rn(a, d)); }
 
 // drift particle g (original order) from tick k0 to tick k1 and predict
-// its v, u and alpha at k1 for the force pass; true if its step ends at k1
-__device__ __forceinline__ bool drift_one(const BatchView &b, long long g, long long k0, long long k1, double tau)
+// its v, u and alpha at k1 for the force pass; true if its step ends at k1.
+// Every input is read before the first store (which the compiler must
+// otherwise assume may alias the next input: one memory round trip per
+// axis); xo, if given, receives the drifted position.
+__device__ __forceinline__ bool drift_one(const BatchView &b, long long g, long long k0, long long k1, double tau,
+                                          double *xo = nullptr)
 {
     const ProbStatic &ps = b.prob[0];
     const PhysParams &ph = ps.ph;
     const long long i = g - ps.base, n = b.ntot;
-    const double dk = __dmul_rn((double)(k1 - k0), tau);
-    double *X[3] = {ps.x, ps.y, ps.z};
-    const double *A[3] = {ps.ax, ps.ay, ps.az};
-    double *VP[3] = {b.vpx, b.vpy, b.vpz};
+    const bool adi = ph.eos == SPH_EOS_ADIABATIC, sw = ph.av_switch != 0;
     const int t0 = b.bt0[g], t1 = b.bt1[g];
+    const double x0[3] = {ps.x[i], ps.y[i], ps.z[i]};
+    const double vh[3] = {b.bvh[g], b.bvh[n + g], b.bvh[2 * n + g]};
+    const double acc[3] = {ps.ax[i], ps.ay[i], ps.az[i]};
+    const double uh = adi ? b.bvh[3 * n + g] : 0.0, du = adi ? ps.du[i] : 0.0, u = adi ? 0.0 : ps.u[i];
+    const double ah = sw ? b.bvh[4 * n + g] : 0.0, da = sw ? ps.dalpha[i] : 0.0;
+    const double dk = __dmul_rn((double)(k1 - k0), tau);
     const double dp = __dmul_rn(__dmul_rn((double)(2 * k1 - t0 - t1), 0.5), tau);  // t - t_mid
+    double *X[3] = {ps.x, ps.y, ps.z};
+    double *VP[3] = {b.vpx, b.vpy, b.vpz};
     for (int a = 0; a < 3; ++a) {
-        const double vh = b.bvh[a * n + g];
-        double x = __dadd_rn(X[a][i], __dmul_rn(vh, dk));
+        double x = __dadd_rn(x0[a], __dmul_rn(vh[a], dk));
         if (ph.periodic) {
             const double lo = ph.box_lo[a], Lb = ph.box_len[a];
             if (x >= lo + Lb) x -= Lb;
             else if (x < lo) x += Lb;
         }
         X[a][i] = x;
-        VP[a][g] = block_kick(vh, A[a][i], dp);
+        if (xo) xo[a] = x;
+        VP[a][g] = block_kick(vh[a], acc[a], dp);
     }
-    b.up[g] = ph.eos == SPH_EOS_ADIABATIC ? block_kick(b.bvh[3 * n + g], ps.du[i], dp) : ps.u[i];
-    if (ph.av_switch) b.ap[g] = block_kick(b.bvh[4 * n + g], ps.dalpha[i], dp);
+    b.up[g] = adi ? block_kick(uh, du, dp) : u;
+    if (sw) b.ap[g] = block_kick(ah, da, dp);
     b.breq[g] = -1;
     return t1 == k1;
 }

@@ -1843,13 +1843,16 @@ __global__ void __launch_bounds__(256) k_block_leaf_tick(BatchView b, int use_pr
         if (lane < n) {
             const ProbStatic &ps = b.prob[0];
             const long long g = b.perm[s], i = g - ps.base;
-            due = drift_one(b, g, k0, k1, tau);
-            b.sx[s] = ps.x[i];
-            b.sy[s] = ps.y[i];
-            b.sz[s] = ps.z[i];
-            b.sm[s] = ps.m[i];
-            b.sh[s] = ps.h[i];
-            const T v = (T)(b.blev[g] + 1);
+            const double m = ps.m[i], h = ps.h[i];  // (read with the drift's inputs, not after its stores)
+            const int lv = b.blev[g];
+            double x[3];
+            due = drift_one(b, g, k0, k1, tau, x);
+            b.sx[s] = x[0];
+            b.sy[s] = x[1];
+            b.sz[s] = x[2];
+            b.sm[s] = m;
+            b.sh[s] = h;
+            const T v = (T)(lv + 1);
             ((T *)b.slev)[s] = due ? v : -v;
         }
         const unsigned dm = __ballot_sync(FULL, due);
