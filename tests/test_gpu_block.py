@@ -120,6 +120,30 @@ def test_two_block_steps_and_limiter_history(S, oracle_mod):
         assert _scale_err(g, ref, f) < 1e-9, f
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_m6_block_step_matches_oracle(S, oracle_mod, prec):
+    """The M6 kernel (support 3h, eta = 1) in block steps: in mixed precision
+    its tasks are up to 4 particles with 8 lanes each (the M4 kernel's take a
+    whole warp per particle); the same levels and evaluations as the oracle
+    and the state at the norms of one evaluation."""
+    O = oracle_mod
+    a, p = ics.sedov(14, seed=3)
+    a["h"] = a["h"] / 1.2  # (the M6 lattice spacing guess)
+    p = dict(p, kernel=1, eta=1.0)
+    L = 4
+    ref, lv_ref, oo = _oracle_block(O, a, p, L)
+    fp64 = prec == "fp64"
+    prob, go = _gpu_block(S, a, p, S.PREC_FP64 if fp64 else S.PREC_MIXED, L)
+    assert np.array_equal(prob.levels(), lv_ref)
+    assert go[0][1] == oo[0][1] and go[0][1] < len(a["x"]) * 2 ** L
+    g = prob.numpy()
+    tol = 1e-12 if fp64 else 1e-5
+    for f in ("vx", "vy", "vz", "u"):
+        assert _scale_err(g, ref, f) < tol, f
+    assert np.max(np.abs(g["rho"] / ref.rho - 1.0)) < tol
+    assert _a_err(g, ref) < (1e-11 if fp64 else 1e-4)
+
+
 def _gravity_block_case(n=3000, seed=93):
     a, p = ics.cloud(n, seed=seed)
     rng = np.random.default_rng(seed)
