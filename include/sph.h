@@ -449,7 +449,8 @@ int sph_density_forces_noalloc(const sph_params *p, int64_t n, const sph_state *
  * leaf_size at 0: a problem of n particles uses lanes[k] lanes per particle
  * (leaf size 32 / lanes[k]) for the first row k with n <= n_max[k]; sizes
  * beyond the last row, and every size when rows == 0 (the state at load
- * time), use the built-in rule (4 lanes up to 200000 particles, else 1).
+ * time), use the built-in rule (2 lanes up to 67023 particles, else 1: the
+ * table the package's autotuner measured on GB300).
  * The table is process-wide and copied; it applies to contexts set up after
  * the call.  lanes[k] must be 1, 2, 4 or 8 and n_max must increase;
  * otherwise SPH_EINVAL and the table is unchanged.  At most 32 rows.  The
