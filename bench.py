@@ -65,6 +65,7 @@ GRAVITY_TREE_N = 1_000_000  # the tree walk's larger cloud
 GRAVITY_THETA = 0.5       # opening angle of the tree-walk measurements
 BLOCK_SEDOV_SIDE = 64     # block time-step measurement: Sedov blast on 64^3 particles
 BLOCK_LEVELS = 6
+E2E_COPIES = 3            # resident copies of the workload in the pipelined end-to-end measurement
 
 
 def parse():
@@ -536,26 +537,29 @@ def run_ours(args):
         stream.synchronize()
         e2e_ms += e0.elapsed_time(e1)
     e2e_serial = world * n * Ke / (e2e_ms * 1e-3)
-    # the same, pipelined: two resident copies of the workload, each on its
-    # own stream, take the steps in turn, so that one copy's host transfers
-    # run on the copy engines while the other's step runs on the SMs (every
-    # step still uploads its input state and reads back its result).  Two
-    # untimed rounds first: the first transfers into freshly pinned buffers
-    # and the first overlapped steps run several times slower than later ones
+    # the same, pipelined: E2E_COPIES resident copies of the workload, each
+    # on its own stream, take the steps in turn, so that one copy's host
+    # transfers run on the copy engines while the others' steps run on the
+    # SMs (every step still uploads its input state and reads back its
+    # result); a third copy gives a transfer that stalls on the host two
+    # steps' time to finish.  Two untimed rounds first: the first transfers
+    # into freshly pinned buffers and the first overlapped steps run several
+    # times slower than later ones
     e2e_pipe = None
     if world == 1:
-        stream2 = torch.cuda.Stream(dev)
-        with torch.cuda.stream(stream2):
-            prob2 = S.Problem(a, prm, device=dev, stream=stream2)
-            S.check(S.sph_density_h(prob2.ctx), "sph_density_h")
-            S.check(S.sph_forces(prob2.ctx), "sph_forces")
-        S.check(S.sph_run(prob2.ctx, 1), "sph_run")
-        host2 = {f: prob2.t[f][:n].cpu().pin_memory() for f in set(fields_in + fields_out)}
-        pairs = ((prob, stream, host), (prob2, stream2, host2))
+        copies = [(prob, stream, host)]
+        for _ in range(E2E_COPIES - 1):
+            sk = torch.cuda.Stream(dev)
+            with torch.cuda.stream(sk):
+                pk = S.Problem(a, prm, device=dev, stream=sk)
+                S.check(S.sph_density_h(pk.ctx), "sph_density_h")
+                S.check(S.sph_forces(pk.ctx), "sph_forces")
+            S.check(S.sph_run(pk.ctx, 1), "sph_run")
+            copies.append((pk, sk, {f: pk.t[f][:n].cpu().pin_memory() for f in set(fields_in + fields_out)}))
 
         def pipelined(nsteps):
             for k in range(nsteps):
-                pr, sk, hk = pairs[k % 2]
+                pr, sk, hk = copies[k % len(copies)]
                 with torch.cuda.stream(sk):
                     for f in fields_in:
                         pr.t[f][:n].copy_(hk[f], non_blocking=True)
@@ -564,20 +568,21 @@ def run_ours(args):
                     for f in fields_out:
                         hk[f].copy_(pr.t[f][:n], non_blocking=True)
 
-        pipelined(4)  # warm-up: two steps of each copy
+        pipelined(2 * len(copies))  # warm-up: two steps of each copy
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        pipelined(2 * Ke)
+        pipelined(len(copies) * Ke)
         torch.cuda.synchronize(dev)
-        e2e_pipe = n * 2 * Ke / (time.perf_counter() - t0)
-        prob2.close()
-        del host2
+        e2e_pipe = n * len(copies) * Ke / (time.perf_counter() - t0)
+        for pk, _, _ in copies[1:]:
+            pk.close()
+        del copies
     e2e = {"value": e2e_pipe if e2e_pipe is not None else e2e_serial, "unit": UNIT,
            "h2d_bytes_per_step": 8 * n * len(fields_in), "d2h_bytes_per_step": 8 * n * len(fields_out),
            "serial": e2e_serial,
-           "timing": ("two resident copies alternating on two streams (one's transfers overlap the other's step), "
-                      "host wall clock over all steps after two untimed steps of each copy" if e2e_pipe is not None else
-                      "one copy: upload, step, read back, CUDA events per step")}
+           "timing": (f"{E2E_COPIES} resident copies taking the steps in turn on their own streams (one's transfers "
+                      "overlap the others' steps), host wall clock over all steps after two untimed steps of each copy"
+                      if e2e_pipe is not None else "one copy: upload, step, read back, CUDA events per step")}
 
     # plain FP64 single-problem GPU path on the same workload
     fp64 = None
