@@ -27,7 +27,7 @@ int sort_items(long long n)
 {
     return n <= (1ll << 18) ? SPH_SORT_ITEMS_S : n <= (1ll << 22) ? SPH_SORT_ITEMS_M : SPH_SORT_ITEMS_L;
 }
-constexpr int kBboxThreads = 1024;
+constexpr int kBboxThreads = 1024, kBboxItems = 64;
 
 __device__ __forceinline__ unsigned spread10(unsigned v)
 {
@@ -61,67 +61,77 @@ __global__ void k_reset_bbox(ProbDyn *dyn, int nprob)
     }
 }
 
-// Bounding box of isolated problems (FP64, ordered-integer atomics after a
-// block reduction when the whole block belongs to one problem).
-__global__ void k_bbox(BatchView b)
+// Bounding box of isolated problems (FP64, ordered-integer atomics).  Each
+// block takes items * blockDim consecutive particles, kept per problem in
+// registers; a block within one problem reduces over the block (one set of
+// atomics per block), else each thread adds its own on a change of problem.
+__device__ __forceinline__ void bbox_flush(const BatchView &b, int p, const unsigned long long *v)
+{
+    if (v[0] == ~0ull) return;  // nothing of an isolated problem seen
+    for (int a = 0; a < 3; ++a) {
+        atomicMin(&b.dyn[p].bbox_bits[a], v[a]);
+        atomicMax(&b.dyn[p].bbox_bits[3 + a], v[3 + a]);
+    }
+}
+
+__global__ void k_bbox(BatchView b, int items)
 {
     __shared__ unsigned long long red[6][kBboxThreads / 32];
-    __shared__ int uniform_p;
-    long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    int p = -1;
-    unsigned long long v[6];
-    for (int a = 0; a < 3; ++a) {
-        v[a] = ~0ull;
-        v[3 + a] = 0ull;
+    __shared__ int pfirst, plast;
+    const long long base = (long long)blockIdx.x * blockDim.x * items;
+    if (base >= b.ntot) return;
+    const long long end = base + (long long)blockDim.x * items < b.ntot ? base + (long long)blockDim.x * items : b.ntot;
+    if (threadIdx.x == 0) {
+        pfirst = find_problem(b.prob_base, b.nprob, base);
+        plast = find_problem(b.prob_base, b.nprob, end - 1);
     }
-    if (g < b.ntot) {
-        p = find_problem(b.prob_base, b.nprob, g);
-        const ProbStatic &ps = b.prob[p];
-        if (!ps.ph.periodic) {
-            long long i = g - ps.base;
-            double X[3] = {ps.x[i], ps.y[i], ps.z[i]};
+    __syncthreads();
+    unsigned long long v[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
+    int cur = -1;
+    for (long long g = base + threadIdx.x; g < end; g += blockDim.x) {
+        const int p = pfirst == plast ? pfirst : find_problem(b.prob_base, b.nprob, g);
+        if (p != cur) {
+            if (cur >= 0) bbox_flush(b, cur, v);
             for (int a = 0; a < 3; ++a) {
-                v[a] = ordered_bits(X[a]);
-                v[3 + a] = v[a];
+                v[a] = ~0ull;
+                v[3 + a] = 0ull;
             }
-        } else {
-            p = -2;  // nothing to do
+            cur = p;
+        }
+        const ProbStatic &ps = b.prob[p];
+        if (ps.ph.periodic) continue;  // (periodic boxes need no pass)
+        const long long i = g - ps.base;
+        const unsigned long long X[3] = {ordered_bits(ps.x[i]), ordered_bits(ps.y[i]), ordered_bits(ps.z[i])};
+        for (int a = 0; a < 3; ++a) {
+            v[a] = X[a] < v[a] ? X[a] : v[a];
+            v[3 + a] = X[a] > v[3 + a] ? X[a] : v[3 + a];
         }
     }
-    if (threadIdx.x == 0) uniform_p = p;
+    if (pfirst != plast) {
+        if (cur >= 0) bbox_flush(b, cur, v);
+        return;
+    }
+    for (int a = 0; a < 6; ++a) {
+        unsigned long long x = v[a];
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
+            x = a < 3 ? (y < x ? y : x) : (y > x ? y : x);
+        }
+        if ((threadIdx.x & 31) == 0) red[a][threadIdx.x >> 5] = x;
+    }
     __syncthreads();
-    int p0 = uniform_p;
-    bool uni = __syncthreads_and(p == p0 || p == -1);
-    if (uni) {
-        if (p0 < 0) return;
+    if (threadIdx.x < 32) {
+        const int nw = blockDim.x >> 5;
+        unsigned long long w[6];
         for (int a = 0; a < 6; ++a) {
-            unsigned long long x = v[a];
+            unsigned long long x = threadIdx.x < nw ? red[a][threadIdx.x] : (a < 3 ? ~0ull : 0ull);
             for (int o = 16; o > 0; o >>= 1) {
-                unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
+                const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
                 x = a < 3 ? (y < x ? y : x) : (y > x ? y : x);
             }
-            if ((threadIdx.x & 31) == 0) red[a][threadIdx.x >> 5] = x;
+            w[a] = x;
         }
-        __syncthreads();
-        if (threadIdx.x < 32) {
-            int nw = blockDim.x >> 5;
-            for (int a = 0; a < 6; ++a) {
-                unsigned long long x = threadIdx.x < nw ? red[a][threadIdx.x] : (a < 3 ? ~0ull : 0ull);
-                for (int o = 16; o > 0; o >>= 1) {
-                    unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
-                    x = a < 3 ? (y < x ? y : x) : (y > x ? y : x);
-                }
-                if (threadIdx.x == 0) {
-                    if (a < 3) atomicMin(&b.dyn[p0].bbox_bits[a], x);
-                    else atomicMax(&b.dyn[p0].bbox_bits[a], x);
-                }
-            }
-        }
-    } else if (p >= 0) {
-        for (int a = 0; a < 3; ++a) {
-            atomicMin(&b.dyn[p].bbox_bits[a], v[a]);
-            atomicMax(&b.dyn[p].bbox_bits[3 + a], v[3 + a]);
-        }
+        if (threadIdx.x == 0) bbox_flush(b, pfirst, w);
     }
 }
 
@@ -324,8 +334,12 @@ cudaError_t launch_domain_and_keys(const BatchView &b, cudaStream_t st)
     if (b.ntot == 0 || !b.any_isolated) return cudaSuccess;
     int pb = (b.nprob + 127) / 128;
     k_reset_bbox<<<pb, 128, 0, st>>>(b.dyn, b.nprob);
-    long long nb = (b.ntot + kBboxThreads - 1) / kBboxThreads;
-    k_bbox<<<(unsigned)nb, kBboxThreads, 0, st>>>(b);
+    // two blocks per SM of up to kBboxItems particles a thread
+    const long long fill = 2LL * dev_info().sm_count * kBboxThreads;
+    long long items = (b.ntot + fill - 1) / fill;
+    items = items < 1 ? 1 : items > kBboxItems ? kBboxItems : items;
+    const long long nb = (b.ntot + kBboxThreads * items - 1) / (kBboxThreads * items);
+    k_bbox<<<(unsigned)nb, kBboxThreads, 0, st>>>(b, (int)items);
     k_domain<<<pb, 128, 0, st>>>(b);
     return cudaGetLastError();
 }
