@@ -37,7 +37,7 @@ __global__ void k_gather(BatchView b)
     b.sx[s] = ps.x[i];
     b.sy[s] = ps.y[i];
     b.sz[s] = ps.z[i];
-    b.sm[s] = ps.m[i];
+    b.sm[s] = ps.uniform_m ? ps.m_uniform : ps.m[i];  // (equal masses: no random read)
     b.sh[s] = ps.h[i];
 }
 

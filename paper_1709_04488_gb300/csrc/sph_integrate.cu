@@ -49,14 +49,22 @@ __global__ void k_kick_drift(BatchView b, double dt_host)
     const PhysParams &ph = ps.ph;
     long long i = g - ps.base;
     const double dt = step_dt(ps.diag, dt_host), hdt = 0.5 * dt;
-    double a[3] = {ps.ax[i], ps.ay[i], ps.az[i]};
+    // every input first (the stores below could alias them for the
+    // compiler: one memory round trip each)
+    const bool adi = ph.eos == SPH_EOS_ADIABATIC, mm = ph.av_switch == SPH_AV_MORRIS_MONAGHAN;
+    const double a[3] = {ps.ax[i], ps.ay[i], ps.az[i]};
+    const double v0[3] = {ps.vx[i], ps.vy[i], ps.vz[i]};
+    const double x0[3] = {ps.x[i], ps.y[i], ps.z[i]};
+    const double u = ps.u[i], du = adi ? ps.du[i] : 0.0, h0 = ps.h[i];
+    const float dv = b.divv ? b.divv[g] : 0.f;
+    const double al0 = mm ? ps.alpha[i] : 0.0, dal = mm ? ps.dalpha[i] : 0.0;
     double *X[3] = {ps.x, ps.y, ps.z};
     double *Vv[3] = {ps.vx, ps.vy, ps.vz};
     double *VP[3] = {b.vpx, b.vpy, b.vpz};
     for (int k = 0; k < 3; ++k) {
-        double vh = Vv[k][i] + hdt * a[k];
+        double vh = v0[k] + hdt * a[k];
         Vv[k][i] = vh;
-        double x = X[k][i] + vh * dt;
+        double x = x0[k] + vh * dt;
         if (ph.periodic) {
             double lo = ph.box_lo[k], L = ph.box_len[k];
             if (x >= lo + L) x -= L;
@@ -68,21 +76,20 @@ __global__ void k_kick_drift(BatchView b, double dt_host)
     // the h iteration starts from the continuity equation's prediction,
     // h exp(div v dt / 3) (h ~ rho^-1/3), bounded to a factor 1.25
     if (b.divv) {
-        const float e = (float)(dt * (1.0 / 3.0)) * b.divv[g];
-        ps.h[i] *= (double)expf(fminf(fmaxf(e, -0.223f), 0.223f));  // (a starting guess: FP32 is enough)
+        const float e = (float)(dt * (1.0 / 3.0)) * dv;
+        ps.h[i] = h0 * (double)expf(fminf(fmaxf(e, -0.223f), 0.223f));  // (a starting guess: FP32 is enough)
     }
-    double u = ps.u[i];
-    if (ph.eos == SPH_EOS_ADIABATIC) {
-        double uh = u + hdt * ps.du[i];
+    if (adi) {
+        double uh = u + hdt * du;
         ps.u[i] = uh;
-        b.up[g] = uh + hdt * ps.du[i];
+        b.up[g] = uh + hdt * du;
     } else {
         b.up[g] = u;
     }
-    if (ph.av_switch == SPH_AV_MORRIS_MONAGHAN) {  // the switch's alpha is kicked and predicted like u
-        const double ah = ps.alpha[i] + hdt * ps.dalpha[i];
+    if (mm) {  // the switch's alpha is kicked and predicted like u
+        const double ah = al0 + hdt * dal;
         ps.alpha[i] = ah;
-        b.ap[g] = ah + hdt * ps.dalpha[i];
+        b.ap[g] = ah + hdt * dal;
     }
 }
 
